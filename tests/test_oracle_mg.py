@@ -1,0 +1,172 @@
+"""Pins of the oracle's adaptive FAS V-cycle (Alg. 1)."""
+import numpy as np
+import pytest
+
+from paper_2512_08555_gb300 import synth
+from oracle.forest import OracleForest
+from oracle.multigrid import OracleSolver
+from oracle.composite import CompositeSystem
+from oracle.lgf import free_space_solve, direct_sum
+from oracle.stencils import rhs_stencil
+from oracle.closed_forms import manufactured_unb
+
+
+def _all(level, coords):
+    return np.ones(len(coords), bool)
+
+
+def _forest(nb, n, max_level, lo=-1.0, L=2.0):
+    desc = synth.adaptive_forest((nb, nb, nb), n, (lo, lo, lo), L / (nb * n), max_level, _all)
+    return desc, OracleForest.from_desc(desc)
+
+
+def _bumps():
+    return synth.c4_bumps(0, k=3, r_lo=0.2, r_hi=0.3)
+
+
+def test_forest_validation_rejects_bad_forests():
+    desc, fo = _forest(4, 8, 1)
+    lev, ijk = desc.leaf_level.copy(), desc.leaf_ijk.copy()
+    # refine a boundary block: drop level-0 leaf (0,0,0), add its 8 children
+    keep = ~((lev == 0) & np.all(ijk == 0, axis=1))
+    kids = np.array([(o & 1, (o >> 1) & 1, (o >> 2) & 1) for o in range(8)], np.int32)
+    with pytest.raises(ValueError, match="boundary"):
+        OracleForest((4, 4, 4), 8, desc.origin, desc.h0, np.concatenate([lev[keep], np.ones(8, np.int32)]),
+                     np.concatenate([ijk[keep], kids]))
+    with pytest.raises(ValueError, match="tile"):
+        OracleForest((4, 4, 4), 8, desc.origin, desc.h0, lev[1:], ijk[1:])
+    with pytest.raises(ValueError, match="even"):
+        OracleForest((4, 4, 4), 9, desc.origin, desc.h0, lev, ijk)
+    # 2:1 violation: refine one interior level-1 block twice more in a 3-level setting
+    d3, _ = _forest(4, 8, 1)
+    l1 = np.nonzero(d3.leaf_level == 1)[0][0]
+    c = d3.leaf_ijk[l1]
+    g = np.array([(2 * c[0] + (o & 1), 2 * c[1] + ((o >> 1) & 1), 2 * c[2] + ((o >> 2) & 1)) for o in range(8)])
+    lev2 = np.concatenate([np.delete(d3.leaf_level, l1), np.full(8, 2)])
+    ijk2 = np.concatenate([np.delete(d3.leaf_ijk, l1, axis=0), g])
+    with pytest.raises(ValueError, match="2:1"):
+        OracleForest((4, 4, 4), 8, d3.origin, d3.h0, lev2, ijk2)
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_single_level_is_one_direct_solve(lgf_cache, M):
+    """On a uniform level the cycle is the LGF solve of f* = R^M f; its residual is rounding."""
+    desc, src = synth.config1(0, n0=16, n=8)
+    fo = OracleForest.from_desc(desc)
+    f = synth.sample_leaves(desc, src)
+    s = OracleSolver(fo, M, G=lgf_cache(M, 17))
+    u, rel = s.solve(f, tol=1e-12, max_cycles=3)
+    assert s.cycles_done == 1 and rel < 1e-13
+    # brute-force direct Green's summation of R^M f on the full 16^3 problem
+    h = desc.h0
+    x = (np.arange(-2, 18)) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    fz = src(X, Y, Z)
+    inside = np.zeros_like(fz, bool)
+    inside[2:18, 2:18, 2:18] = True
+    fz = np.where(inside, fz, 0.0)
+    fstar = np.zeros((16, 16, 16))
+    for (a, b, c), w in np.ndenumerate(rhs_stencil(M)):
+        fstar += w * fz[a:a + 16, b:b + 16, c:c + 16]
+    ref = direct_sum(fstar, lgf_cache(M, 17), h)[1:-1, 1:-1, 1:-1]
+    got = np.zeros((16, 16, 16))
+    for i, (lev, c) in enumerate(zip(desc.leaf_level, desc.leaf_ijk)):
+        got[c[2] * 8:c[2] * 8 + 8, c[1] * 8:c[1] * 8 + 8, c[0] * 8:c[0] * 8 + 8] = u[i]
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_vcycle_converges(lgf_cache, M):
+    desc, fo = _forest(4, 8, 2)
+    f = synth.sample_leaves(desc, _bumps())
+    s = OracleSolver(fo, M, G=lgf_cache(M, 33))
+    hist = []
+    s.solve(f, tol=1e-10, max_cycles=25, history=hist)
+    assert hist[-1] < 1e-10
+    rates = np.array(hist[1:]) / np.array(hist[:-1])
+    assert rates.max() < 0.3, rates
+
+
+def test_fixed_point_solves_composite_system_gmres(lgf_cache):
+    """The V-cycle limit equals the composite leaf system solved by GMRES (no multigrid)."""
+    desc, fo = _forest(3, 8, 1)
+    f = synth.sample_leaves(desc, synth.c4_bumps(1, k=2, r_lo=0.1, r_hi=0.15, box=0.3))
+    G = lgf_cache(4, 25)
+    s = OracleSolver(fo, 4, G=G)
+    u, rel = s.solve(f, tol=1e-14, max_cycles=40)
+    cs = CompositeSystem(OracleSolver(fo, 4, G=G), f)
+    x = cs.solve(rtol=1e-14)
+    assert cs.info == 0
+    ug = cs.leaf_values(x)
+    assert np.abs(u - ug).max() < 1e-12 * np.abs(ug).max()
+
+
+@pytest.mark.parametrize("M", [4, 6])
+def test_fixed_point_zero_composite_residual(lgf_cache, M):
+    """3-level forest: the converged V-cycle state has zero composite-system residual."""
+    desc, fo = _forest(4, 8, 2)
+    f = synth.sample_leaves(desc, _bumps())
+    G = lgf_cache(M, 33)
+    s = OracleSolver(fo, M, G=G)
+    s.solve(f, tol=1e-14, max_cycles=40)
+    cs = CompositeSystem(OracleSolver(fo, M, G=G), f)
+    n = fo.n
+    parts = [s.U[k][cs.leaf_sel[k], 1:1 + n, 1:1 + n, 1:1 + n].reshape(-1) for k in range(1, fo.max_level + 1)]
+    parts.append(s.F[0][cs.cov0].reshape(-1))
+    r = cs.residual(np.concatenate(parts))
+    fscale = max(np.abs(s.F[k]).max() for k in range(len(s.F)))
+    assert np.abs(r).max() < 1e-11 * fscale
+
+
+def test_incompatible_kernel_does_not_converge(lgf_cache):
+    """Sec. 3.3: with a kernel that is not the LGF of L the cycles stall."""
+    desc, fo = _forest(4, 8, 1)
+    f = synth.sample_leaves(desc, _bumps())
+    G = lgf_cache(4, 33).copy()
+    n = np.arange(G.shape[0])
+    r = np.sqrt(n[:, None, None] ** 2 + n[None, :, None] ** 2 + n[None, None, :] ** 2)
+    Gc = np.where(r > 0, -1.0 / (4 * np.pi * np.where(r > 0, r, 1.0)), G[0, 0, 0])
+    s = OracleSolver(fo, 4, G=Gc)
+    hist = []
+    s.solve(f, tol=1e-10, max_cycles=8, history=hist)
+    assert min(hist) > 1e-6
+    ok = OracleSolver(fo, 4, G=G)
+    h2 = []
+    ok.solve(f, tol=1e-10, max_cycles=8, history=h2)
+    assert min(h2) < 1e-7
+
+
+@pytest.mark.parametrize("M,min_order", [(2, 1.8), (4, 3.3)])
+def test_adaptive_convergence_order(lgf_cache, M, min_order):
+    """E_inf against the manufactured u_unb product decays like h^M under uniform refinement of a 2-level forest."""
+    errs = []
+    for n in (8, 16):
+        desc, fo = _forest(4, n, 1, lo=0.0, L=1.0)
+        f = synth.sample_leaves(desc, lambda x, y, z: manufactured_unb(x, y, z)[1])
+        uref = synth.sample_leaves(desc, lambda x, y, z: manufactured_unb(x, y, z)[0])
+        s = OracleSolver(fo, M, G=lgf_cache(M, 4 * n + 1))
+        u, _ = s.solve(f, tol=1e-9, max_cycles=30)
+        errs.append(np.abs(u - uref).max() / np.abs(uref).max())
+    assert np.log2(errs[0] / errs[1]) > min_order, errs
+
+
+def test_uniform_solve_operator_is_symmetric(lgf_cache):
+    """<v, S w> = <S v, w> for S f = h^2 G * (R^M f) with v, w supported away from the boundary."""
+    rng = np.random.default_rng(3)
+    N = 12
+    G = lgf_cache(6, N + 1)
+    R = rhs_stencil(6)
+
+    def S(v):
+        pad = np.zeros((N + 4,) * 3)
+        pad[2:-2, 2:-2, 2:-2] = v
+        fstar = np.zeros((N,) * 3)
+        for (a, b, c), w in np.ndenumerate(R):
+            fstar += w * pad[a:a + N, b:b + N, c:c + N]
+        return free_space_solve(fstar, G, 0.1)[1:-1, 1:-1, 1:-1]
+    v = np.zeros((N,) * 3)
+    w = np.zeros((N,) * 3)
+    v[2:-2, 2:-2, 2:-2] = rng.normal(size=(N - 4,) * 3)
+    w[2:-2, 2:-2, 2:-2] = rng.normal(size=(N - 4,) * 3)
+    a, b = np.vdot(v, S(w)), np.vdot(S(v), w)
+    assert abs(a - b) < 1e-13 * max(abs(a), 1.0)
