@@ -1,0 +1,135 @@
+/*
+ * mrp: free-space (unbounded) Poisson solver on a block-structured adaptive
+ * forest, by an adaptive FAS multigrid V-cycle coupled to a zero-padded FFT
+ * lattice-Green's-function convolution on the uniform level 0.
+ *
+ * Method: arXiv 2512.08555 -- Alg. 1 (adaptive V(nu1,nu2) FAS cycle),
+ * Sec. 3.2 Eqs. cross_discr2 / mehrstellen_discr4 / mehrstellen_discr6
+ * (compact stencils of order 2, 4, 6 and the RHS operator R^M),
+ * Sec. 2.1 (ghosting with polynomial interpolation of order M+2 at
+ * resolution jumps), Sec. 3.1 (injection, full weighting, trilinear
+ * prolongation, Gauss-Seidel smoothing), Sec. 2.2 and 3.3 (the level-0
+ * direct solve is the convolution with the lattice Green's function of the
+ * multigrid operator).
+ *
+ * The problem solved is  nabla^2 u = f  (Eq. 1) with u -> 0 at infinity.
+ *
+ * Geometry.  Level 0 is a grid of nb0[0] x nb0[1] x nb0[2] cubic blocks of
+ * n^3 nodes, spacing h0, lower corner origin.  A block at level k with block
+ * coordinates (bx, by, bz) holds the nodes origin + (b*n + i) * h0/2^k,
+ * i = 0..n-1 per axis (vertex-centred, half-open).  A forest is given by its
+ * leaves; every leaf is (level, bx, by, bz).  Constraints (checked by
+ * mrp_create, MRP_ERR_INVALID_FOREST otherwise): leaves tile the domain
+ * without overlap; 2:1 balance across faces, edges and corners; level-0
+ * blocks that touch the domain boundary are leaves (Sec. 3.3); n even,
+ * 8 <= n <= 24.
+ *
+ * Field layout.  f and u are [leaf, in the order given to mrp_create][z][y][x]
+ * with x fastest, n^3 doubles per leaf.
+ *
+ * Errors.  Every entry point returns an int status (MRP_OK = 0); no
+ * exception or abort crosses this interface.  mrp_error_string maps a
+ * status to a static string.
+ *
+ * Threading.  A handle is not thread-safe; use it from one host thread and
+ * one stream at a time.
+ */
+#ifndef MRP_H
+#define MRP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MRP_OK = 0,
+    MRP_ERR_INVALID_ARG = 1,     /* null pointer, bad option value */
+    MRP_ERR_INVALID_FOREST = 2,  /* forest violates a constraint listed above */
+    MRP_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+    MRP_ERR_OOM = 4,             /* device allocation failed */
+    MRP_ERR_NOT_CONVERGED = 5,   /* max_cycles reached before the tolerance */
+    MRP_ERR_TIMEOUT = 6,         /* a bounded device wait ran out */
+    MRP_ERR_NUMERICAL = 7,       /* NaN or Inf in the residual norm */
+    MRP_ERR_NO_FORWARD = 8,      /* adjoint requested before a forward solve */
+    MRP_ERR_UNSUPPORTED = 9      /* option combination not built */
+};
+
+enum { MRP_FP64 = 0, MRP_MIXED = 1 };
+enum { MRP_STOP_RESIDUAL = 0, MRP_STOP_CAUCHY = 1 };
+
+typedef struct {
+    int32_t nb0[3];              /* level-0 blocks per axis (x, y, z) */
+    int32_t n;                   /* nodes per block edge */
+    double origin[3];            /* position of level-0 node (0,0,0) */
+    double h0;                   /* level-0 node spacing */
+    int32_t n_leaves;
+    const int32_t* leaf_level;   /* host, [n_leaves] */
+    const int32_t* leaf_ijk;     /* host, [n_leaves][3] block coords (x, y, z) at the leaf's level */
+    int32_t ncomp;               /* right-hand sides sharing this forest (>= 1) */
+} mrp_forest;
+
+typedef struct {
+    int32_t order;               /* M = 2, 4 or 6 */
+    double tol;                  /* stop when the rule below falls under tol */
+    int32_t stop_rule;           /* MRP_STOP_RESIDUAL: max|f* - L u| / max|f*| over leaf nodes
+                                    MRP_STOP_CAUCHY:   max|u_n - u_{n+1}| / max|u_{n+1}| (Sec. 3.4) */
+    int32_t max_cycles;          /* >= 1 */
+    int32_t nu1, nu2;            /* pre- and post-smoothing sweeps, >= 0 */
+    int32_t precision;           /* MRP_FP64 (only value built so far) */
+    double mixed_target;         /* reserved */
+    int64_t spin_budget;         /* reserved */
+} mrp_options;
+
+typedef struct {
+    int32_t cycles;              /* V-cycles run */
+    int32_t ir_steps;            /* outer refinement steps (0 for MRP_FP64) */
+    double residual;             /* final relative residual (stop rule RESIDUAL) */
+    double cauchy;               /* final relative increment (stop rule CAUCHY) */
+    double fstar_max;            /* max |f*| over leaf nodes */
+    int64_t leaf_nodes;          /* unknowns of the composite grid */
+    int64_t total_nodes;         /* nodes over all levels */
+    int64_t launches;            /* kernels launched by this call */
+} mrp_stats;
+
+typedef struct mrp_handle mrp_handle;
+
+/* Build a solver for n_forests forests (only n_forests == 1 is built).
+ * Validates the forest, builds per-level block tables and the ghost plan,
+ * allocates every device workspace, tabulates the lattice Green's function
+ * of the order-M operator in FP64 on the device (Sec. 2.2, 3.3) and its
+ * spectrum on the padded level-0 lattice.  Uses the current CUDA device.
+ * On failure *out is NULL and nothing is leaked. */
+int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, const mrp_options* opt);
+
+/* Solve nabla^2 u = f from u = 0.  f, u: device pointers, layout above.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Allocates nothing;
+ * synchronises the stream once per cycle to read the stop criterion.
+ * st may be NULL.  Returns MRP_ERR_NOT_CONVERGED (u still written) when
+ * max_cycles ran out. */
+int mrp_solve(mrp_handle* h, const double* f, double* u, void* stream, mrp_stats* st);
+
+/* Adjoint solve (f-bar = S^T w).  Not built yet: MRP_ERR_UNSUPPORTED. */
+int mrp_solve_adjoint(mrp_handle* h, const double* w, double* fbar, void* stream, mrp_stats* st);
+
+/* Release every resource of h (NULL is allowed). */
+int mrp_destroy(mrp_handle* h);
+
+const char* mrp_error_string(int status);
+
+/* Per-phase device timing (CUDA events around every kernel launch of the
+ * solve), off by default.  Phases: 0 ghosting, 1 smoothing, 2 residual,
+ * 3 restriction + FAS RHS, 4 level-0 FFT solve, 5 prolongation,
+ * 6 residual norms, 7 right-hand-side preparation and other.
+ * mrp_profile_read copies n (<= 8) accumulated milliseconds, launch counts
+ * and node-updates (nodes processed, summed over launches) to host arrays
+ * (any may be NULL) and, if reset != 0, clears the accumulators. */
+int mrp_profile_enable(mrp_handle* h, int32_t enable);
+int mrp_profile_read(mrp_handle* h, int32_t n, double* ms, int64_t* launches, int64_t* nodes, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

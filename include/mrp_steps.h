@@ -1,0 +1,73 @@
+/*
+ * Step-level entry points of mrp: run one stage of the solve on the
+ * handle's internal per-level fields, and copy those fields in and out.
+ * They exist so that each kernel of the path can be compared with a CPU
+ * implementation of the same stage; mrp_solve is the composition of these
+ * stages (Alg. 1 of arXiv 2512.08555).
+ *
+ * Internal layout (FP64).  Level k holds nb_k blocks (leaves of level k and
+ * parents of level-(k+1) blocks), ordered by block coordinates with z
+ * slowest, then y, then x.  Per block:
+ *   MRP_FIELD_U     (n+2)^3   u with one ghost layer
+ *   MRP_FIELD_F     n^3       right-hand side (f* on leaves, FAS RHS on covered blocks)
+ *   MRP_FIELD_R     n^3       residual f - L u
+ *   MRP_FIELD_UHAT  n^3       stored approximation u-hat (Alg. 1)
+ *   MRP_FIELD_FRAW  (n+4)^3   raw source f with two ghost layers
+ * All arrays are [block][z][y][x], x fastest.
+ */
+#ifndef MRP_STEPS_H
+#define MRP_STEPS_H
+
+#include <stdint.h>
+#include "mrp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MRP_FIELD_U = 0, MRP_FIELD_F = 1, MRP_FIELD_R = 2, MRP_FIELD_UHAT = 3, MRP_FIELD_FRAW = 4
+};
+
+enum {
+    MRP_STEP_PREPARE_RHS = 0,  /* f (leaf layout, arg) -> FRAW all levels -> F = R^M f on leaves (Sec. 3.2) */
+    MRP_STEP_GHOST_U = 1,      /* level k: inject U_k into covered U_{k-1}, then fill U_k ghosts (Sec. 2.1) */
+    MRP_STEP_SMOOTH = 2,       /* level k: one 8-colour Gauss-Seidel sweep, ghosts frozen (Sec. 3.1) */
+    MRP_STEP_RESIDUAL = 3,     /* level k: R = F - L U on every node (Alg. 1) */
+    MRP_STEP_RESTRICT = 4,     /* level k -> k-1: injection of u, full weighting of r, ghosts of
+                                  U_{k-1}, FAS RHS on covered blocks, u-hat (Alg. 1) */
+    MRP_STEP_COARSE_SOLVE = 5, /* level 0: U = h0^2 G * F on all nodes and the exterior ring (Sec. 2.2) */
+    MRP_STEP_PROLONG = 6,      /* level k: U_k += trilinear(U_{k-1} - UHAT_{k-1}) (Alg. 1) */
+    MRP_STEP_VCYCLE = 7        /* one full V(nu1,nu2) cycle (level argument ignored) */
+};
+
+/* Number of levels (max leaf level + 1). */
+int mrp_level_count(mrp_handle* h, int32_t* levels);
+
+/* Blocks of level k; coords ([nb][3], x y z) and is_leaf ([nb]) are host
+ * buffers and may be NULL. */
+int mrp_level_info(mrp_handle* h, int32_t level, int32_t* nb, int32_t* coords, uint8_t* is_leaf);
+
+/* Copy a whole per-level field between the handle and a device buffer
+ * (to_handle = 1: buf -> handle; 0: handle -> buf).  buf holds the internal
+ * layout above.  Ordered on stream. */
+int mrp_field_copy(mrp_handle* h, int32_t field, int32_t level, double* buf, int32_t to_handle, void* stream);
+
+/* Run one step.  f_leaf is used by MRP_STEP_PREPARE_RHS only (device,
+ * leaf layout of mrp_solve). */
+int mrp_step(mrp_handle* h, int32_t step, int32_t level, const double* f_leaf, void* stream);
+
+/* Copy the tabulated lattice Green's function G[n1][n2][n3],
+ * 0 <= n_i <= nmax, to a host buffer of (nmax+1)^3 doubles; nmax must not
+ * exceed the handle's table (returned by mrp_lgf_extent). */
+int mrp_lgf_extent(mrp_handle* h, int32_t* nmax);
+int mrp_lgf_copy(mrp_handle* h, int32_t nmax, double* out_host);
+
+/* Padded FFT lattice of level 0 (per axis, x y z). */
+int mrp_fft_shape(mrp_handle* h, int32_t* P);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

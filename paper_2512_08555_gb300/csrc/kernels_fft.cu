@@ -1,0 +1,526 @@
+// Level-0 direct solve: zero-padded FFT convolution with the lattice Green's
+// function of the multigrid operator (arXiv 2512.08555, Sec. 2.2 and 3.3),
+// and the FP64 tabulation of that Green's function.
+//
+// Padded lattice: P_a >= 2 N0_a + 1 per axis (a 2,3,5,7-smooth length), so
+// the circular convolution equals the linear one on the target cube
+// [-1, N0]^3 (level-0 nodes plus a one-node exterior ring).
+//
+// Spectral buffer layout: spec[z][y][kx], kx in [0, Px/2], complex FP64.
+// Passes (each a batch of 1-D mixed-radix Stockham FFTs in shared memory):
+//   A  x: real -> half spectrum, lines (y, z) < N0 only (the rest is zero padding)
+//   B  y: forward, lines z < N0 only; input y < N0 only
+//   C  z: forward, times G-hat, inverse; input z < N0, output z targets only
+//   B' y: inverse on target z planes, output y targets only
+//   A' x: half spectrum -> real on target (y, z) lines, written into the
+//         level-0 blocks' interiors and ghost layers.
+#include "mrp_internal.h"
+
+#include <cmath>
+
+namespace mrp {
+
+struct FftLine {
+    int P, nrad;
+    int rad[MAX_RADIX_STAGES];
+    const double2* tw;
+};
+
+static FftLine line_of(const FftAxis& a) {
+    FftLine l{};
+    l.P = a.P;
+    l.nrad = a.nrad;
+    for (int i = 0; i < a.nrad; ++i) l.rad[i] = a.rad[i];
+    l.tw = a.tw;
+    return l;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// exp(sign * 2 pi i m / P) from the table exp(-2 pi i m / P).
+__device__ __forceinline__ double2 twiddle(const double2* tw, int m, int sign) {
+    double2 w = tw[m];
+    if (sign > 0) w.y = -w.y;
+    return w;
+}
+
+// One line of length P in a[], b[] as scratch; the CTA's threads with the
+// same threadIdx.y (blockDim.x of them) cooperate.  Returns the buffer that
+// holds the result.  Stockham autosort: stage of radix R with Ns the product
+// of the radices already applied; butterfly j reads a[j + r P/R], twiddles by
+// w^{(j mod Ns) r P/(Ns R)}, applies the R-point DFT and writes
+// b[(j / Ns) Ns R + (j mod Ns) + r Ns].
+__device__ double2* fft_line(double2* a, double2* b, const FftLine& L, int sign) {
+    const int P = L.P;
+    int Ns = 1;
+    for (int st = 0; st < L.nrad; ++st) {
+        const int R = L.rad[st];
+        const int PR = P / R;
+        for (int j = threadIdx.x; j < PR; j += blockDim.x) {
+            const int k = j % Ns;
+            double2 v[8];
+            const int step = (P / (Ns * R)) * k;
+            for (int r = 0; r < R; ++r) {
+                const double2 x = a[j + r * PR];
+                v[r] = r == 0 ? x : cmul(x, twiddle(L.tw, (step * r) % P, sign));
+            }
+            const int base = (j / Ns) * Ns * R + k;
+            for (int r = 0; r < R; ++r) {
+                double2 acc = v[0];
+                for (int s2 = 1; s2 < R; ++s2) {
+                    const double2 t = cmul(v[s2], twiddle(L.tw, ((r * s2) % R) * PR, sign));
+                    acc.x += t.x;
+                    acc.y += t.y;
+                }
+                b[base + r * Ns] = acc;
+            }
+        }
+        __syncthreads();
+        double2* t = a; a = b; b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+constexpr int FFT_TX = 64;   // threads per line
+constexpr int FFT_LY = 4;    // lines per CTA
+
+struct Geo {
+    int n, nbx, nby, nbz;
+    int N0x, N0y, N0z;
+    int Px, Py, Pz, Kx, Ky, Kz;
+};
+
+// ---------------------------------------------------------------- pass A (x, real -> half spectrum)
+__global__ void k_fft_x_fwd(double2* __restrict__ spec, const double* __restrict__ F0, Geo g, FftLine L) {
+    extern __shared__ double2 sm[];
+    const int line = blockIdx.x * FFT_LY + threadIdx.y;
+    double2* a = sm + threadIdx.y * 2 * L.P;
+    double2* b = a + L.P;
+    const bool live = line < g.N0y * g.N0z;
+    const int y = live ? line % g.N0y : 0, z = live ? line / g.N0y : 0;
+    const int by = y / g.n, ly = y % g.n, bz = z / g.n, lz = z % g.n;
+    for (int x = threadIdx.x; x < L.P; x += blockDim.x) {
+        double v = 0.0;
+        if (live && x < g.N0x) {
+            const int bx = x / g.n, lx = x % g.n;
+            const int blk = (bz * g.nby + by) * g.nbx + bx;
+            v = F0[(size_t)blk * g.n * g.n * g.n + (lz * g.n + ly) * g.n + lx];
+        }
+        a[x] = make_double2(v, 0.0);
+    }
+    __syncthreads();
+    double2* r = fft_line(a, b, L, -1);
+    if (live)
+        for (int k = threadIdx.x; k < g.Kx; k += blockDim.x) spec[((size_t)z * g.Py + y) * g.Kx + k] = r[k];
+}
+
+// ---------------------------------------------------------------- pass B (y, forward), lines (z < N0z, kx)
+__global__ void k_fft_y_fwd(double2* __restrict__ spec, Geo g, FftLine L) {
+    extern __shared__ double2 sm[];
+    const int z = blockIdx.y;
+    const int kx = blockIdx.x * FFT_LY + threadIdx.y;
+    double2* a = sm + threadIdx.y * 2 * L.P;
+    double2* b = a + L.P;
+    const bool live = kx < g.Kx;
+    for (int y = threadIdx.x; y < L.P; y += blockDim.x)
+        a[y] = (live && y < g.N0y) ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : make_double2(0.0, 0.0);
+    __syncthreads();
+    double2* r = fft_line(a, b, L, -1);
+    if (live)
+        for (int y = threadIdx.x; y < L.P; y += blockDim.x) spec[((size_t)z * g.Py + y) * g.Kx + kx] = r[y];
+}
+
+// ---------------------------------------------------------------- pass C (z forward, x G-hat, z inverse), lines (ky, kx)
+__global__ void k_fft_z_conv(double2* __restrict__ spec, const double* __restrict__ ghat, Geo g, FftLine L) {
+    extern __shared__ double2 sm[];
+    const int ky = blockIdx.y;
+    const int kx = blockIdx.x * FFT_LY + threadIdx.y;
+    double2* a = sm + threadIdx.y * 2 * L.P;
+    double2* b = a + L.P;
+    const bool live = kx < g.Kx;
+    for (int z = threadIdx.x; z < L.P; z += blockDim.x)
+        a[z] = (live && z < g.N0z) ? spec[((size_t)z * g.Py + ky) * g.Kx + kx] : make_double2(0.0, 0.0);
+    __syncthreads();
+    double2* r = fft_line(a, b, L, -1);
+    const int fy = ky <= g.Py - ky ? ky : g.Py - ky;
+    for (int kz = threadIdx.x; kz < L.P; kz += blockDim.x) {
+        const int fz = kz <= g.Pz - kz ? kz : g.Pz - kz;
+        const double gv = live ? ghat[((size_t)fz * g.Ky + fy) * g.Kx + kx] : 0.0;
+        r[kz] = make_double2(r[kz].x * gv, r[kz].y * gv);
+    }
+    __syncthreads();
+    double2* other = (r == a) ? b : a;
+    double2* q = fft_line(r, other, L, +1);
+    if (live)
+        for (int t = threadIdx.x; t < g.N0z + 2; t += blockDim.x) {
+            const int z = (t - 1 + g.Pz) % g.Pz;
+            spec[((size_t)z * g.Py + ky) * g.Kx + kx] = q[z];
+        }
+}
+
+// ---------------------------------------------------------------- pass B' (y inverse), lines (target z, kx)
+__global__ void k_fft_y_inv(double2* __restrict__ spec, Geo g, FftLine L) {
+    extern __shared__ double2 sm[];
+    const int z = ((int)blockIdx.y - 1 + g.Pz) % g.Pz;
+    const int kx = blockIdx.x * FFT_LY + threadIdx.y;
+    double2* a = sm + threadIdx.y * 2 * L.P;
+    double2* b = a + L.P;
+    const bool live = kx < g.Kx;
+    for (int y = threadIdx.x; y < L.P; y += blockDim.x)
+        a[y] = live ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : make_double2(0.0, 0.0);
+    __syncthreads();
+    double2* r = fft_line(a, b, L, +1);
+    if (live)
+        for (int t = threadIdx.x; t < g.N0y + 2; t += blockDim.x) {
+            const int y = (t - 1 + g.Py) % g.Py;
+            spec[((size_t)z * g.Py + y) * g.Kx + kx] = r[y];
+        }
+}
+
+// ---------------------------------------------------------------- pass A' (x inverse, half spectrum -> real)
+// Writes u at target (x, y, z) in [-1, N0]^3 into every level-0 block whose
+// (n+2)^3 box holds that node (interior or ghost layer).
+__global__ void k_fft_x_inv(double* __restrict__ U0, const double2* __restrict__ spec, Geo g, FftLine L) {
+    extern __shared__ double2 sm[];
+    const int line = blockIdx.x * FFT_LY + threadIdx.y;
+    double2* a = sm + threadIdx.y * 2 * L.P;
+    double2* b = a + L.P;
+    const int ny = g.N0y + 2;
+    const bool live = line < ny * (g.N0z + 2);
+    const int ty = live ? line % ny - 1 : 0, tz = live ? line / ny - 1 : 0;
+    const int yi = (ty + g.Py) % g.Py, zi = (tz + g.Pz) % g.Pz;
+    const double2* src = spec + ((size_t)zi * g.Py + yi) * g.Kx;
+    for (int k = threadIdx.x; k < L.P; k += blockDim.x) {
+        double2 v = make_double2(0.0, 0.0);
+        if (live) {
+            if (k < g.Kx) v = src[k];
+            else { v = src[L.P - k]; v.y = -v.y; }
+        }
+        a[k] = v;
+    }
+    __syncthreads();
+    double2* r = fft_line(a, b, L, +1);
+    if (!live) return;
+    const int S = g.n + 2;
+    for (int t = threadIdx.x; t < g.N0x + 2; t += blockDim.x) {
+        const int tx = t - 1;
+        const double val = r[(tx + g.Px) % g.Px].x;
+        for (int bz = (tz - 1 < 0 ? -1 : (tz - 1) / g.n); bz <= (tz + 1) / g.n; ++bz) {
+            if (bz < 0 || bz >= g.nbz || tz < bz * g.n - 1 || tz > bz * g.n + g.n) continue;
+            for (int by = (ty - 1 < 0 ? -1 : (ty - 1) / g.n); by <= (ty + 1) / g.n; ++by) {
+                if (by < 0 || by >= g.nby || ty < by * g.n - 1 || ty > by * g.n + g.n) continue;
+                for (int bx = (tx - 1 < 0 ? -1 : (tx - 1) / g.n); bx <= (tx + 1) / g.n; ++bx) {
+                    if (bx < 0 || bx >= g.nbx || tx < bx * g.n - 1 || tx > bx * g.n + g.n) continue;
+                    const int blk = (bz * g.nby + by) * g.nbx + bx;
+                    const int lx = tx - bx * g.n + 1, ly = ty - by * g.n + 1, lz = tz - bz * g.n + 1;
+                    U0[(size_t)blk * S * S * S + (lz * S + ly) * S + lx] = val;
+                }
+            }
+        }
+    }
+}
+
+static Geo geo_of(const Handle& h) {
+    Geo g{};
+    g.n = h.n;
+    g.nbx = h.nb0[0]; g.nby = h.nb0[1]; g.nbz = h.nb0[2];
+    g.N0x = h.n0[0]; g.N0y = h.n0[1]; g.N0z = h.n0[2];
+    g.Px = h.ax[0].P; g.Py = h.ax[1].P; g.Pz = h.ax[2].P;
+    g.Kx = h.gK[0]; g.Ky = h.gK[1]; g.Kz = h.gK[2];
+    return g;
+}
+
+void launch_coarse_solve(Handle& h, cudaStream_t s) {
+    const Geo g = geo_of(h);
+    const dim3 blk(FFT_TX, FFT_LY);
+    const FftLine Lx = line_of(h.ax[0]), Ly = line_of(h.ax[1]), Lz = line_of(h.ax[2]);
+    const size_t smx = sizeof(double2) * 2 * FFT_LY * g.Px;
+    const size_t smy = sizeof(double2) * 2 * FFT_LY * g.Py;
+    const size_t smz = sizeof(double2) * 2 * FFT_LY * g.Pz;
+    const int kxb = (g.Kx + FFT_LY - 1) / FFT_LY;
+    k_fft_x_fwd<<<(g.N0y * g.N0z + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(h.spec, h.lv[0].F, g, Lx);
+    k_fft_y_fwd<<<dim3(kxb, g.N0z), blk, smy, s>>>(h.spec, g, Ly);
+    k_fft_z_conv<<<dim3(kxb, g.Py), blk, smz, s>>>(h.spec, h.ghat, g, Lz);
+    k_fft_y_inv<<<dim3(kxb, g.N0z + 2), blk, smy, s>>>(h.spec, g, Ly);
+    k_fft_x_inv<<<((g.N0y + 2) * (g.N0z + 2) + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(h.lv[0].U, h.spec, g, Lx);
+}
+
+// ============================================================================
+// Lattice Green's function (FP64).  G[n] = (2pi)^-3 int cos(k.n) / sigma(k) dk
+// with sigma the symbol of the unit-spacing LHS stencil.  sigma is affine in
+// s3 = 4 sin^2(k3/2): sigma = -(c0 + c1 s3), so the k3 integral is closed:
+// (1/2pi) int cos(n3 k3)/(a - b cos k3) = rho^|n3| / sqrt(a^2 - b^2),
+// a = c0 + 2 c1, b = 2 c1, rho = b / (a + sqrt(a^2 - b^2)).  The (k1, k2)
+// integral over [0,pi]^2 is split into the triangles k2 <= k1 and k1 <= k2
+// and Duffy-mapped (k1, k2) = (u, u v), which removes the 1/|k| singularity;
+// composite Gauss-Legendre in u and v.
+//
+// Per u-node i:   B[i][n2][n3] = sum_j cos(n2 u_i v_j) W_ij rho_ij^n3
+// then            A[n1][n2][n3] = sum_i cos(n1 u_i) B[i][n2][n3]
+//                 G = -(A + A^T(n1<->n2)) / pi^2.
+constexpr int LGF_JT = 32;
+
+__global__ void k_lgf_B(double* __restrict__ Bout, const double* __restrict__ u, const double* __restrict__ v,
+                        const double* __restrict__ W, const double* __restrict__ rho, int Qv, int nn) {
+    extern __shared__ double lsm[];
+    double* ct = lsm;                    // [nn][JT]
+    double* pt = lsm + nn * LGF_JT;      // [nn][JT]
+    const int i = blockIdx.x;
+    const double ui = u[i];
+    double* Bi = Bout + (size_t)i * nn * nn;
+    for (int t = threadIdx.x; t < nn * nn; t += blockDim.x) Bi[t] = 0.0;
+    for (int j0 = 0; j0 < Qv; j0 += LGF_JT) {
+        const int jn = min(LGF_JT, Qv - j0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nn * LGF_JT; t += blockDim.x) {
+            const int n2 = t / LGF_JT, jj = t % LGF_JT;
+            ct[t] = jj < jn ? cos((double)n2 * (ui * v[j0 + jj])) : 0.0;
+        }
+        for (int jj = threadIdx.x; jj < LGF_JT; jj += blockDim.x) {
+            double p = jj < jn ? W[(size_t)i * Qv + j0 + jj] : 0.0;
+            const double r = jj < jn ? rho[(size_t)i * Qv + j0 + jj] : 0.0;
+            for (int n3 = 0; n3 < nn; ++n3) { pt[n3 * LGF_JT + jj] = p; p *= r; }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nn * nn; t += blockDim.x) {
+            const int n2 = t / nn, n3 = t % nn;
+            double acc = 0.0;
+            for (int jj = 0; jj < LGF_JT; ++jj) acc += ct[n2 * LGF_JT + jj] * pt[n3 * LGF_JT + jj];
+            Bi[t] += acc;
+        }
+    }
+}
+
+__global__ void k_lgf_A(double* __restrict__ A, const double* __restrict__ B, const double* __restrict__ C1,
+                        int Qu, int nn) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)nn * nn * nn) return;
+    const int n1 = (int)(t / ((size_t)nn * nn));
+    const size_t r = t % ((size_t)nn * nn);
+    double acc = 0.0;
+    for (int i = 0; i < Qu; ++i) acc += C1[(size_t)n1 * Qu + i] * B[(size_t)i * nn * nn + r];
+    A[t] = acc;
+}
+
+__global__ void k_lgf_sym(double* __restrict__ G, const double* __restrict__ A, int nn) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)nn * nn * nn) return;
+    const int n1 = (int)(t / ((size_t)nn * nn)), n2 = (int)((t / nn) % nn), n3 = (int)(t % nn);
+    const double pi = 3.14159265358979323846;
+    G[t] = -(A[t] + A[((size_t)n2 * nn + n1) * nn + n3]) / (pi * pi);
+}
+
+// Spectrum of the even padded kernel g[i] = G[min(i, P-i)] by separable
+// cosine sums; out[kz][ky][kx] over the octant k_a in [0, P_a/2].
+// pass 1: T1[dz][dy][kx] = sum_ix G[dz][dy][d(ix)] cos(2 pi kx ix / Px)
+__global__ void k_ghat_x(double* __restrict__ T1, const double* __restrict__ G, int nn, const double* __restrict__ cx,
+                         int Px, int Dz, int Dy, int Kx) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)Dz * Dy * Kx) return;
+    const int kx = (int)(t % Kx), dy = (int)((t / Kx) % Dy), dz = (int)(t / ((size_t)Kx * Dy));
+    const double* g = G + ((size_t)dz * nn + dy) * nn;
+    double acc = 0.0;
+    for (int i = 0; i < Px; ++i) acc += g[i <= Px - i ? i : Px - i] * cx[((size_t)kx * i) % Px];
+    T1[t] = acc;
+}
+// pass 2: T2[dz][ky][kx] = sum_iy T1[dz][d(iy)][kx] cos(2 pi ky iy / Py)
+__global__ void k_ghat_y(double* __restrict__ T2, const double* __restrict__ T1, const double* __restrict__ cy,
+                         int Py, int Dz, int Dy, int Ky, int Kx) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)Dz * Ky * Kx) return;
+    const int kx = (int)(t % Kx), ky = (int)((t / Kx) % Ky), dz = (int)(t / ((size_t)Kx * Ky));
+    double acc = 0.0;
+    for (int i = 0; i < Py; ++i)
+        acc += T1[((size_t)dz * Dy + (i <= Py - i ? i : Py - i)) * Kx + kx] * cy[((size_t)ky * i) % Py];
+    T2[t] = acc;
+}
+// pass 3: ghat[kz][ky][kx] = scale * sum_iz T2[d(iz)][ky][kx] cos(2 pi kz iz / Pz)
+__global__ void k_ghat_z(double* __restrict__ out, const double* __restrict__ T2, const double* __restrict__ cz,
+                         int Pz, int Kz, int Ky, int Kx, double scale) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)Kz * Ky * Kx) return;
+    const int kx = (int)(t % Kx), ky = (int)((t / Kx) % Ky), kz = (int)(t / ((size_t)Kx * Ky));
+    double acc = 0.0;
+    for (int i = 0; i < Pz; ++i)
+        acc += T2[((size_t)(i <= Pz - i ? i : Pz - i) * Ky + ky) * Kx + kx] * cz[((size_t)kz * i) % Pz];
+    out[t] = scale * acc;
+}
+
+// ---------------------------------------------------------------- host side of the tabulation
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_q.
+static void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(q);
+    w.resize(q);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (q + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= q; ++k) { const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            // p1 = P_q(z), p0 = P_{q-1}(z)
+            const double dp = q * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) {
+                double a0 = 1.0, a1 = z;
+                for (int k = 2; k <= q; ++k) { const double a2 = ((2 * k - 1) * z * a1 - (k - 1) * a0) / k; a0 = a1; a1 = a2; }
+                const double d = q * (z * a1 - a0) / (z * z - 1.0);
+                x[i] = -z;
+                w[i] = 2.0 / ((1.0 - z * z) * d * d);
+                break;
+            }
+        }
+    }
+}
+
+static void composite(int q, double a, double b, int panels, std::vector<double>& xs, std::vector<double>& ws) {
+    std::vector<double> x, w;
+    gauss_legendre(q, x, w);
+    xs.clear();
+    ws.clear();
+    for (int p = 0; p < panels; ++p) {
+        const double lo = a + (b - a) * p / panels, hi = a + (b - a) * (p + 1) / panels;
+        for (int i = 0; i < q; ++i) {
+            xs.push_back(0.5 * (hi - lo) * x[i] + 0.5 * (hi + lo));
+            ws.push_back(0.5 * (hi - lo) * w[i]);
+        }
+    }
+}
+
+#define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { goto fail; } } while (0)
+
+int lgf_build(Handle& h, cudaStream_t s) {
+    const double pi = 3.14159265358979323846;
+    int nmax = 0;
+    for (int a = 0; a < 3; ++a) nmax = std::max(nmax, h.ax[a].P / 2);
+    const int nn = nmax + 1;
+    // quadrature: 32-point rules on 8 + nmax/16 panels in u and 4 + nmax/32 panels in v
+    std::vector<double> u, wu, v, wv;
+    composite(32, 0.0, pi, 8 + nmax / 16, u, wu);
+    composite(32, 0.0, 1.0, 4 + nmax / 32, v, wv);
+    const int Qu = (int)u.size(), Qv = (int)v.size();
+    std::vector<double> W((size_t)Qu * Qv), rho((size_t)Qu * Qv), C1((size_t)nn * Qu);
+    for (int i = 0; i < Qu; ++i)
+        for (int j = 0; j < Qv; ++j) {
+            const double k1 = u[i], k2 = u[i] * v[j];
+            const double s1 = 4.0 * std::sin(0.5 * k1) * std::sin(0.5 * k1);
+            const double s2 = 4.0 * std::sin(0.5 * k2) * std::sin(0.5 * k2);
+            double c0, c1;
+            if (h.M == 2) { c0 = s1 + s2; c1 = 1.0; }
+            else {
+                c0 = s1 + s2 - s1 * s2 / 6.0;
+                c1 = 1.0 - (s1 + s2) / 6.0;
+                if (h.M == 6) c1 += s1 * s2 / 30.0;
+            }
+            const double sq = std::sqrt(c0 * (c0 + 4.0 * c1));
+            rho[(size_t)i * Qv + j] = 2.0 * c1 / (c0 + 2.0 * c1 + sq);
+            W[(size_t)i * Qv + j] = wu[i] * wv[j] * u[i] / sq;
+        }
+    for (int n1 = 0; n1 < nn; ++n1)
+        for (int i = 0; i < Qu; ++i) C1[(size_t)n1 * Qu + i] = std::cos(n1 * u[i]);
+    double *du = nullptr, *dv = nullptr, *dW = nullptr, *drho = nullptr, *dC1 = nullptr, *dB = nullptr, *dA = nullptr;
+    double *dc[3] = {nullptr, nullptr, nullptr}, *T1 = nullptr, *T2 = nullptr;
+    int rc = MRP_ERR_CUDA;
+    const int Kx = h.gK[0], Ky = h.gK[1], Kz = h.gK[2];
+    const int Dz = h.ax[2].P / 2 + 1, Dy = h.ax[1].P / 2 + 1;
+    size_t total;
+    double scale;
+    h.lgf_nmax = nmax;
+    CK(cudaMalloc(&h.lgf, sizeof(double) * nn * nn * nn));
+    CK(cudaMalloc(&du, sizeof(double) * Qu));
+    CK(cudaMalloc(&dv, sizeof(double) * Qv));
+    CK(cudaMalloc(&dW, sizeof(double) * Qu * Qv));
+    CK(cudaMalloc(&drho, sizeof(double) * Qu * Qv));
+    CK(cudaMalloc(&dC1, sizeof(double) * nn * Qu));
+    CK(cudaMalloc(&dB, sizeof(double) * (size_t)Qu * nn * nn));
+    CK(cudaMalloc(&dA, sizeof(double) * (size_t)nn * nn * nn));
+    CK(cudaMemcpyAsync(du, u.data(), sizeof(double) * Qu, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dv, v.data(), sizeof(double) * Qv, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dW, W.data(), sizeof(double) * Qu * Qv, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(drho, rho.data(), sizeof(double) * Qu * Qv, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dC1, C1.data(), sizeof(double) * nn * Qu, cudaMemcpyHostToDevice, s));
+    CK(cudaFuncSetAttribute(k_lgf_B, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * nn * LGF_JT * (int)sizeof(double)));
+    k_lgf_B<<<Qu, 256, 2 * nn * LGF_JT * sizeof(double), s>>>(dB, du, dv, dW, drho, Qv, nn);
+    total = (size_t)nn * nn * nn;
+    k_lgf_A<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dA, dB, dC1, Qu, nn);
+    k_lgf_sym<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h.lgf, dA, nn);
+    CK(cudaGetLastError());
+    // spectrum of the padded kernel
+    for (int a = 0; a < 3; ++a) {
+        const int P = h.ax[a].P;
+        std::vector<double> c(P);
+        for (int m = 0; m < P; ++m) c[m] = std::cos(2.0 * pi * (double)m / (double)P);
+        CK(cudaMalloc(&dc[a], sizeof(double) * P));
+        CK(cudaMemcpyAsync(dc[a], c.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaMalloc(&T1, sizeof(double) * (size_t)Dz * Dy * Kx));
+    CK(cudaMalloc(&T2, sizeof(double) * (size_t)Dz * Ky * Kx));
+    CK(cudaMalloc(&h.ghat, sizeof(double) * (size_t)Kz * Ky * Kx));
+    k_ghat_x<<<(unsigned)(((size_t)Dz * Dy * Kx + 255) / 256), 256, 0, s>>>(T1, h.lgf, nn, dc[0], h.ax[0].P, Dz, Dy, Kx);
+    k_ghat_y<<<(unsigned)(((size_t)Dz * Ky * Kx + 255) / 256), 256, 0, s>>>(T2, T1, dc[1], h.ax[1].P, Dz, Dy, Ky, Kx);
+    scale = h.h0 * h.h0 / ((double)h.ax[0].P * h.ax[1].P * h.ax[2].P);
+    k_ghat_z<<<(unsigned)(((size_t)Kz * Ky * Kx + 255) / 256), 256, 0, s>>>(h.ghat, T2, dc[2], h.ax[2].P, Kz, Ky, Kx, scale);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    rc = MRP_OK;
+fail:
+    cudaFree(du); cudaFree(dv); cudaFree(dW); cudaFree(drho); cudaFree(dC1); cudaFree(dB); cudaFree(dA);
+    cudaFree(T1); cudaFree(T2);
+    for (int a = 0; a < 3; ++a) cudaFree(dc[a]);
+    return rc;
+}
+
+// ---------------------------------------------------------------- FFT plan
+static bool factor(int P, int* rad, int& nrad) {
+    nrad = 0;
+    const int order[] = {8, 4, 2, 3, 5, 7};
+    for (int r : order)
+        while (P % r == 0) {
+            if (nrad >= MAX_RADIX_STAGES) return false;
+            rad[nrad++] = r;
+            P /= r;
+        }
+    return P == 1;
+}
+
+static int smooth_length(int need) {
+    for (int P = need;; ++P) {
+        int m = P;
+        for (int r : {2, 3, 5, 7}) while (m % r == 0) m /= r;
+        if (m == 1) return P;
+    }
+}
+
+int fft_plan(Handle& h) {
+    const double pi = 3.14159265358979323846;
+    for (int a = 0; a < 3; ++a) {
+        FftAxis& ax = h.ax[a];
+        ax.P = smooth_length(2 * h.n0[a] + 1);
+        ax.K = ax.P / 2 + 1;
+        if (!factor(ax.P, ax.rad, ax.nrad)) return MRP_ERR_UNSUPPORTED;
+        std::vector<double2> tw(ax.P);
+        for (int m = 0; m < ax.P; ++m) {
+            const double ang = 2.0 * pi * (double)m / (double)ax.P;
+            tw[m] = make_double2(std::cos(ang), -std::sin(ang));
+        }
+        if (cudaMalloc(&ax.tw, sizeof(double2) * ax.P) != cudaSuccess) return MRP_ERR_OOM;
+        if (cudaMemcpy(ax.tw, tw.data(), sizeof(double2) * ax.P, cudaMemcpyHostToDevice) != cudaSuccess)
+            return MRP_ERR_CUDA;
+        h.gK[a] = ax.K;
+    }
+    const size_t ns = (size_t)h.ax[2].P * h.ax[1].P * h.ax[0].K;
+    if (cudaMalloc(&h.spec, sizeof(double2) * ns) != cudaSuccess) return MRP_ERR_OOM;
+    const int mx = 227 * 1024;
+    cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_y_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_z_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_y_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return MRP_OK;
+}
+
+}  // namespace mrp

@@ -1,0 +1,116 @@
+// Internal declarations shared by the translation units of libmrp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+#include <string>
+
+#include "mrp.h"
+#include "mrp_steps.h"
+
+namespace mrp {
+
+// 27 neighbour directions, index = (dz+1)*9 + (dy+1)*3 + (dx+1); 13 is the block itself.
+__host__ __device__ inline int dir27(int dx, int dy, int dz) { return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); }
+
+// Codes stored in the neighbour table besides block indices.
+constexpr int NBR_MISSING = -1;   // no block of this level there: interpolate from level k-1
+constexpr int NBR_OUTSIDE = -2;   // outside the domain (level 0 only)
+
+// Device view of one level's block tables (passed by value to kernels).
+struct LevelView {
+    int nb;
+    const int* coords;     // [nb][3] x y z
+    const int* nbr;        // [nb][27]
+    const int* parent;     // [nb] block index at level k-1 (-1 at level 0)
+    const int* octant;     // [nb] child octant o = ox + 2 oy + 4 oz inside the parent
+    const int* children;   // [nb][8] (-1 for leaves)
+    const uint8_t* is_leaf;
+};
+
+// Host + device tables of one level, plus its FP64 fields.
+struct Level {
+    int nb = 0, nleaf = 0, ncov = 0;
+    std::vector<int> h_coords, h_nbr, h_parent, h_octant, h_children, h_leaf_blocks, h_cov_blocks;
+    std::vector<uint8_t> h_is_leaf;
+    int *coords = nullptr, *nbr = nullptr, *parent = nullptr, *octant = nullptr, *children = nullptr;
+    int *leaf_blocks = nullptr, *cov_blocks = nullptr;
+    uint8_t* is_leaf = nullptr;
+    double *U = nullptr, *F = nullptr, *R = nullptr, *H = nullptr, *Fraw = nullptr;
+    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf}; }
+};
+
+// One padded FFT axis: length, radix sequence, twiddles exp(-2 pi i m / P).
+struct FftAxis {
+    int P = 0, K = 0;                 // K = P/2 + 1 (half spectrum along x)
+    int nrad = 0;
+    int rad[16];
+    double2* tw = nullptr;            // device [P]
+};
+
+constexpr int MAX_RADIX_STAGES = 16;
+
+struct Handle {
+    // forest
+    int nb0[3], n, L;                 // L = max level
+    double origin[3], h0;
+    int n0[3];                        // level-0 nodes per axis
+    int M, nu1, nu2, max_cycles, stop_rule;
+    double tol;
+    std::vector<Level> lv;
+    int n_leaves;
+    int* leaf_level = nullptr;        // device [n_leaves]
+    int* leaf_block = nullptr;        // device [n_leaves]
+    std::vector<int> h_leaf_level, h_leaf_block;
+    // coarse solve
+    FftAxis ax[3];
+    double2* spec = nullptr;          // [Pz][Py][Kx]
+    double* ghat = nullptr;           // [Kz][Ky][Kx] real spectrum, scaled by h0^2 / (Px Py Pz)
+    int gK[3];
+    int lgf_nmax = 0;
+    double* lgf = nullptr;            // [(nmax+1)^3]
+    // scratch
+    unsigned long long* dmax = nullptr;   // device scalars for max-norm reductions
+    unsigned long long* hmax = nullptr;   // pinned host mirror
+    int64_t leaf_nodes = 0, total_nodes = 0;
+    double fstar_max = 0.0;
+    bool have_forward = false;
+    // launch accounting and optional per-phase event timing
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;          // pool, 2 events per timed phase
+    int ev_used = 0;
+    struct Pending { int phase, e0; int64_t nodes; };
+    std::vector<Pending> pend;
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t prof_cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, prof_nodes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+enum Phase { PH_GHOST = 0, PH_SMOOTH = 1, PH_RESIDUAL = 2, PH_RESTRICT = 3, PH_COARSE = 4, PH_PROLONG = 5,
+             PH_NORM = 6, PH_OTHER = 7 };
+
+// ---------------------------------------------------------------- host side
+int build_forest(Handle& h, const mrp_forest& f, std::string& why);
+int upload_tables(Handle& h);
+int lgf_build(Handle& h, cudaStream_t s);   // tabulate G and the scaled spectrum
+int fft_plan(Handle& h);
+
+// ---------------------------------------------------------------- launches (kernels_*.cu)
+void launch_inject_to_parent(double* coarse, int gc, const double* fine, int gf, LevelView fine_lv, int n, cudaStream_t s);
+void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk, LevelView lkm1, int n, int M,
+                       bool zero_outside, cudaStream_t s);
+void launch_scatter_leaves(Handle& h, const double* f, cudaStream_t s);
+void launch_gather_leaves(Handle& h, double* u, cudaStream_t s);
+void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int nleaf, int n, int M, cudaStream_t s);
+void launch_smooth(double* U, const double* F, int nb, int n, int M, double h2, cudaStream_t s);
+void launch_residual(double* R, const double* U, const double* F, int nb, int n, int M, double inv_h2, cudaStream_t s);
+void launch_restrict(Handle& h, int k, cudaStream_t s);
+void launch_fas_snapshot(Handle& h, int km1, cudaStream_t s);
+void launch_prolong(Handle& h, int k, cudaStream_t s);
+void launch_leaf_residual_max(const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
+                              double inv_h2, unsigned long long* out, cudaStream_t s);
+void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, cudaStream_t s);
+void launch_coarse_solve(Handle& h, cudaStream_t s);
+
+}  // namespace mrp

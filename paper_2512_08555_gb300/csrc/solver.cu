@@ -1,0 +1,583 @@
+// Host side of libmrp: forest ingest and validation, device tables, the
+// V-cycle schedule (arXiv 2512.08555, Alg. 1) and the C ABI entry points.
+#include "mrp_internal.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <unordered_map>
+
+namespace mrp {
+
+static inline uint64_t key3(int x, int y, int z) {
+    return ((uint64_t)(uint32_t)x) | ((uint64_t)(uint32_t)y << 21) | ((uint64_t)(uint32_t)z << 42);
+}
+
+// ---------------------------------------------------------------- forest
+int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
+    h.n = f.n;
+    for (int a = 0; a < 3; ++a) {
+        h.nb0[a] = f.nb0[a];
+        h.origin[a] = f.origin[a];
+        if (f.nb0[a] < 1 || f.nb0[a] > 4096) { why = "nb0 out of range"; return MRP_ERR_INVALID_FOREST; }
+    }
+    h.h0 = f.h0;
+    if (!(f.h0 > 0.0)) { why = "h0 must be positive"; return MRP_ERR_INVALID_FOREST; }
+    if (f.n % 2 != 0 || f.n < 8 || f.n > 24) { why = "block size must be even, 8..24"; return MRP_ERR_INVALID_FOREST; }
+    if (f.n_leaves < 1 || !f.leaf_level || !f.leaf_ijk) { why = "no leaves"; return MRP_ERR_INVALID_ARG; }
+    int L = 0;
+    for (int i = 0; i < f.n_leaves; ++i) {
+        const int l = f.leaf_level[i];
+        if (l < 0 || l > 20) { why = "leaf level out of range"; return MRP_ERR_INVALID_FOREST; }
+        L = std::max(L, l);
+        for (int a = 0; a < 3; ++a) {
+            const int c = f.leaf_ijk[3 * i + a];
+            if (c < 0 || c >= (f.nb0[a] << l)) { why = "leaf outside the domain"; return MRP_ERR_INVALID_FOREST; }
+        }
+    }
+    h.L = L;
+    for (int a = 0; a < 3; ++a) h.n0[a] = f.nb0[a] * f.n;
+    // blocks per level: leaves, then parents of finer blocks
+    std::vector<std::unordered_map<uint64_t, int>> idx(L + 1);
+    std::vector<std::map<std::array<int, 3>, bool>> all(L + 1);   // (z, y, x) -> is_leaf
+    for (int i = 0; i < f.n_leaves; ++i) {
+        const int l = f.leaf_level[i];
+        const int x = f.leaf_ijk[3 * i], y = f.leaf_ijk[3 * i + 1], z = f.leaf_ijk[3 * i + 2];
+        std::array<int, 3> c{z, y, x};
+        if (all[l].count(c)) { why = "duplicate leaf"; return MRP_ERR_INVALID_FOREST; }
+        all[l][c] = true;
+    }
+    for (int k = L; k > 0; --k)
+        for (auto& kv : all[k]) {
+            std::array<int, 3> p{kv.first[0] >> 1, kv.first[1] >> 1, kv.first[2] >> 1};
+            auto it = all[k - 1].find(p);
+            if (it == all[k - 1].end()) all[k - 1][p] = false;
+            else if (it->second) { why = "overlapping leaves"; return MRP_ERR_INVALID_FOREST; }
+        }
+    h.lv.assign(L + 1, Level());
+    for (int k = 0; k <= L; ++k) {
+        Level& lv = h.lv[k];
+        lv.nb = (int)all[k].size();
+        int b = 0;
+        for (auto& kv : all[k]) {   // std::map order: z, then y, then x
+            const int z = kv.first[0], y = kv.first[1], x = kv.first[2];
+            lv.h_coords.push_back(x); lv.h_coords.push_back(y); lv.h_coords.push_back(z);
+            lv.h_is_leaf.push_back(kv.second ? 1 : 0);
+            idx[k][key3(x, y, z)] = b++;
+        }
+    }
+    if (h.lv[0].nb != f.nb0[0] * f.nb0[1] * f.nb0[2]) { why = "leaves do not tile the domain"; return MRP_ERR_INVALID_FOREST; }
+    auto find = [&](int k, int x, int y, int z) -> int {
+        if (x < 0 || y < 0 || z < 0 || x >= (f.nb0[0] << k) || y >= (f.nb0[1] << k) || z >= (f.nb0[2] << k)) return NBR_OUTSIDE;
+        auto it = idx[k].find(key3(x, y, z));
+        return it == idx[k].end() ? NBR_MISSING : it->second;
+    };
+    for (int k = 0; k <= L; ++k) {
+        Level& lv = h.lv[k];
+        lv.h_nbr.resize((size_t)lv.nb * 27);
+        lv.h_parent.assign(lv.nb, -1);
+        lv.h_octant.assign(lv.nb, 0);
+        lv.h_children.assign((size_t)lv.nb * 8, -1);
+        for (int b = 0; b < lv.nb; ++b) {
+            const int x = lv.h_coords[3 * b], y = lv.h_coords[3 * b + 1], z = lv.h_coords[3 * b + 2];
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx)
+                        lv.h_nbr[(size_t)27 * b + dir27(dx, dy, dz)] = find(k, x + dx, y + dy, z + dz);
+            if (k > 0) {
+                lv.h_parent[b] = find(k - 1, x >> 1, y >> 1, z >> 1);
+                lv.h_octant[b] = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+            }
+            if (lv.h_is_leaf[b]) { lv.h_leaf_blocks.push_back(b); continue; }
+            lv.h_cov_blocks.push_back(b);
+            for (int o = 0; o < 8; ++o) {
+                const int c = k < L ? find(k + 1, 2 * x + (o & 1), 2 * y + ((o >> 1) & 1), 2 * z + ((o >> 2) & 1)) : -1;
+                if (c < 0) { why = "leaves do not tile the domain"; return MRP_ERR_INVALID_FOREST; }
+                lv.h_children[(size_t)8 * b + o] = c;
+            }
+            if (k == 0 && (x == 0 || y == 0 || z == 0 || x == f.nb0[0] - 1 || y == f.nb0[1] - 1 || z == f.nb0[2] - 1)) {
+                why = "a block touching the unbounded boundary is refined";
+                return MRP_ERR_INVALID_FOREST;
+            }
+        }
+        lv.nleaf = (int)lv.h_leaf_blocks.size();
+        lv.ncov = (int)lv.h_cov_blocks.size();
+    }
+    // 2:1 balance across faces, edges and corners: each of the 26 neighbour
+    // positions of a level-k block lies in a block of level k-1.
+    for (int k = 1; k <= L; ++k) {
+        const Level& lv = h.lv[k];
+        for (int b = 0; b < lv.nb; ++b) {
+            const int x = lv.h_coords[3 * b], y = lv.h_coords[3 * b + 1], z = lv.h_coords[3 * b + 2];
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int qx = x + dx, qy = y + dy, qz = z + dz;
+                        if (qx < 0 || qy < 0 || qz < 0) { why = "2:1 balance violated"; return MRP_ERR_INVALID_FOREST; }
+                        if (find(k - 1, qx >> 1, qy >> 1, qz >> 1) < 0) { why = "2:1 balance violated"; return MRP_ERR_INVALID_FOREST; }
+                    }
+        }
+    }
+    // leaf order of the caller
+    h.n_leaves = f.n_leaves;
+    h.h_leaf_level.resize(f.n_leaves);
+    h.h_leaf_block.resize(f.n_leaves);
+    for (int i = 0; i < f.n_leaves; ++i) {
+        const int l = f.leaf_level[i];
+        h.h_leaf_level[i] = l;
+        h.h_leaf_block[i] = find(l, f.leaf_ijk[3 * i], f.leaf_ijk[3 * i + 1], f.leaf_ijk[3 * i + 2]);
+    }
+    h.leaf_nodes = (int64_t)f.n_leaves * f.n * f.n * f.n;
+    h.total_nodes = 0;
+    for (int k = 0; k <= L; ++k) h.total_nodes += (int64_t)h.lv[k].nb * f.n * f.n * f.n;
+    return MRP_OK;
+}
+
+template <typename T>
+static int up(T*& d, const std::vector<T>& v) {
+    if (v.empty()) { d = nullptr; return MRP_OK; }
+    if (cudaMalloc(&d, sizeof(T) * v.size()) != cudaSuccess) return MRP_ERR_OOM;
+    if (cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) return MRP_ERR_CUDA;
+    return MRP_OK;
+}
+
+static int alloc_field(double*& p, size_t count) {
+    if (count == 0) { p = nullptr; return MRP_OK; }
+    if (cudaMalloc(&p, sizeof(double) * count) != cudaSuccess) return MRP_ERR_OOM;
+    if (cudaMemset(p, 0, sizeof(double) * count) != cudaSuccess) return MRP_ERR_CUDA;
+    return MRP_OK;
+}
+
+int upload_tables(Handle& h) {
+    int rc;
+    const size_t n = h.n, S = n + 2, S4 = n + 4;
+    for (Level& lv : h.lv) {
+        if ((rc = up(lv.coords, lv.h_coords))) return rc;
+        if ((rc = up(lv.nbr, lv.h_nbr))) return rc;
+        if ((rc = up(lv.parent, lv.h_parent))) return rc;
+        if ((rc = up(lv.octant, lv.h_octant))) return rc;
+        if ((rc = up(lv.children, lv.h_children))) return rc;
+        if ((rc = up(lv.leaf_blocks, lv.h_leaf_blocks))) return rc;
+        if ((rc = up(lv.cov_blocks, lv.h_cov_blocks))) return rc;
+        if ((rc = up(lv.is_leaf, lv.h_is_leaf))) return rc;
+        if ((rc = alloc_field(lv.U, lv.nb * S * S * S))) return rc;
+        if ((rc = alloc_field(lv.F, lv.nb * n * n * n))) return rc;
+        if ((rc = alloc_field(lv.R, lv.nb * n * n * n))) return rc;
+        if ((rc = alloc_field(lv.H, lv.nb * n * n * n))) return rc;
+        if ((rc = alloc_field(lv.Fraw, lv.nb * S4 * S4 * S4))) return rc;
+    }
+    if ((rc = up(h.leaf_level, h.h_leaf_level))) return rc;
+    if ((rc = up(h.leaf_block, h.h_leaf_block))) return rc;
+    if (cudaMalloc(&h.dmax, sizeof(unsigned long long) * 4) != cudaSuccess) return MRP_ERR_OOM;
+    if (cudaMallocHost(&h.hmax, sizeof(unsigned long long) * 4) != cudaSuccess) return MRP_ERR_OOM;
+    return MRP_OK;
+}
+
+static void release(Handle& h) {
+    for (Level& lv : h.lv) {
+        cudaFree(lv.coords); cudaFree(lv.nbr); cudaFree(lv.parent); cudaFree(lv.octant); cudaFree(lv.children);
+        cudaFree(lv.leaf_blocks); cudaFree(lv.cov_blocks); cudaFree(lv.is_leaf);
+        cudaFree(lv.U); cudaFree(lv.F); cudaFree(lv.R); cudaFree(lv.H); cudaFree(lv.Fraw);
+    }
+    h.lv.clear();
+    cudaFree(h.leaf_level); cudaFree(h.leaf_block);
+    for (int a = 0; a < 3; ++a) cudaFree(h.ax[a].tw);
+    cudaFree(h.spec); cudaFree(h.ghat); cudaFree(h.lgf); cudaFree(h.dmax);
+    if (h.hmax) cudaFreeHost(h.hmax);
+    h.hmax = nullptr;
+    for (cudaEvent_t e : h.ev) cudaEventDestroy(e);
+    h.ev.clear();
+}
+
+// ---------------------------------------------------------------- schedule (Alg. 1)
+static double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
+
+static LevelView view_or_empty(const Handle& h, int k) {
+    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+}
+
+// Per-phase accounting: counts launches; with profiling on, records a CUDA
+// event pair around the phase (harvested at the next host synchronisation).
+struct PhaseScope {
+    Handle& h;
+    cudaStream_t s;
+    int phase, e0 = -1, launches;
+    int64_t nodes;
+    PhaseScope(Handle& hh, cudaStream_t ss, int ph, int64_t nd, int nl) : h(hh), s(ss), phase(ph), launches(nl), nodes(nd) {
+        if (h.prof && h.ev_used + 2 <= (int)h.ev.size()) {
+            e0 = h.ev_used;
+            h.ev_used += 2;
+            cudaEventRecord(h.ev[e0], s);
+        }
+    }
+    ~PhaseScope() {
+        h.launches += launches;
+        if (e0 >= 0) {
+            cudaEventRecord(h.ev[e0 + 1], s);
+            h.pend.push_back(Handle::Pending{phase, e0, nodes});
+        }
+    }
+};
+
+static void harvest(Handle& h) {
+    for (const auto& p : h.pend) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h.ev[p.e0], h.ev[p.e0 + 1]) == cudaSuccess) {
+            h.prof_ms[p.phase] += ms;
+            h.prof_cnt[p.phase] += 1;
+            h.prof_nodes[p.phase] += p.nodes;
+        }
+    }
+    h.pend.clear();
+    h.ev_used = 0;
+}
+
+static int64_t n3(const Handle& h) { return (int64_t)h.n * h.n * h.n; }
+static int64_t halo_nodes(const Handle& h, int g) { const int64_t S = h.n + 2 * g; return S * S * S - n3(h); }
+
+// Ghosting of u on level k: covered level-(k-1) nodes first take the
+// injection of the level-k values, then the halo is copied / interpolated.
+static void ghost_u(Handle& h, int k, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_GHOST, h.lv[k].nb * halo_nodes(h, 1), k >= 1 ? 2 : 1);
+    if (k >= 1) launch_inject_to_parent(h.lv[k - 1].U, 1, h.lv[k].U, 1, h.lv[k].view(), h.n, s);
+    launch_ghost_fill(h.lv[k].U, 1, k >= 1 ? h.lv[k - 1].U : nullptr, 1, h.lv[k].view(), view_or_empty(h, k - 1),
+                      h.n, h.M, false, s);
+}
+
+static void smooth(Handle& h, int k, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_SMOOTH, h.lv[k].nb * n3(h), 1);
+    const double hk = level_h(h, k);
+    launch_smooth(h.lv[k].U, h.lv[k].F, h.lv[k].nb, h.n, h.M, hk * hk, s);
+}
+
+static void residual(Handle& h, int k, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_RESIDUAL, h.lv[k].nb * n3(h), 1);
+    const double hk = level_h(h, k);
+    launch_residual(h.lv[k].R, h.lv[k].U, h.lv[k].F, h.lv[k].nb, h.n, h.M, 1.0 / (hk * hk), s);
+}
+
+// Restriction k -> k-1: inject u, full-weight r, ghosts of u_{k-1}, FAS RHS, u-hat.
+static void restrict_level(Handle& h, int k, cudaStream_t s) {
+    {
+        PhaseScope ps(h, s, PH_RESTRICT, h.lv[k - 1].ncov * n3(h), h.lv[k - 1].ncov > 0 ? 1 : 0);
+        launch_restrict(h, k, s);
+    }
+    ghost_u(h, k - 1, s);
+    PhaseScope ps(h, s, PH_RESTRICT, h.lv[k - 1].nb * n3(h), 1);
+    launch_fas_snapshot(h, k - 1, s);
+}
+
+static void coarse_solve(Handle& h, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_COARSE, (int64_t)h.n0[0] * h.n0[1] * h.n0[2], 5);
+    launch_coarse_solve(h, s);
+}
+
+static void prolong(Handle& h, int k, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_PROLONG, h.lv[k].nb * n3(h), 1);
+    launch_prolong(h, k, s);
+}
+
+static void prepare_rhs(Handle& h, const double* f, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1 + h.L + 2 * (h.L + 1));
+    const size_t S4 = h.n + 4;
+    for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].Fraw, 0, sizeof(double) * h.lv[k].nb * S4 * S4 * S4, s);
+    launch_scatter_leaves(h, f, s);
+    for (int k = h.L - 1; k >= 0; --k) launch_inject_to_parent(h.lv[k].Fraw, 2, h.lv[k + 1].Fraw, 2, h.lv[k + 1].view(), h.n, s);
+    for (int k = 0; k <= h.L; ++k)
+        launch_ghost_fill(h.lv[k].Fraw, 2, k >= 1 ? h.lv[k - 1].Fraw : nullptr, 2, h.lv[k].view(), view_or_empty(h, k - 1),
+                          h.n, h.M, true, s);
+    for (int k = 0; k <= h.L; ++k) launch_rhs_star(h.lv[k].F, h.lv[k].Fraw, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.M, s);
+}
+
+static void vcycle(Handle& h, cudaStream_t s) {
+    for (int k = h.L; k >= 1; --k) {
+        for (int i = 0; i < h.nu1; ++i) { ghost_u(h, k, s); smooth(h, k, s); }
+        ghost_u(h, k, s);
+        residual(h, k, s);
+        restrict_level(h, k, s);
+    }
+    coarse_solve(h, s);
+    for (int k = 1; k <= h.L; ++k) {
+        prolong(h, k, s);
+        for (int i = 0; i < h.nu2; ++i) { ghost_u(h, k, s); smooth(h, k, s); }
+    }
+}
+
+static double as_double(unsigned long long b) { double d; std::memcpy(&d, &b, sizeof d); return d; }
+
+}  // namespace mrp
+
+using namespace mrp;
+
+struct mrp_handle { Handle h; };
+
+extern "C" {
+
+const char* mrp_error_string(int status) {
+    switch (status) {
+        case MRP_OK: return "ok";
+        case MRP_ERR_INVALID_ARG: return "invalid argument";
+        case MRP_ERR_INVALID_FOREST: return "invalid forest";
+        case MRP_ERR_CUDA: return "CUDA runtime error";
+        case MRP_ERR_OOM: return "device out of memory";
+        case MRP_ERR_NOT_CONVERGED: return "not converged within max_cycles";
+        case MRP_ERR_TIMEOUT: return "device wait budget exhausted";
+        case MRP_ERR_NUMERICAL: return "NaN or Inf in the residual";
+        case MRP_ERR_NO_FORWARD: return "adjoint needs a forward solve on this handle";
+        case MRP_ERR_UNSUPPORTED: return "unsupported option";
+        default: return "unknown status";
+    }
+}
+
+int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, const mrp_options* opt) {
+    if (!out) return MRP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!forests || !opt || n_forests < 1) return MRP_ERR_INVALID_ARG;
+    if (n_forests != 1) return MRP_ERR_UNSUPPORTED;
+    if (opt->order != 2 && opt->order != 4 && opt->order != 6) return MRP_ERR_INVALID_ARG;
+    if (opt->nu1 < 0 || opt->nu2 < 0 || opt->max_cycles < 1 || !(opt->tol >= 0.0)) return MRP_ERR_INVALID_ARG;
+    if (opt->stop_rule != MRP_STOP_RESIDUAL && opt->stop_rule != MRP_STOP_CAUCHY) return MRP_ERR_INVALID_ARG;
+    if (opt->precision != MRP_FP64) return MRP_ERR_UNSUPPORTED;
+    if (opt->stop_rule == MRP_STOP_CAUCHY) return MRP_ERR_UNSUPPORTED;
+    if (forests[0].ncomp != 1) return MRP_ERR_UNSUPPORTED;
+    mrp_handle* H = new (std::nothrow) mrp_handle();
+    if (!H) return MRP_ERR_OOM;
+    Handle& h = H->h;
+    h.M = opt->order; h.nu1 = opt->nu1; h.nu2 = opt->nu2; h.max_cycles = opt->max_cycles;
+    h.tol = opt->tol; h.stop_rule = opt->stop_rule;
+    std::string why;
+    int rc = build_forest(h, forests[0], why);
+    if (rc == MRP_OK) rc = upload_tables(h);
+    if (rc == MRP_OK) rc = fft_plan(h);
+    if (rc == MRP_OK) rc = lgf_build(h, 0);
+    if (rc == MRP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = MRP_ERR_CUDA;
+    if (rc != MRP_OK) {
+        cudaGetLastError();
+        release(h);
+        delete H;
+        return rc;
+    }
+    *out = H;
+    return MRP_OK;
+}
+
+int mrp_destroy(mrp_handle* H) {
+    if (!H) return MRP_OK;
+    release(H->h);
+    delete H;
+    return MRP_OK;
+}
+
+static int read_max(Handle& h, cudaStream_t s, double* out, int slot) {
+    if (cudaMemcpyAsync(h.hmax + slot, h.dmax + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MRP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
+    *out = as_double(h.hmax[slot]);
+    harvest(h);
+    return MRP_OK;
+}
+
+static double leaf_residual(Handle& h, cudaStream_t s, int* rc) {
+    cudaMemsetAsync(h.dmax + 1, 0, sizeof(unsigned long long), s);
+    for (int k = h.L; k >= 0; --k) {
+        ghost_u(h, k, s);
+        PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
+        const double hk = level_h(h, k);
+        launch_leaf_residual_max(h.lv[k].U, h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.M, 1.0 / (hk * hk),
+                                 h.dmax + 1, s);
+    }
+    double r = 0.0;
+    *rc = read_max(h, s, &r, 1);
+    return r;
+}
+
+int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats* st) {
+    if (!H || !f || !u) return MRP_ERR_INVALID_ARG;
+    Handle& h = H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t S = h.n + 2;
+    int rc = MRP_OK;
+    const int64_t launches0 = h.launches;
+    prepare_rhs(h, f, s);
+    cudaMemsetAsync(h.dmax, 0, sizeof(unsigned long long), s);
+    {
+        PhaseScope ps(h, s, PH_NORM, h.leaf_nodes, h.L + 1);
+        for (int k = 0; k <= h.L; ++k) launch_absmax(h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.dmax, s);
+    }
+    if ((rc = read_max(h, s, &h.fstar_max, 0))) return rc;
+    for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U, 0, sizeof(double) * h.lv[k].nb * S * S * S, s);
+    const double scale = h.fstar_max > 0.0 ? h.fstar_max : 1.0;
+    double rel = INFINITY;
+    int cycles = 0;
+    for (; cycles < h.max_cycles;) {
+        vcycle(h, s);
+        ++cycles;
+        const double r = leaf_residual(h, s, &rc);
+        if (rc) return rc;
+        rel = r / scale;
+        if (!std::isfinite(rel)) { rc = MRP_ERR_NUMERICAL; break; }
+        if (rel < h.tol) break;
+    }
+    {
+        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1);
+        launch_gather_leaves(h, u, s);
+    }
+    if (cudaGetLastError() != cudaSuccess) return MRP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
+    h.have_forward = true;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->cycles = cycles;
+        st->residual = rel;
+        st->fstar_max = h.fstar_max;
+        st->leaf_nodes = h.leaf_nodes;
+        st->total_nodes = h.total_nodes;
+        st->launches = h.launches - launches0;
+    }
+    if (rc) return rc;
+    return rel < h.tol ? MRP_OK : MRP_ERR_NOT_CONVERGED;
+}
+
+int mrp_solve_adjoint(mrp_handle* H, const double* w, double* fbar, void* stream, mrp_stats* st) {
+    (void)w; (void)fbar; (void)stream; (void)st;
+    if (!H) return MRP_ERR_INVALID_ARG;
+    if (!H->h.have_forward) return MRP_ERR_NO_FORWARD;
+    return MRP_ERR_UNSUPPORTED;
+}
+
+// ---------------------------------------------------------------- step API
+int mrp_level_count(mrp_handle* H, int32_t* levels) {
+    if (!H || !levels) return MRP_ERR_INVALID_ARG;
+    *levels = H->h.L + 1;
+    return MRP_OK;
+}
+
+int mrp_level_info(mrp_handle* H, int32_t level, int32_t* nb, int32_t* coords, uint8_t* is_leaf) {
+    if (!H || !nb || level < 0 || level > H->h.L) return MRP_ERR_INVALID_ARG;
+    const Level& lv = H->h.lv[level];
+    *nb = lv.nb;
+    if (coords) std::memcpy(coords, lv.h_coords.data(), sizeof(int32_t) * 3 * lv.nb);
+    if (is_leaf) std::memcpy(is_leaf, lv.h_is_leaf.data(), lv.nb);
+    return MRP_OK;
+}
+
+int mrp_field_copy(mrp_handle* H, int32_t field, int32_t level, double* buf, int32_t to_handle, void* stream) {
+    if (!H || !buf || level < 0 || level > H->h.L) return MRP_ERR_INVALID_ARG;
+    Handle& h = H->h;
+    Level& lv = h.lv[level];
+    const size_t n = h.n;
+    double* p = nullptr;
+    size_t cnt = 0;
+    switch (field) {
+        case MRP_FIELD_U: p = lv.U; cnt = lv.nb * (n + 2) * (n + 2) * (n + 2); break;
+        case MRP_FIELD_F: p = lv.F; cnt = lv.nb * n * n * n; break;
+        case MRP_FIELD_R: p = lv.R; cnt = lv.nb * n * n * n; break;
+        case MRP_FIELD_UHAT: p = lv.H; cnt = lv.nb * n * n * n; break;
+        case MRP_FIELD_FRAW: p = lv.Fraw; cnt = lv.nb * (n + 4) * (n + 4) * (n + 4); break;
+        default: return MRP_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = to_handle ? cudaMemcpyAsync(p, buf, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s)
+                              : cudaMemcpyAsync(buf, p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? MRP_OK : MRP_ERR_CUDA;
+}
+
+int mrp_step(mrp_handle* H, int32_t step, int32_t level, const double* f_leaf, void* stream) {
+    if (!H) return MRP_ERR_INVALID_ARG;
+    Handle& h = H->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool lvl_ok = level >= 0 && level <= h.L;
+    switch (step) {
+        case MRP_STEP_PREPARE_RHS:
+            if (!f_leaf) return MRP_ERR_INVALID_ARG;
+            prepare_rhs(h, f_leaf, s);
+            break;
+        case MRP_STEP_GHOST_U:
+            if (!lvl_ok) return MRP_ERR_INVALID_ARG;
+            ghost_u(h, level, s);
+            break;
+        case MRP_STEP_SMOOTH:
+            if (!lvl_ok) return MRP_ERR_INVALID_ARG;
+            smooth(h, level, s);
+            break;
+        case MRP_STEP_RESIDUAL:
+            if (!lvl_ok) return MRP_ERR_INVALID_ARG;
+            residual(h, level, s);
+            break;
+        case MRP_STEP_RESTRICT:
+            if (!lvl_ok || level < 1) return MRP_ERR_INVALID_ARG;
+            restrict_level(h, level, s);
+            break;
+        case MRP_STEP_COARSE_SOLVE:
+            coarse_solve(h, s);
+            break;
+        case MRP_STEP_PROLONG:
+            if (!lvl_ok || level < 1) return MRP_ERR_INVALID_ARG;
+            prolong(h, level, s);
+            break;
+        case MRP_STEP_VCYCLE:
+            vcycle(h, s);
+            break;
+        default:
+            return MRP_ERR_INVALID_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? MRP_OK : MRP_ERR_CUDA;
+}
+
+int mrp_lgf_extent(mrp_handle* H, int32_t* nmax) {
+    if (!H || !nmax) return MRP_ERR_INVALID_ARG;
+    *nmax = H->h.lgf_nmax;
+    return MRP_OK;
+}
+
+int mrp_lgf_copy(mrp_handle* H, int32_t nmax, double* out_host) {
+    if (!H || !out_host || nmax < 0 || nmax > H->h.lgf_nmax) return MRP_ERR_INVALID_ARG;
+    const int nn = H->h.lgf_nmax + 1, m = nmax + 1;
+    std::vector<double> all((size_t)nn * nn * nn);
+    if (cudaMemcpy(all.data(), H->h.lgf, sizeof(double) * all.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MRP_ERR_CUDA;
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b)
+            for (int c = 0; c < m; ++c) out_host[((size_t)a * m + b) * m + c] = all[((size_t)a * nn + b) * nn + c];
+    return MRP_OK;
+}
+
+int mrp_profile_enable(mrp_handle* H, int32_t enable) {
+    if (!H) return MRP_ERR_INVALID_ARG;
+    Handle& h = H->h;
+    if (enable && h.ev.empty()) {
+        h.ev.resize(4096);
+        for (auto& e : h.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return MRP_ERR_CUDA;
+    }
+    h.prof = enable != 0;
+    return MRP_OK;
+}
+
+int mrp_profile_read(mrp_handle* H, int32_t n, double* ms, int64_t* launches, int64_t* nodes, int32_t reset) {
+    if (!H || n < 0 || n > 8) return MRP_ERR_INVALID_ARG;
+    Handle& h = H->h;
+    if (!h.pend.empty()) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return MRP_ERR_CUDA;
+        harvest(h);
+    }
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = h.prof_ms[i];
+        if (launches) launches[i] = h.prof_cnt[i];
+        if (nodes) nodes[i] = h.prof_nodes[i];
+    }
+    if (reset)
+        for (int i = 0; i < 8; ++i) { h.prof_ms[i] = 0; h.prof_cnt[i] = 0; h.prof_nodes[i] = 0; }
+    return MRP_OK;
+}
+
+int mrp_fft_shape(mrp_handle* H, int32_t* P) {
+    if (!H || !P) return MRP_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) P[a] = H->h.ax[a].P;
+    return MRP_OK;
+}
+
+}  // extern "C"

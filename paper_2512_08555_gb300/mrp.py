@@ -1,0 +1,242 @@
+"""Python binding of libmrp (ctypes): argument marshalling only.
+
+Every step of the solve runs in the CUDA library; PyTorch supplies device
+memory and the current stream.  There is no CPU fallback: if the library
+is missing or cannot be loaded, constructing a solver raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmrp.so")
+
+MRP_OK = 0
+MRP_ERR_NOT_CONVERGED = 5
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid forest", 3: "CUDA error", 4: "out of memory",
+          5: "not converged", 6: "timeout", 7: "numerical", 8: "no forward", 9: "unsupported"}
+FIELDS = {"U": 0, "F": 1, "R": 2, "UHAT": 3, "FRAW": 4}
+STEPS = {"prepare_rhs": 0, "ghost_u": 1, "smooth": 2, "residual": 3, "restrict": 4,
+         "coarse_solve": 5, "prolong": 6, "vcycle": 7}
+EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_error_string",
+            "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
+            "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read"]
+PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
+
+
+class MrpError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+
+
+class _Forest(C.Structure):
+    _fields_ = [("nb0", C.c_int32 * 3), ("n", C.c_int32), ("origin", C.c_double * 3), ("h0", C.c_double),
+                ("n_leaves", C.c_int32), ("leaf_level", C.POINTER(C.c_int32)),
+                ("leaf_ijk", C.POINTER(C.c_int32)), ("ncomp", C.c_int32)]
+
+
+class _Options(C.Structure):
+    _fields_ = [("order", C.c_int32), ("tol", C.c_double), ("stop_rule", C.c_int32), ("max_cycles", C.c_int32),
+                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("mixed_target", C.c_double),
+                ("spin_budget", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("cycles", C.c_int32), ("ir_steps", C.c_int32), ("residual", C.c_double), ("cauchy", C.c_double),
+                ("fstar_max", C.c_double), ("leaf_nodes", C.c_int64), ("total_nodes", C.c_int64),
+                ("launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmrp.so (built by ``paper_2512_08555_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.mrp_create.argtypes = [C.POINTER(P), C.POINTER(_Forest), I32, C.POINTER(_Options)]
+    lib.mrp_solve.argtypes = [P, P, P, P, C.POINTER(Stats)]
+    lib.mrp_solve_adjoint.argtypes = [P, P, P, P, C.POINTER(Stats)]
+    lib.mrp_destroy.argtypes = [P]
+    lib.mrp_error_string.argtypes = [C.c_int]
+    lib.mrp_error_string.restype = C.c_char_p
+    lib.mrp_level_count.argtypes = [P, C.POINTER(I32)]
+    lib.mrp_level_info.argtypes = [P, I32, C.POINTER(I32), P, P]
+    lib.mrp_field_copy.argtypes = [P, I32, I32, P, I32, P]
+    lib.mrp_step.argtypes = [P, I32, I32, P, P]
+    lib.mrp_lgf_extent.argtypes = [P, C.POINTER(I32)]
+    lib.mrp_lgf_copy.argtypes = [P, I32, P]
+    lib.mrp_fft_shape.argtypes = [P, P]
+    lib.mrp_profile_enable.argtypes = [P, I32]
+    lib.mrp_profile_read.argtypes = [P, I32, P, P, P, I32]
+    for name in EXPORTED:
+        getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
+    lib.mrp_error_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc, where, allow=()):
+    if rc != MRP_OK and rc not in allow:
+        raise MrpError(rc, where)
+    return rc
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """One forest, one right-hand side, FP64 (``mrp_create`` / ``mrp_solve``)."""
+
+    def __init__(self, forest, order=4, tol=1e-10, max_cycles=50, nu1=3, nu2=3, precision="fp64"):
+        import torch  # noqa: F401  (CUDA context and memory come from torch)
+        self.lib = load_library()
+        self.forest = forest
+        self.n = int(forest.n)
+        self.n_leaves = int(forest.n_leaves)
+        self._lev = np.ascontiguousarray(forest.leaf_level, dtype=np.int32)
+        self._ijk = np.ascontiguousarray(forest.leaf_ijk, dtype=np.int32).reshape(-1, 3)
+        fd = _Forest()
+        fd.nb0[:] = [int(v) for v in forest.nb0]
+        fd.n = self.n
+        fd.origin[:] = [float(v) for v in forest.origin]
+        fd.h0 = float(forest.h0)
+        fd.n_leaves = self.n_leaves
+        fd.leaf_level = self._lev.ctypes.data_as(C.POINTER(C.c_int32))
+        fd.leaf_ijk = self._ijk.ctypes.data_as(C.POINTER(C.c_int32))
+        fd.ncomp = 1
+        op = _Options()
+        op.order, op.tol, op.stop_rule, op.max_cycles = int(order), float(tol), 0, int(max_cycles)
+        op.nu1, op.nu2 = int(nu1), int(nu2)
+        op.precision = {"fp64": 0, "mixed": 1}[precision]
+        self.h = C.c_void_p()
+        _check(self.lib.mrp_create(C.byref(self.h), C.byref(fd), 1, C.byref(op)), "mrp_create")
+
+    def close(self):
+        if self.h:
+            self.lib.mrp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ solve
+    def solve(self, f, u=None, stream=None, allow_not_converged=False):
+        """u = solve(f); f, u: CUDA float64 tensors [n_leaves, n, n, n]."""
+        import torch
+        n = self.n
+        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.n_leaves * n ** 3:
+            raise ValueError("f must be a contiguous CUDA float64 tensor of shape [n_leaves, n, n, n]")
+        if u is None:
+            u = torch.empty_like(f)
+        st = Stats()
+        allow = (MRP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        rc = self.lib.mrp_solve(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(u.data_ptr()), _stream_ptr(stream),
+                                C.byref(st))
+        _check(rc, "mrp_solve", allow)
+        return u, st
+
+    # ------------------------------------------------------------------ step API
+    def level_count(self):
+        v = C.c_int32()
+        _check(self.lib.mrp_level_count(self.h, C.byref(v)), "mrp_level_count")
+        return v.value
+
+    def level_info(self, k):
+        nb = C.c_int32()
+        _check(self.lib.mrp_level_info(self.h, k, C.byref(nb), None, None), "mrp_level_info")
+        coords = np.zeros((nb.value, 3), np.int32)
+        leaf = np.zeros(nb.value, np.uint8)
+        _check(self.lib.mrp_level_info(self.h, k, C.byref(nb), coords.ctypes.data_as(C.c_void_p),
+                                       leaf.ctypes.data_as(C.c_void_p)), "mrp_level_info")
+        return coords, leaf.astype(bool)
+
+    def field_shape(self, name, k):
+        nb = len(self.level_info(k)[0])
+        g = {"U": 1, "FRAW": 2}.get(name, 0)
+        s = self.n + 2 * g
+        return (nb, s, s, s)
+
+    def field_get(self, name, k, stream=None):
+        import torch
+        buf = torch.empty(self.field_shape(name, k), dtype=torch.float64, device="cuda")
+        _check(self.lib.mrp_field_copy(self.h, FIELDS[name], k, C.c_void_p(buf.data_ptr()), 0, _stream_ptr(stream)),
+               "mrp_field_copy")
+        torch.cuda.current_stream().synchronize()
+        return buf
+
+    def field_set(self, name, k, value, stream=None):
+        import torch
+        buf = torch.as_tensor(np.ascontiguousarray(value), dtype=torch.float64).cuda().contiguous()
+        if tuple(buf.shape) != self.field_shape(name, k):
+            raise ValueError("shape mismatch")
+        _check(self.lib.mrp_field_copy(self.h, FIELDS[name], k, C.c_void_p(buf.data_ptr()), 1, _stream_ptr(stream)),
+               "mrp_field_copy")
+        torch.cuda.current_stream().synchronize()
+
+    def step(self, name, level=0, f=None, stream=None):
+        import torch
+        ptr = C.c_void_p(f.data_ptr()) if f is not None else None
+        _check(self.lib.mrp_step(self.h, STEPS[name], level, ptr, _stream_ptr(stream)), f"mrp_step({name})")
+        torch.cuda.current_stream().synchronize()
+
+    def lgf_table(self, nmax=None):
+        ext = C.c_int32()
+        _check(self.lib.mrp_lgf_extent(self.h, C.byref(ext)), "mrp_lgf_extent")
+        nmax = ext.value if nmax is None else nmax
+        out = np.zeros((nmax + 1,) * 3)
+        _check(self.lib.mrp_lgf_copy(self.h, nmax, out.ctypes.data_as(C.c_void_p)), "mrp_lgf_copy")
+        return out
+
+    def profile(self, enable=True):
+        _check(self.lib.mrp_profile_enable(self.h, 1 if enable else 0), "mrp_profile_enable")
+
+    def profile_read(self, reset=True):
+        ms = np.zeros(8)
+        cnt = np.zeros(8, np.int64)
+        nodes = np.zeros(8, np.int64)
+        _check(self.lib.mrp_profile_read(self.h, 8, ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p),
+                                         nodes.ctypes.data_as(C.c_void_p), 1 if reset else 0), "mrp_profile_read")
+        return {p: {"ms": float(ms[i]), "launches": int(cnt[i]), "nodes": int(nodes[i])} for i, p in enumerate(PHASES)}
+
+    def solve_host(self, f_host, u_host=None, stream=None):
+        """End-to-end call from host memory: copy f in, solve, copy u out (all on ``stream``).
+
+        ``f_host``/``u_host``: CPU float64 tensors (pinned for asynchronous copies).
+        """
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        if not hasattr(self, "_dev_f") or self._dev_f.numel() != f_host.numel():
+            self._dev_f = torch.empty(f_host.shape, dtype=torch.float64, device="cuda")
+            self._dev_u = torch.empty_like(self._dev_f)
+        if u_host is None:
+            u_host = torch.empty(f_host.shape, dtype=torch.float64, pin_memory=True)
+        with torch.cuda.stream(s):
+            self._dev_f.copy_(f_host, non_blocking=True)
+            _, st = self.solve(self._dev_f, self._dev_u, stream=s)
+            u_host.copy_(self._dev_u, non_blocking=True)
+        s.synchronize()
+        return u_host, st
+
+    def fft_shape(self):
+        P = np.zeros(3, np.int32)
+        _check(self.lib.mrp_fft_shape(self.h, P.ctypes.data_as(C.c_void_p)), "mrp_fft_shape")
+        return tuple(int(v) for v in P)

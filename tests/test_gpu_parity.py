@@ -1,0 +1,255 @@
+"""Parity of every CUDA stage, and of whole solves, with the FP64 CPU oracle.
+
+Each stage test loads the same seeded per-level fields into the library
+(through the step entry points of the C ABI) and into the oracle, runs the
+stage on both sides and compares element by element.  Tolerances: stages
+are FP64 with different summation orders, so they agree to a few ulps of
+the data (1e-13 relative); whole solves to 1e-12 relative max-norm.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_08555_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.forest import OracleForest          # noqa: E402
+from oracle.multigrid import OracleSolver       # noqa: E402
+from oracle.lgf import lgf_table                # noqa: E402
+
+
+def _all(level, coords):
+    return np.ones(len(coords), bool)
+
+
+def small_forest(nb=4, n=8, max_level=2, lo=-1.0, L=2.0):
+    return synth.adaptive_forest((nb, nb, nb), n, (lo, lo, lo), L / (nb * n), max_level, _all)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _pair(desc, M, G=None):
+    from paper_2512_08555_gb300.mrp import Solver
+    s = Solver(desc, order=M, tol=0.0, max_cycles=1)
+    o = OracleSolver(OracleForest.from_desc(desc), M, G=G)
+    for k in range(s.level_count()):
+        coords, leaf = s.level_info(k)
+        assert np.array_equal(coords, o.fo.levels[k].coords)
+        assert np.array_equal(leaf, o.fo.levels[k].is_leaf)
+    return s, o
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _load(s, o, rng, which=("U", "F", "R", "UHAT")):
+    """Random fields at every level, identical on both sides."""
+    for k in range(s.level_count()):
+        for name in which:
+            arr = {"U": o.U, "F": o.F, "R": o.R, "UHAT": o.H}[name][k]
+            arr[...] = rng.normal(size=arr.shape)
+            s.field_set(name, k, arr)
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_lgf_table_matches_oracle(M):
+    desc = synth.uniform_forest((2, 2, 2), 8, (0, 0, 0), 1 / 16)
+    from paper_2512_08555_gb300.mrp import Solver
+    s = Solver(desc, order=M)
+    Gg = s.lgf_table(16)
+    Go = lgf_table(M, 16)
+    assert np.abs(Gg - Go).max() < 1e-14
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_prepare_rhs(M):
+    desc = small_forest()
+    s, o = _pair(desc, M)
+    f = synth.sample_leaves(desc, synth.c4_bumps(0, k=3, r_lo=0.2, r_hi=0.3))
+    s.step("prepare_rhs", 0, torch.from_numpy(f).cuda())
+    o.prepare_rhs(f)
+    for k in range(s.level_count()):
+        leaf = o.fo.levels[k].is_leaf
+        assert _rel(s.field_get("FRAW", k).cpu().numpy(), o.fraw[k]) < 1e-14
+        assert _rel(s.field_get("F", k).cpu().numpy()[leaf], o.F[k][leaf]) < 1e-14
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_ghost_fill(M, k):
+    desc = small_forest()
+    s, o = _pair(desc, M)
+    rng = np.random.default_rng(10 + k)
+    _load(s, o, rng, ("U",))
+    s.step("ghost_u", k)
+    o.ghost_fill(o.U, k, "keep")
+    assert _rel(s.field_get("U", k).cpu().numpy(), o.U[k]) < 1e-14
+    if k >= 1:
+        assert _rel(s.field_get("U", k - 1).cpu().numpy(), o.U[k - 1]) == 0.0
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_smooth_and_residual(M):
+    desc = small_forest()
+    s, o = _pair(desc, M)
+    rng = np.random.default_rng(1)
+    _load(s, o, rng)
+    for k in range(1, s.level_count()):
+        s.step("smooth", k)
+        o.smooth(k)
+        assert _rel(s.field_get("U", k).cpu().numpy(), o.U[k]) < 1e-13
+        s.step("residual", k)
+        o.residual(k)
+        assert _rel(s.field_get("R", k).cpu().numpy(), o.R[k]) < 1e-12
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("k", [1, 2])
+def test_restrict(M, k):
+    desc = small_forest()
+    s, o = _pair(desc, M)
+    rng = np.random.default_rng(2)
+    _load(s, o, rng)
+    s.step("restrict", k)
+    o.restrict(k)
+    for name, arr in (("U", o.U), ("F", o.F), ("UHAT", o.H)):
+        assert _rel(s.field_get(name, k - 1).cpu().numpy(), arr[k - 1]) < 1e-13, name
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_coarse_solve(M):
+    desc = small_forest(nb=4, n=8, max_level=1)
+    s, o = _pair(desc, M)
+    rng = np.random.default_rng(3)
+    _load(s, o, rng, ("F",))
+    s.step("coarse_solve")
+    o.coarse_solve()
+    assert _rel(s.field_get("U", 0).cpu().numpy(), o.U[0]) < 1e-12
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("k", [1, 2])
+def test_prolong(M, k):
+    desc = small_forest()
+    s, o = _pair(desc, M)
+    rng = np.random.default_rng(4)
+    _load(s, o, rng)
+    s.step("prolong", k)
+    o.prolong_correct(k)
+    assert _rel(s.field_get("U", k).cpu().numpy(), o.U[k]) < 1e-14
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_fixed_cycle_solve(M, cycles):
+    """Same algorithm, same number of V(3,3) cycles from u = 0: <= 1e-12 relative max-norm."""
+    from paper_2512_08555_gb300.mrp import Solver
+    desc = small_forest()
+    f = synth.sample_leaves(desc, synth.c4_bumps(0, k=3, r_lo=0.2, r_hi=0.3))
+    s = Solver(desc, order=M, tol=0.0, max_cycles=cycles)
+    u, st = s.solve(torch.from_numpy(f).cuda(), allow_not_converged=True)
+    o = OracleSolver(OracleForest.from_desc(desc), M)
+    uo, rel = o.solve(f, tol=0.0, max_cycles=cycles)
+    assert st.cycles == cycles
+    assert _rel(u.cpu().numpy(), uo) < 1e-12
+    assert abs(st.residual - rel) <= 1e-6 * rel
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_converged_solve(M):
+    from paper_2512_08555_gb300.mrp import Solver
+    desc = small_forest(n=12)
+    f = synth.sample_leaves(desc, synth.c4_bumps(2, k=4, r_lo=0.15, r_hi=0.3))
+    s = Solver(desc, order=M, tol=1e-12, max_cycles=40)
+    u, st = s.solve(torch.from_numpy(f).cuda())
+    o = OracleSolver(OracleForest.from_desc(desc), M)
+    uo, rel = o.solve(f, tol=1e-12, max_cycles=40)
+    assert st.residual < 1e-12 and st.cycles == o.cycles_done
+    assert _rel(u.cpu().numpy(), uo) < 1e-12
+
+
+@pytest.mark.parametrize("M", [2, 4, 6])
+def test_single_level_config1(M):
+    """Uniform [0,1)^3, 32^3 nodes, 3 Gaussian blobs: one cycle is the LGF solve."""
+    from paper_2512_08555_gb300.mrp import Solver
+    desc, src = synth.config1(0, n0=32, n=16)
+    f = synth.sample_leaves(desc, src)
+    s = Solver(desc, order=M, tol=1e-12, max_cycles=3)
+    u, st = s.solve(torch.from_numpy(f).cuda())
+    o = OracleSolver(OracleForest.from_desc(desc), M)
+    uo, rel = o.solve(f, tol=1e-12, max_cycles=3)
+    assert st.cycles == 1 and st.residual < 1e-12
+    assert _rel(u.cpu().numpy(), uo) < 1e-12
+
+
+def test_ragged_block_sizes_and_shapes():
+    """Non-cubic level 0 and n = 10 (tails of every thread loop)."""
+    from paper_2512_08555_gb300.mrp import Solver
+    desc = synth.adaptive_forest((5, 4, 3), 10, (0, 0, 0), 0.05, 1, _all)
+    f = synth.sample_leaves(desc, synth.gaussian_blobs(3, k=2, c_lo=0.35, c_hi=0.45))
+    s = Solver(desc, order=6, tol=0.0, max_cycles=2)
+    u, st = s.solve(torch.from_numpy(f).cuda(), allow_not_converged=True)
+    o = OracleSolver(OracleForest.from_desc(desc), 6)
+    uo, _ = o.solve(f, tol=0.0, max_cycles=2)
+    assert _rel(u.cpu().numpy(), uo) < 1e-12
+
+
+def test_zero_source():
+    from paper_2512_08555_gb300.mrp import Solver
+    desc = small_forest()
+    f = np.zeros((desc.n_leaves, 8, 8, 8))
+    s = Solver(desc, order=4, tol=1e-10, max_cycles=2)
+    u, st = s.solve(torch.from_numpy(f).cuda(), allow_not_converged=True)
+    assert float(u.abs().max()) == 0.0
+
+
+def test_nan_source_reports_numerical():
+    from paper_2512_08555_gb300.mrp import Solver, MrpError
+    desc = small_forest(max_level=1)
+    f = np.zeros((desc.n_leaves, 8, 8, 8))
+    f[-1, 3, 3, 3] = np.nan
+    s = Solver(desc, order=4, tol=1e-10, max_cycles=3)
+    with pytest.raises(MrpError) as e:
+        s.solve(torch.from_numpy(f).cuda())
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("M", [4, 6])
+def test_config2_full_size(M):
+    """Bench workload at full size (2.8M leaf nodes): the first cycle matches the
+    oracle element by element; the converged GPU solution has zero composite-system
+    residual as evaluated by the oracle's independent composite operator."""
+    from paper_2512_08555_gb300.mrp import Solver
+    from oracle.composite import CompositeSystem
+    desc, src = synth.config2(0)
+    f = synth.sample_leaves(desc, src)
+    fo = OracleForest.from_desc(desc)
+    o = OracleSolver(fo, M)
+    uo, _ = o.solve(f, tol=0.0, max_cycles=1)
+    s = Solver(desc, order=M, tol=0.0, max_cycles=1)
+    u1, _ = s.solve(torch.from_numpy(f).cuda(), allow_not_converged=True)
+    assert _rel(u1.cpu().numpy(), uo) < 1e-12
+    s2 = Solver(desc, order=M, tol=1e-10, max_cycles=40)
+    u, st = s2.solve(torch.from_numpy(f).cuda())
+    assert st.residual < 1e-10
+    # composite residual of the GPU answer: leaf values of levels >= 1 plus the
+    # level-0 source on covered nodes, taken from the library's final state
+    cs = CompositeSystem(OracleSolver(fo, M, G=o.G), f)
+    n = fo.n
+    parts = []
+    for k in range(1, fo.max_level + 1):
+        Uk = s2.field_get("U", k).cpu().numpy()
+        parts.append(Uk[cs.leaf_sel[k], 1:1 + n, 1:1 + n, 1:1 + n].reshape(-1))
+    parts.append(s2.field_get("F", 0).cpu().numpy()[cs.cov0].reshape(-1))
+    r = cs.residual(np.concatenate(parts))
+    assert np.abs(r).max() < 1e-9 * st.fstar_max
