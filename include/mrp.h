@@ -53,7 +53,8 @@ enum {
     MRP_ERR_TIMEOUT = 6,         /* a bounded device wait ran out */
     MRP_ERR_NUMERICAL = 7,       /* NaN or Inf in the residual norm */
     MRP_ERR_NO_FORWARD = 8,      /* adjoint requested before a forward solve */
-    MRP_ERR_UNSUPPORTED = 9      /* option combination not built */
+    MRP_ERR_UNSUPPORTED = 9,     /* option combination not built */
+    MRP_ERR_TOO_LARGE = 10       /* problem exceeds a fixed-size scratch array */
 };
 
 enum { MRP_FP64 = 0, MRP_MIXED = 1 };

@@ -66,6 +66,30 @@ int mrp_lgf_copy(mrp_handle* h, int32_t nmax, double* out_host);
 /* Padded FFT lattice of level 0 (per axis, x y z). */
 int mrp_fft_shape(mrp_handle* h, int32_t* P);
 
+/* The level-0 solve of MRP_STEP_COARSE_SOLVE, for callers that cannot
+ * allocate device memory when they call it (while capturing a stream into a
+ * CUDA graph, inside a host whose own pool owns all device memory, in loops
+ * that must not synchronise).  The paper has no counterpart: this is a
+ * deployment variant of the same computation.
+ *
+ * f0: device, level-0 source in the internal F layout ([block][z][y][x],
+ * n^3 doubles per level-0 block); u0: device, level-0 result in the internal
+ * U layout ((n+2)^3 per block, interior and ghost layer including the
+ * exterior ring).  Both are the caller's.  The handle supplies only
+ * read-only tables (Green's-function spectrum, twiddles).
+ *
+ * Scratch: a fixed 48 MiB device array inside the library (every GPU that
+ * loads the library holds it until exit); it fits level-0 lattices with
+ * Pz * Py * (Px/2 + 1) <= 3,145,728 complex values (e.g. P = 162 per axis);
+ * larger ones return MRP_ERR_TOO_LARGE.  Nothing is allocated or freed.
+ * The first call on a device looks the array's address up (a runtime call
+ * that is not a stream operation): make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's
+ * contents; every entry a call reads was written earlier in the same call,
+ * so nothing needs clearing.  Calls whose GPU work overlaps (other streams,
+ * other threads, other handles) race on the array: serialise them. */
+int mrp_coarse_solve_noalloc(mrp_handle* h, const double* f0, double* u0, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

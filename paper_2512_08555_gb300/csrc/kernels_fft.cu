@@ -248,6 +248,23 @@ void launch_coarse_solve(Handle& h, cudaStream_t s) {
     k_fft_x_inv<<<((g.N0y + 2) * (g.N0z + 2) + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(h.lv[0].U, h.spec, g, Lx);
 }
 
+// Same five passes with the spectral buffer, source and output given by the
+// caller (spec must hold Pz * Py * (Px/2+1) complex values).
+void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s) {
+    const Geo g = geo_of(h);
+    const dim3 blk(FFT_TX, FFT_LY);
+    const FftLine Lx = line_of(h.ax[0]), Ly = line_of(h.ax[1]), Lz = line_of(h.ax[2]);
+    const size_t smx = sizeof(double2) * 2 * FFT_LY * g.Px;
+    const size_t smy = sizeof(double2) * 2 * FFT_LY * g.Py;
+    const size_t smz = sizeof(double2) * 2 * FFT_LY * g.Pz;
+    const int kxb = (g.Kx + FFT_LY - 1) / FFT_LY;
+    k_fft_x_fwd<<<(g.N0y * g.N0z + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(spec, F0, g, Lx);
+    k_fft_y_fwd<<<dim3(kxb, g.N0z), blk, smy, s>>>(spec, g, Ly);
+    k_fft_z_conv<<<dim3(kxb, g.Py), blk, smz, s>>>(spec, h.ghat, g, Lz);
+    k_fft_y_inv<<<dim3(kxb, g.N0z + 2), blk, smy, s>>>(spec, g, Ly);
+    k_fft_x_inv<<<((g.N0y + 2) * (g.N0z + 2) + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(U0, spec, g, Lx);
+}
+
 // ============================================================================
 // Lattice Green's function (FP64).  G[n] = (2pi)^-3 int cos(k.n) / sigma(k) dk
 // with sigma the symbol of the unit-spacing LHS stencil.  sigma is affine in

@@ -112,5 +112,6 @@ void launch_leaf_residual_max(const double* U, const double* F, const int* leaf_
                               double inv_h2, unsigned long long* out, cudaStream_t s);
 void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, cudaStream_t s);
 void launch_coarse_solve(Handle& h, cudaStream_t s);
+void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s);
 
 }  // namespace mrp

@@ -328,6 +328,7 @@ const char* mrp_error_string(int status) {
         case MRP_ERR_NUMERICAL: return "NaN or Inf in the residual";
         case MRP_ERR_NO_FORWARD: return "adjoint needs a forward solve on this handle";
         case MRP_ERR_UNSUPPORTED: return "unsupported option";
+        case MRP_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the no-allocation entry point";
         default: return "unknown status";
     }
 }

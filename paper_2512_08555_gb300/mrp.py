@@ -17,13 +17,15 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmrp.so")
 MRP_OK = 0
 MRP_ERR_NOT_CONVERGED = 5
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid forest", 3: "CUDA error", 4: "out of memory",
-          5: "not converged", 6: "timeout", 7: "numerical", 8: "no forward", 9: "unsupported"}
+          5: "not converged", 6: "timeout", 7: "numerical", 8: "no forward", 9: "unsupported",
+          10: "too large for the fixed scratch"}
 FIELDS = {"U": 0, "F": 1, "R": 2, "UHAT": 3, "FRAW": 4}
 STEPS = {"prepare_rhs": 0, "ghost_u": 1, "smooth": 2, "residual": 3, "restrict": 4,
          "coarse_solve": 5, "prolong": 6, "vcycle": 7}
 EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_error_string",
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
-            "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read"]
+            "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
+            "mrp_coarse_solve_noalloc"]
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 
 
@@ -81,6 +83,7 @@ def load_library(path=LIB_PATH):
     lib.mrp_fft_shape.argtypes = [P, P]
     lib.mrp_profile_enable.argtypes = [P, I32]
     lib.mrp_profile_read.argtypes = [P, I32, P, P, P, I32]
+    lib.mrp_coarse_solve_noalloc.argtypes = [P, P, P, P]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
     lib.mrp_error_string.restype = C.c_char_p
