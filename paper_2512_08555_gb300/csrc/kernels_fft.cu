@@ -46,36 +46,109 @@ __device__ __forceinline__ double2 twiddle(const double2* tw, int m, int sign) {
     return w;
 }
 
-// One line of length P in a[], b[] as scratch; the CTA's threads with the
-// same threadIdx.y (blockDim.x of them) cooperate.  Returns the buffer that
-// holds the result.  Stockham autosort: stage of radix R with Ns the product
-// of the radices already applied; butterfly j reads a[j + r P/R], twiddles by
+// Small DFTs X_k = sum_j v_j w^(sign j k), w = exp(2 pi i / R), in registers.
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// i * s * a
+__device__ __forceinline__ double2 cmuli(double2 a, double s) { return make_double2(-a.y * s, a.x * s); }
+
+template <int R> struct Dft;
+template <> struct Dft<2> {
+    static __device__ __forceinline__ void run(double2* v, int) {
+        const double2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <> struct Dft<3> {
+    static __device__ __forceinline__ void run(double2* v, int sign) {
+        const double c = -0.5, sn = 0.86602540378443864676;   // cos, sin of 2 pi / 3
+        const double2 a = cadd(v[1], v[2]), b = csub(v[1], v[2]);
+        const double2 m = cadd(v[0], cscale(a, c));
+        const double2 t = cmuli(b, sign * sn);
+        v[0] = cadd(v[0], a);
+        v[1] = cadd(m, t);
+        v[2] = csub(m, t);
+    }
+};
+template <> struct Dft<4> {
+    static __device__ __forceinline__ void run(double2* v, int sign) {
+        const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        const double2 c = cadd(v[1], v[3]), d = cmuli(csub(v[1], v[3]), (double)sign);
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, d);
+        v[3] = csub(b, d);
+    }
+};
+template <> struct Dft<5> {
+    static __device__ __forceinline__ void run(double2* v, int sign) {
+        const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2pi/5), cos(4pi/5)
+        const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2pi/5), sin(4pi/5)
+        const double2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        const double2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        const double2 m1 = cadd(v[0], cadd(cscale(a1, c1), cscale(a2, c2)));
+        const double2 m2 = cadd(v[0], cadd(cscale(a1, c2), cscale(a2, c1)));
+        const double2 t1 = cmuli(cadd(cscale(b1, s1), cscale(b2, s2)), (double)sign);
+        const double2 t2 = cmuli(csub(cscale(b1, s2), cscale(b2, s1)), (double)sign);
+        v[0] = cadd(v[0], cadd(a1, a2));
+        v[1] = cadd(m1, t1);
+        v[4] = csub(m1, t1);
+        v[2] = cadd(m2, t2);
+        v[3] = csub(m2, t2);
+    }
+};
+template <> struct Dft<7> {   // direct sum with the line's twiddle table (P divisible by 7)
+    static __device__ __forceinline__ void run(double2* v, int sign, const double2* tw, int P) {
+        double2 out[7];
+        for (int r = 0; r < 7; ++r) {
+            double2 acc = v[0];
+            for (int j = 1; j < 7; ++j) acc = cadd(acc, cmul(v[j], twiddle(tw, ((r * j) % 7) * (P / 7), sign)));
+            out[r] = acc;
+        }
+        for (int r = 0; r < 7; ++r) v[r] = out[r];
+    }
+};
+
+// One Stockham stage of radix R: butterfly j reads a[j + r P/R], twiddles by
 // w^{(j mod Ns) r P/(Ns R)}, applies the R-point DFT and writes
 // b[(j / Ns) Ns R + (j mod Ns) + r Ns].
+template <int R>
+__device__ __forceinline__ void stockham_stage(const double2* __restrict__ a, double2* __restrict__ b, int P, int Ns,
+                                               const double2* tw, int sign) {
+    const int PR = P / R;
+    for (int j = threadIdx.x; j < PR; j += blockDim.x) {
+        const int k = j % Ns;
+        const int step = (P / (Ns * R)) * k;
+        double2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const double2 x = a[j + r * PR];
+            v[r] = r == 0 ? x : cmul(x, twiddle(tw, step * r, sign));
+        }
+        if constexpr (R == 7) Dft<7>::run(v, sign, tw, P);
+        else Dft<R>::run(v, sign);
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) b[base + r * Ns] = v[r];
+    }
+}
+
+// One line of length P in a[], b[] as scratch; the CTA's threads with the
+// same threadIdx.y (blockDim.x of them) cooperate.  Returns the buffer that
+// holds the result (Stockham autosort, mixed radix).
 __device__ double2* fft_line(double2* a, double2* b, const FftLine& L, int sign) {
     const int P = L.P;
     int Ns = 1;
     for (int st = 0; st < L.nrad; ++st) {
         const int R = L.rad[st];
-        const int PR = P / R;
-        for (int j = threadIdx.x; j < PR; j += blockDim.x) {
-            const int k = j % Ns;
-            double2 v[8];
-            const int step = (P / (Ns * R)) * k;
-            for (int r = 0; r < R; ++r) {
-                const double2 x = a[j + r * PR];
-                v[r] = r == 0 ? x : cmul(x, twiddle(L.tw, (step * r) % P, sign));
-            }
-            const int base = (j / Ns) * Ns * R + k;
-            for (int r = 0; r < R; ++r) {
-                double2 acc = v[0];
-                for (int s2 = 1; s2 < R; ++s2) {
-                    const double2 t = cmul(v[s2], twiddle(L.tw, ((r * s2) % R) * PR, sign));
-                    acc.x += t.x;
-                    acc.y += t.y;
-                }
-                b[base + r * Ns] = acc;
-            }
+        switch (R) {
+            case 2: stockham_stage<2>(a, b, P, Ns, L.tw, sign); break;
+            case 3: stockham_stage<3>(a, b, P, Ns, L.tw, sign); break;
+            case 4: stockham_stage<4>(a, b, P, Ns, L.tw, sign); break;
+            case 5: stockham_stage<5>(a, b, P, Ns, L.tw, sign); break;
+            default: stockham_stage<7>(a, b, P, Ns, L.tw, sign); break;
         }
         __syncthreads();
         double2* t = a; a = b; b = t;
@@ -494,7 +567,7 @@ fail:
 // ---------------------------------------------------------------- FFT plan
 static bool factor(int P, int* rad, int& nrad) {
     nrad = 0;
-    const int order[] = {8, 4, 2, 3, 5, 7};
+    const int order[] = {4, 2, 3, 5, 7};
     for (int r : order)
         while (P % r == 0) {
             if (nrad >= MAX_RADIX_STAGES) return false;
@@ -531,7 +604,7 @@ int fft_plan(Handle& h) {
     }
     const size_t ns = (size_t)h.ax[2].P * h.ax[1].P * h.ax[0].K;
     if (cudaMalloc(&h.spec, sizeof(double2) * ns) != cudaSuccess) return MRP_ERR_OOM;
-    const int mx = 227 * 1024;
+    const int mx = MAX_DYN_SMEM;
     cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_fft_y_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_fft_z_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

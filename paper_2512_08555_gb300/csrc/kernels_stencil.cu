@@ -271,7 +271,7 @@ __global__ void k_smooth(T* __restrict__ U, const T* __restrict__ F, int n, T h2
 static void smooth_attributes() {
     static bool done = false;
     if (done) return;
-    const int mx = 227 * 1024;
+    const int mx = MAX_DYN_SMEM;
     cudaFuncSetAttribute(k_smooth<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_smooth<4, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_smooth<6, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

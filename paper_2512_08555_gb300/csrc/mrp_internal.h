@@ -50,6 +50,9 @@ struct FftAxis {
 };
 
 constexpr int MAX_RADIX_STAGES = 16;
+// Opt-in dynamic shared memory per CTA requested for the large-tile kernels
+// (below the 227 KB limit so that their small static arrays still fit).
+constexpr int MAX_DYN_SMEM = 200 * 1024;
 
 struct Handle {
     // forest
@@ -100,6 +103,7 @@ int fft_plan(Handle& h);
 void launch_inject_to_parent(double* coarse, int gc, const double* fine, int gf, LevelView fine_lv, int n, cudaStream_t s);
 void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk, LevelView lkm1, int n, int M,
                        bool zero_outside, cudaStream_t s);
+void launch_ghost_u(double* A, const double* Ac, LevelView lk, LevelView lkm1, int n, int M, cudaStream_t s);
 void launch_scatter_leaves(Handle& h, const double* f, cudaStream_t s);
 void launch_gather_leaves(Handle& h, double* u, cudaStream_t s);
 void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int nleaf, int n, int M, cudaStream_t s);

@@ -243,8 +243,7 @@ static int64_t halo_nodes(const Handle& h, int g) { const int64_t S = h.n + 2 * 
 static void ghost_u(Handle& h, int k, cudaStream_t s) {
     PhaseScope ps(h, s, PH_GHOST, h.lv[k].nb * halo_nodes(h, 1), k >= 1 ? 2 : 1);
     if (k >= 1) launch_inject_to_parent(h.lv[k - 1].U, 1, h.lv[k].U, 1, h.lv[k].view(), h.n, s);
-    launch_ghost_fill(h.lv[k].U, 1, k >= 1 ? h.lv[k - 1].U : nullptr, 1, h.lv[k].view(), view_or_empty(h, k - 1),
-                      h.n, h.M, false, s);
+    launch_ghost_u(h.lv[k].U, k >= 1 ? h.lv[k - 1].U : nullptr, h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, s);
 }
 
 static void smooth(Handle& h, int k, cudaStream_t s) {
