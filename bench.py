@@ -1,11 +1,13 @@
 """Benchmark: free-space multigrid-FFT Poisson solve on the adaptive bump forest.
 
-One step = one full solve (mrp_solve: RHS preparation, V(3,3) cycles to a
-relative leaf residual of 1e-10, gather) of the three-level forest
-(Omega = [-1,1)^3, 5^3 level-0 blocks of 16^3 nodes, 8 C4 bumps,
-2.8M leaf nodes), order-4 Mehrstellen, FP64.  value = leaf nodes / solve
-time, inputs resident in HBM.  e2e = the same metric through the host-memory
-call (pinned H2D of f, solve, D2H of u inside the timed region).
+One step = one full solve (mrp_solve: RHS preparation, cycles to a relative
+residual of 1e-10, gather) of the three-level forest (Omega = [-1,1)^3,
+5^3 level-0 blocks of 16^3 nodes, 8 C4 bumps, 2.8M leaf nodes), order-4
+Mehrstellen.  value = leaf nodes / solve time of the chosen form (FP32
+V(3,3) cycles inside FP64 iterative refinement), inputs resident in HBM; the
+plain FP64 path is timed beside it and the chosen result's max error against
+it is reported.  e2e = the chosen form through the host-memory call (pinned
+H2D of f, solve, D2H of u inside the timed region).
 
 --impl reference times the CPU oracle (plain numpy FP64) on the same
 workload: preparation plus one V-cycle, extrapolated to the cycle count of
@@ -35,6 +37,18 @@ ORACLE_CYCLES = {4: 11, 6: 12, 2: 17}
 STENCIL_POINTS = {2: 7, 4: 19, 6: 27}
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak()
 
 
 def _dist():
@@ -140,6 +154,60 @@ def _config(desc, order):
             "cycle": "V(3,3)", "tol": TOL, "l2": "flushed (256 MB write) before every timed solve"}
 
 
+def _time_solves(solver, f, steps, warmup, flush, stream):
+    """Warm up, then time `steps` solves (L2 flushed before each) with CUDA events."""
+    import torch
+    for _ in range(warmup):
+        u, st = solver.solve(f)
+    torch.cuda.synchronize()
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches, sts = 0, []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        u, st = solver.solve(f)
+        ev[i][1].record(stream)
+        launches += int(st.launches)
+        sts.append(st)
+    torch.cuda.synchronize()
+    host = (time.perf_counter() - t0) / steps
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    return ms, u, sts[-1], launches, prof, host
+
+
+def _roofline(prof, order, steps):
+    """Dominant-kernel roofline: the smoother of the chosen path (FP32, bytes) and of the FP64 path (flops)."""
+    out = {}
+    sm32 = prof.get("smooth_f32")
+    if sm32 and sm32["ms"] > 0:
+        byt = sm32["nodes"] * 3 * 4                   # read u, read f, write u (FP32 words)
+        ach = byt / (sm32["ms"] / 1e3) / 1e9
+        out = {"bound": "hbm", "kernel": "k_smooth<M,float> (Gauss-Seidel sweep, FP32)", "achieved": ach,
+               "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS, "traffic": None,
+               "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+               "bytes_per_node": 12, "avg_launch_us": sm32["ms"] * 1e3 / max(sm32["launches"], 1)}
+    sm64 = prof.get("smooth_f64")
+    if sm64 and sm64["ms"] > 0:
+        fl = sm64["nodes"] * 2 * STENCIL_POINTS[order]
+        ach = fl / (sm64["ms"] / 1e3) / 1e12
+        r64 = {"bound": "alu", "kernel": "k_smooth<M,double> (Gauss-Seidel sweep, FP64)", "achieved": ach,
+               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+               "peak_source": "FP64 units x clock (152 SMs x 2 FMA/clk x 2.07 GHz), nominal",
+               "flops_per_node": 2 * STENCIL_POINTS[order],
+               "avg_launch_us": sm64["ms"] * 1e3 / max(sm64["launches"], 1)}
+        if not out:
+            out = r64
+        else:
+            out["fp64_smoother"] = r64
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -154,51 +222,33 @@ def run_ours(args):
     from paper_2512_08555_gb300.mrp import Solver
     desc, f_np = workload(rank)
     f = torch.from_numpy(f_np).cuda()
-    solver = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        u, st = solver.solve(f)
-    torch.cuda.synchronize()
+    plain = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES)
+    chosen = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed")
     if ws > 1:
         dist.barrier()
-    solver.profile(True)
-    solver.profile_read(reset=True)
     p, path = start_clock_sampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches = 0
-    cycles = []
-    torch.cuda.synchronize()
-    t_host0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        u, st = solver.solve(f)
-        ev[i][1].record(stream)
-        launches += int(st.launches)
-        cycles.append(int(st.cycles))
-    torch.cuda.synchronize()
-    t_host = time.perf_counter() - t_host0
+    ms_c, u_c, st_c, launches, prof_c, host_c = _time_solves(chosen, f, args.steps, args.warmup, flush, stream)
+    ms_p, u_p, st_p, _, prof_p, host_p = _time_solves(plain, f, args.steps, args.warmup, flush, stream)
     clocks = stop_clock_sampler(p, path)
-    prof = solver.profile_read(reset=True)
-    solver.profile(False)
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    t_step = ms / 1e3
+    err = float((u_c - u_p).abs().max() / u_p.abs().max())
+    t_step, t_plain = ms_c / 1e3, ms_p / 1e3
     if ws > 1:
-        tt = torch.tensor([t_step], device="cuda")
+        tt = torch.tensor([t_step, t_plain], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+        t_step, t_plain = float(tt[0]), float(tt[1])
     value = ws * desc.leaf_nodes / t_step
-    # end to end through host memory
+    # end to end through host memory (chosen path)
     f_host = torch.from_numpy(f_np).pin_memory()
     u_host = torch.empty_like(f_host).pin_memory()
-    solver.solve_host(f_host, u_host)
+    chosen.solve_host(f_host, u_host)
     e2e_t = []
     for i in range(args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        solver.solve_host(f_host, u_host)
+        chosen.solve_host(f_host, u_host)
         b.record(stream)
         torch.cuda.synchronize()
         e2e_t.append(a.elapsed_time(b) / 1e3)
@@ -207,37 +257,36 @@ def run_ours(args):
         tt = torch.tensor([e2e_step], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_step = float(tt.item())
-    # roofline of the dominant kernel (Gauss-Seidel smoother, FP64 ALU-bound)
-    sm = prof["smooth"]
-    flops = sm["nodes"] * 2 * STENCIL_POINTS[args.order]
-    achieved = flops / (sm["ms"] / 1e3) / 1e12 if sm["ms"] > 0 else None
-    total_ms = sum(v["ms"] for v in prof.values())
+    tot_c = sum(v["ms"] for v in prof_c.values())
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(desc, args.order),
-        "cycles": cycles[-1], "final_rel_residual": float(st.residual),
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": _config(desc, args.order),
+        "chosen": "mixed precision: FP32 V(3,3) cycles inside FP64 iterative refinement",
+        "max_rel_err_vs_fp64": err,
+        "cycles": int(st_c.cycles), "ir_steps": int(st_c.ir_steps), "final_rel_residual": float(st_c.residual),
+        "plain_fp64": {"value": ws * desc.leaf_nodes / t_plain, "unit": "cells/s", "ms_per_step": t_plain * 1e3,
+                       "cycles": int(st_p.cycles), "final_rel_residual": float(st_p.residual),
+                       "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof_p.items()}},
+        "speedup_vs_plain_fp64": t_plain / t_step,
         "e2e": {"value": ws * desc.leaf_nodes / e2e_step, "unit": "cells/s",
                 "h2d_bytes_per_step": int(f_host.numel() * 8), "d2h_bytes_per_step": int(u_host.numel() * 8)},
-        "roofline": {"bound": "alu", "kernel": "k_smooth (Gauss-Seidel sweep, FP64)",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
-                     "peak_source": "FP64 units x clock (152 SMs x 2 FMA/clk x 2.07 GHz), nominal",
-                     "flops_per_node": 2 * STENCIL_POINTS[args.order]},
-        "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "phase_share": {k: (v["ms"] / total_ms if total_ms else None) for k, v in prof.items()},
+        "roofline": _roofline({**prof_c, **{k: v for k, v in prof_p.items() if k == "smooth_f64"}}, args.order,
+                              args.steps),
+        "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof_c.items()},
+        "phase_share": {k: (v["ms"] / tot_c if tot_c else None) for k, v in prof_c.items()},
         "gpu_launches": launches,
         "clocks": clocks,
-        "host_wall_s_per_step": t_host / args.steps,
+        "host_wall_s_per_step": host_c,
     }
     if rank == 0 and not args.no_cpu_baseline:
         o, tp, tc = oracle_sample(desc, f_np, args.order)
-        cyc = cycles[-1]
+        cyc = ORACLE_CYCLES[args.order]
         cpu_value = desc.leaf_nodes / (tp + cyc * tc)
         line["cpu_baseline"] = {"value": cpu_value, "unit": "cells/s", "cores": 1, "kind": "oracle",
                                 "sample": f"RHS preparation ({tp:.1f} s) + 1 V(3,3) cycle ({tc:.1f} s) of the full "
-                                          f"workload, extrapolated to {cyc} cycles"}
-        # live parity of that first cycle against the CUDA path
+                                          f"workload, extrapolated to {cyc} cycles (the oracle's count to 1e-10)"}
+        # live parity of that first cycle against the FP64 CUDA path
         s1 = Solver(desc, order=args.order, tol=0.0, max_cycles=1)
         u1, _ = s1.solve(f, allow_not_converged=True)
         uo = o.leaf_u()

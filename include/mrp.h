@@ -78,9 +78,15 @@ typedef struct {
                                     MRP_STOP_CAUCHY:   max|u_n - u_{n+1}| / max|u_{n+1}| (Sec. 3.4) */
     int32_t max_cycles;          /* >= 1 */
     int32_t nu1, nu2;            /* pre- and post-smoothing sweeps, >= 0 */
-    int32_t precision;           /* MRP_FP64 (only value built so far) */
+    int32_t precision;           /* MRP_FP64: every stage in FP64.
+                                    MRP_MIXED: FP64 outer refinement (Green's function, outer
+                                    residual, level-0 convolution of the accumulated source,
+                                    correction accumulation) around FP32 V-cycles; tol then
+                                    bounds the relative residual of the composite system */
     double mixed_target;         /* reserved */
     int64_t spin_budget;         /* reserved */
+    int32_t inner_cycles;        /* MRP_MIXED: FP32 V-cycles per refinement step (0 = 4) */
+    int32_t max_outer;           /* MRP_MIXED: refinement steps at most (0 = 12) */
 } mrp_options;
 
 typedef struct {
@@ -122,8 +128,9 @@ const char* mrp_error_string(int status);
 /* Per-phase device timing (CUDA events around every kernel launch of the
  * solve), off by default.  Phases: 0 ghosting, 1 smoothing, 2 residual,
  * 3 restriction + FAS RHS, 4 level-0 FFT solve, 5 prolongation,
- * 6 residual norms, 7 right-hand-side preparation and other.
- * mrp_profile_read copies n (<= 8) accumulated milliseconds, launch counts
+ * 6 residual norms, 7 right-hand-side preparation and other; FP64 work at
+ * these indices, FP32 work (inner cycles of MRP_MIXED) at index + 8.
+ * mrp_profile_read copies n (<= 16) accumulated milliseconds, launch counts
  * and node-updates (nodes processed, summed over launches) to host arrays
  * (any may be NULL) and, if reset != 0, clears the accumulators. */
 int mrp_profile_enable(mrp_handle* h, int32_t enable);

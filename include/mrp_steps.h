@@ -31,11 +31,14 @@ enum {
 
 enum {
     MRP_STEP_PREPARE_RHS = 0,  /* f (leaf layout, arg) -> FRAW all levels -> F = R^M f on leaves (Sec. 3.2) */
-    MRP_STEP_GHOST_U = 1,      /* level k: inject U_k into covered U_{k-1}, then fill U_k ghosts (Sec. 2.1) */
-    MRP_STEP_SMOOTH = 2,       /* level k: one 8-colour Gauss-Seidel sweep, ghosts frozen (Sec. 3.1) */
-    MRP_STEP_RESIDUAL = 3,     /* level k: R = F - L U on every node (Alg. 1) */
-    MRP_STEP_RESTRICT = 4,     /* level k -> k-1: injection of u, full weighting of r, ghosts of
-                                  U_{k-1}, FAS RHS on covered blocks, u-hat (Alg. 1) */
+    MRP_STEP_GHOST_U = 1,      /* level k: inject U_k into covered U_{k-1}, then write into U_k's stored
+                                  ghost layer the ghosts the stencil kernels build (Sec. 2.1) */
+    MRP_STEP_SMOOTH = 2,       /* level k: one 8-colour Gauss-Seidel sweep with the ghost layer built from
+                                  the current neighbours and frozen during the sweep (Sec. 3.1); the
+                                  stored ghost layer of U_k is not updated */
+    MRP_STEP_RESIDUAL = 3,     /* level k: R = F - L U on every node, ghosts built in the kernel (Alg. 1) */
+    MRP_STEP_RESTRICT = 4,     /* level k -> k-1: injection of u, full weighting of r, FAS RHS on covered
+                                  blocks (ghosts of U_{k-1} built in the kernel), u-hat (Alg. 1) */
     MRP_STEP_COARSE_SOLVE = 5, /* level 0: U = h0^2 G * F on all nodes and the exterior ring (Sec. 2.2) */
     MRP_STEP_PROLONG = 6,      /* level k: U_k += trilinear(U_{k-1} - UHAT_{k-1}) (Alg. 1) */
     MRP_STEP_VCYCLE = 7        /* one full V(nu1,nu2) cycle (level argument ignored) */

@@ -20,78 +20,83 @@
 
 namespace mrp {
 
+// Complex type of each real type.
+template <typename R> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+
+template <typename R>
 struct FftLine {
     int P, nrad;
     int rad[MAX_RADIX_STAGES];
-    const double2* tw;
+    const typename Cx<R>::T* tw;
 };
 
-static FftLine line_of(const FftAxis& a) {
-    FftLine l{};
+template <typename R>
+static FftLine<R> line_of(const FftAxis& a) {
+    FftLine<R> l{};
     l.P = a.P;
     l.nrad = a.nrad;
     for (int i = 0; i < a.nrad; ++i) l.rad[i] = a.rad[i];
-    l.tw = a.tw;
+    if constexpr (sizeof(R) == 8) l.tw = a.tw;
+    else l.tw = a.tw32;
     return l;
 }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return C{a.x * s, a.y * s}; }
+// i * s * a
+template <typename C, typename R> __device__ __forceinline__ C cmuli(C a, R s) { return C{-a.y * s, a.x * s}; }
 
 // exp(sign * 2 pi i m / P) from the table exp(-2 pi i m / P).
-__device__ __forceinline__ double2 twiddle(const double2* tw, int m, int sign) {
-    double2 w = tw[m];
+template <typename C> __device__ __forceinline__ C twiddle(const C* tw, int m, int sign) {
+    C w = tw[m];
     if (sign > 0) w.y = -w.y;
     return w;
 }
 
 // Small DFTs X_k = sum_j v_j w^(sign j k), w = exp(2 pi i / R), in registers.
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-// i * s * a
-__device__ __forceinline__ double2 cmuli(double2 a, double s) { return make_double2(-a.y * s, a.x * s); }
-
-template <int R> struct Dft;
-template <> struct Dft<2> {
-    static __device__ __forceinline__ void run(double2* v, int) {
-        const double2 a = v[0], b = v[1];
+template <int RAD, typename R> struct Dft;
+template <typename R> struct Dft<2, R> {
+    template <typename C> static __device__ __forceinline__ void run(C* v, int) {
+        const C a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     }
 };
-template <> struct Dft<3> {
-    static __device__ __forceinline__ void run(double2* v, int sign) {
-        const double c = -0.5, sn = 0.86602540378443864676;   // cos, sin of 2 pi / 3
-        const double2 a = cadd(v[1], v[2]), b = csub(v[1], v[2]);
-        const double2 m = cadd(v[0], cscale(a, c));
-        const double2 t = cmuli(b, sign * sn);
+template <typename R> struct Dft<3, R> {
+    template <typename C> static __device__ __forceinline__ void run(C* v, int sign) {
+        const R c = R(-0.5), sn = R(0.86602540378443864676);   // cos, sin of 2 pi / 3
+        const C a = cadd(v[1], v[2]), b = csub(v[1], v[2]);
+        const C m = cadd(v[0], cscale(a, c));
+        const C t = cmuli(b, R(sign) * sn);
         v[0] = cadd(v[0], a);
         v[1] = cadd(m, t);
         v[2] = csub(m, t);
     }
 };
-template <> struct Dft<4> {
-    static __device__ __forceinline__ void run(double2* v, int sign) {
-        const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-        const double2 c = cadd(v[1], v[3]), d = cmuli(csub(v[1], v[3]), (double)sign);
+template <typename R> struct Dft<4, R> {
+    template <typename C> static __device__ __forceinline__ void run(C* v, int sign) {
+        const C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        const C c = cadd(v[1], v[3]), d = cmuli(csub(v[1], v[3]), R(sign));
         v[0] = cadd(a, c);
         v[2] = csub(a, c);
         v[1] = cadd(b, d);
         v[3] = csub(b, d);
     }
 };
-template <> struct Dft<5> {
-    static __device__ __forceinline__ void run(double2* v, int sign) {
-        const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2pi/5), cos(4pi/5)
-        const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2pi/5), sin(4pi/5)
-        const double2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
-        const double2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
-        const double2 m1 = cadd(v[0], cadd(cscale(a1, c1), cscale(a2, c2)));
-        const double2 m2 = cadd(v[0], cadd(cscale(a1, c2), cscale(a2, c1)));
-        const double2 t1 = cmuli(cadd(cscale(b1, s1), cscale(b2, s2)), (double)sign);
-        const double2 t2 = cmuli(csub(cscale(b1, s2), cscale(b2, s1)), (double)sign);
+template <typename R> struct Dft<5, R> {
+    template <typename C> static __device__ __forceinline__ void run(C* v, int sign) {
+        const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);   // cos(2pi/5), cos(4pi/5)
+        const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);    // sin(2pi/5), sin(4pi/5)
+        const C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        const C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        const C m1 = cadd(v[0], cadd(cscale(a1, c1), cscale(a2, c2)));
+        const C m2 = cadd(v[0], cadd(cscale(a1, c2), cscale(a2, c1)));
+        const C t1 = cmuli(cadd(cscale(b1, s1), cscale(b2, s2)), R(sign));
+        const C t2 = cmuli(csub(cscale(b1, s2), cscale(b2, s1)), R(sign));
         v[0] = cadd(v[0], cadd(a1, a2));
         v[1] = cadd(m1, t1);
         v[4] = csub(m1, t1);
@@ -99,60 +104,63 @@ template <> struct Dft<5> {
         v[3] = csub(m2, t2);
     }
 };
-template <> struct Dft<7> {   // direct sum with the line's twiddle table (P divisible by 7)
-    static __device__ __forceinline__ void run(double2* v, int sign, const double2* tw, int P) {
-        double2 out[7];
-        for (int r = 0; r < 7; ++r) {
-            double2 acc = v[0];
-            for (int j = 1; j < 7; ++j) acc = cadd(acc, cmul(v[j], twiddle(tw, ((r * j) % 7) * (P / 7), sign)));
-            out[r] = acc;
-        }
-        for (int r = 0; r < 7; ++r) v[r] = out[r];
-    }
-};
 
-// One Stockham stage of radix R: butterfly j reads a[j + r P/R], twiddles by
-// w^{(j mod Ns) r P/(Ns R)}, applies the R-point DFT and writes
-// b[(j / Ns) Ns R + (j mod Ns) + r Ns].
-template <int R>
-__device__ __forceinline__ void stockham_stage(const double2* __restrict__ a, double2* __restrict__ b, int P, int Ns,
-                                               const double2* tw, int sign) {
-    const int PR = P / R;
+// One Stockham stage of radix RAD: butterfly j reads a[j + r P/RAD], twiddles
+// by w^{(j mod Ns) r P/(Ns RAD)}, applies the RAD-point DFT and writes
+// b[(j / Ns) Ns RAD + (j mod Ns) + r Ns].  Radix 7 uses the direct sum with
+// the line's twiddle table.
+template <int RAD, typename R, typename C>
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int P, int Ns, const C* tw,
+                                               int sign) {
+    const int PR = P / RAD;
     for (int j = threadIdx.x; j < PR; j += blockDim.x) {
         const int k = j % Ns;
-        const int step = (P / (Ns * R)) * k;
-        double2 v[R];
+        const int step = (P / (Ns * RAD)) * k;
+        C v[RAD];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const double2 x = a[j + r * PR];
+        for (int r = 0; r < RAD; ++r) {
+            const C x = a[j + r * PR];
             v[r] = r == 0 ? x : cmul(x, twiddle(tw, step * r, sign));
         }
-        if constexpr (R == 7) Dft<7>::run(v, sign, tw, P);
-        else Dft<R>::run(v, sign);
-        const int base = (j / Ns) * Ns * R + k;
+        if constexpr (RAD == 7) {
+            C out[7];
 #pragma unroll
-        for (int r = 0; r < R; ++r) b[base + r * Ns] = v[r];
+            for (int r = 0; r < 7; ++r) {
+                C acc = v[0];
+#pragma unroll
+                for (int q = 1; q < 7; ++q) acc = cadd(acc, cmul(v[q], twiddle(tw, ((r * q) % 7) * PR, sign)));
+                out[r] = acc;
+            }
+#pragma unroll
+            for (int r = 0; r < 7; ++r) v[r] = out[r];
+        } else {
+            Dft<RAD, R>::run(v, sign);
+        }
+        const int base = (j / Ns) * Ns * RAD + k;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) b[base + r * Ns] = v[r];
     }
 }
 
 // One line of length P in a[], b[] as scratch; the CTA's threads with the
 // same threadIdx.y (blockDim.x of them) cooperate.  Returns the buffer that
 // holds the result (Stockham autosort, mixed radix).
-__device__ double2* fft_line(double2* a, double2* b, const FftLine& L, int sign) {
+template <typename R, typename C>
+__device__ C* fft_line(C* a, C* b, const FftLine<R>& L, int sign) {
     const int P = L.P;
     int Ns = 1;
     for (int st = 0; st < L.nrad; ++st) {
-        const int R = L.rad[st];
-        switch (R) {
-            case 2: stockham_stage<2>(a, b, P, Ns, L.tw, sign); break;
-            case 3: stockham_stage<3>(a, b, P, Ns, L.tw, sign); break;
-            case 4: stockham_stage<4>(a, b, P, Ns, L.tw, sign); break;
-            case 5: stockham_stage<5>(a, b, P, Ns, L.tw, sign); break;
-            default: stockham_stage<7>(a, b, P, Ns, L.tw, sign); break;
+        const int RAD = L.rad[st];
+        switch (RAD) {
+            case 2: stockham_stage<2, R>(a, b, P, Ns, L.tw, sign); break;
+            case 3: stockham_stage<3, R>(a, b, P, Ns, L.tw, sign); break;
+            case 4: stockham_stage<4, R>(a, b, P, Ns, L.tw, sign); break;
+            case 5: stockham_stage<5, R>(a, b, P, Ns, L.tw, sign); break;
+            default: stockham_stage<7, R>(a, b, P, Ns, L.tw, sign); break;
         }
         __syncthreads();
-        double2* t = a; a = b; b = t;
-        Ns *= R;
+        C* t = a; a = b; b = t;
+        Ns *= RAD;
     }
     return a;
 }
@@ -167,66 +175,75 @@ struct Geo {
 };
 
 // ---------------------------------------------------------------- pass A (x, real -> half spectrum)
-__global__ void k_fft_x_fwd(double2* __restrict__ spec, const double* __restrict__ F0, Geo g, FftLine L) {
-    extern __shared__ double2 sm[];
+template <typename R>
+__global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ F0, Geo g, FftLine<R> L) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    C* sm = reinterpret_cast<C*>(fsm);
     const int line = blockIdx.x * FFT_LY + threadIdx.y;
-    double2* a = sm + threadIdx.y * 2 * L.P;
-    double2* b = a + L.P;
+    C* a = sm + threadIdx.y * 2 * L.P;
+    C* b = a + L.P;
     const bool live = line < g.N0y * g.N0z;
     const int y = live ? line % g.N0y : 0, z = live ? line / g.N0y : 0;
     const int by = y / g.n, ly = y % g.n, bz = z / g.n, lz = z % g.n;
     for (int x = threadIdx.x; x < L.P; x += blockDim.x) {
-        double v = 0.0;
+        R v = R(0);
         if (live && x < g.N0x) {
             const int bx = x / g.n, lx = x % g.n;
             const int blk = (bz * g.nby + by) * g.nbx + bx;
             v = F0[(size_t)blk * g.n * g.n * g.n + (lz * g.n + ly) * g.n + lx];
         }
-        a[x] = make_double2(v, 0.0);
+        a[x] = C{v, R(0)};
     }
     __syncthreads();
-    double2* r = fft_line(a, b, L, -1);
+    C* r = fft_line<R>(a, b, L, -1);
     if (live)
         for (int k = threadIdx.x; k < g.Kx; k += blockDim.x) spec[((size_t)z * g.Py + y) * g.Kx + k] = r[k];
 }
 
 // ---------------------------------------------------------------- pass B (y, forward), lines (z < N0z, kx)
-__global__ void k_fft_y_fwd(double2* __restrict__ spec, Geo g, FftLine L) {
-    extern __shared__ double2 sm[];
+template <typename R>
+__global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    C* sm = reinterpret_cast<C*>(fsm);
     const int z = blockIdx.y;
     const int kx = blockIdx.x * FFT_LY + threadIdx.y;
-    double2* a = sm + threadIdx.y * 2 * L.P;
-    double2* b = a + L.P;
+    C* a = sm + threadIdx.y * 2 * L.P;
+    C* b = a + L.P;
     const bool live = kx < g.Kx;
     for (int y = threadIdx.x; y < L.P; y += blockDim.x)
-        a[y] = (live && y < g.N0y) ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : make_double2(0.0, 0.0);
+        a[y] = (live && y < g.N0y) ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : C{R(0), R(0)};
     __syncthreads();
-    double2* r = fft_line(a, b, L, -1);
+    C* r = fft_line<R>(a, b, L, -1);
     if (live)
         for (int y = threadIdx.x; y < L.P; y += blockDim.x) spec[((size_t)z * g.Py + y) * g.Kx + kx] = r[y];
 }
 
 // ---------------------------------------------------------------- pass C (z forward, x G-hat, z inverse), lines (ky, kx)
-__global__ void k_fft_z_conv(double2* __restrict__ spec, const double* __restrict__ ghat, Geo g, FftLine L) {
-    extern __shared__ double2 sm[];
+template <typename R>
+__global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g, FftLine<R> L) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    C* sm = reinterpret_cast<C*>(fsm);
     const int ky = blockIdx.y;
     const int kx = blockIdx.x * FFT_LY + threadIdx.y;
-    double2* a = sm + threadIdx.y * 2 * L.P;
-    double2* b = a + L.P;
+    C* a = sm + threadIdx.y * 2 * L.P;
+    C* b = a + L.P;
     const bool live = kx < g.Kx;
     for (int z = threadIdx.x; z < L.P; z += blockDim.x)
-        a[z] = (live && z < g.N0z) ? spec[((size_t)z * g.Py + ky) * g.Kx + kx] : make_double2(0.0, 0.0);
+        a[z] = (live && z < g.N0z) ? spec[((size_t)z * g.Py + ky) * g.Kx + kx] : C{R(0), R(0)};
     __syncthreads();
-    double2* r = fft_line(a, b, L, -1);
+    C* r = fft_line<R>(a, b, L, -1);
     const int fy = ky <= g.Py - ky ? ky : g.Py - ky;
     for (int kz = threadIdx.x; kz < L.P; kz += blockDim.x) {
         const int fz = kz <= g.Pz - kz ? kz : g.Pz - kz;
-        const double gv = live ? ghat[((size_t)fz * g.Ky + fy) * g.Kx + kx] : 0.0;
-        r[kz] = make_double2(r[kz].x * gv, r[kz].y * gv);
+        const R gv = live ? ghat[((size_t)fz * g.Ky + fy) * g.Kx + kx] : R(0);
+        r[kz] = C{r[kz].x * gv, r[kz].y * gv};
     }
     __syncthreads();
-    double2* other = (r == a) ? b : a;
-    double2* q = fft_line(r, other, L, +1);
+    C* other = (r == a) ? b : a;
+    C* q = fft_line<R>(r, other, L, +1);
     if (live)
         for (int t = threadIdx.x; t < g.N0z + 2; t += blockDim.x) {
             const int z = (t - 1 + g.Pz) % g.Pz;
@@ -235,17 +252,20 @@ __global__ void k_fft_z_conv(double2* __restrict__ spec, const double* __restric
 }
 
 // ---------------------------------------------------------------- pass B' (y inverse), lines (target z, kx)
-__global__ void k_fft_y_inv(double2* __restrict__ spec, Geo g, FftLine L) {
-    extern __shared__ double2 sm[];
+template <typename R>
+__global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    C* sm = reinterpret_cast<C*>(fsm);
     const int z = ((int)blockIdx.y - 1 + g.Pz) % g.Pz;
     const int kx = blockIdx.x * FFT_LY + threadIdx.y;
-    double2* a = sm + threadIdx.y * 2 * L.P;
-    double2* b = a + L.P;
+    C* a = sm + threadIdx.y * 2 * L.P;
+    C* b = a + L.P;
     const bool live = kx < g.Kx;
     for (int y = threadIdx.x; y < L.P; y += blockDim.x)
-        a[y] = live ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : make_double2(0.0, 0.0);
+        a[y] = live ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : C{R(0), R(0)};
     __syncthreads();
-    double2* r = fft_line(a, b, L, +1);
+    C* r = fft_line<R>(a, b, L, +1);
     if (live)
         for (int t = threadIdx.x; t < g.N0y + 2; t += blockDim.x) {
             const int y = (t - 1 + g.Py) % g.Py;
@@ -256,18 +276,21 @@ __global__ void k_fft_y_inv(double2* __restrict__ spec, Geo g, FftLine L) {
 // ---------------------------------------------------------------- pass A' (x inverse, half spectrum -> real)
 // Writes u at target (x, y, z) in [-1, N0]^3 into every level-0 block whose
 // (n+2)^3 box holds that node (interior or ghost layer).
-__global__ void k_fft_x_inv(double* __restrict__ U0, const double2* __restrict__ spec, Geo g, FftLine L) {
-    extern __shared__ double2 sm[];
+template <typename R>
+__global__ void k_fft_x_inv(R* __restrict__ U0, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    C* sm = reinterpret_cast<C*>(fsm);
     const int line = blockIdx.x * FFT_LY + threadIdx.y;
-    double2* a = sm + threadIdx.y * 2 * L.P;
-    double2* b = a + L.P;
+    C* a = sm + threadIdx.y * 2 * L.P;
+    C* b = a + L.P;
     const int ny = g.N0y + 2;
     const bool live = line < ny * (g.N0z + 2);
     const int ty = live ? line % ny - 1 : 0, tz = live ? line / ny - 1 : 0;
     const int yi = (ty + g.Py) % g.Py, zi = (tz + g.Pz) % g.Pz;
-    const double2* src = spec + ((size_t)zi * g.Py + yi) * g.Kx;
+    const C* src = spec + ((size_t)zi * g.Py + yi) * g.Kx;
     for (int k = threadIdx.x; k < L.P; k += blockDim.x) {
-        double2 v = make_double2(0.0, 0.0);
+        C v = C{R(0), R(0)};
         if (live) {
             if (k < g.Kx) v = src[k];
             else { v = src[L.P - k]; v.y = -v.y; }
@@ -275,12 +298,12 @@ __global__ void k_fft_x_inv(double* __restrict__ U0, const double2* __restrict__
         a[k] = v;
     }
     __syncthreads();
-    double2* r = fft_line(a, b, L, +1);
+    C* r = fft_line<R>(a, b, L, +1);
     if (!live) return;
     const int S = g.n + 2;
     for (int t = threadIdx.x; t < g.N0x + 2; t += blockDim.x) {
         const int tx = t - 1;
-        const double val = r[(tx + g.Px) % g.Px].x;
+        const R val = r[(tx + g.Px) % g.Px].x;
         for (int bz = (tz - 1 < 0 ? -1 : (tz - 1) / g.n); bz <= (tz + 1) / g.n; ++bz) {
             if (bz < 0 || bz >= g.nbz || tz < bz * g.n - 1 || tz > bz * g.n + g.n) continue;
             for (int by = (ty - 1 < 0 ? -1 : (ty - 1) / g.n); by <= (ty + 1) / g.n; ++by) {
@@ -306,36 +329,39 @@ static Geo geo_of(const Handle& h) {
     return g;
 }
 
-void launch_coarse_solve(Handle& h, cudaStream_t s) {
+template <typename R>
+static void coarse_passes(const Handle& h, typename Cx<R>::T* spec, const R* ghat, const R* F0, R* U0, cudaStream_t s) {
+    using C = typename Cx<R>::T;
     const Geo g = geo_of(h);
     const dim3 blk(FFT_TX, FFT_LY);
-    const FftLine Lx = line_of(h.ax[0]), Ly = line_of(h.ax[1]), Lz = line_of(h.ax[2]);
-    const size_t smx = sizeof(double2) * 2 * FFT_LY * g.Px;
-    const size_t smy = sizeof(double2) * 2 * FFT_LY * g.Py;
-    const size_t smz = sizeof(double2) * 2 * FFT_LY * g.Pz;
+    const FftLine<R> Lx = line_of<R>(h.ax[0]), Ly = line_of<R>(h.ax[1]), Lz = line_of<R>(h.ax[2]);
+    const size_t smx = sizeof(C) * 2 * FFT_LY * g.Px;
+    const size_t smy = sizeof(C) * 2 * FFT_LY * g.Py;
+    const size_t smz = sizeof(C) * 2 * FFT_LY * g.Pz;
     const int kxb = (g.Kx + FFT_LY - 1) / FFT_LY;
-    k_fft_x_fwd<<<(g.N0y * g.N0z + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(h.spec, h.lv[0].F, g, Lx);
-    k_fft_y_fwd<<<dim3(kxb, g.N0z), blk, smy, s>>>(h.spec, g, Ly);
-    k_fft_z_conv<<<dim3(kxb, g.Py), blk, smz, s>>>(h.spec, h.ghat, g, Lz);
-    k_fft_y_inv<<<dim3(kxb, g.N0z + 2), blk, smy, s>>>(h.spec, g, Ly);
-    k_fft_x_inv<<<((g.N0y + 2) * (g.N0z + 2) + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(h.lv[0].U, h.spec, g, Lx);
+    k_fft_x_fwd<R><<<(g.N0y * g.N0z + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(spec, F0, g, Lx);
+    k_fft_y_fwd<R><<<dim3(kxb, g.N0z), blk, smy, s>>>(spec, g, Ly);
+    k_fft_z_conv<R><<<dim3(kxb, g.Py), blk, smz, s>>>(spec, ghat, g, Lz);
+    k_fft_y_inv<R><<<dim3(kxb, g.N0z + 2), blk, smy, s>>>(spec, g, Ly);
+    k_fft_x_inv<R><<<((g.N0y + 2) * (g.N0z + 2) + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(U0, spec, g, Lx);
 }
+
+void launch_coarse_solve(Handle& h, cudaStream_t s) {
+    coarse_passes<double>(h, h.spec, h.ghat, h.lv[0].F, h.lv[0].U, s);
+}
+
+template <typename T>
+void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s) {
+    if constexpr (sizeof(T) == 8) coarse_passes<double>(h, h.spec, h.ghat, F0, U0, s);
+    else coarse_passes<float>(h, h.spec32, h.ghat32, F0, U0, s);
+}
+template void launch_coarse_solve_t<double>(const Handle&, const double*, double*, cudaStream_t);
+template void launch_coarse_solve_t<float>(const Handle&, const float*, float*, cudaStream_t);
 
 // Same five passes with the spectral buffer, source and output given by the
 // caller (spec must hold Pz * Py * (Px/2+1) complex values).
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s) {
-    const Geo g = geo_of(h);
-    const dim3 blk(FFT_TX, FFT_LY);
-    const FftLine Lx = line_of(h.ax[0]), Ly = line_of(h.ax[1]), Lz = line_of(h.ax[2]);
-    const size_t smx = sizeof(double2) * 2 * FFT_LY * g.Px;
-    const size_t smy = sizeof(double2) * 2 * FFT_LY * g.Py;
-    const size_t smz = sizeof(double2) * 2 * FFT_LY * g.Pz;
-    const int kxb = (g.Kx + FFT_LY - 1) / FFT_LY;
-    k_fft_x_fwd<<<(g.N0y * g.N0z + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(spec, F0, g, Lx);
-    k_fft_y_fwd<<<dim3(kxb, g.N0z), blk, smy, s>>>(spec, g, Ly);
-    k_fft_z_conv<<<dim3(kxb, g.Py), blk, smz, s>>>(spec, h.ghat, g, Lz);
-    k_fft_y_inv<<<dim3(kxb, g.N0z + 2), blk, smy, s>>>(spec, g, Ly);
-    k_fft_x_inv<<<((g.N0y + 2) * (g.N0z + 2) + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(U0, spec, g, Lx);
+    coarse_passes<double>(h, spec, h.ghat, F0, U0, s);
 }
 
 // ============================================================================
@@ -605,11 +631,16 @@ int fft_plan(Handle& h) {
     const size_t ns = (size_t)h.ax[2].P * h.ax[1].P * h.ax[0].K;
     if (cudaMalloc(&h.spec, sizeof(double2) * ns) != cudaSuccess) return MRP_ERR_OOM;
     const int mx = MAX_DYN_SMEM;
-    cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_y_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_z_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_y_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_x_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_y_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_z_conv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_y_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_x_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_x_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_y_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_z_conv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_y_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_fft_x_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return MRP_OK;
 }
 

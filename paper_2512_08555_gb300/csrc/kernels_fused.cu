@@ -1,0 +1,504 @@
+// Stencil kernels that build their block's ghost layer in shared memory
+// (arXiv 2512.08555, Sec. 2.1 ghosting fused into the Sec. 3.1 smoother,
+// residual and FAS right-hand side).
+//
+// Each CTA handles one block of level k.  build_halo() stages the block and a
+// one-node ghost layer in shared memory:
+//  * interior: the block's own values;
+//  * ghost regions whose same-level neighbour exists: that neighbour's values;
+//  * ghost regions outside the domain (level 0 only): the block's stored ghost
+//    layer, i.e. the exterior ring written by the level-0 solve;
+//  * the other ghost regions: the I-point (I = M + 2) tensor-product Lagrange
+//    interpolant of level k-1, evaluated separably (reduction along the
+//    region's normal axes into a small array, then the tangential stencil).
+//    A coarse node covered by level k takes the value of its coincident
+//    level-k node (the injection of the current fine values), read from the
+//    fine level directly.
+// All values are read from the input buffers, which no CTA of the launch
+// writes: ghost layers are frozen for the duration of a sweep, which writes
+// its result to a second buffer.
+#include "mrp_internal.h"
+
+namespace mrp {
+
+template <int M> struct LW;
+template <> struct LW<2> { static constexpr double den = 1, c = -6, f = 1, e = 0, k = 0; };
+template <> struct LW<4> { static constexpr double den = 6, c = -24, f = 2, e = 1, k = 0; };
+template <> struct LW<6> { static constexpr double den = 30, c = -128, f = 14, e = 3, k = 1; };
+
+template <int M, typename T>
+__device__ __forceinline__ T offc(const T* __restrict__ a, int o, int S, int S2) {
+    using W = LW<M>;
+    T acc = T(W::f) * ((a[o - 1] + a[o + 1]) + (a[o - S] + a[o + S]) + (a[o - S2] + a[o + S2]));
+    if (W::e != 0)
+        acc += T(W::e) * ((a[o - 1 - S] + a[o + 1 - S]) + (a[o - 1 + S] + a[o + 1 + S])
+                          + (a[o - 1 - S2] + a[o + 1 - S2]) + (a[o - 1 + S2] + a[o + 1 + S2])
+                          + (a[o - S - S2] + a[o + S - S2]) + (a[o - S + S2] + a[o + S + S2]));
+    if (W::k != 0)
+        acc += T(W::k) * ((a[o - 1 - S - S2] + a[o + 1 - S - S2]) + (a[o - 1 + S - S2] + a[o + 1 + S - S2])
+                          + (a[o - 1 - S + S2] + a[o + 1 - S + S2]) + (a[o - 1 + S + S2] + a[o + 1 + S + S2]));
+    return acc;
+}
+
+template <int M, typename T>
+__device__ __forceinline__ T lhs(const T* __restrict__ a, int o, int S, int S2) {
+    return T(LW<M>::c) * a[o] + offc<M>(a, o, S, S2);
+}
+
+template <int I> __device__ __forceinline__ double midw(int m);
+template <> __device__ __forceinline__ double midw<4>(int m) { return (m == 0 || m == 3 ? -1.0 : 9.0) / 16.0; }
+template <> __device__ __forceinline__ double midw<6>(int m) {
+    return (m == 0 || m == 5 ? 3.0 : (m == 1 || m == 4 ? -25.0 : 150.0)) / 256.0;
+}
+template <> __device__ __forceinline__ double midw<8>(int m) {
+    const int k = m < 4 ? m : 7 - m;
+    return (k == 0 ? -5.0 : (k == 1 ? 49.0 : (k == 2 ? -245.0 : 1225.0))) / 2048.0;
+}
+
+// Reduced-array extent per tangential axis: patch indices [tlo, tlo + TN)
+// cover every tangential stencil of fine coordinates 0..n-1.  Patch index
+// 4 + floor(q/2) is the coarse node at or left of fine coordinate q.
+template <int I> __device__ __forceinline__ int tan_lo() { return 4 - I / 2 + 1; }
+__host__ __device__ inline int tan_n(int n, int I) { return n / 2 + I - 1; }
+
+// Coordinates of shell node t of an S^3 box without its (S-2)^3 interior:
+// the z = 0 and z = S-1 planes, then the ring of each inner z plane.
+__device__ __forceinline__ void shell_coords(int t, int S, int& x, int& y, int& z) {
+    const int S2 = S * S;
+    if (t < S2) { z = 0; y = t / S; x = t % S; return; }
+    t -= S2;
+    if (t < S2) { z = S - 1; y = t / S; x = t % S; return; }
+    t -= S2;
+    const int ring = 4 * S - 4;
+    z = 1 + t / ring;
+    int q = t % ring;
+    if (q < S) { y = 0; x = q; return; }
+    q -= S;
+    if (q < S) { y = S - 1; x = q; return; }
+    q -= S;
+    y = 1 + (q >> 1);
+    x = (q & 1) ? S - 1 : 0;
+}
+
+// Shared scratch of build_halo besides the block itself.
+template <typename T>
+struct HaloSmem {
+    int snbr[27], cnbr[27], cleaf[27], cch[27 * 8], off[27], rdir[27], rstart[27];
+    T sw[8];
+    int interp, nreg, ntot;
+};
+
+__host__ __device__ inline int pool_size(int n, int I) {
+    const int TN = tan_n(n, I);
+    return 6 * TN * TN + 12 * TN + 8;
+}
+
+template <typename T, int I>
+__device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, HaloSmem<T>& hs,
+                           const T* __restrict__ Uk,
+                           const T* __restrict__ Uc, const LevelView& lk, const LevelView& lc, int b, int n) {
+    const int S = n + 2, S2 = S * S, S3 = S2 * S;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    if (tid < 27) hs.snbr[tid] = lk.nbr[27 * b + tid];
+    if (tid < I) hs.sw[tid] = T(midw<I>(tid));
+    __syncthreads();
+    const T* Ub = Uk + (size_t)b * S3;
+    if (tid == 0) {
+        int any = 0;
+        for (int d = 0; d < 27; ++d) any |= (d != 13 && hs.snbr[d] == NBR_MISSING);
+        hs.interp = any;
+    }
+    const int n3 = n * n * n;
+    for (int t = tid; t < n3; t += nth) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const int o = ((z + 1) * S + y + 1) * S + x + 1;
+        su[o] = Ub[o];
+    }
+    const int shell = S3 - n3;
+    for (int t = tid; t < shell; t += nth) {
+        int x, y, z;
+        shell_coords(t, S, x, y, z);
+        const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
+        const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
+        const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
+        const int j = hs.snbr[dir27(dx, dy, dz)];
+        const int o = (z * S + y) * S + x;
+        if (j >= 0) su[o] = Uk[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)];
+        else if (j == NBR_OUTSIDE) su[o] = Ub[o];
+    }
+    __syncthreads();
+    if (!hs.interp) return;
+    // coarse-neighbourhood tables of the parent
+    const int P = lk.parent[b];
+    if (tid < 27) {
+        const int cb = lc.nbr[27 * P + tid];
+        hs.cnbr[tid] = cb;
+        hs.cleaf[tid] = cb >= 0 ? (int)lc.is_leaf[cb] : 1;
+        for (int o = 0; o < 8; ++o) hs.cch[8 * tid + o] = (cb >= 0 && !hs.cleaf[tid]) ? lc.children[8 * cb + o] : -1;
+    }
+    const int TN = tan_n(n, I), TN2 = TN * TN;
+    if (tid == 0) {
+        int o = 0, nr = 0;
+        for (int d = 0; d < 27; ++d) {
+            hs.off[d] = o;
+            if (d == 13 || hs.snbr[d] != NBR_MISSING) continue;
+            const int nt = (d % 3 == 1) + ((d / 3) % 3 == 1) + (d / 9 == 1);
+            hs.rdir[nr] = d;
+            hs.rstart[nr] = o;
+            ++nr;
+            o += nt == 2 ? TN2 : (nt == 1 ? TN : 1);
+        }
+        hs.nreg = nr;
+        hs.ntot = o;
+    }
+    __syncthreads();
+    const int h = n >> 1;
+    const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
+    // stage the coarse patch, patch indices [plo, plo + PL) per axis (every
+    // normal and tangential stencil of this block's ghosts lies inside)
+    constexpr int plo = 4 - I / 2;
+    const int PL = h + I, PL2 = PL * PL, PL3 = PL2 * PL;
+    const int base[3] = {(bx & 1) * h - 4 + plo, (by & 1) * h - 4 + plo, (bz & 1) * h - 4 + plo};
+    for (int t = tid; t < PL3; t += nth) {
+        const int px = t % PL, py = (t / PL) % PL, pz = t / PL2;
+        const int rx = base[0] + px, ry = base[1] + py, rz = base[2] + pz;
+        const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0);
+        const int ey = ry < 0 ? -1 : (ry >= n ? 1 : 0);
+        const int ez = rz < 0 ? -1 : (rz >= n ? 1 : 0);
+        const int d = dir27(ex, ey, ez);
+        const int lx = rx - ex * n, ly = ry - ey * n, lz = rz - ez * n;
+        T v;
+        if (hs.cleaf[d]) {
+            v = Uc[(size_t)hs.cnbr[d] * S3 + ((lz + 1) * S + ly + 1) * S + lx + 1];
+        } else {
+            // covered coarse node: the coincident fine node of the current level
+            const int ox = lx >= h, oy = ly >= h, oz = lz >= h;
+            const int ch = hs.cch[8 * d + ox + 2 * oy + 4 * oz];
+            const int fo = ((2 * lz - oz * n + 1) * S + 2 * ly - oy * n + 1) * S + 2 * lx - ox * n + 1;
+            v = ch == b ? su[fo] : Uk[(size_t)ch * S3 + fo];
+        }
+        patch[t] = v;
+    }
+    __syncthreads();
+    // phase 1: reduce every interpolated region along its normal axes; the
+    // (region, element) pairs are spread evenly over the CTA
+    const int lo = 0;                   // stencil around fine coordinate -1: patch [4 - I/2, 4 + I/2) - plo
+    const int up = 4 + h - plo;         // patch index coincident with fine coordinate n
+    const int tlo = tan_lo<I>() - plo;
+    const int total = hs.ntot;
+    for (int f = tid; f < total; f += nth) {
+        int r = 0;
+        while (r + 1 < hs.nreg && hs.rstart[r + 1] <= f) ++r;
+        const int d = hs.rdir[r];
+        const int e = f - hs.rstart[r];
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        int tc[3] = {0, 0, 0};
+        int rem = e;
+        if (dx == 0) { tc[0] = tlo + rem % TN; rem /= TN; }
+        if (dy == 0) { tc[1] = tlo + rem % TN; rem /= TN; }
+        if (dz == 0) { tc[2] = tlo + rem % TN; }
+        const int cx = dx < 0 ? I : 1, cy = dy < 0 ? I : 1, cz = dz < 0 ? I : 1;
+        const int x0 = dx < 0 ? lo : (dx > 0 ? up : tc[0]);
+        const int y0 = dy < 0 ? lo : (dy > 0 ? up : tc[1]);
+        const int z0 = dz < 0 ? lo : (dz > 0 ? up : tc[2]);
+        T acc = T(0);
+        for (int mz = 0; mz < cz; ++mz) {
+            T ay = T(0);
+            for (int my = 0; my < cy; ++my) {
+                const T* row = patch + ((z0 + mz) * PL + y0 + my) * PL + x0;
+                T ax = T(0);
+                if (cx == 1) ax = row[0];
+                else {
+#pragma unroll
+                    for (int mx = 0; mx < I; ++mx) ax += hs.sw[mx] * row[mx];
+                }
+                ay += (cy == 1 ? T(1) : hs.sw[my]) * ax;
+            }
+            acc += (cz == 1 ? T(1) : hs.sw[mz]) * ay;
+        }
+        pool[hs.off[d] + e] = acc;
+    }
+    __syncthreads();
+    // phase 2: tangential interpolation of each ghost node from its region's reduced array
+    for (int t = tid; t < shell; t += nth) {
+        int x, y, z;
+        shell_coords(t, S, x, y, z);
+        const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
+        const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
+        const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
+        const int d = dir27(dx, dy, dz);
+        if (hs.snbr[d] != NBR_MISSING) continue;
+        const T* R = pool + hs.off[d];
+        int st0 = 0, st1 = 0, cn0 = 1, cn1 = 1, sd0 = 0, sd1 = 0, nt = 0, stride = 1;
+        const int q[3] = {x - 1, y - 1, z - 1};
+        const int dd[3] = {dx, dy, dz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (dd[a] != 0) continue;
+            const int qa = q[a];
+            // reduced-array index = patch index - tan_lo (patch index 4 + floor(q/2) at or left of q)
+            const int st = (qa & 1) ? 4 + ((qa - 1) >> 1) - I / 2 + 1 - tan_lo<I>() : 4 + (qa >> 1) - tan_lo<I>();
+            const int cn = (qa & 1) ? I : 1;
+            if (nt == 0) { st0 = st; cn0 = cn; sd0 = stride; }
+            else { st1 = st; cn1 = cn; sd1 = stride; }
+            stride *= TN;
+            ++nt;
+        }
+        T acc = T(0);
+        for (int m1 = 0; m1 < cn1; ++m1) {
+            T a0 = T(0);
+            const int rb = (st1 + m1) * sd1 + st0 * sd0;
+            for (int m0 = 0; m0 < cn0; ++m0) a0 += (cn0 == 1 ? T(1) : hs.sw[m0]) * R[rb + m0 * sd0];
+            acc += (cn1 == 1 ? T(1) : hs.sw[m1]) * a0;
+        }
+        su[(z * S + y) * S + x] = acc;
+    }
+    __syncthreads();
+}
+
+__host__ __device__ inline int patch_size(int n, int I) {
+    const int PL = n / 2 + I;
+    return PL * PL * PL;
+}
+
+template <typename T>
+__host__ __device__ inline size_t fused_smem(int n, int I) {
+    const size_t S = n + 2;
+    return sizeof(T) * (S * S * S + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
+}
+
+// ---------------------------------------------------------------- smoother
+// One Gauss-Seidel iteration (Sec. 3.1): 8 colours c = (x&1) + 2(y&1) + 4(z&1),
+// u <- (den h^2 f - offcentre) / c; reads Uin, writes the interior to Uout.
+template <int M, typename T, int I>
+__global__ void __launch_bounds__(256) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
+                                                      const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
+                                                      LevelView lc, int n, T h2den, const int* __restrict__ order) {
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    T* su = reinterpret_cast<T*>(fz_smem);
+    const int S = n + 2, S2 = S * S, S3 = S2 * S;
+    T* pool = su + S3;
+    T* patch = pool + pool_size(n, I);
+    __shared__ HaloSmem<T> hs;
+    const int b = order ? order[blockIdx.x] : blockIdx.x;
+    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, lc, b, n);
+    const T* Fb = F + (size_t)b * n * n * n;
+    const int h = n >> 1, h3 = h * h * h;
+    const T inv_c = T(1) / T(LW<M>::c);
+    for (int col = 0; col < 8; ++col) {
+        const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
+        for (int q = threadIdx.x; q < h3; q += blockDim.x) {
+            const int x = 2 * (q % h) + cx, y = 2 * ((q / h) % h) + cy, z = 2 * (q / (h * h)) + cz;
+            const int o = ((z + 1) * S + y + 1) * S + x + 1;
+            su[o] = (h2den * Fb[(z * n + y) * n + x] - offc<M>(su, o, S, S2)) * inv_c;
+        }
+        __syncthreads();
+    }
+    T* Ob = Uout + (size_t)b * S3;
+    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const int o = ((z + 1) * S + y + 1) * S + x + 1;
+        Ob[o] = su[o];
+    }
+}
+
+// ---------------------------------------------------------------- residual r = f - L u (all nodes)
+template <int M, typename T, int I>
+__global__ void __launch_bounds__(256) k_residual_fused(T* __restrict__ R, const T* __restrict__ U, const T* __restrict__ F,
+                                                        const T* __restrict__ Uc, LevelView lk, LevelView lc, int n, T scale,
+                                                        const int* __restrict__ order) {
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    T* su = reinterpret_cast<T*>(fz_smem);
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
+    T* pool = su + S3;
+    T* patch = pool + pool_size(n, I);
+    __shared__ HaloSmem<T> hs;
+    const int b = order ? order[blockIdx.x] : blockIdx.x;
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        R[(size_t)b * n3 + t] = F[(size_t)b * n3 + t] - scale * lhs<M>(su, ((z + 1) * S + y + 1) * S + x + 1, S, S2);
+    }
+}
+
+// ---------------------------------------------------------------- FAS RHS and u-hat (Alg. 1)
+// F += L u on covered blocks; H = u on every block.
+template <int M, typename T, int I>
+__global__ void __launch_bounds__(256) k_fas_fused(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U,
+                                                   const T* __restrict__ Uc, LevelView lk, LevelView lc, int n, T scale,
+                                                   const int* __restrict__ order) {
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    T* su = reinterpret_cast<T*>(fz_smem);
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
+    T* pool = su + S3;
+    T* patch = pool + pool_size(n, I);
+    __shared__ HaloSmem<T> hs;
+    const int b = order ? order[blockIdx.x] : blockIdx.x;
+    const bool cov = !lk.is_leaf[b];
+    if (!cov) {
+        const T* Ub = U + (size_t)b * S3;
+        for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+            const int x = t % n, y = (t / n) % n, z = t / (n * n);
+            H[(size_t)b * n3 + t] = Ub[((z + 1) * S + y + 1) * S + x + 1];
+        }
+        return;
+    }
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const int o = ((z + 1) * S + y + 1) * S + x + 1;
+        F[(size_t)b * n3 + t] += scale * lhs<M>(su, o, S, S2);
+        H[(size_t)b * n3 + t] = su[o];
+    }
+}
+
+// ---------------------------------------------------------------- leaf residual (FP64 stop rule / outer residual)
+__device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
+    __shared__ double red[32];
+    if (v != v) v = __longlong_as_double(0x7ff0000000000000ULL);
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+template <int M, int I>
+__global__ void __launch_bounds__(256) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
+                                                       const double* __restrict__ F, const double* __restrict__ Uc,
+                                                       const int* __restrict__ blocks, LevelView lk, LevelView lc, int n,
+                                                       double scale, unsigned long long* out) {
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    double* su = reinterpret_cast<double*>(fz_smem);
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
+    double* pool = su + S3;
+    double* patch = pool + pool_size(n, I);
+    __shared__ HaloSmem<double> hs;
+    const int b = blocks[blockIdx.x];
+    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
+    double m = 0.0;
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const double r = F[(size_t)b * n3 + t] - scale * lhs<M>(su, ((z + 1) * S + y + 1) * S + x + 1, S, S2);
+        if (R) R[(size_t)b * n3 + t] = r;
+        m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
+    }
+    bmax_atomic(m, out);
+}
+
+// ---------------------------------------------------------------- halo dump (step API)
+// Writes the ghost layer build_halo() produces into the block's stored ghost layer.
+template <typename T, int I>
+__global__ void __launch_bounds__(256) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, LevelView lc, int n) {
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    T* su = reinterpret_cast<T*>(fz_smem);
+    const int S = n + 2, S3 = S * S * S;
+    T* pool = su + S3;
+    T* patch = pool + pool_size(n, I);
+    __shared__ HaloSmem<T> hs;
+    const int b = blockIdx.x;
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int x = t % S, y = (t / S) % S, z = t / (S * S);
+        const bool interior = x > 0 && x < S - 1 && y > 0 && y < S - 1 && z > 0 && z < S - 1;
+        if (!interior) U[(size_t)b * S3 + t] = su[t];
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename K>
+static void allow(K kern) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM); }
+
+template <int M, typename T>
+static void set_attrs_m() {
+    constexpr int I = M + 2;
+    allow(k_smooth_fused<M, T, I>);
+    allow(k_residual_fused<M, T, I>);
+    allow(k_fas_fused<M, T, I>);
+}
+
+template <typename T>
+static void set_attrs() {
+    static bool done = false;
+    if (done) return;
+    set_attrs_m<2, T>(); set_attrs_m<4, T>(); set_attrs_m<6, T>();
+    allow(k_halo_dump<T, 4>); allow(k_halo_dump<T, 6>); allow(k_halo_dump<T, 8>);
+    if constexpr (sizeof(T) == 8) {
+        allow(k_leafres_fused<2, 4>); allow(k_leafres_fused<4, 6>); allow(k_leafres_fused<6, 8>);
+    }
+    done = true;
+}
+
+template <typename T>
+void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
+                         double h2, cudaStream_t s) {
+    if (lk.nb == 0) return;
+    set_attrs<T>();
+    const size_t sm = fused_smem<T>(n, M + 2);
+    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, 256, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<2>::den), lk.order);
+    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, 256, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<4>::den), lk.order);
+    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, 256, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<6>::den), lk.order);
+}
+
+template <typename T>
+void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
+                           double inv_h2, cudaStream_t s) {
+    if (lk.nb == 0) return;
+    set_attrs<T>();
+    const size_t sm = fused_smem<T>(n, M + 2);
+    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, 256, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, 256, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, 256, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+}
+
+template <typename T>
+void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, double inv_h2,
+                      cudaStream_t s) {
+    if (lk.nb == 0) return;
+    set_attrs<T>();
+    const size_t sm = fused_smem<T>(n, M + 2);
+    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, 256, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, 256, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, 256, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+}
+
+void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
+                          LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, cudaStream_t s) {
+    if (nblocks == 0) return;
+    set_attrs<double>();
+    const size_t sm = fused_smem<double>(n, M + 2);
+    if (M == 2) k_leafres_fused<2, 4><<<nblocks, 256, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<2>::den, out);
+    if (M == 4) k_leafres_fused<4, 6><<<nblocks, 256, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<4>::den, out);
+    if (M == 6) k_leafres_fused<6, 8><<<nblocks, 256, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<6>::den, out);
+}
+
+template <typename T>
+void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s) {
+    if (lk.nb == 0) return;
+    set_attrs<T>();
+    const size_t sm = fused_smem<T>(n, M + 2);
+    if (M == 2) k_halo_dump<T, 4><<<lk.nb, 256, sm, s>>>(U, Uc, lk, lc, n);
+    if (M == 4) k_halo_dump<T, 6><<<lk.nb, 256, sm, s>>>(U, Uc, lk, lc, n);
+    if (M == 6) k_halo_dump<T, 8><<<lk.nb, 256, sm, s>>>(U, Uc, lk, lc, n);
+}
+
+template void launch_smooth_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView, int,
+                                          int, double, cudaStream_t);
+template void launch_smooth_fused<float>(float*, const float*, const float*, const float*, LevelView, LevelView, int, int,
+                                         double, cudaStream_t);
+template void launch_residual_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView,
+                                            int, int, double, cudaStream_t);
+template void launch_residual_fused<float>(float*, const float*, const float*, const float*, LevelView, LevelView, int,
+                                           int, double, cudaStream_t);
+template void launch_fas_fused<double>(double*, double*, const double*, const double*, LevelView, LevelView, int, int,
+                                       double, cudaStream_t);
+template void launch_fas_fused<float>(float*, float*, const float*, const float*, LevelView, LevelView, int, int, double,
+                                      cudaStream_t);
+template void launch_halo_dump<double>(double*, const double*, LevelView, LevelView, int, int, cudaStream_t);
+template void launch_halo_dump<float>(float*, const float*, LevelView, LevelView, int, int, cudaStream_t);
+
+}  // namespace mrp

@@ -177,24 +177,28 @@ __global__ void __launch_bounds__(256) k_ghost_u(T* __restrict__ A, const T* __r
     }
 }
 
-size_t ghost_u_smem(int n) {
+template <typename T>
+static size_t ghost_u_smem(int n) {
     const int C = n / 2 + 9;
-    return sizeof(double) * ((size_t)C * C * C + 6 * C * C + 12 * C + 8);
+    return sizeof(T) * ((size_t)C * C * C + 6 * C * C + 12 * C + 8);
 }
 
-void launch_ghost_u(double* A, const double* Ac, LevelView lk, LevelView lkm1, int n, int M, cudaStream_t s) {
+template <typename T>
+void launch_ghost_u(T* A, const T* Ac, LevelView lk, LevelView lkm1, int n, int M, cudaStream_t s) {
     if (lk.nb == 0) return;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_ghost_u<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        cudaFuncSetAttribute(k_ghost_u<double, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        cudaFuncSetAttribute(k_ghost_u<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_ghost_u<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_ghost_u<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_ghost_u<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
         attr = true;
     }
-    const size_t sm = ghost_u_smem(n);
-    if (M == 2) k_ghost_u<double, 4><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lkm1, n);
-    if (M == 4) k_ghost_u<double, 6><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lkm1, n);
-    if (M == 6) k_ghost_u<double, 8><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lkm1, n);
+    const size_t sm = ghost_u_smem<T>(n);
+    if (M == 2) k_ghost_u<T, 4><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lkm1, n);
+    if (M == 4) k_ghost_u<T, 6><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lkm1, n);
+    if (M == 6) k_ghost_u<T, 8><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lkm1, n);
 }
+template void launch_ghost_u<double>(double*, const double*, LevelView, LevelView, int, int, cudaStream_t);
+template void launch_ghost_u<float>(float*, const float*, LevelView, LevelView, int, int, cudaStream_t);
 
 }  // namespace mrp

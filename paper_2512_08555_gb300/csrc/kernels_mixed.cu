@@ -1,0 +1,142 @@
+// Kernels of the FP64 iterative-refinement loop around FP32 V-cycles.
+//
+// The FP64 state is u at every node of levels >= 1 and the level-0 source f0
+// (f* on level-0 leaves, the unknown source s on level-0 nodes covered by
+// level 1); the level-0 field is always the FP64 free-space convolution of
+// f0.  The outer residual of the composite system has two parts: the leaf
+// equations f* - L_k u of levels >= 1, and c0 = u0(X) - u1(2X) on covered
+// level-0 nodes (the injection the converged multigrid state satisfies).
+#include "mrp_internal.h"
+
+namespace mrp {
+
+template <int M> struct LhsW64;
+template <> struct LhsW64<2> { static constexpr double den = 1, c = -6, f = 1, e = 0, k = 0; };
+template <> struct LhsW64<4> { static constexpr double den = 6, c = -24, f = 2, e = 1, k = 0; };
+template <> struct LhsW64<6> { static constexpr double den = 30, c = -128, f = 14, e = 3, k = 1; };
+
+template <int M>
+__device__ __forceinline__ double lhs64(const double* __restrict__ a, int o, int S, int S2) {
+    using W = LhsW64<M>;
+    double acc = W::c * a[o];
+    acc += W::f * ((a[o - 1] + a[o + 1]) + (a[o - S] + a[o + S]) + (a[o - S2] + a[o + S2]));
+    if (W::e != 0)
+        acc += W::e * ((a[o - 1 - S] + a[o + 1 - S]) + (a[o - 1 + S] + a[o + 1 + S])
+                       + (a[o - 1 - S2] + a[o + 1 - S2]) + (a[o - 1 + S2] + a[o + 1 + S2])
+                       + (a[o - S - S2] + a[o + S - S2]) + (a[o - S + S2] + a[o + S + S2]));
+    if (W::k != 0)
+        acc += W::k * ((a[o - 1 - S - S2] + a[o + 1 - S - S2]) + (a[o - 1 + S - S2] + a[o + 1 + S - S2])
+                       + (a[o - 1 - S + S2] + a[o + 1 - S + S2]) + (a[o - 1 + S + S2] + a[o + 1 + S + S2]));
+    return acc;
+}
+
+__device__ __forceinline__ void block_max_atomic64(double v, unsigned long long* out) {
+    __shared__ double red[32];
+    if (v != v) v = __longlong_as_double(0x7ff0000000000000ULL);
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// R = F - L U on leaf blocks (FP64), and the max-norm of R.
+template <int M>
+__global__ void k_leaf_residual_store(double* __restrict__ R, const double* __restrict__ U, const double* __restrict__ F,
+                                      const int* __restrict__ blocks, int n, double scale, unsigned long long* out) {
+    const int b = blocks[blockIdx.x];
+    const int S = n + 2, S2 = S * S, n3 = n * n * n;
+    const double* Ub = U + (size_t)b * S2 * S;
+    double m = 0.0;
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const double r = F[(size_t)b * n3 + t] - scale * lhs64<M>(Ub, ((z + 1) * S + y + 1) * S + x + 1, S, S2);
+        R[(size_t)b * n3 + t] = r;
+        m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
+    }
+    block_max_atomic64(m, out);
+}
+
+void launch_leaf_residual_store(double* R, const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
+                                double inv_h2, unsigned long long* out, cudaStream_t s) {
+    if (nleaf == 0) return;
+    if (M == 2) k_leaf_residual_store<2><<<nleaf, 256, 0, s>>>(R, U, F, leaf_blocks, n, inv_h2 / LhsW64<2>::den, out);
+    if (M == 4) k_leaf_residual_store<4><<<nleaf, 256, 0, s>>>(R, U, F, leaf_blocks, n, inv_h2 / LhsW64<4>::den, out);
+    if (M == 6) k_leaf_residual_store<6><<<nleaf, 256, 0, s>>>(R, U, F, leaf_blocks, n, inv_h2 / LhsW64<6>::den, out);
+}
+
+// c0 = u0(X) - u1(2X) on covered level-0 blocks; off32 = -c0 (FP32); max |c0| / h0^2.
+__global__ void k_c0(double* __restrict__ c0, float* __restrict__ off32, const double* __restrict__ U0,
+                     const double* __restrict__ U1, const int* __restrict__ cov0, const int* __restrict__ children0, int n,
+                     double inv_h2, unsigned long long* out) {
+    const int P = cov0[blockIdx.x];
+    const int S = n + 2, S3 = S * S * S, n3 = n * n * n, h = n >> 1;
+    double m = 0.0;
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int i = t % n, j = (t / n) % n, l = t / (n * n);
+        const int ox = i >= h, oy = j >= h, oz = l >= h;
+        const int c = children0[8 * P + ox + 2 * oy + 4 * oz];
+        const int fx = 2 * i - ox * n, fy = 2 * j - oy * n, fz = 2 * l - oz * n;
+        const double v = U0[(size_t)P * S3 + ((l + 1) * S + j + 1) * S + i + 1]
+                       - U1[(size_t)c * S3 + ((fz + 1) * S + fy + 1) * S + fx + 1];
+        c0[(size_t)P * n3 + t] = v;
+        off32[(size_t)P * n3 + t] = (float)(-v);
+        const double a = fabs(v) * inv_h2;
+        m = (v != v) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, a);
+    }
+    block_max_atomic64(m, out);
+}
+
+void launch_c0(double* c0, float* off32, const double* U0, const double* U1, const int* cov0, int ncov0, const int* children0,
+               int n, double inv_h2, unsigned long long* out, cudaStream_t s) {
+    if (ncov0 == 0) return;
+    k_c0<<<ncov0, 256, 0, s>>>(c0, off32, U0, U1, cov0, children0, n, inv_h2, out);
+}
+
+// FP32 right-hand side of the correction cycles: the FP64 leaf residual (or 0).
+__global__ void k_cast_rhs(float* __restrict__ F32, const double* __restrict__ R64, const int* __restrict__ blocks, int n,
+                           bool zero) {
+    const int b = blocks[blockIdx.x];
+    const int n3 = n * n * n;
+    for (int t = threadIdx.x; t < n3; t += blockDim.x)
+        F32[(size_t)b * n3 + t] = zero ? 0.0f : (float)R64[(size_t)b * n3 + t];
+}
+
+void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int nleaf, int n, bool zero, cudaStream_t s) {
+    if (nleaf == 0) return;
+    k_cast_rhs<<<nleaf, 256, 0, s>>>(F32, R64, leaf_blocks, n, zero);
+}
+
+// U64 += U32 on the interior of every block of a level.
+__global__ void k_accumulate_u(double* __restrict__ U64, const float* __restrict__ U32, int n) {
+    const int b = blockIdx.x;
+    const int S = n + 2, S3 = S * S * S;
+    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const size_t o = (size_t)b * S3 + ((z + 1) * S + y + 1) * S + x + 1;
+        U64[o] += (double)U32[o];
+    }
+}
+
+void launch_accumulate_u(double* U64, const float* U32, int nb, int n, cudaStream_t s) {
+    if (nb == 0) return;
+    k_accumulate_u<<<nb, 256, 0, s>>>(U64, U32, n);
+}
+
+// F64 += F32 on the given blocks (level-0 source on covered nodes).
+__global__ void k_accumulate_f(double* __restrict__ F64, const float* __restrict__ F32, const int* __restrict__ blocks, int n) {
+    const int b = blocks[blockIdx.x];
+    const int n3 = n * n * n;
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) F64[(size_t)b * n3 + t] += (double)F32[(size_t)b * n3 + t];
+}
+
+void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int nblocks, int n, cudaStream_t s) {
+    if (nblocks == 0) return;
+    k_accumulate_f<<<nblocks, 256, 0, s>>>(F64, F32, blocks, n);
+}
+
+}  // namespace mrp

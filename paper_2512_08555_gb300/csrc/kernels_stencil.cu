@@ -61,7 +61,7 @@ static InterpW interp_weights(int M) {
 // blocks that ghosting at a resolution jump reads).
 template <typename T>
 __global__ void k_inject_to_parent(T* __restrict__ coarse, int gc, const T* __restrict__ fine, int gf,
-                                   LevelView lf, int n) {
+                                   LevelView lf, int n, const T* __restrict__ off) {
     const int B = blockIdx.x;
     const int P = lf.parent[B];
     const int o = lf.octant[B];
@@ -69,18 +69,23 @@ __global__ void k_inject_to_parent(T* __restrict__ coarse, int gc, const T* __re
     const int Sf = n + 2 * gf, Sc = n + 2 * gc;
     const T* src = fine + (size_t)B * Sf * Sf * Sf;
     T* dst = coarse + (size_t)P * Sc * Sc * Sc;
+    const T* ob = off ? off + (size_t)P * n * n * n : nullptr;
     const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
     for (int t = threadIdx.x; t < h * h * h; t += blockDim.x) {
         const int i = t % h, j = (t / h) % h, l = t / (h * h);
-        dst[((gc + oz + l) * Sc + gc + oy + j) * Sc + gc + ox + i] =
-            src[((gf + 2 * l) * Sf + gf + 2 * j) * Sf + gf + 2 * i];
+        T v = src[((gf + 2 * l) * Sf + gf + 2 * j) * Sf + gf + 2 * i];
+        if (ob) v += ob[((oz + l) * n + oy + j) * n + ox + i];
+        dst[((gc + oz + l) * Sc + gc + oy + j) * Sc + gc + ox + i] = v;
     }
 }
 
-void launch_inject_to_parent(double* coarse, int gc, const double* fine, int gf, LevelView lf, int n, cudaStream_t s) {
+template <typename T>
+void launch_inject_to_parent(T* coarse, int gc, const T* fine, int gf, LevelView lf, int n, const T* off, cudaStream_t s) {
     if (lf.nb == 0) return;
-    k_inject_to_parent<double><<<lf.nb, 256, 0, s>>>(coarse, gc, fine, gf, lf, n);
+    k_inject_to_parent<T><<<lf.nb, 256, 0, s>>>(coarse, gc, fine, gf, lf, n, off);
 }
+template void launch_inject_to_parent<double>(double*, int, const double*, int, LevelView, int, const double*, cudaStream_t);
+template void launch_inject_to_parent<float>(float*, int, const float*, int, LevelView, int, const float*, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Ghosting (Sec. 2.1).  Halo node of block b in direction d: copied from the
@@ -268,24 +273,28 @@ __global__ void k_smooth(T* __restrict__ U, const T* __restrict__ F, int n, T h2
     }
 }
 
+template <typename T>
 static void smooth_attributes() {
     static bool done = false;
     if (done) return;
     const int mx = MAX_DYN_SMEM;
-    cudaFuncSetAttribute(k_smooth<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_smooth<4, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_smooth<6, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_smooth<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_smooth<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_smooth<6, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     done = true;
 }
 
-void launch_smooth(double* U, const double* F, int nb, int n, int M, double h2, cudaStream_t s) {
+template <typename T>
+void launch_smooth(T* U, const T* F, int nb, int n, int M, double h2, cudaStream_t s) {
     if (nb == 0) return;
-    smooth_attributes();
-    const size_t sm = sizeof(double) * (n + 2) * (n + 2) * (n + 2);
-    if (M == 2) k_smooth<2, double><<<nb, 256, sm, s>>>(U, F, n, h2 * LhsW<2>::den);
-    if (M == 4) k_smooth<4, double><<<nb, 256, sm, s>>>(U, F, n, h2 * LhsW<4>::den);
-    if (M == 6) k_smooth<6, double><<<nb, 256, sm, s>>>(U, F, n, h2 * LhsW<6>::den);
+    smooth_attributes<T>();
+    const size_t sm = sizeof(T) * (n + 2) * (n + 2) * (n + 2);
+    if (M == 2) k_smooth<2, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LhsW<2>::den));
+    if (M == 4) k_smooth<4, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LhsW<4>::den));
+    if (M == 6) k_smooth<6, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LhsW<6>::den));
 }
+template void launch_smooth<double>(double*, const double*, int, int, int, double, cudaStream_t);
+template void launch_smooth<float>(float*, const float*, int, int, int, double, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // r = f - L u on every node of every block (Alg. 1).
@@ -301,12 +310,15 @@ __global__ void k_residual(T* __restrict__ R, const T* __restrict__ U, const T* 
     }
 }
 
-void launch_residual(double* R, const double* U, const double* F, int nb, int n, int M, double inv_h2, cudaStream_t s) {
+template <typename T>
+void launch_residual(T* R, const T* U, const T* F, int nb, int n, int M, double inv_h2, cudaStream_t s) {
     if (nb == 0) return;
-    if (M == 2) k_residual<2, double><<<nb, 256, 0, s>>>(R, U, F, n, inv_h2 / LhsW<2>::den);
-    if (M == 4) k_residual<4, double><<<nb, 256, 0, s>>>(R, U, F, n, inv_h2 / LhsW<4>::den);
-    if (M == 6) k_residual<6, double><<<nb, 256, 0, s>>>(R, U, F, n, inv_h2 / LhsW<6>::den);
+    if (M == 2) k_residual<2, T><<<nb, 256, 0, s>>>(R, U, F, n, T(inv_h2 / LhsW<2>::den));
+    if (M == 4) k_residual<4, T><<<nb, 256, 0, s>>>(R, U, F, n, T(inv_h2 / LhsW<4>::den));
+    if (M == 6) k_residual<6, T><<<nb, 256, 0, s>>>(R, U, F, n, T(inv_h2 / LhsW<6>::den));
 }
+template void launch_residual<double>(double*, const double*, const double*, int, int, int, double, cudaStream_t);
+template void launch_residual<float>(float*, const float*, const float*, int, int, int, double, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Restriction from level k to the covered blocks of level k-1 (Alg. 1):
@@ -315,7 +327,7 @@ void launch_residual(double* R, const double* U, const double* F, int nb, int n,
 // restricted residual is left in F_{k-1}; k_fas_snapshot adds L u_{k-1}.
 template <typename T>
 __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __restrict__ Uf, const T* __restrict__ Rf,
-                           const int* __restrict__ cov, LevelView lc, LevelView lf, int n) {
+                           const int* __restrict__ cov, LevelView lc, LevelView lf, int n, const T* __restrict__ off) {
     const int P = cov[blockIdx.x];
     const int S = n + 2, S3 = S * S * S, n3 = n * n * n, h = n >> 1;
     const int* kids = lc.children + 8 * P;
@@ -324,7 +336,8 @@ __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __re
         const int ox = i >= h, oy = j >= h, oz = l >= h;
         const int c = kids[ox + 2 * oy + 4 * oz];
         const int fx = 2 * i - ox * n, fy = 2 * j - oy * n, fz = 2 * l - oz * n;
-        Uc[(size_t)P * S3 + ((l + 1) * S + j + 1) * S + i + 1] = Uf[(size_t)c * S3 + ((fz + 1) * S + fy + 1) * S + fx + 1];
+        Uc[(size_t)P * S3 + ((l + 1) * S + j + 1) * S + i + 1] = Uf[(size_t)c * S3 + ((fz + 1) * S + fy + 1) * S + fx + 1]
+                                                               + (off ? off[(size_t)P * n3 + t] : T(0));
         const int* cn = lf.nbr + 27 * c;
         T acc = T(0);
         bool inside = true;
@@ -349,12 +362,16 @@ __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __re
     }
 }
 
-void launch_restrict(Handle& h, int k, cudaStream_t s) {
-    Level& c = h.lv[k - 1];
-    Level& f = h.lv[k];
-    if (c.ncov == 0) return;
-    k_restrict<double><<<c.ncov, 256, 0, s>>>(c.U, c.F, f.U, f.R, c.cov_blocks, c.view(), f.view(), h.n);
+template <typename T>
+void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, const int* cov, int ncov, LevelView lc, LevelView lf, int n,
+                     const T* off, cudaStream_t s) {
+    if (ncov == 0) return;
+    k_restrict<T><<<ncov, 256, 0, s>>>(Uc, Fc, Uf, Rf, cov, lc, lf, n, off);
 }
+template void launch_restrict<double>(double*, double*, const double*, const double*, const int*, int, LevelView, LevelView,
+                                      int, const double*, cudaStream_t);
+template void launch_restrict<float>(float*, float*, const float*, const float*, const int*, int, LevelView, LevelView,
+                                     int, const float*, cudaStream_t);
 
 // F += L u on covered blocks; u-hat = u on every block of the level (Alg. 1).
 template <int M, typename T>
@@ -372,14 +389,15 @@ __global__ void k_fas_snapshot(T* __restrict__ F, T* __restrict__ H, const T* __
     }
 }
 
-void launch_fas_snapshot(Handle& h, int km1, cudaStream_t s) {
-    Level& c = h.lv[km1];
-    const double hk = h.h0 / (double)(1 << km1);
-    const double inv_h2 = 1.0 / (hk * hk);
-    if (h.M == 2) k_fas_snapshot<2, double><<<c.nb, 256, 0, s>>>(c.F, c.H, c.U, c.is_leaf, h.n, inv_h2 / LhsW<2>::den);
-    if (h.M == 4) k_fas_snapshot<4, double><<<c.nb, 256, 0, s>>>(c.F, c.H, c.U, c.is_leaf, h.n, inv_h2 / LhsW<4>::den);
-    if (h.M == 6) k_fas_snapshot<6, double><<<c.nb, 256, 0, s>>>(c.F, c.H, c.U, c.is_leaf, h.n, inv_h2 / LhsW<6>::den);
+template <typename T>
+void launch_fas_snapshot(T* F, T* H, const T* U, const uint8_t* is_leaf, int nb, int n, int M, double inv_h2, cudaStream_t s) {
+    if (nb == 0) return;
+    if (M == 2) k_fas_snapshot<2, T><<<nb, 256, 0, s>>>(F, H, U, is_leaf, n, T(inv_h2 / LhsW<2>::den));
+    if (M == 4) k_fas_snapshot<4, T><<<nb, 256, 0, s>>>(F, H, U, is_leaf, n, T(inv_h2 / LhsW<4>::den));
+    if (M == 6) k_fas_snapshot<6, T><<<nb, 256, 0, s>>>(F, H, U, is_leaf, n, T(inv_h2 / LhsW<6>::den));
 }
+template void launch_fas_snapshot<double>(double*, double*, const double*, const uint8_t*, int, int, int, double, cudaStream_t);
+template void launch_fas_snapshot<float>(float*, float*, const float*, const uint8_t*, int, int, int, double, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Coarse-grid correction (Alg. 1): eps = u_{k-1} - uhat_{k-1} on the coarse
@@ -424,12 +442,14 @@ __global__ void k_prolong(T* __restrict__ Uf, const T* __restrict__ Uc, const T*
     }
 }
 
-void launch_prolong(Handle& h, int k, cudaStream_t s) {
-    Level& f = h.lv[k];
-    Level& c = h.lv[k - 1];
-    const int E = h.n / 2 + 1;
-    k_prolong<double><<<f.nb, 256, sizeof(double) * E * E * E, s>>>(f.U, c.U, c.H, f.view(), c.view(), h.n);
+template <typename T>
+void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc, int n, cudaStream_t s) {
+    if (lf.nb == 0) return;
+    const int E = n / 2 + 1;
+    k_prolong<T><<<lf.nb, 256, sizeof(T) * E * E * E, s>>>(Uf, Uc, Hc, lf, lc, n);
 }
+template void launch_prolong<double>(double*, const double*, const double*, LevelView, LevelView, int, cudaStream_t);
+template void launch_prolong<float>(float*, const float*, const float*, LevelView, LevelView, int, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Max-norm reductions: warp shuffle, then one atomicMax per CTA on the bit

@@ -27,18 +27,22 @@ struct LevelView {
     const int* octant;     // [nb] child octant o = ox + 2 oy + 4 oz inside the parent
     const int* children;   // [nb][8] (-1 for leaves)
     const uint8_t* is_leaf;
+    const int* order;      // [nb] launch order: blocks with interpolated ghosts first
 };
 
 // Host + device tables of one level, plus its FP64 fields.
 struct Level {
     int nb = 0, nleaf = 0, ncov = 0;
-    std::vector<int> h_coords, h_nbr, h_parent, h_octant, h_children, h_leaf_blocks, h_cov_blocks;
+    std::vector<int> h_coords, h_nbr, h_parent, h_octant, h_children, h_leaf_blocks, h_cov_blocks, h_order;
     std::vector<uint8_t> h_is_leaf;
     int *coords = nullptr, *nbr = nullptr, *parent = nullptr, *octant = nullptr, *children = nullptr;
-    int *leaf_blocks = nullptr, *cov_blocks = nullptr;
+    int *leaf_blocks = nullptr, *cov_blocks = nullptr, *order = nullptr;
     uint8_t* is_leaf = nullptr;
     double *U = nullptr, *F = nullptr, *R = nullptr, *H = nullptr, *Fraw = nullptr;
-    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf}; }
+    double* Ualt = nullptr;           // second u buffer: a sweep reads U and writes Ualt, then they swap
+    float *U32 = nullptr, *F32 = nullptr, *R32 = nullptr, *H32 = nullptr;   // mixed precision inner cycles
+    float* U32alt = nullptr;
+    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order}; }
 };
 
 // One padded FFT axis: length, radix sequence, twiddles exp(-2 pi i m / P).
@@ -47,6 +51,7 @@ struct FftAxis {
     int nrad = 0;
     int rad[16];
     double2* tw = nullptr;            // device [P]
+    float2* tw32 = nullptr;           // device [P], FP32 copy
 };
 
 constexpr int MAX_RADIX_STAGES = 16;
@@ -70,6 +75,13 @@ struct Handle {
     FftAxis ax[3];
     double2* spec = nullptr;          // [Pz][Py][Kx]
     double* ghat = nullptr;           // [Kz][Ky][Kx] real spectrum, scaled by h0^2 / (Px Py Pz)
+    float* ghat32 = nullptr;          // FP32 copy
+    float2* spec32 = nullptr;         // FP32 spectral buffer
+    // mixed precision
+    bool mixed = false;
+    int inner_cycles = 4, max_ir = 12;
+    double* c0 = nullptr;             // [nb0 blocks][n^3] injection mismatch on covered level-0 nodes (FP64)
+    float* off32 = nullptr;           // [nb0 blocks][n^3] -c0 in FP32 (offset of the level-1 -> 0 injection)
     int gK[3];
     int lgf_nmax = 0;
     double* lgf = nullptr;            // [(nmax+1)^3]
@@ -86,12 +98,14 @@ struct Handle {
     int ev_used = 0;
     struct Pending { int phase, e0; int64_t nodes; };
     std::vector<Pending> pend;
-    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int64_t prof_cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, prof_nodes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double prof_ms[16] = {};
+    int64_t prof_cnt[16] = {}, prof_nodes[16] = {};
 };
 
 enum Phase { PH_GHOST = 0, PH_SMOOTH = 1, PH_RESIDUAL = 2, PH_RESTRICT = 3, PH_COARSE = 4, PH_PROLONG = 5,
              PH_NORM = 6, PH_OTHER = 7 };
+// Phases of FP32 work are counted separately, at index + 8.
+template <typename T> constexpr int ph(int p) { return p + (sizeof(T) == 4 ? 8 : 0); }
 
 // ---------------------------------------------------------------- host side
 int build_forest(Handle& h, const mrp_forest& f, std::string& why);
@@ -100,22 +114,56 @@ int lgf_build(Handle& h, cudaStream_t s);   // tabulate G and the scaled spectru
 int fft_plan(Handle& h);
 
 // ---------------------------------------------------------------- launches (kernels_*.cu)
-void launch_inject_to_parent(double* coarse, int gc, const double* fine, int gf, LevelView fine_lv, int n, cudaStream_t s);
+// Templated launchers are instantiated for double (FP64 path, outer refinement)
+// and float (inner cycles of the mixed-precision path).
+template <typename T>
+void launch_inject_to_parent(T* coarse, int gc, const T* fine, int gf, LevelView fine_lv, int n, const T* off, cudaStream_t s);
+template <typename T>
+void launch_ghost_u(T* A, const T* Ac, LevelView lk, LevelView lkm1, int n, int M, cudaStream_t s);
+template <typename T>
+void launch_smooth(T* U, const T* F, int nb, int n, int M, double h2, cudaStream_t s);
+template <typename T>
+void launch_residual(T* R, const T* U, const T* F, int nb, int n, int M, double inv_h2, cudaStream_t s);
+template <typename T>
+void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, const int* cov, int ncov, LevelView lc, LevelView lf, int n,
+                     const T* off, cudaStream_t s);
+template <typename T>
+void launch_fas_snapshot(T* F, T* H, const T* U, const uint8_t* is_leaf, int nb, int n, int M, double inv_h2, cudaStream_t s);
+template <typename T>
+void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc, int n, cudaStream_t s);
+template <typename T>
+void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
+// stencil kernels with the ghost layer built in shared memory (kernels_fused.cu)
+template <typename T>
+void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
+                         double h2, cudaStream_t s);
+template <typename T>
+void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
+                           double inv_h2, cudaStream_t s);
+template <typename T>
+void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, double inv_h2,
+                      cudaStream_t s);
+template <typename T>
+void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
+void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
+                          LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, cudaStream_t s);
+
 void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk, LevelView lkm1, int n, int M,
                        bool zero_outside, cudaStream_t s);
-void launch_ghost_u(double* A, const double* Ac, LevelView lk, LevelView lkm1, int n, int M, cudaStream_t s);
 void launch_scatter_leaves(Handle& h, const double* f, cudaStream_t s);
 void launch_gather_leaves(Handle& h, double* u, cudaStream_t s);
 void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int nleaf, int n, int M, cudaStream_t s);
-void launch_smooth(double* U, const double* F, int nb, int n, int M, double h2, cudaStream_t s);
-void launch_residual(double* R, const double* U, const double* F, int nb, int n, int M, double inv_h2, cudaStream_t s);
-void launch_restrict(Handle& h, int k, cudaStream_t s);
-void launch_fas_snapshot(Handle& h, int km1, cudaStream_t s);
-void launch_prolong(Handle& h, int k, cudaStream_t s);
 void launch_leaf_residual_max(const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
                               double inv_h2, unsigned long long* out, cudaStream_t s);
 void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, cudaStream_t s);
 void launch_coarse_solve(Handle& h, cudaStream_t s);
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s);
-
+// mixed precision helpers (kernels_mixed.cu)
+void launch_leaf_residual_store(double* R, const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
+                                double inv_h2, unsigned long long* out, cudaStream_t s);
+void launch_c0(double* c0, float* off32, const double* U0, const double* U1, const int* cov0, int ncov0, const int* children0,
+               int n, double inv_h2, unsigned long long* out, cudaStream_t s);
+void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int nleaf, int n, bool zero, cudaStream_t s);
+void launch_accumulate_u(double* U64, const float* U32, int nb, int n, cudaStream_t s);
+void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int nblocks, int n, cudaStream_t s);
 }  // namespace mrp

@@ -105,6 +105,14 @@ int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
         }
         lv.nleaf = (int)lv.h_leaf_blocks.size();
         lv.ncov = (int)lv.h_cov_blocks.size();
+        // launch order: blocks that interpolate ghosts (heavier) first
+        auto interp = [&](int b) {
+            for (int d = 0; d < 27; ++d) if (lv.h_nbr[(size_t)27 * b + d] == NBR_MISSING) return true;
+            return false;
+        };
+        for (int pass = 0; pass < 2; ++pass)
+            for (int b = 0; b < lv.nb; ++b) if (interp(b) == (pass == 0)) lv.h_order.push_back(b);
+        std::stable_partition(lv.h_leaf_blocks.begin(), lv.h_leaf_blocks.end(), interp);
     }
     // 2:1 balance across faces, edges and corners: each of the 26 neighbour
     // positions of a level-k block lies in a block of level k-1.
@@ -162,8 +170,10 @@ int upload_tables(Handle& h) {
         if ((rc = up(lv.children, lv.h_children))) return rc;
         if ((rc = up(lv.leaf_blocks, lv.h_leaf_blocks))) return rc;
         if ((rc = up(lv.cov_blocks, lv.h_cov_blocks))) return rc;
+        if ((rc = up(lv.order, lv.h_order))) return rc;
         if ((rc = up(lv.is_leaf, lv.h_is_leaf))) return rc;
         if ((rc = alloc_field(lv.U, lv.nb * S * S * S))) return rc;
+        if ((rc = alloc_field(lv.Ualt, lv.nb * S * S * S))) return rc;
         if ((rc = alloc_field(lv.F, lv.nb * n * n * n))) return rc;
         if ((rc = alloc_field(lv.R, lv.nb * n * n * n))) return rc;
         if ((rc = alloc_field(lv.H, lv.nb * n * n * n))) return rc;
@@ -179,10 +189,14 @@ int upload_tables(Handle& h) {
 static void release(Handle& h) {
     for (Level& lv : h.lv) {
         cudaFree(lv.coords); cudaFree(lv.nbr); cudaFree(lv.parent); cudaFree(lv.octant); cudaFree(lv.children);
-        cudaFree(lv.leaf_blocks); cudaFree(lv.cov_blocks); cudaFree(lv.is_leaf);
+        cudaFree(lv.leaf_blocks); cudaFree(lv.cov_blocks); cudaFree(lv.is_leaf); cudaFree(lv.order);
         cudaFree(lv.U); cudaFree(lv.F); cudaFree(lv.R); cudaFree(lv.H); cudaFree(lv.Fraw);
+        cudaFree(lv.U32); cudaFree(lv.F32); cudaFree(lv.R32); cudaFree(lv.H32);
+        cudaFree(lv.Ualt); cudaFree(lv.U32alt);
     }
     h.lv.clear();
+    for (int a = 0; a < 3; ++a) cudaFree(h.ax[a].tw32);
+    cudaFree(h.spec32); cudaFree(h.ghat32); cudaFree(h.c0); cudaFree(h.off32);
     cudaFree(h.leaf_level); cudaFree(h.leaf_block);
     for (int a = 0; a < 3; ++a) cudaFree(h.ax[a].tw);
     cudaFree(h.spec); cudaFree(h.ghat); cudaFree(h.lgf); cudaFree(h.dmax);
@@ -192,11 +206,55 @@ static void release(Handle& h) {
     h.ev.clear();
 }
 
+// FP32 workspace of the mixed-precision path: per-level fields, FP32 copies
+// of the twiddles and of the Green's-function spectrum, the FP32 spectral
+// buffer, and the level-0 injection mismatch (FP64) with its FP32 offset.
+static int mixed_setup(Handle& h) {
+    const size_t n = h.n, S = n + 2;
+    for (Level& lv : h.lv) {
+        const size_t nb = lv.nb;
+        if (cudaMalloc(&lv.U32, sizeof(float) * nb * S * S * S) != cudaSuccess) return MRP_ERR_OOM;
+        if (cudaMalloc(&lv.U32alt, sizeof(float) * nb * S * S * S) != cudaSuccess) return MRP_ERR_OOM;
+        cudaMemset(lv.U32alt, 0, sizeof(float) * nb * S * S * S);
+        if (cudaMalloc(&lv.F32, sizeof(float) * nb * n * n * n) != cudaSuccess) return MRP_ERR_OOM;
+        if (cudaMalloc(&lv.R32, sizeof(float) * nb * n * n * n) != cudaSuccess) return MRP_ERR_OOM;
+        if (cudaMalloc(&lv.H32, sizeof(float) * nb * n * n * n) != cudaSuccess) return MRP_ERR_OOM;
+        cudaMemset(lv.U32, 0, sizeof(float) * nb * S * S * S);
+        cudaMemset(lv.F32, 0, sizeof(float) * nb * n * n * n);
+        cudaMemset(lv.R32, 0, sizeof(float) * nb * n * n * n);
+        cudaMemset(lv.H32, 0, sizeof(float) * nb * n * n * n);
+    }
+    const size_t nb0 = h.lv[0].nb;
+    if (cudaMalloc(&h.c0, sizeof(double) * nb0 * n * n * n) != cudaSuccess) return MRP_ERR_OOM;
+    if (cudaMalloc(&h.off32, sizeof(float) * nb0 * n * n * n) != cudaSuccess) return MRP_ERR_OOM;
+    cudaMemset(h.c0, 0, sizeof(double) * nb0 * n * n * n);
+    cudaMemset(h.off32, 0, sizeof(float) * nb0 * n * n * n);
+    for (int a = 0; a < 3; ++a) {
+        const int P = h.ax[a].P;
+        std::vector<double2> tw(P);
+        std::vector<float2> tw32(P);
+        if (cudaMemcpy(tw.data(), h.ax[a].tw, sizeof(double2) * P, cudaMemcpyDeviceToHost) != cudaSuccess) return MRP_ERR_CUDA;
+        for (int m = 0; m < P; ++m) tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
+        if (cudaMalloc(&h.ax[a].tw32, sizeof(float2) * P) != cudaSuccess) return MRP_ERR_OOM;
+        if (cudaMemcpy(h.ax[a].tw32, tw32.data(), sizeof(float2) * P, cudaMemcpyHostToDevice) != cudaSuccess) return MRP_ERR_CUDA;
+    }
+    const size_t ng = (size_t)h.gK[0] * h.gK[1] * h.gK[2];
+    std::vector<double> g(ng);
+    std::vector<float> g32(ng);
+    if (cudaMemcpy(g.data(), h.ghat, sizeof(double) * ng, cudaMemcpyDeviceToHost) != cudaSuccess) return MRP_ERR_CUDA;
+    for (size_t i = 0; i < ng; ++i) g32[i] = (float)g[i];
+    if (cudaMalloc(&h.ghat32, sizeof(float) * ng) != cudaSuccess) return MRP_ERR_OOM;
+    if (cudaMemcpy(h.ghat32, g32.data(), sizeof(float) * ng, cudaMemcpyHostToDevice) != cudaSuccess) return MRP_ERR_CUDA;
+    const size_t ns = (size_t)h.ax[2].P * h.ax[1].P * h.ax[0].K;
+    if (cudaMalloc(&h.spec32, sizeof(float2) * ns) != cudaSuccess) return MRP_ERR_OOM;
+    return MRP_OK;
+}
+
 // ---------------------------------------------------------------- schedule (Alg. 1)
 static double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
 
 static LevelView view_or_empty(const Handle& h, int k) {
-    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 }
 
 // Per-phase accounting: counts launches; with profiling on, records a CUDA
@@ -238,45 +296,91 @@ static void harvest(Handle& h) {
 static int64_t n3(const Handle& h) { return (int64_t)h.n * h.n * h.n; }
 static int64_t halo_nodes(const Handle& h, int g) { const int64_t S = h.n + 2 * g; return S * S * S - n3(h); }
 
-// Ghosting of u on level k: covered level-(k-1) nodes first take the
-// injection of the level-k values, then the halo is copied / interpolated.
+// Per-level fields of one working precision: FP64 (plain path and outer
+// refinement) or FP32 (inner cycles of the mixed path).
+template <typename T> struct Fld { T *U, *F, *R, *H; };
+template <typename T> static Fld<T> fld(Handle& h, int k) {
+    if constexpr (sizeof(T) == 8) return Fld<T>{h.lv[k].U, h.lv[k].F, h.lv[k].R, h.lv[k].H};
+    else return Fld<T>{h.lv[k].U32, h.lv[k].F32, h.lv[k].R32, h.lv[k].H32};
+}
+// Offset added when level 1 is injected into the covered level-0 nodes: the
+// FP32 correction cycles carry -c0 there (see kernels_mixed.cu).
+template <typename T> static const T* off0(Handle& h) {
+    if constexpr (sizeof(T) == 4) return h.mixed ? h.off32 : nullptr;
+    else return nullptr;
+}
+
+template <typename T> static T*& ualt(Handle& h, int k) {
+    if constexpr (sizeof(T) == 8) return h.lv[k].Ualt;
+    else return h.lv[k].U32alt;
+}
+template <typename T> static T*& ucur(Handle& h, int k) {
+    if constexpr (sizeof(T) == 8) return h.lv[k].U;
+    else return h.lv[k].U32;
+}
+template <typename T> static const T* ucoarse(Handle& h, int k) { return k >= 1 ? ucur<T>(h, k - 1) : nullptr; }
+
+// Covered level-(k-1) nodes take the injection of the level-k values.
+template <typename T>
+static void inject_level(Handle& h, int k, cudaStream_t s) {
+    PhaseScope ps(h, s, ph<T>(PH_GHOST), h.lv[k].nb * n3(h) / 8, 1);
+    launch_inject_to_parent<T>(ucur<T>(h, k - 1), 1, ucur<T>(h, k), 1, h.lv[k].view(), h.n, k == 1 ? off0<T>(h) : nullptr, s);
+}
+
+// Ghosting of u on level k into the stored ghost layer (step API): the
+// injection into the covered level-(k-1) nodes, then the ghost layer that the
+// fused kernels build in shared memory.
+template <typename T>
 static void ghost_u(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_GHOST, h.lv[k].nb * halo_nodes(h, 1), k >= 1 ? 2 : 1);
-    if (k >= 1) launch_inject_to_parent(h.lv[k - 1].U, 1, h.lv[k].U, 1, h.lv[k].view(), h.n, s);
-    launch_ghost_u(h.lv[k].U, k >= 1 ? h.lv[k - 1].U : nullptr, h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, s);
+    if (k >= 1) inject_level<T>(h, k, s);
+    PhaseScope ps(h, s, ph<T>(PH_GHOST), h.lv[k].nb * halo_nodes(h, 1), 1);
+    launch_halo_dump<T>(ucur<T>(h, k), ucoarse<T>(h, k), h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, s);
 }
 
+// One Gauss-Seidel sweep with its ghost layer built in the kernel; reads the
+// current buffer, writes the other, then the two swap.
+template <typename T>
 static void smooth(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_SMOOTH, h.lv[k].nb * n3(h), 1);
+    PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h), 1);
     const double hk = level_h(h, k);
-    launch_smooth(h.lv[k].U, h.lv[k].F, h.lv[k].nb, h.n, h.M, hk * hk, s);
+    launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
+                           view_or_empty(h, k - 1), h.n, h.M, hk * hk, s);
+    std::swap(ualt<T>(h, k), ucur<T>(h, k));
 }
 
+template <typename T>
 static void residual(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_RESIDUAL, h.lv[k].nb * n3(h), 1);
+    PhaseScope ps(h, s, ph<T>(PH_RESIDUAL), h.lv[k].nb * n3(h), 1);
     const double hk = level_h(h, k);
-    launch_residual(h.lv[k].R, h.lv[k].U, h.lv[k].F, h.lv[k].nb, h.n, h.M, 1.0 / (hk * hk), s);
+    launch_residual_fused<T>(fld<T>(h, k).R, ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
+                             view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), s);
 }
 
-// Restriction k -> k-1: inject u, full-weight r, ghosts of u_{k-1}, FAS RHS, u-hat.
+// Restriction k -> k-1: inject u, full-weight r, FAS RHS on covered blocks, u-hat.
+template <typename T>
 static void restrict_level(Handle& h, int k, cudaStream_t s) {
+    Level& c = h.lv[k - 1];
     {
-        PhaseScope ps(h, s, PH_RESTRICT, h.lv[k - 1].ncov * n3(h), h.lv[k - 1].ncov > 0 ? 1 : 0);
-        launch_restrict(h, k, s);
+        PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.ncov * n3(h), c.ncov > 0 ? 1 : 0);
+        launch_restrict<T>(ucur<T>(h, k - 1), fld<T>(h, k - 1).F, ucur<T>(h, k), fld<T>(h, k).R, c.cov_blocks, c.ncov,
+                           c.view(), h.lv[k].view(), h.n, k == 1 ? off0<T>(h) : nullptr, s);
     }
-    ghost_u(h, k - 1, s);
-    PhaseScope ps(h, s, PH_RESTRICT, h.lv[k - 1].nb * n3(h), 1);
-    launch_fas_snapshot(h, k - 1, s);
+    PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.nb * n3(h), 1);
+    const double hk = level_h(h, k - 1);
+    launch_fas_fused<T>(fld<T>(h, k - 1).F, fld<T>(h, k - 1).H, ucur<T>(h, k - 1), ucoarse<T>(h, k - 1), c.view(),
+                        view_or_empty(h, k - 2), h.n, h.M, 1.0 / (hk * hk), s);
 }
 
+template <typename T>
 static void coarse_solve(Handle& h, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_COARSE, (int64_t)h.n0[0] * h.n0[1] * h.n0[2], 5);
-    launch_coarse_solve(h, s);
+    PhaseScope ps(h, s, ph<T>(PH_COARSE), (int64_t)h.n0[0] * h.n0[1] * h.n0[2], 5);
+    launch_coarse_solve_t<T>(h, fld<T>(h, 0).F, ucur<T>(h, 0), s);
 }
 
+template <typename T>
 static void prolong(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_PROLONG, h.lv[k].nb * n3(h), 1);
-    launch_prolong(h, k, s);
+    PhaseScope ps(h, s, ph<T>(PH_PROLONG), h.lv[k].nb * n3(h), 1);
+    launch_prolong<T>(ucur<T>(h, k), ucur<T>(h, k - 1), fld<T>(h, k - 1).H, h.lv[k].view(), h.lv[k - 1].view(), h.n, s);
 }
 
 static void prepare_rhs(Handle& h, const double* f, cudaStream_t s) {
@@ -284,28 +388,94 @@ static void prepare_rhs(Handle& h, const double* f, cudaStream_t s) {
     const size_t S4 = h.n + 4;
     for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].Fraw, 0, sizeof(double) * h.lv[k].nb * S4 * S4 * S4, s);
     launch_scatter_leaves(h, f, s);
-    for (int k = h.L - 1; k >= 0; --k) launch_inject_to_parent(h.lv[k].Fraw, 2, h.lv[k + 1].Fraw, 2, h.lv[k + 1].view(), h.n, s);
+    for (int k = h.L - 1; k >= 0; --k)
+        launch_inject_to_parent<double>(h.lv[k].Fraw, 2, h.lv[k + 1].Fraw, 2, h.lv[k + 1].view(), h.n, nullptr, s);
     for (int k = 0; k <= h.L; ++k)
         launch_ghost_fill(h.lv[k].Fraw, 2, k >= 1 ? h.lv[k - 1].Fraw : nullptr, 2, h.lv[k].view(), view_or_empty(h, k - 1),
                           h.n, h.M, true, s);
     for (int k = 0; k <= h.L; ++k) launch_rhs_star(h.lv[k].F, h.lv[k].Fraw, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.M, s);
 }
 
+// One adaptive V(nu1, nu2) cycle, Alg. 1, in precision T.
+template <typename T>
 static void vcycle(Handle& h, cudaStream_t s) {
     for (int k = h.L; k >= 1; --k) {
-        for (int i = 0; i < h.nu1; ++i) { ghost_u(h, k, s); smooth(h, k, s); }
-        ghost_u(h, k, s);
-        residual(h, k, s);
-        restrict_level(h, k, s);
+        for (int i = 0; i < h.nu1; ++i) smooth<T>(h, k, s);
+        residual<T>(h, k, s);
+        restrict_level<T>(h, k, s);
     }
-    coarse_solve(h, s);
+    coarse_solve<T>(h, s);
     for (int k = 1; k <= h.L; ++k) {
-        prolong(h, k, s);
-        for (int i = 0; i < h.nu2; ++i) { ghost_u(h, k, s); smooth(h, k, s); }
+        prolong<T>(h, k, s);
+        for (int i = 0; i < h.nu2; ++i) smooth<T>(h, k, s);
     }
 }
 
 static double as_double(unsigned long long b) { double d; std::memcpy(&d, &b, sizeof d); return d; }
+
+static int read_max(Handle& h, cudaStream_t s, double* out, int slot) {
+    if (cudaMemcpyAsync(h.hmax + slot, h.dmax + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MRP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
+    *out = as_double(h.hmax[slot]);
+    harvest(h);
+    return MRP_OK;
+}
+
+// Iterative refinement: FP64 outer residual of the composite system, FP32
+// correction V-cycles, FP64 accumulation.  Returns MRP_OK with *rel set.
+static int solve_mixed(Handle& h, cudaStream_t s, double scale, double* rel_out, int* cycles_out, int* ir_out) {
+    const size_t n = h.n, S = n + 2, n3 = n * n * n;
+    Level& l0 = h.lv[0];
+    const double inv_h02 = 1.0 / (h.h0 * h.h0);
+    int cycles = 0, ir = 0;
+    double rel = INFINITY;
+    for (;;) {
+        // level-0 field of the accumulated source, in FP64
+        coarse_solve<double>(h, s);
+        cudaMemsetAsync(h.dmax + 1, 0, sizeof(unsigned long long), s);
+        for (int k = h.L; k >= 2; --k) inject_level<double>(h, k, s);
+        if (h.L >= 1) {
+            PhaseScope ps(h, s, PH_NORM, l0.ncov * n3, l0.ncov > 0 ? 1 : 0);
+            launch_c0(h.c0, h.off32, l0.U, h.lv[1].U, l0.cov_blocks, l0.ncov, l0.children, h.n, inv_h02, h.dmax + 1, s);
+        }
+        for (int k = 1; k <= h.L; ++k) {
+            PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3, h.lv[k].nleaf > 0 ? 1 : 0);
+            const double hk = level_h(h, k);
+            launch_leafres_fused(h.lv[k].R, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks,
+                                 h.lv[k].nleaf, h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk),
+                                 h.dmax + 1, s);
+        }
+        double r = 0.0;
+        const int rc = read_max(h, s, &r, 1);
+        if (rc) return rc;
+        rel = r / scale;
+        if (!std::isfinite(rel)) { *rel_out = rel; *cycles_out = cycles; *ir_out = ir; return MRP_ERR_NUMERICAL; }
+        if (rel < h.tol || ir >= h.max_ir || cycles >= h.max_cycles) break;
+        // FP32 correction cycles on the residual
+        {
+            PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, h.L + 1);
+            for (int k = 1; k <= h.L; ++k)
+                launch_cast_rhs(h.lv[k].F32, h.lv[k].R, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, false, s);
+            launch_cast_rhs(l0.F32, nullptr, l0.leaf_blocks, l0.nleaf, h.n, true, s);
+        }
+        for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U32, 0, sizeof(float) * h.lv[k].nb * S * S * S, s);
+        for (int c = 0; c < h.inner_cycles; ++c) {
+            vcycle<float>(h, s);
+            ++cycles;
+        }
+        {
+            PhaseScope ps(h, s, PH_OTHER, h.total_nodes, h.L + 1);
+            for (int k = 1; k <= h.L; ++k) launch_accumulate_u(h.lv[k].U, h.lv[k].U32, h.lv[k].nb, h.n, s);
+            launch_accumulate_f(l0.F, l0.F32, l0.cov_blocks, l0.ncov, h.n, s);
+        }
+        ++ir;
+    }
+    *rel_out = rel;
+    *cycles_out = cycles;
+    *ir_out = ir;
+    return MRP_OK;
+}
 
 }  // namespace mrp
 
@@ -340,7 +510,8 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
     if (opt->order != 2 && opt->order != 4 && opt->order != 6) return MRP_ERR_INVALID_ARG;
     if (opt->nu1 < 0 || opt->nu2 < 0 || opt->max_cycles < 1 || !(opt->tol >= 0.0)) return MRP_ERR_INVALID_ARG;
     if (opt->stop_rule != MRP_STOP_RESIDUAL && opt->stop_rule != MRP_STOP_CAUCHY) return MRP_ERR_INVALID_ARG;
-    if (opt->precision != MRP_FP64) return MRP_ERR_UNSUPPORTED;
+    if (opt->precision != MRP_FP64 && opt->precision != MRP_MIXED) return MRP_ERR_INVALID_ARG;
+    if (opt->inner_cycles < 0 || opt->max_outer < 0) return MRP_ERR_INVALID_ARG;
     if (opt->stop_rule == MRP_STOP_CAUCHY) return MRP_ERR_UNSUPPORTED;
     if (forests[0].ncomp != 1) return MRP_ERR_UNSUPPORTED;
     mrp_handle* H = new (std::nothrow) mrp_handle();
@@ -348,11 +519,15 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
     Handle& h = H->h;
     h.M = opt->order; h.nu1 = opt->nu1; h.nu2 = opt->nu2; h.max_cycles = opt->max_cycles;
     h.tol = opt->tol; h.stop_rule = opt->stop_rule;
+    h.mixed = opt->precision == MRP_MIXED;
+    h.inner_cycles = opt->inner_cycles > 0 ? opt->inner_cycles : 4;
+    h.max_ir = opt->max_outer > 0 ? opt->max_outer : 12;
     std::string why;
     int rc = build_forest(h, forests[0], why);
     if (rc == MRP_OK) rc = upload_tables(h);
     if (rc == MRP_OK) rc = fft_plan(h);
     if (rc == MRP_OK) rc = lgf_build(h, 0);
+    if (rc == MRP_OK && h.mixed) rc = mixed_setup(h);
     if (rc == MRP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = MRP_ERR_CUDA;
     if (rc != MRP_OK) {
         cudaGetLastError();
@@ -371,23 +546,15 @@ int mrp_destroy(mrp_handle* H) {
     return MRP_OK;
 }
 
-static int read_max(Handle& h, cudaStream_t s, double* out, int slot) {
-    if (cudaMemcpyAsync(h.hmax + slot, h.dmax + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return MRP_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
-    *out = as_double(h.hmax[slot]);
-    harvest(h);
-    return MRP_OK;
-}
 
 static double leaf_residual(Handle& h, cudaStream_t s, int* rc) {
     cudaMemsetAsync(h.dmax + 1, 0, sizeof(unsigned long long), s);
+    for (int k = h.L; k >= 1; --k) inject_level<double>(h, k, s);
     for (int k = h.L; k >= 0; --k) {
-        ghost_u(h, k, s);
         PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
         const double hk = level_h(h, k);
-        launch_leaf_residual_max(h.lv[k].U, h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.M, 1.0 / (hk * hk),
-                                 h.dmax + 1, s);
+        launch_leafres_fused(nullptr, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
+                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.dmax + 1, s);
     }
     double r = 0.0;
     *rc = read_max(h, s, &r, 1);
@@ -401,6 +568,7 @@ int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats
     const size_t S = h.n + 2;
     int rc = MRP_OK;
     const int64_t launches0 = h.launches;
+    if (h.mixed) cudaMemsetAsync(h.lv[0].F, 0, sizeof(double) * h.lv[0].nb * h.n * h.n * h.n, s);
     prepare_rhs(h, f, s);
     cudaMemsetAsync(h.dmax, 0, sizeof(unsigned long long), s);
     {
@@ -411,15 +579,20 @@ int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats
     for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U, 0, sizeof(double) * h.lv[k].nb * S * S * S, s);
     const double scale = h.fstar_max > 0.0 ? h.fstar_max : 1.0;
     double rel = INFINITY;
-    int cycles = 0;
-    for (; cycles < h.max_cycles;) {
-        vcycle(h, s);
-        ++cycles;
-        const double r = leaf_residual(h, s, &rc);
-        if (rc) return rc;
-        rel = r / scale;
-        if (!std::isfinite(rel)) { rc = MRP_ERR_NUMERICAL; break; }
-        if (rel < h.tol) break;
+    int cycles = 0, ir = 0;
+    if (!h.mixed) {
+        for (; cycles < h.max_cycles;) {
+            vcycle<double>(h, s);
+            ++cycles;
+            const double r = leaf_residual(h, s, &rc);
+            if (rc) return rc;
+            rel = r / scale;
+            if (!std::isfinite(rel)) { rc = MRP_ERR_NUMERICAL; break; }
+            if (rel < h.tol) break;
+        }
+    } else {
+        rc = solve_mixed(h, s, scale, &rel, &cycles, &ir);
+        if (rc == MRP_ERR_CUDA) return rc;
     }
     {
         PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1);
@@ -431,6 +604,7 @@ int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats
     if (st) {
         std::memset(st, 0, sizeof(*st));
         st->cycles = cycles;
+        st->ir_steps = ir;
         st->residual = rel;
         st->fstar_max = h.fstar_max;
         st->leaf_nodes = h.leaf_nodes;
@@ -497,29 +671,29 @@ int mrp_step(mrp_handle* H, int32_t step, int32_t level, const double* f_leaf, v
             break;
         case MRP_STEP_GHOST_U:
             if (!lvl_ok) return MRP_ERR_INVALID_ARG;
-            ghost_u(h, level, s);
+            ghost_u<double>(h, level, s);
             break;
         case MRP_STEP_SMOOTH:
             if (!lvl_ok) return MRP_ERR_INVALID_ARG;
-            smooth(h, level, s);
+            smooth<double>(h, level, s);
             break;
         case MRP_STEP_RESIDUAL:
             if (!lvl_ok) return MRP_ERR_INVALID_ARG;
-            residual(h, level, s);
+            residual<double>(h, level, s);
             break;
         case MRP_STEP_RESTRICT:
             if (!lvl_ok || level < 1) return MRP_ERR_INVALID_ARG;
-            restrict_level(h, level, s);
+            restrict_level<double>(h, level, s);
             break;
         case MRP_STEP_COARSE_SOLVE:
-            coarse_solve(h, s);
+            coarse_solve<double>(h, s);
             break;
         case MRP_STEP_PROLONG:
             if (!lvl_ok || level < 1) return MRP_ERR_INVALID_ARG;
-            prolong(h, level, s);
+            prolong<double>(h, level, s);
             break;
         case MRP_STEP_VCYCLE:
-            vcycle(h, s);
+            vcycle<double>(h, s);
             break;
         default:
             return MRP_ERR_INVALID_ARG;
@@ -558,7 +732,7 @@ int mrp_profile_enable(mrp_handle* H, int32_t enable) {
 }
 
 int mrp_profile_read(mrp_handle* H, int32_t n, double* ms, int64_t* launches, int64_t* nodes, int32_t reset) {
-    if (!H || n < 0 || n > 8) return MRP_ERR_INVALID_ARG;
+    if (!H || n < 0 || n > 16) return MRP_ERR_INVALID_ARG;
     Handle& h = H->h;
     if (!h.pend.empty()) {
         if (cudaDeviceSynchronize() != cudaSuccess) return MRP_ERR_CUDA;
@@ -570,7 +744,7 @@ int mrp_profile_read(mrp_handle* H, int32_t n, double* ms, int64_t* launches, in
         if (nodes) nodes[i] = h.prof_nodes[i];
     }
     if (reset)
-        for (int i = 0; i < 8; ++i) { h.prof_ms[i] = 0; h.prof_cnt[i] = 0; h.prof_nodes[i] = 0; }
+        for (int i = 0; i < 16; ++i) { h.prof_ms[i] = 0; h.prof_cnt[i] = 0; h.prof_nodes[i] = 0; }
     return MRP_OK;
 }
 

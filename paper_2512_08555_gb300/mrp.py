@@ -27,6 +27,7 @@ EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
             "mrp_coarse_solve_noalloc"]
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
+PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
 
 
 class MrpError(RuntimeError):
@@ -44,7 +45,7 @@ class _Forest(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("order", C.c_int32), ("tol", C.c_double), ("stop_rule", C.c_int32), ("max_cycles", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("mixed_target", C.c_double),
-                ("spin_budget", C.c_int64)]
+                ("spin_budget", C.c_int64), ("inner_cycles", C.c_int32), ("max_outer", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -106,7 +107,8 @@ def _stream_ptr(stream):
 class Solver:
     """One forest, one right-hand side, FP64 (``mrp_create`` / ``mrp_solve``)."""
 
-    def __init__(self, forest, order=4, tol=1e-10, max_cycles=50, nu1=3, nu2=3, precision="fp64"):
+    def __init__(self, forest, order=4, tol=1e-10, max_cycles=50, nu1=3, nu2=3, precision="fp64",
+                 inner_cycles=0, max_outer=0):
         import torch  # noqa: F401  (CUDA context and memory come from torch)
         self.lib = load_library()
         self.forest = forest
@@ -127,6 +129,7 @@ class Solver:
         op.order, op.tol, op.stop_rule, op.max_cycles = int(order), float(tol), 0, int(max_cycles)
         op.nu1, op.nu2 = int(nu1), int(nu2)
         op.precision = {"fp64": 0, "mixed": 1}[precision]
+        op.inner_cycles, op.max_outer = int(inner_cycles), int(max_outer)
         self.h = C.c_void_p()
         _check(self.lib.mrp_create(C.byref(self.h), C.byref(fd), 1, C.byref(op)), "mrp_create")
 
@@ -213,12 +216,13 @@ class Solver:
         _check(self.lib.mrp_profile_enable(self.h, 1 if enable else 0), "mrp_profile_enable")
 
     def profile_read(self, reset=True):
-        ms = np.zeros(8)
-        cnt = np.zeros(8, np.int64)
-        nodes = np.zeros(8, np.int64)
-        _check(self.lib.mrp_profile_read(self.h, 8, ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p),
+        ms = np.zeros(16)
+        cnt = np.zeros(16, np.int64)
+        nodes = np.zeros(16, np.int64)
+        _check(self.lib.mrp_profile_read(self.h, 16, ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p),
                                          nodes.ctypes.data_as(C.c_void_p), 1 if reset else 0), "mrp_profile_read")
-        return {p: {"ms": float(ms[i]), "launches": int(cnt[i]), "nodes": int(nodes[i])} for i, p in enumerate(PHASES)}
+        return {p: {"ms": float(ms[i]), "launches": int(cnt[i]), "nodes": int(nodes[i])}
+                for i, p in enumerate(PHASES16) if cnt[i] > 0}
 
     def solve_host(self, f_host, u_host=None, stream=None):
         """End-to-end call from host memory: copy f in, solve, copy u out (all on ``stream``).
