@@ -54,6 +54,11 @@ class OracleSolver:
         self._kids = [self._children_table(k) for k in range(len(nbs))]
         self._prolong_cache = {}
         self.cycles_done = 0
+        # optional offset added to the covered level-0 nodes when level 1 is
+        # restricted to level 0 ([covered level-0 block][z][y][x]); a correction
+        # solve carries there the mismatch between the level-0 field and the
+        # injection of level 1.  None in a plain solve.
+        self.off0 = None
 
     # ------------------------------------------------------------------ forest helpers
     def _neighbour_table(self, k):
@@ -152,11 +157,13 @@ class OracleSolver:
         g = (fields[k].shape[1] - n) // 2
         gc = (fields[k - 1].shape[1] - n) // 2
         kids = self._children(k - 1)
-        for P in np.nonzero(~self.fo.levels[k - 1].is_leaf)[0]:
+        covered = np.nonzero(~self.fo.levels[k - 1].is_leaf)[0]
+        for P in covered:
             for o in range(8):
                 ox, oy, oz = (o & 1) * h, ((o >> 1) & 1) * h, ((o >> 2) & 1) * h
                 fields[k - 1][P, gc + oz:gc + oz + h, gc + oy:gc + oy + h, gc + ox:gc + ox + h] = \
                     fields[k][kids[P, o], g:g + n:2, g:g + n:2, g:g + n:2]
+
 
     def ghost_fill(self, fields, k, exterior):
         """Fill the halo of every level-k block (Sec. 2.1 ghosting).
@@ -283,6 +290,9 @@ class OracleSolver:
                 ox, oy, oz = (o & 1) * h, ((o >> 1) & 1) * h, ((o >> 2) & 1) * h
                 self.U[k - 1][P, 1 + oz:1 + oz + h, 1 + oy:1 + oy + h, 1 + ox:1 + ox + h] = \
                     self.U[k][kids[P, o], 1:1 + n:2, 1:1 + n:2, 1:1 + n:2]
+            if k == 1 and self.off0 is not None:
+                j = int(np.searchsorted(covered, P))
+                self.U[0][P, 1:1 + n, 1:1 + n, 1:1 + n] += self.off0[j]
             B = lvc.coords[P]
             lo = 2 * B[::-1] * n - 1 - base            # fine window [2Bn-1, 2Bn+2n-1], (z, y, x)
             win = D[lo[0]:lo[0] + 2 * n + 1, lo[1]:lo[1] + 2 * n + 1, lo[2]:lo[2] + 2 * n + 1]

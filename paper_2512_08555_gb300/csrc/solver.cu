@@ -303,8 +303,9 @@ template <typename T> static Fld<T> fld(Handle& h, int k) {
     if constexpr (sizeof(T) == 8) return Fld<T>{h.lv[k].U, h.lv[k].F, h.lv[k].R, h.lv[k].H};
     else return Fld<T>{h.lv[k].U32, h.lv[k].F32, h.lv[k].R32, h.lv[k].H32};
 }
-// Offset added when level 1 is injected into the covered level-0 nodes: the
-// FP32 correction cycles carry -c0 there (see kernels_mixed.cu).
+// Offset added when level 1 is restricted into the covered level-0 nodes: the
+// FP32 correction cycles carry -c0 in the level-0 state there (see
+// kernels_mixed.cu); ghost interpolation of level 1 reads the plain injection.
 template <typename T> static const T* off0(Handle& h) {
     if constexpr (sizeof(T) == 4) return h.mixed ? h.off32 : nullptr;
     else return nullptr;
@@ -324,7 +325,7 @@ template <typename T> static const T* ucoarse(Handle& h, int k) { return k >= 1 
 template <typename T>
 static void inject_level(Handle& h, int k, cudaStream_t s) {
     PhaseScope ps(h, s, ph<T>(PH_GHOST), h.lv[k].nb * n3(h) / 8, 1);
-    launch_inject_to_parent<T>(ucur<T>(h, k - 1), 1, ucur<T>(h, k), 1, h.lv[k].view(), h.n, k == 1 ? off0<T>(h) : nullptr, s);
+    launch_inject_to_parent<T>(ucur<T>(h, k - 1), 1, ucur<T>(h, k), 1, h.lv[k].view(), h.n, nullptr, s);
 }
 
 // Ghosting of u on level k into the stored ghost layer (step API): the
