@@ -117,7 +117,25 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
  * max_cycles ran out. */
 int mrp_solve(mrp_handle* h, const double* f, double* u, void* stream, mrp_stats* st);
 
-/* Adjoint solve (f-bar = S^T w).  Not built yet: MRP_ERR_UNSUPPORTED. */
+/* Gradient of the converged solve: fbar = S^T w, where u = S f is the
+ * composite solution mrp_solve converges to (the map is linear).  S
+ * factors as f* = B f (Sec. 3.2 with f ghosts), 0 = c(f*) - K x (the
+ * composite leaf system: L_k u = f* at leaves of levels >= 1, and on level-0
+ * nodes covered by level 1 the level-0 field h0^2 G * f0 of Sec. 2.2 equal to
+ * the injection of level 1) and u = E(x, f*); so fbar = B^T (E_f^T w +
+ * c^T lambda) with K^T lambda = E_x^T w.  Every factor is the exact
+ * transpose of the forward stage (ghost fill, injection, stencils, level-0
+ * convolution).  K^T lambda = E_x^T w is solved in FP64 by refinement with the
+ * transposed correction V-cycle (Gauss-Seidel colours reversed, full
+ * weighting and trilinear correction exchanged, ghost fills turned into
+ * scatters); it stops when max|E_x^T w - K^T lambda| / max|E_x^T w| < tol or
+ * after max_cycles transposed cycles (MRP_ERR_NOT_CONVERGED, fbar still
+ * written).  w, fbar: device pointers in the leaf layout of f and u.  Needs
+ * no earlier mrp_solve (no forward state enters).  The first call allocates
+ * the adjoint workspace (about 5 fields per level plus 6 vectors of
+ * total_nodes doubles); later calls allocate nothing.  Both precision
+ * options run this in FP64.  st->cycles = st->ir_steps = transposed cycles,
+ * st->residual = the final relative residual above. */
 int mrp_solve_adjoint(mrp_handle* h, const double* w, double* fbar, void* stream, mrp_stats* st);
 
 /* Release every resource of h (NULL is allowed). */

@@ -93,6 +93,26 @@ int mrp_fft_shape(mrp_handle* h, int32_t* P);
  * other threads, other handles) race on the array: serialise them. */
 int mrp_coarse_solve_noalloc(mrp_handle* h, const double* f0, double* u0, void* stream);
 
+/* The factors of mrp_solve_adjoint one at a time (for parity checks).
+ * Vectors of the unknown / residual space have *len = total_nodes doubles:
+ * [nb_k][n^3] per level k = 0..L in level order, blocks in the order of
+ * mrp_level_info; levels >= 1 carry values on their leaf blocks, level 0 on
+ * its covered blocks, and every other entry must be zero (outputs keep them
+ * zero).  in / out: device.  Allocates the adjoint workspace on first use;
+ * synchronises the stream.
+ *   MRP_ADJ_CYCLE_T  in: x-space vector -> out: M^T in (residual space), M the
+ *                    correction V-cycle of Alg. 1 from u = 0 (leaf rows drive
+ *                    the leaf blocks, covered level-0 rows the offset of the
+ *                    injection into level 0); reads the handle's nu1, nu2
+ *   MRP_ADJ_RES_T    in: lambda -> out[0, len): x-bar of res^T lambda,
+ *                    out[len, 2 len): f*-bar (leaf blocks of every level)
+ *   MRP_ADJ_OUT_T    in: w (leaf layout) -> out[0, len): E_x^T w,
+ *                    out[len, 2 len): E_f^T w
+ *   MRP_ADJ_RHS_T    in: f*-bar (len, leaf blocks) -> out: B^T f*-bar (leaf layout) */
+enum { MRP_ADJ_CYCLE_T = 0, MRP_ADJ_RES_T = 1, MRP_ADJ_OUT_T = 2, MRP_ADJ_RHS_T = 3 };
+int mrp_adjoint_len(mrp_handle* h, int64_t* len);
+int mrp_adjoint_op(mrp_handle* h, int32_t op, const double* in, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,322 @@
+// Gradient of the converged solve on the device: f-bar = S^T w, where
+// u_leaf = S f is the composite solution the V-cycles of Alg. 1 converge to.
+//
+// S factors as f* = B f (Sec. 3.2, with f ghosts), 0 = c(f*) - K x (the
+// composite leaf system: leaf rows f* - L_k u at levels >= 1, and on covered
+// level-0 nodes the mismatch (h0^2 G * f0 - inject u_1) / h0^2), and
+// u_leaf = E(x, f*) (level-0 leaves from the convolution).  Hence
+//     f-bar = B^T (E_f^T w + c^T lambda),   K^T lambda = E_x^T w.
+// K^T lambda = g is solved by FP64 refinement, lambda += M^T (g - K^T lambda),
+// with M^T the transposed correction V-cycle; I - M^T K^T = (I - K M)^T has
+// the spectrum of the forward cycle's error propagator, so the refinement
+// contracts at the forward rate.  No state of a forward solve is needed: all
+// of these maps are linear and fixed by the forest and the order.
+//
+// Vectors of the unknown / residual space hold [nb_k][n^3] per level k at
+// offset xoff[k]: levels >= 1 use their leaf blocks, level 0 its covered
+// blocks; every other entry stays zero.
+#include "mrp_internal.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace mrp {
+
+static int adj_alloc(double*& p, size_t count) {
+    if (cudaMalloc(&p, sizeof(double) * (count ? count : 1)) != cudaSuccess) return MRP_ERR_OOM;
+    if (cudaMemset(p, 0, sizeof(double) * (count ? count : 1)) != cudaSuccess) return MRP_ERR_CUDA;
+    return MRP_OK;
+}
+
+int adjoint_setup(Handle& h) {
+    if (!h.adj.empty()) return MRP_OK;
+    const size_t n = h.n, S = n + 2, S4 = n + 4, nn = n * n * n;
+    h.adj.resize(h.L + 1);
+    h.xoff.assign(h.L + 2, 0);
+    int rc;
+    for (int k = 0; k <= h.L; ++k) {
+        const size_t nb = h.lv[k].nb;
+        Handle::AdjLevel& a = h.adj[k];
+        if ((rc = adj_alloc(a.Ub, nb * S * S * S))) return rc;
+        if ((rc = adj_alloc(a.Fb, nb * nn))) return rc;
+        if ((rc = adj_alloc(a.Rb, nb * nn))) return rc;
+        if ((rc = adj_alloc(a.Hb, nb * nn))) return rc;
+        if ((rc = adj_alloc(a.Rawb, nb * S4 * S4 * S4))) return rc;
+        h.xoff[k + 1] = h.xoff[k] + nb * nn;
+    }
+    const size_t len = h.xoff[h.L + 1];
+    for (double** p : {&h.lam, &h.rho, &h.gvec, &h.xb, &h.fsb, &h.wl})
+        if ((rc = adj_alloc(*p, len))) return rc;
+    const size_t C = (size_t)(h.n0[0] + 2) * (h.n0[1] + 2) * (h.n0[2] + 2);
+    if ((rc = adj_alloc(h.cube, C))) return rc;
+    if ((rc = adj_alloc(h.dense, (size_t)h.n0[0] * h.n0[1] * h.n0[2]))) return rc;
+    if ((rc = adj_alloc(h.off0b, (size_t)h.lv[0].nb * nn))) return rc;
+    return MRP_OK;
+}
+
+void adjoint_release(Handle& h) {
+    for (auto& a : h.adj) { cudaFree(a.Ub); cudaFree(a.Fb); cudaFree(a.Rb); cudaFree(a.Hb); cudaFree(a.Rawb); }
+    h.adj.clear();
+    for (double* p : {h.lam, h.rho, h.gvec, h.xb, h.fsb, h.wl, h.cube, h.dense, h.off0b}) cudaFree(p);
+    h.lam = h.rho = h.gvec = h.xb = h.fsb = h.wl = h.cube = h.dense = h.off0b = nullptr;
+}
+
+static size_t xlen(const Handle& h) { return h.xoff[h.L + 1]; }
+static size_t box_bytes(const Handle& h, int k, int g) {
+    const size_t S = h.n + 2 * g;
+    return sizeof(double) * h.lv[k].nb * S * S * S;
+}
+
+// Transpose of the ghost fill of level k (u layout, halo 1), including the
+// injection of level k into the covered level-(k-1) nodes that precedes it.
+static void ghost_fill_T(Handle& h, int k, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_GHOST, h.lv[k].nb * n3(h), k >= 1 ? 2 : 1);
+    launch_ghost_T(h.adj[k].Ub, 1, k >= 1 ? h.adj[k - 1].Ub : nullptr, 1, h.lv[k].view(), view_or_empty(h, k - 1), h.n,
+                   h.M, s);
+    if (k >= 1) launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, h.lv[k].view(), h.n, s);
+}
+
+// Transpose of the level-0 convolution read on the level-0 boxes: the adjoint
+// of every box (interior and exterior ring) -> the dense source adjoint h.dense.
+static void conv_T(Handle& h, const double* U0bar, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_COARSE, (int64_t)h.n0[0] * h.n0[1] * h.n0[2], 6);
+    launch_window_T(h.cube, U0bar, h.n, h.nb0, s);
+    launch_conv_transpose(h, h.cube, h.dense, s);
+}
+
+// res^T lambda -> x-bar (into xb); with fsb, also adds c^T lambda (the f*-bar
+// of the leaf rows and of the level-0 convolution) into fsb.
+static void res_T(Handle& h, const double* lam, double* xb, double* fsb, cudaStream_t s) {
+    const int L = h.L, n = h.n;
+    Level& l0 = h.lv[0];
+    const double ih02 = 1.0 / (h.h0 * h.h0);
+    for (int k = 0; k <= L; ++k) cudaMemsetAsync(h.adj[k].Ub, 0, box_bytes(h, k, 1), s);
+    {
+        PhaseScope ps(h, s, PH_RESIDUAL, h.leaf_nodes, 1 + L);
+        // covered level-0 rows: (conv - inject u_1) / h0^2
+        launch_interior_add(h.adj[0].Ub, 1, lam + h.xoff[0], l0.cov_blocks, l0.ncov, n, -ih02, s);
+        // leaf rows of levels >= 1: f* - L_k u
+        for (int k = 1; k <= L; ++k) {
+            const double hk = level_h(h, k);
+            launch_stencil_T(h.adj[k].Ub, lam + h.xoff[k], fsb ? fsb + h.xoff[k] : nullptr, h.lv[k].leaf_blocks,
+                             h.lv[k].nleaf, n, h.M, -1.0 / (hk * hk), s);
+        }
+    }
+    // the ghost fills of levels L..1 (each with its injection), reversed
+    for (int k = 1; k <= L; ++k) ghost_fill_T(h, k, s);
+    {
+        PhaseScope ps(h, s, PH_OTHER, l0.ncov * n3(h), 1);
+        launch_interior_add(h.adj[0].Ub, 1, lam + h.xoff[0], l0.cov_blocks, l0.ncov, n, ih02, s);
+    }
+    conv_T(h, h.adj[0].Ub, s);
+    {
+        PhaseScope ps(h, s, PH_OTHER, h.total_nodes, (fsb ? 2 : 1) + L + (L >= 2 ? L - 1 : 0));
+        launch_dense_to_blocks(xb + h.xoff[0], h.dense, l0.cov_blocks, l0.ncov, l0.coords, n, h.n0, false, s);
+        if (fsb) launch_dense_to_blocks(fsb + h.xoff[0], h.dense, l0.leaf_blocks, l0.nleaf, l0.coords, n, h.n0, true, s);
+        // the injections of levels L..2 that set the covered nodes first, reversed
+        for (int k = 2; k <= L; ++k) launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, h.lv[k].view(), n, s);
+        for (int k = 1; k <= L; ++k)
+            launch_interior_get(xb + h.xoff[k], h.adj[k].Ub, 1, h.lv[k].leaf_blocks, h.lv[k].nleaf, n, 1.0, s);
+    }
+}
+
+// E^T: leaf adjoint w (caller layout) -> g = E_x^T w (into gvec) and E_f^T w (into fsb, which it sets).
+static void out_T(Handle& h, const double* w, cudaStream_t s) {
+    const int L = h.L, n = h.n;
+    Level& l0 = h.lv[0];
+    const size_t len = xlen(h);
+    cudaMemsetAsync(h.wl, 0, sizeof(double) * len, s);
+    cudaMemsetAsync(h.fsb, 0, sizeof(double) * len, s);
+    {
+        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 2);
+        LevelPtrs lp{};
+        for (int k = 0; k <= L; ++k) lp.p[k] = h.wl + h.xoff[k];
+        launch_scatter_leaves_to(h, w, lp, 0, s);
+        cudaMemcpyAsync(h.gvec, h.wl, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(h.gvec, 0, sizeof(double) * h.xoff[1], s);
+        cudaMemsetAsync(h.adj[0].Ub, 0, box_bytes(h, 0, 1), s);
+        launch_interior_add(h.adj[0].Ub, 1, h.wl, l0.leaf_blocks, l0.nleaf, n, 1.0, s);
+    }
+    conv_T(h, h.adj[0].Ub, s);
+    PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 2);
+    launch_dense_to_blocks(h.gvec, h.dense, l0.cov_blocks, l0.ncov, l0.coords, n, h.n0, false, s);
+    launch_dense_to_blocks(h.fsb, h.dense, l0.leaf_blocks, l0.nleaf, l0.coords, n, h.n0, false, s);
+}
+
+// B^T: f*-bar (leaf blocks, per level) -> f-bar (caller layout).
+static void rhs_T(Handle& h, const double* fsb, double* fbar, cudaStream_t s) {
+    const int L = h.L, n = h.n;
+    {
+        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, L + 1);
+        for (int k = 0; k <= L; ++k) {
+            cudaMemsetAsync(h.adj[k].Rawb, 0, box_bytes(h, k, 2), s);
+            launch_rstencil_T(h.adj[k].Rawb, fsb + h.xoff[k], h.lv[k].leaf_blocks, h.lv[k].nleaf, n, h.M, s);
+        }
+    }
+    PhaseScope ps(h, s, PH_GHOST, h.total_nodes, 2 * L + 1 + L + 1);
+    for (int k = L; k >= 0; --k) {
+        launch_ghost_T(h.adj[k].Rawb, 2, k >= 1 ? h.adj[k - 1].Rawb : nullptr, 2, h.lv[k].view(), view_or_empty(h, k - 1),
+                       n, h.M, s);
+        if (k >= 1) launch_inject_T(h.adj[k].Rawb, 2, h.adj[k - 1].Rawb, 2, h.lv[k].view(), n, s);
+    }
+    for (int k = 0; k < L; ++k) launch_inject_T(h.adj[k + 1].Rawb, 2, h.adj[k].Rawb, 2, h.lv[k + 1].view(), n, s);
+    LevelPtrs lp{};
+    for (int k = 0; k <= L; ++k) lp.p[k] = h.adj[k].Rawb;
+    launch_gather_leaves_from(h, fbar, lp, 2, s);
+}
+
+// M^T: the transposed correction V-cycle, x-space vector xin -> residual-space rout.
+static void cycle_T(Handle& h, const double* xin, double* rout, cudaStream_t s) {
+    const int L = h.L, n = h.n;
+    Level& l0 = h.lv[0];
+    for (int k = 0; k <= L; ++k) {
+        cudaMemsetAsync(h.adj[k].Ub, 0, box_bytes(h, k, 1), s);
+        cudaMemsetAsync(h.adj[k].Fb, 0, sizeof(double) * h.lv[k].nb * n3(h), s);
+        cudaMemsetAsync(h.adj[k].Hb, 0, sizeof(double) * h.lv[k].nb * n3(h), s);
+    }
+    {
+        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, L + 1);
+        for (int k = 1; k <= L; ++k)
+            launch_interior_add(h.adj[k].Ub, 1, xin + h.xoff[k], h.lv[k].leaf_blocks, h.lv[k].nleaf, n, 1.0, s);
+        launch_block_copy(h.adj[0].Fb, xin, l0.cov_blocks, l0.ncov, n, 1.0, s);
+    }
+    auto smooth_T = [&](int k) {
+        PhaseScope ps(h, s, PH_SMOOTH, h.lv[k].nb * n3(h), 1);
+        const double hk = level_h(h, k);
+        launch_smooth_T(h.adj[k].Ub, h.adj[k].Fb, h.lv[k].nb, n, h.M, hk * hk, s);
+    };
+    // coarse-to-fine half, reversed
+    for (int k = L; k >= 1; --k) {
+        for (int i = 0; i < h.nu2; ++i) { smooth_T(k); ghost_fill_T(h, k, s); }
+        PhaseScope ps(h, s, PH_PROLONG, h.lv[k].nb * n3(h), 1);
+        launch_prolong_T(h.adj[k - 1].Ub, h.adj[k - 1].Hb, h.adj[k].Ub, h.lv[k].view(), h.lv[k - 1].view(), n, s);
+    }
+    // level-0 solve: the source adjoint gains the convolution transpose of u_0's adjoint
+    conv_T(h, h.adj[0].Ub, s);
+    {
+        PhaseScope ps(h, s, PH_COARSE, l0.nb * n3(h), 1);
+        launch_dense_to_blocks(h.adj[0].Fb, h.dense, l0.order, l0.nb, l0.coords, n, h.n0, true, s);
+        cudaMemsetAsync(h.adj[0].Ub, 0, box_bytes(h, 0, 1), s);
+    }
+    // fine-to-coarse half, reversed
+    for (int k = 1; k <= L; ++k) {
+        Level& c = h.lv[k - 1];
+        Level& f = h.lv[k];
+        {
+            PhaseScope ps(h, s, PH_RESTRICT, c.nb * n3(h), 2);
+            const double hc = level_h(h, k - 1);
+            // uhat_{k-1} = u_{k-1}; f_{k-1} += L u_{k-1} on covered blocks
+            launch_interior_add(h.adj[k - 1].Ub, 1, h.adj[k - 1].Hb, c.order, c.nb, n, 1.0, s);
+            cudaMemsetAsync(h.adj[k - 1].Hb, 0, sizeof(double) * c.nb * n3(h), s);
+            launch_stencil_T(h.adj[k - 1].Ub, h.adj[k - 1].Fb, nullptr, c.cov_blocks, c.ncov, n, h.M, 1.0 / (hc * hc), s);
+        }
+        ghost_fill_T(h, k - 1, s);
+        {
+            PhaseScope ps(h, s, PH_RESTRICT, f.nb * n3(h), 3 + (k == 1 ? 1 : 0));
+            // f_{k-1} = FW r_k on covered blocks
+            launch_fw_T(h.adj[k].Rb, h.adj[k - 1].Fb, f.view(), n, s);
+            launch_block_zero(h.adj[k - 1].Fb, c.cov_blocks, c.ncov, n, s);
+            // u_{k-1} = inject u_k (+ the level-0 offset carrying the covered level-0 rows)
+            if (k == 1) launch_interior_get(h.off0b, h.adj[0].Ub, 1, l0.cov_blocks, l0.ncov, n, 1.0, s);
+            launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, f.view(), n, s);
+        }
+        {
+            PhaseScope ps(h, s, PH_RESIDUAL, f.nb * n3(h), 1);
+            const double hk = level_h(h, k);
+            launch_stencil_T(h.adj[k].Ub, h.adj[k].Rb, h.adj[k].Fb, f.order, f.nb, n, h.M, -1.0 / (hk * hk), s);
+        }
+        ghost_fill_T(h, k, s);
+        for (int i = 0; i < h.nu1; ++i) { smooth_T(k); ghost_fill_T(h, k, s); }
+    }
+    PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, L + 1);
+    for (int k = 1; k <= L; ++k)
+        launch_block_copy(rout + h.xoff[k], h.adj[k].Fb, h.lv[k].leaf_blocks, h.lv[k].nleaf, n, 1.0, s);
+    launch_block_copy(rout, h.off0b, l0.cov_blocks, l0.ncov, n, -h.h0 * h.h0, s);
+}
+
+// The whole gradient.  Returns MRP_OK, MRP_ERR_NOT_CONVERGED (fbar still
+// written) or an error status.
+int solve_adjoint(Handle& h, const double* w, double* fbar, cudaStream_t s, int* cycles_out, double* rel_out) {
+    int rc = adjoint_setup(h);
+    if (rc) return rc;
+    const size_t len = xlen(h);
+    out_T(h, w, s);
+    cudaMemsetAsync(h.lam, 0, sizeof(double) * len, s);
+    cudaMemsetAsync(h.dmax + 2, 0, sizeof(unsigned long long), s);
+    {
+        PhaseScope ps(h, s, PH_NORM, (int64_t)len, 1);
+        launch_lincomb(h.rho, 1.0, h.gvec, 0.0, h.gvec, len, h.dmax + 2, s);
+    }
+    double gmax = 0.0;
+    if ((rc = read_max(h, s, &gmax, 2))) return rc;
+    const double scale = gmax > 0.0 ? gmax : 1.0;
+    double rel = gmax / scale;
+    int cycles = 0;
+    while (rel >= h.tol && cycles < h.max_cycles) {
+        cycle_T(h, h.rho, h.xb, s);
+        ++cycles;
+        {
+            PhaseScope ps(h, s, PH_NORM, (int64_t)len, 1);
+            launch_lincomb(h.lam, 1.0, h.lam, 1.0, h.xb, len, nullptr, s);
+        }
+        res_T(h, h.lam, h.xb, nullptr, s);
+        cudaMemsetAsync(h.dmax + 2, 0, sizeof(unsigned long long), s);
+        {
+            // rho = g - K^T lambda = g + x-bar
+            PhaseScope ps(h, s, PH_NORM, (int64_t)len, 1);
+            launch_lincomb(h.rho, 1.0, h.gvec, 1.0, h.xb, len, h.dmax + 2, s);
+        }
+        double r = 0.0;
+        if ((rc = read_max(h, s, &r, 2))) return rc;
+        rel = r / scale;
+        if (!std::isfinite(rel)) { *cycles_out = cycles; *rel_out = rel; return MRP_ERR_NUMERICAL; }
+    }
+    res_T(h, h.lam, h.xb, h.fsb, s);
+    rhs_T(h, h.fsb, fbar, s);
+    if (cudaGetLastError() != cudaSuccess) return MRP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
+    harvest(h);
+    *cycles_out = cycles;
+    *rel_out = rel;
+    return rel < h.tol ? MRP_OK : MRP_ERR_NOT_CONVERGED;
+}
+
+// Single transposed operators for parity checks (see mrp_adjoint_op).
+int adjoint_op(Handle& h, int op, const double* in, double* out, cudaStream_t s) {
+    int rc = adjoint_setup(h);
+    if (rc) return rc;
+    const size_t len = xlen(h);
+    switch (op) {
+        case MRP_ADJ_CYCLE_T:
+            cudaMemcpyAsync(h.rho, in, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            cudaMemsetAsync(h.xb, 0, sizeof(double) * len, s);
+            cycle_T(h, h.rho, h.xb, s);
+            cudaMemcpyAsync(out, h.xb, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            break;
+        case MRP_ADJ_RES_T:
+            cudaMemcpyAsync(h.lam, in, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            cudaMemsetAsync(h.xb, 0, sizeof(double) * len, s);
+            cudaMemsetAsync(h.fsb, 0, sizeof(double) * len, s);
+            res_T(h, h.lam, h.xb, h.fsb, s);
+            cudaMemcpyAsync(out, h.xb, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(out + len, h.fsb, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            break;
+        case MRP_ADJ_OUT_T:
+            out_T(h, in, s);
+            cudaMemcpyAsync(out, h.gvec, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(out + len, h.fsb, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            break;
+        case MRP_ADJ_RHS_T:
+            cudaMemcpyAsync(h.fsb, in, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+            rhs_T(h, h.fsb, out, s);
+            break;
+        default:
+            return MRP_ERR_INVALID_ARG;
+    }
+    if (cudaGetLastError() != cudaSuccess) return MRP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
+    harvest(h);
+    return MRP_OK;
+}
+
+}  // namespace mrp

@@ -1,0 +1,526 @@
+// Transposed operators for the gradient of the converged solve (FP64).
+//
+// The converged map f -> u_leaf is linear, and so is one correction V-cycle
+// (Alg. 1 started from u = 0).  Their transposes are built from the
+// transposes of the elementary steps, applied in reverse order:
+//   stencil application       -> gather of the (symmetric) weights over the rows
+//   Gauss-Seidel sweep         -> colours 7..0, each colour's update transposed
+//   ghost fill (Sec. 2.1)      -> each ghost adjoint is added back to its sources
+//                                 (same-level interior node, or the I-point
+//                                 Lagrange coarse stencil), then cleared
+//   injection into covered coarse nodes -> coarse adjoint moved to the
+//                                 coincident fine node, then cleared
+//   full weighting             -> its transpose (a trilinear-type spread)
+//   trilinear correction       -> its transpose (a full-weighting-type gather)
+//   level-0 convolution        -> the convolution with source and target exchanged
+// Scatters across blocks (ghost and correction transposes) use FP64 atomics.
+#include "mrp_internal.h"
+
+namespace mrp {
+
+// LHS weights of the order-M stencil as integers over den (Sec. 3.2).
+template <int M> struct LWa;
+template <> struct LWa<2> { static constexpr double den = 1, c = -6, f = 1, e = 0, k = 0; };
+template <> struct LWa<4> { static constexpr double den = 6, c = -24, f = 2, e = 1, k = 0; };
+template <> struct LWa<6> { static constexpr double den = 30, c = -128, f = 14, e = 3, k = 1; };
+
+// Weight of the neighbour with m non-zero offsets (m = 0 centre, 1 face, 2 edge, 3 corner).
+template <int M>
+__device__ __forceinline__ double lhs_w(int m) {
+    using W = LWa<M>;
+    return m == 0 ? W::c : (m == 1 ? W::f : (m == 2 ? W::e : W::k));
+}
+
+template <int M>
+__device__ __forceinline__ double rhs_weight(int dx, int dy, int dz) {
+    const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+    if (M == 2) return (ax | ay | az) == 0 ? 1.0 : 0.0;
+    if (ax > 1 || ay > 1 || az > 1) {
+        if (M == 4) return 0.0;
+        const int nz = (ax != 0) + (ay != 0) + (az != 0);     // axis +-2 terms of R^6
+        return (nz == 1 && (ax == 2 || ay == 2 || az == 2)) ? -1.0 / 240.0 : 0.0;
+    }
+    const int o = (ax != 0) + (ay != 0) + (az != 0);
+    if (M == 4) return o == 0 ? 0.5 : (o == 1 ? 1.0 / 12.0 : 0.0);
+    return o == 0 ? 67.0 / 120.0 : (o == 1 ? 1.0 / 18.0 : (o == 2 ? 1.0 / 90.0 : 0.0));
+}
+
+// ---------------------------------------------------------------- stencils
+// out[b] (halo layout, g = 1) += scale * L^T lam[b] on the listed blocks: every
+// node q of the (n+2)^3 box gathers the weights of the interior rows p with
+// |p - q| <= 1.  With fadd, also fadd[b] += lam[b] (the f-part of r = f - L u).
+template <int M>
+__global__ void k_stencil_T(double* __restrict__ out, const double* __restrict__ lam, double* __restrict__ fadd,
+                            const int* __restrict__ blocks, int n, double scale) {
+    const int b = blocks[blockIdx.x];
+    const int S = n + 2, S3 = S * S * S, n3 = n * n * n;
+    const double* lb = lam + (size_t)b * n3;
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int qx = t % S - 1, qy = (t / S) % S - 1, qz = t / (S * S) - 1;   // interior coordinates of q
+        double acc = 0.0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int pz = qz + dz;
+            if (pz < 0 || pz >= n) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int py = qy + dy;
+                if (py < 0 || py >= n) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int px = qx + dx;
+                    if (px < 0 || px >= n) continue;
+                    const double w = lhs_w<M>((dx != 0) + (dy != 0) + (dz != 0));
+                    if (w != 0.0) acc += w * lb[(pz * n + py) * n + px];
+                }
+            }
+        }
+        out[(size_t)b * S3 + t] += scale * acc;
+    }
+    if (fadd)
+        for (int t = threadIdx.x; t < n3; t += blockDim.x) fadd[(size_t)b * n3 + t] += lb[t];
+}
+
+void launch_stencil_T(double* out, const double* lam, double* fadd, const int* blocks, int nblocks, int n, int M,
+                      double inv_h2, cudaStream_t s) {
+    if (nblocks == 0) return;
+    if (M == 2) k_stencil_T<2><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, inv_h2 / LWa<2>::den);
+    if (M == 4) k_stencil_T<4><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, inv_h2 / LWa<4>::den);
+    if (M == 6) k_stencil_T<6><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, inv_h2 / LWa<6>::den);
+}
+
+// out[b] (raw-f layout, g = 2) = R^T fsb[b] on the listed blocks.
+template <int M>
+__global__ void k_rstencil_T(double* __restrict__ out, const double* __restrict__ fsb, const int* __restrict__ blocks, int n) {
+    const int b = blocks[blockIdx.x];
+    const int S = n + 4, S3 = S * S * S, n3 = n * n * n;
+    const double* lb = fsb + (size_t)b * n3;
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int qx = t % S - 2, qy = (t / S) % S - 2, qz = t / (S * S) - 2;
+        double acc = 0.0;
+        for (int dz = -2; dz <= 2; ++dz) {
+            const int pz = qz + dz;
+            if (pz < 0 || pz >= n) continue;
+            for (int dy = -2; dy <= 2; ++dy) {
+                const int py = qy + dy;
+                if (py < 0 || py >= n) continue;
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const int px = qx + dx;
+                    if (px < 0 || px >= n) continue;
+                    const double w = rhs_weight<M>(dx, dy, dz);
+                    if (w != 0.0) acc += w * lb[(pz * n + py) * n + px];
+                }
+            }
+        }
+        out[(size_t)b * S3 + t] = acc;
+    }
+}
+
+void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nblocks, int n, int M, cudaStream_t s) {
+    if (nblocks == 0) return;
+    if (M == 2) k_rstencil_T<2><<<nblocks, 256, 0, s>>>(out, fsb, blocks, n);
+    if (M == 4) k_rstencil_T<4><<<nblocks, 256, 0, s>>>(out, fsb, blocks, n);
+    if (M == 6) k_rstencil_T<6><<<nblocks, 256, 0, s>>>(out, fsb, blocks, n);
+}
+
+// ---------------------------------------------------------------- Gauss-Seidel sweep
+// Transpose of one 8-colour sweep with frozen halo (forward: nodes p of colour
+// c take (den h^2 f_p - sum_q w_q u_q) / w_c).  Colours run 7..0.  For one
+// colour, a node q whose parity differs from c in m axes has exactly the
+// colour-c neighbours q +- 1 in those axes (2^m of them, all of weight w_m):
+// it gathers -w_m / w_c times their adjoints; then the colour-c nodes pass
+// den h^2 / w_c of their adjoint to f and clear it.  The halo accumulates too
+// (it is scattered afterwards by the ghost transpose).
+template <int M>
+__global__ void k_smooth_T(double* __restrict__ U, double* __restrict__ F, int n, double h2den) {
+    extern __shared__ double su[];
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n, h = n >> 1, h3 = h * h * h;
+    const int b = blockIdx.x;
+    double* Ub = U + (size_t)b * S3;
+    double* Fb = F + (size_t)b * n3;
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) su[t] = Ub[t];
+    __syncthreads();
+    const double inv_c = 1.0 / LWa<M>::c;
+    for (int col = 7; col >= 0; --col) {
+        const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
+        for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+            const int qx = t % S - 1, qy = (t / S) % S - 1, qz = t / S2 - 1;
+            const int mx = (qx & 1) != cx, my = (qy & 1) != cy, mz = (qz & 1) != cz;
+            const int m = mx + my + mz;
+            if (m == 0) continue;
+            const double w = lhs_w<M>(m);
+            if (w == 0.0) continue;
+            double acc = 0.0;
+            for (int sz = -mz; sz <= mz; sz += 2) {
+                const int pz = qz + sz;
+                if (pz < 0 || pz >= n) continue;
+                for (int sy = -my; sy <= my; sy += 2) {
+                    const int py = qy + sy;
+                    if (py < 0 || py >= n) continue;
+                    for (int sx = -mx; sx <= mx; sx += 2) {
+                        const int px = qx + sx;
+                        if (px < 0 || px >= n) continue;
+                        acc += su[((pz + 1) * S + py + 1) * S + px + 1];
+                    }
+                }
+            }
+            su[t] -= w * inv_c * acc;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < h3; q += blockDim.x) {
+            const int x = 2 * (q % h) + cx, y = 2 * ((q / h) % h) + cy, z = 2 * (q / (h * h)) + cz;
+            const int o = ((z + 1) * S + y + 1) * S + x + 1;
+            Fb[(z * n + y) * n + x] += h2den * inv_c * su[o];
+            su[o] = 0.0;
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) Ub[t] = su[t];
+}
+
+void launch_smooth_T(double* U, double* F, int nb, int n, int M, double h2, cudaStream_t s) {
+    if (nb == 0) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_smooth_T<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_smooth_T<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_smooth_T<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        attr = true;
+    }
+    const size_t sm = sizeof(double) * (n + 2) * (n + 2) * (n + 2);
+    if (M == 2) k_smooth_T<2><<<nb, 256, sm, s>>>(U, F, n, h2 * LWa<2>::den);
+    if (M == 4) k_smooth_T<4><<<nb, 256, sm, s>>>(U, F, n, h2 * LWa<4>::den);
+    if (M == 6) k_smooth_T<6><<<nb, 256, sm, s>>>(U, F, n, h2 * LWa<6>::den);
+}
+
+// ---------------------------------------------------------------- ghosts and injection
+// Transpose of the ghost fill of level k (halo g): every ghost adjoint goes
+// back to its sources, then the ghost layer is cleared.  Outside the domain
+// it is dropped (f is zero there; u's exterior ring is not an input).
+template <int I>
+__global__ void k_ghost_T(double* __restrict__ A, int g, double* __restrict__ Ac, int gc, LevelView lk, LevelView lc, int n) {
+    __shared__ int snbr[27], cnbr[27];
+    __shared__ double sw[8];
+    const int b = blockIdx.x;
+    const int par = lk.parent ? lk.parent[b] : -1;
+    if (threadIdx.x < 27) {
+        snbr[threadIdx.x] = lk.nbr[27 * b + threadIdx.x];
+        cnbr[threadIdx.x] = par >= 0 ? lc.nbr[27 * par + threadIdx.x] : -1;
+    }
+    if (threadIdx.x < I) {
+        const int m = threadIdx.x;
+        double w;
+        if (I == 4) w = (m == 0 || m == 3 ? -1.0 : 9.0) / 16.0;
+        else if (I == 6) w = (m == 0 || m == 5 ? 3.0 : (m == 1 || m == 4 ? -25.0 : 150.0)) / 256.0;
+        else { const int q = m < 4 ? m : 7 - m; w = (q == 0 ? -5.0 : (q == 1 ? 49.0 : (q == 2 ? -245.0 : 1225.0))) / 2048.0; }
+        sw[m] = w;
+    }
+    __syncthreads();
+    const int S = n + 2 * g, S2 = S * S, S3 = S2 * S;
+    const int Sc = n + 2 * gc, Sc3 = Sc * Sc * Sc;
+    double* Ab = A + (size_t)b * S3;
+    const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int x = t % S, y = (t / S) % S, z = t / S2;
+        const int dx = x < g ? -1 : (x >= g + n ? 1 : 0);
+        const int dy = y < g ? -1 : (y >= g + n ? 1 : 0);
+        const int dz = z < g ? -1 : (z >= g + n ? 1 : 0);
+        if ((dx | dy | dz) == 0) continue;
+        const double a = Ab[t];
+        Ab[t] = 0.0;
+        if (a == 0.0) continue;
+        const int j = snbr[dir27(dx, dy, dz)];
+        if (j >= 0) {
+            atomicAdd(&A[(size_t)j * S3 + (size_t)((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)], a);
+            continue;
+        }
+        if (j != NBR_MISSING || par < 0) continue;
+        // level-k node p; even coordinates coincide with a coarse node, odd ones
+        // take the I-point midpoint interpolant; coarse nodes are addressed in
+        // the parent's 27-neighbourhood
+        const int p[3] = {bx * n + x - g, by * n + y - g, bz * n + z - g};
+        const int porig[3] = {(bx >> 1) * n, (by >> 1) * n, (bz >> 1) * n};
+        int cnt[3], c0[3];
+        for (int q = 0; q < 3; ++q) {
+            if ((p[q] & 1) == 0) { cnt[q] = 1; c0[q] = (p[q] >> 1) - porig[q]; }
+            else { cnt[q] = I; c0[q] = ((p[q] - 1) >> 1) - I / 2 + 1 - porig[q]; }
+        }
+        for (int mz = 0; mz < cnt[2]; ++mz) {
+            const int rz = c0[2] + mz, ez = rz < 0 ? -1 : (rz >= n ? 1 : 0), lz = rz - ez * n;
+            const double wz = cnt[2] == 1 ? 1.0 : sw[mz];
+            for (int my = 0; my < cnt[1]; ++my) {
+                const int ry = c0[1] + my, ey = ry < 0 ? -1 : (ry >= n ? 1 : 0), ly = ry - ey * n;
+                const double wy = cnt[1] == 1 ? 1.0 : sw[my];
+                for (int mx = 0; mx < cnt[0]; ++mx) {
+                    const int rx = c0[0] + mx, ex = rx < 0 ? -1 : (rx >= n ? 1 : 0), lx = rx - ex * n;
+                    const double wx = cnt[0] == 1 ? 1.0 : sw[mx];
+                    const int cb = cnbr[dir27(ex, ey, ez)];
+                    if (cb < 0) continue;   // unreachable in a 2:1 balanced forest
+                    atomicAdd(&Ac[(size_t)cb * Sc3 + (size_t)((gc + lz) * Sc + gc + ly) * Sc + gc + lx], wx * wy * wz * a);
+                }
+            }
+        }
+    }
+}
+
+void launch_ghost_T(double* A, int g, double* Ac, int gc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s) {
+    if (lk.nb == 0) return;
+    if (M == 2) k_ghost_T<4><<<lk.nb, 256, 0, s>>>(A, g, Ac, gc, lk, lc, n);
+    if (M == 4) k_ghost_T<6><<<lk.nb, 256, 0, s>>>(A, g, Ac, gc, lk, lc, n);
+    if (M == 6) k_ghost_T<8><<<lk.nb, 256, 0, s>>>(A, g, Ac, gc, lk, lc, n);
+}
+
+// Transpose of the injection of level k into its parents' covered nodes
+// (one CTA per level-k block; the covered interiors are disjoint).
+__global__ void k_inject_T(double* __restrict__ fine, int gf, double* __restrict__ coarse, int gc, LevelView lf, int n) {
+    const int B = blockIdx.x;
+    const int P = lf.parent[B], o = lf.octant[B];
+    const int h = n >> 1;
+    const int Sf = n + 2 * gf, Sc = n + 2 * gc;
+    double* fb = fine + (size_t)B * Sf * Sf * Sf;
+    double* cb = coarse + (size_t)P * Sc * Sc * Sc;
+    const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
+    for (int t = threadIdx.x; t < h * h * h; t += blockDim.x) {
+        const int i = t % h, j = (t / h) % h, l = t / (h * h);
+        const size_t c = ((size_t)(gc + oz + l) * Sc + gc + oy + j) * Sc + gc + ox + i;
+        fb[((gf + 2 * l) * Sf + gf + 2 * j) * Sf + gf + 2 * i] += cb[c];
+        cb[c] = 0.0;
+    }
+}
+
+void launch_inject_T(double* fine, int gf, double* coarse, int gc, LevelView lf, int n, cudaStream_t s) {
+    if (lf.nb == 0) return;
+    k_inject_T<<<lf.nb, 256, 0, s>>>(fine, gf, coarse, gc, lf, n);
+}
+
+// ---------------------------------------------------------------- grid transfers
+// Transpose of u_k += trilinear(u_{k-1} - uhat_{k-1}): the (n/2+1)^3 coarse
+// window of block B (its parent's part plus the next coarse node on each
+// upper side) gathers the fine adjoints with weights 1 (coincident) and 1/2
+// (midpoint neighbours); it is added to u_{k-1} and subtracted from uhat_{k-1}.
+__global__ void k_prolong_T(double* __restrict__ Uc, double* __restrict__ Hc, const double* __restrict__ Uf, LevelView lf,
+                            LevelView lc, int n) {
+    const int B = blockIdx.x;
+    const int P = lf.parent[B], o = lf.octant[B];
+    const int h = n >> 1, E = h + 1;
+    const int S = n + 2, S3 = S * S * S, n3 = n * n * n;
+    const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
+    const int* cn = lc.nbr + 27 * P;
+    const double* Ub = Uf + (size_t)B * S3;
+    for (int t = threadIdx.x; t < E * E * E; t += blockDim.x) {
+        const int i = t % E, j = (t / E) % E, l = t / (E * E);
+        double acc = 0.0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = 2 * l + dz;
+            if (z < 0 || z >= n) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = 2 * j + dy;
+                if (y < 0 || y >= n) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = 2 * i + dx;
+                    if (x < 0 || x >= n) continue;
+                    const double w = (dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0);
+                    acc += w * Ub[((z + 1) * S + y + 1) * S + x + 1];
+                }
+            }
+        }
+        if (acc == 0.0) continue;
+        const int cx = ox + i, cy = oy + j, cz = oz + l;
+        const int ex = cx >= n, ey = cy >= n, ez = cz >= n;
+        const int blk = cn[dir27(ex, ey, ez)];
+        const int lx = cx - ex * n, ly = cy - ey * n, lz = cz - ez * n;
+        atomicAdd(&Uc[(size_t)blk * S3 + ((lz + 1) * S + ly + 1) * S + lx + 1], acc);
+        atomicAdd(&Hc[(size_t)blk * n3 + (lz * n + ly) * n + lx], -acc);
+    }
+}
+
+void launch_prolong_T(double* Uc, double* Hc, const double* Uf, LevelView lf, LevelView lc, int n, cudaStream_t s) {
+    if (lf.nb == 0) return;
+    k_prolong_T<<<lf.nb, 256, 0, s>>>(Uc, Hc, Uf, lf, lc, n);
+}
+
+// Transpose of the restriction of r (full weighting (1/4)[1 2 1]^3, or
+// injection where the 27-point window of the coarse node leaves Omega_k):
+// each node p of level-k block B gathers from the covered coarse nodes X
+// with |2X - p| <= 1.  The fine image 2X lies in B or in B's upper
+// neighbours; X's window is complete when the level-k blocks below 2X exist
+// along the axes where 2X sits on the block's lower face.  Writes Rf[B].
+__global__ void k_fw_T(double* __restrict__ Rf, const double* __restrict__ Fc, LevelView lf, int n) {
+    __shared__ int nb27[27];
+    const int B = blockIdx.x;
+    if (threadIdx.x < 27) nb27[threadIdx.x] = lf.nbr[27 * B + threadIdx.x];
+    __syncthreads();
+    const int h = n >> 1, n3 = n * n * n;
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int p[3] = {t % n, (t / n) % n, t / (n * n)};
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            if (p[a] & 1) { lo[a] = -1; hi[a] = 1; }
+            else { lo[a] = 0; hi[a] = 0; }
+        }
+        double acc = 0.0;
+        for (int dz = lo[2]; dz <= hi[2]; dz += 2)
+            for (int dy = lo[1]; dy <= hi[1]; dy += 2)
+                for (int dx = lo[0]; dx <= hi[0]; dx += 2) {
+                    const int d[3] = {dx, dy, dz};
+                    int e[3], q[3];
+                    for (int a = 0; a < 3; ++a) {
+                        const int v = p[a] + d[a];          // 0..n, even
+                        e[a] = v >= n ? 1 : 0;
+                        q[a] = v - e[a] * n;
+                    }
+                    const int c = nb27[dir27(e[0], e[1], e[2])];
+                    if (c < 0) continue;                     // 2X not in Omega_k: X is not covered
+                    bool inside = true;
+                    for (int sz = 0; sz <= (q[2] == 0); ++sz)
+                        for (int sy = 0; sy <= (q[1] == 0); ++sy)
+                            for (int sx = 0; sx <= (q[0] == 0); ++sx)
+                                if (lf.nbr[27 * c + dir27(-sx, -sy, -sz)] < 0) inside = false;
+                    const int P = lf.parent[c], o = lf.octant[c];
+                    const int X = (o & 1) * h + (q[0] >> 1), Y = ((o >> 1) & 1) * h + (q[1] >> 1),
+                              Z = ((o >> 2) & 1) * h + (q[2] >> 1);
+                    const double v = Fc[(size_t)P * n3 + (Z * n + Y) * n + X];
+                    if (inside) {
+                        const double w = (dx ? 1.0 : 2.0) * (dy ? 1.0 : 2.0) * (dz ? 1.0 : 2.0) / 64.0;
+                        acc += w * v;
+                    } else if ((dx | dy | dz) == 0) {
+                        acc += v;
+                    }
+                }
+        Rf[(size_t)B * n3 + t] = acc;
+    }
+}
+
+void launch_fw_T(double* Rf, const double* Fc, LevelView lf, int n, cudaStream_t s) {
+    if (lf.nb == 0) return;
+    k_fw_T<<<lf.nb, 256, 0, s>>>(Rf, Fc, lf, n);
+}
+
+// ---------------------------------------------------------------- level 0
+// Transpose of the write of the level-0 target cube [-1, N0]^3 into every
+// level-0 block's (n+2)^3 box: each cube node sums the boxes that hold it.
+__global__ void k_window_T(double* __restrict__ cube, const double* __restrict__ U0, int n, int nbx, int nby, int nbz) {
+    const int Cx = nbx * n + 2, Cy = nby * n + 2, Cz = nbz * n + 2;
+    const size_t total = (size_t)Cx * Cy * Cz;
+    const int S = n + 2, S3 = S * S * S;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int tx = (int)(t % Cx) - 1, ty = (int)((t / Cx) % Cy) - 1, tz = (int)(t / ((size_t)Cx * Cy)) - 1;
+        double acc = 0.0;
+        for (int bz = (tz - 1 < 0 ? -1 : (tz - 1) / n); bz <= (tz + 1) / n; ++bz) {
+            if (bz < 0 || bz >= nbz || tz < bz * n - 1 || tz > bz * n + n) continue;
+            for (int by = (ty - 1 < 0 ? -1 : (ty - 1) / n); by <= (ty + 1) / n; ++by) {
+                if (by < 0 || by >= nby || ty < by * n - 1 || ty > by * n + n) continue;
+                for (int bx = (tx - 1 < 0 ? -1 : (tx - 1) / n); bx <= (tx + 1) / n; ++bx) {
+                    if (bx < 0 || bx >= nbx || tx < bx * n - 1 || tx > bx * n + n) continue;
+                    const int blk = (bz * nby + by) * nbx + bx;
+                    acc += U0[(size_t)blk * S3 + ((tz - bz * n + 1) * S + ty - by * n + 1) * S + tx - bx * n + 1];
+                }
+            }
+        }
+        cube[t] = acc;
+    }
+}
+
+void launch_window_T(double* cube, const double* U0, int n, const int* nb0, cudaStream_t s) {
+    k_window_T<<<4 * 152, 256, 0, s>>>(cube, U0, n, nb0[0], nb0[1], nb0[2]);
+}
+
+// Dense level-0 source array [0, N0)^3 -> per-block n^3 arrays of the listed blocks (add or set).
+__global__ void k_dense_to_blocks(double* __restrict__ out, const double* __restrict__ dense, const int* __restrict__ blocks,
+                                  const int* __restrict__ coords, int n, int N0x, int N0y, bool add) {
+    const int b = blocks[blockIdx.x];
+    const int cx = coords[3 * b] * n, cy = coords[3 * b + 1] * n, cz = coords[3 * b + 2] * n;
+    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const double v = dense[((size_t)(cz + z) * N0y + cy + y) * N0x + cx + x];
+        if (add) out[(size_t)b * n * n * n + t] += v;
+        else out[(size_t)b * n * n * n + t] = v;
+    }
+}
+
+void launch_dense_to_blocks(double* out, const double* dense, const int* blocks, int nblocks, const int* coords, int n,
+                            const int* n0, bool add, cudaStream_t s) {
+    if (nblocks == 0) return;
+    k_dense_to_blocks<<<nblocks, 256, 0, s>>>(out, dense, blocks, coords, n, n0[0], n0[1], add);
+}
+
+// ---------------------------------------------------------------- block and vector helpers
+// out[b] = scale * interior of A[b] (halo g) for the listed blocks.
+__global__ void k_interior_get(double* __restrict__ out, const double* __restrict__ A, int g, const int* __restrict__ blocks,
+                               int n, double scale) {
+    const int b = blocks[blockIdx.x];
+    const int S = n + 2 * g;
+    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        out[(size_t)b * n * n * n + t] = scale * A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g];
+    }
+}
+
+void launch_interior_get(double* out, const double* A, int g, const int* blocks, int nblocks, int n, double scale,
+                         cudaStream_t s) {
+    if (nblocks == 0) return;
+    k_interior_get<<<nblocks, 256, 0, s>>>(out, A, g, blocks, n, scale);
+}
+
+// interior of A[b] (halo g) += scale * v[b] for the listed blocks.
+__global__ void k_interior_add(double* __restrict__ A, int g, const double* __restrict__ v, const int* __restrict__ blocks,
+                               int n, double scale) {
+    const int b = blocks[blockIdx.x];
+    const int S = n + 2 * g;
+    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g] += scale * v[(size_t)b * n * n * n + t];
+    }
+}
+
+void launch_interior_add(double* A, int g, const double* v, const int* blocks, int nblocks, int n, double scale,
+                         cudaStream_t s) {
+    if (nblocks == 0) return;
+    k_interior_add<<<nblocks, 256, 0, s>>>(A, g, v, blocks, n, scale);
+}
+
+// out[b] = scale * in[b] (n^3 arrays) for the listed blocks; in may be null (zero).
+__global__ void k_block_copy(double* __restrict__ out, const double* __restrict__ in, const int* __restrict__ blocks, int n,
+                             double scale) {
+    const int b = blocks[blockIdx.x];
+    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x)
+        out[(size_t)b * n * n * n + t] = in ? scale * in[(size_t)b * n * n * n + t] : 0.0;
+}
+
+void launch_block_copy(double* out, const double* in, const int* blocks, int nblocks, int n, double scale, cudaStream_t s) {
+    if (nblocks == 0) return;
+    k_block_copy<<<nblocks, 256, 0, s>>>(out, in, blocks, n, scale);
+}
+
+void launch_block_zero(double* out, const int* blocks, int nblocks, int n, cudaStream_t s) {
+    if (nblocks == 0) return;
+    k_block_copy<<<nblocks, 256, 0, s>>>(out, nullptr, blocks, n, 0.0);
+}
+
+// out = a x + b y over a flat vector (out may alias x or y); optionally
+// max |out| into *absmax (bit pattern of a non-negative double, NaN mapped to +Inf).
+__global__ void k_lincomb(double* out, double a, const double* x, double b, const double* y, size_t len,
+                          unsigned long long* absmax) {
+    __shared__ double red[32];
+    double m = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = a * x[i] + b * y[i];
+        out[i] = v;
+        m = fmax(m, v != v ? __longlong_as_double(0x7ff0000000000000ULL) : fabs(v));
+    }
+    if (!absmax) return;
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = m;
+    __syncthreads();
+    if (w == 0) {
+        m = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (lane == 0) atomicMax(absmax, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+void launch_lincomb(double* out, double a, const double* x, double b, const double* y, size_t len,
+                    unsigned long long* absmax, cudaStream_t s) {
+    if (len == 0) return;
+    k_lincomb<<<4 * 152, 256, 0, s>>>(out, a, x, b, y, len, absmax);
+}
+
+}  // namespace mrp

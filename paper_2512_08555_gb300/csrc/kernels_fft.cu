@@ -168,56 +168,77 @@ __device__ C* fft_line(C* a, C* b, const FftLine<R>& L, int sign) {
 constexpr int FFT_TX = 64;   // threads per line
 constexpr int FFT_LY = 4;    // lines per CTA
 
+// Geometry of one convolution: padded lengths, half spectrum, and the input
+// (source) and output (target) node ranges per axis (x, y, z).  A node i of a
+// range sits at padded index (i + P) mod P.  The circular convolution equals
+// the linear one when in_n + out_n - 1 <= P on every axis.
 struct Geo {
     int n, nbx, nby, nbz;
-    int N0x, N0y, N0z;
     int Px, Py, Pz, Kx, Ky, Kz;
+    int in_lo[3], in_n[3], out_lo[3], out_n[3];
+    int dense_in, dense_out;   // 0: level-0 block layouts, 1: dense arrays over the ranges
 };
 
+__device__ __forceinline__ int pidx(int i, int P) { return (i % P + P) % P; }
+
 // ---------------------------------------------------------------- pass A (x, real -> half spectrum)
+// lines: input (y, z) range; x input range.
 template <typename R>
-__global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ F0, Geo g, FftLine<R> L) {
+__global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ src, Geo g, FftLine<R> L) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
     const int line = blockIdx.x * FFT_LY + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
-    const bool live = line < g.N0y * g.N0z;
-    const int y = live ? line % g.N0y : 0, z = live ? line / g.N0y : 0;
-    const int by = y / g.n, ly = y % g.n, bz = z / g.n, lz = z % g.n;
-    for (int x = threadIdx.x; x < L.P; x += blockDim.x) {
-        R v = R(0);
-        if (live && x < g.N0x) {
-            const int bx = x / g.n, lx = x % g.n;
-            const int blk = (bz * g.nby + by) * g.nbx + bx;
-            v = F0[(size_t)blk * g.n * g.n * g.n + (lz * g.n + ly) * g.n + lx];
+    const bool live = line < g.in_n[1] * g.in_n[2];
+    const int ty = live ? line % g.in_n[1] : 0, tz = live ? line / g.in_n[1] : 0;
+    const int y = g.in_lo[1] + ty, z = g.in_lo[2] + tz;
+    for (int j = threadIdx.x; j < L.P; j += blockDim.x) a[j] = C{R(0), R(0)};
+    __syncthreads();
+    if (live)
+        for (int tx = threadIdx.x; tx < g.in_n[0]; tx += blockDim.x) {
+            const int x = g.in_lo[0] + tx;
+            R v;
+            if (g.dense_in) {
+                v = src[((size_t)tz * g.in_n[1] + ty) * g.in_n[0] + tx];
+            } else {
+                const int bx = x / g.n, lx = x % g.n, by = y / g.n, ly = y % g.n, bz = z / g.n, lz = z % g.n;
+                const int blk = (bz * g.nby + by) * g.nbx + bx;
+                v = src[(size_t)blk * g.n * g.n * g.n + (lz * g.n + ly) * g.n + lx];
+            }
+            a[pidx(x, L.P)] = C{v, R(0)};
         }
-        a[x] = C{v, R(0)};
-    }
     __syncthreads();
     C* r = fft_line<R>(a, b, L, -1);
-    if (live)
-        for (int k = threadIdx.x; k < g.Kx; k += blockDim.x) spec[((size_t)z * g.Py + y) * g.Kx + k] = r[k];
+    if (live) {
+        const size_t row = ((size_t)pidx(z, g.Pz) * g.Py + pidx(y, g.Py)) * g.Kx;
+        for (int k = threadIdx.x; k < g.Kx; k += blockDim.x) spec[row + k] = r[k];
+    }
 }
 
-// ---------------------------------------------------------------- pass B (y, forward), lines (z < N0z, kx)
+// ---------------------------------------------------------------- pass B (y, forward), lines (input z, kx)
 template <typename R>
 __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const int z = blockIdx.y;
+    const int zi = pidx(g.in_lo[2] + (int)blockIdx.y, g.Pz);
     const int kx = blockIdx.x * FFT_LY + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
     const bool live = kx < g.Kx;
-    for (int y = threadIdx.x; y < L.P; y += blockDim.x)
-        a[y] = (live && y < g.N0y) ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : C{R(0), R(0)};
+    for (int j = threadIdx.x; j < L.P; j += blockDim.x) a[j] = C{R(0), R(0)};
+    __syncthreads();
+    if (live)
+        for (int t = threadIdx.x; t < g.in_n[1]; t += blockDim.x) {
+            const int j = pidx(g.in_lo[1] + t, g.Py);
+            a[j] = spec[((size_t)zi * g.Py + j) * g.Kx + kx];
+        }
     __syncthreads();
     C* r = fft_line<R>(a, b, L, -1);
     if (live)
-        for (int y = threadIdx.x; y < L.P; y += blockDim.x) spec[((size_t)z * g.Py + y) * g.Kx + kx] = r[y];
+        for (int y = threadIdx.x; y < L.P; y += blockDim.x) spec[((size_t)zi * g.Py + y) * g.Kx + kx] = r[y];
 }
 
 // ---------------------------------------------------------------- pass C (z forward, x G-hat, z inverse), lines (ky, kx)
@@ -231,8 +252,13 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
     const bool live = kx < g.Kx;
-    for (int z = threadIdx.x; z < L.P; z += blockDim.x)
-        a[z] = (live && z < g.N0z) ? spec[((size_t)z * g.Py + ky) * g.Kx + kx] : C{R(0), R(0)};
+    for (int j = threadIdx.x; j < L.P; j += blockDim.x) a[j] = C{R(0), R(0)};
+    __syncthreads();
+    if (live)
+        for (int t = threadIdx.x; t < g.in_n[2]; t += blockDim.x) {
+            const int j = pidx(g.in_lo[2] + t, g.Pz);
+            a[j] = spec[((size_t)j * g.Py + ky) * g.Kx + kx];
+        }
     __syncthreads();
     C* r = fft_line<R>(a, b, L, -1);
     const int fy = ky <= g.Py - ky ? ky : g.Py - ky;
@@ -245,19 +271,19 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
     C* other = (r == a) ? b : a;
     C* q = fft_line<R>(r, other, L, +1);
     if (live)
-        for (int t = threadIdx.x; t < g.N0z + 2; t += blockDim.x) {
-            const int z = (t - 1 + g.Pz) % g.Pz;
+        for (int t = threadIdx.x; t < g.out_n[2]; t += blockDim.x) {
+            const int z = pidx(g.out_lo[2] + t, g.Pz);
             spec[((size_t)z * g.Py + ky) * g.Kx + kx] = q[z];
         }
 }
 
-// ---------------------------------------------------------------- pass B' (y inverse), lines (target z, kx)
+// ---------------------------------------------------------------- pass B' (y inverse), lines (output z, kx)
 template <typename R>
 __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const int z = ((int)blockIdx.y - 1 + g.Pz) % g.Pz;
+    const int z = pidx(g.out_lo[2] + (int)blockIdx.y, g.Pz);
     const int kx = blockIdx.x * FFT_LY + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
@@ -267,28 +293,28 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
     __syncthreads();
     C* r = fft_line<R>(a, b, L, +1);
     if (live)
-        for (int t = threadIdx.x; t < g.N0y + 2; t += blockDim.x) {
-            const int y = (t - 1 + g.Py) % g.Py;
+        for (int t = threadIdx.x; t < g.out_n[1]; t += blockDim.x) {
+            const int y = pidx(g.out_lo[1] + t, g.Py);
             spec[((size_t)z * g.Py + y) * g.Kx + kx] = r[y];
         }
 }
 
 // ---------------------------------------------------------------- pass A' (x inverse, half spectrum -> real)
-// Writes u at target (x, y, z) in [-1, N0]^3 into every level-0 block whose
-// (n+2)^3 box holds that node (interior or ghost layer).
+// lines: output (y, z) range.  Block mode writes node (x, y, z) into every
+// level-0 block whose (n+2)^3 box holds it (interior or ghost layer); dense
+// mode writes the dense output range.
 template <typename R>
-__global__ void k_fft_x_inv(R* __restrict__ U0, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
+__global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
     const int line = blockIdx.x * FFT_LY + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
-    const int ny = g.N0y + 2;
-    const bool live = line < ny * (g.N0z + 2);
-    const int ty = live ? line % ny - 1 : 0, tz = live ? line / ny - 1 : 0;
-    const int yi = (ty + g.Py) % g.Py, zi = (tz + g.Pz) % g.Pz;
-    const C* src = spec + ((size_t)zi * g.Py + yi) * g.Kx;
+    const bool live = line < g.out_n[1] * g.out_n[2];
+    const int oy = live ? line % g.out_n[1] : 0, oz = live ? line / g.out_n[1] : 0;
+    const int ty = g.out_lo[1] + oy, tz = g.out_lo[2] + oz;
+    const C* src = spec + ((size_t)pidx(tz, g.Pz) * g.Py + pidx(ty, g.Py)) * g.Kx;
     for (int k = threadIdx.x; k < L.P; k += blockDim.x) {
         C v = C{R(0), R(0)};
         if (live) {
@@ -300,10 +326,15 @@ __global__ void k_fft_x_inv(R* __restrict__ U0, const typename Cx<R>::T* __restr
     __syncthreads();
     C* r = fft_line<R>(a, b, L, +1);
     if (!live) return;
+    if (g.dense_out) {
+        for (int ox = threadIdx.x; ox < g.out_n[0]; ox += blockDim.x)
+            dst[((size_t)oz * g.out_n[1] + oy) * g.out_n[0] + ox] = r[pidx(g.out_lo[0] + ox, g.Px)].x;
+        return;
+    }
     const int S = g.n + 2;
-    for (int t = threadIdx.x; t < g.N0x + 2; t += blockDim.x) {
-        const int tx = t - 1;
-        const R val = r[(tx + g.Px) % g.Px].x;
+    for (int ox = threadIdx.x; ox < g.out_n[0]; ox += blockDim.x) {
+        const int tx = g.out_lo[0] + ox;
+        const R val = r[pidx(tx, g.Px)].x;
         for (int bz = (tz - 1 < 0 ? -1 : (tz - 1) / g.n); bz <= (tz + 1) / g.n; ++bz) {
             if (bz < 0 || bz >= g.nbz || tz < bz * g.n - 1 || tz > bz * g.n + g.n) continue;
             for (int by = (ty - 1 < 0 ? -1 : (ty - 1) / g.n); by <= (ty + 1) / g.n; ++by) {
@@ -312,38 +343,47 @@ __global__ void k_fft_x_inv(R* __restrict__ U0, const typename Cx<R>::T* __restr
                     if (bx < 0 || bx >= g.nbx || tx < bx * g.n - 1 || tx > bx * g.n + g.n) continue;
                     const int blk = (bz * g.nby + by) * g.nbx + bx;
                     const int lx = tx - bx * g.n + 1, ly = ty - by * g.n + 1, lz = tz - bz * g.n + 1;
-                    U0[(size_t)blk * S * S * S + (lz * S + ly) * S + lx] = val;
+                    dst[(size_t)blk * S * S * S + (lz * S + ly) * S + lx] = val;
                 }
             }
         }
     }
 }
 
+// Forward geometry: sources on level-0 nodes [0, N0), targets [-1, N0].
 static Geo geo_of(const Handle& h) {
     Geo g{};
     g.n = h.n;
     g.nbx = h.nb0[0]; g.nby = h.nb0[1]; g.nbz = h.nb0[2];
-    g.N0x = h.n0[0]; g.N0y = h.n0[1]; g.N0z = h.n0[2];
     g.Px = h.ax[0].P; g.Py = h.ax[1].P; g.Pz = h.ax[2].P;
     g.Kx = h.gK[0]; g.Ky = h.gK[1]; g.Kz = h.gK[2];
+    for (int a = 0; a < 3; ++a) {
+        g.in_lo[a] = 0; g.in_n[a] = h.n0[a];
+        g.out_lo[a] = -1; g.out_n[a] = h.n0[a] + 2;
+    }
     return g;
 }
 
 template <typename R>
-static void coarse_passes(const Handle& h, typename Cx<R>::T* spec, const R* ghat, const R* F0, R* U0, cudaStream_t s) {
+static void conv_passes(const Handle& h, const Geo& g, typename Cx<R>::T* spec, const R* ghat, const R* src, R* dst,
+                        cudaStream_t s) {
     using C = typename Cx<R>::T;
-    const Geo g = geo_of(h);
     const dim3 blk(FFT_TX, FFT_LY);
     const FftLine<R> Lx = line_of<R>(h.ax[0]), Ly = line_of<R>(h.ax[1]), Lz = line_of<R>(h.ax[2]);
     const size_t smx = sizeof(C) * 2 * FFT_LY * g.Px;
     const size_t smy = sizeof(C) * 2 * FFT_LY * g.Py;
     const size_t smz = sizeof(C) * 2 * FFT_LY * g.Pz;
     const int kxb = (g.Kx + FFT_LY - 1) / FFT_LY;
-    k_fft_x_fwd<R><<<(g.N0y * g.N0z + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(spec, F0, g, Lx);
-    k_fft_y_fwd<R><<<dim3(kxb, g.N0z), blk, smy, s>>>(spec, g, Ly);
+    k_fft_x_fwd<R><<<(g.in_n[1] * g.in_n[2] + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(spec, src, g, Lx);
+    k_fft_y_fwd<R><<<dim3(kxb, g.in_n[2]), blk, smy, s>>>(spec, g, Ly);
     k_fft_z_conv<R><<<dim3(kxb, g.Py), blk, smz, s>>>(spec, ghat, g, Lz);
-    k_fft_y_inv<R><<<dim3(kxb, g.N0z + 2), blk, smy, s>>>(spec, g, Ly);
-    k_fft_x_inv<R><<<((g.N0y + 2) * (g.N0z + 2) + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(U0, spec, g, Lx);
+    k_fft_y_inv<R><<<dim3(kxb, g.out_n[2]), blk, smy, s>>>(spec, g, Ly);
+    k_fft_x_inv<R><<<(g.out_n[1] * g.out_n[2] + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(dst, spec, g, Lx);
+}
+
+template <typename R>
+static void coarse_passes(const Handle& h, typename Cx<R>::T* spec, const R* ghat, const R* F0, R* U0, cudaStream_t s) {
+    conv_passes<R>(h, geo_of(h), spec, ghat, F0, U0, s);
 }
 
 void launch_coarse_solve(Handle& h, cudaStream_t s) {
@@ -362,6 +402,20 @@ template void launch_coarse_solve_t<float>(const Handle&, const float*, float*, 
 // caller (spec must hold Pz * Py * (Px/2+1) complex values).
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s) {
     coarse_passes<double>(h, spec, h.ghat, F0, U0, s);
+}
+
+// Transpose of the level-0 convolution (FP64): dense adjoint on the target
+// cube [-1, N0]^3 -> dense adjoint on the sources [0, N0)^3.  The kernel is
+// even, so this is the convolution with the two ranges exchanged.
+void launch_conv_transpose(const Handle& h, const double* cube_in, double* src_out, cudaStream_t s) {
+    Geo g = geo_of(h);
+    for (int a = 0; a < 3; ++a) {
+        g.in_lo[a] = -1; g.in_n[a] = h.n0[a] + 2;
+        g.out_lo[a] = 0; g.out_n[a] = h.n0[a];
+    }
+    g.dense_in = 1;
+    g.dense_out = 1;
+    conv_passes<double>(h, g, h.spec, h.ghat, cube_in, src_out, s);
 }
 
 // ============================================================================

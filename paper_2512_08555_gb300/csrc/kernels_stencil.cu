@@ -163,7 +163,6 @@ void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk,
 // ----------------------------------------------------------------------------
 // Leaf scatter / gather between the caller's [leaf][n^3] layout and the
 // per-level halo layout.
-struct LevelPtrs { double* p[32]; };
 
 __global__ void k_scatter_leaves(const double* __restrict__ f, const int* __restrict__ leaf_level,
                                  const int* __restrict__ leaf_block, LevelPtrs dst, int n, int g) {
@@ -199,6 +198,14 @@ void launch_gather_leaves(Handle& h, double* u, cudaStream_t s) {
     LevelPtrs lp{};
     for (int k = 0; k <= h.L; ++k) lp.p[k] = h.lv[k].U;
     k_gather_leaves<<<h.n_leaves, 256, 0, s>>>(u, h.leaf_level, h.leaf_block, lp, h.n, 1);
+}
+
+void launch_scatter_leaves_to(const Handle& h, const double* f, const LevelPtrs& dst, int g, cudaStream_t s) {
+    k_scatter_leaves<<<h.n_leaves, 256, 0, s>>>(f, h.leaf_level, h.leaf_block, dst, h.n, g);
+}
+
+void launch_gather_leaves_from(const Handle& h, double* u, const LevelPtrs& src, int g, cudaStream_t s) {
+    k_gather_leaves<<<h.n_leaves, 256, 0, s>>>(u, h.leaf_level, h.leaf_block, src, h.n, g);
 }
 
 // ----------------------------------------------------------------------------

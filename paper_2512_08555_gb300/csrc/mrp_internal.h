@@ -100,18 +100,64 @@ struct Handle {
     std::vector<Pending> pend;
     double prof_ms[16] = {};
     int64_t prof_cnt[16] = {}, prof_nodes[16] = {};
+    // gradient of the converged solve (adjoint.cu), allocated at its first call
+    struct AdjLevel { double *Ub = nullptr, *Fb = nullptr, *Rb = nullptr, *Hb = nullptr, *Rawb = nullptr; };
+    std::vector<AdjLevel> adj;
+    std::vector<size_t> xoff;         // level k's offset in the vectors below, which hold [nb_k][n^3] per level
+    double *lam = nullptr, *rho = nullptr, *gvec = nullptr, *xb = nullptr, *fsb = nullptr, *wl = nullptr;
+    double *cube = nullptr, *dense = nullptr, *off0b = nullptr;
 };
+
+inline double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
+inline int64_t n3(const Handle& h) { return (int64_t)h.n * h.n * h.n; }
+inline LevelView view_or_empty(const Handle& h, int k) {
+    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+}
+
+// Per-level base pointers, passed by value to the leaf scatter / gather kernels.
+struct LevelPtrs { double* p[32]; };
 
 enum Phase { PH_GHOST = 0, PH_SMOOTH = 1, PH_RESIDUAL = 2, PH_RESTRICT = 3, PH_COARSE = 4, PH_PROLONG = 5,
              PH_NORM = 6, PH_OTHER = 7 };
 // Phases of FP32 work are counted separately, at index + 8.
 template <typename T> constexpr int ph(int p) { return p + (sizeof(T) == 4 ? 8 : 0); }
 
+// Per-phase accounting: counts launches; with profiling on, records a CUDA
+// event pair around the phase (harvested at the next host synchronisation).
+struct PhaseScope {
+    Handle& h;
+    cudaStream_t s;
+    int phase, e0 = -1, launches;
+    int64_t nodes;
+    PhaseScope(Handle& hh, cudaStream_t ss, int ph, int64_t nd, int nl) : h(hh), s(ss), phase(ph), launches(nl), nodes(nd) {
+        if (h.prof && h.ev_used + 2 <= (int)h.ev.size()) {
+            e0 = h.ev_used;
+            h.ev_used += 2;
+            cudaEventRecord(h.ev[e0], s);
+        }
+    }
+    ~PhaseScope() {
+        h.launches += launches;
+        if (e0 >= 0) {
+            cudaEventRecord(h.ev[e0 + 1], s);
+            h.pend.push_back(Handle::Pending{phase, e0, nodes});
+        }
+    }
+};
+void harvest(Handle& h);
+// Copies device scalar h.dmax[slot] (a max-norm) to *out; synchronises s.
+int read_max(Handle& h, cudaStream_t s, double* out, int slot);
+
 // ---------------------------------------------------------------- host side
 int build_forest(Handle& h, const mrp_forest& f, std::string& why);
 int upload_tables(Handle& h);
 int lgf_build(Handle& h, cudaStream_t s);   // tabulate G and the scaled spectrum
 int fft_plan(Handle& h);
+// gradient of the converged solve (adjoint.cu)
+int adjoint_setup(Handle& h);
+void adjoint_release(Handle& h);
+int solve_adjoint(Handle& h, const double* w, double* fbar, cudaStream_t s, int* cycles_out, double* rel_out);
+int adjoint_op(Handle& h, int op, const double* in, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- launches (kernels_*.cu)
 // Templated launchers are instantiated for double (FP64 path, outer refinement)
@@ -158,6 +204,29 @@ void launch_leaf_residual_max(const double* U, const double* F, const int* leaf_
 void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, cudaStream_t s);
 void launch_coarse_solve(Handle& h, cudaStream_t s);
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s);
+void launch_conv_transpose(const Handle& h, const double* cube_in, double* src_out, cudaStream_t s);
+void launch_scatter_leaves_to(const Handle& h, const double* f, const LevelPtrs& dst, int g, cudaStream_t s);
+void launch_gather_leaves_from(const Handle& h, double* u, const LevelPtrs& src, int g, cudaStream_t s);
+// transposed operators (kernels_adjoint.cu)
+void launch_stencil_T(double* out, const double* lam, double* fadd, const int* blocks, int nblocks, int n, int M,
+                      double inv_h2, cudaStream_t s);
+void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nblocks, int n, int M, cudaStream_t s);
+void launch_ghost_T(double* A, int g, double* Ac, int gc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
+void launch_inject_T(double* fine, int gf, double* coarse, int gc, LevelView lf, int n, cudaStream_t s);
+void launch_smooth_T(double* U, double* F, int nb, int n, int M, double h2, cudaStream_t s);
+void launch_prolong_T(double* Uc, double* Hc, const double* Uf, LevelView lf, LevelView lc, int n, cudaStream_t s);
+void launch_fw_T(double* Rf, const double* Fc, LevelView lf, int n, cudaStream_t s);
+void launch_window_T(double* cube, const double* U0, int n, const int* nb0, cudaStream_t s);
+void launch_dense_to_blocks(double* out, const double* dense, const int* blocks, int nblocks, const int* coords, int n,
+                            const int* n0, bool add, cudaStream_t s);
+void launch_interior_get(double* out, const double* A, int g, const int* blocks, int nblocks, int n, double scale,
+                         cudaStream_t s);
+void launch_interior_add(double* A, int g, const double* v, const int* blocks, int nblocks, int n, double scale,
+                         cudaStream_t s);
+void launch_block_copy(double* out, const double* in, const int* blocks, int nblocks, int n, double scale, cudaStream_t s);
+void launch_block_zero(double* out, const int* blocks, int nblocks, int n, cudaStream_t s);
+void launch_lincomb(double* out, double a, const double* x, double b, const double* y, size_t len,
+                    unsigned long long* absmax, cudaStream_t s);
 // mixed precision helpers (kernels_mixed.cu)
 void launch_leaf_residual_store(double* R, const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
                                 double inv_h2, unsigned long long* out, cudaStream_t s);

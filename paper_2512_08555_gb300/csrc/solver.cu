@@ -187,6 +187,7 @@ int upload_tables(Handle& h) {
 }
 
 static void release(Handle& h) {
+    adjoint_release(h);
     for (Level& lv : h.lv) {
         cudaFree(lv.coords); cudaFree(lv.nbr); cudaFree(lv.parent); cudaFree(lv.octant); cudaFree(lv.children);
         cudaFree(lv.leaf_blocks); cudaFree(lv.cov_blocks); cudaFree(lv.is_leaf); cudaFree(lv.order);
@@ -251,36 +252,7 @@ static int mixed_setup(Handle& h) {
 }
 
 // ---------------------------------------------------------------- schedule (Alg. 1)
-static double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
-
-static LevelView view_or_empty(const Handle& h, int k) {
-    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-}
-
-// Per-phase accounting: counts launches; with profiling on, records a CUDA
-// event pair around the phase (harvested at the next host synchronisation).
-struct PhaseScope {
-    Handle& h;
-    cudaStream_t s;
-    int phase, e0 = -1, launches;
-    int64_t nodes;
-    PhaseScope(Handle& hh, cudaStream_t ss, int ph, int64_t nd, int nl) : h(hh), s(ss), phase(ph), launches(nl), nodes(nd) {
-        if (h.prof && h.ev_used + 2 <= (int)h.ev.size()) {
-            e0 = h.ev_used;
-            h.ev_used += 2;
-            cudaEventRecord(h.ev[e0], s);
-        }
-    }
-    ~PhaseScope() {
-        h.launches += launches;
-        if (e0 >= 0) {
-            cudaEventRecord(h.ev[e0 + 1], s);
-            h.pend.push_back(Handle::Pending{phase, e0, nodes});
-        }
-    }
-};
-
-static void harvest(Handle& h) {
+void harvest(Handle& h) {
     for (const auto& p : h.pend) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h.ev[p.e0], h.ev[p.e0 + 1]) == cudaSuccess) {
@@ -293,7 +265,6 @@ static void harvest(Handle& h) {
     h.ev_used = 0;
 }
 
-static int64_t n3(const Handle& h) { return (int64_t)h.n * h.n * h.n; }
 static int64_t halo_nodes(const Handle& h, int g) { const int64_t S = h.n + 2 * g; return S * S * S - n3(h); }
 
 // Per-level fields of one working precision: FP64 (plain path and outer
@@ -414,7 +385,7 @@ static void vcycle(Handle& h, cudaStream_t s) {
 
 static double as_double(unsigned long long b) { double d; std::memcpy(&d, &b, sizeof d); return d; }
 
-static int read_max(Handle& h, cudaStream_t s, double* out, int slot) {
+int read_max(Handle& h, cudaStream_t s, double* out, int slot) {
     if (cudaMemcpyAsync(h.hmax + slot, h.dmax + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return MRP_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
@@ -617,10 +588,33 @@ int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats
 }
 
 int mrp_solve_adjoint(mrp_handle* H, const double* w, double* fbar, void* stream, mrp_stats* st) {
-    (void)w; (void)fbar; (void)stream; (void)st;
-    if (!H) return MRP_ERR_INVALID_ARG;
-    if (!H->h.have_forward) return MRP_ERR_NO_FORWARD;
-    return MRP_ERR_UNSUPPORTED;
+    if (!H || !w || !fbar) return MRP_ERR_INVALID_ARG;
+    Handle& h = H->h;
+    const int64_t launches0 = h.launches;
+    int cycles = 0;
+    double rel = INFINITY;
+    const int rc = solve_adjoint(h, w, fbar, (cudaStream_t)stream, &cycles, &rel);
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->cycles = cycles;
+        st->ir_steps = cycles;
+        st->residual = rel;
+        st->leaf_nodes = h.leaf_nodes;
+        st->total_nodes = h.total_nodes;
+        st->launches = h.launches - launches0;
+    }
+    return rc;
+}
+
+int mrp_adjoint_len(mrp_handle* H, int64_t* len) {
+    if (!H || !len) return MRP_ERR_INVALID_ARG;
+    *len = H->h.total_nodes;
+    return MRP_OK;
+}
+
+int mrp_adjoint_op(mrp_handle* H, int32_t op, const double* in, double* out, void* stream) {
+    if (!H || !in || !out) return MRP_ERR_INVALID_ARG;
+    return adjoint_op(H->h, op, in, out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------- step API

@@ -25,7 +25,8 @@ STEPS = {"prepare_rhs": 0, "ghost_u": 1, "smooth": 2, "residual": 3, "restrict":
 EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_error_string",
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
-            "mrp_coarse_solve_noalloc"]
+            "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op"]
+ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
 
@@ -85,6 +86,8 @@ def load_library(path=LIB_PATH):
     lib.mrp_profile_enable.argtypes = [P, I32]
     lib.mrp_profile_read.argtypes = [P, I32, P, P, P, I32]
     lib.mrp_coarse_solve_noalloc.argtypes = [P, P, P, P]
+    lib.mrp_adjoint_len.argtypes = [P, C.POINTER(I64)]
+    lib.mrp_adjoint_op.argtypes = [P, I32, P, P, P]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
     lib.mrp_error_string.restype = C.c_char_p
@@ -159,6 +162,40 @@ class Solver:
                                 C.byref(st))
         _check(rc, "mrp_solve", allow)
         return u, st
+
+    def solve_adjoint(self, w, fbar=None, stream=None, allow_not_converged=False):
+        """fbar = S^T w, the gradient of <w, u> with respect to f for the converged solve.
+
+        w, fbar: CUDA float64 tensors [n_leaves, n, n, n] (leaf layout of solve).
+        """
+        import torch
+        n = self.n
+        if w.dtype != torch.float64 or not w.is_cuda or not w.is_contiguous() or w.numel() != self.n_leaves * n ** 3:
+            raise ValueError("w must be a contiguous CUDA float64 tensor of shape [n_leaves, n, n, n]")
+        if fbar is None:
+            fbar = torch.empty_like(w)
+        st = Stats()
+        allow = (MRP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        rc = self.lib.mrp_solve_adjoint(self.h, C.c_void_p(w.data_ptr()), C.c_void_p(fbar.data_ptr()),
+                                        _stream_ptr(stream), C.byref(st))
+        _check(rc, "mrp_solve_adjoint", allow)
+        return fbar, st
+
+    def adjoint_len(self):
+        v = C.c_int64()
+        _check(self.lib.mrp_adjoint_len(self.h, C.byref(v)), "mrp_adjoint_len")
+        return v.value
+
+    def adjoint_op(self, name, x, stream=None):
+        """One factor of the gradient (``ADJ_OPS``); see mrp_adjoint_op for the vector layouts."""
+        import torch
+        L = self.adjoint_len()
+        out_len = {"cycle_T": L, "res_T": 2 * L, "out_T": 2 * L, "rhs_T": self.n_leaves * self.n ** 3}[name]
+        x = x.contiguous()
+        out = torch.zeros(out_len, dtype=torch.float64, device="cuda")
+        _check(self.lib.mrp_adjoint_op(self.h, ADJ_OPS[name], C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                       _stream_ptr(stream)), f"mrp_adjoint_op({name})")
+        return out
 
     # ------------------------------------------------------------------ step API
     def level_count(self):
@@ -247,3 +284,25 @@ class Solver:
         P = np.zeros(3, np.int32)
         _check(self.lib.mrp_fft_shape(self.h, P.ctypes.data_as(C.c_void_p)), "mrp_fft_shape")
         return tuple(int(v) for v in P)
+
+
+def poisson_solve(solver, f):
+    """u = S f with a gradient: differentiable wrapper of ``Solver.solve``.
+
+    The backward pass is ``Solver.solve_adjoint`` (the transposed solve on the
+    device), so d<w, u>/df = S^T w for the converged composite solution.
+    """
+    import torch
+
+    class _Solve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, f_in):
+            u, _ = solver.solve(f_in.contiguous())
+            return u
+
+        @staticmethod
+        def backward(ctx, u_bar):
+            f_bar, _ = solver.solve_adjoint(u_bar.contiguous())
+            return f_bar
+
+    return _Solve.apply(f)
