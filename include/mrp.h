@@ -117,6 +117,20 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
  * max_cycles ran out. */
 int mrp_solve(mrp_handle* h, const double* f, double* u, void* stream, mrp_stats* st);
 
+/* The same solve as mrp_solve, run as one CUDA graph launch with no host
+ * synchronisation inside: per block-size group, a prologue (f*, norms,
+ * u = 0), a device-controlled WHILE loop over cycles (MRP_FP64) or
+ * refinement steps (MRP_MIXED) whose last kernel compares every problem's
+ * relative residual with tol and sets the loop condition, and the gather of
+ * u; the groups' chains are independent branches of the graph and run
+ * concurrently.  The graph is built (captured and instantiated) on the first
+ * call and again whenever f or u differ from the previous call's: such a call
+ * synchronises the stream first and allocates; other calls launch the graph
+ * and synchronise the stream once at the end to read the statistics.  Same
+ * results and status as mrp_solve (st->launches counts the kernels the
+ * graph ran). */
+int mrp_solve_graph(mrp_handle* h, const double* f, double* u, void* stream, mrp_stats* st);
+
 /* Gradient of the converged solve: fbar = S^T w, where u = S f is the
  * composite solution mrp_solve converges to (the map is linear).  S
  * factors as f* = B f (Sec. 3.2 with f ghosts), 0 = c(f*) - K x (the

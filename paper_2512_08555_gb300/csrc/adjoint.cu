@@ -17,6 +17,7 @@
 // blocks; every other entry stays zero.
 #include "mrp_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -47,9 +48,13 @@ int adjoint_setup(Handle& h) {
     const size_t len = h.xoff[h.L + 1];
     for (double** p : {&h.lam, &h.rho, &h.gvec, &h.xb, &h.fsb, &h.wl})
         if ((rc = adj_alloc(*p, len))) return rc;
-    const size_t C = (size_t)(h.n0[0] + 2) * (h.n0[1] + 2) * (h.n0[2] + 2);
+    size_t C = 0, D = 0;
+    for (const Problem& p : h.pr) {
+        C = std::max(C, (size_t)(p.n0[0] + 2) * (p.n0[1] + 2) * (p.n0[2] + 2));
+        D = std::max(D, (size_t)p.n0[0] * p.n0[1] * p.n0[2]);
+    }
     if ((rc = adj_alloc(h.cube, C))) return rc;
-    if ((rc = adj_alloc(h.dense, (size_t)h.n0[0] * h.n0[1] * h.n0[2]))) return rc;
+    if ((rc = adj_alloc(h.dense, D))) return rc;
     if ((rc = adj_alloc(h.off0b, (size_t)h.lv[0].nb * nn))) return rc;
     return MRP_OK;
 }
@@ -76,12 +81,23 @@ static void ghost_fill_T(Handle& h, int k, cudaStream_t s) {
     if (k >= 1) launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, h.lv[k].view(), h.n, s);
 }
 
-// Transpose of the level-0 convolution read on the level-0 boxes: the adjoint
-// of every box (interior and exterior ring) -> the dense source adjoint h.dense.
-static void conv_T(Handle& h, const double* U0bar, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_COARSE, (int64_t)h.n0[0] * h.n0[1] * h.n0[2], 6);
-    launch_window_T(h.cube, U0bar, h.n, h.nb0, s);
-    launch_conv_transpose(h, h.cube, h.dense, s);
+// Transpose of problem p's level-0 convolution read on its level-0 boxes:
+// the adjoint of every box (interior and exterior ring) -> the dense source
+// adjoint h.dense of that problem.
+static void conv_T(Handle& h, const Problem& p, const double* U0bar, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_COARSE, (int64_t)p.n0[0] * p.n0[1] * p.n0[2], 6);
+    const size_t S = h.n + 2;
+    launch_window_T(h.cube, U0bar + (size_t)p.base0 * S * S * S, h.n, p.nb0, s);
+    launch_conv_transpose(h, p, h.cube, h.dense, s);
+}
+
+// h.dense of problem p -> per-block arrays of its covered (cov = true) or leaf
+// level-0 blocks, added or set.
+static void dense_to(Handle& h, const Problem& p, double* out, bool cov, bool add, cudaStream_t s) {
+    const Level& l0 = h.lv[0];
+    const int* list = cov ? l0.cov_blocks + p.cov0_lo : l0.leaf_blocks + p.leaf0_lo;
+    const int cnt = cov ? p.cov0_hi - p.cov0_lo : p.leaf0_hi - p.leaf0_lo;
+    launch_dense_to_blocks(out, h.dense, list, cnt, l0.coords, h.n, p.n0, add, s);
 }
 
 // res^T lambda -> x-bar (into xb); with fsb, also adds c^T lambda (the f*-bar
@@ -108,11 +124,14 @@ static void res_T(Handle& h, const double* lam, double* xb, double* fsb, cudaStr
         PhaseScope ps(h, s, PH_OTHER, l0.ncov * n3(h), 1);
         launch_interior_add(h.adj[0].Ub, 1, lam + h.xoff[0], l0.cov_blocks, l0.ncov, n, ih02, s);
     }
-    conv_T(h, h.adj[0].Ub, s);
+    for (const Problem& p : h.pr) {
+        conv_T(h, p, h.adj[0].Ub, s);
+        PhaseScope ps(h, s, PH_OTHER, (int64_t)l0.nb * n3(h), fsb ? 2 : 1);
+        dense_to(h, p, xb + h.xoff[0], true, false, s);
+        if (fsb) dense_to(h, p, fsb + h.xoff[0], false, true, s);
+    }
     {
-        PhaseScope ps(h, s, PH_OTHER, h.total_nodes, (fsb ? 2 : 1) + L + (L >= 2 ? L - 1 : 0));
-        launch_dense_to_blocks(xb + h.xoff[0], h.dense, l0.cov_blocks, l0.ncov, l0.coords, n, h.n0, false, s);
-        if (fsb) launch_dense_to_blocks(fsb + h.xoff[0], h.dense, l0.leaf_blocks, l0.nleaf, l0.coords, n, h.n0, true, s);
+        PhaseScope ps(h, s, PH_OTHER, h.total_nodes, L + (L >= 2 ? L - 1 : 0));
         // the injections of levels L..2 that set the covered nodes first, reversed
         for (int k = 2; k <= L; ++k) launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, h.lv[k].view(), n, s);
         for (int k = 1; k <= L; ++k)
@@ -131,16 +150,18 @@ static void out_T(Handle& h, const double* w, cudaStream_t s) {
         PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 2);
         LevelPtrs lp{};
         for (int k = 0; k <= L; ++k) lp.p[k] = h.wl + h.xoff[k];
-        launch_scatter_leaves_to(h, w, lp, 0, s);
+        launch_scatter_leaves_to(h, w, lp, 0, false, s);
         cudaMemcpyAsync(h.gvec, h.wl, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(h.gvec, 0, sizeof(double) * h.xoff[1], s);
         cudaMemsetAsync(h.adj[0].Ub, 0, box_bytes(h, 0, 1), s);
         launch_interior_add(h.adj[0].Ub, 1, h.wl, l0.leaf_blocks, l0.nleaf, n, 1.0, s);
     }
-    conv_T(h, h.adj[0].Ub, s);
-    PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 2);
-    launch_dense_to_blocks(h.gvec, h.dense, l0.cov_blocks, l0.ncov, l0.coords, n, h.n0, false, s);
-    launch_dense_to_blocks(h.fsb, h.dense, l0.leaf_blocks, l0.nleaf, l0.coords, n, h.n0, false, s);
+    for (const Problem& p : h.pr) {
+        conv_T(h, p, h.adj[0].Ub, s);
+        PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 2);
+        dense_to(h, p, h.gvec, true, false, s);
+        dense_to(h, p, h.fsb, false, false, s);
+    }
 }
 
 // B^T: f*-bar (leaf blocks, per level) -> f-bar (caller layout).
@@ -162,7 +183,7 @@ static void rhs_T(Handle& h, const double* fsb, double* fbar, cudaStream_t s) {
     for (int k = 0; k < L; ++k) launch_inject_T(h.adj[k + 1].Rawb, 2, h.adj[k].Rawb, 2, h.lv[k + 1].view(), n, s);
     LevelPtrs lp{};
     for (int k = 0; k <= L; ++k) lp.p[k] = h.adj[k].Rawb;
-    launch_gather_leaves_from(h, fbar, lp, 2, s);
+    launch_gather_leaves_from(h, fbar, lp, 2, true, s);
 }
 
 // M^T: the transposed correction V-cycle, x-space vector xin -> residual-space rout.
@@ -192,12 +213,13 @@ static void cycle_T(Handle& h, const double* xin, double* rout, cudaStream_t s) 
         launch_prolong_T(h.adj[k - 1].Ub, h.adj[k - 1].Hb, h.adj[k].Ub, h.lv[k].view(), h.lv[k - 1].view(), n, s);
     }
     // level-0 solve: the source adjoint gains the convolution transpose of u_0's adjoint
-    conv_T(h, h.adj[0].Ub, s);
-    {
-        PhaseScope ps(h, s, PH_COARSE, l0.nb * n3(h), 1);
-        launch_dense_to_blocks(h.adj[0].Fb, h.dense, l0.order, l0.nb, l0.coords, n, h.n0, true, s);
-        cudaMemsetAsync(h.adj[0].Ub, 0, box_bytes(h, 0, 1), s);
+    for (const Problem& p : h.pr) {
+        conv_T(h, p, h.adj[0].Ub, s);
+        PhaseScope ps(h, s, PH_COARSE, l0.nb * n3(h), 2);
+        dense_to(h, p, h.adj[0].Fb, true, true, s);
+        dense_to(h, p, h.adj[0].Fb, false, true, s);
     }
+    cudaMemsetAsync(h.adj[0].Ub, 0, box_bytes(h, 0, 1), s);
     // fine-to-coarse half, reversed
     for (int k = 1; k <= L; ++k) {
         Level& c = h.lv[k - 1];
@@ -236,21 +258,33 @@ static void cycle_T(Handle& h, const double* xin, double* rout, cudaStream_t s) 
 
 // The whole gradient.  Returns MRP_OK, MRP_ERR_NOT_CONVERGED (fbar still
 // written) or an error status.
+// Per-problem max |v| over an unknown-space vector into slot 2.
+static void xnorm_launch(Handle& h, const double* v, cudaStream_t s) {
+    cudaMemsetAsync(h.slot(2), 0, sizeof(unsigned long long) * h.nprob(), s);
+    PhaseScope ps(h, s, PH_NORM, h.total_nodes, h.L + 1);
+    for (int k = 0; k <= h.L; ++k)
+        launch_absmax(v + h.xoff[k], h.lv[k].order, h.lv[k].nb, h.n, h.slot(2), h.lv[k].prob, s);
+}
+
+// The whole gradient.  Returns MRP_OK, MRP_ERR_NOT_CONVERGED (fbar still
+// written) or an error status; *rel_out is the worst problem's relative residual.
 int solve_adjoint(Handle& h, const double* w, double* fbar, cudaStream_t s, int* cycles_out, double* rel_out) {
     int rc = adjoint_setup(h);
     if (rc) return rc;
     const size_t len = xlen(h);
+    const int np = h.nprob();
     out_T(h, w, s);
     cudaMemsetAsync(h.lam, 0, sizeof(double) * len, s);
-    cudaMemsetAsync(h.dmax + 2, 0, sizeof(unsigned long long), s);
-    {
-        PhaseScope ps(h, s, PH_NORM, (int64_t)len, 1);
-        launch_lincomb(h.rho, 1.0, h.gvec, 0.0, h.gvec, len, h.dmax + 2, s);
-    }
-    double gmax = 0.0;
-    if ((rc = read_max(h, s, &gmax, 2))) return rc;
-    const double scale = gmax > 0.0 ? gmax : 1.0;
-    double rel = gmax / scale;
+    cudaMemcpyAsync(h.rho, h.gvec, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    xnorm_launch(h, h.rho, s);
+    std::vector<double> gmax(np), r(np);
+    if ((rc = read_max(h, s, gmax.data(), 2))) return rc;
+    auto worst = [&](const std::vector<double>& v) {
+        double m = 0.0;
+        for (int p = 0; p < np; ++p) m = std::max(m, v[p] / (gmax[p] > 0.0 ? gmax[p] : 1.0));
+        return m;
+    };
+    double rel = worst(gmax);
     int cycles = 0;
     while (rel >= h.tol && cycles < h.max_cycles) {
         cycle_T(h, h.rho, h.xb, s);
@@ -260,15 +294,14 @@ int solve_adjoint(Handle& h, const double* w, double* fbar, cudaStream_t s, int*
             launch_lincomb(h.lam, 1.0, h.lam, 1.0, h.xb, len, nullptr, s);
         }
         res_T(h, h.lam, h.xb, nullptr, s);
-        cudaMemsetAsync(h.dmax + 2, 0, sizeof(unsigned long long), s);
         {
             // rho = g - K^T lambda = g + x-bar
             PhaseScope ps(h, s, PH_NORM, (int64_t)len, 1);
-            launch_lincomb(h.rho, 1.0, h.gvec, 1.0, h.xb, len, h.dmax + 2, s);
+            launch_lincomb(h.rho, 1.0, h.gvec, 1.0, h.xb, len, nullptr, s);
         }
-        double r = 0.0;
-        if ((rc = read_max(h, s, &r, 2))) return rc;
-        rel = r / scale;
+        xnorm_launch(h, h.rho, s);
+        if ((rc = read_max(h, s, r.data(), 2))) return rc;
+        rel = worst(r);
         if (!std::isfinite(rel)) { *cycles_out = cycles; *rel_out = rel; return MRP_ERR_NUMERICAL; }
     }
     res_T(h, h.lam, h.xb, h.fsb, s);

@@ -350,26 +350,26 @@ __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __rest
     }
 }
 
-// Forward geometry: sources on level-0 nodes [0, N0), targets [-1, N0].
-static Geo geo_of(const Handle& h) {
+// Forward geometry of problem p: sources on level-0 nodes [0, N0), targets [-1, N0].
+static Geo geo_of(const Handle& h, const Problem& p) {
     Geo g{};
     g.n = h.n;
-    g.nbx = h.nb0[0]; g.nby = h.nb0[1]; g.nbz = h.nb0[2];
-    g.Px = h.ax[0].P; g.Py = h.ax[1].P; g.Pz = h.ax[2].P;
-    g.Kx = h.gK[0]; g.Ky = h.gK[1]; g.Kz = h.gK[2];
+    g.nbx = p.nb0[0]; g.nby = p.nb0[1]; g.nbz = p.nb0[2];
+    g.Px = p.ax[0].P; g.Py = p.ax[1].P; g.Pz = p.ax[2].P;
+    g.Kx = p.gK[0]; g.Ky = p.gK[1]; g.Kz = p.gK[2];
     for (int a = 0; a < 3; ++a) {
-        g.in_lo[a] = 0; g.in_n[a] = h.n0[a];
-        g.out_lo[a] = -1; g.out_n[a] = h.n0[a] + 2;
+        g.in_lo[a] = 0; g.in_n[a] = p.n0[a];
+        g.out_lo[a] = -1; g.out_n[a] = p.n0[a] + 2;
     }
     return g;
 }
 
 template <typename R>
-static void conv_passes(const Handle& h, const Geo& g, typename Cx<R>::T* spec, const R* ghat, const R* src, R* dst,
+static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec, const R* ghat, const R* src, R* dst,
                         cudaStream_t s) {
     using C = typename Cx<R>::T;
     const dim3 blk(FFT_TX, FFT_LY);
-    const FftLine<R> Lx = line_of<R>(h.ax[0]), Ly = line_of<R>(h.ax[1]), Lz = line_of<R>(h.ax[2]);
+    const FftLine<R> Lx = line_of<R>(p.ax[0]), Ly = line_of<R>(p.ax[1]), Lz = line_of<R>(p.ax[2]);
     const size_t smx = sizeof(C) * 2 * FFT_LY * g.Px;
     const size_t smy = sizeof(C) * 2 * FFT_LY * g.Py;
     const size_t smz = sizeof(C) * 2 * FFT_LY * g.Pz;
@@ -381,41 +381,40 @@ static void conv_passes(const Handle& h, const Geo& g, typename Cx<R>::T* spec, 
     k_fft_x_inv<R><<<(g.out_n[1] * g.out_n[2] + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(dst, spec, g, Lx);
 }
 
-template <typename R>
-static void coarse_passes(const Handle& h, typename Cx<R>::T* spec, const R* ghat, const R* F0, R* U0, cudaStream_t s) {
-    conv_passes<R>(h, geo_of(h), spec, ghat, F0, U0, s);
-}
-
-void launch_coarse_solve(Handle& h, cudaStream_t s) {
-    coarse_passes<double>(h, h.spec, h.ghat, h.lv[0].F, h.lv[0].U, s);
-}
-
+// Level-0 solve of every problem of the handle, one after another on s (they
+// share the spectral buffer); problem p's level-0 blocks start at block base0.
 template <typename T>
 void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s) {
-    if constexpr (sizeof(T) == 8) coarse_passes<double>(h, h.spec, h.ghat, F0, U0, s);
-    else coarse_passes<float>(h, h.spec32, h.ghat32, F0, U0, s);
+    const size_t n3 = (size_t)h.n * h.n * h.n, S3 = (size_t)(h.n + 2) * (h.n + 2) * (h.n + 2);
+    for (const Problem& p : h.pr) {
+        if constexpr (sizeof(T) == 8)
+            conv_passes<double>(p, geo_of(h, p), h.spec, p.ghat, F0 + p.base0 * n3, U0 + p.base0 * S3, s);
+        else
+            conv_passes<float>(p, geo_of(h, p), h.spec32, p.ghat32, F0 + p.base0 * n3, U0 + p.base0 * S3, s);
+    }
 }
 template void launch_coarse_solve_t<double>(const Handle&, const double*, double*, cudaStream_t);
 template void launch_coarse_solve_t<float>(const Handle&, const float*, float*, cudaStream_t);
 
-// Same five passes with the spectral buffer, source and output given by the
-// caller (spec must hold Pz * Py * (Px/2+1) complex values).
+// Same five passes for problem 0 with the spectral buffer, source and output
+// given by the caller (spec must hold Pz * Py * (Px/2+1) complex values).
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s) {
-    coarse_passes<double>(h, spec, h.ghat, F0, U0, s);
+    const Problem& p = h.pr[0];
+    conv_passes<double>(p, geo_of(h, p), spec, p.ghat, F0, U0, s);
 }
 
-// Transpose of the level-0 convolution (FP64): dense adjoint on the target
-// cube [-1, N0]^3 -> dense adjoint on the sources [0, N0)^3.  The kernel is
-// even, so this is the convolution with the two ranges exchanged.
-void launch_conv_transpose(const Handle& h, const double* cube_in, double* src_out, cudaStream_t s) {
-    Geo g = geo_of(h);
+// Transpose of problem p's level-0 convolution (FP64): dense adjoint on the
+// target cube [-1, N0]^3 -> dense adjoint on the sources [0, N0)^3.  The
+// kernel is even, so this is the convolution with the two ranges exchanged.
+void launch_conv_transpose(const Handle& h, const Problem& p, const double* cube_in, double* src_out, cudaStream_t s) {
+    Geo g = geo_of(h, p);
     for (int a = 0; a < 3; ++a) {
-        g.in_lo[a] = -1; g.in_n[a] = h.n0[a] + 2;
-        g.out_lo[a] = 0; g.out_n[a] = h.n0[a];
+        g.in_lo[a] = -1; g.in_n[a] = p.n0[a] + 2;
+        g.out_lo[a] = 0; g.out_n[a] = p.n0[a];
     }
     g.dense_in = 1;
     g.dense_out = 1;
-    conv_passes<double>(h, g, h.spec, h.ghat, cube_in, src_out, s);
+    conv_passes<double>(p, g, h.spec, p.ghat, cube_in, src_out, s);
 }
 
 // ============================================================================
@@ -562,10 +561,44 @@ static void composite(int q, double a, double b, int panels, std::vector<double>
 
 #define CK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { goto fail; } } while (0)
 
+// Spectrum of problem p's padded kernel, scaled by h0^2 / (Px Py Pz) with the handle's h0.
+static int ghat_build(const Handle& h, Problem& p, cudaStream_t s) {
+    const double pi = 3.14159265358979323846;
+    const int nn = h.lgf_nmax + 1;
+    const int Kx = p.gK[0], Ky = p.gK[1], Kz = p.gK[2];
+    const int Dz = p.ax[2].P / 2 + 1, Dy = p.ax[1].P / 2 + 1;
+    double *dc[3] = {nullptr, nullptr, nullptr}, *T1 = nullptr, *T2 = nullptr;
+    int rc = MRP_ERR_CUDA;
+    double scale;
+    for (int a = 0; a < 3; ++a) {
+        const int P = p.ax[a].P;
+        std::vector<double> c(P);
+        for (int m = 0; m < P; ++m) c[m] = std::cos(2.0 * pi * (double)m / (double)P);
+        CK(cudaMalloc(&dc[a], sizeof(double) * P));
+        CK(cudaMemcpyAsync(dc[a], c.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaMalloc(&T1, sizeof(double) * (size_t)Dz * Dy * Kx));
+    CK(cudaMalloc(&T2, sizeof(double) * (size_t)Dz * Ky * Kx));
+    CK(cudaMalloc(&p.ghat, sizeof(double) * (size_t)Kz * Ky * Kx));
+    k_ghat_x<<<(unsigned)(((size_t)Dz * Dy * Kx + 255) / 256), 256, 0, s>>>(T1, h.lgf, nn, dc[0], p.ax[0].P, Dz, Dy, Kx);
+    k_ghat_y<<<(unsigned)(((size_t)Dz * Ky * Kx + 255) / 256), 256, 0, s>>>(T2, T1, dc[1], p.ax[1].P, Dz, Dy, Ky, Kx);
+    scale = h.h0 * h.h0 / ((double)p.ax[0].P * p.ax[1].P * p.ax[2].P);
+    k_ghat_z<<<(unsigned)(((size_t)Kz * Ky * Kx + 255) / 256), 256, 0, s>>>(p.ghat, T2, dc[2], p.ax[2].P, Kz, Ky, Kx, scale);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    rc = MRP_OK;
+fail:
+    cudaFree(T1); cudaFree(T2);
+    for (int a = 0; a < 3; ++a) cudaFree(dc[a]);
+    return rc;
+}
+
 int lgf_build(Handle& h, cudaStream_t s) {
     const double pi = 3.14159265358979323846;
     int nmax = 0;
-    for (int a = 0; a < 3; ++a) nmax = std::max(nmax, h.ax[a].P / 2);
+    for (const Problem& p : h.pr)
+        for (int a = 0; a < 3; ++a) nmax = std::max(nmax, p.ax[a].P / 2);
     const int nn = nmax + 1;
     // quadrature: 32-point rules on 8 + nmax/16 panels in u and 4 + nmax/32 panels in v
     std::vector<double> u, wu, v, wv;
@@ -592,12 +625,8 @@ int lgf_build(Handle& h, cudaStream_t s) {
     for (int n1 = 0; n1 < nn; ++n1)
         for (int i = 0; i < Qu; ++i) C1[(size_t)n1 * Qu + i] = std::cos(n1 * u[i]);
     double *du = nullptr, *dv = nullptr, *dW = nullptr, *drho = nullptr, *dC1 = nullptr, *dB = nullptr, *dA = nullptr;
-    double *dc[3] = {nullptr, nullptr, nullptr}, *T1 = nullptr, *T2 = nullptr;
     int rc = MRP_ERR_CUDA;
-    const int Kx = h.gK[0], Ky = h.gK[1], Kz = h.gK[2];
-    const int Dz = h.ax[2].P / 2 + 1, Dy = h.ax[1].P / 2 + 1;
     size_t total;
-    double scale;
     h.lgf_nmax = nmax;
     CK(cudaMalloc(&h.lgf, sizeof(double) * nn * nn * nn));
     CK(cudaMalloc(&du, sizeof(double) * Qu));
@@ -618,29 +647,12 @@ int lgf_build(Handle& h, cudaStream_t s) {
     k_lgf_A<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dA, dB, dC1, Qu, nn);
     k_lgf_sym<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h.lgf, dA, nn);
     CK(cudaGetLastError());
-    // spectrum of the padded kernel
-    for (int a = 0; a < 3; ++a) {
-        const int P = h.ax[a].P;
-        std::vector<double> c(P);
-        for (int m = 0; m < P; ++m) c[m] = std::cos(2.0 * pi * (double)m / (double)P);
-        CK(cudaMalloc(&dc[a], sizeof(double) * P));
-        CK(cudaMemcpyAsync(dc[a], c.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-    }
-    CK(cudaMalloc(&T1, sizeof(double) * (size_t)Dz * Dy * Kx));
-    CK(cudaMalloc(&T2, sizeof(double) * (size_t)Dz * Ky * Kx));
-    CK(cudaMalloc(&h.ghat, sizeof(double) * (size_t)Kz * Ky * Kx));
-    k_ghat_x<<<(unsigned)(((size_t)Dz * Dy * Kx + 255) / 256), 256, 0, s>>>(T1, h.lgf, nn, dc[0], h.ax[0].P, Dz, Dy, Kx);
-    k_ghat_y<<<(unsigned)(((size_t)Dz * Ky * Kx + 255) / 256), 256, 0, s>>>(T2, T1, dc[1], h.ax[1].P, Dz, Dy, Ky, Kx);
-    scale = h.h0 * h.h0 / ((double)h.ax[0].P * h.ax[1].P * h.ax[2].P);
-    k_ghat_z<<<(unsigned)(((size_t)Kz * Ky * Kx + 255) / 256), 256, 0, s>>>(h.ghat, T2, dc[2], h.ax[2].P, Kz, Ky, Kx, scale);
-    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     rc = MRP_OK;
+    for (Problem& p : h.pr)
+        if ((rc = ghat_build(h, p, s)) != MRP_OK) break;
 fail:
     cudaFree(du); cudaFree(dv); cudaFree(dW); cudaFree(drho); cudaFree(dC1); cudaFree(dB); cudaFree(dA);
-    cudaFree(T1); cudaFree(T2);
-    for (int a = 0; a < 3; ++a) cudaFree(dc[a]);
     return rc;
 }
 
@@ -667,22 +679,25 @@ static int smooth_length(int need) {
 
 int fft_plan(Handle& h) {
     const double pi = 3.14159265358979323846;
-    for (int a = 0; a < 3; ++a) {
-        FftAxis& ax = h.ax[a];
-        ax.P = smooth_length(2 * h.n0[a] + 1);
-        ax.K = ax.P / 2 + 1;
-        if (!factor(ax.P, ax.rad, ax.nrad)) return MRP_ERR_UNSUPPORTED;
-        std::vector<double2> tw(ax.P);
-        for (int m = 0; m < ax.P; ++m) {
-            const double ang = 2.0 * pi * (double)m / (double)ax.P;
-            tw[m] = make_double2(std::cos(ang), -std::sin(ang));
+    size_t ns = 0;
+    for (Problem& p : h.pr) {
+        for (int a = 0; a < 3; ++a) {
+            FftAxis& ax = p.ax[a];
+            ax.P = smooth_length(2 * p.n0[a] + 1);
+            ax.K = ax.P / 2 + 1;
+            if (!factor(ax.P, ax.rad, ax.nrad)) return MRP_ERR_UNSUPPORTED;
+            std::vector<double2> tw(ax.P);
+            for (int m = 0; m < ax.P; ++m) {
+                const double ang = 2.0 * pi * (double)m / (double)ax.P;
+                tw[m] = make_double2(std::cos(ang), -std::sin(ang));
+            }
+            if (cudaMalloc(&ax.tw, sizeof(double2) * ax.P) != cudaSuccess) return MRP_ERR_OOM;
+            if (cudaMemcpy(ax.tw, tw.data(), sizeof(double2) * ax.P, cudaMemcpyHostToDevice) != cudaSuccess)
+                return MRP_ERR_CUDA;
+            p.gK[a] = ax.K;
         }
-        if (cudaMalloc(&ax.tw, sizeof(double2) * ax.P) != cudaSuccess) return MRP_ERR_OOM;
-        if (cudaMemcpy(ax.tw, tw.data(), sizeof(double2) * ax.P, cudaMemcpyHostToDevice) != cudaSuccess)
-            return MRP_ERR_CUDA;
-        h.gK[a] = ax.K;
+        ns = std::max(ns, (size_t)p.ax[2].P * p.ax[1].P * p.ax[0].K);
     }
-    const size_t ns = (size_t)h.ax[2].P * h.ax[1].P * h.ax[0].K;
     if (cudaMalloc(&h.spec, sizeof(double2) * ns) != cudaSuccess) return MRP_ERR_OOM;
     const int mx = MAX_DYN_SMEM;
     cudaFuncSetAttribute(k_fft_x_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256) k_leafres_fused(double* __restrict__ R, c
         if (R) R[(size_t)b * n3 + t] = r;
         m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
     }
-    bmax_atomic(m, out);
+    bmax_atomic(m, out + (lk.prob ? lk.prob[b] : 0));
 }
 
 // ---------------------------------------------------------------- halo dump (step API)

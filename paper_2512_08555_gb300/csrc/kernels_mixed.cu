@@ -44,35 +44,11 @@ __device__ __forceinline__ void block_max_atomic64(double v, unsigned long long*
     }
 }
 
-// R = F - L U on leaf blocks (FP64), and the max-norm of R.
-template <int M>
-__global__ void k_leaf_residual_store(double* __restrict__ R, const double* __restrict__ U, const double* __restrict__ F,
-                                      const int* __restrict__ blocks, int n, double scale, unsigned long long* out) {
-    const int b = blocks[blockIdx.x];
-    const int S = n + 2, S2 = S * S, n3 = n * n * n;
-    const double* Ub = U + (size_t)b * S2 * S;
-    double m = 0.0;
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const double r = F[(size_t)b * n3 + t] - scale * lhs64<M>(Ub, ((z + 1) * S + y + 1) * S + x + 1, S, S2);
-        R[(size_t)b * n3 + t] = r;
-        m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
-    }
-    block_max_atomic64(m, out);
-}
-
-void launch_leaf_residual_store(double* R, const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
-                                double inv_h2, unsigned long long* out, cudaStream_t s) {
-    if (nleaf == 0) return;
-    if (M == 2) k_leaf_residual_store<2><<<nleaf, 256, 0, s>>>(R, U, F, leaf_blocks, n, inv_h2 / LhsW64<2>::den, out);
-    if (M == 4) k_leaf_residual_store<4><<<nleaf, 256, 0, s>>>(R, U, F, leaf_blocks, n, inv_h2 / LhsW64<4>::den, out);
-    if (M == 6) k_leaf_residual_store<6><<<nleaf, 256, 0, s>>>(R, U, F, leaf_blocks, n, inv_h2 / LhsW64<6>::den, out);
-}
-
-// c0 = u0(X) - u1(2X) on covered level-0 blocks; off32 = -c0 (FP32); max |c0| / h0^2.
+// c0 = u0(X) - u1(2X) on covered level-0 blocks; off32 = -c0 (FP32); max |c0| / h0^2
+// into out[prob[P]] (out[0] without a problem table).
 __global__ void k_c0(double* __restrict__ c0, float* __restrict__ off32, const double* __restrict__ U0,
                      const double* __restrict__ U1, const int* __restrict__ cov0, const int* __restrict__ children0, int n,
-                     double inv_h2, unsigned long long* out) {
+                     double inv_h2, unsigned long long* out, const int* __restrict__ prob) {
     const int P = cov0[blockIdx.x];
     const int S = n + 2, S3 = S * S * S, n3 = n * n * n, h = n >> 1;
     double m = 0.0;
@@ -88,13 +64,13 @@ __global__ void k_c0(double* __restrict__ c0, float* __restrict__ off32, const d
         const double a = fabs(v) * inv_h2;
         m = (v != v) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, a);
     }
-    block_max_atomic64(m, out);
+    block_max_atomic64(m, out + (prob ? prob[P] : 0));
 }
 
 void launch_c0(double* c0, float* off32, const double* U0, const double* U1, const int* cov0, int ncov0, const int* children0,
-               int n, double inv_h2, unsigned long long* out, cudaStream_t s) {
+               int n, double inv_h2, unsigned long long* out, const int* prob, cudaStream_t s) {
     if (ncov0 == 0) return;
-    k_c0<<<ncov0, 256, 0, s>>>(c0, off32, U0, U1, cov0, children0, n, inv_h2, out);
+    k_c0<<<ncov0, 256, 0, s>>>(c0, off32, U0, U1, cov0, children0, n, inv_h2, out, prob);
 }
 
 // FP32 right-hand side of the correction cycles: the FP64 leaf residual (or 0).

@@ -161,51 +161,57 @@ void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk,
 }
 
 // ----------------------------------------------------------------------------
-// Leaf scatter / gather between the caller's [leaf][n^3] layout and the
-// per-level halo layout.
-
+// Leaf scatter / gather between the caller's layout (leaf i at element
+// offset src[i], n^3 values, x fastest) and the per-level halo layout
+// (halo g); values are multiplied by scale[i] when a scale table is given.
 __global__ void k_scatter_leaves(const double* __restrict__ f, const int* __restrict__ leaf_level,
-                                 const int* __restrict__ leaf_block, LevelPtrs dst, int n, int g) {
+                                 const int* __restrict__ leaf_block, const int64_t* __restrict__ src_off,
+                                 const double* __restrict__ scale, LevelPtrs dst, int n, int g) {
     const int i = blockIdx.x;
     const int S = n + 2 * g;
     double* d = dst.p[leaf_level[i]] + (size_t)leaf_block[i] * S * S * S;
-    const double* src = f + (size_t)i * n * n * n;
+    const double* src = f + src_off[i];
+    const double a = scale ? scale[i] : 1.0;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        d[((z + g) * S + y + g) * S + x + g] = src[t];
+        d[((z + g) * S + y + g) * S + x + g] = a * src[t];
     }
 }
 
 __global__ void k_gather_leaves(double* __restrict__ u, const int* __restrict__ leaf_level,
-                                const int* __restrict__ leaf_block, LevelPtrs src, int n, int g) {
+                                const int* __restrict__ leaf_block, const int64_t* __restrict__ dst_off,
+                                const double* __restrict__ scale, LevelPtrs src, int n, int g) {
     const int i = blockIdx.x;
     const int S = n + 2 * g;
     const double* s = src.p[leaf_level[i]] + (size_t)leaf_block[i] * S * S * S;
-    double* d = u + (size_t)i * n * n * n;
+    double* d = u + dst_off[i];
+    const double a = scale ? scale[i] : 1.0;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        d[t] = s[((z + g) * S + y + g) * S + x + g];
+        d[t] = a * s[((z + g) * S + y + g) * S + x + g];
     }
 }
 
 void launch_scatter_leaves(Handle& h, const double* f, cudaStream_t s) {
     LevelPtrs lp{};
     for (int k = 0; k <= h.L; ++k) lp.p[k] = h.lv[k].Fraw;
-    k_scatter_leaves<<<h.n_leaves, 256, 0, s>>>(f, h.leaf_level, h.leaf_block, lp, h.n, 2);
+    k_scatter_leaves<<<h.n_leaves, 256, 0, s>>>(f, h.leaf_level, h.leaf_block, h.leaf_src, h.leaf_scale, lp, h.n, 2);
 }
 
 void launch_gather_leaves(Handle& h, double* u, cudaStream_t s) {
     LevelPtrs lp{};
     for (int k = 0; k <= h.L; ++k) lp.p[k] = h.lv[k].U;
-    k_gather_leaves<<<h.n_leaves, 256, 0, s>>>(u, h.leaf_level, h.leaf_block, lp, h.n, 1);
+    k_gather_leaves<<<h.n_leaves, 256, 0, s>>>(u, h.leaf_level, h.leaf_block, h.leaf_src, nullptr, lp, h.n, 1);
 }
 
-void launch_scatter_leaves_to(const Handle& h, const double* f, const LevelPtrs& dst, int g, cudaStream_t s) {
-    k_scatter_leaves<<<h.n_leaves, 256, 0, s>>>(f, h.leaf_level, h.leaf_block, dst, h.n, g);
+void launch_scatter_leaves_to(const Handle& h, const double* f, const LevelPtrs& dst, int g, bool scaled, cudaStream_t s) {
+    k_scatter_leaves<<<h.n_leaves, 256, 0, s>>>(f, h.leaf_level, h.leaf_block, h.leaf_src, scaled ? h.leaf_scale : nullptr,
+                                                dst, h.n, g);
 }
 
-void launch_gather_leaves_from(const Handle& h, double* u, const LevelPtrs& src, int g, cudaStream_t s) {
-    k_gather_leaves<<<h.n_leaves, 256, 0, s>>>(u, h.leaf_level, h.leaf_block, src, h.n, g);
+void launch_gather_leaves_from(const Handle& h, double* u, const LevelPtrs& src, int g, bool scaled, cudaStream_t s) {
+    k_gather_leaves<<<h.n_leaves, 256, 0, s>>>(u, h.leaf_level, h.leaf_block, h.leaf_src, scaled ? h.leaf_scale : nullptr,
+                                               src, h.n, g);
 }
 
 // ----------------------------------------------------------------------------
@@ -476,31 +482,9 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* o
     }
 }
 
-template <int M>
-__global__ void k_leaf_residual_max(const double* __restrict__ U, const double* __restrict__ F, const int* __restrict__ blocks,
-                                    int n, double scale, unsigned long long* out) {
-    const int b = blocks[blockIdx.x];
-    const int S = n + 2, S2 = S * S, n3 = n * n * n;
-    const double* Ub = U + (size_t)b * S2 * S;
-    double m = 0.0;
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 1) * S + y + 1) * S + x + 1;
-        const double r = F[(size_t)b * n3 + t] - scale * lhs_scaled<M>(Ub, o, S, S2);
-        m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
-    }
-    block_max_atomic(m, out);
-}
-
-void launch_leaf_residual_max(const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
-                              double inv_h2, unsigned long long* out, cudaStream_t s) {
-    if (nleaf == 0) return;
-    if (M == 2) k_leaf_residual_max<2><<<nleaf, 256, 0, s>>>(U, F, leaf_blocks, n, inv_h2 / LhsW<2>::den, out);
-    if (M == 4) k_leaf_residual_max<4><<<nleaf, 256, 0, s>>>(U, F, leaf_blocks, n, inv_h2 / LhsW<4>::den, out);
-    if (M == 6) k_leaf_residual_max<6><<<nleaf, 256, 0, s>>>(U, F, leaf_blocks, n, inv_h2 / LhsW<6>::den, out);
-}
-
-__global__ void k_absmax(const double* __restrict__ F, const int* __restrict__ blocks, int n, unsigned long long* out) {
+// max |F| over the listed blocks into out[prob[b]] (out[0] without a problem table).
+__global__ void k_absmax(const double* __restrict__ F, const int* __restrict__ blocks, int n, unsigned long long* out,
+                         const int* __restrict__ prob) {
     const int b = blocks[blockIdx.x];
     const int n3 = n * n * n;
     double m = 0.0;
@@ -508,12 +492,13 @@ __global__ void k_absmax(const double* __restrict__ F, const int* __restrict__ b
         const double v = F[(size_t)b * n3 + t];
         m = (v != v) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(v));
     }
-    block_max_atomic(m, out);
+    block_max_atomic(m, out + (prob ? prob[b] : 0));
 }
 
-void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, cudaStream_t s) {
+void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, const int* prob,
+                   cudaStream_t s) {
     if (nblocks == 0) return;
-    k_absmax<<<nblocks, 256, 0, s>>>(F, blocks, n, out);
+    k_absmax<<<nblocks, 256, 0, s>>>(F, blocks, n, out, prob);
 }
 
 }  // namespace mrp

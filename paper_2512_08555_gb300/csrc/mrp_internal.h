@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <vector>
 #include <string>
+#include <memory>
 
 #include "mrp.h"
 #include "mrp_steps.h"
@@ -28,6 +29,7 @@ struct LevelView {
     const int* children;   // [nb][8] (-1 for leaves)
     const uint8_t* is_leaf;
     const int* order;      // [nb] launch order: blocks with interpolated ghosts first
+    const int* prob;       // [nb] problem of each block (per-problem norms of a batched handle)
 };
 
 // Host + device tables of one level, plus its FP64 fields.
@@ -35,14 +37,15 @@ struct Level {
     int nb = 0, nleaf = 0, ncov = 0;
     std::vector<int> h_coords, h_nbr, h_parent, h_octant, h_children, h_leaf_blocks, h_cov_blocks, h_order;
     std::vector<uint8_t> h_is_leaf;
+    std::vector<int> h_prob;
     int *coords = nullptr, *nbr = nullptr, *parent = nullptr, *octant = nullptr, *children = nullptr;
-    int *leaf_blocks = nullptr, *cov_blocks = nullptr, *order = nullptr;
+    int *leaf_blocks = nullptr, *cov_blocks = nullptr, *order = nullptr, *prob = nullptr;
     uint8_t* is_leaf = nullptr;
     double *U = nullptr, *F = nullptr, *R = nullptr, *H = nullptr, *Fraw = nullptr;
     double* Ualt = nullptr;           // second u buffer: a sweep reads U and writes Ualt, then they swap
     float *U32 = nullptr, *F32 = nullptr, *R32 = nullptr, *H32 = nullptr;   // mixed precision inner cycles
     float* U32alt = nullptr;
-    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order}; }
+    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order, prob}; }
 };
 
 // One padded FFT axis: length, radix sequence, twiddles exp(-2 pi i m / P).
@@ -59,36 +62,59 @@ constexpr int MAX_RADIX_STAGES = 16;
 // (below the 227 KB limit so that their small static arrays still fit).
 constexpr int MAX_DYN_SMEM = 200 * 1024;
 
+// One problem of a handle: a forest, or one component of a forest's vector
+// right-hand side.  Its blocks are contiguous in every level's pool; it has
+// its own level-0 lattice and FFT.  All problems of a handle share the block
+// size n, the order and one reference spacing h0: a problem of spacing h0_p
+// enters with f scaled by (h0_p / h0)^2, which leaves u unchanged since the
+// discrete operator at every level scales as 1/h^2 and the level-0 solve as h^2.
+struct Problem {
+    int forest = 0, comp = 0;
+    int nb0[3] = {0, 0, 0}, n0[3] = {0, 0, 0};   // level-0 blocks and nodes per axis
+    double h0 = 0.0, scale = 1.0;
+    int L = 0;                        // finest level
+    int base0 = 0;                    // first level-0 block
+    int cov0_lo = 0, cov0_hi = 0;     // range in level 0's covered-block list
+    int leaf0_lo = 0, leaf0_hi = 0;   // range in level 0's leaf-block list
+    FftAxis ax[3];
+    int gK[3] = {0, 0, 0};
+    double* ghat = nullptr;           // [Kz][Ky][Kx] real spectrum of G, scaled by h0^2 / (Px Py Pz) (handle's h0)
+    float* ghat32 = nullptr;          // FP32 copy
+};
+
 struct Handle {
-    // forest
-    int nb0[3], n, L;                 // L = max level
-    double origin[3], h0;
-    int n0[3];                        // level-0 nodes per axis
+    // forest: the problems' blocks pooled per level
+    int n, L;                         // block size; finest level over all problems
+    double h0;                        // reference level-0 spacing (problem 0's)
+    std::vector<Problem> pr;
     int M, nu1, nu2, max_cycles, stop_rule;
     double tol;
     std::vector<Level> lv;
-    int n_leaves;
+    int n_leaves;                     // leaves over all problems
     int* leaf_level = nullptr;        // device [n_leaves]
     int* leaf_block = nullptr;        // device [n_leaves]
+    int64_t* leaf_src = nullptr;      // device [n_leaves] element offset of the leaf in the caller's f / u
+    double* leaf_scale = nullptr;     // device [n_leaves] scale of the leaf's problem
     std::vector<int> h_leaf_level, h_leaf_block;
-    // coarse solve
-    FftAxis ax[3];
+    std::vector<int64_t> h_leaf_src;
+    std::vector<double> h_leaf_scale;
+    // coarse solve (spectral buffers sized for the largest lattice; problems run one after another)
     double2* spec = nullptr;          // [Pz][Py][Kx]
-    double* ghat = nullptr;           // [Kz][Ky][Kx] real spectrum, scaled by h0^2 / (Px Py Pz)
-    float* ghat32 = nullptr;          // FP32 copy
     float2* spec32 = nullptr;         // FP32 spectral buffer
     // mixed precision
     bool mixed = false;
     int inner_cycles = 4, max_ir = 12;
     double* c0 = nullptr;             // [nb0 blocks][n^3] injection mismatch on covered level-0 nodes (FP64)
     float* off32 = nullptr;           // [nb0 blocks][n^3] -c0 in FP32 (offset of the level-1 -> 0 injection)
-    int gK[3];
     int lgf_nmax = 0;
     double* lgf = nullptr;            // [(nmax+1)^3]
-    // scratch
-    unsigned long long* dmax = nullptr;   // device scalars for max-norm reductions
+    // max-norm reductions: slot s of problem p at dmax[s * nprob + p] (s < 4)
+    unsigned long long* dmax = nullptr;
     unsigned long long* hmax = nullptr;   // pinned host mirror
+    int nprob() const { return (int)pr.size(); }
+    unsigned long long* slot(int s) const { return dmax + (size_t)s * pr.size(); }
     int64_t leaf_nodes = 0, total_nodes = 0;
+    std::vector<double> fstar;        // max |f*| per problem
     double fstar_max = 0.0;
     bool have_forward = false;
     // launch accounting and optional per-phase event timing
@@ -100,6 +126,10 @@ struct Handle {
     std::vector<Pending> pend;
     double prof_ms[16] = {};
     int64_t prof_cnt[16] = {}, prof_nodes[16] = {};
+    // device-side loop control of the graph-captured solve (graph.cu)
+    int* loop_ctr = nullptr;          // [4]: cycles, refinement steps, status, unused
+    double* loop_rel = nullptr;       // [nprob] relative residuals
+    int64_t gl_pro = 0, gl_body = 0, gl_epi = 0;   // kernels in the graph's prologue, loop body, epilogue
     // gradient of the converged solve (adjoint.cu), allocated at its first call
     struct AdjLevel { double *Ub = nullptr, *Fb = nullptr, *Rb = nullptr, *Hb = nullptr, *Rawb = nullptr; };
     std::vector<AdjLevel> adj;
@@ -111,7 +141,7 @@ struct Handle {
 inline double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
 inline int64_t n3(const Handle& h) { return (int64_t)h.n * h.n * h.n; }
 inline LevelView view_or_empty(const Handle& h, int k) {
-    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 }
 
 // Per-level base pointers, passed by value to the leaf scatter / gather kernels.
@@ -145,19 +175,34 @@ struct PhaseScope {
     }
 };
 void harvest(Handle& h);
-// Copies device scalar h.dmax[slot] (a max-norm) to *out; synchronises s.
+// Copies the per-problem max-norms of slot `slot` to out[0 .. nprob); synchronises s.
 int read_max(Handle& h, cudaStream_t s, double* out, int slot);
 
 // ---------------------------------------------------------------- host side
-int build_forest(Handle& h, const mrp_forest& f, std::string& why);
+// One problem to build: forest, component, and the caller-layout element
+// offset of its first leaf.
+struct ProblemDesc { const mrp_forest* f; int forest, comp; int64_t src_off; };
+int build_forest(Handle& h, const std::vector<ProblemDesc>& list, std::string& why);
 int upload_tables(Handle& h);
 int lgf_build(Handle& h, cudaStream_t s);   // tabulate G and the scaled spectrum
 int fft_plan(Handle& h);
+// pieces of a solve (solver.cu), also captured into the solve graph (graph.cu)
+template <typename T> void vcycle(Handle& h, cudaStream_t s);
+void solve_begin(Handle& h, const double* f, cudaStream_t s);
+void leaf_residual_launch(Handle& h, cudaStream_t s);
+void outer_residual_launch(Handle& h, cudaStream_t s);
+void correction_launch(Handle& h, cudaStream_t s);
+void solve_end(Handle& h, double* u, cudaStream_t s);
 // gradient of the converged solve (adjoint.cu)
 int adjoint_setup(Handle& h);
 void adjoint_release(Handle& h);
 int solve_adjoint(Handle& h, const double* w, double* fbar, cudaStream_t s, int* cycles_out, double* rel_out);
 int adjoint_op(Handle& h, int op, const double* in, double* out, cudaStream_t s);
+}  // namespace mrp
+struct mrp_handle;
+namespace mrp {
+// the solve graph (graph.cu)
+void graph_release(mrp_handle* H);
 
 // ---------------------------------------------------------------- launches (kernels_*.cu)
 // Templated launchers are instantiated for double (FP64 path, outer refinement)
@@ -199,14 +244,12 @@ void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk,
 void launch_scatter_leaves(Handle& h, const double* f, cudaStream_t s);
 void launch_gather_leaves(Handle& h, double* u, cudaStream_t s);
 void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int nleaf, int n, int M, cudaStream_t s);
-void launch_leaf_residual_max(const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
-                              double inv_h2, unsigned long long* out, cudaStream_t s);
-void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, cudaStream_t s);
-void launch_coarse_solve(Handle& h, cudaStream_t s);
+void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, const int* prob,
+                   cudaStream_t s);
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s);
-void launch_conv_transpose(const Handle& h, const double* cube_in, double* src_out, cudaStream_t s);
-void launch_scatter_leaves_to(const Handle& h, const double* f, const LevelPtrs& dst, int g, cudaStream_t s);
-void launch_gather_leaves_from(const Handle& h, double* u, const LevelPtrs& src, int g, cudaStream_t s);
+void launch_conv_transpose(const Handle& h, const Problem& p, const double* cube_in, double* src_out, cudaStream_t s);
+void launch_scatter_leaves_to(const Handle& h, const double* f, const LevelPtrs& dst, int g, bool scaled, cudaStream_t s);
+void launch_gather_leaves_from(const Handle& h, double* u, const LevelPtrs& src, int g, bool scaled, cudaStream_t s);
 // transposed operators (kernels_adjoint.cu)
 void launch_stencil_T(double* out, const double* lam, double* fadd, const int* blocks, int nblocks, int n, int M,
                       double inv_h2, cudaStream_t s);
@@ -228,11 +271,24 @@ void launch_block_zero(double* out, const int* blocks, int nblocks, int n, cudaS
 void launch_lincomb(double* out, double a, const double* x, double b, const double* y, size_t len,
                     unsigned long long* absmax, cudaStream_t s);
 // mixed precision helpers (kernels_mixed.cu)
-void launch_leaf_residual_store(double* R, const double* U, const double* F, const int* leaf_blocks, int nleaf, int n, int M,
-                                double inv_h2, unsigned long long* out, cudaStream_t s);
 void launch_c0(double* c0, float* off32, const double* U0, const double* U1, const int* cov0, int ncov0, const int* children0,
-               int n, double inv_h2, unsigned long long* out, cudaStream_t s);
+               int n, double inv_h2, unsigned long long* out, const int* prob, cudaStream_t s);
 void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int nleaf, int n, bool zero, cudaStream_t s);
 void launch_accumulate_u(double* U64, const float* U32, int nb, int n, cudaStream_t s);
 void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int nblocks, int n, cudaStream_t s);
 }  // namespace mrp
+
+// Opaque handle of the C ABI: one internal handle per block size; the
+// problems of one block size share its pooled levels.
+struct mrp_handle {
+    std::vector<std::unique_ptr<mrp::Handle>> g;
+    std::vector<cudaStream_t> gs;     // one stream per group when there are several
+    std::vector<cudaEvent_t> ev;      // fork event, then one join event per group
+    int64_t elems = 0;                // doubles of f (and u): every forest, component and leaf
+    // the whole solve as one CUDA graph (mrp_solve_graph), built for one (f, u) pair
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;       // capture stream
+    const double* gf = nullptr;
+    double* gu = nullptr;
+};

@@ -38,13 +38,13 @@ static int noalloc_scratch(double2** out) {
 
 }  // namespace mrp
 
-struct mrp_handle { mrp::Handle h; };
-
 extern "C" int mrp_coarse_solve_noalloc(mrp_handle* H, const double* f0, double* u0, void* stream) {
     using namespace mrp;
     if (!H || !f0 || !u0) return MRP_ERR_INVALID_ARG;
-    const Handle& h = H->h;
-    const size_t need = sizeof(double2) * (size_t)h.ax[2].P * h.ax[1].P * h.ax[0].K;
+    if (H->g.size() != 1 || H->g[0]->nprob() != 1) return MRP_ERR_UNSUPPORTED;
+    const Handle& h = *H->g[0];
+    const Problem& p = h.pr[0];
+    const size_t need = sizeof(double2) * (size_t)p.ax[2].P * p.ax[1].P * p.ax[0].K;
     if (need > NOALLOC_SCRATCH_BYTES) return MRP_ERR_TOO_LARGE;
     double2* spec = nullptr;
     const int rc = noalloc_scratch(&spec);

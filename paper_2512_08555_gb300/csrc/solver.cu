@@ -17,14 +17,16 @@ static inline uint64_t key3(int x, int y, int z) {
 }
 
 // ---------------------------------------------------------------- forest
-int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
-    h.n = f.n;
-    for (int a = 0; a < 3; ++a) {
-        h.nb0[a] = f.nb0[a];
-        h.origin[a] = f.origin[a];
+// Host tables of one forest with block indices local to it.
+struct OneForest {
+    int L = 0;
+    std::vector<Level> lv;
+    std::vector<int> leaf_block;      // per leaf (caller order): block index at its level
+};
+
+static int build_one(const mrp_forest& f, OneForest& out, std::string& why) {
+    for (int a = 0; a < 3; ++a)
         if (f.nb0[a] < 1 || f.nb0[a] > 4096) { why = "nb0 out of range"; return MRP_ERR_INVALID_FOREST; }
-    }
-    h.h0 = f.h0;
     if (!(f.h0 > 0.0)) { why = "h0 must be positive"; return MRP_ERR_INVALID_FOREST; }
     if (f.n % 2 != 0 || f.n < 8 || f.n > 24) { why = "block size must be even, 8..24"; return MRP_ERR_INVALID_FOREST; }
     if (f.n_leaves < 1 || !f.leaf_level || !f.leaf_ijk) { why = "no leaves"; return MRP_ERR_INVALID_ARG; }
@@ -38,8 +40,7 @@ int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
             if (c < 0 || c >= (f.nb0[a] << l)) { why = "leaf outside the domain"; return MRP_ERR_INVALID_FOREST; }
         }
     }
-    h.L = L;
-    for (int a = 0; a < 3; ++a) h.n0[a] = f.nb0[a] * f.n;
+    out.L = L;
     // blocks per level: leaves, then parents of finer blocks
     std::vector<std::unordered_map<uint64_t, int>> idx(L + 1);
     std::vector<std::map<std::array<int, 3>, bool>> all(L + 1);   // (z, y, x) -> is_leaf
@@ -57,9 +58,9 @@ int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
             if (it == all[k - 1].end()) all[k - 1][p] = false;
             else if (it->second) { why = "overlapping leaves"; return MRP_ERR_INVALID_FOREST; }
         }
-    h.lv.assign(L + 1, Level());
+    out.lv.assign(L + 1, Level());
     for (int k = 0; k <= L; ++k) {
-        Level& lv = h.lv[k];
+        Level& lv = out.lv[k];
         lv.nb = (int)all[k].size();
         int b = 0;
         for (auto& kv : all[k]) {   // std::map order: z, then y, then x
@@ -69,14 +70,14 @@ int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
             idx[k][key3(x, y, z)] = b++;
         }
     }
-    if (h.lv[0].nb != f.nb0[0] * f.nb0[1] * f.nb0[2]) { why = "leaves do not tile the domain"; return MRP_ERR_INVALID_FOREST; }
+    if (out.lv[0].nb != f.nb0[0] * f.nb0[1] * f.nb0[2]) { why = "leaves do not tile the domain"; return MRP_ERR_INVALID_FOREST; }
     auto find = [&](int k, int x, int y, int z) -> int {
         if (x < 0 || y < 0 || z < 0 || x >= (f.nb0[0] << k) || y >= (f.nb0[1] << k) || z >= (f.nb0[2] << k)) return NBR_OUTSIDE;
         auto it = idx[k].find(key3(x, y, z));
         return it == idx[k].end() ? NBR_MISSING : it->second;
     };
     for (int k = 0; k <= L; ++k) {
-        Level& lv = h.lv[k];
+        Level& lv = out.lv[k];
         lv.h_nbr.resize((size_t)lv.nb * 27);
         lv.h_parent.assign(lv.nb, -1);
         lv.h_octant.assign(lv.nb, 0);
@@ -91,8 +92,7 @@ int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
                 lv.h_parent[b] = find(k - 1, x >> 1, y >> 1, z >> 1);
                 lv.h_octant[b] = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
             }
-            if (lv.h_is_leaf[b]) { lv.h_leaf_blocks.push_back(b); continue; }
-            lv.h_cov_blocks.push_back(b);
+            if (lv.h_is_leaf[b]) continue;
             for (int o = 0; o < 8; ++o) {
                 const int c = k < L ? find(k + 1, 2 * x + (o & 1), 2 * y + ((o >> 1) & 1), 2 * z + ((o >> 2) & 1)) : -1;
                 if (c < 0) { why = "leaves do not tile the domain"; return MRP_ERR_INVALID_FOREST; }
@@ -103,21 +103,11 @@ int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
                 return MRP_ERR_INVALID_FOREST;
             }
         }
-        lv.nleaf = (int)lv.h_leaf_blocks.size();
-        lv.ncov = (int)lv.h_cov_blocks.size();
-        // launch order: blocks that interpolate ghosts (heavier) first
-        auto interp = [&](int b) {
-            for (int d = 0; d < 27; ++d) if (lv.h_nbr[(size_t)27 * b + d] == NBR_MISSING) return true;
-            return false;
-        };
-        for (int pass = 0; pass < 2; ++pass)
-            for (int b = 0; b < lv.nb; ++b) if (interp(b) == (pass == 0)) lv.h_order.push_back(b);
-        std::stable_partition(lv.h_leaf_blocks.begin(), lv.h_leaf_blocks.end(), interp);
     }
     // 2:1 balance across faces, edges and corners: each of the 26 neighbour
     // positions of a level-k block lies in a block of level k-1.
     for (int k = 1; k <= L; ++k) {
-        const Level& lv = h.lv[k];
+        const Level& lv = out.lv[k];
         for (int b = 0; b < lv.nb; ++b) {
             const int x = lv.h_coords[3 * b], y = lv.h_coords[3 * b + 1], z = lv.h_coords[3 * b + 2];
             for (int dz = -1; dz <= 1; ++dz)
@@ -129,18 +119,107 @@ int build_forest(Handle& h, const mrp_forest& f, std::string& why) {
                     }
         }
     }
-    // leaf order of the caller
-    h.n_leaves = f.n_leaves;
-    h.h_leaf_level.resize(f.n_leaves);
-    h.h_leaf_block.resize(f.n_leaves);
-    for (int i = 0; i < f.n_leaves; ++i) {
-        const int l = f.leaf_level[i];
-        h.h_leaf_level[i] = l;
-        h.h_leaf_block[i] = find(l, f.leaf_ijk[3 * i], f.leaf_ijk[3 * i + 1], f.leaf_ijk[3 * i + 2]);
+    out.leaf_block.resize(f.n_leaves);
+    for (int i = 0; i < f.n_leaves; ++i)
+        out.leaf_block[i] = find(f.leaf_level[i], f.leaf_ijk[3 * i], f.leaf_ijk[3 * i + 1], f.leaf_ijk[3 * i + 2]);
+    return MRP_OK;
+}
+
+// Pools the problems' blocks per level (problem after problem), with the
+// neighbour, parent and child tables re-indexed into the pools.
+int build_forest(Handle& h, const std::vector<ProblemDesc>& list, std::string& why) {
+    if (list.empty()) { why = "no problems"; return MRP_ERR_INVALID_ARG; }
+    h.n = list[0].f->n;
+    h.h0 = list[0].f->h0;
+    std::vector<OneForest> one(list.size());
+    int L = 0;
+    for (size_t p = 0; p < list.size(); ++p) {
+        if (list[p].f->n != h.n) { why = "problems of one handle share the block size"; return MRP_ERR_INVALID_ARG; }
+        const int rc = build_one(*list[p].f, one[p], why);
+        if (rc) return rc;
+        L = std::max(L, one[p].L);
     }
-    h.leaf_nodes = (int64_t)f.n_leaves * f.n * f.n * f.n;
+    h.L = L;
+    h.lv.assign(L + 1, Level());
+    h.pr.assign(list.size(), Problem());
+    std::vector<std::vector<int>> base(list.size(), std::vector<int>(L + 2, 0));
+    for (int k = 0; k <= L; ++k) {
+        int b = 0;
+        for (size_t p = 0; p < list.size(); ++p) {
+            base[p][k] = b;
+            if (k <= one[p].L) b += one[p].lv[k].nb;
+        }
+        h.lv[k].nb = b;
+    }
+    for (size_t p = 0; p < list.size(); ++p) {
+        const mrp_forest& f = *list[p].f;
+        Problem& pr = h.pr[p];
+        pr.forest = list[p].forest;
+        pr.comp = list[p].comp;
+        pr.h0 = f.h0;
+        pr.scale = (f.h0 / h.h0) * (f.h0 / h.h0);
+        pr.L = one[p].L;
+        pr.base0 = base[p][0];
+        for (int a = 0; a < 3; ++a) { pr.nb0[a] = f.nb0[a]; pr.n0[a] = f.nb0[a] * f.n; }
+        for (int k = 0; k <= one[p].L; ++k) {
+            const Level& s = one[p].lv[k];
+            Level& d = h.lv[k];
+            const int off = base[p][k];
+            const int offc = k > 0 ? base[p][k - 1] : 0, offf = base[p][k + 1];
+            d.h_coords.insert(d.h_coords.end(), s.h_coords.begin(), s.h_coords.end());
+            d.h_is_leaf.insert(d.h_is_leaf.end(), s.h_is_leaf.begin(), s.h_is_leaf.end());
+            d.h_octant.insert(d.h_octant.end(), s.h_octant.begin(), s.h_octant.end());
+            for (int v : s.h_nbr) d.h_nbr.push_back(v >= 0 ? v + off : v);
+            for (int v : s.h_parent) d.h_parent.push_back(v >= 0 ? v + offc : v);
+            for (int v : s.h_children) d.h_children.push_back(v >= 0 ? v + offf : v);
+            for (int b = 0; b < s.nb; ++b) d.h_prob.push_back((int)p);
+        }
+    }
+    for (int k = 0; k <= L; ++k) {
+        Level& lv = h.lv[k];
+        for (int b = 0; b < lv.nb; ++b) (lv.h_is_leaf[b] ? lv.h_leaf_blocks : lv.h_cov_blocks).push_back(b);
+        lv.nleaf = (int)lv.h_leaf_blocks.size();
+        lv.ncov = (int)lv.h_cov_blocks.size();
+        // launch order: blocks that interpolate ghosts (heavier) first
+        auto interp = [&](int b) {
+            for (int d = 0; d < 27; ++d) if (lv.h_nbr[(size_t)27 * b + d] == NBR_MISSING) return true;
+            return false;
+        };
+        for (int pass = 0; pass < 2; ++pass)
+            for (int b = 0; b < lv.nb; ++b) if (interp(b) == (pass == 0)) lv.h_order.push_back(b);
+        std::stable_partition(lv.h_leaf_blocks.begin(), lv.h_leaf_blocks.end(), interp);
+    }
+    // level-0 list ranges per problem (level 0 never interpolates, so its lists stay in block order)
+    const Level& l0 = h.lv[0];
+    for (size_t p = 0; p < list.size(); ++p) {
+        Problem& pr = h.pr[p];
+        const int lo = pr.base0, hi = pr.base0 + pr.nb0[0] * pr.nb0[1] * pr.nb0[2];
+        auto range = [&](const std::vector<int>& v, int& a, int& b) {
+            a = (int)(std::lower_bound(v.begin(), v.end(), lo) - v.begin());
+            b = (int)(std::lower_bound(v.begin(), v.end(), hi) - v.begin());
+        };
+        range(l0.h_leaf_blocks, pr.leaf0_lo, pr.leaf0_hi);
+        range(l0.h_cov_blocks, pr.cov0_lo, pr.cov0_hi);
+    }
+    // leaves in the caller's order, with their element offsets and scales
+    h.n_leaves = 0;
+    h.h_leaf_level.clear(); h.h_leaf_block.clear(); h.h_leaf_src.clear(); h.h_leaf_scale.clear();
+    const int64_t n3 = (int64_t)h.n * h.n * h.n;
+    for (size_t p = 0; p < list.size(); ++p) {
+        const mrp_forest& f = *list[p].f;
+        for (int i = 0; i < f.n_leaves; ++i) {
+            const int l = f.leaf_level[i];
+            h.h_leaf_level.push_back(l);
+            h.h_leaf_block.push_back(one[p].leaf_block[i] + base[p][l]);
+            h.h_leaf_src.push_back(list[p].src_off + (int64_t)i * n3);
+            h.h_leaf_scale.push_back(h.pr[p].scale);
+        }
+        h.n_leaves += f.n_leaves;
+    }
+    h.leaf_nodes = (int64_t)h.n_leaves * n3;
     h.total_nodes = 0;
-    for (int k = 0; k <= L; ++k) h.total_nodes += (int64_t)h.lv[k].nb * f.n * f.n * f.n;
+    for (int k = 0; k <= L; ++k) h.total_nodes += (int64_t)h.lv[k].nb * n3;
+    h.fstar.assign(list.size(), 0.0);
     return MRP_OK;
 }
 
@@ -172,6 +251,7 @@ int upload_tables(Handle& h) {
         if ((rc = up(lv.cov_blocks, lv.h_cov_blocks))) return rc;
         if ((rc = up(lv.order, lv.h_order))) return rc;
         if ((rc = up(lv.is_leaf, lv.h_is_leaf))) return rc;
+        if ((rc = up(lv.prob, lv.h_prob))) return rc;
         if ((rc = alloc_field(lv.U, lv.nb * S * S * S))) return rc;
         if ((rc = alloc_field(lv.Ualt, lv.nb * S * S * S))) return rc;
         if ((rc = alloc_field(lv.F, lv.nb * n * n * n))) return rc;
@@ -181,8 +261,11 @@ int upload_tables(Handle& h) {
     }
     if ((rc = up(h.leaf_level, h.h_leaf_level))) return rc;
     if ((rc = up(h.leaf_block, h.h_leaf_block))) return rc;
-    if (cudaMalloc(&h.dmax, sizeof(unsigned long long) * 4) != cudaSuccess) return MRP_ERR_OOM;
-    if (cudaMallocHost(&h.hmax, sizeof(unsigned long long) * 4) != cudaSuccess) return MRP_ERR_OOM;
+    if ((rc = up(h.leaf_src, h.h_leaf_src))) return rc;
+    if ((rc = up(h.leaf_scale, h.h_leaf_scale))) return rc;
+    const size_t nslot = 4 * h.pr.size();
+    if (cudaMalloc(&h.dmax, sizeof(unsigned long long) * nslot) != cudaSuccess) return MRP_ERR_OOM;
+    if (cudaMallocHost(&h.hmax, sizeof(unsigned long long) * nslot) != cudaSuccess) return MRP_ERR_OOM;
     return MRP_OK;
 }
 
@@ -190,17 +273,20 @@ static void release(Handle& h) {
     adjoint_release(h);
     for (Level& lv : h.lv) {
         cudaFree(lv.coords); cudaFree(lv.nbr); cudaFree(lv.parent); cudaFree(lv.octant); cudaFree(lv.children);
-        cudaFree(lv.leaf_blocks); cudaFree(lv.cov_blocks); cudaFree(lv.is_leaf); cudaFree(lv.order);
+        cudaFree(lv.leaf_blocks); cudaFree(lv.cov_blocks); cudaFree(lv.is_leaf); cudaFree(lv.order); cudaFree(lv.prob);
         cudaFree(lv.U); cudaFree(lv.F); cudaFree(lv.R); cudaFree(lv.H); cudaFree(lv.Fraw);
         cudaFree(lv.U32); cudaFree(lv.F32); cudaFree(lv.R32); cudaFree(lv.H32);
         cudaFree(lv.Ualt); cudaFree(lv.U32alt);
     }
     h.lv.clear();
-    for (int a = 0; a < 3; ++a) cudaFree(h.ax[a].tw32);
-    cudaFree(h.spec32); cudaFree(h.ghat32); cudaFree(h.c0); cudaFree(h.off32);
-    cudaFree(h.leaf_level); cudaFree(h.leaf_block);
-    for (int a = 0; a < 3; ++a) cudaFree(h.ax[a].tw);
-    cudaFree(h.spec); cudaFree(h.ghat); cudaFree(h.lgf); cudaFree(h.dmax);
+    for (Problem& p : h.pr) {
+        for (int a = 0; a < 3; ++a) { cudaFree(p.ax[a].tw); cudaFree(p.ax[a].tw32); }
+        cudaFree(p.ghat); cudaFree(p.ghat32);
+    }
+    h.pr.clear();
+    cudaFree(h.spec32); cudaFree(h.c0); cudaFree(h.off32);
+    cudaFree(h.leaf_level); cudaFree(h.leaf_block); cudaFree(h.leaf_src); cudaFree(h.leaf_scale);
+    cudaFree(h.spec); cudaFree(h.lgf); cudaFree(h.dmax);
     if (h.hmax) cudaFreeHost(h.hmax);
     h.hmax = nullptr;
     for (cudaEvent_t e : h.ev) cudaEventDestroy(e);
@@ -230,23 +316,28 @@ static int mixed_setup(Handle& h) {
     if (cudaMalloc(&h.off32, sizeof(float) * nb0 * n * n * n) != cudaSuccess) return MRP_ERR_OOM;
     cudaMemset(h.c0, 0, sizeof(double) * nb0 * n * n * n);
     cudaMemset(h.off32, 0, sizeof(float) * nb0 * n * n * n);
-    for (int a = 0; a < 3; ++a) {
-        const int P = h.ax[a].P;
-        std::vector<double2> tw(P);
-        std::vector<float2> tw32(P);
-        if (cudaMemcpy(tw.data(), h.ax[a].tw, sizeof(double2) * P, cudaMemcpyDeviceToHost) != cudaSuccess) return MRP_ERR_CUDA;
-        for (int m = 0; m < P; ++m) tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
-        if (cudaMalloc(&h.ax[a].tw32, sizeof(float2) * P) != cudaSuccess) return MRP_ERR_OOM;
-        if (cudaMemcpy(h.ax[a].tw32, tw32.data(), sizeof(float2) * P, cudaMemcpyHostToDevice) != cudaSuccess) return MRP_ERR_CUDA;
+    size_t ns = 0;
+    for (Problem& p : h.pr) {
+        for (int a = 0; a < 3; ++a) {
+            const int P = p.ax[a].P;
+            std::vector<double2> tw(P);
+            std::vector<float2> tw32(P);
+            if (cudaMemcpy(tw.data(), p.ax[a].tw, sizeof(double2) * P, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return MRP_ERR_CUDA;
+            for (int m = 0; m < P; ++m) tw32[m] = make_float2((float)tw[m].x, (float)tw[m].y);
+            if (cudaMalloc(&p.ax[a].tw32, sizeof(float2) * P) != cudaSuccess) return MRP_ERR_OOM;
+            if (cudaMemcpy(p.ax[a].tw32, tw32.data(), sizeof(float2) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+                return MRP_ERR_CUDA;
+        }
+        const size_t ng = (size_t)p.gK[0] * p.gK[1] * p.gK[2];
+        std::vector<double> g(ng);
+        std::vector<float> g32(ng);
+        if (cudaMemcpy(g.data(), p.ghat, sizeof(double) * ng, cudaMemcpyDeviceToHost) != cudaSuccess) return MRP_ERR_CUDA;
+        for (size_t i = 0; i < ng; ++i) g32[i] = (float)g[i];
+        if (cudaMalloc(&p.ghat32, sizeof(float) * ng) != cudaSuccess) return MRP_ERR_OOM;
+        if (cudaMemcpy(p.ghat32, g32.data(), sizeof(float) * ng, cudaMemcpyHostToDevice) != cudaSuccess) return MRP_ERR_CUDA;
+        ns = std::max(ns, (size_t)p.ax[2].P * p.ax[1].P * p.ax[0].K);
     }
-    const size_t ng = (size_t)h.gK[0] * h.gK[1] * h.gK[2];
-    std::vector<double> g(ng);
-    std::vector<float> g32(ng);
-    if (cudaMemcpy(g.data(), h.ghat, sizeof(double) * ng, cudaMemcpyDeviceToHost) != cudaSuccess) return MRP_ERR_CUDA;
-    for (size_t i = 0; i < ng; ++i) g32[i] = (float)g[i];
-    if (cudaMalloc(&h.ghat32, sizeof(float) * ng) != cudaSuccess) return MRP_ERR_OOM;
-    if (cudaMemcpy(h.ghat32, g32.data(), sizeof(float) * ng, cudaMemcpyHostToDevice) != cudaSuccess) return MRP_ERR_CUDA;
-    const size_t ns = (size_t)h.ax[2].P * h.ax[1].P * h.ax[0].K;
     if (cudaMalloc(&h.spec32, sizeof(float2) * ns) != cudaSuccess) return MRP_ERR_OOM;
     return MRP_OK;
 }
@@ -345,7 +436,9 @@ static void restrict_level(Handle& h, int k, cudaStream_t s) {
 
 template <typename T>
 static void coarse_solve(Handle& h, cudaStream_t s) {
-    PhaseScope ps(h, s, ph<T>(PH_COARSE), (int64_t)h.n0[0] * h.n0[1] * h.n0[2], 5);
+    int64_t nodes = 0;
+    for (const Problem& p : h.pr) nodes += (int64_t)p.n0[0] * p.n0[1] * p.n0[2];
+    PhaseScope ps(h, s, ph<T>(PH_COARSE), nodes, 5 * h.nprob());
     launch_coarse_solve_t<T>(h, fld<T>(h, 0).F, ucur<T>(h, 0), s);
 }
 
@@ -370,7 +463,7 @@ static void prepare_rhs(Handle& h, const double* f, cudaStream_t s) {
 
 // One adaptive V(nu1, nu2) cycle, Alg. 1, in precision T.
 template <typename T>
-static void vcycle(Handle& h, cudaStream_t s) {
+void vcycle(Handle& h, cudaStream_t s) {
     for (int k = h.L; k >= 1; --k) {
         for (int i = 0; i < h.nu1; ++i) smooth<T>(h, k, s);
         residual<T>(h, k, s);
@@ -383,77 +476,159 @@ static void vcycle(Handle& h, cudaStream_t s) {
     }
 }
 
+template void vcycle<double>(Handle&, cudaStream_t);
+template void vcycle<float>(Handle&, cudaStream_t);
+
 static double as_double(unsigned long long b) { double d; std::memcpy(&d, &b, sizeof d); return d; }
 
 int read_max(Handle& h, cudaStream_t s, double* out, int slot) {
-    if (cudaMemcpyAsync(h.hmax + slot, h.dmax + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    const int np = h.nprob();
+    if (cudaMemcpyAsync(h.hmax + (size_t)slot * np, h.slot(slot), sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess)
         return MRP_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
-    *out = as_double(h.hmax[slot]);
+    for (int p = 0; p < np; ++p) out[p] = as_double(h.hmax[(size_t)slot * np + p]);
     harvest(h);
     return MRP_OK;
 }
 
-// Iterative refinement: FP64 outer residual of the composite system, FP32
-// correction V-cycles, FP64 accumulation.  Returns MRP_OK with *rel set.
-static int solve_mixed(Handle& h, cudaStream_t s, double scale, double* rel_out, int* cycles_out, int* ir_out) {
-    const size_t n = h.n, S = n + 2, n3 = n * n * n;
+// ---------------------------------------------------------------- solve, in steps
+// A solve is begin (right-hand side, its norms), then step / check pairs until
+// every problem of the handle meets the stop rule, then end (the leaf
+// values).  Steps only launch work on the stream; checks synchronise it.  A
+// handle with several block sizes runs one such sequence per block size, in
+// lockstep, each on its own stream.
+struct SolveState {
+    std::vector<double> scale, rel;   // per problem: max |f*| (or 1) and the last relative residual
+    int cycles = 0, ir = 0;
+    bool started = false, done = false;
+    int rc = MRP_OK;
+    double worst() const {
+        double w = 0.0;
+        for (double r : rel) w = std::max(w, r);
+        return w;
+    }
+};
+
+void solve_begin(Handle& h, const double* f, cudaStream_t s) {
+    const size_t S = h.n + 2;
+    if (h.mixed) cudaMemsetAsync(h.lv[0].F, 0, sizeof(double) * h.lv[0].nb * n3(h), s);
+    prepare_rhs(h, f, s);
+    cudaMemsetAsync(h.slot(0), 0, sizeof(unsigned long long) * h.nprob(), s);
+    {
+        PhaseScope ps(h, s, PH_NORM, h.leaf_nodes, h.L + 1);
+        for (int k = 0; k <= h.L; ++k)
+            launch_absmax(h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.slot(0), h.lv[k].prob, s);
+    }
+    for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U, 0, sizeof(double) * h.lv[k].nb * S * S * S, s);
+}
+
+static int solve_begin_read(Handle& h, cudaStream_t s, SolveState& st) {
+    const int rc = read_max(h, s, h.fstar.data(), 0);
+    if (rc) return rc;
+    st = SolveState();
+    st.scale.resize(h.nprob());
+    st.rel.assign(h.nprob(), INFINITY);
+    h.fstar_max = 0.0;
+    for (int p = 0; p < h.nprob(); ++p) {
+        st.scale[p] = h.fstar[p] > 0.0 ? h.fstar[p] : 1.0;
+        h.fstar_max = std::max(h.fstar_max, h.fstar[p]);
+    }
+    return MRP_OK;
+}
+
+// FP64 composite residual: max |f* - L u| over the leaves of every level
+// (level 0 with the exterior ring of the last convolution) into slot 1.
+void leaf_residual_launch(Handle& h, cudaStream_t s) {
+    cudaMemsetAsync(h.slot(1), 0, sizeof(unsigned long long) * h.nprob(), s);
+    for (int k = h.L; k >= 1; --k) inject_level<double>(h, k, s);
+    for (int k = h.L; k >= 0; --k) {
+        PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
+        const double hk = level_h(h, k);
+        launch_leafres_fused(nullptr, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
+                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1), s);
+    }
+}
+
+// Mixed precision, iterative refinement: FP64 outer residual of the composite
+// system (leaf rows, and on covered level-0 nodes the mismatch c0 between the
+// convolution of the accumulated FP64 source and the injection of level 1),
+// FP32 correction cycles from zero, FP64 accumulation.
+void outer_residual_launch(Handle& h, cudaStream_t s) {
     Level& l0 = h.lv[0];
     const double inv_h02 = 1.0 / (h.h0 * h.h0);
-    int cycles = 0, ir = 0;
-    double rel = INFINITY;
-    for (;;) {
-        // level-0 field of the accumulated source, in FP64
-        coarse_solve<double>(h, s);
-        cudaMemsetAsync(h.dmax + 1, 0, sizeof(unsigned long long), s);
-        for (int k = h.L; k >= 2; --k) inject_level<double>(h, k, s);
-        if (h.L >= 1) {
-            PhaseScope ps(h, s, PH_NORM, l0.ncov * n3, l0.ncov > 0 ? 1 : 0);
-            launch_c0(h.c0, h.off32, l0.U, h.lv[1].U, l0.cov_blocks, l0.ncov, l0.children, h.n, inv_h02, h.dmax + 1, s);
-        }
-        for (int k = 1; k <= h.L; ++k) {
-            PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3, h.lv[k].nleaf > 0 ? 1 : 0);
-            const double hk = level_h(h, k);
-            launch_leafres_fused(h.lv[k].R, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks,
-                                 h.lv[k].nleaf, h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk),
-                                 h.dmax + 1, s);
-        }
-        double r = 0.0;
-        const int rc = read_max(h, s, &r, 1);
-        if (rc) return rc;
-        rel = r / scale;
-        if (!std::isfinite(rel)) { *rel_out = rel; *cycles_out = cycles; *ir_out = ir; return MRP_ERR_NUMERICAL; }
-        if (rel < h.tol || ir >= h.max_ir || cycles >= h.max_cycles) break;
-        // FP32 correction cycles on the residual
-        {
-            PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, h.L + 1);
-            for (int k = 1; k <= h.L; ++k)
-                launch_cast_rhs(h.lv[k].F32, h.lv[k].R, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, false, s);
-            launch_cast_rhs(l0.F32, nullptr, l0.leaf_blocks, l0.nleaf, h.n, true, s);
-        }
-        for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U32, 0, sizeof(float) * h.lv[k].nb * S * S * S, s);
-        for (int c = 0; c < h.inner_cycles; ++c) {
-            vcycle<float>(h, s);
-            ++cycles;
-        }
-        {
-            PhaseScope ps(h, s, PH_OTHER, h.total_nodes, h.L + 1);
-            for (int k = 1; k <= h.L; ++k) launch_accumulate_u(h.lv[k].U, h.lv[k].U32, h.lv[k].nb, h.n, s);
-            launch_accumulate_f(l0.F, l0.F32, l0.cov_blocks, l0.ncov, h.n, s);
-        }
-        ++ir;
+    coarse_solve<double>(h, s);
+    cudaMemsetAsync(h.slot(1), 0, sizeof(unsigned long long) * h.nprob(), s);
+    for (int k = h.L; k >= 2; --k) inject_level<double>(h, k, s);
+    if (h.L >= 1) {
+        PhaseScope ps(h, s, PH_NORM, l0.ncov * n3(h), l0.ncov > 0 ? 1 : 0);
+        launch_c0(h.c0, h.off32, l0.U, h.lv[1].U, l0.cov_blocks, l0.ncov, l0.children, h.n, inv_h02, h.slot(1), l0.prob, s);
     }
-    *rel_out = rel;
-    *cycles_out = cycles;
-    *ir_out = ir;
+    for (int k = 1; k <= h.L; ++k) {
+        PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
+        const double hk = level_h(h, k);
+        launch_leafres_fused(h.lv[k].R, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
+                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1), s);
+    }
+}
+
+void correction_launch(Handle& h, cudaStream_t s) {
+    const size_t S = h.n + 2;
+    Level& l0 = h.lv[0];
+    {
+        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, h.L + 1);
+        for (int k = 1; k <= h.L; ++k)
+            launch_cast_rhs(h.lv[k].F32, h.lv[k].R, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, false, s);
+        launch_cast_rhs(l0.F32, nullptr, l0.leaf_blocks, l0.nleaf, h.n, true, s);
+    }
+    for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U32, 0, sizeof(float) * h.lv[k].nb * S * S * S, s);
+    for (int c = 0; c < h.inner_cycles; ++c) vcycle<float>(h, s);
+    PhaseScope ps(h, s, PH_OTHER, h.total_nodes, h.L + 1);
+    for (int k = 1; k <= h.L; ++k) launch_accumulate_u(h.lv[k].U, h.lv[k].U32, h.lv[k].nb, h.n, s);
+    launch_accumulate_f(l0.F, l0.F32, l0.cov_blocks, l0.ncov, h.n, s);
+}
+
+static void solve_step(Handle& h, cudaStream_t s, SolveState& st) {
+    if (!h.mixed) {
+        vcycle<double>(h, s);
+        ++st.cycles;
+        leaf_residual_launch(h, s);
+        return;
+    }
+    if (st.started) {
+        correction_launch(h, s);
+        st.cycles += h.inner_cycles;
+        ++st.ir;
+    }
+    st.started = true;
+    outer_residual_launch(h, s);
+}
+
+static int solve_check(Handle& h, cudaStream_t s, SolveState& st) {
+    std::vector<double> r(h.nprob());
+    const int rc = read_max(h, s, r.data(), 1);
+    if (rc) { st.rc = rc; st.done = true; return rc; }
+    bool all = true;
+    for (int p = 0; p < h.nprob(); ++p) {
+        st.rel[p] = r[p] / st.scale[p];
+        if (!std::isfinite(st.rel[p])) { st.rc = MRP_ERR_NUMERICAL; st.done = true; return MRP_OK; }
+        if (!(st.rel[p] < h.tol)) all = false;
+    }
+    if (all) st.done = true;
+    else if (!h.mixed && st.cycles >= h.max_cycles) st.done = true;
+    else if (h.mixed && (st.ir >= h.max_ir || st.cycles >= h.max_cycles)) st.done = true;
     return MRP_OK;
+}
+
+void solve_end(Handle& h, double* u, cudaStream_t s) {
+    PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1);
+    launch_gather_leaves(h, u, s);
 }
 
 }  // namespace mrp
 
 using namespace mrp;
 
-struct mrp_handle { Handle h; };
 
 extern "C" {
 
@@ -474,37 +649,73 @@ const char* mrp_error_string(int status) {
     }
 }
 
+static void destroy_handle(mrp_handle* H) {
+    graph_release(H);
+    for (auto& g : H->g) release(*g);
+    for (cudaStream_t st : H->gs) cudaStreamDestroy(st);
+    for (cudaEvent_t e : H->ev) cudaEventDestroy(e);
+    delete H;
+}
+
 int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, const mrp_options* opt) {
     if (!out) return MRP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!forests || !opt || n_forests < 1) return MRP_ERR_INVALID_ARG;
-    if (n_forests != 1) return MRP_ERR_UNSUPPORTED;
     if (opt->order != 2 && opt->order != 4 && opt->order != 6) return MRP_ERR_INVALID_ARG;
     if (opt->nu1 < 0 || opt->nu2 < 0 || opt->max_cycles < 1 || !(opt->tol >= 0.0)) return MRP_ERR_INVALID_ARG;
     if (opt->stop_rule != MRP_STOP_RESIDUAL && opt->stop_rule != MRP_STOP_CAUCHY) return MRP_ERR_INVALID_ARG;
     if (opt->precision != MRP_FP64 && opt->precision != MRP_MIXED) return MRP_ERR_INVALID_ARG;
     if (opt->inner_cycles < 0 || opt->max_outer < 0) return MRP_ERR_INVALID_ARG;
     if (opt->stop_rule == MRP_STOP_CAUCHY) return MRP_ERR_UNSUPPORTED;
-    if (forests[0].ncomp != 1) return MRP_ERR_UNSUPPORTED;
+    // problems (forest, component) in the caller's layout order, grouped by block size
+    std::map<int, std::vector<ProblemDesc>> by_n;
+    int64_t off = 0;
+    for (int i = 0; i < n_forests; ++i) {
+        const mrp_forest& f = forests[i];
+        if (f.ncomp < 1 || f.n_leaves < 1 || !f.leaf_level || !f.leaf_ijk) return MRP_ERR_INVALID_ARG;
+        if (f.n % 2 != 0 || f.n < 8 || f.n > 24) return MRP_ERR_INVALID_FOREST;
+        for (int c = 0; c < f.ncomp; ++c) {
+            by_n[f.n].push_back(ProblemDesc{&f, i, c, off});
+            off += (int64_t)f.n_leaves * f.n * f.n * f.n;
+        }
+    }
     mrp_handle* H = new (std::nothrow) mrp_handle();
     if (!H) return MRP_ERR_OOM;
-    Handle& h = H->h;
-    h.M = opt->order; h.nu1 = opt->nu1; h.nu2 = opt->nu2; h.max_cycles = opt->max_cycles;
-    h.tol = opt->tol; h.stop_rule = opt->stop_rule;
-    h.mixed = opt->precision == MRP_MIXED;
-    h.inner_cycles = opt->inner_cycles > 0 ? opt->inner_cycles : 4;
-    h.max_ir = opt->max_outer > 0 ? opt->max_outer : 12;
-    std::string why;
-    int rc = build_forest(h, forests[0], why);
-    if (rc == MRP_OK) rc = upload_tables(h);
-    if (rc == MRP_OK) rc = fft_plan(h);
-    if (rc == MRP_OK) rc = lgf_build(h, 0);
-    if (rc == MRP_OK && h.mixed) rc = mixed_setup(h);
+    H->elems = off;
+    int rc = MRP_OK;
+    for (auto& kv : by_n) {
+        H->g.emplace_back(new (std::nothrow) Handle());
+        if (!H->g.back()) { rc = MRP_ERR_OOM; break; }
+        Handle& h = *H->g.back();
+        h.M = opt->order; h.nu1 = opt->nu1; h.nu2 = opt->nu2; h.max_cycles = opt->max_cycles;
+        h.tol = opt->tol; h.stop_rule = opt->stop_rule;
+        h.mixed = opt->precision == MRP_MIXED;
+        h.inner_cycles = opt->inner_cycles > 0 ? opt->inner_cycles : 4;
+        h.max_ir = opt->max_outer > 0 ? opt->max_outer : 12;
+        std::string why;
+        rc = build_forest(h, kv.second, why);
+        if (rc == MRP_OK) rc = upload_tables(h);
+        if (rc == MRP_OK) rc = fft_plan(h);
+        if (rc == MRP_OK) rc = lgf_build(h, 0);
+        if (rc == MRP_OK && h.mixed) rc = mixed_setup(h);
+        if (rc != MRP_OK) break;
+    }
+    if (rc == MRP_OK && H->g.size() > 1) {
+        for (size_t i = 0; i < H->g.size() && rc == MRP_OK; ++i) {
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = MRP_ERR_CUDA;
+            else H->gs.push_back(st);
+        }
+        for (size_t i = 0; i < 1 + H->g.size() && rc == MRP_OK; ++i) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = MRP_ERR_CUDA;
+            else H->ev.push_back(e);
+        }
+    }
     if (rc == MRP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = MRP_ERR_CUDA;
     if (rc != MRP_OK) {
         cudaGetLastError();
-        release(h);
-        delete H;
+        destroy_handle(H);
         return rc;
     }
     *out = H;
@@ -513,120 +724,120 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
 
 int mrp_destroy(mrp_handle* H) {
     if (!H) return MRP_OK;
-    release(H->h);
-    delete H;
+    destroy_handle(H);
     return MRP_OK;
 }
 
+// Streams of the groups: the caller's stream alone for one group; otherwise
+// one stream per group, forked from and joined back into the caller's stream.
+static std::vector<cudaStream_t> fork_streams(mrp_handle* H, cudaStream_t s) {
+    if (H->g.size() == 1) return {s};
+    cudaEventRecord(H->ev[0], s);
+    for (cudaStream_t gs : H->gs) cudaStreamWaitEvent(gs, H->ev[0], 0);
+    return H->gs;
+}
 
-static double leaf_residual(Handle& h, cudaStream_t s, int* rc) {
-    cudaMemsetAsync(h.dmax + 1, 0, sizeof(unsigned long long), s);
-    for (int k = h.L; k >= 1; --k) inject_level<double>(h, k, s);
-    for (int k = h.L; k >= 0; --k) {
-        PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
-        const double hk = level_h(h, k);
-        launch_leafres_fused(nullptr, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
-                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.dmax + 1, s);
+static void join_streams(mrp_handle* H, cudaStream_t s) {
+    if (H->g.size() == 1) return;
+    for (size_t i = 0; i < H->gs.size(); ++i) {
+        cudaEventRecord(H->ev[1 + i], H->gs[i]);
+        cudaStreamWaitEvent(s, H->ev[1 + i], 0);
     }
-    double r = 0.0;
-    *rc = read_max(h, s, &r, 1);
-    return r;
 }
 
 int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats* st) {
     if (!H || !f || !u) return MRP_ERR_INVALID_ARG;
-    Handle& h = H->h;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t S = h.n + 2;
+    const size_t G = H->g.size();
+    std::vector<int64_t> launches0(G);
+    for (size_t i = 0; i < G; ++i) launches0[i] = H->g[i]->launches;
+    const std::vector<cudaStream_t> gs = fork_streams(H, s);
+    for (size_t i = 0; i < G; ++i) solve_begin(*H->g[i], f, gs[i]);
+    std::vector<SolveState> ss(G);
     int rc = MRP_OK;
-    const int64_t launches0 = h.launches;
-    if (h.mixed) cudaMemsetAsync(h.lv[0].F, 0, sizeof(double) * h.lv[0].nb * h.n * h.n * h.n, s);
-    prepare_rhs(h, f, s);
-    cudaMemsetAsync(h.dmax, 0, sizeof(unsigned long long), s);
-    {
-        PhaseScope ps(h, s, PH_NORM, h.leaf_nodes, h.L + 1);
-        for (int k = 0; k <= h.L; ++k) launch_absmax(h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.dmax, s);
+    for (size_t i = 0; i < G && rc == MRP_OK; ++i) rc = solve_begin_read(*H->g[i], gs[i], ss[i]);
+    if (rc) return rc;
+    for (;;) {
+        bool any = false;
+        for (size_t i = 0; i < G; ++i)
+            if (!ss[i].done) { solve_step(*H->g[i], gs[i], ss[i]); any = true; }
+        if (!any) break;
+        for (size_t i = 0; i < G; ++i)
+            if (!ss[i].done && solve_check(*H->g[i], gs[i], ss[i]) == MRP_ERR_CUDA) return MRP_ERR_CUDA;
     }
-    if ((rc = read_max(h, s, &h.fstar_max, 0))) return rc;
-    for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U, 0, sizeof(double) * h.lv[k].nb * S * S * S, s);
-    const double scale = h.fstar_max > 0.0 ? h.fstar_max : 1.0;
-    double rel = INFINITY;
-    int cycles = 0, ir = 0;
-    if (!h.mixed) {
-        for (; cycles < h.max_cycles;) {
-            vcycle<double>(h, s);
-            ++cycles;
-            const double r = leaf_residual(h, s, &rc);
-            if (rc) return rc;
-            rel = r / scale;
-            if (!std::isfinite(rel)) { rc = MRP_ERR_NUMERICAL; break; }
-            if (rel < h.tol) break;
-        }
-    } else {
-        rc = solve_mixed(h, s, scale, &rel, &cycles, &ir);
-        if (rc == MRP_ERR_CUDA) return rc;
-    }
-    {
-        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1);
-        launch_gather_leaves(h, u, s);
-    }
+    for (size_t i = 0; i < G; ++i) solve_end(*H->g[i], u, gs[i]);
+    join_streams(H, s);
     if (cudaGetLastError() != cudaSuccess) return MRP_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
-    h.have_forward = true;
+    bool converged = true;
+    for (size_t i = 0; i < G; ++i) {
+        H->g[i]->have_forward = true;
+        if (ss[i].rc && !rc) rc = ss[i].rc;
+        if (!(ss[i].worst() < H->g[i]->tol)) converged = false;
+    }
     if (st) {
         std::memset(st, 0, sizeof(*st));
-        st->cycles = cycles;
-        st->ir_steps = ir;
-        st->residual = rel;
-        st->fstar_max = h.fstar_max;
-        st->leaf_nodes = h.leaf_nodes;
-        st->total_nodes = h.total_nodes;
-        st->launches = h.launches - launches0;
+        for (size_t i = 0; i < G; ++i) {
+            const Handle& h = *H->g[i];
+            st->cycles = std::max(st->cycles, ss[i].cycles);
+            st->ir_steps = std::max(st->ir_steps, ss[i].ir);
+            st->residual = std::max(st->residual, ss[i].worst());
+            st->fstar_max = std::max(st->fstar_max, h.fstar_max);
+            st->leaf_nodes += h.leaf_nodes;
+            st->total_nodes += h.total_nodes;
+            st->launches += h.launches - launches0[i];
+        }
     }
     if (rc) return rc;
-    return rel < h.tol ? MRP_OK : MRP_ERR_NOT_CONVERGED;
+    return converged ? MRP_OK : MRP_ERR_NOT_CONVERGED;
 }
 
 int mrp_solve_adjoint(mrp_handle* H, const double* w, double* fbar, void* stream, mrp_stats* st) {
     if (!H || !w || !fbar) return MRP_ERR_INVALID_ARG;
-    Handle& h = H->h;
-    const int64_t launches0 = h.launches;
-    int cycles = 0;
-    double rel = INFINITY;
-    const int rc = solve_adjoint(h, w, fbar, (cudaStream_t)stream, &cycles, &rel);
-    if (st) {
-        std::memset(st, 0, sizeof(*st));
-        st->cycles = cycles;
-        st->ir_steps = cycles;
-        st->residual = rel;
-        st->leaf_nodes = h.leaf_nodes;
-        st->total_nodes = h.total_nodes;
-        st->launches = h.launches - launches0;
+    int rc = MRP_OK;
+    if (st) std::memset(st, 0, sizeof(*st));
+    for (auto& g : H->g) {
+        Handle& h = *g;
+        const int64_t launches0 = h.launches;
+        int cycles = 0;
+        double rel = INFINITY;
+        const int r = solve_adjoint(h, w, fbar, (cudaStream_t)stream, &cycles, &rel);
+        if (r == MRP_ERR_CUDA || r == MRP_ERR_OOM) return r;
+        if (r && (!rc || rc == MRP_ERR_NOT_CONVERGED)) rc = r;
+        if (st) {
+            st->cycles = std::max(st->cycles, cycles);
+            st->ir_steps = st->cycles;
+            st->residual = std::max(st->residual, rel);
+            st->leaf_nodes += h.leaf_nodes;
+            st->total_nodes += h.total_nodes;
+            st->launches += h.launches - launches0;
+        }
     }
     return rc;
 }
 
 int mrp_adjoint_len(mrp_handle* H, int64_t* len) {
     if (!H || !len) return MRP_ERR_INVALID_ARG;
-    *len = H->h.total_nodes;
+    *len = H->g[0]->total_nodes;
     return MRP_OK;
 }
 
 int mrp_adjoint_op(mrp_handle* H, int32_t op, const double* in, double* out, void* stream) {
     if (!H || !in || !out) return MRP_ERR_INVALID_ARG;
-    return adjoint_op(H->h, op, in, out, (cudaStream_t)stream);
+    if (H->g.size() != 1) return MRP_ERR_UNSUPPORTED;
+    return adjoint_op(*H->g[0], op, in, out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------- step API
 int mrp_level_count(mrp_handle* H, int32_t* levels) {
     if (!H || !levels) return MRP_ERR_INVALID_ARG;
-    *levels = H->h.L + 1;
+    *levels = H->g[0]->L + 1;
     return MRP_OK;
 }
 
 int mrp_level_info(mrp_handle* H, int32_t level, int32_t* nb, int32_t* coords, uint8_t* is_leaf) {
-    if (!H || !nb || level < 0 || level > H->h.L) return MRP_ERR_INVALID_ARG;
-    const Level& lv = H->h.lv[level];
+    if (!H || !nb || level < 0 || level > H->g[0]->L) return MRP_ERR_INVALID_ARG;
+    const Level& lv = H->g[0]->lv[level];
     *nb = lv.nb;
     if (coords) std::memcpy(coords, lv.h_coords.data(), sizeof(int32_t) * 3 * lv.nb);
     if (is_leaf) std::memcpy(is_leaf, lv.h_is_leaf.data(), lv.nb);
@@ -634,8 +845,8 @@ int mrp_level_info(mrp_handle* H, int32_t level, int32_t* nb, int32_t* coords, u
 }
 
 int mrp_field_copy(mrp_handle* H, int32_t field, int32_t level, double* buf, int32_t to_handle, void* stream) {
-    if (!H || !buf || level < 0 || level > H->h.L) return MRP_ERR_INVALID_ARG;
-    Handle& h = H->h;
+    if (!H || !buf || level < 0 || level > H->g[0]->L) return MRP_ERR_INVALID_ARG;
+    Handle& h = *H->g[0];
     Level& lv = h.lv[level];
     const size_t n = h.n;
     double* p = nullptr;
@@ -656,7 +867,7 @@ int mrp_field_copy(mrp_handle* H, int32_t field, int32_t level, double* buf, int
 
 int mrp_step(mrp_handle* H, int32_t step, int32_t level, const double* f_leaf, void* stream) {
     if (!H) return MRP_ERR_INVALID_ARG;
-    Handle& h = H->h;
+    Handle& h = *H->g[0];
     cudaStream_t s = (cudaStream_t)stream;
     const bool lvl_ok = level >= 0 && level <= h.L;
     switch (step) {
@@ -698,15 +909,15 @@ int mrp_step(mrp_handle* H, int32_t step, int32_t level, const double* f_leaf, v
 
 int mrp_lgf_extent(mrp_handle* H, int32_t* nmax) {
     if (!H || !nmax) return MRP_ERR_INVALID_ARG;
-    *nmax = H->h.lgf_nmax;
+    *nmax = H->g[0]->lgf_nmax;
     return MRP_OK;
 }
 
 int mrp_lgf_copy(mrp_handle* H, int32_t nmax, double* out_host) {
-    if (!H || !out_host || nmax < 0 || nmax > H->h.lgf_nmax) return MRP_ERR_INVALID_ARG;
-    const int nn = H->h.lgf_nmax + 1, m = nmax + 1;
+    if (!H || !out_host || nmax < 0 || nmax > H->g[0]->lgf_nmax) return MRP_ERR_INVALID_ARG;
+    const int nn = H->g[0]->lgf_nmax + 1, m = nmax + 1;
     std::vector<double> all((size_t)nn * nn * nn);
-    if (cudaMemcpy(all.data(), H->h.lgf, sizeof(double) * all.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpy(all.data(), H->g[0]->lgf, sizeof(double) * all.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return MRP_ERR_CUDA;
     for (int a = 0; a < m; ++a)
         for (int b = 0; b < m; ++b)
@@ -716,7 +927,7 @@ int mrp_lgf_copy(mrp_handle* H, int32_t nmax, double* out_host) {
 
 int mrp_profile_enable(mrp_handle* H, int32_t enable) {
     if (!H) return MRP_ERR_INVALID_ARG;
-    Handle& h = H->h;
+    Handle& h = *H->g[0];
     if (enable && h.ev.empty()) {
         h.ev.resize(4096);
         for (auto& e : h.ev)
@@ -728,7 +939,7 @@ int mrp_profile_enable(mrp_handle* H, int32_t enable) {
 
 int mrp_profile_read(mrp_handle* H, int32_t n, double* ms, int64_t* launches, int64_t* nodes, int32_t reset) {
     if (!H || n < 0 || n > 16) return MRP_ERR_INVALID_ARG;
-    Handle& h = H->h;
+    Handle& h = *H->g[0];
     if (!h.pend.empty()) {
         if (cudaDeviceSynchronize() != cudaSuccess) return MRP_ERR_CUDA;
         harvest(h);
@@ -745,7 +956,7 @@ int mrp_profile_read(mrp_handle* H, int32_t n, double* ms, int64_t* launches, in
 
 int mrp_fft_shape(mrp_handle* H, int32_t* P) {
     if (!H || !P) return MRP_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a) P[a] = H->h.ax[a].P;
+    for (int a = 0; a < 3; ++a) P[a] = H->g[0]->pr[0].ax[a].P;
     return MRP_OK;
 }
 

@@ -25,7 +25,7 @@ STEPS = {"prepare_rhs": 0, "ghost_u": 1, "smooth": 2, "residual": 3, "restrict":
 EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_error_string",
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
-            "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op"]
+            "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph"]
 ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
@@ -88,6 +88,7 @@ def load_library(path=LIB_PATH):
     lib.mrp_coarse_solve_noalloc.argtypes = [P, P, P, P]
     lib.mrp_adjoint_len.argtypes = [P, C.POINTER(I64)]
     lib.mrp_adjoint_op.argtypes = [P, I32, P, P, P]
+    lib.mrp_solve_graph.argtypes = [P, P, P, P, C.POINTER(Stats)]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
     lib.mrp_error_string.restype = C.c_char_p
@@ -108,33 +109,59 @@ def _stream_ptr(stream):
 
 
 class Solver:
-    """One forest, one right-hand side, FP64 (``mrp_create`` / ``mrp_solve``)."""
+    """Solver for one forest, or a batch of forests (``mrp_create`` / ``mrp_solve``).
+
+    ``forest``: a forest, or a list of forests solved together.  ``ncomp``:
+    right-hand sides per forest (an int for all, or one per forest).  The
+    caller layout of f and u is [forest][component][leaf][n][n][n], float64.
+    """
 
     def __init__(self, forest, order=4, tol=1e-10, max_cycles=50, nu1=3, nu2=3, precision="fp64",
-                 inner_cycles=0, max_outer=0):
+                 inner_cycles=0, max_outer=0, ncomp=1):
         import torch  # noqa: F401  (CUDA context and memory come from torch)
         self.lib = load_library()
-        self.forest = forest
-        self.n = int(forest.n)
-        self.n_leaves = int(forest.n_leaves)
-        self._lev = np.ascontiguousarray(forest.leaf_level, dtype=np.int32)
-        self._ijk = np.ascontiguousarray(forest.leaf_ijk, dtype=np.int32).reshape(-1, 3)
-        fd = _Forest()
-        fd.nb0[:] = [int(v) for v in forest.nb0]
-        fd.n = self.n
-        fd.origin[:] = [float(v) for v in forest.origin]
-        fd.h0 = float(forest.h0)
-        fd.n_leaves = self.n_leaves
-        fd.leaf_level = self._lev.ctypes.data_as(C.POINTER(C.c_int32))
-        fd.leaf_ijk = self._ijk.ctypes.data_as(C.POINTER(C.c_int32))
-        fd.ncomp = 1
+        forests = list(forest) if isinstance(forest, (list, tuple)) else [forest]
+        comps = list(ncomp) if isinstance(ncomp, (list, tuple)) else [int(ncomp)] * len(forests)
+        if len(comps) != len(forests):
+            raise ValueError("ncomp needs one entry per forest")
+        self.forests = forests
+        self.forest = forests[0]
+        self.ncomp = comps
+        self.n = int(forests[0].n)
+        self.n_leaves = int(forests[0].n_leaves)
+        self.elems = sum(int(c) * int(f.n_leaves) * int(f.n) ** 3 for f, c in zip(forests, comps))
+        self._keep = []
+        arr = (_Forest * len(forests))()
+        for i, (f, c) in enumerate(zip(forests, comps)):
+            lev = np.ascontiguousarray(f.leaf_level, dtype=np.int32)
+            ijk = np.ascontiguousarray(f.leaf_ijk, dtype=np.int32).reshape(-1, 3)
+            self._keep += [lev, ijk]
+            fd = arr[i]
+            fd.nb0[:] = [int(v) for v in f.nb0]
+            fd.n = int(f.n)
+            fd.origin[:] = [float(v) for v in f.origin]
+            fd.h0 = float(f.h0)
+            fd.n_leaves = int(f.n_leaves)
+            fd.leaf_level = lev.ctypes.data_as(C.POINTER(C.c_int32))
+            fd.leaf_ijk = ijk.ctypes.data_as(C.POINTER(C.c_int32))
+            fd.ncomp = int(c)
         op = _Options()
         op.order, op.tol, op.stop_rule, op.max_cycles = int(order), float(tol), 0, int(max_cycles)
         op.nu1, op.nu2 = int(nu1), int(nu2)
         op.precision = {"fp64": 0, "mixed": 1}[precision]
         op.inner_cycles, op.max_outer = int(inner_cycles), int(max_outer)
         self.h = C.c_void_p()
-        _check(self.lib.mrp_create(C.byref(self.h), C.byref(fd), 1, C.byref(op)), "mrp_create")
+        _check(self.lib.mrp_create(C.byref(self.h), arr, len(forests), C.byref(op)), "mrp_create")
+
+    def slices(self):
+        """(start, stop) element ranges of every (forest, component) in the caller layout."""
+        out, off = [], 0
+        for f, c in zip(self.forests, self.ncomp):
+            m = int(f.n_leaves) * int(f.n) ** 3
+            for _ in range(int(c)):
+                out.append((off, off + m))
+                off += m
+        return out
 
     def close(self):
         if self.h:
@@ -151,9 +178,8 @@ class Solver:
     def solve(self, f, u=None, stream=None, allow_not_converged=False):
         """u = solve(f); f, u: CUDA float64 tensors [n_leaves, n, n, n]."""
         import torch
-        n = self.n
-        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.n_leaves * n ** 3:
-            raise ValueError("f must be a contiguous CUDA float64 tensor of shape [n_leaves, n, n, n]")
+        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.elems:
+            raise ValueError("f must be a contiguous CUDA float64 tensor in the caller layout")
         if u is None:
             u = torch.empty_like(f)
         st = Stats()
@@ -163,15 +189,28 @@ class Solver:
         _check(rc, "mrp_solve", allow)
         return u, st
 
+    def solve_graph(self, f, u=None, stream=None, allow_not_converged=False):
+        """Same as ``solve``, as one CUDA graph launch (built on first use and when f or u change)."""
+        import torch
+        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous() or f.numel() != self.elems:
+            raise ValueError("f must be a contiguous CUDA float64 tensor in the caller layout")
+        if u is None:
+            u = torch.empty_like(f)
+        st = Stats()
+        allow = (MRP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        rc = self.lib.mrp_solve_graph(self.h, C.c_void_p(f.data_ptr()), C.c_void_p(u.data_ptr()), _stream_ptr(stream),
+                                      C.byref(st))
+        _check(rc, "mrp_solve_graph", allow)
+        return u, st
+
     def solve_adjoint(self, w, fbar=None, stream=None, allow_not_converged=False):
         """fbar = S^T w, the gradient of <w, u> with respect to f for the converged solve.
 
         w, fbar: CUDA float64 tensors [n_leaves, n, n, n] (leaf layout of solve).
         """
         import torch
-        n = self.n
-        if w.dtype != torch.float64 or not w.is_cuda or not w.is_contiguous() or w.numel() != self.n_leaves * n ** 3:
-            raise ValueError("w must be a contiguous CUDA float64 tensor of shape [n_leaves, n, n, n]")
+        if w.dtype != torch.float64 or not w.is_cuda or not w.is_contiguous() or w.numel() != self.elems:
+            raise ValueError("w must be a contiguous CUDA float64 tensor in the caller layout")
         if fbar is None:
             fbar = torch.empty_like(w)
         st = Stats()
@@ -190,7 +229,7 @@ class Solver:
         """One factor of the gradient (``ADJ_OPS``); see mrp_adjoint_op for the vector layouts."""
         import torch
         L = self.adjoint_len()
-        out_len = {"cycle_T": L, "res_T": 2 * L, "out_T": 2 * L, "rhs_T": self.n_leaves * self.n ** 3}[name]
+        out_len = {"cycle_T": L, "res_T": 2 * L, "out_T": 2 * L, "rhs_T": self.elems}[name]
         x = x.contiguous()
         out = torch.zeros(out_len, dtype=torch.float64, device="cuda")
         _check(self.lib.mrp_adjoint_op(self.h, ADJ_OPS[name], C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),

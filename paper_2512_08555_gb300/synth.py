@@ -95,8 +95,8 @@ def adaptive_forest(nb0, n, origin, h0, max_level, want_refine, keep_boundary=Tr
     """
     nb0 = tuple(int(v) for v in nb0)
     D = _nbrs26()
-    ref = [set() for _ in range(max_level)]      # refined blocks per level
-    forb = [set() for _ in range(max_level)]
+    ref = [set() for _ in range(max_level + 1)]      # refined blocks per level
+    forb = [set() for _ in range(max_level + 1)]
 
     def in_dom(k, c):
         return all(0 <= c[a] < nb0[a] << k for a in range(3))
@@ -374,8 +374,78 @@ def config3(seed=0, max_level=4, n=16):
     return config2(seed, max_level=max_level, n=n)
 
 
+def vortex_forest(seed=0, max_level=3, n=16, nb=6, half=1.5, thresh=1e-3):
+    """Forest of the vortex-ring problem: [-1.5,1.5)^3, 6^3 level-0 blocks of 16^3, levels 0..3.
+
+    A block is refined where max |omega| over its nodes exceeds 1e-3 times the
+    core peak Gamma / (2 pi sigma^2).  With 4^3 level-0 blocks the boundary
+    rule (boundary blocks stay level-0 leaves) and 2:1 balance stop the
+    refinement at level 2; 6^3 blocks (h0 = 1/32) reach level 3.
+    """
+    ring = vortex_ring(seed)
+    h0 = 2 * half / (nb * n)
+    origin = (-half, -half, -half)
+    peak = ring.gamma / (2 * np.pi * ring.sigma ** 2)
+
+    def mag(x, y, z):
+        p = [x - ring.centre[0], y - ring.centre[1], z - ring.centre[2]]
+        nrm = ring.normal
+        along = p[0] * nrm[0] + p[1] * nrm[1] + p[2] * nrm[2]
+        q2 = (p[0] - along * nrm[0]) ** 2 + (p[1] - along * nrm[1]) ** 2 + (p[2] - along * nrm[2]) ** 2
+        rho2 = (np.sqrt(q2) - ring.R0) ** 2 + along ** 2
+        return peak * np.exp(-rho2 / (2 * ring.sigma ** 2))
+
+    def want(level, coords):
+        h = h0 / (1 << level)
+        i = np.arange(n)
+        out = np.zeros(len(coords), bool)
+        for s in range(0, len(coords), 64):
+            sel = slice(s, s + 64)
+            X = origin[0] + (coords[sel, 0][:, None] * n + i) * h
+            Y = origin[1] + (coords[sel, 1][:, None] * n + i) * h
+            Z = origin[2] + (coords[sel, 2][:, None] * n + i) * h
+            v = mag(X[:, None, None, :], Y[:, None, :, None], Z[:, :, None, None])
+            out[sel] = v.reshape(v.shape[0], -1).max(axis=1) > thresh * peak
+        return out
+
+    forest = adaptive_forest((nb, nb, nb), n, origin, h0, max_level, want)
+    forest.meta.update(workload=f"vortex ring on [-1.5,1.5)^3, levels 0..{max_level}, {n}^3 blocks", seed=seed)
+    return forest, ring
+
+
 def batched_scalar_problem(i, seed=0):
     """Problem ``i`` of the batched set: levels = 2 + (i mod 4), n = {12,14,16,18,20}[i mod 5]."""
     n = (12, 14, 16, 18, 20)[i % 5]
     max_level = 1 + (i % 4)
     return _bump_forest(seed + 1000 + i, max_level, n=n)
+
+
+def config4(seed=0, n_scalar=16, scale_levels=0):
+    """The batched workload: the vortex ring (3 components) plus ``n_scalar`` scalar problems.
+
+    Returns ``[(forest, ncomp, [source per component])]``; the ring's sources
+    are -omega_x, -omega_y, -omega_z (so that the solutions are the vector
+    potential components).  ``scale_levels`` lowers every problem's finest
+    level by that many (a smaller instance of the same mix).
+    """
+    out = []
+    ring_forest, ring = vortex_forest(seed, max_level=max(0, 3 - scale_levels))
+
+    def neg(fn):
+        return lambda x, y, z: -fn(x, y, z)
+    out.append((ring_forest, 3, [neg(ring.component(c)) for c in range(3)]))
+    for i in range(n_scalar):
+        n = (12, 14, 16, 18, 20)[i % 5]
+        ml = max(0, 1 + (i % 4) - scale_levels)
+        forest, src = _bump_forest(seed + 1000 + i, ml, n=n)
+        out.append((forest, 1, [src]))
+    return out
+
+
+def batched_rhs(problems):
+    """Concatenated right-hand side of :func:`config4` in the caller layout [forest][component][leaf][n^3]."""
+    parts = []
+    for forest, ncomp, srcs in problems:
+        for c in range(ncomp):
+            parts.append(sample_leaves(forest, srcs[c]).reshape(-1))
+    return np.concatenate(parts)
