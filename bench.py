@@ -9,6 +9,15 @@ plain FP64 path is timed beside it and the chosen result's max error against
 it is reported.  e2e = the chosen form through the host-memory call (pinned
 H2D of f, solve, D2H of u inside the timed region).
 
+Besides the headline, rank 0 reports (unless --no-extras):
+  adjoint     the gradient of the converged solve (mrp_solve_adjoint, FP64) on
+              the same forest, with the dot-product identity <w, S f> = <S^T w, f>;
+  five_level  the same generator at five levels (29.5M leaf nodes), chosen vs
+              plain FP64, with the smoother's roofline at sizes beyond L2;
+  batched     the vortex ring (3 components, 4 levels) plus 16 uneven scalar
+              problems (2..5 levels, blocks of 12^3..20^3): 195M leaf nodes
+              solved as one CUDA graph launch, chosen vs plain FP64.
+
 --impl reference times the CPU oracle (plain numpy FP64) on the same
 workload: preparation plus one V-cycle, extrapolated to the cycle count of
 the solve.  N > 1 ranks run independent replicas (seed = rank).
@@ -181,6 +190,103 @@ def _time_solves(solver, f, steps, warmup, flush, stream):
     return ms, u, sts[-1], launches, prof, host
 
 
+def _time_calls(fn, steps, warmup, flush, stream):
+    """Warm up, then time `steps` calls of fn() (L2 flushed before each) with CUDA events; returns (ms, last result)."""
+    import torch
+    out = None
+    for _ in range(warmup):
+        out = fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return float(np.mean(times)), out
+
+
+def bench_adjoint(desc, f, u_plain, ms_plain, order, flush, stream, steps):
+    """Gradient of <w, u> for a seeded Gaussian weight w, FP64, on the headline forest."""
+    import torch
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver
+    s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES)
+    w = torch.from_numpy(synth.sample_leaves(desc, synth.gaussian_weight(0))).cuda()
+    ms, (g, st) = _time_calls(lambda: s.solve_adjoint(w), steps, 3, flush, stream)
+    a = float((w * u_plain).sum())
+    b = float((g * f).sum())
+    out = {"what": "f-bar = S^T w, FP64 refinement with transposed correction V-cycles",
+           "ms_per_gradient": ms, "transposed_cycles": int(st.cycles), "final_rel_residual": float(st.residual),
+           "ratio_to_plain_fp64_forward": ms / ms_plain,
+           "dot_identity_rel": abs(a - b) / abs(a), "launches_per_gradient": int(st.launches)}
+    s.close()
+    return out
+
+
+def bench_five_level(order, flush, stream, steps):
+    import torch
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver
+    desc, src = synth.config3(0)
+    f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
+    out = {"workload": f"adaptive [-1,1)^3, levels 0..{desc.max_level}, 5^3 level-0 blocks of 16^3, 8 C4 bumps",
+           "leaf_nodes": int(desc.leaf_nodes)}
+    res = {}
+    for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
+        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec)
+        for _ in range(3):
+            s.solve(f)
+        s.profile(True)
+        s.profile_read(reset=True)
+        ms, (u, st) = _time_calls(lambda: s.solve(f), steps, 0, flush, stream)
+        prof = s.profile_read(reset=True)
+        s.profile(False)
+        res[name] = (ms, u, st, prof)
+        out[name] = {"value": desc.leaf_nodes / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms,
+                     "cycles": int(st.cycles), "ir_steps": int(st.ir_steps), "final_rel_residual": float(st.residual),
+                     "phases_ms_per_step": {k: v["ms"] / steps for k, v in prof.items()}}
+        if name == "chosen":
+            out["roofline_smoother"] = _roofline(prof, order, steps)
+        s.close()
+    out["max_rel_err_vs_fp64"] = float((res["chosen"][1] - res["plain_fp64"][1]).abs().max()
+                                       / res["plain_fp64"][1].abs().max())
+    out["speedup_vs_plain_fp64"] = res["plain_fp64"][0] / res["chosen"][0]
+    return out
+
+
+def bench_batched(order, flush, stream, steps):
+    import torch
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver
+    problems = synth.config4(0)
+    forests = [p[0] for p in problems]
+    comps = [p[1] for p in problems]
+    f = torch.from_numpy(synth.batched_rhs(problems)).cuda()
+    nodes = int(f.numel())
+    out = {"workload": "vortex ring on [-1.5,1.5)^3 (3 components, levels 0..3, 16^3 blocks) + 16 scalar C4-bump "
+                       "problems on [-1,1)^3 with levels 0..1+(i mod 4) and blocks of {12,14,16,18,20}^3",
+           "problems": int(sum(comps)), "forests": len(forests), "leaf_nodes": nodes,
+           "launch": "one CUDA graph launch per solve (mrp_solve_graph): device-controlled loops per block size"}
+    res = {}
+    for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
+        s = Solver(forests, order=order, tol=TOL, max_cycles=MAX_CYCLES, ncomp=comps, precision=prec)
+        u = torch.empty_like(f)
+        ms, (u, st) = _time_calls(lambda: s.solve_graph(f, u), steps, 3, flush, stream)
+        res[name] = (ms, u.clone(), st)
+        out[name] = {"value": nodes / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms, "cycles": int(st.cycles),
+                     "ir_steps": int(st.ir_steps), "final_rel_residual": float(st.residual),
+                     "kernels_per_solve": int(st.launches)}
+        s.close()
+    out["max_rel_err_vs_fp64"] = float((res["chosen"][1] - res["plain_fp64"][1]).abs().max()
+                                       / res["plain_fp64"][1].abs().max())
+    out["speedup_vs_plain_fp64"] = res["plain_fp64"][0] / res["chosen"][0]
+    return out
+
+
 def _roofline(prof, order, steps):
     """Dominant-kernel roofline: the smoother of the chosen path (FP32, bytes) and of the FP64 path (flops)."""
     out = {}
@@ -292,10 +398,36 @@ def run_ours(args):
         uo = o.leaf_u()
         line["parity_1cycle_max_rel"] = float(np.abs(u1.cpu().numpy() - uo).max() / np.abs(uo).max())
         s1.close()
+    if rank == 0 and not args.no_extras:
+        xs = max(2, min(args.steps, 3))
+        line["adjoint"] = bench_adjoint(desc, f, u_p, ms_p, args.order, flush, stream, xs)
+        line["five_level"] = bench_five_level(args.order, flush, stream, xs)
+        line["batched"] = bench_batched(args.order, flush, stream, xs)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    """A short run of one workload for ncu captures: build, tune, `warmup` + `steps` solves, no timing output."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver
+    if args.profile_case == "five_level":
+        desc, src = synth.config3(0)
+    else:
+        desc, src = synth.config2(0)
+    f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
+    s = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed")
+    for _ in range(args.warmup + args.steps):
+        s.solve(f)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "leaf_nodes": int(desc.leaf_nodes)}))
     return 0
 
 
@@ -307,7 +439,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--order", type=int, default=ORDER, choices=[2, 4, 6])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline line only")
+    ap.add_argument("--profile-case", choices=["headline", "five_level"], default=None,
+                    help="run the chosen solver on one workload without timing (for ncu)")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -147,6 +147,8 @@ int graph_build(mrp_handle* H, const double* f, double* u) {
     if (H->gexec) { cudaGraphExecDestroy(H->gexec); H->gexec = nullptr; }
     if (H->graph) { cudaGraphDestroy(H->graph); H->graph = nullptr; }
     if (!H->cap) GK(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
+    for (auto& g : H->g)
+        if (autotune(*g, H->cap)) return MRP_ERR_CUDA;
     GK(cudaGraphCreate(&H->graph, 0));
     for (auto& g : H->g) {
         const bool prof = g->prof;

@@ -271,7 +271,7 @@ __host__ __device__ inline size_t fused_smem(int n, int I) {
 // One Gauss-Seidel iteration (Sec. 3.1): 8 colours c = (x&1) + 2(y&1) + 4(z&1),
 // u <- (den h^2 f - offcentre) / c; reads Uin, writes the interior to Uout.
 template <int M, typename T, int I>
-__global__ void __launch_bounds__(256) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
+__global__ void __launch_bounds__(1024) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
                                                       const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
                                                       LevelView lc, int n, T h2den, const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_smooth_fused(T* __restrict__ Uout, cons
 
 // ---------------------------------------------------------------- residual r = f - L u (all nodes)
 template <int M, typename T, int I>
-__global__ void __launch_bounds__(256) k_residual_fused(T* __restrict__ R, const T* __restrict__ U, const T* __restrict__ F,
+__global__ void __launch_bounds__(1024) k_residual_fused(T* __restrict__ R, const T* __restrict__ U, const T* __restrict__ F,
                                                         const T* __restrict__ Uc, LevelView lk, LevelView lc, int n, T scale,
                                                         const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) k_residual_fused(T* __restrict__ R, const
 // ---------------------------------------------------------------- FAS RHS and u-hat (Alg. 1)
 // F += L u on covered blocks; H = u on every block.
 template <int M, typename T, int I>
-__global__ void __launch_bounds__(256) k_fas_fused(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U,
+__global__ void __launch_bounds__(1024) k_fas_fused(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U,
                                                    const T* __restrict__ Uc, LevelView lk, LevelView lc, int n, T scale,
                                                    const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
@@ -368,7 +368,7 @@ __device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
 }
 
 template <int M, int I>
-__global__ void __launch_bounds__(256) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
+__global__ void __launch_bounds__(1024) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
                                                        const double* __restrict__ F, const double* __restrict__ Uc,
                                                        const int* __restrict__ blocks, LevelView lk, LevelView lc, int n,
                                                        double scale, unsigned long long* out) {
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(256) k_leafres_fused(double* __restrict__ R, c
 // ---------------------------------------------------------------- halo dump (step API)
 // Writes the ghost layer build_halo() produces into the block's stored ghost layer.
 template <typename T, int I>
-__global__ void __launch_bounds__(256) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, LevelView lc, int n) {
+__global__ void __launch_bounds__(1024) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, LevelView lc, int n) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
     const int S = n + 2, S3 = S * S * S;
@@ -435,45 +435,46 @@ static void set_attrs() {
 
 template <typename T>
 void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
-                         double h2, cudaStream_t s) {
+                         double h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, 256, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<2>::den), lk.order);
-    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, 256, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<4>::den), lk.order);
-    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, 256, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<6>::den), lk.order);
+    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, nt, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<2>::den), lk.order);
+    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, nt, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<4>::den), lk.order);
+    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, nt, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<6>::den), lk.order);
 }
 
 template <typename T>
 void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
-                           double inv_h2, cudaStream_t s) {
+                           double inv_h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, 256, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, 256, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, 256, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, nt, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, nt, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, nt, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
 }
 
 template <typename T>
 void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, double inv_h2,
-                      cudaStream_t s) {
+                      int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, 256, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, 256, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, 256, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, nt, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, nt, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, nt, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
 }
 
 void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
-                          LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, cudaStream_t s) {
+                          LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, int nt,
+                          cudaStream_t s) {
     if (nblocks == 0) return;
     set_attrs<double>();
     const size_t sm = fused_smem<double>(n, M + 2);
-    if (M == 2) k_leafres_fused<2, 4><<<nblocks, 256, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<2>::den, out);
-    if (M == 4) k_leafres_fused<4, 6><<<nblocks, 256, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<4>::den, out);
-    if (M == 6) k_leafres_fused<6, 8><<<nblocks, 256, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<6>::den, out);
+    if (M == 2) k_leafres_fused<2, 4><<<nblocks, nt, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<2>::den, out);
+    if (M == 4) k_leafres_fused<4, 6><<<nblocks, nt, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<4>::den, out);
+    if (M == 6) k_leafres_fused<6, 8><<<nblocks, nt, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<6>::den, out);
 }
 
 template <typename T>
@@ -487,17 +488,17 @@ void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int 
 }
 
 template void launch_smooth_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView, int,
-                                          int, double, cudaStream_t);
+                                          int, double, int, cudaStream_t);
 template void launch_smooth_fused<float>(float*, const float*, const float*, const float*, LevelView, LevelView, int, int,
-                                         double, cudaStream_t);
+                                         double, int, cudaStream_t);
 template void launch_residual_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView,
-                                            int, int, double, cudaStream_t);
+                                            int, int, double, int, cudaStream_t);
 template void launch_residual_fused<float>(float*, const float*, const float*, const float*, LevelView, LevelView, int,
-                                           int, double, cudaStream_t);
+                                           int, double, int, cudaStream_t);
 template void launch_fas_fused<double>(double*, double*, const double*, const double*, LevelView, LevelView, int, int,
-                                       double, cudaStream_t);
+                                       double, int, cudaStream_t);
 template void launch_fas_fused<float>(float*, float*, const float*, const float*, LevelView, LevelView, int, int, double,
-                                      cudaStream_t);
+                                      int, cudaStream_t);
 template void launch_halo_dump<double>(double*, const double*, LevelView, LevelView, int, int, cudaStream_t);
 template void launch_halo_dump<float>(float*, const float*, LevelView, LevelView, int, int, cudaStream_t);
 

@@ -126,6 +126,11 @@ struct Handle {
     std::vector<Pending> pend;
     double prof_ms[16] = {};
     int64_t prof_cnt[16] = {}, prof_nodes[16] = {};
+    // CTA sizes of the fused stencil kernels per precision (0 FP64, 1 FP32) and
+    // level, chosen by timing at the first solve (autotune in solver.cu)
+    static constexpr int MAXL = 32;
+    int nt_smooth[2][MAXL], nt_res[2][MAXL], nt_fas[2][MAXL], nt_leafres[MAXL];
+    bool tuned = false;
     // device-side loop control of the graph-captured solve (graph.cu)
     int* loop_ctr = nullptr;          // [4]: cycles, refinement steps, status, unused
     double* loop_rel = nullptr;       // [nprob] relative residuals
@@ -193,6 +198,7 @@ void leaf_residual_launch(Handle& h, cudaStream_t s);
 void outer_residual_launch(Handle& h, cudaStream_t s);
 void correction_launch(Handle& h, cudaStream_t s);
 void solve_end(Handle& h, double* u, cudaStream_t s);
+int autotune(Handle& h, cudaStream_t s);
 // gradient of the converged solve (adjoint.cu)
 int adjoint_setup(Handle& h);
 void adjoint_release(Handle& h);
@@ -227,17 +233,18 @@ void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
 // stencil kernels with the ghost layer built in shared memory (kernels_fused.cu)
 template <typename T>
 void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
-                         double h2, cudaStream_t s);
+                         double h2, int nt, cudaStream_t s);
 template <typename T>
 void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
-                           double inv_h2, cudaStream_t s);
+                           double inv_h2, int nt, cudaStream_t s);
 template <typename T>
 void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, double inv_h2,
-                      cudaStream_t s);
+                      int nt, cudaStream_t s);
 template <typename T>
 void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
 void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
-                          LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, cudaStream_t s);
+                          LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, int nt,
+                          cudaStream_t s);
 
 void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk, LevelView lkm1, int n, int M,
                        bool zero_outside, cudaStream_t s);

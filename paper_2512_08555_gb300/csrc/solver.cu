@@ -400,6 +400,8 @@ static void ghost_u(Handle& h, int k, cudaStream_t s) {
     launch_halo_dump<T>(ucur<T>(h, k), ucoarse<T>(h, k), h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, s);
 }
 
+template <typename T> static constexpr int pidx() { return sizeof(T) == 4 ? 1 : 0; }
+
 // One Gauss-Seidel sweep with its ghost layer built in the kernel; reads the
 // current buffer, writes the other, then the two swap.
 template <typename T>
@@ -407,7 +409,7 @@ static void smooth(Handle& h, int k, cudaStream_t s) {
     PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h), 1);
     const double hk = level_h(h, k);
     launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
-                           view_or_empty(h, k - 1), h.n, h.M, hk * hk, s);
+                           view_or_empty(h, k - 1), h.n, h.M, hk * hk, h.nt_smooth[pidx<T>()][k], s);
     std::swap(ualt<T>(h, k), ucur<T>(h, k));
 }
 
@@ -416,7 +418,7 @@ static void residual(Handle& h, int k, cudaStream_t s) {
     PhaseScope ps(h, s, ph<T>(PH_RESIDUAL), h.lv[k].nb * n3(h), 1);
     const double hk = level_h(h, k);
     launch_residual_fused<T>(fld<T>(h, k).R, ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
-                             view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), s);
+                             view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.nt_res[pidx<T>()][k], s);
 }
 
 // Restriction k -> k-1: inject u, full-weight r, FAS RHS on covered blocks, u-hat.
@@ -431,7 +433,7 @@ static void restrict_level(Handle& h, int k, cudaStream_t s) {
     PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.nb * n3(h), 1);
     const double hk = level_h(h, k - 1);
     launch_fas_fused<T>(fld<T>(h, k - 1).F, fld<T>(h, k - 1).H, ucur<T>(h, k - 1), ucoarse<T>(h, k - 1), c.view(),
-                        view_or_empty(h, k - 2), h.n, h.M, 1.0 / (hk * hk), s);
+                        view_or_empty(h, k - 2), h.n, h.M, 1.0 / (hk * hk), h.nt_fas[pidx<T>()][k - 1], s);
 }
 
 template <typename T>
@@ -510,6 +512,79 @@ struct SolveState {
     }
 };
 
+// CTA size of each fused stencil kernel, per precision and level: the fastest
+// of 128, 256, 512 and 1024 threads on the level's own block pool (few blocks
+// favour large CTAs, which shorten the serial colour sweeps of one block;
+// many blocks favour smaller ones).  The timed launches write only scratch
+// that every solve overwrites before reading (the other ping-pong buffer, R,
+// and F, H of covered blocks).
+template <typename T>
+static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    const int cand[4] = {128, 256, 512, 1024};
+    constexpr int pi = pidx<T>();
+    auto pick = [&](auto&& launch) {
+        float best = 1e30f;
+        int arg = 256;
+        for (int c : cand) {
+            launch(c);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) launch(c);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) { best = ms; arg = c; }
+        }
+        return arg;
+    };
+    for (int k = 0; k <= h.L; ++k) {
+        const double hk = level_h(h, k);
+        Level& lv = h.lv[k];
+        if (k >= 1) {
+            h.nt_smooth[pi][k] = pick([&](int nt) {
+                launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), lv.view(),
+                                       view_or_empty(h, k - 1), h.n, h.M, hk * hk, nt, s);
+            });
+            h.nt_res[pi][k] = pick([&](int nt) {
+                launch_residual_fused<T>(fld<T>(h, k).R, ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), lv.view(),
+                                         view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), nt, s);
+            });
+        }
+        if (k < h.L)
+            h.nt_fas[pi][k] = pick([&](int nt) {
+                launch_fas_fused<T>(fld<T>(h, k).F, fld<T>(h, k).H, ucur<T>(h, k), ucoarse<T>(h, k), lv.view(),
+                                    view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), nt, s);
+            });
+        if (pi == 0 && lv.nleaf > 0)
+            h.nt_leafres[k] = pick([&](int nt) {
+                launch_leafres_fused(nullptr, lv.U, lv.F, ucoarse<double>(h, k), lv.leaf_blocks, lv.nleaf, lv.view(),
+                                     view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(3), nt, s);
+            });
+    }
+}
+
+static void tune_defaults(Handle& h) {
+    for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < Handle::MAXL; ++k) {
+            h.nt_smooth[p][k] = h.nt_res[p][k] = h.nt_fas[p][k] = 256;
+            h.nt_leafres[k] = 256;
+        }
+}
+
+int autotune(Handle& h, cudaStream_t s) {
+    if (h.tuned) return MRP_OK;
+    tune_defaults(h);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return MRP_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MRP_ERR_CUDA; }
+    tune_precision<double>(h, s, e0, e1);
+    if (h.mixed) tune_precision<float>(h, s, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
+    h.tuned = true;
+    return MRP_OK;
+}
+
 void solve_begin(Handle& h, const double* f, cudaStream_t s) {
     const size_t S = h.n + 2;
     if (h.mixed) cudaMemsetAsync(h.lv[0].F, 0, sizeof(double) * h.lv[0].nb * n3(h), s);
@@ -546,7 +621,8 @@ void leaf_residual_launch(Handle& h, cudaStream_t s) {
         PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
         const double hk = level_h(h, k);
         launch_leafres_fused(nullptr, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
-                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1), s);
+                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1),
+                             h.nt_leafres[k], s);
     }
 }
 
@@ -568,7 +644,8 @@ void outer_residual_launch(Handle& h, cudaStream_t s) {
         PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
         const double hk = level_h(h, k);
         launch_leafres_fused(h.lv[k].R, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
-                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1), s);
+                             h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1),
+                             h.nt_leafres[k], s);
     }
 }
 
@@ -692,6 +769,7 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
         h.mixed = opt->precision == MRP_MIXED;
         h.inner_cycles = opt->inner_cycles > 0 ? opt->inner_cycles : 4;
         h.max_ir = opt->max_outer > 0 ? opt->max_outer : 12;
+        tune_defaults(h);
         std::string why;
         rc = build_forest(h, kv.second, why);
         if (rc == MRP_OK) rc = upload_tables(h);
@@ -751,6 +829,8 @@ int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats
     const size_t G = H->g.size();
     std::vector<int64_t> launches0(G);
     for (size_t i = 0; i < G; ++i) launches0[i] = H->g[i]->launches;
+    for (size_t i = 0; i < G; ++i)
+        if (autotune(*H->g[i], s)) return MRP_ERR_CUDA;
     const std::vector<cudaStream_t> gs = fork_streams(H, s);
     for (size_t i = 0; i < G; ++i) solve_begin(*H->g[i], f, gs[i]);
     std::vector<SolveState> ss(G);
