@@ -76,8 +76,8 @@ static size_t box_bytes(const Handle& h, int k, int g) {
 // injection of level k into the covered level-(k-1) nodes that precedes it.
 static void ghost_fill_T(Handle& h, int k, cudaStream_t s) {
     PhaseScope ps(h, s, PH_GHOST, h.lv[k].nb * n3(h), k >= 1 ? 2 : 1);
-    launch_ghost_T(h.adj[k].Ub, 1, k >= 1 ? h.adj[k - 1].Ub : nullptr, 1, h.lv[k].view(), view_or_empty(h, k - 1), h.n,
-                   h.M, s);
+    launch_ghost_T_fused(h.adj[k].Ub, k >= 1 ? h.adj[k - 1].Ub : nullptr, h.lv[k].view(), view_or_empty(h, k - 1), h.n,
+                         h.M, s);
     if (k >= 1) launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, h.lv[k].view(), h.n, s);
 }
 

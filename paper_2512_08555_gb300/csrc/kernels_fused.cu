@@ -26,23 +26,98 @@ template <> struct LW<2> { static constexpr double den = 1, c = -6, f = 1, e = 0
 template <> struct LW<4> { static constexpr double den = 6, c = -24, f = 2, e = 1, k = 0; };
 template <> struct LW<6> { static constexpr double den = 30, c = -128, f = 14, e = 3, k = 1; };
 
-template <int M, typename T>
-__device__ __forceinline__ T offc(const T* __restrict__ a, int o, int S, int S2) {
-    using W = LW<M>;
-    T acc = T(W::f) * ((a[o - 1] + a[o + 1]) + (a[o - S] + a[o + S]) + (a[o - S2] + a[o + S2]));
-    if (W::e != 0)
-        acc += T(W::e) * ((a[o - 1 - S] + a[o + 1 - S]) + (a[o - 1 + S] + a[o + 1 + S])
-                          + (a[o - 1 - S2] + a[o + 1 - S2]) + (a[o - 1 + S2] + a[o + 1 + S2])
-                          + (a[o - S - S2] + a[o + S - S2]) + (a[o - S + S2] + a[o + S + S2]));
-    if (W::k != 0)
-        acc += T(W::k) * ((a[o - 1 - S - S2] + a[o + 1 - S - S2]) + (a[o - 1 + S - S2] + a[o + 1 + S - S2])
-                          + (a[o - 1 - S + S2] + a[o + 1 - S + S2]) + (a[o - 1 + S + S2] + a[o + 1 + S + S2]));
-    return acc;
+// ---------------------------------------------------------------- parity-split box
+// The block's (n+2)^3 box (ghost layer included) is kept in shared memory as
+// 8 sub-arrays by the parity of the box coordinates (X, Y, Z):
+//     at(X, Y, Z) = ((Z&1)*4 + (Y&1)*2 + (X&1)) * H3p + ((Z>>1) H + (Y>>1)) H + (X>>1),
+// H = (n+2)/2, sub-array stride H3p >= H^3 with H3p = 16 (mod 32).  In one
+// Gauss-Seidel colour every stencil neighbour of the colour's nodes lies in
+// one sub-array per offset, at unit stride along x across a warp: no bank
+// conflicts; the two x-parities of a row fall 16 banks apart.
+struct Split {
+    int H, H2, H3p;
+    __device__ __forceinline__ int at(int X, int Y, int Z) const {
+        return (((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1)) * H3p + ((Z >> 1) * H + (Y >> 1)) * H + (X >> 1);
+    }
+};
+__host__ __device__ inline int split_h3p(int n) {
+    const int H = n / 2 + 1, H3 = H * H * H;
+    return H3 + ((16 - H3 % 32) % 32 + 32) % 32;
+}
+__device__ __forceinline__ Split split_of(int n) {
+    Split sp;
+    sp.H = n / 2 + 1;
+    sp.H2 = sp.H * sp.H;
+    sp.H3p = split_h3p(n);
+    return sp;
 }
 
+// The thread's nodes of one colour: node q = tid + k * nt (k < KMAX) of the
+// (n/2)^3 nodes (i, j, l) of a colour, packed i | j << 10 | l << 20; a colour
+// c = (cx, cy, cz) places it at interior coordinates (2i+cx, 2j+cy, 2l+cz).
+constexpr int KMAX = 8;
+struct Cset { int cnt; int q[KMAX]; };
+__device__ __forceinline__ void cset_init(Cset& cs, int h) {
+    const int h3 = h * h * h;
+    cs.cnt = 0;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int q = threadIdx.x + k * blockDim.x;
+        cs.q[k] = 0;
+        if (q < h3) {
+            const int i = q % h, j = (q / h) % h, l = q / (h * h);
+            cs.q[k] = i | (j << 10) | (l << 20);
+            cs.cnt = k + 1;
+        }
+    }
+}
+
+// Offsets of colour col: cb = sub-array of the (-1,-1,-1) neighbour; dX, dY,
+// dZ = step from a (-1) neighbour to the centre along each axis (the (+1)
+// neighbour is 1, H, H^2 past the (-1) one); fo / go = natural interior /
+// box offsets of the colour.
+struct Col { int cb, dX, dY, dZ, fo, go; };
+__device__ __forceinline__ Col colour(int col, const Split& sp, int n) {
+    const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
+    const int S = n + 2;
+    Col c;
+    c.cb = sp.H3p * (4 * cz + 2 * cy + cx);
+    c.dX = sp.H3p * (1 - 2 * cx) + cx;
+    c.dY = 2 * sp.H3p * (1 - 2 * cy) + sp.H * cy;
+    c.dZ = 4 * sp.H3p * (1 - 2 * cz) + sp.H2 * cz;
+    c.fo = (cz * n + cy) * n + cx;
+    c.go = (cz * S + cy) * S + cx;
+    return c;
+}
+
+// Per node of a colour: split index of its (-1,-1,-1) neighbour, natural
+// interior index and natural box index (each before the colour's offsets).
+struct Node { int b0, f, g; };
+__device__ __forceinline__ Node node_of(int packed, const Split& sp, int n) {
+    const int i = packed & 1023, j = (packed >> 10) & 1023, l = packed >> 20;
+    const int S = n + 2;
+    Node d;
+    d.b0 = (l * sp.H + j) * sp.H + i;
+    d.f = ((2 * l) * n + 2 * j) * n + 2 * i;
+    d.g = ((2 * l + 1) * S + 2 * j + 1) * S + 2 * i + 1;
+    return d;
+}
+
+// Weighted sum of the 26 off-centre neighbours (integer weights of LW<M>) of
+// the node whose (-1,-1,-1) neighbour sits at split index b0.
 template <int M, typename T>
-__device__ __forceinline__ T lhs(const T* __restrict__ a, int o, int S, int S2) {
-    return T(LW<M>::c) * a[o] + offc<M>(a, o, S, S2);
+__device__ __forceinline__ T offc_s(const T* __restrict__ a, int b0, int dX, int dY, int dZ, int H, int H2) {
+    using W = LW<M>;
+    T acc = T(W::f) * ((a[b0 + dY + dZ] + a[b0 + 1 + dY + dZ]) + (a[b0 + dX + dZ] + a[b0 + dX + H + dZ])
+                       + (a[b0 + dX + dY] + a[b0 + dX + dY + H2]));
+    if (W::e != 0)
+        acc += T(W::e) * ((a[b0 + dZ] + a[b0 + 1 + dZ]) + (a[b0 + H + dZ] + a[b0 + 1 + H + dZ])
+                          + (a[b0 + dY] + a[b0 + 1 + dY]) + (a[b0 + dY + H2] + a[b0 + 1 + dY + H2])
+                          + (a[b0 + dX] + a[b0 + dX + H]) + (a[b0 + dX + H2] + a[b0 + dX + H + H2]));
+    if (W::k != 0)
+        acc += T(W::k) * ((a[b0] + a[b0 + 1]) + (a[b0 + H] + a[b0 + 1 + H])
+                          + (a[b0 + H2] + a[b0 + 1 + H2]) + (a[b0 + H + H2] + a[b0 + 1 + H + H2]));
+    return acc;
 }
 
 template <int I> __device__ __forceinline__ double midw(int m);
@@ -95,8 +170,8 @@ __host__ __device__ inline int pool_size(int n, int I) {
 
 template <typename T, int I>
 __device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, HaloSmem<T>& hs,
-                           const T* __restrict__ Uk,
-                           const T* __restrict__ Uc, const LevelView& lk, const LevelView& lc, int b, int n) {
+                           const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk, const LevelView& lc,
+                           int b, int n, const Split& sp, const Cset& cs) {
     const int S = n + 2, S2 = S * S, S3 = S2 * S;
     const int tid = threadIdx.x, nth = blockDim.x;
     if (tid < 27) hs.snbr[tid] = lk.nbr[27 * b + tid];
@@ -109,10 +184,14 @@ __device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restri
         hs.interp = any;
     }
     const int n3 = n * n * n;
-    for (int t = tid; t < n3; t += nth) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 1) * S + y + 1) * S + x + 1;
-        su[o] = Ub[o];
+    for (int col = 0; col < 8; ++col) {
+        const Col c = colour(col, sp, n);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < cs.cnt) {
+                const Node d = node_of(cs.q[k], sp, n);
+                su[c.cb + d.b0 + c.dX + c.dY + c.dZ] = Ub[d.g + c.go];
+            }
     }
     const int shell = S3 - n3;
     for (int t = tid; t < shell; t += nth) {
@@ -123,8 +202,8 @@ __device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restri
         const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
         const int j = hs.snbr[dir27(dx, dy, dz)];
         const int o = (z * S + y) * S + x;
-        if (j >= 0) su[o] = Uk[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)];
-        else if (j == NBR_OUTSIDE) su[o] = Ub[o];
+        if (j >= 0) su[sp.at(x, y, z)] = Uk[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)];
+        else if (j == NBR_OUTSIDE) su[sp.at(x, y, z)] = Ub[o];
     }
     __syncthreads();
     if (!hs.interp) return;
@@ -174,8 +253,8 @@ __device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restri
             // covered coarse node: the coincident fine node of the current level
             const int ox = lx >= h, oy = ly >= h, oz = lz >= h;
             const int ch = hs.cch[8 * d + ox + 2 * oy + 4 * oz];
-            const int fo = ((2 * lz - oz * n + 1) * S + 2 * ly - oy * n + 1) * S + 2 * lx - ox * n + 1;
-            v = ch == b ? su[fo] : Uk[(size_t)ch * S3 + fo];
+            const int FX = 2 * lx - ox * n + 1, FY = 2 * ly - oy * n + 1, FZ = 2 * lz - oz * n + 1;
+            v = ch == b ? su[sp.at(FX, FY, FZ)] : Uk[(size_t)ch * S3 + (FZ * S + FY) * S + FX];
         }
         patch[t] = v;
     }
@@ -251,7 +330,7 @@ __device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restri
             for (int m0 = 0; m0 < cn0; ++m0) a0 += (cn0 == 1 ? T(1) : hs.sw[m0]) * R[rb + m0 * sd0];
             acc += (cn1 == 1 ? T(1) : hs.sw[m1]) * a0;
         }
-        su[(z * S + y) * S + x] = acc;
+        su[sp.at(x, y, z)] = acc;
     }
     __syncthreads();
 }
@@ -263,92 +342,126 @@ __host__ __device__ inline int patch_size(int n, int I) {
 
 template <typename T>
 __host__ __device__ inline size_t fused_smem(int n, int I) {
-    const size_t S = n + 2;
-    return sizeof(T) * (S * S * S + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
+    return sizeof(T) * (8 * (size_t)split_h3p(n) + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
 }
 
 // ---------------------------------------------------------------- smoother
 // One Gauss-Seidel iteration (Sec. 3.1): 8 colours c = (x&1) + 2(y&1) + 4(z&1),
 // u <- (den h^2 f - offcentre) / c; reads Uin, writes the interior to Uout.
 template <int M, typename T, int I>
-__global__ void __launch_bounds__(1024) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
+__global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
                                                       const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
                                                       LevelView lc, int n, T h2den, const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const int S = n + 2, S2 = S * S, S3 = S2 * S;
-    T* pool = su + S3;
+    const Split sp = split_of(n);
+    T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem<T> hs;
+    Cset cs;
+    cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, lc, b, n);
+    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, lc, b, n, sp, cs);
     const T* Fb = F + (size_t)b * n * n * n;
-    const int h = n >> 1, h3 = h * h * h;
     const T inv_c = T(1) / T(LW<M>::c);
     for (int col = 0; col < 8; ++col) {
-        const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
-        for (int q = threadIdx.x; q < h3; q += blockDim.x) {
-            const int x = 2 * (q % h) + cx, y = 2 * ((q / h) % h) + cy, z = 2 * (q / (h * h)) + cz;
-            const int o = ((z + 1) * S + y + 1) * S + x + 1;
-            su[o] = (h2den * Fb[(z * n + y) * n + x] - offc<M>(su, o, S, S2)) * inv_c;
-        }
+        const Col c = colour(col, sp, n);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < cs.cnt) {
+                const Node d = node_of(cs.q[k], sp, n);
+                const int b0 = c.cb + d.b0;
+                su[b0 + c.dX + c.dY + c.dZ] =
+                    (h2den * Fb[d.f + c.fo] - offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2)) * inv_c;
+            }
         __syncthreads();
     }
-    T* Ob = Uout + (size_t)b * S3;
-    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 1) * S + y + 1) * S + x + 1;
-        Ob[o] = su[o];
+    T* Ob = Uout + (size_t)b * (n + 2) * (n + 2) * (n + 2);
+    for (int col = 0; col < 8; ++col) {
+        const Col c = colour(col, sp, n);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < cs.cnt) {
+                const Node d = node_of(cs.q[k], sp, n);
+                Ob[d.g + c.go] = su[c.cb + d.b0 + c.dX + c.dY + c.dZ];
+            }
     }
 }
 
 // ---------------------------------------------------------------- residual r = f - L u (all nodes)
 template <int M, typename T, int I>
-__global__ void __launch_bounds__(1024) k_residual_fused(T* __restrict__ R, const T* __restrict__ U, const T* __restrict__ F,
-                                                        const T* __restrict__ Uc, LevelView lk, LevelView lc, int n, T scale,
-                                                        const int* __restrict__ order) {
+__global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const T* __restrict__ U,
+                                                        const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
+                                                        LevelView lc, int n, T scale, const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
-    T* pool = su + S3;
+    const Split sp = split_of(n);
+    T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem<T> hs;
+    Cset cs;
+    cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        R[(size_t)b * n3 + t] = F[(size_t)b * n3 + t] - scale * lhs<M>(su, ((z + 1) * S + y + 1) * S + x + 1, S, S2);
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    const size_t n3 = (size_t)n * n * n;
+    for (int col = 0; col < 8; ++col) {
+        const Col c = colour(col, sp, n);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < cs.cnt) {
+                const Node d = node_of(cs.q[k], sp, n);
+                const int b0 = c.cb + d.b0;
+                const T l = T(LW<M>::c) * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const size_t fi = b * n3 + d.f + c.fo;
+                R[fi] = F[fi] - scale * l;
+            }
     }
 }
 
 // ---------------------------------------------------------------- FAS RHS and u-hat (Alg. 1)
 // F += L u on covered blocks; H = u on every block.
 template <int M, typename T, int I>
-__global__ void __launch_bounds__(1024) k_fas_fused(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U,
+__global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U,
                                                    const T* __restrict__ Uc, LevelView lk, LevelView lc, int n, T scale,
                                                    const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
-    T* pool = su + S3;
+    const Split sp = split_of(n);
+    T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem<T> hs;
+    const int S = n + 2, S3 = S * S * S;
+    const size_t n3 = (size_t)n * n * n;
     const int b = order ? order[blockIdx.x] : blockIdx.x;
+    Cset cs;
+    cset_init(cs, n >> 1);
     const bool cov = !lk.is_leaf[b];
     if (!cov) {
         const T* Ub = U + (size_t)b * S3;
-        for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-            const int x = t % n, y = (t / n) % n, z = t / (n * n);
-            H[(size_t)b * n3 + t] = Ub[((z + 1) * S + y + 1) * S + x + 1];
+        for (int col = 0; col < 8; ++col) {
+            const Col c = colour(col, sp, n);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < cs.cnt) {
+                    const Node d = node_of(cs.q[k], sp, n);
+                    H[b * n3 + d.f + c.fo] = Ub[d.g + c.go];
+                }
         }
         return;
     }
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 1) * S + y + 1) * S + x + 1;
-        F[(size_t)b * n3 + t] += scale * lhs<M>(su, o, S, S2);
-        H[(size_t)b * n3 + t] = su[o];
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    for (int col = 0; col < 8; ++col) {
+        const Col c = colour(col, sp, n);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < cs.cnt) {
+                const Node d = node_of(cs.q[k], sp, n);
+                const int b0 = c.cb + d.b0;
+                const T u = su[b0 + c.dX + c.dY + c.dZ];
+                const size_t fi = b * n3 + d.f + c.fo;
+                F[fi] += scale * (T(LW<M>::c) * u + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2));
+                H[fi] = u;
+            }
     }
 }
 
@@ -368,24 +481,35 @@ __device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
 }
 
 template <int M, int I>
-__global__ void __launch_bounds__(1024) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
+__global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
                                                        const double* __restrict__ F, const double* __restrict__ Uc,
                                                        const int* __restrict__ blocks, LevelView lk, LevelView lc, int n,
                                                        double scale, unsigned long long* out) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     double* su = reinterpret_cast<double*>(fz_smem);
-    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
-    double* pool = su + S3;
+    const Split sp = split_of(n);
+    double* pool = su + 8 * sp.H3p;
     double* patch = pool + pool_size(n, I);
     __shared__ HaloSmem<double> hs;
+    Cset cs;
+    cset_init(cs, n >> 1);
     const int b = blocks[blockIdx.x];
-    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
+    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    const size_t n3 = (size_t)n * n * n;
     double m = 0.0;
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const double r = F[(size_t)b * n3 + t] - scale * lhs<M>(su, ((z + 1) * S + y + 1) * S + x + 1, S, S2);
-        if (R) R[(size_t)b * n3 + t] = r;
-        m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
+    for (int col = 0; col < 8; ++col) {
+        const Col c = colour(col, sp, n);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < cs.cnt) {
+                const Node d = node_of(cs.q[k], sp, n);
+                const int b0 = c.cb + d.b0;
+                const double l = LW<M>::c * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const size_t fi = b * n3 + d.f + c.fo;
+                const double r = F[fi] - scale * l;
+                if (R) R[fi] = r;
+                m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
+            }
     }
     bmax_atomic(m, out + (lk.prob ? lk.prob[b] : 0));
 }
@@ -393,25 +517,224 @@ __global__ void __launch_bounds__(1024) k_leafres_fused(double* __restrict__ R, 
 // ---------------------------------------------------------------- halo dump (step API)
 // Writes the ghost layer build_halo() produces into the block's stored ghost layer.
 template <typename T, int I>
-__global__ void __launch_bounds__(1024) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, LevelView lc, int n) {
+__global__ void __launch_bounds__(512) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, LevelView lc,
+                                                   int n) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const int S = n + 2, S3 = S * S * S;
-    T* pool = su + S3;
+    const Split sp = split_of(n);
+    T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem<T> hs;
+    Cset cs;
+    cset_init(cs, n >> 1);
+    const int S = n + 2, S3 = S * S * S;
     const int b = blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n);
-    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
-        const int x = t % S, y = (t / S) % S, z = t / (S * S);
-        const bool interior = x > 0 && x < S - 1 && y > 0 && y < S - 1 && z > 0 && z < S - 1;
-        if (!interior) U[(size_t)b * S3 + t] = su[t];
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    for (int t = threadIdx.x; t < S3 - n * n * n; t += blockDim.x) {
+        int x, y, z;
+        shell_coords(t, S, x, y, z);
+        U[(size_t)b * S3 + (z * S + y) * S + x] = su[sp.at(x, y, z)];
     }
 }
 
 // ---------------------------------------------------------------- launchers
 template <typename K>
 static void allow(K kern) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM); }
+
+// ---------------------------------------------------------------- ghost fill, transposed (FP64)
+// Exact transpose of the ghost layer build_halo() produces for block b
+// (halo 1): the adjoints on b's ghost layer A[b] are sent back to their
+// sources, then the ghost layer is cleared.  Copied regions add to the
+// same-level neighbour's interior; interpolated regions run the two
+// separable passes of build_halo() backwards in shared memory (tangential,
+// then normal, with shared atomics) into the coarse patch, whose entries add
+// to the coarse level's interior (leaf coarse blocks) or to the coincident
+// node of the current level (covered coarse blocks, which the forward reads
+// from the fine level); outside the domain the adjoint is dropped.  Global
+// writes are atomic and land only on interiors, never on ghost layers, so
+// blocks of one launch do not interfere.
+template <int I>
+__global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, double* __restrict__ Ac, LevelView lk,
+                                                       LevelView lc, int n) {
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    double* pool = reinterpret_cast<double*>(fz_smem);
+    __shared__ HaloSmem<double> hs;
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int b = blockIdx.x;
+    if (tid < 27) hs.snbr[tid] = lk.nbr[27 * b + tid];
+    if (tid < I) hs.sw[tid] = midw<I>(tid);
+    __syncthreads();
+    if (tid == 0) {
+        int any = 0;
+        for (int d = 0; d < 27; ++d) any |= (d != 13 && hs.snbr[d] == NBR_MISSING);
+        hs.interp = any;
+    }
+    double* Ab = A + (size_t)b * S3;
+    const int shell = S3 - n3;
+    // copied regions
+    for (int t = tid; t < shell; t += nth) {
+        int x, y, z;
+        shell_coords(t, S, x, y, z);
+        const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
+        const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
+        const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
+        const int j = hs.snbr[dir27(dx, dy, dz)];
+        if (j < 0) continue;
+        const int o = (z * S + y) * S + x;
+        const double a = Ab[o];
+        Ab[o] = 0.0;
+        if (a != 0.0) atomicAdd(&A[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)], a);
+    }
+    __syncthreads();
+    if (!hs.interp) {
+        for (int t = tid; t < shell; t += nth) {      // outside-domain ghosts: dropped
+            int x, y, z;
+            shell_coords(t, S, x, y, z);
+            Ab[(z * S + y) * S + x] = 0.0;
+        }
+        return;
+    }
+    const int P = lk.parent[b];
+    if (tid < 27) {
+        const int cb = lc.nbr[27 * P + tid];
+        hs.cnbr[tid] = cb;
+        hs.cleaf[tid] = cb >= 0 ? (int)lc.is_leaf[cb] : 1;
+        for (int o = 0; o < 8; ++o) hs.cch[8 * tid + o] = (cb >= 0 && !hs.cleaf[tid]) ? lc.children[8 * cb + o] : -1;
+    }
+    const int TN = tan_n(n, I), TN2 = TN * TN;
+    if (tid == 0) {
+        int o = 0, nr = 0;
+        for (int d = 0; d < 27; ++d) {
+            hs.off[d] = o;
+            if (d == 13 || hs.snbr[d] != NBR_MISSING) continue;
+            const int nt = (d % 3 == 1) + ((d / 3) % 3 == 1) + (d / 9 == 1);
+            hs.rdir[nr] = d;
+            hs.rstart[nr] = o;
+            ++nr;
+            o += nt == 2 ? TN2 : (nt == 1 ? TN : 1);
+        }
+        hs.nreg = nr;
+        hs.ntot = o;
+    }
+    const int h = n >> 1;
+    constexpr int plo = 4 - I / 2;
+    const int PL = h + I, PL2 = PL * PL, PL3 = PL2 * PL;
+    double* patch = pool + pool_size(n, I);
+    for (int t = tid; t < pool_size(n, I) + PL3; t += nth) pool[t] = 0.0;
+    __syncthreads();
+    // phase 2 transposed: each interpolated ghost node spreads over its region's reduced array
+    for (int t = tid; t < shell; t += nth) {
+        int x, y, z;
+        shell_coords(t, S, x, y, z);
+        const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
+        const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
+        const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
+        const int d = dir27(dx, dy, dz);
+        const int o = (z * S + y) * S + x;
+        if (hs.snbr[d] != NBR_MISSING) {
+            if (hs.snbr[d] == NBR_OUTSIDE) Ab[o] = 0.0;
+            continue;
+        }
+        const double a = Ab[o];
+        Ab[o] = 0.0;
+        if (a == 0.0) continue;
+        double* R = pool + hs.off[d];
+        int st0 = 0, st1 = 0, cn0 = 1, cn1 = 1, sd0 = 0, sd1 = 0, nt = 0, stride = 1;
+        const int q[3] = {x - 1, y - 1, z - 1};
+        const int dd[3] = {dx, dy, dz};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            if (dd[ax] != 0) continue;
+            const int qa = q[ax];
+            const int st = (qa & 1) ? 4 + ((qa - 1) >> 1) - I / 2 + 1 - tan_lo<I>() : 4 + (qa >> 1) - tan_lo<I>();
+            const int cn = (qa & 1) ? I : 1;
+            if (nt == 0) { st0 = st; cn0 = cn; sd0 = stride; }
+            else { st1 = st; cn1 = cn; sd1 = stride; }
+            stride *= TN;
+            ++nt;
+        }
+        for (int m1 = 0; m1 < cn1; ++m1) {
+            const double a1 = (cn1 == 1 ? 1.0 : hs.sw[m1]) * a;
+            const int rb = (st1 + m1) * sd1 + st0 * sd0;
+            for (int m0 = 0; m0 < cn0; ++m0) atomicAdd(&R[rb + m0 * sd0], (cn0 == 1 ? 1.0 : hs.sw[m0]) * a1);
+        }
+    }
+    __syncthreads();
+    // phase 1 transposed: each reduced element spreads along its region's normal axes into the patch
+    const int lo = 0, up = 4 + h - plo, tlo = tan_lo<I>() - plo;
+    for (int f = tid; f < hs.ntot; f += nth) {
+        int r = 0;
+        while (r + 1 < hs.nreg && hs.rstart[r + 1] <= f) ++r;
+        const int d = hs.rdir[r];
+        const int e = f - hs.rstart[r];
+        const double a = pool[f];
+        if (a == 0.0) continue;
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        int tc[3] = {0, 0, 0};
+        int rem = e;
+        if (dx == 0) { tc[0] = tlo + rem % TN; rem /= TN; }
+        if (dy == 0) { tc[1] = tlo + rem % TN; rem /= TN; }
+        if (dz == 0) { tc[2] = tlo + rem % TN; }
+        const int cx = dx < 0 ? I : 1, cy = dy < 0 ? I : 1, cz = dz < 0 ? I : 1;
+        const int x0 = dx < 0 ? lo : (dx > 0 ? up : tc[0]);
+        const int y0 = dy < 0 ? lo : (dy > 0 ? up : tc[1]);
+        const int z0 = dz < 0 ? lo : (dz > 0 ? up : tc[2]);
+        for (int mz = 0; mz < cz; ++mz) {
+            const double az = (cz == 1 ? 1.0 : hs.sw[mz]) * a;
+            for (int my = 0; my < cy; ++my) {
+                const double ay = (cy == 1 ? 1.0 : hs.sw[my]) * az;
+                double* row = patch + ((z0 + mz) * PL + y0 + my) * PL + x0;
+                for (int mx = 0; mx < cx; ++mx) atomicAdd(&row[mx], (cx == 1 ? 1.0 : hs.sw[mx]) * ay);
+            }
+        }
+    }
+    __syncthreads();
+    // the patch back to its sources
+    const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
+    const int base[3] = {(bx & 1) * h - 4 + plo, (by & 1) * h - 4 + plo, (bz & 1) * h - 4 + plo};
+    for (int t = tid; t < PL3; t += nth) {
+        const double a = patch[t];
+        if (a == 0.0) continue;
+        const int px = t % PL, py = (t / PL) % PL, pz = t / PL2;
+        const int rx = base[0] + px, ry = base[1] + py, rz = base[2] + pz;
+        const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0);
+        const int ey = ry < 0 ? -1 : (ry >= n ? 1 : 0);
+        const int ez = rz < 0 ? -1 : (rz >= n ? 1 : 0);
+        const int d = dir27(ex, ey, ez);
+        const int lx = rx - ex * n, ly = ry - ey * n, lz = rz - ez * n;
+        if (hs.cleaf[d]) {
+            if (hs.cnbr[d] >= 0) atomicAdd(&Ac[(size_t)hs.cnbr[d] * S3 + ((lz + 1) * S + ly + 1) * S + lx + 1], a);
+        } else {
+            const int ox = lx >= h, oy = ly >= h, oz = lz >= h;
+            const int ch = hs.cch[8 * d + ox + 2 * oy + 4 * oz];
+            const int FX = 2 * lx - ox * n + 1, FY = 2 * ly - oy * n + 1, FZ = 2 * lz - oz * n + 1;
+            atomicAdd(&A[(size_t)ch * S3 + (FZ * S + FY) * S + FX], a);
+        }
+    }
+}
+
+void launch_ghost_T_fused(double* A, double* Ac, LevelView lk, LevelView lc, int n, int M, cudaStream_t s) {
+    if (lk.nb == 0) return;
+    const int I = M + 2, PL = n / 2 + I;
+    const size_t sm = sizeof(double) * ((size_t)pool_size(n, I) + (size_t)PL * PL * PL);
+    static bool attr = false;
+    if (!attr) {
+        allow(k_ghost_T_fused<4>); allow(k_ghost_T_fused<6>); allow(k_ghost_T_fused<8>);
+        attr = true;
+    }
+    if (M == 2) k_ghost_T_fused<4><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
+    if (M == 4) k_ghost_T_fused<6><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
+    if (M == 6) k_ghost_T_fused<8><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
+}
+
+// CTA size actually launched: the requested one, raised (in warps) until each
+// thread holds at most KMAX nodes of a colour.
+static int cta_size(int n, int nt) {
+    const int h3 = (n / 2) * (n / 2) * (n / 2);
+    while (nt < 512 && nt * KMAX < h3) nt += 32;
+    return nt;
+}
 
 template <int M, typename T>
 static void set_attrs_m() {
@@ -439,9 +762,10 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, nt, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<2>::den), lk.order);
-    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, nt, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<4>::den), lk.order);
-    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, nt, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<6>::den), lk.order);
+    const int ct = cta_size(n, nt);
+    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<2>::den), lk.order);
+    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<4>::den), lk.order);
+    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<6>::den), lk.order);
 }
 
 template <typename T>
@@ -450,9 +774,10 @@ void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView 
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, nt, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, nt, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, nt, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+    const int ct = cta_size(n, nt);
+    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
 }
 
 template <typename T>
@@ -461,9 +786,10 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, nt, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, nt, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, nt, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+    const int ct = cta_size(n, nt);
+    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
 }
 
 void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
@@ -472,9 +798,9 @@ void launch_leafres_fused(double* R, const double* U, const double* F, const dou
     if (nblocks == 0) return;
     set_attrs<double>();
     const size_t sm = fused_smem<double>(n, M + 2);
-    if (M == 2) k_leafres_fused<2, 4><<<nblocks, nt, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<2>::den, out);
-    if (M == 4) k_leafres_fused<4, 6><<<nblocks, nt, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<4>::den, out);
-    if (M == 6) k_leafres_fused<6, 8><<<nblocks, nt, sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<6>::den, out);
+    if (M == 2) k_leafres_fused<2, 4><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<2>::den, out);
+    if (M == 4) k_leafres_fused<4, 6><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<4>::den, out);
+    if (M == 6) k_leafres_fused<6, 8><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<6>::den, out);
 }
 
 template <typename T>

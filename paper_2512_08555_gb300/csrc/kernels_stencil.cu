@@ -93,62 +93,89 @@ template void launch_inject_to_parent<float>(float*, int, const float*, int, Lev
 // otherwise the I-point tensor-product Lagrange interpolant of level k-1
 // (identity along axes where the node coincides with a coarse node).  The
 // coarse nodes lie in the 27-neighbourhood of b's parent.
-template <typename T>
-__global__ void k_ghost_fill(T* __restrict__ A, int g, const T* __restrict__ Ac, int gc, LevelView lk,
+//
+// Interface blocks first stage, in shared memory, every coarse node their
+// interpolants can touch: parent-local indices [pb, pb + PL) per axis with
+// pb = (b&1) n/2 - (g+1)/2 - I/2 and PL = n/2 + g + I + 1 (nodes of missing
+// coarse blocks, which no interpolant uses, read as 0).
+template <int I>
+__global__ void k_ghost_fill(double* __restrict__ A, int g, const double* __restrict__ Ac, int gc, LevelView lk,
                              LevelView lc, int n, InterpW iw, bool zero_outside) {
+    extern __shared__ double gpatch[];
+    __shared__ int snbr[27], cnbr[27];
+    __shared__ double sw[8];
+    __shared__ int interp;
     const int b = blockIdx.x;
     const int S = n + 2 * g, S2 = S * S, S3 = S2 * S;
     const int Sc = n + 2 * gc, Sc2 = Sc * Sc, Sc3 = Sc2 * Sc;
-    const int* nbr = lk.nbr + b * 27;
-    T* Ab = A + (size_t)b * S3;
+    const int h = n >> 1;
+    const int P = lk.parent[b];
+    if (threadIdx.x < 27) {
+        snbr[threadIdx.x] = lk.nbr[27 * b + threadIdx.x];
+        cnbr[threadIdx.x] = P >= 0 ? lc.nbr[27 * P + threadIdx.x] : -1;
+    }
+    if (threadIdx.x < I) sw[threadIdx.x] = iw.w[threadIdx.x];
+    if (threadIdx.x == 0) interp = 0;
+    __syncthreads();
+    if (threadIdx.x < 27 && threadIdx.x != 13 && snbr[threadIdx.x] == NBR_MISSING) interp = 1;
+    __syncthreads();
+    double* Ab = A + (size_t)b * S3;
     const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
+    const int PL = h + g + I + 1, PL2 = PL * PL;
+    const int pb[3] = {(bx & 1) * h - (g + 1) / 2 - I / 2, (by & 1) * h - (g + 1) / 2 - I / 2,
+                       (bz & 1) * h - (g + 1) / 2 - I / 2};
+    if (interp) {
+        for (int t = threadIdx.x; t < PL2 * PL; t += blockDim.x) {
+            const int r[3] = {pb[0] + t % PL, pb[1] + (t / PL) % PL, pb[2] + t / PL2};
+            int e[3], l[3];
+            for (int a = 0; a < 3; ++a) { e[a] = r[a] < 0 ? -1 : (r[a] >= n ? 1 : 0); l[a] = r[a] - e[a] * n; }
+            const int cb = cnbr[dir27(e[0], e[1], e[2])];
+            gpatch[t] = cb >= 0 ? Ac[(size_t)cb * Sc3 + (size_t)((gc + l[2]) * Sc + gc + l[1]) * Sc + gc + l[0]] : 0.0;
+        }
+        __syncthreads();
+    }
     for (int t = threadIdx.x; t < S3; t += blockDim.x) {
         const int x = t % S, y = (t / S) % S, z = t / S2;
         const int dx = x < g ? -1 : (x >= g + n ? 1 : 0);
         const int dy = y < g ? -1 : (y >= g + n ? 1 : 0);
         const int dz = z < g ? -1 : (z >= g + n ? 1 : 0);
         if ((dx | dy | dz) == 0) continue;
-        const int j = nbr[dir27(dx, dy, dz)];
+        const int j = snbr[dir27(dx, dy, dz)];
         if (j >= 0) {
             Ab[t] = A[(size_t)j * S3 + (size_t)((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)];
             continue;
         }
         if (j == NBR_OUTSIDE) {
-            if (zero_outside) Ab[t] = T(0);
+            if (zero_outside) Ab[t] = 0.0;
             continue;
         }
-        // interpolation from level k-1
-        const int P = lk.parent[b];
-        const int* cnbr = lc.nbr + P * 27;
+        // interpolation from level k-1 (parent-local coarse indices, then patch indices)
         const int p[3] = {bx * n + x - g, by * n + y - g, bz * n + z - g};
         const int porig[3] = {(bx >> 1) * n, (by >> 1) * n, (bz >> 1) * n};
         int cnt[3], c0[3];
         for (int a = 0; a < 3; ++a) {
-            if ((p[a] & 1) == 0) { cnt[a] = 1; c0[a] = (p[a] >> 1) - porig[a]; }
-            else { cnt[a] = iw.I; c0[a] = ((p[a] - 1) >> 1) - iw.I / 2 + 1 - porig[a]; }
+            if ((p[a] & 1) == 0) { cnt[a] = 1; c0[a] = (p[a] >> 1) - porig[a] - pb[a]; }
+            else { cnt[a] = I; c0[a] = ((p[a] - 1) >> 1) - I / 2 + 1 - porig[a] - pb[a]; }
         }
-        T accz = T(0);
+        double accz = 0.0;
         for (int mz = 0; mz < cnt[2]; ++mz) {
-            const int rz = c0[2] + mz;
-            const int ddz = rz < 0 ? -1 : (rz >= n ? 1 : 0);
-            const int lz = rz - ddz * n;
-            T accy = T(0);
+            double accy = 0.0;
             for (int my = 0; my < cnt[1]; ++my) {
-                const int ry = c0[1] + my;
-                const int ddy = ry < 0 ? -1 : (ry >= n ? 1 : 0);
-                const int ly = ry - ddy * n;
-                T accx = T(0);
-                for (int mx = 0; mx < cnt[0]; ++mx) {
-                    const int rx = c0[0] + mx;
-                    const int ddx = rx < 0 ? -1 : (rx >= n ? 1 : 0);
-                    const int lx = rx - ddx * n;
-                    const int cb = cnbr[dir27(ddx, ddy, ddz)];
-                    const T v = Ac[(size_t)cb * Sc3 + (size_t)((gc + lz) * Sc + gc + ly) * Sc + gc + lx];
-                    accx += (cnt[0] == 1 ? T(1) : T(iw.w[mx])) * v;
+                const double* row = gpatch + ((c0[2] + mz) * PL + c0[1] + my) * PL + c0[0];
+                double accx;
+                if (cnt[0] == 1) {
+                    accx = row[0];
+                } else {
+                    double v[I];
+#pragma unroll
+                    for (int mx = 0; mx < I; ++mx) v[mx] = row[mx];
+                    accx = 0.0;
+#pragma unroll
+                    for (int mx = 0; mx < I; ++mx) accx += sw[mx] * v[mx];
                 }
-                accy += (cnt[1] == 1 ? T(1) : T(iw.w[my])) * accx;
+                accy += (cnt[1] == 1 ? 1.0 : sw[my]) * accx;
             }
-            accz += (cnt[2] == 1 ? T(1) : T(iw.w[mz])) * accy;
+            accz += (cnt[2] == 1 ? 1.0 : sw[mz]) * accy;
         }
         Ab[t] = accz;
     }
@@ -157,7 +184,19 @@ __global__ void k_ghost_fill(T* __restrict__ A, int g, const T* __restrict__ Ac,
 void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk, LevelView lkm1, int n, int M,
                        bool zero_outside, cudaStream_t s) {
     if (lk.nb == 0) return;
-    k_ghost_fill<double><<<lk.nb, 256, 0, s>>>(A, g, Ac, gc, lk, lkm1, n, interp_weights(M), zero_outside);
+    const InterpW iw = interp_weights(M);
+    const int PL = n / 2 + g + iw.I + 1;
+    const size_t sm = sizeof(double) * PL * PL * PL;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ghost_fill<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_ghost_fill<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_ghost_fill<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        attr = true;
+    }
+    if (iw.I == 4) k_ghost_fill<4><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
+    if (iw.I == 6) k_ghost_fill<6><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
+    if (iw.I == 8) k_ghost_fill<8><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
 }
 
 // ----------------------------------------------------------------------------
@@ -253,164 +292,85 @@ void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int 
 }
 
 // ----------------------------------------------------------------------------
-// One Gauss-Seidel iteration (Sec. 3.1) on every block: the block with its
-// frozen ghost layer is staged in shared memory, nodes are updated colour by
-// colour (c = (x&1) + 2(y&1) + 4(z&1), c = 0..7) with
-//   u <- (den h^2 f - offcentre) / c,
-// the same-colour nodes of one colour being independent for a 27-point stencil.
-template <int M, typename T>
-__global__ void k_smooth(T* __restrict__ U, const T* __restrict__ F, int n, T h2den) {
-    extern __shared__ unsigned char smem_raw[];
-    T* s = reinterpret_cast<T*>(smem_raw);
-    const int S = n + 2, S2 = S * S, S3 = S2 * S;
-    const int b = blockIdx.x;
-    T* Ub = U + (size_t)b * S3;
-    const T* Fb = F + (size_t)b * n * n * n;
-    for (int t = threadIdx.x; t < S3; t += blockDim.x) s[t] = Ub[t];
-    __syncthreads();
-    const int h = n >> 1, h3 = h * h * h;
-    const T inv_c = T(1) / T(LhsW<M>::c);
-    for (int col = 0; col < 8; ++col) {
-        const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
-        for (int q = threadIdx.x; q < h3; q += blockDim.x) {
-            const int x = 2 * (q % h) + cx, y = 2 * ((q / h) % h) + cy, z = 2 * (q / (h * h)) + cz;
-            const int o = ((z + 1) * S + y + 1) * S + x + 1;
-            s[o] = (h2den * Fb[(z * n + y) * n + x] - offcentre<M>(s, o, S, S2)) * inv_c;
-        }
-        __syncthreads();
-    }
-    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 1) * S + y + 1) * S + x + 1;
-        Ub[o] = s[o];
-    }
-}
-
-template <typename T>
-static void smooth_attributes() {
-    static bool done = false;
-    if (done) return;
-    const int mx = MAX_DYN_SMEM;
-    cudaFuncSetAttribute(k_smooth<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_smooth<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_smooth<6, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    done = true;
-}
-
-template <typename T>
-void launch_smooth(T* U, const T* F, int nb, int n, int M, double h2, cudaStream_t s) {
-    if (nb == 0) return;
-    smooth_attributes<T>();
-    const size_t sm = sizeof(T) * (n + 2) * (n + 2) * (n + 2);
-    if (M == 2) k_smooth<2, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LhsW<2>::den));
-    if (M == 4) k_smooth<4, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LhsW<4>::den));
-    if (M == 6) k_smooth<6, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LhsW<6>::den));
-}
-template void launch_smooth<double>(double*, const double*, int, int, int, double, cudaStream_t);
-template void launch_smooth<float>(float*, const float*, int, int, int, double, cudaStream_t);
-
-// ----------------------------------------------------------------------------
-// r = f - L u on every node of every block (Alg. 1).
-template <int M, typename T>
-__global__ void k_residual(T* __restrict__ R, const T* __restrict__ U, const T* __restrict__ F, int n, T scale) {
-    const int S = n + 2, S2 = S * S;
-    const int b = blockIdx.x;
-    const T* Ub = U + (size_t)b * S2 * S;
-    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 1) * S + y + 1) * S + x + 1;
-        R[(size_t)b * n * n * n + t] = F[(size_t)b * n * n * n + t] - scale * lhs_scaled<M>(Ub, o, S, S2);
-    }
-}
-
-template <typename T>
-void launch_residual(T* R, const T* U, const T* F, int nb, int n, int M, double inv_h2, cudaStream_t s) {
-    if (nb == 0) return;
-    if (M == 2) k_residual<2, T><<<nb, 256, 0, s>>>(R, U, F, n, T(inv_h2 / LhsW<2>::den));
-    if (M == 4) k_residual<4, T><<<nb, 256, 0, s>>>(R, U, F, n, T(inv_h2 / LhsW<4>::den));
-    if (M == 6) k_residual<6, T><<<nb, 256, 0, s>>>(R, U, F, n, T(inv_h2 / LhsW<6>::den));
-}
-template void launch_residual<double>(double*, const double*, const double*, int, int, int, double, cudaStream_t);
-template void launch_residual<float>(float*, const float*, const float*, int, int, int, double, cudaStream_t);
-
-// ----------------------------------------------------------------------------
 // Restriction from level k to the covered blocks of level k-1 (Alg. 1):
 // u_{k-1} = injection of u_k;  r_{k-1} = full weighting (1/4)[1 2 1]^3 of r_k,
 // or injection where the 27-point stencil reaches outside Omega_k.  The
-// restricted residual is left in F_{k-1}; k_fas_snapshot adds L u_{k-1}.
+// restricted residual is left in F_{k-1}; the FAS kernel adds L u_{k-1}.
+// One CTA per level-k block B computes the (n/2)^3 coarse nodes whose fine
+// image 2X lies in B: it stages r_k on B's nodes and on the planes just below
+// them (local coordinates -1 .. n-1, from the lower neighbours); the window
+// of X is complete when those neighbours exist along the axes where 2X sits
+// on B's lower face (the upper side always lies in B).
 template <typename T>
 __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __restrict__ Uf, const T* __restrict__ Rf,
-                           const int* __restrict__ cov, LevelView lc, LevelView lf, int n, const T* __restrict__ off) {
-    const int P = cov[blockIdx.x];
-    const int S = n + 2, S3 = S * S * S, n3 = n * n * n, h = n >> 1;
-    const int* kids = lc.children + 8 * P;
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int i = t % n, j = (t / n) % n, l = t / (n * n);
-        const int ox = i >= h, oy = j >= h, oz = l >= h;
-        const int c = kids[ox + 2 * oy + 4 * oz];
-        const int fx = 2 * i - ox * n, fy = 2 * j - oy * n, fz = 2 * l - oz * n;
-        Uc[(size_t)P * S3 + ((l + 1) * S + j + 1) * S + i + 1] = Uf[(size_t)c * S3 + ((fz + 1) * S + fy + 1) * S + fx + 1]
-                                                               + (off ? off[(size_t)P * n3 + t] : T(0));
-        const int* cn = lf.nbr + 27 * c;
-        T acc = T(0);
-        bool inside = true;
-        for (int dz = -1; dz <= 1 && inside; ++dz) {
-            const int zz = fz + dz, ez = zz < 0 ? -1 : 0;
-            T accy = T(0);
-            for (int dy = -1; dy <= 1 && inside; ++dy) {
-                const int yy = fy + dy, ey = yy < 0 ? -1 : 0;
-                T accx = T(0);
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int xx = fx + dx, ex = xx < 0 ? -1 : 0;
-                    const int blk = cn[dir27(ex, ey, ez)];
-                    if (blk < 0) { inside = false; break; }
-                    const T v = Rf[(size_t)blk * n3 + ((zz - ez * n) * n + yy - ey * n) * n + xx - ex * n];
-                    accx += T(2 - (dx < 0 ? -dx : dx)) * v;
+                           LevelView lf, int n, const T* __restrict__ off) {
+    extern __shared__ __align__(16) unsigned char rs_raw[];
+    T* sr = reinterpret_cast<T*>(rs_raw);
+    __shared__ int nb27[27];
+    __shared__ int ins[8];
+    const int B = blockIdx.x;
+    if (threadIdx.x < 27) nb27[threadIdx.x] = lf.nbr[27 * B + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int m = threadIdx.x;
+        int ok = 1;
+        for (int sz = 0; sz <= ((m >> 2) & 1); ++sz)
+            for (int sy = 0; sy <= ((m >> 1) & 1); ++sy)
+                for (int sx = 0; sx <= (m & 1); ++sx)
+                    if (nb27[dir27(-sx, -sy, -sz)] < 0) ok = 0;
+        ins[m] = ok;
+    }
+    const int N1 = n + 1, N12 = N1 * N1, n3 = n * n * n, h = n >> 1;
+    for (int t = threadIdx.x; t < N12 * N1; t += blockDim.x) {
+        const int x = t % N1 - 1, y = (t / N1) % N1 - 1, z = t / N12 - 1;
+        const int ex = x < 0 ? -1 : 0, ey = y < 0 ? -1 : 0, ez = z < 0 ? -1 : 0;
+        const int blk = nb27[dir27(ex, ey, ez)];
+        sr[t] = blk >= 0 ? Rf[(size_t)blk * n3 + ((z - ez * n) * n + (y - ey * n)) * n + (x - ex * n)] : T(0);
+    }
+    __syncthreads();
+    const int P = lf.parent[B], o = lf.octant[B];
+    const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
+    const int S = n + 2, S3 = S * S * S;
+    for (int q = threadIdx.x; q < h * h * h; q += blockDim.x) {
+        const int i = q % h, j = (q / h) % h, l = q / (h * h);
+        const int fx = 2 * i, fy = 2 * j, fz = 2 * l;
+        const int cidx = ((oz + l) * n + oy + j) * n + ox + i;
+        Uc[(size_t)P * S3 + ((oz + l + 1) * S + oy + j + 1) * S + ox + i + 1] =
+            Uf[(size_t)B * S3 + ((fz + 1) * S + fy + 1) * S + fx + 1] + (off ? off[(size_t)P * n3 + cidx] : T(0));
+        const T* c = sr + ((fz + 1) * N1 + fy + 1) * N1 + fx + 1;
+        T v;
+        if (ins[(fx == 0) | ((fy == 0) << 1) | ((fz == 0) << 2)]) {
+            T acc = T(0);
+            for (int dz = -1; dz <= 1; ++dz) {
+                T accy = T(0);
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const T* r = c + dz * N12 + dy * N1;
+                    accy += T(2 - (dy < 0 ? -dy : dy)) * (r[-1] + T(2) * r[0] + r[1]);
                 }
-                accy += T(2 - (dy < 0 ? -dy : dy)) * accx;
+                acc += T(2 - (dz < 0 ? -dz : dz)) * accy;
             }
-            acc += T(2 - (dz < 0 ? -dz : dz)) * accy;
+            v = acc * T(1.0 / 64.0);
+        } else {
+            v = c[0];
         }
-        Fc[(size_t)P * n3 + t] = inside ? acc * T(1.0 / 64.0) : Rf[(size_t)c * n3 + (fz * n + fy) * n + fx];
+        Fc[(size_t)P * n3 + cidx] = v;
     }
 }
 
 template <typename T>
-void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, const int* cov, int ncov, LevelView lc, LevelView lf, int n,
-                     const T* off, cudaStream_t s) {
-    if (ncov == 0) return;
-    k_restrict<T><<<ncov, 256, 0, s>>>(Uc, Fc, Uf, Rf, cov, lc, lf, n, off);
-}
-template void launch_restrict<double>(double*, double*, const double*, const double*, const int*, int, LevelView, LevelView,
-                                      int, const double*, cudaStream_t);
-template void launch_restrict<float>(float*, float*, const float*, const float*, const int*, int, LevelView, LevelView,
-                                     int, const float*, cudaStream_t);
-
-// F += L u on covered blocks; u-hat = u on every block of the level (Alg. 1).
-template <int M, typename T>
-__global__ void k_fas_snapshot(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U, const uint8_t* __restrict__ is_leaf,
-                               int n, T scale) {
-    const int b = blockIdx.x;
-    const int S = n + 2, S2 = S * S, n3 = n * n * n;
-    const T* Ub = U + (size_t)b * S2 * S;
-    const bool cov = !is_leaf[b];
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 1) * S + y + 1) * S + x + 1;
-        if (cov) F[(size_t)b * n3 + t] += scale * lhs_scaled<M>(Ub, o, S, S2);
-        H[(size_t)b * n3 + t] = Ub[o];
+void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, LevelView lf, int n, const T* off, cudaStream_t s) {
+    if (lf.nb == 0) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        attr = true;
     }
+    const size_t sm = sizeof(T) * (n + 1) * (n + 1) * (n + 1);
+    k_restrict<T><<<lf.nb, 256, sm, s>>>(Uc, Fc, Uf, Rf, lf, n, off);
 }
-
-template <typename T>
-void launch_fas_snapshot(T* F, T* H, const T* U, const uint8_t* is_leaf, int nb, int n, int M, double inv_h2, cudaStream_t s) {
-    if (nb == 0) return;
-    if (M == 2) k_fas_snapshot<2, T><<<nb, 256, 0, s>>>(F, H, U, is_leaf, n, T(inv_h2 / LhsW<2>::den));
-    if (M == 4) k_fas_snapshot<4, T><<<nb, 256, 0, s>>>(F, H, U, is_leaf, n, T(inv_h2 / LhsW<4>::den));
-    if (M == 6) k_fas_snapshot<6, T><<<nb, 256, 0, s>>>(F, H, U, is_leaf, n, T(inv_h2 / LhsW<6>::den));
-}
-template void launch_fas_snapshot<double>(double*, double*, const double*, const uint8_t*, int, int, int, double, cudaStream_t);
-template void launch_fas_snapshot<float>(float*, float*, const float*, const uint8_t*, int, int, int, double, cudaStream_t);
+template void launch_restrict<double>(double*, double*, const double*, const double*, LevelView, int, const double*,
+                                      cudaStream_t);
+template void launch_restrict<float>(float*, float*, const float*, const float*, LevelView, int, const float*, cudaStream_t);
 
 // ----------------------------------------------------------------------------
 // Coarse-grid correction (Alg. 1): eps = u_{k-1} - uhat_{k-1} on the coarse

@@ -216,16 +216,7 @@ void graph_release(mrp_handle* H);
 template <typename T>
 void launch_inject_to_parent(T* coarse, int gc, const T* fine, int gf, LevelView fine_lv, int n, const T* off, cudaStream_t s);
 template <typename T>
-void launch_ghost_u(T* A, const T* Ac, LevelView lk, LevelView lkm1, int n, int M, cudaStream_t s);
-template <typename T>
-void launch_smooth(T* U, const T* F, int nb, int n, int M, double h2, cudaStream_t s);
-template <typename T>
-void launch_residual(T* R, const T* U, const T* F, int nb, int n, int M, double inv_h2, cudaStream_t s);
-template <typename T>
-void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, const int* cov, int ncov, LevelView lc, LevelView lf, int n,
-                     const T* off, cudaStream_t s);
-template <typename T>
-void launch_fas_snapshot(T* F, T* H, const T* U, const uint8_t* is_leaf, int nb, int n, int M, double inv_h2, cudaStream_t s);
+void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, LevelView lf, int n, const T* off, cudaStream_t s);
 template <typename T>
 void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc, int n, cudaStream_t s);
 template <typename T>
@@ -262,6 +253,7 @@ void launch_stencil_T(double* out, const double* lam, double* fadd, const int* b
                       double inv_h2, cudaStream_t s);
 void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nblocks, int n, int M, cudaStream_t s);
 void launch_ghost_T(double* A, int g, double* Ac, int gc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
+void launch_ghost_T_fused(double* A, double* Ac, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
 void launch_inject_T(double* fine, int gf, double* coarse, int gc, LevelView lf, int n, cudaStream_t s);
 void launch_smooth_T(double* U, double* F, int nb, int n, int M, double h2, cudaStream_t s);
 void launch_prolong_T(double* Uc, double* Hc, const double* Uf, LevelView lf, LevelView lc, int n, cudaStream_t s);

@@ -401,12 +401,14 @@ static void ghost_u(Handle& h, int k, cudaStream_t s) {
 }
 
 template <typename T> static constexpr int pidx() { return sizeof(T) == 4 ? 1 : 0; }
+// Launches of a fused stencil kernel on a level.
+static int fused_launches(const Level& lv) { return lv.nb > 0 ? 1 : 0; }
 
 // One Gauss-Seidel sweep with its ghost layer built in the kernel; reads the
 // current buffer, writes the other, then the two swap.
 template <typename T>
 static void smooth(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h), 1);
+    PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h), fused_launches(h.lv[k]));
     const double hk = level_h(h, k);
     launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
                            view_or_empty(h, k - 1), h.n, h.M, hk * hk, h.nt_smooth[pidx<T>()][k], s);
@@ -415,7 +417,7 @@ static void smooth(Handle& h, int k, cudaStream_t s) {
 
 template <typename T>
 static void residual(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, ph<T>(PH_RESIDUAL), h.lv[k].nb * n3(h), 1);
+    PhaseScope ps(h, s, ph<T>(PH_RESIDUAL), h.lv[k].nb * n3(h), fused_launches(h.lv[k]));
     const double hk = level_h(h, k);
     launch_residual_fused<T>(fld<T>(h, k).R, ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
                              view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.nt_res[pidx<T>()][k], s);
@@ -426,11 +428,11 @@ template <typename T>
 static void restrict_level(Handle& h, int k, cudaStream_t s) {
     Level& c = h.lv[k - 1];
     {
-        PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.ncov * n3(h), c.ncov > 0 ? 1 : 0);
-        launch_restrict<T>(ucur<T>(h, k - 1), fld<T>(h, k - 1).F, ucur<T>(h, k), fld<T>(h, k).R, c.cov_blocks, c.ncov,
-                           c.view(), h.lv[k].view(), h.n, k == 1 ? off0<T>(h) : nullptr, s);
+        PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.ncov * n3(h), h.lv[k].nb > 0 ? 1 : 0);
+        launch_restrict<T>(ucur<T>(h, k - 1), fld<T>(h, k - 1).F, ucur<T>(h, k), fld<T>(h, k).R, h.lv[k].view(), h.n,
+                           k == 1 ? off0<T>(h) : nullptr, s);
     }
-    PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.nb * n3(h), 1);
+    PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.nb * n3(h), fused_launches(c));
     const double hk = level_h(h, k - 1);
     launch_fas_fused<T>(fld<T>(h, k - 1).F, fld<T>(h, k - 1).H, ucur<T>(h, k - 1), ucoarse<T>(h, k - 1), c.view(),
                         view_or_empty(h, k - 2), h.n, h.M, 1.0 / (hk * hk), h.nt_fas[pidx<T>()][k - 1], s);
@@ -513,14 +515,14 @@ struct SolveState {
 };
 
 // CTA size of each fused stencil kernel, per precision and level: the fastest
-// of 128, 256, 512 and 1024 threads on the level's own block pool (few blocks
+// of 128, 256 and 512 threads on the level's own block pool (few blocks
 // favour large CTAs, which shorten the serial colour sweeps of one block;
 // many blocks favour smaller ones).  The timed launches write only scratch
 // that every solve overwrites before reading (the other ping-pong buffer, R,
 // and F, H of covered blocks).
 template <typename T>
 static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
-    const int cand[4] = {128, 256, 512, 1024};
+    const int cand[3] = {128, 256, 512};
     constexpr int pi = pidx<T>();
     auto pick = [&](auto&& launch) {
         float best = 1e30f;
