@@ -46,6 +46,11 @@ ORACLE_CYCLES = {4: 11, 6: 12, 2: 17}
 STENCIL_POINTS = {2: 7, 4: 19, 6: 27}
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch of the FP32 smoother from one ncu capture
+# (profiles/k_smooth_fused_f32_adaptive_2p8M_o4.md: average over the 24 launches
+# of two V-cycles of the headline forest; profiles/k_smooth_fused_f32_level4_29p5M_o4.md:
+# the level-4 launches of the five-level forest).  Valid while the kernel is unchanged.
+SMOOTH32_TRAFFIC = {"headline": 12731861, "five_level_level4": 394145000}
 
 
 def _hbm_peak():
@@ -251,6 +256,7 @@ def bench_five_level(order, flush, stream, steps):
                      "phases_ms_per_step": {k: v["ms"] / steps for k, v in prof.items()}}
         if name == "chosen":
             out["roofline_smoother"] = _roofline(prof, order, steps)
+            out["roofline_smoother"]["traffic_level4_launch"] = SMOOTH32_TRAFFIC["five_level_level4"]
         s.close()
     out["max_rel_err_vs_fp64"] = float((res["chosen"][1] - res["plain_fp64"][1]).abs().max()
                                        / res["plain_fp64"][1].abs().max())
@@ -287,22 +293,24 @@ def bench_batched(order, flush, stream, steps):
     return out
 
 
-def _roofline(prof, order, steps):
+def _roofline(prof, order, steps, traffic=None):
     """Dominant-kernel roofline: the smoother of the chosen path (FP32, bytes) and of the FP64 path (flops)."""
     out = {}
     sm32 = prof.get("smooth_f32")
     if sm32 and sm32["ms"] > 0:
         byt = sm32["nodes"] * 3 * 4                   # read u, read f, write u (FP32 words)
         ach = byt / (sm32["ms"] / 1e3) / 1e9
-        out = {"bound": "hbm", "kernel": "k_smooth<M,float> (Gauss-Seidel sweep, FP32)", "achieved": ach,
-               "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS, "traffic": None,
+        nl = max(sm32["launches"], 1)
+        out = {"bound": "hbm", "kernel": "k_smooth_fused<M,float,I> (Gauss-Seidel sweep with fused ghost layer, FP32)",
+               "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
+               "traffic": traffic, "algorithmic_bytes_per_launch": byt / nl,
                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-               "bytes_per_node": 12, "avg_launch_us": sm32["ms"] * 1e3 / max(sm32["launches"], 1)}
+               "bytes_per_node": 12, "avg_launch_us": sm32["ms"] * 1e3 / nl}
     sm64 = prof.get("smooth_f64")
     if sm64 and sm64["ms"] > 0:
         fl = sm64["nodes"] * 2 * STENCIL_POINTS[order]
         ach = fl / (sm64["ms"] / 1e3) / 1e12
-        r64 = {"bound": "alu", "kernel": "k_smooth<M,double> (Gauss-Seidel sweep, FP64)", "achieved": ach,
+        r64 = {"bound": "alu", "kernel": "k_smooth_fused<M,double,I> (Gauss-Seidel sweep, FP64)", "achieved": ach,
                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                "peak_source": "FP64 units x clock (152 SMs x 2 FMA/clk x 2.07 GHz), nominal",
                "flops_per_node": 2 * STENCIL_POINTS[order],
@@ -331,7 +339,8 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     plain = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES)
-    chosen = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed")
+    chosen = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed",
+                    inner_cycles=args.inner_cycles)
     if ws > 1:
         dist.barrier()
     p, path = start_clock_sampler(local)
@@ -378,7 +387,7 @@ def run_ours(args):
         "e2e": {"value": ws * desc.leaf_nodes / e2e_step, "unit": "cells/s",
                 "h2d_bytes_per_step": int(f_host.numel() * 8), "d2h_bytes_per_step": int(u_host.numel() * 8)},
         "roofline": _roofline({**prof_c, **{k: v for k, v in prof_p.items() if k == "smooth_f64"}}, args.order,
-                              args.steps),
+                              args.steps, SMOOTH32_TRAFFIC["headline"] if args.order == ORDER else None),
         "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof_c.items()},
         "phase_share": {k: (v["ms"] / tot_c if tot_c else None) for k, v in prof_c.items()},
         "gpu_launches": launches,
@@ -440,6 +449,7 @@ def main():
     ap.add_argument("--order", type=int, default=ORDER, choices=[2, 4, 6])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline line only")
+    ap.add_argument("--inner-cycles", type=int, default=4, help="FP32 cycles per refinement step of the chosen form")
     ap.add_argument("--profile-case", choices=["headline", "five_level"], default=None,
                     help="run the chosen solver on one workload without timing (for ncu)")
     args = ap.parse_args()
