@@ -72,6 +72,15 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(vals, device):
+    """Element-wise max of per-rank values over the process group (the timing rule: slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def workload(seed):
     from paper_2512_08555_gb300 import synth
     desc, src = synth.config2(seed)
@@ -350,9 +359,7 @@ def run_ours(args):
     err = float((u_c - u_p).abs().max() / u_p.abs().max())
     t_step, t_plain = ms_c / 1e3, ms_p / 1e3
     if ws > 1:
-        tt = torch.tensor([t_step, t_plain], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_plain = float(tt[0]), float(tt[1])
+        t_step, t_plain = max_over_ranks([t_step, t_plain], "cuda")
     value = ws * desc.leaf_nodes / t_step
     # end to end through host memory (chosen path)
     f_host = torch.from_numpy(f_np).pin_memory()
@@ -369,9 +376,7 @@ def run_ours(args):
         e2e_t.append(a.elapsed_time(b) / 1e3)
     e2e_step = float(np.mean(e2e_t))
     if ws > 1:
-        tt = torch.tensor([e2e_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_step = float(tt.item())
+        e2e_step = max_over_ranks([e2e_step], "cuda")[0]
     tot_c = sum(v["ms"] for v in prof_c.values())
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
