@@ -224,20 +224,27 @@ def _time_calls(fn, steps, warmup, flush, stream):
 
 
 def bench_adjoint(desc, f, u_plain, ms_plain, order, flush, stream, steps):
-    """Gradient of <w, u> for a seeded Gaussian weight w, FP64, on the headline forest."""
+    """Gradient of <w, u> for a seeded Gaussian weight w on the headline forest, chosen and plain FP64."""
     import torch
     from paper_2512_08555_gb300 import synth
     from paper_2512_08555_gb300.mrp import Solver
-    s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES)
     w = torch.from_numpy(synth.sample_leaves(desc, synth.gaussian_weight(0))).cuda()
-    ms, (g, st) = _time_calls(lambda: s.solve_adjoint(w), steps, 3, flush, stream)
-    a = float((w * u_plain).sum())
-    b = float((g * f).sum())
-    out = {"what": "f-bar = S^T w, FP64 refinement with transposed correction V-cycles",
-           "ms_per_gradient": ms, "transposed_cycles": int(st.cycles), "final_rel_residual": float(st.residual),
-           "ratio_to_plain_fp64_forward": ms / ms_plain,
-           "dot_identity_rel": abs(a - b) / abs(a), "launches_per_gradient": int(st.launches)}
-    s.close()
+    out = {"what": "f-bar = S^T w: FP64 refinement lambda += M^T (E^T w - K^T lambda) with transposed V-cycles M^T"}
+    grads = {}
+    for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
+        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec)
+        ms, (g, st) = _time_calls(lambda: s.solve_adjoint(w), steps, 3, flush, stream)
+        grads[name] = g.clone()
+        a = float((w * u_plain).sum())
+        b = float((g * f).sum())
+        out[name] = {"ms_per_gradient": ms, "transposed_cycles": int(st.cycles), "final_rel_residual": float(st.residual),
+                     "ratio_to_plain_fp64_forward": ms / ms_plain, "dot_identity_rel": abs(a - b) / abs(a),
+                     "launches_per_gradient": int(st.launches)}
+        s.close()
+    out["chosen"]["cycles_precision"] = "FP32 transposed cycles"
+    out["plain_fp64"]["cycles_precision"] = "FP64 transposed cycles"
+    out["max_rel_diff_chosen_vs_fp64"] = float((grads["chosen"] - grads["plain_fp64"]).abs().max()
+                                               / grads["plain_fp64"].abs().max())
     return out
 
 
@@ -266,6 +273,12 @@ def bench_five_level(order, flush, stream, steps):
         if name == "chosen":
             out["roofline_smoother"] = _roofline(prof, order, steps)
             out["roofline_smoother"]["traffic_level4_launch"] = SMOOTH32_TRAFFIC["five_level_level4"]
+            w = torch.from_numpy(synth.sample_leaves(desc, synth.gaussian_weight(0))).cuda()
+            msg, (g, stg) = _time_calls(lambda: s.solve_adjoint(w), steps, 1, flush, stream)
+            out["gradient_chosen"] = {"ms_per_gradient": msg, "transposed_cycles": int(stg.cycles),
+                                      "final_rel_residual": float(stg.residual),
+                                      "dot_identity_rel": abs(float((w * u).sum()) - float((g * f).sum()))
+                                      / abs(float((w * u).sum()))}
         s.close()
     out["max_rel_err_vs_fp64"] = float((res["chosen"][1] - res["plain_fp64"][1]).abs().max()
                                        / res["plain_fp64"][1].abs().max())

@@ -56,48 +56,90 @@ int adjoint_setup(Handle& h) {
     if ((rc = adj_alloc(h.cube, C))) return rc;
     if ((rc = adj_alloc(h.dense, D))) return rc;
     if ((rc = adj_alloc(h.off0b, (size_t)h.lv[0].nb * nn))) return rc;
+    if (h.mixed) {
+        auto alloc32 = [](float*& p, size_t count) {
+            if (cudaMalloc(&p, sizeof(float) * (count ? count : 1)) != cudaSuccess) return MRP_ERR_OOM;
+            return cudaMemset(p, 0, sizeof(float) * (count ? count : 1)) == cudaSuccess ? MRP_OK : MRP_ERR_CUDA;
+        };
+        h.adj32.resize(h.L + 1);
+        for (int k = 0; k <= h.L; ++k) {
+            const size_t nb = h.lv[k].nb;
+            Handle::AdjLevel32& a = h.adj32[k];
+            if ((rc = alloc32(a.Ub, nb * S * S * S))) return rc;
+            if ((rc = alloc32(a.Fb, nb * nn))) return rc;
+            if ((rc = alloc32(a.Rb, nb * nn))) return rc;
+            if ((rc = alloc32(a.Hb, nb * nn))) return rc;
+        }
+        if ((rc = alloc32(h.cube32, C))) return rc;
+        if ((rc = alloc32(h.dense32, D))) return rc;
+        if ((rc = alloc32(h.off0b32, (size_t)h.lv[0].nb * nn))) return rc;
+    }
     return MRP_OK;
 }
 
 void adjoint_release(Handle& h) {
     for (auto& a : h.adj) { cudaFree(a.Ub); cudaFree(a.Fb); cudaFree(a.Rb); cudaFree(a.Hb); cudaFree(a.Rawb); }
     h.adj.clear();
+    for (auto& a : h.adj32) { cudaFree(a.Ub); cudaFree(a.Fb); cudaFree(a.Rb); cudaFree(a.Hb); }
+    h.adj32.clear();
+    for (float* p : {h.cube32, h.dense32, h.off0b32}) cudaFree(p);
+    h.cube32 = h.dense32 = h.off0b32 = nullptr;
     for (double* p : {h.lam, h.rho, h.gvec, h.xb, h.fsb, h.wl, h.cube, h.dense, h.off0b}) cudaFree(p);
     h.lam = h.rho = h.gvec = h.xb = h.fsb = h.wl = h.cube = h.dense = h.off0b = nullptr;
 }
 
 static size_t xlen(const Handle& h) { return h.xoff[h.L + 1]; }
+template <typename T = double>
 static size_t box_bytes(const Handle& h, int k, int g) {
     const size_t S = h.n + 2 * g;
-    return sizeof(double) * h.lv[k].nb * S * S * S;
+    return sizeof(T) * h.lv[k].nb * S * S * S;
+}
+
+// Per-level adjoint fields and level-0 scratch of one working precision.
+template <typename T> struct AdjF { T *Ub, *Fb, *Rb, *Hb; };
+template <typename T> static AdjF<T> af(Handle& h, int k) {
+    if constexpr (sizeof(T) == 8) return AdjF<T>{h.adj[k].Ub, h.adj[k].Fb, h.adj[k].Rb, h.adj[k].Hb};
+    else return AdjF<T>{h.adj32[k].Ub, h.adj32[k].Fb, h.adj32[k].Rb, h.adj32[k].Hb};
+}
+template <typename T> static T* cube_of(Handle& h) {
+    if constexpr (sizeof(T) == 8) return h.cube; else return h.cube32;
+}
+template <typename T> static T* dense_of(Handle& h) {
+    if constexpr (sizeof(T) == 8) return h.dense; else return h.dense32;
+}
+template <typename T> static T* off0b_of(Handle& h) {
+    if constexpr (sizeof(T) == 8) return h.off0b; else return h.off0b32;
 }
 
 // Transpose of the ghost fill of level k (u layout, halo 1), including the
 // injection of level k into the covered level-(k-1) nodes that precedes it.
+template <typename T>
 static void ghost_fill_T(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_GHOST, h.lv[k].nb * n3(h), k >= 1 ? 2 : 1);
-    launch_ghost_T_fused(h.adj[k].Ub, k >= 1 ? h.adj[k - 1].Ub : nullptr, h.lv[k].view(), view_or_empty(h, k - 1), h.n,
-                         h.M, s);
-    if (k >= 1) launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, h.lv[k].view(), h.n, s);
+    PhaseScope ps(h, s, ph<T>(PH_GHOST), h.lv[k].nb * n3(h), k >= 1 ? 2 : 1);
+    launch_ghost_T_fused<T>(af<T>(h, k).Ub, k >= 1 ? af<T>(h, k - 1).Ub : nullptr, h.lv[k].view(),
+                            view_or_empty(h, k - 1), h.n, h.M, s);
+    if (k >= 1) launch_inject_T<T>(af<T>(h, k).Ub, 1, af<T>(h, k - 1).Ub, 1, h.lv[k].view(), h.n, s);
 }
 
 // Transpose of problem p's level-0 convolution read on its level-0 boxes:
 // the adjoint of every box (interior and exterior ring) -> the dense source
-// adjoint h.dense of that problem.
-static void conv_T(Handle& h, const Problem& p, const double* U0bar, cudaStream_t s) {
-    PhaseScope ps(h, s, PH_COARSE, (int64_t)p.n0[0] * p.n0[1] * p.n0[2], 6);
+// adjoint of that problem.
+template <typename T>
+static void conv_T(Handle& h, const Problem& p, const T* U0bar, cudaStream_t s) {
+    PhaseScope ps(h, s, ph<T>(PH_COARSE), (int64_t)p.n0[0] * p.n0[1] * p.n0[2], 6);
     const size_t S = h.n + 2;
-    launch_window_T(h.cube, U0bar + (size_t)p.base0 * S * S * S, h.n, p.nb0, s);
-    launch_conv_transpose(h, p, h.cube, h.dense, s);
+    launch_window_T<T>(cube_of<T>(h), U0bar + (size_t)p.base0 * S * S * S, h.n, p.nb0, s);
+    launch_conv_transpose<T>(h, p, cube_of<T>(h), dense_of<T>(h), s);
 }
 
-// h.dense of problem p -> per-block arrays of its covered (cov = true) or leaf
-// level-0 blocks, added or set.
-static void dense_to(Handle& h, const Problem& p, double* out, bool cov, bool add, cudaStream_t s) {
+// The dense source adjoint of problem p -> per-block arrays of its covered
+// (cov = true) or leaf level-0 blocks, added or set.
+template <typename T>
+static void dense_to(Handle& h, const Problem& p, T* out, bool cov, bool add, cudaStream_t s) {
     const Level& l0 = h.lv[0];
     const int* list = cov ? l0.cov_blocks + p.cov0_lo : l0.leaf_blocks + p.leaf0_lo;
     const int cnt = cov ? p.cov0_hi - p.cov0_lo : p.leaf0_hi - p.leaf0_lo;
-    launch_dense_to_blocks(out, h.dense, list, cnt, l0.coords, h.n, p.n0, add, s);
+    launch_dense_to_blocks<T>(out, dense_of<T>(h), list, cnt, l0.coords, h.n, p.n0, add, s);
 }
 
 // res^T lambda -> x-bar (into xb); with fsb, also adds c^T lambda (the f*-bar
@@ -119,16 +161,16 @@ static void res_T(Handle& h, const double* lam, double* xb, double* fsb, cudaStr
         }
     }
     // the ghost fills of levels L..1 (each with its injection), reversed
-    for (int k = 1; k <= L; ++k) ghost_fill_T(h, k, s);
+    for (int k = 1; k <= L; ++k) ghost_fill_T<double>(h, k, s);
     {
         PhaseScope ps(h, s, PH_OTHER, l0.ncov * n3(h), 1);
         launch_interior_add(h.adj[0].Ub, 1, lam + h.xoff[0], l0.cov_blocks, l0.ncov, n, ih02, s);
     }
     for (const Problem& p : h.pr) {
-        conv_T(h, p, h.adj[0].Ub, s);
+        conv_T<double>(h, p, h.adj[0].Ub, s);
         PhaseScope ps(h, s, PH_OTHER, (int64_t)l0.nb * n3(h), fsb ? 2 : 1);
-        dense_to(h, p, xb + h.xoff[0], true, false, s);
-        if (fsb) dense_to(h, p, fsb + h.xoff[0], false, true, s);
+        dense_to<double>(h, p, xb + h.xoff[0], true, false, s);
+        if (fsb) dense_to<double>(h, p, fsb + h.xoff[0], false, true, s);
     }
     {
         PhaseScope ps(h, s, PH_OTHER, h.total_nodes, L + (L >= 2 ? L - 1 : 0));
@@ -157,10 +199,10 @@ static void out_T(Handle& h, const double* w, cudaStream_t s) {
         launch_interior_add(h.adj[0].Ub, 1, h.wl, l0.leaf_blocks, l0.nleaf, n, 1.0, s);
     }
     for (const Problem& p : h.pr) {
-        conv_T(h, p, h.adj[0].Ub, s);
+        conv_T<double>(h, p, h.adj[0].Ub, s);
         PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 2);
-        dense_to(h, p, h.gvec, true, false, s);
-        dense_to(h, p, h.fsb, false, false, s);
+        dense_to<double>(h, p, h.gvec, true, false, s);
+        dense_to<double>(h, p, h.fsb, false, false, s);
     }
 }
 
@@ -186,78 +228,81 @@ static void rhs_T(Handle& h, const double* fsb, double* fbar, cudaStream_t s) {
     launch_gather_leaves_from(h, fbar, lp, 2, true, s);
 }
 
-// M^T: the transposed correction V-cycle, x-space vector xin -> residual-space rout.
+// M^T: the transposed correction V-cycle in precision T (FP64, or FP32 on a
+// mixed-precision handle), x-space vector xin -> residual-space rout (both FP64).
+template <typename T>
 static void cycle_T(Handle& h, const double* xin, double* rout, cudaStream_t s) {
     const int L = h.L, n = h.n;
     Level& l0 = h.lv[0];
     for (int k = 0; k <= L; ++k) {
-        cudaMemsetAsync(h.adj[k].Ub, 0, box_bytes(h, k, 1), s);
-        cudaMemsetAsync(h.adj[k].Fb, 0, sizeof(double) * h.lv[k].nb * n3(h), s);
-        cudaMemsetAsync(h.adj[k].Hb, 0, sizeof(double) * h.lv[k].nb * n3(h), s);
+        cudaMemsetAsync(af<T>(h, k).Ub, 0, box_bytes<T>(h, k, 1), s);
+        cudaMemsetAsync(af<T>(h, k).Fb, 0, sizeof(T) * h.lv[k].nb * n3(h), s);
+        cudaMemsetAsync(af<T>(h, k).Hb, 0, sizeof(T) * h.lv[k].nb * n3(h), s);
     }
     {
-        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, L + 1);
+        PhaseScope ps(h, s, ph<T>(PH_OTHER), h.leaf_nodes, L + 1);
         for (int k = 1; k <= L; ++k)
-            launch_interior_add(h.adj[k].Ub, 1, xin + h.xoff[k], h.lv[k].leaf_blocks, h.lv[k].nleaf, n, 1.0, s);
-        launch_block_copy(h.adj[0].Fb, xin, l0.cov_blocks, l0.ncov, n, 1.0, s);
+            launch_interior_add<T, double>(af<T>(h, k).Ub, 1, xin + h.xoff[k], h.lv[k].leaf_blocks, h.lv[k].nleaf, n,
+                                           1.0, s);
+        launch_block_copy<T, double>(af<T>(h, 0).Fb, xin, l0.cov_blocks, l0.ncov, n, 1.0, s);
     }
     auto smooth_T = [&](int k) {
-        PhaseScope ps(h, s, PH_SMOOTH, h.lv[k].nb * n3(h), 1);
+        PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h), 1);
         const double hk = level_h(h, k);
-        launch_smooth_T(h.adj[k].Ub, h.adj[k].Fb, h.lv[k].nb, n, h.M, hk * hk, s);
+        launch_smooth_T<T>(af<T>(h, k).Ub, af<T>(h, k).Fb, h.lv[k].nb, n, h.M, hk * hk, s);
     };
     // coarse-to-fine half, reversed
     for (int k = L; k >= 1; --k) {
-        for (int i = 0; i < h.nu2; ++i) { smooth_T(k); ghost_fill_T(h, k, s); }
-        PhaseScope ps(h, s, PH_PROLONG, h.lv[k].nb * n3(h), 1);
-        launch_prolong_T(h.adj[k - 1].Ub, h.adj[k - 1].Hb, h.adj[k].Ub, h.lv[k].view(), h.lv[k - 1].view(), n, s);
+        for (int i = 0; i < h.nu2; ++i) { smooth_T(k); ghost_fill_T<T>(h, k, s); }
+        PhaseScope ps(h, s, ph<T>(PH_PROLONG), h.lv[k].nb * n3(h), 1);
+        launch_prolong_T<T>(af<T>(h, k - 1).Ub, af<T>(h, k - 1).Hb, af<T>(h, k).Ub, h.lv[k].view(), h.lv[k - 1].view(),
+                            n, s);
     }
     // level-0 solve: the source adjoint gains the convolution transpose of u_0's adjoint
     for (const Problem& p : h.pr) {
-        conv_T(h, p, h.adj[0].Ub, s);
-        PhaseScope ps(h, s, PH_COARSE, l0.nb * n3(h), 2);
-        dense_to(h, p, h.adj[0].Fb, true, true, s);
-        dense_to(h, p, h.adj[0].Fb, false, true, s);
+        conv_T<T>(h, p, af<T>(h, 0).Ub, s);
+        PhaseScope ps(h, s, ph<T>(PH_COARSE), l0.nb * n3(h), 2);
+        dense_to<T>(h, p, af<T>(h, 0).Fb, true, true, s);
+        dense_to<T>(h, p, af<T>(h, 0).Fb, false, true, s);
     }
-    cudaMemsetAsync(h.adj[0].Ub, 0, box_bytes(h, 0, 1), s);
+    cudaMemsetAsync(af<T>(h, 0).Ub, 0, box_bytes<T>(h, 0, 1), s);
     // fine-to-coarse half, reversed
     for (int k = 1; k <= L; ++k) {
         Level& c = h.lv[k - 1];
         Level& f = h.lv[k];
+        const AdjF<T> ac = af<T>(h, k - 1), a = af<T>(h, k);
         {
-            PhaseScope ps(h, s, PH_RESTRICT, c.nb * n3(h), 2);
+            PhaseScope ps(h, s, ph<T>(PH_RESTRICT), c.nb * n3(h), 2);
             const double hc = level_h(h, k - 1);
             // uhat_{k-1} = u_{k-1}; f_{k-1} += L u_{k-1} on covered blocks
-            launch_interior_add(h.adj[k - 1].Ub, 1, h.adj[k - 1].Hb, c.order, c.nb, n, 1.0, s);
-            cudaMemsetAsync(h.adj[k - 1].Hb, 0, sizeof(double) * c.nb * n3(h), s);
-            launch_stencil_T(h.adj[k - 1].Ub, h.adj[k - 1].Fb, nullptr, c.cov_blocks, c.ncov, n, h.M, 1.0 / (hc * hc), s);
+            launch_interior_add<T, T>(ac.Ub, 1, ac.Hb, c.order, c.nb, n, 1.0, s);
+            cudaMemsetAsync(ac.Hb, 0, sizeof(T) * c.nb * n3(h), s);
+            launch_stencil_T<T>(ac.Ub, ac.Fb, nullptr, c.cov_blocks, c.ncov, n, h.M, 1.0 / (hc * hc), s);
         }
-        ghost_fill_T(h, k - 1, s);
+        ghost_fill_T<T>(h, k - 1, s);
         {
-            PhaseScope ps(h, s, PH_RESTRICT, f.nb * n3(h), 3 + (k == 1 ? 1 : 0));
+            PhaseScope ps(h, s, ph<T>(PH_RESTRICT), f.nb * n3(h), 3 + (k == 1 ? 1 : 0));
             // f_{k-1} = FW r_k on covered blocks
-            launch_fw_T(h.adj[k].Rb, h.adj[k - 1].Fb, f.view(), n, s);
-            launch_block_zero(h.adj[k - 1].Fb, c.cov_blocks, c.ncov, n, s);
+            launch_fw_T<T>(a.Rb, ac.Fb, f.view(), n, s);
+            launch_block_zero<T>(ac.Fb, c.cov_blocks, c.ncov, n, s);
             // u_{k-1} = inject u_k (+ the level-0 offset carrying the covered level-0 rows)
-            if (k == 1) launch_interior_get(h.off0b, h.adj[0].Ub, 1, l0.cov_blocks, l0.ncov, n, 1.0, s);
-            launch_inject_T(h.adj[k].Ub, 1, h.adj[k - 1].Ub, 1, f.view(), n, s);
+            if (k == 1) launch_interior_get<T, T>(off0b_of<T>(h), af<T>(h, 0).Ub, 1, l0.cov_blocks, l0.ncov, n, 1.0, s);
+            launch_inject_T<T>(a.Ub, 1, ac.Ub, 1, f.view(), n, s);
         }
         {
-            PhaseScope ps(h, s, PH_RESIDUAL, f.nb * n3(h), 1);
+            PhaseScope ps(h, s, ph<T>(PH_RESIDUAL), f.nb * n3(h), 1);
             const double hk = level_h(h, k);
-            launch_stencil_T(h.adj[k].Ub, h.adj[k].Rb, h.adj[k].Fb, f.order, f.nb, n, h.M, -1.0 / (hk * hk), s);
+            launch_stencil_T<T>(a.Ub, a.Rb, a.Fb, f.order, f.nb, n, h.M, -1.0 / (hk * hk), s);
         }
-        ghost_fill_T(h, k, s);
-        for (int i = 0; i < h.nu1; ++i) { smooth_T(k); ghost_fill_T(h, k, s); }
+        ghost_fill_T<T>(h, k, s);
+        for (int i = 0; i < h.nu1; ++i) { smooth_T(k); ghost_fill_T<T>(h, k, s); }
     }
-    PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, L + 1);
+    PhaseScope ps(h, s, ph<T>(PH_OTHER), h.leaf_nodes, L + 1);
     for (int k = 1; k <= L; ++k)
-        launch_block_copy(rout + h.xoff[k], h.adj[k].Fb, h.lv[k].leaf_blocks, h.lv[k].nleaf, n, 1.0, s);
-    launch_block_copy(rout, h.off0b, l0.cov_blocks, l0.ncov, n, -h.h0 * h.h0, s);
+        launch_block_copy<double, T>(rout + h.xoff[k], af<T>(h, k).Fb, h.lv[k].leaf_blocks, h.lv[k].nleaf, n, 1.0, s);
+    launch_block_copy<double, T>(rout, off0b_of<T>(h), l0.cov_blocks, l0.ncov, n, -h.h0 * h.h0, s);
 }
 
-// The whole gradient.  Returns MRP_OK, MRP_ERR_NOT_CONVERGED (fbar still
-// written) or an error status.
 // Per-problem max |v| over an unknown-space vector into slot 2.
 static void xnorm_launch(Handle& h, const double* v, cudaStream_t s) {
     cudaMemsetAsync(h.slot(2), 0, sizeof(unsigned long long) * h.nprob(), s);
@@ -287,7 +332,8 @@ int solve_adjoint(Handle& h, const double* w, double* fbar, cudaStream_t s, int*
     double rel = worst(gmax);
     int cycles = 0;
     while (rel >= h.tol && cycles < h.max_cycles) {
-        cycle_T(h, h.rho, h.xb, s);
+        if (h.mixed) cycle_T<float>(h, h.rho, h.xb, s);
+        else cycle_T<double>(h, h.rho, h.xb, s);
         ++cycles;
         {
             PhaseScope ps(h, s, PH_NORM, (int64_t)len, 1);
@@ -323,7 +369,7 @@ int adjoint_op(Handle& h, int op, const double* in, double* out, cudaStream_t s)
         case MRP_ADJ_CYCLE_T:
             cudaMemcpyAsync(h.rho, in, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
             cudaMemsetAsync(h.xb, 0, sizeof(double) * len, s);
-            cycle_T(h, h.rho, h.xb, s);
+            cycle_T<double>(h, h.rho, h.xb, s);
             cudaMemcpyAsync(out, h.xb, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
             break;
         case MRP_ADJ_RES_T:

@@ -49,15 +49,15 @@ __device__ __forceinline__ double rhs_weight(int dx, int dy, int dz) {
 // out[b] (halo layout, g = 1) += scale * L^T lam[b] on the listed blocks: every
 // node q of the (n+2)^3 box gathers the weights of the interior rows p with
 // |p - q| <= 1.  With fadd, also fadd[b] += lam[b] (the f-part of r = f - L u).
-template <int M>
-__global__ void k_stencil_T(double* __restrict__ out, const double* __restrict__ lam, double* __restrict__ fadd,
-                            const int* __restrict__ blocks, int n, double scale) {
+template <int M, typename T>
+__global__ void k_stencil_T(T* __restrict__ out, const T* __restrict__ lam, T* __restrict__ fadd,
+                            const int* __restrict__ blocks, int n, T scale) {
     const int b = blocks[blockIdx.x];
     const int S = n + 2, S3 = S * S * S, n3 = n * n * n;
-    const double* lb = lam + (size_t)b * n3;
+    const T* lb = lam + (size_t)b * n3;
     for (int t = threadIdx.x; t < S3; t += blockDim.x) {
         const int qx = t % S - 1, qy = (t / S) % S - 1, qz = t / (S * S) - 1;   // interior coordinates of q
-        double acc = 0.0;
+        T acc = T(0);
         for (int dz = -1; dz <= 1; ++dz) {
             const int pz = qz + dz;
             if (pz < 0 || pz >= n) continue;
@@ -67,8 +67,8 @@ __global__ void k_stencil_T(double* __restrict__ out, const double* __restrict__
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int px = qx + dx;
                     if (px < 0 || px >= n) continue;
-                    const double w = lhs_w<M>((dx != 0) + (dy != 0) + (dz != 0));
-                    if (w != 0.0) acc += w * lb[(pz * n + py) * n + px];
+                    const T w = T(lhs_w<M>((dx != 0) + (dy != 0) + (dz != 0)));
+                    if (w != T(0)) acc += w * lb[(pz * n + py) * n + px];
                 }
             }
         }
@@ -78,13 +78,16 @@ __global__ void k_stencil_T(double* __restrict__ out, const double* __restrict__
         for (int t = threadIdx.x; t < n3; t += blockDim.x) fadd[(size_t)b * n3 + t] += lb[t];
 }
 
-void launch_stencil_T(double* out, const double* lam, double* fadd, const int* blocks, int nblocks, int n, int M,
-                      double inv_h2, cudaStream_t s) {
+template <typename T>
+void launch_stencil_T(T* out, const T* lam, T* fadd, const int* blocks, int nblocks, int n, int M, double inv_h2,
+                      cudaStream_t s) {
     if (nblocks == 0) return;
-    if (M == 2) k_stencil_T<2><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, inv_h2 / LWa<2>::den);
-    if (M == 4) k_stencil_T<4><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, inv_h2 / LWa<4>::den);
-    if (M == 6) k_stencil_T<6><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, inv_h2 / LWa<6>::den);
+    if (M == 2) k_stencil_T<2, T><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<2>::den));
+    if (M == 4) k_stencil_T<4, T><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<4>::den));
+    if (M == 6) k_stencil_T<6, T><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<6>::den));
 }
+template void launch_stencil_T<double>(double*, const double*, double*, const int*, int, int, int, double, cudaStream_t);
+template void launch_stencil_T<float>(float*, const float*, float*, const int*, int, int, int, double, cudaStream_t);
 
 // out[b] (raw-f layout, g = 2) = R^T fsb[b] on the listed blocks.
 template <int M>
@@ -128,16 +131,17 @@ void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nb
 // it gathers -w_m / w_c times their adjoints; then the colour-c nodes pass
 // den h^2 / w_c of their adjoint to f and clear it.  The halo accumulates too
 // (it is scattered afterwards by the ghost transpose).
-template <int M>
-__global__ void k_smooth_T(double* __restrict__ U, double* __restrict__ F, int n, double h2den) {
-    extern __shared__ double su[];
+template <int M, typename T>
+__global__ void k_smooth_T(T* __restrict__ U, T* __restrict__ F, int n, T h2den) {
+    extern __shared__ __align__(16) unsigned char st_raw[];
+    T* su = reinterpret_cast<T*>(st_raw);
     const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n, h = n >> 1, h3 = h * h * h;
     const int b = blockIdx.x;
-    double* Ub = U + (size_t)b * S3;
-    double* Fb = F + (size_t)b * n3;
+    T* Ub = U + (size_t)b * S3;
+    T* Fb = F + (size_t)b * n3;
     for (int t = threadIdx.x; t < S3; t += blockDim.x) su[t] = Ub[t];
     __syncthreads();
-    const double inv_c = 1.0 / LWa<M>::c;
+    const T inv_c = T(1.0 / LWa<M>::c);
     for (int col = 7; col >= 0; --col) {
         const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
         for (int t = threadIdx.x; t < S3; t += blockDim.x) {
@@ -145,9 +149,9 @@ __global__ void k_smooth_T(double* __restrict__ U, double* __restrict__ F, int n
             const int mx = (qx & 1) != cx, my = (qy & 1) != cy, mz = (qz & 1) != cz;
             const int m = mx + my + mz;
             if (m == 0) continue;
-            const double w = lhs_w<M>(m);
-            if (w == 0.0) continue;
-            double acc = 0.0;
+            const T w = T(lhs_w<M>(m));
+            if (w == T(0)) continue;
+            T acc = T(0);
             for (int sz = -mz; sz <= mz; sz += 2) {
                 const int pz = qz + sz;
                 if (pz < 0 || pz >= n) continue;
@@ -168,27 +172,30 @@ __global__ void k_smooth_T(double* __restrict__ U, double* __restrict__ F, int n
             const int x = 2 * (q % h) + cx, y = 2 * ((q / h) % h) + cy, z = 2 * (q / (h * h)) + cz;
             const int o = ((z + 1) * S + y + 1) * S + x + 1;
             Fb[(z * n + y) * n + x] += h2den * inv_c * su[o];
-            su[o] = 0.0;
+            su[o] = T(0);
         }
         __syncthreads();
     }
     for (int t = threadIdx.x; t < S3; t += blockDim.x) Ub[t] = su[t];
 }
 
-void launch_smooth_T(double* U, double* F, int nb, int n, int M, double h2, cudaStream_t s) {
+template <typename T>
+void launch_smooth_T(T* U, T* F, int nb, int n, int M, double h2, cudaStream_t s) {
     if (nb == 0) return;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_smooth_T<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        cudaFuncSetAttribute(k_smooth_T<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        cudaFuncSetAttribute(k_smooth_T<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_smooth_T<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_smooth_T<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_smooth_T<6, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
         attr = true;
     }
-    const size_t sm = sizeof(double) * (n + 2) * (n + 2) * (n + 2);
-    if (M == 2) k_smooth_T<2><<<nb, 256, sm, s>>>(U, F, n, h2 * LWa<2>::den);
-    if (M == 4) k_smooth_T<4><<<nb, 256, sm, s>>>(U, F, n, h2 * LWa<4>::den);
-    if (M == 6) k_smooth_T<6><<<nb, 256, sm, s>>>(U, F, n, h2 * LWa<6>::den);
+    const size_t sm = sizeof(T) * (n + 2) * (n + 2) * (n + 2);
+    if (M == 2) k_smooth_T<2, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<2>::den));
+    if (M == 4) k_smooth_T<4, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<4>::den));
+    if (M == 6) k_smooth_T<6, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<6>::den));
 }
+template void launch_smooth_T<double>(double*, double*, int, int, int, double, cudaStream_t);
+template void launch_smooth_T<float>(float*, float*, int, int, int, double, cudaStream_t);
 
 // ---------------------------------------------------------------- ghosts and injection
 // Transpose of the ghost fill of level k (halo g): every ghost adjoint goes
@@ -269,44 +276,49 @@ void launch_ghost_T(double* A, int g, double* Ac, int gc, LevelView lk, LevelVie
 
 // Transpose of the injection of level k into its parents' covered nodes
 // (one CTA per level-k block; the covered interiors are disjoint).
-__global__ void k_inject_T(double* __restrict__ fine, int gf, double* __restrict__ coarse, int gc, LevelView lf, int n) {
+template <typename T>
+__global__ void k_inject_T(T* __restrict__ fine, int gf, T* __restrict__ coarse, int gc, LevelView lf, int n) {
     const int B = blockIdx.x;
     const int P = lf.parent[B], o = lf.octant[B];
     const int h = n >> 1;
     const int Sf = n + 2 * gf, Sc = n + 2 * gc;
-    double* fb = fine + (size_t)B * Sf * Sf * Sf;
-    double* cb = coarse + (size_t)P * Sc * Sc * Sc;
+    T* fb = fine + (size_t)B * Sf * Sf * Sf;
+    T* cb = coarse + (size_t)P * Sc * Sc * Sc;
     const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
     for (int t = threadIdx.x; t < h * h * h; t += blockDim.x) {
         const int i = t % h, j = (t / h) % h, l = t / (h * h);
         const size_t c = ((size_t)(gc + oz + l) * Sc + gc + oy + j) * Sc + gc + ox + i;
         fb[((gf + 2 * l) * Sf + gf + 2 * j) * Sf + gf + 2 * i] += cb[c];
-        cb[c] = 0.0;
+        cb[c] = T(0);
     }
 }
 
-void launch_inject_T(double* fine, int gf, double* coarse, int gc, LevelView lf, int n, cudaStream_t s) {
+template <typename T>
+void launch_inject_T(T* fine, int gf, T* coarse, int gc, LevelView lf, int n, cudaStream_t s) {
     if (lf.nb == 0) return;
-    k_inject_T<<<lf.nb, 256, 0, s>>>(fine, gf, coarse, gc, lf, n);
+    k_inject_T<T><<<lf.nb, 256, 0, s>>>(fine, gf, coarse, gc, lf, n);
 }
+template void launch_inject_T<double>(double*, int, double*, int, LevelView, int, cudaStream_t);
+template void launch_inject_T<float>(float*, int, float*, int, LevelView, int, cudaStream_t);
 
 // ---------------------------------------------------------------- grid transfers
 // Transpose of u_k += trilinear(u_{k-1} - uhat_{k-1}): the (n/2+1)^3 coarse
 // window of block B (its parent's part plus the next coarse node on each
 // upper side) gathers the fine adjoints with weights 1 (coincident) and 1/2
 // (midpoint neighbours); it is added to u_{k-1} and subtracted from uhat_{k-1}.
-__global__ void k_prolong_T(double* __restrict__ Uc, double* __restrict__ Hc, const double* __restrict__ Uf, LevelView lf,
-                            LevelView lc, int n) {
+template <typename T>
+__global__ void k_prolong_T(T* __restrict__ Uc, T* __restrict__ Hc, const T* __restrict__ Uf, LevelView lf, LevelView lc,
+                            int n) {
     const int B = blockIdx.x;
     const int P = lf.parent[B], o = lf.octant[B];
     const int h = n >> 1, E = h + 1;
     const int S = n + 2, S3 = S * S * S, n3 = n * n * n;
     const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
     const int* cn = lc.nbr + 27 * P;
-    const double* Ub = Uf + (size_t)B * S3;
+    const T* Ub = Uf + (size_t)B * S3;
     for (int t = threadIdx.x; t < E * E * E; t += blockDim.x) {
         const int i = t % E, j = (t / E) % E, l = t / (E * E);
-        double acc = 0.0;
+        T acc = T(0);
         for (int dz = -1; dz <= 1; ++dz) {
             const int z = 2 * l + dz;
             if (z < 0 || z >= n) continue;
@@ -316,12 +328,12 @@ __global__ void k_prolong_T(double* __restrict__ Uc, double* __restrict__ Hc, co
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int x = 2 * i + dx;
                     if (x < 0 || x >= n) continue;
-                    const double w = (dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0);
+                    const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
                     acc += w * Ub[((z + 1) * S + y + 1) * S + x + 1];
                 }
             }
         }
-        if (acc == 0.0) continue;
+        if (acc == T(0)) continue;
         const int cx = ox + i, cy = oy + j, cz = oz + l;
         const int ex = cx >= n, ey = cy >= n, ez = cz >= n;
         const int blk = cn[dir27(ex, ey, ez)];
@@ -331,10 +343,13 @@ __global__ void k_prolong_T(double* __restrict__ Uc, double* __restrict__ Hc, co
     }
 }
 
-void launch_prolong_T(double* Uc, double* Hc, const double* Uf, LevelView lf, LevelView lc, int n, cudaStream_t s) {
+template <typename T>
+void launch_prolong_T(T* Uc, T* Hc, const T* Uf, LevelView lf, LevelView lc, int n, cudaStream_t s) {
     if (lf.nb == 0) return;
-    k_prolong_T<<<lf.nb, 256, 0, s>>>(Uc, Hc, Uf, lf, lc, n);
+    k_prolong_T<T><<<lf.nb, 256, 0, s>>>(Uc, Hc, Uf, lf, lc, n);
 }
+template void launch_prolong_T<double>(double*, double*, const double*, LevelView, LevelView, int, cudaStream_t);
+template void launch_prolong_T<float>(float*, float*, const float*, LevelView, LevelView, int, cudaStream_t);
 
 // Transpose of the restriction of r (full weighting (1/4)[1 2 1]^3, or
 // injection where the 27-point window of the coarse node leaves Omega_k):
@@ -342,7 +357,8 @@ void launch_prolong_T(double* Uc, double* Hc, const double* Uf, LevelView lf, Le
 // with |2X - p| <= 1.  The fine image 2X lies in B or in B's upper
 // neighbours; X's window is complete when the level-k blocks below 2X exist
 // along the axes where 2X sits on the block's lower face.  Writes Rf[B].
-__global__ void k_fw_T(double* __restrict__ Rf, const double* __restrict__ Fc, LevelView lf, int n) {
+template <typename T>
+__global__ void k_fw_T(T* __restrict__ Rf, const T* __restrict__ Fc, LevelView lf, int n) {
     __shared__ int nb27[27];
     const int B = blockIdx.x;
     if (threadIdx.x < 27) nb27[threadIdx.x] = lf.nbr[27 * B + threadIdx.x];
@@ -355,7 +371,7 @@ __global__ void k_fw_T(double* __restrict__ Rf, const double* __restrict__ Fc, L
             if (p[a] & 1) { lo[a] = -1; hi[a] = 1; }
             else { lo[a] = 0; hi[a] = 0; }
         }
-        double acc = 0.0;
+        T acc = T(0);
         for (int dz = lo[2]; dz <= hi[2]; dz += 2)
             for (int dy = lo[1]; dy <= hi[1]; dy += 2)
                 for (int dx = lo[0]; dx <= hi[0]; dx += 2) {
@@ -376,9 +392,9 @@ __global__ void k_fw_T(double* __restrict__ Rf, const double* __restrict__ Fc, L
                     const int P = lf.parent[c], o = lf.octant[c];
                     const int X = (o & 1) * h + (q[0] >> 1), Y = ((o >> 1) & 1) * h + (q[1] >> 1),
                               Z = ((o >> 2) & 1) * h + (q[2] >> 1);
-                    const double v = Fc[(size_t)P * n3 + (Z * n + Y) * n + X];
+                    const T v = Fc[(size_t)P * n3 + (Z * n + Y) * n + X];
                     if (inside) {
-                        const double w = (dx ? 1.0 : 2.0) * (dy ? 1.0 : 2.0) * (dz ? 1.0 : 2.0) / 64.0;
+                        const T w = T((dx ? 1.0 : 2.0) * (dy ? 1.0 : 2.0) * (dz ? 1.0 : 2.0) / 64.0);
                         acc += w * v;
                     } else if ((dx | dy | dz) == 0) {
                         acc += v;
@@ -388,21 +404,25 @@ __global__ void k_fw_T(double* __restrict__ Rf, const double* __restrict__ Fc, L
     }
 }
 
-void launch_fw_T(double* Rf, const double* Fc, LevelView lf, int n, cudaStream_t s) {
+template <typename T>
+void launch_fw_T(T* Rf, const T* Fc, LevelView lf, int n, cudaStream_t s) {
     if (lf.nb == 0) return;
-    k_fw_T<<<lf.nb, 256, 0, s>>>(Rf, Fc, lf, n);
+    k_fw_T<T><<<lf.nb, 256, 0, s>>>(Rf, Fc, lf, n);
 }
+template void launch_fw_T<double>(double*, const double*, LevelView, int, cudaStream_t);
+template void launch_fw_T<float>(float*, const float*, LevelView, int, cudaStream_t);
 
 // ---------------------------------------------------------------- level 0
 // Transpose of the write of the level-0 target cube [-1, N0]^3 into every
 // level-0 block's (n+2)^3 box: each cube node sums the boxes that hold it.
-__global__ void k_window_T(double* __restrict__ cube, const double* __restrict__ U0, int n, int nbx, int nby, int nbz) {
+template <typename T>
+__global__ void k_window_T(T* __restrict__ cube, const T* __restrict__ U0, int n, int nbx, int nby, int nbz) {
     const int Cx = nbx * n + 2, Cy = nby * n + 2, Cz = nbz * n + 2;
     const size_t total = (size_t)Cx * Cy * Cz;
     const int S = n + 2, S3 = S * S * S;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int tx = (int)(t % Cx) - 1, ty = (int)((t / Cx) % Cy) - 1, tz = (int)(t / ((size_t)Cx * Cy)) - 1;
-        double acc = 0.0;
+        T acc = T(0);
         for (int bz = (tz - 1 < 0 ? -1 : (tz - 1) / n); bz <= (tz + 1) / n; ++bz) {
             if (bz < 0 || bz >= nbz || tz < bz * n - 1 || tz > bz * n + n) continue;
             for (int by = (ty - 1 < 0 ? -1 : (ty - 1) / n); by <= (ty + 1) / n; ++by) {
@@ -418,81 +438,105 @@ __global__ void k_window_T(double* __restrict__ cube, const double* __restrict__
     }
 }
 
-void launch_window_T(double* cube, const double* U0, int n, const int* nb0, cudaStream_t s) {
-    k_window_T<<<4 * 152, 256, 0, s>>>(cube, U0, n, nb0[0], nb0[1], nb0[2]);
+template <typename T>
+void launch_window_T(T* cube, const T* U0, int n, const int* nb0, cudaStream_t s) {
+    k_window_T<T><<<4 * 152, 256, 0, s>>>(cube, U0, n, nb0[0], nb0[1], nb0[2]);
 }
+template void launch_window_T<double>(double*, const double*, int, const int*, cudaStream_t);
+template void launch_window_T<float>(float*, const float*, int, const int*, cudaStream_t);
 
 // Dense level-0 source array [0, N0)^3 -> per-block n^3 arrays of the listed blocks (add or set).
-__global__ void k_dense_to_blocks(double* __restrict__ out, const double* __restrict__ dense, const int* __restrict__ blocks,
+template <typename T>
+__global__ void k_dense_to_blocks(T* __restrict__ out, const T* __restrict__ dense, const int* __restrict__ blocks,
                                   const int* __restrict__ coords, int n, int N0x, int N0y, bool add) {
     const int b = blocks[blockIdx.x];
     const int cx = coords[3 * b] * n, cy = coords[3 * b + 1] * n, cz = coords[3 * b + 2] * n;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const double v = dense[((size_t)(cz + z) * N0y + cy + y) * N0x + cx + x];
+        const T v = dense[((size_t)(cz + z) * N0y + cy + y) * N0x + cx + x];
         if (add) out[(size_t)b * n * n * n + t] += v;
         else out[(size_t)b * n * n * n + t] = v;
     }
 }
 
-void launch_dense_to_blocks(double* out, const double* dense, const int* blocks, int nblocks, const int* coords, int n,
-                            const int* n0, bool add, cudaStream_t s) {
+template <typename T>
+void launch_dense_to_blocks(T* out, const T* dense, const int* blocks, int nblocks, const int* coords, int n, const int* n0,
+                            bool add, cudaStream_t s) {
     if (nblocks == 0) return;
-    k_dense_to_blocks<<<nblocks, 256, 0, s>>>(out, dense, blocks, coords, n, n0[0], n0[1], add);
+    k_dense_to_blocks<T><<<nblocks, 256, 0, s>>>(out, dense, blocks, coords, n, n0[0], n0[1], add);
 }
+template void launch_dense_to_blocks<double>(double*, const double*, const int*, int, const int*, int, const int*, bool,
+                                             cudaStream_t);
+template void launch_dense_to_blocks<float>(float*, const float*, const int*, int, const int*, int, const int*, bool,
+                                            cudaStream_t);
 
 // ---------------------------------------------------------------- block and vector helpers
 // out[b] = scale * interior of A[b] (halo g) for the listed blocks.
-__global__ void k_interior_get(double* __restrict__ out, const double* __restrict__ A, int g, const int* __restrict__ blocks,
-                               int n, double scale) {
+template <typename TO, typename TI>
+__global__ void k_interior_get(TO* __restrict__ out, const TI* __restrict__ A, int g, const int* __restrict__ blocks, int n,
+                               double scale) {
     const int b = blocks[blockIdx.x];
     const int S = n + 2 * g;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        out[(size_t)b * n * n * n + t] = scale * A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g];
+        out[(size_t)b * n * n * n + t] = TO(scale * (double)A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g]);
     }
 }
 
-void launch_interior_get(double* out, const double* A, int g, const int* blocks, int nblocks, int n, double scale,
-                         cudaStream_t s) {
+template <typename TO, typename TI>
+void launch_interior_get(TO* out, const TI* A, int g, const int* blocks, int nblocks, int n, double scale, cudaStream_t s) {
     if (nblocks == 0) return;
-    k_interior_get<<<nblocks, 256, 0, s>>>(out, A, g, blocks, n, scale);
+    k_interior_get<TO, TI><<<nblocks, 256, 0, s>>>(out, A, g, blocks, n, scale);
 }
+template void launch_interior_get<double, double>(double*, const double*, int, const int*, int, int, double, cudaStream_t);
+template void launch_interior_get<float, float>(float*, const float*, int, const int*, int, int, double, cudaStream_t);
 
 // interior of A[b] (halo g) += scale * v[b] for the listed blocks.
-__global__ void k_interior_add(double* __restrict__ A, int g, const double* __restrict__ v, const int* __restrict__ blocks,
-                               int n, double scale) {
+template <typename TA, typename TV>
+__global__ void k_interior_add(TA* __restrict__ A, int g, const TV* __restrict__ v, const int* __restrict__ blocks, int n,
+                               double scale) {
     const int b = blocks[blockIdx.x];
     const int S = n + 2 * g;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g] += scale * v[(size_t)b * n * n * n + t];
+        A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g] += TA(scale * (double)v[(size_t)b * n * n * n + t]);
     }
 }
 
-void launch_interior_add(double* A, int g, const double* v, const int* blocks, int nblocks, int n, double scale,
-                         cudaStream_t s) {
+template <typename TA, typename TV>
+void launch_interior_add(TA* A, int g, const TV* v, const int* blocks, int nblocks, int n, double scale, cudaStream_t s) {
     if (nblocks == 0) return;
-    k_interior_add<<<nblocks, 256, 0, s>>>(A, g, v, blocks, n, scale);
+    k_interior_add<TA, TV><<<nblocks, 256, 0, s>>>(A, g, v, blocks, n, scale);
 }
+template void launch_interior_add<double, double>(double*, int, const double*, const int*, int, int, double, cudaStream_t);
+template void launch_interior_add<float, float>(float*, int, const float*, const int*, int, int, double, cudaStream_t);
+template void launch_interior_add<float, double>(float*, int, const double*, const int*, int, int, double, cudaStream_t);
 
 // out[b] = scale * in[b] (n^3 arrays) for the listed blocks; in may be null (zero).
-__global__ void k_block_copy(double* __restrict__ out, const double* __restrict__ in, const int* __restrict__ blocks, int n,
+template <typename TO, typename TI>
+__global__ void k_block_copy(TO* __restrict__ out, const TI* __restrict__ in, const int* __restrict__ blocks, int n,
                              double scale) {
     const int b = blocks[blockIdx.x];
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x)
-        out[(size_t)b * n * n * n + t] = in ? scale * in[(size_t)b * n * n * n + t] : 0.0;
+        out[(size_t)b * n * n * n + t] = in ? TO(scale * (double)in[(size_t)b * n * n * n + t]) : TO(0);
 }
 
-void launch_block_copy(double* out, const double* in, const int* blocks, int nblocks, int n, double scale, cudaStream_t s) {
+template <typename TO, typename TI>
+void launch_block_copy(TO* out, const TI* in, const int* blocks, int nblocks, int n, double scale, cudaStream_t s) {
     if (nblocks == 0) return;
-    k_block_copy<<<nblocks, 256, 0, s>>>(out, in, blocks, n, scale);
+    k_block_copy<TO, TI><<<nblocks, 256, 0, s>>>(out, in, blocks, n, scale);
 }
+template void launch_block_copy<double, double>(double*, const double*, const int*, int, int, double, cudaStream_t);
+template void launch_block_copy<float, double>(float*, const double*, const int*, int, int, double, cudaStream_t);
+template void launch_block_copy<double, float>(double*, const float*, const int*, int, int, double, cudaStream_t);
 
-void launch_block_zero(double* out, const int* blocks, int nblocks, int n, cudaStream_t s) {
+template <typename T>
+void launch_block_zero(T* out, const int* blocks, int nblocks, int n, cudaStream_t s) {
     if (nblocks == 0) return;
-    k_block_copy<<<nblocks, 256, 0, s>>>(out, nullptr, blocks, n, 0.0);
+    k_block_copy<T, T><<<nblocks, 256, 0, s>>>(out, nullptr, blocks, n, 0.0);
 }
+template void launch_block_zero<double>(double*, const int*, int, int, cudaStream_t);
+template void launch_block_zero<float>(float*, const int*, int, int, cudaStream_t);
 
 // out = a x + b y over a flat vector (out may alias x or y); optionally
 // max |out| into *absmax (bit pattern of a non-negative double, NaN mapped to +Inf).

@@ -403,10 +403,12 @@ void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, d
     conv_passes<double>(p, geo_of(h, p), spec, p.ghat, F0, U0, s);
 }
 
-// Transpose of problem p's level-0 convolution (FP64): dense adjoint on the
-// target cube [-1, N0]^3 -> dense adjoint on the sources [0, N0)^3.  The
-// kernel is even, so this is the convolution with the two ranges exchanged.
-void launch_conv_transpose(const Handle& h, const Problem& p, const double* cube_in, double* src_out, cudaStream_t s) {
+// Transpose of problem p's level-0 convolution: dense adjoint on the target
+// cube [-1, N0]^3 -> dense adjoint on the sources [0, N0)^3 (FP64, or FP32
+// with the FP32 spectrum of a mixed-precision handle).  The kernel is even,
+// so this is the convolution with the two ranges exchanged.
+template <typename T>
+void launch_conv_transpose(const Handle& h, const Problem& p, const T* cube_in, T* src_out, cudaStream_t s) {
     Geo g = geo_of(h, p);
     for (int a = 0; a < 3; ++a) {
         g.in_lo[a] = -1; g.in_n[a] = p.n0[a] + 2;
@@ -414,8 +416,11 @@ void launch_conv_transpose(const Handle& h, const Problem& p, const double* cube
     }
     g.dense_in = 1;
     g.dense_out = 1;
-    conv_passes<double>(p, g, h.spec, p.ghat, cube_in, src_out, s);
+    if constexpr (sizeof(T) == 8) conv_passes<double>(p, g, h.spec, p.ghat, cube_in, src_out, s);
+    else conv_passes<float>(p, g, h.spec32, p.ghat32, cube_in, src_out, s);
 }
+template void launch_conv_transpose<double>(const Handle&, const Problem&, const double*, double*, cudaStream_t);
+template void launch_conv_transpose<float>(const Handle&, const Problem&, const float*, float*, cudaStream_t);
 
 // ============================================================================
 // Lattice Green's function (FP64).  G[n] = (2pi)^-3 int cos(k.n) / sigma(k) dk

@@ -553,24 +553,24 @@ static void allow(K kern) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynam
 // from the fine level); outside the domain the adjoint is dropped.  Global
 // writes are atomic and land only on interiors, never on ghost layers, so
 // blocks of one launch do not interfere.
-template <int I>
-__global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, double* __restrict__ Ac, LevelView lk,
-                                                       LevelView lc, int n) {
+template <typename T, int I>
+__global__ void __launch_bounds__(256) k_ghost_T_fused(T* __restrict__ A, T* __restrict__ Ac, LevelView lk, LevelView lc,
+                                                       int n) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
-    double* pool = reinterpret_cast<double*>(fz_smem);
-    __shared__ HaloSmem<double> hs;
+    T* pool = reinterpret_cast<T*>(fz_smem);
+    __shared__ HaloSmem<T> hs;
     const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int b = blockIdx.x;
     if (tid < 27) hs.snbr[tid] = lk.nbr[27 * b + tid];
-    if (tid < I) hs.sw[tid] = midw<I>(tid);
+    if (tid < I) hs.sw[tid] = T(midw<I>(tid));
     __syncthreads();
     if (tid == 0) {
         int any = 0;
         for (int d = 0; d < 27; ++d) any |= (d != 13 && hs.snbr[d] == NBR_MISSING);
         hs.interp = any;
     }
-    double* Ab = A + (size_t)b * S3;
+    T* Ab = A + (size_t)b * S3;
     const int shell = S3 - n3;
     // copied regions
     for (int t = tid; t < shell; t += nth) {
@@ -582,16 +582,16 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
         const int j = hs.snbr[dir27(dx, dy, dz)];
         if (j < 0) continue;
         const int o = (z * S + y) * S + x;
-        const double a = Ab[o];
-        Ab[o] = 0.0;
-        if (a != 0.0) atomicAdd(&A[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)], a);
+        const T a = Ab[o];
+        Ab[o] = T(0);
+        if (a != T(0)) atomicAdd(&A[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)], a);
     }
     __syncthreads();
     if (!hs.interp) {
         for (int t = tid; t < shell; t += nth) {      // outside-domain ghosts: dropped
             int x, y, z;
             shell_coords(t, S, x, y, z);
-            Ab[(z * S + y) * S + x] = 0.0;
+            Ab[(z * S + y) * S + x] = T(0);
         }
         return;
     }
@@ -620,8 +620,8 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
     const int h = n >> 1;
     constexpr int plo = 4 - I / 2;
     const int PL = h + I, PL2 = PL * PL, PL3 = PL2 * PL;
-    double* patch = pool + pool_size(n, I);
-    for (int t = tid; t < pool_size(n, I) + PL3; t += nth) pool[t] = 0.0;
+    T* patch = pool + pool_size(n, I);
+    for (int t = tid; t < pool_size(n, I) + PL3; t += nth) pool[t] = T(0);
     __syncthreads();
     // phase 2 transposed: each interpolated ghost node spreads over its region's reduced array
     for (int t = tid; t < shell; t += nth) {
@@ -633,13 +633,13 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
         const int d = dir27(dx, dy, dz);
         const int o = (z * S + y) * S + x;
         if (hs.snbr[d] != NBR_MISSING) {
-            if (hs.snbr[d] == NBR_OUTSIDE) Ab[o] = 0.0;
+            if (hs.snbr[d] == NBR_OUTSIDE) Ab[o] = T(0);
             continue;
         }
-        const double a = Ab[o];
-        Ab[o] = 0.0;
-        if (a == 0.0) continue;
-        double* R = pool + hs.off[d];
+        const T a = Ab[o];
+        Ab[o] = T(0);
+        if (a == T(0)) continue;
+        T* R = pool + hs.off[d];
         int st0 = 0, st1 = 0, cn0 = 1, cn1 = 1, sd0 = 0, sd1 = 0, nt = 0, stride = 1;
         const int q[3] = {x - 1, y - 1, z - 1};
         const int dd[3] = {dx, dy, dz};
@@ -655,9 +655,9 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
             ++nt;
         }
         for (int m1 = 0; m1 < cn1; ++m1) {
-            const double a1 = (cn1 == 1 ? 1.0 : hs.sw[m1]) * a;
+            const T a1 = (cn1 == 1 ? T(1) : hs.sw[m1]) * a;
             const int rb = (st1 + m1) * sd1 + st0 * sd0;
-            for (int m0 = 0; m0 < cn0; ++m0) atomicAdd(&R[rb + m0 * sd0], (cn0 == 1 ? 1.0 : hs.sw[m0]) * a1);
+            for (int m0 = 0; m0 < cn0; ++m0) atomicAdd(&R[rb + m0 * sd0], (cn0 == 1 ? T(1) : hs.sw[m0]) * a1);
         }
     }
     __syncthreads();
@@ -668,8 +668,8 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
         while (r + 1 < hs.nreg && hs.rstart[r + 1] <= f) ++r;
         const int d = hs.rdir[r];
         const int e = f - hs.rstart[r];
-        const double a = pool[f];
-        if (a == 0.0) continue;
+        const T a = pool[f];
+        if (a == T(0)) continue;
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
         int tc[3] = {0, 0, 0};
         int rem = e;
@@ -681,11 +681,11 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
         const int y0 = dy < 0 ? lo : (dy > 0 ? up : tc[1]);
         const int z0 = dz < 0 ? lo : (dz > 0 ? up : tc[2]);
         for (int mz = 0; mz < cz; ++mz) {
-            const double az = (cz == 1 ? 1.0 : hs.sw[mz]) * a;
+            const T az = (cz == 1 ? T(1) : hs.sw[mz]) * a;
             for (int my = 0; my < cy; ++my) {
-                const double ay = (cy == 1 ? 1.0 : hs.sw[my]) * az;
-                double* row = patch + ((z0 + mz) * PL + y0 + my) * PL + x0;
-                for (int mx = 0; mx < cx; ++mx) atomicAdd(&row[mx], (cx == 1 ? 1.0 : hs.sw[mx]) * ay);
+                const T ay = (cy == 1 ? T(1) : hs.sw[my]) * az;
+                T* row = patch + ((z0 + mz) * PL + y0 + my) * PL + x0;
+                for (int mx = 0; mx < cx; ++mx) atomicAdd(&row[mx], (cx == 1 ? T(1) : hs.sw[mx]) * ay);
             }
         }
     }
@@ -694,8 +694,8 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
     const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
     const int base[3] = {(bx & 1) * h - 4 + plo, (by & 1) * h - 4 + plo, (bz & 1) * h - 4 + plo};
     for (int t = tid; t < PL3; t += nth) {
-        const double a = patch[t];
-        if (a == 0.0) continue;
+        const T a = patch[t];
+        if (a == T(0)) continue;
         const int px = t % PL, py = (t / PL) % PL, pz = t / PL2;
         const int rx = base[0] + px, ry = base[1] + py, rz = base[2] + pz;
         const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0);
@@ -714,19 +714,22 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(double* __restrict__ A, d
     }
 }
 
-void launch_ghost_T_fused(double* A, double* Ac, LevelView lk, LevelView lc, int n, int M, cudaStream_t s) {
+template <typename T>
+void launch_ghost_T_fused(T* A, T* Ac, LevelView lk, LevelView lc, int n, int M, cudaStream_t s) {
     if (lk.nb == 0) return;
     const int I = M + 2, PL = n / 2 + I;
-    const size_t sm = sizeof(double) * ((size_t)pool_size(n, I) + (size_t)PL * PL * PL);
+    const size_t sm = sizeof(T) * ((size_t)pool_size(n, I) + (size_t)PL * PL * PL);
     static bool attr = false;
     if (!attr) {
-        allow(k_ghost_T_fused<4>); allow(k_ghost_T_fused<6>); allow(k_ghost_T_fused<8>);
+        allow(k_ghost_T_fused<T, 4>); allow(k_ghost_T_fused<T, 6>); allow(k_ghost_T_fused<T, 8>);
         attr = true;
     }
-    if (M == 2) k_ghost_T_fused<4><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
-    if (M == 4) k_ghost_T_fused<6><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
-    if (M == 6) k_ghost_T_fused<8><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
+    if (M == 2) k_ghost_T_fused<T, 4><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
+    if (M == 4) k_ghost_T_fused<T, 6><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
+    if (M == 6) k_ghost_T_fused<T, 8><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
 }
+template void launch_ghost_T_fused<double>(double*, double*, LevelView, LevelView, int, int, cudaStream_t);
+template void launch_ghost_T_fused<float>(float*, float*, LevelView, LevelView, int, int, cudaStream_t);
 
 // CTA size actually launched: the requested one, raised (in warps) until each
 // thread holds at most KMAX nodes of a colour.

@@ -141,6 +141,9 @@ struct Handle {
     std::vector<size_t> xoff;         // level k's offset in the vectors below, which hold [nb_k][n^3] per level
     double *lam = nullptr, *rho = nullptr, *gvec = nullptr, *xb = nullptr, *fsb = nullptr, *wl = nullptr;
     double *cube = nullptr, *dense = nullptr, *off0b = nullptr;
+    struct AdjLevel32 { float *Ub = nullptr, *Fb = nullptr, *Rb = nullptr, *Hb = nullptr; };
+    std::vector<AdjLevel32> adj32;    // FP32 transposed cycles of a mixed-precision handle
+    float *cube32 = nullptr, *dense32 = nullptr, *off0b32 = nullptr;
 };
 
 inline double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
@@ -245,28 +248,39 @@ void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int 
 void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, const int* prob,
                    cudaStream_t s);
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s);
-void launch_conv_transpose(const Handle& h, const Problem& p, const double* cube_in, double* src_out, cudaStream_t s);
+template <typename T>
+void launch_conv_transpose(const Handle& h, const Problem& p, const T* cube_in, T* src_out, cudaStream_t s);
 void launch_scatter_leaves_to(const Handle& h, const double* f, const LevelPtrs& dst, int g, bool scaled, cudaStream_t s);
 void launch_gather_leaves_from(const Handle& h, double* u, const LevelPtrs& src, int g, bool scaled, cudaStream_t s);
-// transposed operators (kernels_adjoint.cu)
-void launch_stencil_T(double* out, const double* lam, double* fadd, const int* blocks, int nblocks, int n, int M,
-                      double inv_h2, cudaStream_t s);
+// transposed operators (kernels_adjoint.cu); T = double, or float for the FP32 transposed cycles
+template <typename T>
+void launch_stencil_T(T* out, const T* lam, T* fadd, const int* blocks, int nblocks, int n, int M, double inv_h2,
+                      cudaStream_t s);
 void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nblocks, int n, int M, cudaStream_t s);
 void launch_ghost_T(double* A, int g, double* Ac, int gc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
-void launch_ghost_T_fused(double* A, double* Ac, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
-void launch_inject_T(double* fine, int gf, double* coarse, int gc, LevelView lf, int n, cudaStream_t s);
-void launch_smooth_T(double* U, double* F, int nb, int n, int M, double h2, cudaStream_t s);
-void launch_prolong_T(double* Uc, double* Hc, const double* Uf, LevelView lf, LevelView lc, int n, cudaStream_t s);
-void launch_fw_T(double* Rf, const double* Fc, LevelView lf, int n, cudaStream_t s);
-void launch_window_T(double* cube, const double* U0, int n, const int* nb0, cudaStream_t s);
-void launch_dense_to_blocks(double* out, const double* dense, const int* blocks, int nblocks, const int* coords, int n,
-                            const int* n0, bool add, cudaStream_t s);
-void launch_interior_get(double* out, const double* A, int g, const int* blocks, int nblocks, int n, double scale,
-                         cudaStream_t s);
-void launch_interior_add(double* A, int g, const double* v, const int* blocks, int nblocks, int n, double scale,
-                         cudaStream_t s);
-void launch_block_copy(double* out, const double* in, const int* blocks, int nblocks, int n, double scale, cudaStream_t s);
-void launch_block_zero(double* out, const int* blocks, int nblocks, int n, cudaStream_t s);
+template <typename T>
+void launch_ghost_T_fused(T* A, T* Ac, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
+template <typename T>
+void launch_inject_T(T* fine, int gf, T* coarse, int gc, LevelView lf, int n, cudaStream_t s);
+template <typename T>
+void launch_smooth_T(T* U, T* F, int nb, int n, int M, double h2, cudaStream_t s);
+template <typename T>
+void launch_prolong_T(T* Uc, T* Hc, const T* Uf, LevelView lf, LevelView lc, int n, cudaStream_t s);
+template <typename T>
+void launch_fw_T(T* Rf, const T* Fc, LevelView lf, int n, cudaStream_t s);
+template <typename T>
+void launch_window_T(T* cube, const T* U0, int n, const int* nb0, cudaStream_t s);
+template <typename T>
+void launch_dense_to_blocks(T* out, const T* dense, const int* blocks, int nblocks, const int* coords, int n, const int* n0,
+                            bool add, cudaStream_t s);
+template <typename TO, typename TI>
+void launch_interior_get(TO* out, const TI* A, int g, const int* blocks, int nblocks, int n, double scale, cudaStream_t s);
+template <typename TA, typename TV>
+void launch_interior_add(TA* A, int g, const TV* v, const int* blocks, int nblocks, int n, double scale, cudaStream_t s);
+template <typename TO, typename TI>
+void launch_block_copy(TO* out, const TI* in, const int* blocks, int nblocks, int n, double scale, cudaStream_t s);
+template <typename T>
+void launch_block_zero(T* out, const int* blocks, int nblocks, int n, cudaStream_t s);
 void launch_lincomb(double* out, double a, const double* x, double b, const double* y, size_t len,
                     unsigned long long* absmax, cudaStream_t s);
 // mixed precision helpers (kernels_mixed.cu)

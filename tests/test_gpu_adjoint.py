@@ -220,3 +220,16 @@ def test_dot_product_identity_full_size():
     a = float((w * u).sum())
     b = float((g * f).sum())
     assert abs(a - b) < 1e-7 * float((w.abs() * u.abs()).sum())
+
+
+@pytest.mark.parametrize("M", [4, 6])
+def test_mixed_precision_gradient_matches_oracle(M):
+    """FP32 transposed cycles inside the FP64 refinement reach the FP64 gradient."""
+    from paper_2512_08555_gb300.mrp import Solver
+    desc, fo, adj, _ = _case(M)
+    w = synth.sample_leaves(desc, synth.gaussian_weight(0))
+    g_o = adj.gradient_ir(w, tol=1e-13)
+    s = Solver(desc, order=M, tol=1e-12, max_cycles=80, precision="mixed")
+    g_g, st = s.solve_adjoint(torch.from_numpy(w).cuda(), allow_not_converged=True)
+    assert st.residual < 1e-11
+    assert _rel(g_g.cpu().numpy(), g_o) < 1e-9
