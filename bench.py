@@ -286,6 +286,73 @@ def bench_five_level(order, flush, stream, steps):
     return out
 
 
+def fft_bytes_flops(N0, P, elem):
+    """Algorithmic DRAM bytes and flops of one level-0 convolution (five passes) on an N0^3 lattice padded to P^3.
+
+    Passes and the data each must move (complex values take 2 elem bytes): x forward (read the N0^3 source,
+    write N0^2 half-spectrum lines of K = P/2+1), y forward (read N0 and write P values per line, N0 K lines),
+    z with the G-hat product and the inverse (read N0 and write N0+2 values per line, P K lines; read G-hat's
+    K^3 octant), y inverse (read P, write N0+2 per line, (N0+2) K lines), x inverse (read K per line, write
+    (N0+2)^3 reals).  Flops: 5 L log2 L per complex FFT of length L = P, one per line and pass, two in the
+    z pass.
+    """
+    import math
+    K = P // 2 + 1
+    c = 2 * elem
+    byt = (N0 ** 3 * elem + N0 * N0 * K * c
+           + N0 * N0 * K * c + N0 * P * K * c
+           + N0 * P * K * c + K ** 3 * elem + (N0 + 2) * P * K * c
+           + (N0 + 2) * P * K * c + (N0 + 2) ** 2 * K * c
+           + (N0 + 2) ** 2 * K * c + (N0 + 2) ** 3 * elem)
+    fft = 5 * P * math.log2(P)
+    lines = N0 * N0 + N0 * K + 2 * P * K + (N0 + 2) * K + (N0 + 2) ** 2
+    return byt, lines * fft
+
+
+def bench_fft_large(order, flush, stream, steps):
+    """Level-0 convolution on a lattice far larger than L2: 15^3 blocks of 16^3 (N0 = 240, P = 486), one central
+    block refined once; each FP32 cycle is then essentially one FP32 convolution."""
+    import torch
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver
+
+    def want(level, coords):
+        return (coords == 7).all(axis=1)
+    desc = synth.adaptive_forest((15, 15, 15), 16, (-1.0, -1.0, -1.0), 2.0 / 240, 1, want)
+    f = torch.from_numpy(synth.sample_leaves(desc, synth.c4_bumps(0, k=3, r_lo=0.1, r_hi=0.2, box=0.4))).cuda()
+    s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed")
+    P = s.fft_shape()[0]
+    N0 = 240
+    for _ in range(3):
+        s.solve(f)
+    s.profile(True)
+    s.profile_read(reset=True)
+    ms, (u, st) = _time_calls(lambda: s.solve(f), steps, 0, flush, stream)
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    s.close()
+    out = {"workload": f"level-0 lattice {N0}^3 padded to {P}^3 (one refined block)", "P": P,
+           "ms_per_solve": ms, "cycles": int(st.cycles), "ir_steps": int(st.ir_steps)}
+    for key, elem, name in (("coarse_fft_f32", 4, "fp32"), ("coarse_fft_f64", 8, "fp64")):
+        ph = prof.get(key)
+        if not ph or ph["launches"] == 0:
+            continue
+        convs = ph["launches"]                    # one timed phase per level-0 convolution (5 kernels)
+        t = ph["ms"] / 1e3 / convs
+        byt, fl = fft_bytes_flops(N0, P, elem)
+        r = {"convolutions_per_solve": convs / steps, "ms_per_convolution": t * 1e3,
+             "algorithmic_bytes": byt, "algorithmic_flops": fl,
+             "achieved_GBs": byt / t / 1e9, "hbm_frac": byt / t / 1e9 / HBM_PEAK_GBS,
+             "achieved_TFLOPs": fl / t / 1e12}
+        if name == "fp64":
+            r["fp64_alu_frac"] = fl / t / 1e12 / FP64_PEAK_TFLOPS
+            r["bound"] = "alu (FP64)"
+        else:
+            r["bound"] = "hbm"
+        out[name] = r
+    return out
+
+
 def bench_batched(order, flush, stream, steps):
     import torch
     from paper_2512_08555_gb300 import synth
@@ -430,6 +497,7 @@ def run_ours(args):
         line["adjoint"] = bench_adjoint(desc, f, u_p, ms_p, args.order, flush, stream, xs)
         line["five_level"] = bench_five_level(args.order, flush, stream, xs)
         line["batched"] = bench_batched(args.order, flush, stream, xs)
+        line["fft_large"] = bench_fft_large(args.order, flush, stream, xs)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -447,6 +515,10 @@ def run_profile_case(args):
     from paper_2512_08555_gb300.mrp import Solver
     if args.profile_case == "five_level":
         desc, src = synth.config3(0)
+    elif args.profile_case == "fft_large":
+        desc = synth.adaptive_forest((15, 15, 15), 16, (-1.0, -1.0, -1.0), 2.0 / 240, 1,
+                                     lambda level, coords: (coords == 7).all(axis=1))
+        src = synth.c4_bumps(0, k=3, r_lo=0.1, r_hi=0.2, box=0.4)
     else:
         desc, src = synth.config2(0)
     f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
@@ -468,7 +540,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline line only")
     ap.add_argument("--inner-cycles", type=int, default=4, help="FP32 cycles per refinement step of the chosen form")
-    ap.add_argument("--profile-case", choices=["headline", "five_level"], default=None,
+    ap.add_argument("--profile-case", choices=["headline", "five_level", "fft_large"], default=None,
                     help="run the chosen solver on one workload without timing (for ncu)")
     args = ap.parse_args()
     if args.profile_case:

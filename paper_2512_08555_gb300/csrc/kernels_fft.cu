@@ -25,10 +25,16 @@ template <typename R> struct Cx;
 template <> struct Cx<double> { using T = double2; };
 template <> struct Cx<float> { using T = float2; };
 
+// One line length with its radix sequence.  Per stage st: ns[st] = product of
+// the earlier radices, nsm[st] = floor(2^32 / ns) + 1 (so that j / ns =
+// umulhi(j, nsm) for j, ns < 2^16; ns = 1 is handled apart), tstep[st] =
+// P / (ns * rad) (the twiddle stride of one butterfly index).
 template <typename R>
 struct FftLine {
     int P, nrad;
     int rad[MAX_RADIX_STAGES];
+    int ns[MAX_RADIX_STAGES], tstep[MAX_RADIX_STAGES];
+    unsigned nsm[MAX_RADIX_STAGES];
     const typename Cx<R>::T* tw;
 };
 
@@ -37,7 +43,14 @@ static FftLine<R> line_of(const FftAxis& a) {
     FftLine<R> l{};
     l.P = a.P;
     l.nrad = a.nrad;
-    for (int i = 0; i < a.nrad; ++i) l.rad[i] = a.rad[i];
+    int ns = 1;
+    for (int i = 0; i < a.nrad; ++i) {
+        l.rad[i] = a.rad[i];
+        l.ns[i] = ns;
+        l.nsm[i] = ns > 1 ? (unsigned)((1ULL << 32) / (unsigned long long)ns + 1ULL) : 0u;
+        l.tstep[i] = a.P / (ns * a.rad[i]);
+        ns *= a.rad[i];
+    }
     if constexpr (sizeof(R) == 8) l.tw = a.tw;
     else l.tw = a.tw32;
     return l;
@@ -110,12 +123,13 @@ template <typename R> struct Dft<5, R> {
 // b[(j / Ns) Ns RAD + (j mod Ns) + r Ns].  Radix 7 uses the direct sum with
 // the line's twiddle table.
 template <int RAD, typename R, typename C>
-__device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int P, int Ns, const C* tw,
-                                               int sign) {
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int P, int Ns, unsigned nsm,
+                                               int tstep, const C* tw, int sign) {
     const int PR = P / RAD;
     for (int j = threadIdx.x; j < PR; j += blockDim.x) {
-        const int k = j % Ns;
-        const int step = (P / (Ns * RAD)) * k;
+        const int qd = Ns == 1 ? j : (int)__umulhi((unsigned)j, nsm);     // j / Ns
+        const int k = j - qd * Ns;                                         // j % Ns
+        const int step = tstep * k;
         C v[RAD];
 #pragma unroll
         for (int r = 0; r < RAD; ++r) {
@@ -136,37 +150,55 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
         } else {
             Dft<RAD, R>::run(v, sign);
         }
-        const int base = (j / Ns) * Ns * RAD + k;
+        const int base = qd * Ns * RAD + k;
 #pragma unroll
         for (int r = 0; r < RAD; ++r) b[base + r * Ns] = v[r];
     }
 }
 
-// One line of length P in a[], b[] as scratch; the CTA's threads with the
-// same threadIdx.y (blockDim.x of them) cooperate.  Returns the buffer that
-// holds the result (Stockham autosort, mixed radix).
+// Threads per line and lines per CTA (shared memory (2 LY + 1) P complex
+// values).  FP32 runs one warp per line, 8 lines, with warp barriers between
+// stages; FP64, bound by its arithmetic, keeps 64 threads per line, 4 lines.
+template <typename R> __host__ __device__ constexpr int fft_tx() { return sizeof(R) == 4 ? 32 : 64; }
+template <typename R> __host__ __device__ constexpr int fft_ly() { return sizeof(R) == 4 ? 8 : 4; }
+
+// One line of length P in a[], b[] as scratch; the fft_tx<R>() threads with
+// the same threadIdx.y cooperate.  With one warp per line the stages are
+// separated by warp barriers, else by CTA barriers (every thread of the CTA
+// must then call this).  Returns the buffer that holds the result (Stockham
+// autosort, mixed radix).
 template <typename R, typename C>
 __device__ C* fft_line(C* a, C* b, const FftLine<R>& L, int sign) {
     const int P = L.P;
-    int Ns = 1;
     for (int st = 0; st < L.nrad; ++st) {
-        const int RAD = L.rad[st];
+        const int RAD = L.rad[st], Ns = L.ns[st], ts = L.tstep[st];
+        const unsigned nsm = L.nsm[st];
         switch (RAD) {
-            case 2: stockham_stage<2, R>(a, b, P, Ns, L.tw, sign); break;
-            case 3: stockham_stage<3, R>(a, b, P, Ns, L.tw, sign); break;
-            case 4: stockham_stage<4, R>(a, b, P, Ns, L.tw, sign); break;
-            case 5: stockham_stage<5, R>(a, b, P, Ns, L.tw, sign); break;
-            default: stockham_stage<7, R>(a, b, P, Ns, L.tw, sign); break;
+            case 2: stockham_stage<2, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
+            case 3: stockham_stage<3, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
+            case 4: stockham_stage<4, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
+            case 5: stockham_stage<5, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
+            default: stockham_stage<7, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
         }
-        __syncthreads();
+        if constexpr (fft_tx<R>() == 32) __syncwarp();
+        else __syncthreads();
         C* t = a; a = b; b = t;
-        Ns *= RAD;
     }
     return a;
 }
 
-constexpr int FFT_TX = 64;   // threads per line
-constexpr int FFT_LY = 4;    // lines per CTA
+
+// Copies the line's twiddle table into shared memory (after the CTA's line
+// buffers) and returns the line descriptor that reads it from there; the
+// table is complete when the next __syncthreads() of the caller has passed.
+template <typename R>
+__device__ __forceinline__ FftLine<R> stage_twiddles(const FftLine<R>& Lg, typename Cx<R>::T* stw) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    for (int j = tid; j < Lg.P; j += nth) stw[j] = Lg.tw[j];
+    FftLine<R> L = Lg;
+    L.tw = stw;
+    return L;
+}
 
 // Geometry of one convolution: padded lengths, half spectrum, and the input
 // (source) and output (target) node ranges per axis (x, y, z).  A node i of a
@@ -179,16 +211,18 @@ struct Geo {
     int dense_in, dense_out;   // 0: level-0 block layouts, 1: dense arrays over the ranges
 };
 
-__device__ __forceinline__ int pidx(int i, int P) { return (i % P + P) % P; }
+// Padded index of a lattice coordinate i in [-P, 2P) (every range here lies inside).
+__device__ __forceinline__ int pidx(int i, int P) { return i < 0 ? i + P : (i >= P ? i - P : i); }
 
 // ---------------------------------------------------------------- pass A (x, real -> half spectrum)
 // lines: input (y, z) range; x input range.
 template <typename R>
-__global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ src, Geo g, FftLine<R> L) {
+__global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ src, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const int line = blockIdx.x * FFT_LY + threadIdx.y;
+    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const int line = blockIdx.x * fft_ly<R>() + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
     const bool live = line < g.in_n[1] * g.in_n[2];
@@ -217,86 +251,110 @@ __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __res
     }
 }
 
+// The y and z passes take LY = fft_ly<R>() lines of consecutive kx per CTA.
+// Their global loads and stores walk the lines' elements with kx fastest
+// across the CTA's threads (element e: line e % LY, position e / LY), so that
+// a warp touches whole sectors; the transforms themselves run per line.
+
 // ---------------------------------------------------------------- pass B (y, forward), lines (input z, kx)
 template <typename R>
-__global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
+__global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
+    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const int P = L.P, P2 = 2 * P;
     const int zi = pidx(g.in_lo[2] + (int)blockIdx.y, g.Pz);
-    const int kx = blockIdx.x * FFT_LY + threadIdx.y;
-    C* a = sm + threadIdx.y * 2 * L.P;
-    C* b = a + L.P;
-    const bool live = kx < g.Kx;
-    for (int j = threadIdx.x; j < L.P; j += blockDim.x) a[j] = C{R(0), R(0)};
+    const int kx0 = blockIdx.x * fft_ly<R>();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    C* a = sm + threadIdx.y * P2;
+    C* b = a + P;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
     __syncthreads();
-    if (live)
-        for (int t = threadIdx.x; t < g.in_n[1]; t += blockDim.x) {
-            const int j = pidx(g.in_lo[1] + t, g.Py);
-            a[j] = spec[((size_t)zi * g.Py + j) * g.Kx + kx];
-        }
+    for (int e = tid; e < fft_ly<R>() * g.in_n[1]; e += nth) {
+        const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
+        if (kx0 + ly >= g.Kx) continue;
+        const int j = pidx(g.in_lo[1] + t, g.Py);
+        sm[ly * P2 + j] = spec[((size_t)zi * g.Py + j) * g.Kx + kx0 + ly];
+    }
     __syncthreads();
-    C* r = fft_line<R>(a, b, L, -1);
-    if (live)
-        for (int y = threadIdx.x; y < L.P; y += blockDim.x) spec[((size_t)zi * g.Py + y) * g.Kx + kx] = r[y];
+    const int roff = (int)(fft_line<R>(a, b, L, -1) - a);
+    __syncthreads();
+    for (int e = tid; e < fft_ly<R>() * P; e += nth) {
+        const int ly = e % fft_ly<R>(), y = e / fft_ly<R>();
+        if (kx0 + ly < g.Kx) spec[((size_t)zi * g.Py + y) * g.Kx + kx0 + ly] = sm[ly * P2 + roff + y];
+    }
 }
 
 // ---------------------------------------------------------------- pass C (z forward, x G-hat, z inverse), lines (ky, kx)
 template <typename R>
-__global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g, FftLine<R> L) {
+__global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
+    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const int P = L.P, P2 = 2 * P;
     const int ky = blockIdx.y;
-    const int kx = blockIdx.x * FFT_LY + threadIdx.y;
-    C* a = sm + threadIdx.y * 2 * L.P;
-    C* b = a + L.P;
+    const int kx0 = blockIdx.x * fft_ly<R>();
+    const int kx = kx0 + threadIdx.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    C* a = sm + threadIdx.y * P2;
+    C* b = a + P;
     const bool live = kx < g.Kx;
-    for (int j = threadIdx.x; j < L.P; j += blockDim.x) a[j] = C{R(0), R(0)};
+    for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
     __syncthreads();
-    if (live)
-        for (int t = threadIdx.x; t < g.in_n[2]; t += blockDim.x) {
-            const int j = pidx(g.in_lo[2] + t, g.Pz);
-            a[j] = spec[((size_t)j * g.Py + ky) * g.Kx + kx];
-        }
+    for (int e = tid; e < fft_ly<R>() * g.in_n[2]; e += nth) {
+        const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
+        if (kx0 + ly >= g.Kx) continue;
+        const int j = pidx(g.in_lo[2] + t, g.Pz);
+        sm[ly * P2 + j] = spec[((size_t)j * g.Py + ky) * g.Kx + kx0 + ly];
+    }
     __syncthreads();
     C* r = fft_line<R>(a, b, L, -1);
     const int fy = ky <= g.Py - ky ? ky : g.Py - ky;
-    for (int kz = threadIdx.x; kz < L.P; kz += blockDim.x) {
+    for (int kz = threadIdx.x; kz < P; kz += blockDim.x) {
         const int fz = kz <= g.Pz - kz ? kz : g.Pz - kz;
         const R gv = live ? ghat[((size_t)fz * g.Ky + fy) * g.Kx + kx] : R(0);
         r[kz] = C{r[kz].x * gv, r[kz].y * gv};
     }
     __syncthreads();
     C* other = (r == a) ? b : a;
-    C* q = fft_line<R>(r, other, L, +1);
-    if (live)
-        for (int t = threadIdx.x; t < g.out_n[2]; t += blockDim.x) {
-            const int z = pidx(g.out_lo[2] + t, g.Pz);
-            spec[((size_t)z * g.Py + ky) * g.Kx + kx] = q[z];
-        }
+    const int qoff = (int)(fft_line<R>(r, other, L, +1) - a);
+    __syncthreads();
+    for (int e = tid; e < fft_ly<R>() * g.out_n[2]; e += nth) {
+        const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
+        if (kx0 + ly >= g.Kx) continue;
+        const int z = pidx(g.out_lo[2] + t, g.Pz);
+        spec[((size_t)z * g.Py + ky) * g.Kx + kx0 + ly] = sm[ly * P2 + qoff + z];
+    }
 }
 
 // ---------------------------------------------------------------- pass B' (y inverse), lines (output z, kx)
 template <typename R>
-__global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
+__global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
+    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const int P = L.P, P2 = 2 * P;
     const int z = pidx(g.out_lo[2] + (int)blockIdx.y, g.Pz);
-    const int kx = blockIdx.x * FFT_LY + threadIdx.y;
-    C* a = sm + threadIdx.y * 2 * L.P;
-    C* b = a + L.P;
-    const bool live = kx < g.Kx;
-    for (int y = threadIdx.x; y < L.P; y += blockDim.x)
-        a[y] = live ? spec[((size_t)z * g.Py + y) * g.Kx + kx] : C{R(0), R(0)};
+    const int kx0 = blockIdx.x * fft_ly<R>();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    C* a = sm + threadIdx.y * P2;
+    C* b = a + P;
+    for (int e = tid; e < fft_ly<R>() * P; e += nth) {
+        const int ly = e % fft_ly<R>(), y = e / fft_ly<R>();
+        sm[ly * P2 + y] = kx0 + ly < g.Kx ? spec[((size_t)z * g.Py + y) * g.Kx + kx0 + ly] : C{R(0), R(0)};
+    }
     __syncthreads();
-    C* r = fft_line<R>(a, b, L, +1);
-    if (live)
-        for (int t = threadIdx.x; t < g.out_n[1]; t += blockDim.x) {
-            const int y = pidx(g.out_lo[1] + t, g.Py);
-            spec[((size_t)z * g.Py + y) * g.Kx + kx] = r[y];
-        }
+    const int roff = (int)(fft_line<R>(a, b, L, +1) - a);
+    __syncthreads();
+    for (int e = tid; e < fft_ly<R>() * g.out_n[1]; e += nth) {
+        const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
+        if (kx0 + ly >= g.Kx) continue;
+        const int y = pidx(g.out_lo[1] + t, g.Py);
+        spec[((size_t)z * g.Py + y) * g.Kx + kx0 + ly] = sm[ly * P2 + roff + y];
+    }
 }
 
 // ---------------------------------------------------------------- pass A' (x inverse, half spectrum -> real)
@@ -304,11 +362,12 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
 // level-0 block whose (n+2)^3 box holds it (interior or ghost layer); dense
 // mode writes the dense output range.
 template <typename R>
-__global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> L) {
+__global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const int line = blockIdx.x * FFT_LY + threadIdx.y;
+    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const int line = blockIdx.x * fft_ly<R>() + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
     const bool live = line < g.out_n[1] * g.out_n[2];
@@ -368,17 +427,17 @@ template <typename R>
 static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec, const R* ghat, const R* src, R* dst,
                         cudaStream_t s) {
     using C = typename Cx<R>::T;
-    const dim3 blk(FFT_TX, FFT_LY);
+    const dim3 blk(fft_tx<R>(), fft_ly<R>());
     const FftLine<R> Lx = line_of<R>(p.ax[0]), Ly = line_of<R>(p.ax[1]), Lz = line_of<R>(p.ax[2]);
-    const size_t smx = sizeof(C) * 2 * FFT_LY * g.Px;
-    const size_t smy = sizeof(C) * 2 * FFT_LY * g.Py;
-    const size_t smz = sizeof(C) * 2 * FFT_LY * g.Pz;
-    const int kxb = (g.Kx + FFT_LY - 1) / FFT_LY;
-    k_fft_x_fwd<R><<<(g.in_n[1] * g.in_n[2] + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(spec, src, g, Lx);
+    const size_t smx = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Px;
+    const size_t smy = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Py;
+    const size_t smz = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Pz;
+    const int kxb = (g.Kx + fft_ly<R>() - 1) / fft_ly<R>();
+    k_fft_x_fwd<R><<<(g.in_n[1] * g.in_n[2] + fft_ly<R>() - 1) / fft_ly<R>(), blk, smx, s>>>(spec, src, g, Lx);
     k_fft_y_fwd<R><<<dim3(kxb, g.in_n[2]), blk, smy, s>>>(spec, g, Ly);
     k_fft_z_conv<R><<<dim3(kxb, g.Py), blk, smz, s>>>(spec, ghat, g, Lz);
     k_fft_y_inv<R><<<dim3(kxb, g.out_n[2]), blk, smy, s>>>(spec, g, Ly);
-    k_fft_x_inv<R><<<(g.out_n[1] * g.out_n[2] + FFT_LY - 1) / FFT_LY, blk, smx, s>>>(dst, spec, g, Lx);
+    k_fft_x_inv<R><<<(g.out_n[1] * g.out_n[2] + fft_ly<R>() - 1) / fft_ly<R>(), blk, smx, s>>>(dst, spec, g, Lx);
 }
 
 // Level-0 solve of every problem of the handle, one after another on s (they
@@ -691,6 +750,10 @@ int fft_plan(Handle& h) {
             ax.P = smooth_length(2 * p.n0[a] + 1);
             ax.K = ax.P / 2 + 1;
             if (!factor(ax.P, ax.rad, ax.nrad)) return MRP_ERR_UNSUPPORTED;
+            // a CTA holds (2 LY + 1) P complex values of its lines and twiddles
+            if (sizeof(double2) * (2 * fft_ly<double>() + 1) * (size_t)ax.P > (size_t)MAX_DYN_SMEM ||
+                sizeof(float2) * (2 * fft_ly<float>() + 1) * (size_t)ax.P > (size_t)MAX_DYN_SMEM)
+                return MRP_ERR_UNSUPPORTED;
             std::vector<double2> tw(ax.P);
             for (int m = 0; m < ax.P; ++m) {
                 const double ang = 2.0 * pi * (double)m / (double)ax.P;
