@@ -155,10 +155,13 @@ __device__ __forceinline__ void shell_coords(int t, int S, int& x, int& y, int& 
     x = (q & 1) ? S - 1 : 0;
 }
 
-// Shared scratch of build_halo besides the block itself.
+// Shared scratch of build_halo besides the block itself.  The second group
+// of fields belongs to the transposed ghost fill.
 template <typename T>
 struct HaloSmem {
-    int snbr[27], cnbr[27], cleaf[27], cch[27 * 8], off[27], rdir[27], rstart[27];
+    int snbr[27], cnbr[27], cleaf[27], cch[27 * 8];
+    int rdir[26], roff[26], raoff[26], lo3[3], hi3[3];
+    int off[27], rstart[27];
     T sw[8];
     int interp, nreg, ntot;
 };
@@ -168,169 +171,301 @@ __host__ __device__ inline int pool_size(int n, int I) {
     return 6 * TN * TN + 12 * TN + 8;
 }
 
+// x / d for 0 <= x < 2^16 and 2 <= d < 2^16, with m = magic_of(d).
+__device__ __forceinline__ unsigned magic_of(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
+__device__ __forceinline__ int fdiv(int x, unsigned m) { return (int)__umulhi((unsigned)x, m); }
+
+// Per-axis description of one interpolated ghost region d: its tangential
+// axes ta0 < ta1 (x, y, z order) with their patch strides, the patch strides
+// of the normal axes on a -1 side (I-point midpoint stencils) and the patch
+// offset of its element 0 (a +1 side is the coincident coarse node, patch
+// index `up`; a tangential axis starts at patch index 1).  All fields are
+// scalars so that the region stays in registers.
+struct Region {
+    int d0, d1, d2;            // side per axis: -1, 0 (tangential), +1
+    int nt, nn, ta0, ta1;
+    int ts0, ts1, ns0, ns1, ns2, p0;
+};
+__device__ __forceinline__ Region region_of(int d, int PL, int up) {
+    Region g;
+    g.d0 = d % 3 - 1; g.d1 = (d / 3) % 3 - 1; g.d2 = d / 9 - 1;
+    g.nt = 0; g.nn = 0; g.ta0 = 0; g.ta1 = 0;
+    g.ts0 = 0; g.ts1 = 0; g.ns0 = 0; g.ns1 = 0; g.ns2 = 0; g.p0 = 0;
+    const int dd[3] = {g.d0, g.d1, g.d2};
+    int st = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] == 0) {
+            if (g.nt == 0) { g.ta0 = a; g.ts0 = st; } else { g.ta1 = a; g.ts1 = st; }
+            ++g.nt;
+            g.p0 += st;
+        } else if (dd[a] < 0) {
+            if (g.nn == 0) g.ns0 = st; else if (g.nn == 1) g.ns1 = st; else g.ns2 = st;
+            ++g.nn;
+        } else {
+            g.p0 += up * st;
+        }
+        st *= PL;
+    }
+    return g;
+}
+// Box coordinate on axis a of the region's ghost node with tangential box
+// coordinates u1 (axis ta0) and v1 (axis ta1).
+__device__ __forceinline__ int box_coord(int side, int a, const Region& g, int S, int u1, int v1) {
+    return side != 0 ? (side < 0 ? 0 : S - 1) : (a == g.ta0 ? u1 : v1);
+}
+
+// Builds the block's (n+2)^3 box in shared memory (parity-split layout).
+//  1. Copied values, one thread per (X, Y) column of the box, walking Z: the
+//     block's own interior, same-level neighbours' interiors, and the stored
+//     ghost layer where the region lies outside the domain.
+//  2. Interpolated regions (no same-level neighbour), separably:
+//     a. stage the coarse patch over the hull of the regions' stencils;
+//     b. reduce each region along its normal axes (one value per coarse
+//        tangential node);
+//     c. faces: interpolate along the first tangential axis into fine x
+//        coarse rows; edges and corners: final values;
+//     d. faces: interpolate along the second tangential axis.
+//     Work items are ordered so that the lanes of a warp share the parity of
+//     the interpolated coordinate (the same stencil length).
 template <typename T, int I>
 __device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, HaloSmem<T>& hs,
                            const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk, const LevelView& lc,
-                           int b, int n, const Split& sp, const Cset& cs) {
+                           int b, int n, const Split& sp) {
     const int S = n + 2, S2 = S * S, S3 = S2 * S;
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int H = sp.H, H2 = sp.H2, H3p = sp.H3p;
+    const int h = n >> 1;
     if (tid < 27) hs.snbr[tid] = lk.nbr[27 * b + tid];
-    if (tid < I) hs.sw[tid] = T(midw<I>(tid));
     __syncthreads();
-    const T* Ub = Uk + (size_t)b * S3;
-    if (tid == 0) {
-        int any = 0;
-        for (int d = 0; d < 27; ++d) any |= (d != 13 && hs.snbr[d] == NBR_MISSING);
-        hs.interp = any;
+    if (tid < 32) {
+        const bool miss = tid < 27 && tid != 13 && hs.snbr[tid] == NBR_MISSING;
+        const unsigned any = __ballot_sync(0xffffffffu, miss);
+        if (tid == 0) hs.interp = any != 0u;
     }
-    const int n3 = n * n * n;
-    for (int col = 0; col < 8; ++col) {
-        const Col c = colour(col, sp, n);
+    // 1. copied values
+    for (int c = tid; c < S2; c += nth) {
+        const int Y = c / S, X = c - Y * S;
+        const int rx = X == 0 ? -1 : (X == S - 1 ? 1 : 0);
+        const int ry = Y == 0 ? -1 : (Y == S - 1 ? 1 : 0);
+        T* dcol = su + ((((Y & 1) << 1) | (X & 1)) * H3p + (Y >> 1) * H + (X >> 1));
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < cs.cnt) {
-                const Node d = node_of(cs.q[k], sp, n);
-                su[c.cb + d.b0 + c.dX + c.dY + c.dZ] = Ub[d.g + c.go];
+        for (int rz = -1; rz <= 1; ++rz) {
+            const int j = hs.snbr[dir27(rx, ry, rz)];
+            if (j == NBR_MISSING) continue;
+            // source column: same-level block j (shifted into its own box), or this block's stored ghost layer
+            const size_t col = j >= 0 ? (size_t)j * S3 + (size_t)((Y - ry * n) * S + X - rx * n)
+                                      : (size_t)b * S3 + (size_t)(Y * S + X);
+            if (rz != 0) {
+                const int Z = rz < 0 ? 0 : S - 1;
+                const int Zs = j >= 0 ? Z - rz * n : Z;
+                dcol[(Z & 1) * 4 * H3p + (Z >> 1) * H2] = Uk[col + (size_t)Zs * S2];
+            } else {
+                // Z = 2m + 1 (odd sub-array, index m) and Z = 2m + 2 (even sub-array, index m + 1)
+                for (int m0 = 0; m0 < h; m0 += 4) {
+                    T v[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (m0 + q < h) {
+                            v[2 * q] = Uk[col + (size_t)(2 * (m0 + q) + 1) * S2];
+                            v[2 * q + 1] = Uk[col + (size_t)(2 * (m0 + q) + 2) * S2];
+                        }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (m0 + q < h) {
+                            dcol[4 * H3p + (m0 + q) * H2] = v[2 * q];
+                            dcol[(m0 + q + 1) * H2] = v[2 * q + 1];
+                        }
+                }
             }
-    }
-    const int shell = S3 - n3;
-    for (int t = tid; t < shell; t += nth) {
-        int x, y, z;
-        shell_coords(t, S, x, y, z);
-        const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
-        const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
-        const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
-        const int j = hs.snbr[dir27(dx, dy, dz)];
-        const int o = (z * S + y) * S + x;
-        if (j >= 0) su[sp.at(x, y, z)] = Uk[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)];
-        else if (j == NBR_OUTSIDE) su[sp.at(x, y, z)] = Ub[o];
+        }
     }
     __syncthreads();
     if (!hs.interp) return;
-    // coarse-neighbourhood tables of the parent
+    // 2. interpolated regions: coarse-neighbourhood tables of the parent, region list, patch hull
     const int P = lk.parent[b];
     if (tid < 27) {
         const int cb = lc.nbr[27 * P + tid];
+        const int leaf = cb >= 0 ? (int)lc.is_leaf[cb] : 1;
         hs.cnbr[tid] = cb;
-        hs.cleaf[tid] = cb >= 0 ? (int)lc.is_leaf[cb] : 1;
-        for (int o = 0; o < 8; ++o) hs.cch[8 * tid + o] = (cb >= 0 && !hs.cleaf[tid]) ? lc.children[8 * cb + o] : -1;
+        hs.cleaf[tid] = leaf;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) hs.cch[8 * tid + o] = (cb >= 0 && !leaf) ? lc.children[8 * cb + o] : -1;
     }
+    constexpr int plo = 4 - I / 2;
     const int TN = tan_n(n, I), TN2 = TN * TN;
+    const int PL = h + I, PL2 = PL * PL;
+    const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
     if (tid == 0) {
-        int o = 0, nr = 0;
+        int o = 0, oa = 0, nr = 0;
+        int lo3[3] = {PL, PL, PL}, hi3[3] = {0, 0, 0};
         for (int d = 0; d < 27; ++d) {
-            hs.off[d] = o;
             if (d == 13 || hs.snbr[d] != NBR_MISSING) continue;
-            const int nt = (d % 3 == 1) + ((d / 3) % 3 == 1) + (d / 9 == 1);
+            const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+            int nt = 0;
+            for (int a = 0; a < 3; ++a) {
+                const int l = dd[a] < 0 ? 0 : (dd[a] > 0 ? up : 1);
+                const int e = dd[a] < 0 ? I : (dd[a] > 0 ? up + 1 : PL);
+                nt += dd[a] == 0;
+                lo3[a] = l < lo3[a] ? l : lo3[a];
+                hi3[a] = e > hi3[a] ? e : hi3[a];
+            }
             hs.rdir[nr] = d;
-            hs.rstart[nr] = o;
-            ++nr;
+            hs.roff[nr] = o;
+            hs.raoff[nr] = oa;
             o += nt == 2 ? TN2 : (nt == 1 ? TN : 1);
+            oa += nt == 2 ? n * TN : 0;
+            ++nr;
         }
         hs.nreg = nr;
-        hs.ntot = o;
+        for (int a = 0; a < 3; ++a) { hs.lo3[a] = lo3[a]; hs.hi3[a] = hi3[a]; }
     }
     __syncthreads();
-    const int h = n >> 1;
-    const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
-    // stage the coarse patch, patch indices [plo, plo + PL) per axis (every
-    // normal and tangential stencil of this block's ghosts lies inside)
-    constexpr int plo = 4 - I / 2;
-    const int PL = h + I, PL2 = PL * PL, PL3 = PL2 * PL;
-    const int base[3] = {(bx & 1) * h - 4 + plo, (by & 1) * h - 4 + plo, (bz & 1) * h - 4 + plo};
-    for (int t = tid; t < PL3; t += nth) {
-        const int px = t % PL, py = (t / PL) % PL, pz = t / PL2;
-        const int rx = base[0] + px, ry = base[1] + py, rz = base[2] + pz;
-        const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0);
-        const int ey = ry < 0 ? -1 : (ry >= n ? 1 : 0);
-        const int ez = rz < 0 ? -1 : (rz >= n ? 1 : 0);
-        const int d = dir27(ex, ey, ez);
-        const int lx = rx - ex * n, ly = ry - ey * n, lz = rz - ez * n;
-        T v;
-        if (hs.cleaf[d]) {
-            v = Uc[(size_t)hs.cnbr[d] * S3 + ((lz + 1) * S + ly + 1) * S + lx + 1];
-        } else {
-            // covered coarse node: the coincident fine node of the current level
-            const int ox = lx >= h, oy = ly >= h, oz = lz >= h;
-            const int ch = hs.cch[8 * d + ox + 2 * oy + 4 * oz];
-            const int FX = 2 * lx - ox * n + 1, FY = 2 * ly - oy * n + 1, FZ = 2 * lz - oz * n + 1;
-            v = ch == b ? su[sp.at(FX, FY, FZ)] : Uk[(size_t)ch * S3 + (FZ * S + FY) * S + FX];
-        }
-        patch[t] = v;
-    }
-    __syncthreads();
-    // phase 1: reduce every interpolated region along its normal axes; the
-    // (region, element) pairs are spread evenly over the CTA
-    const int lo = 0;                   // stencil around fine coordinate -1: patch [4 - I/2, 4 + I/2) - plo
-    const int up = 4 + h - plo;         // patch index coincident with fine coordinate n
-    const int tlo = tan_lo<I>() - plo;
-    const int total = hs.ntot;
-    for (int f = tid; f < total; f += nth) {
-        int r = 0;
-        while (r + 1 < hs.nreg && hs.rstart[r + 1] <= f) ++r;
-        const int d = hs.rdir[r];
-        const int e = f - hs.rstart[r];
-        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        int tc[3] = {0, 0, 0};
-        int rem = e;
-        if (dx == 0) { tc[0] = tlo + rem % TN; rem /= TN; }
-        if (dy == 0) { tc[1] = tlo + rem % TN; rem /= TN; }
-        if (dz == 0) { tc[2] = tlo + rem % TN; }
-        const int cx = dx < 0 ? I : 1, cy = dy < 0 ? I : 1, cz = dz < 0 ? I : 1;
-        const int x0 = dx < 0 ? lo : (dx > 0 ? up : tc[0]);
-        const int y0 = dy < 0 ? lo : (dy > 0 ? up : tc[1]);
-        const int z0 = dz < 0 ? lo : (dz > 0 ? up : tc[2]);
-        T acc = T(0);
-        for (int mz = 0; mz < cz; ++mz) {
-            T ay = T(0);
-            for (int my = 0; my < cy; ++my) {
-                const T* row = patch + ((z0 + mz) * PL + y0 + my) * PL + x0;
-                T ax = T(0);
-                if (cx == 1) ax = row[0];
-                else {
-#pragma unroll
-                    for (int mx = 0; mx < I; ++mx) ax += hs.sw[mx] * row[mx];
+    // 2a. coarse patch over the hull; patch index p on an axis is coarse
+    //     coordinate base + p relative to the parent's origin
+    {
+        const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
+        const int bs0 = (bx & 1) * h - 4 + plo, bs1 = (by & 1) * h - 4 + plo, bs2 = (bz & 1) * h - 4 + plo;
+        const int L0 = hs.hi3[0] - hs.lo3[0], L1 = hs.hi3[1] - hs.lo3[1];
+        const int z0 = hs.lo3[2], z1 = hs.hi3[2];
+        for (int c = tid; c < L0 * L1; c += nth) {
+            const int q1 = c / L0, q0 = c - q1 * L0;
+            const int px = hs.lo3[0] + q0, py = hs.lo3[1] + q1;
+            const int rx = bs0 + px, ry = bs1 + py;
+            const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0), ey = ry < 0 ? -1 : (ry >= n ? 1 : 0);
+            const int lx = rx - ex * n, ly = ry - ey * n;
+            const int ox = lx >= h, oy = ly >= h;
+            const int FX = 2 * lx - ox * n + 1, FY = 2 * ly - oy * n + 1;
+            T* pcol = patch + py * PL + px;
+#pragma unroll 4
+            for (int pz = z0; pz < z1; ++pz) {
+                const int rz = bs2 + pz;
+                const int ez = rz < 0 ? -1 : (rz >= n ? 1 : 0);
+                const int lz = rz - ez * n;
+                const int d = dir27(ex, ey, ez);
+                const T* src;
+                if (hs.cleaf[d]) {
+                    src = Uc + ((size_t)hs.cnbr[d] * S3 + (size_t)(((lz + 1) * S + ly + 1) * S + lx + 1));
+                } else {
+                    // covered coarse node: the coincident fine node of the current level
+                    const int oz = lz >= h;
+                    const int ch = hs.cch[8 * d + ox + 2 * oy + 4 * oz];
+                    const int FZ = 2 * lz - oz * n + 1;
+                    src = ch == b ? su + sp.at(FX, FY, FZ) : Uk + ((size_t)ch * S3 + (size_t)((FZ * S + FY) * S + FX));
                 }
-                ay += (cy == 1 ? T(1) : hs.sw[my]) * ax;
+                pcol[pz * PL2] = *src;
             }
-            acc += (cz == 1 ? T(1) : hs.sw[mz]) * ay;
         }
-        pool[hs.off[d] + e] = acc;
     }
     __syncthreads();
-    // phase 2: tangential interpolation of each ghost node from its region's reduced array
-    for (int t = tid; t < shell; t += nth) {
-        int x, y, z;
-        shell_coords(t, S, x, y, z);
-        const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
-        const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
-        const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
-        const int d = dir27(dx, dy, dz);
-        if (hs.snbr[d] != NBR_MISSING) continue;
-        const T* R = pool + hs.off[d];
-        int st0 = 0, st1 = 0, cn0 = 1, cn1 = 1, sd0 = 0, sd1 = 0, nt = 0, stride = 1;
-        const int q[3] = {x - 1, y - 1, z - 1};
-        const int dd[3] = {dx, dy, dz};
+    T w[I];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (dd[a] != 0) continue;
-            const int qa = q[a];
-            // reduced-array index = patch index - tan_lo (patch index 4 + floor(q/2) at or left of q)
-            const int st = (qa & 1) ? 4 + ((qa - 1) >> 1) - I / 2 + 1 - tan_lo<I>() : 4 + (qa >> 1) - tan_lo<I>();
-            const int cn = (qa & 1) ? I : 1;
-            if (nt == 0) { st0 = st; cn0 = cn; sd0 = stride; }
-            else { st1 = st; cn1 = cn; sd1 = stride; }
-            stride *= TN;
-            ++nt;
+    for (int m = 0; m < I; ++m) w[m] = T(midw<I>(m));
+    const unsigned mTN = magic_of(TN);
+    // 2b. reduction along the normal axes: one value per coarse tangential node
+    for (int r = 0; r < hs.nreg; ++r) {
+        const Region g = region_of(hs.rdir[r], PL, up);
+        const int cnt = g.nt == 2 ? TN2 : (g.nt == 1 ? TN : 1);
+        const int s0 = g.ns0, s1 = g.ns1, s2 = g.ns2, t0 = g.ts0, t1 = g.ts1;
+        T* R = pool + hs.roff[r];
+        for (int e = tid; e < cnt; e += nth) {
+            const int e1 = g.nt == 2 ? fdiv(e, mTN) : 0, e0 = e - e1 * TN;
+            const T* p = patch + g.p0 + e0 * t0 + e1 * t1;
+            T acc = T(0);
+            if (g.nn == 0) {
+                acc = p[0];
+            } else if (g.nn == 1) {
+#pragma unroll
+                for (int m = 0; m < I; ++m) acc += w[m] * p[m * s0];
+            } else if (g.nn == 2) {
+#pragma unroll
+                for (int m1 = 0; m1 < I; ++m1) {
+                    T a = T(0);
+#pragma unroll
+                    for (int m = 0; m < I; ++m) a += w[m] * p[m * s0 + m1 * s1];
+                    acc += w[m1] * a;
+                }
+            } else {
+#pragma unroll 1
+                for (int m2 = 0; m2 < I; ++m2) {
+                    T a2 = T(0);
+#pragma unroll 1
+                    for (int m1 = 0; m1 < I; ++m1) {
+                        T a = T(0);
+#pragma unroll
+                        for (int m = 0; m < I; ++m) a += w[m] * p[m * s0 + m1 * s1 + m2 * s2];
+                        a2 += T(midw<I>(m1)) * a;
+                    }
+                    acc += T(midw<I>(m2)) * a2;
+                }
+            }
+            R[e] = acc;
         }
-        T acc = T(0);
-        for (int m1 = 0; m1 < cn1; ++m1) {
-            T a0 = T(0);
-            const int rb = (st1 + m1) * sd1 + st0 * sd0;
-            for (int m0 = 0; m0 < cn0; ++m0) a0 += (cn0 == 1 ? T(1) : hs.sw[m0]) * R[rb + m0 * sd0];
-            acc += (cn1 == 1 ? T(1) : hs.sw[m1]) * a0;
+    }
+    __syncthreads();
+    // 2c. faces: along the first tangential axis into A[v'][u] (fine u, coarse
+    //     v'); edges and corners: their ghost values.  A reuses the patch.
+    //     Reduced-array start of the stencil of fine coordinate q: q/2 + I/2 - 1
+    //     (q even, one point) or (q - 1)/2 (q odd, I points).
+    T* A = patch;
+    const unsigned mh = magic_of(h), mn = magic_of(n);
+    for (int r = 0; r < hs.nreg; ++r) {
+        const Region g = region_of(hs.rdir[r], PL, up);
+        const T* R = pool + hs.roff[r];
+        if (g.nt == 2) {
+            T* Ar = A + hs.raoff[r];
+            for (int e = tid; e < n * TN; e += nth) {
+                const int par = e >= h * TN;
+                const int e2 = e - par * h * TN;
+                const int v = fdiv(e2, mh), u = 2 * (e2 - v * h) + par;
+                T acc = T(0);
+                if (!par) {
+                    acc = R[v * TN + u / 2 + I / 2 - 1];
+                } else {
+                    const T* q = R + v * TN + (u - 1) / 2;
+#pragma unroll
+                    for (int m = 0; m < I; ++m) acc += w[m] * q[m];
+                }
+                Ar[v * n + u] = acc;
+            }
+        } else if (g.nt == 1) {
+            for (int u = tid; u < n; u += nth) {
+                T acc = T(0);
+                if (!(u & 1)) {
+                    acc = R[u / 2 + I / 2 - 1];
+                } else {
+#pragma unroll
+                    for (int m = 0; m < I; ++m) acc += w[m] * R[(u - 1) / 2 + m];
+                }
+                su[sp.at(box_coord(g.d0, 0, g, S, u + 1, 0), box_coord(g.d1, 1, g, S, u + 1, 0),
+                         box_coord(g.d2, 2, g, S, u + 1, 0))] = acc;
+            }
+        } else if (tid == 0) {
+            su[sp.at(box_coord(g.d0, 0, g, S, 0, 0), box_coord(g.d1, 1, g, S, 0, 0), box_coord(g.d2, 2, g, S, 0, 0))] =
+                R[0];
         }
-        su[sp.at(x, y, z)] = acc;
+    }
+    __syncthreads();
+    // 2d. faces: along the second tangential axis (fine v), rows of fine u
+    for (int r = 0; r < hs.nreg; ++r) {
+        const Region g = region_of(hs.rdir[r], PL, up);
+        if (g.nt != 2) continue;
+        const T* Ar = A + hs.raoff[r];
+        for (int e = tid; e < n * n; e += nth) {
+            const int row = fdiv(e, mn), u = e - row * n;
+            const int par = row >= h;
+            const int v = 2 * (row - par * h) + par;
+            T acc = T(0);
+            if (!par) {
+                acc = Ar[(v / 2 + I / 2 - 1) * n + u];
+            } else {
+                const T* q = Ar + ((v - 1) / 2) * n + u;
+#pragma unroll
+                for (int m = 0; m < I; ++m) acc += w[m] * q[m * n];
+            }
+            su[sp.at(box_coord(g.d0, 0, g, S, u + 1, v + 1), box_coord(g.d1, 1, g, S, u + 1, v + 1),
+                     box_coord(g.d2, 2, g, S, u + 1, v + 1))] = acc;
+        }
     }
     __syncthreads();
 }
@@ -361,7 +496,7 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, lc, b, n, sp, cs);
+    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, lc, b, n, sp);
     const T* Fb = F + (size_t)b * n * n * n;
     const T inv_c = T(1) / T(LW<M>::c);
     for (int col = 0; col < 8; ++col) {
@@ -376,15 +511,18 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
             }
         __syncthreads();
     }
-    T* Ob = Uout + (size_t)b * (n + 2) * (n + 2) * (n + 2);
-    for (int col = 0; col < 8; ++col) {
-        const Col c = colour(col, sp, n);
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < cs.cnt) {
-                const Node d = node_of(cs.q[k], sp, n);
-                Ob[d.g + c.go] = su[c.cb + d.b0 + c.dX + c.dY + c.dZ];
-            }
+    // interior back to global, one thread per (x, y) column
+    const int S = n + 2, S2 = S * S;
+    T* Ob = Uout + (size_t)b * S2 * S;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int y = c / n, x = c - y * n;
+        const int X = x + 1, Y = y + 1;
+        const T* scol = su + ((((Y & 1) << 1) | (X & 1)) * sp.H3p + (Y >> 1) * sp.H + (X >> 1));
+        T* gcol = Ob + (Y * S + X);
+        for (int m = 0; m < (n >> 1); ++m) {
+            gcol[(2 * m + 1) * S2] = scol[4 * sp.H3p + m * sp.H2];
+            gcol[(2 * m + 2) * S2] = scol[(m + 1) * sp.H2];
+        }
     }
 }
 
@@ -402,7 +540,7 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     for (int col = 0; col < 8; ++col) {
         const Col c = colour(col, sp, n);
@@ -449,7 +587,7 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
         }
         return;
     }
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
     for (int col = 0; col < 8; ++col) {
         const Col c = colour(col, sp, n);
 #pragma unroll
@@ -494,7 +632,7 @@ __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, c
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = blocks[blockIdx.x];
-    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     double m = 0.0;
     for (int col = 0; col < 8; ++col) {
@@ -525,11 +663,9 @@ __global__ void __launch_bounds__(512) k_halo_dump(T* __restrict__ U, const T* _
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem<T> hs;
-    Cset cs;
-    cset_init(cs, n >> 1);
     const int S = n + 2, S3 = S * S * S;
     const int b = blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp, cs);
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
     for (int t = threadIdx.x; t < S3 - n * n * n; t += blockDim.x) {
         int x, y, z;
         shell_coords(t, S, x, y, z);
