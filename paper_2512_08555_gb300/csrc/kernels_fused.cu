@@ -155,13 +155,15 @@ __device__ __forceinline__ void shell_coords(int t, int S, int& x, int& y, int& 
     x = (q & 1) ? S - 1 : 0;
 }
 
-// Shared scratch of build_halo besides the block itself.  The second group
-// of fields belongs to the transposed ghost fill.
+// Shared scratch of build_halo besides the block itself: the block's
+// neighbourhood record.
+struct __align__(16) HaloSmem {
+    int rec[REC_INTS];
+};
+// Shared scratch of the transposed ghost fill.
 template <typename T>
-struct HaloSmem {
-    int snbr[27], cnbr[27], cleaf[27], cch[27 * 8];
-    int rdir[26], roff[26], raoff[26], lo3[3], hi3[3];
-    int off[27], rstart[27];
+struct HaloSmemT {
+    int snbr[27], cnbr[27], cleaf[27], cch[27 * 8], off[27], rdir[27], rstart[27];
     T sw[8];
     int interp, nreg, ntot;
 };
@@ -174,6 +176,20 @@ __host__ __device__ inline int pool_size(int n, int I) {
 // x / d for 0 <= x < 2^16 and 2 <= d < 2^16, with m = magic_of(d).
 __device__ __forceinline__ unsigned magic_of(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
 __device__ __forceinline__ int fdiv(int x, unsigned m) { return (int)__umulhi((unsigned)x, m); }
+
+// Asynchronous global -> shared copies (cp.async): one element, or 16 bytes.
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* sdst, const T* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Per-axis description of one interpolated ghost region d: its tangential
 // axes ta0 < ta1 (x, y, z order) with their patch strides, the patch strides
@@ -215,10 +231,31 @@ __device__ __forceinline__ int box_coord(int side, int a, const Region& g, int S
     return side != 0 ? (side < 0 ? 0 : S - 1) : (a == g.ta0 ? u1 : v1);
 }
 
+// Starts the copy of block b's neighbourhood record into shared memory (one
+// cp.async group, committed); the caller waits for it.
+__device__ __forceinline__ void load_record(HaloSmem& hs, const LevelView& lk, int b) {
+    for (int c = threadIdx.x; c < REC_INTS / 4; c += blockDim.x)
+        cp_async16(&hs.rec[4 * c], lk.rec + (size_t)b * REC_INTS + 4 * c);
+    cp_async_commit();
+}
+
+// Starts the copy of block b's n^3 right-hand side into shared memory if
+// `on` (F and fs 16-byte aligned), and commits a cp.async group either way.
+template <typename T>
+__device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict__ F, int b, int n, bool on) {
+    const int chunks = on ? n * n * n * (int)sizeof(T) / 16 : 0;
+    const char* src = reinterpret_cast<const char*>(F + (size_t)b * n * n * n);
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) cp_async16(reinterpret_cast<char*>(fs) + 16 * c, src + 16 * c);
+    cp_async_commit();
+}
+
 // Builds the block's (n+2)^3 box in shared memory (parity-split layout).
+// Expects the block's record in hs (complete and visible: the caller waited
+// for its copy and synchronised).  Waits for every cp.async group of the
+// thread, so a right-hand side staged by the caller is complete on return.
 //  1. Copied values, one thread per (X, Y) column of the box, walking Z: the
 //     block's own interior, same-level neighbours' interiors, and the stored
-//     ghost layer where the region lies outside the domain.
+//     ghost layer where the region lies outside the domain (cp.async).
 //  2. Interpolated regions (no same-level neighbour), separably:
 //     a. stage the coarse patch over the hull of the regions' stencils;
 //     b. reduce each region along its normal axes (one value per coarse
@@ -229,20 +266,14 @@ __device__ __forceinline__ int box_coord(int side, int a, const Region& g, int S
 //     Work items are ordered so that the lanes of a warp share the parity of
 //     the interpolated coordinate (the same stencil length).
 template <typename T, int I>
-__device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, HaloSmem<T>& hs,
-                           const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk, const LevelView& lc,
-                           int b, int n, const Split& sp) {
+__device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, const HaloSmem& hs,
+                           const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk, int b, int n,
+                           const Split& sp) {
     const int S = n + 2, S2 = S * S, S3 = S2 * S;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int H = sp.H, H2 = sp.H2, H3p = sp.H3p;
     const int h = n >> 1;
-    if (tid < 27) hs.snbr[tid] = lk.nbr[27 * b + tid];
-    __syncthreads();
-    if (tid < 32) {
-        const bool miss = tid < 27 && tid != 13 && hs.snbr[tid] == NBR_MISSING;
-        const unsigned any = __ballot_sync(0xffffffffu, miss);
-        if (tid == 0) hs.interp = any != 0u;
-    }
+    const int* __restrict__ snbr = hs.rec + REC_SNBR;
     // 1. copied values
     for (int c = tid; c < S2; c += nth) {
         const int Y = c / S, X = c - Y * S;
@@ -251,221 +282,196 @@ __device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restri
         T* dcol = su + ((((Y & 1) << 1) | (X & 1)) * H3p + (Y >> 1) * H + (X >> 1));
 #pragma unroll
         for (int rz = -1; rz <= 1; ++rz) {
-            const int j = hs.snbr[dir27(rx, ry, rz)];
+            const int j = snbr[dir27(rx, ry, rz)];
             if (j == NBR_MISSING) continue;
             // source column: same-level block j (shifted into its own box), or this block's stored ghost layer
-            const size_t col = j >= 0 ? (size_t)j * S3 + (size_t)((Y - ry * n) * S + X - rx * n)
-                                      : (size_t)b * S3 + (size_t)(Y * S + X);
+            const T* col = Uk + (j >= 0 ? (size_t)j * S3 + (size_t)((Y - ry * n) * S + X - rx * n)
+                                        : (size_t)b * S3 + (size_t)(Y * S + X));
             if (rz != 0) {
                 const int Z = rz < 0 ? 0 : S - 1;
                 const int Zs = j >= 0 ? Z - rz * n : Z;
-                dcol[(Z & 1) * 4 * H3p + (Z >> 1) * H2] = Uk[col + (size_t)Zs * S2];
+                cp_async_el(dcol + (Z & 1) * 4 * H3p + (Z >> 1) * H2, col + (size_t)Zs * S2);
             } else {
                 // Z = 2m + 1 (odd sub-array, index m) and Z = 2m + 2 (even sub-array, index m + 1)
-                for (int m0 = 0; m0 < h; m0 += 4) {
-                    T v[8];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (m0 + q < h) {
-                            v[2 * q] = Uk[col + (size_t)(2 * (m0 + q) + 1) * S2];
-                            v[2 * q + 1] = Uk[col + (size_t)(2 * (m0 + q) + 2) * S2];
-                        }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (m0 + q < h) {
-                            dcol[4 * H3p + (m0 + q) * H2] = v[2 * q];
-                            dcol[(m0 + q + 1) * H2] = v[2 * q + 1];
-                        }
+                for (int m = 0; m < h; ++m) {
+                    cp_async_el(dcol + 4 * H3p + m * H2, col + (size_t)(2 * m + 1) * S2);
+                    cp_async_el(dcol + (m + 1) * H2, col + (size_t)(2 * m + 2) * S2);
                 }
             }
         }
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    if (!hs.interp) return;
-    // 2. interpolated regions: coarse-neighbourhood tables of the parent, region list, patch hull
-    const int P = lk.parent[b];
-    if (tid < 27) {
-        const int cb = lc.nbr[27 * P + tid];
-        const int leaf = cb >= 0 ? (int)lc.is_leaf[cb] : 1;
-        hs.cnbr[tid] = cb;
-        hs.cleaf[tid] = leaf;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) hs.cch[8 * tid + o] = (cb >= 0 && !leaf) ? lc.children[8 * cb + o] : -1;
-    }
+    const int nreg = hs.rec[REC_NREG];
+    if (nreg == 0) return;
+    // 2. interpolated regions
     constexpr int plo = 4 - I / 2;
-    const int TN = tan_n(n, I), TN2 = TN * TN;
+    const int TN = tan_n(n, I);
     const int PL = h + I, PL2 = PL * PL;
     const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
-    if (tid == 0) {
-        int o = 0, oa = 0, nr = 0;
-        int lo3[3] = {PL, PL, PL}, hi3[3] = {0, 0, 0};
-        for (int d = 0; d < 27; ++d) {
-            if (d == 13 || hs.snbr[d] != NBR_MISSING) continue;
-            const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
-            int nt = 0;
-            for (int a = 0; a < 3; ++a) {
-                const int l = dd[a] < 0 ? 0 : (dd[a] > 0 ? up : 1);
-                const int e = dd[a] < 0 ? I : (dd[a] > 0 ? up + 1 : PL);
-                nt += dd[a] == 0;
-                lo3[a] = l < lo3[a] ? l : lo3[a];
-                hi3[a] = e > hi3[a] ? e : hi3[a];
-            }
-            hs.rdir[nr] = d;
-            hs.roff[nr] = o;
-            hs.raoff[nr] = oa;
-            o += nt == 2 ? TN2 : (nt == 1 ? TN : 1);
-            oa += nt == 2 ? n * TN : 0;
-            ++nr;
-        }
-        hs.nreg = nr;
-        for (int a = 0; a < 3; ++a) { hs.lo3[a] = lo3[a]; hs.hi3[a] = hi3[a]; }
-    }
-    __syncthreads();
+    const int* __restrict__ pnbr = hs.rec + REC_PNBR;
+    const int* __restrict__ pch = hs.rec + REC_PCH;
     // 2a. coarse patch over the hull; patch index p on an axis is coarse
     //     coordinate base + p relative to the parent's origin
     {
         const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
         const int bs0 = (bx & 1) * h - 4 + plo, bs1 = (by & 1) * h - 4 + plo, bs2 = (bz & 1) * h - 4 + plo;
-        const int L0 = hs.hi3[0] - hs.lo3[0], L1 = hs.hi3[1] - hs.lo3[1];
-        const int z0 = hs.lo3[2], z1 = hs.hi3[2];
+        const int lo0 = hs.rec[REC_LO], lo1 = hs.rec[REC_LO + 1], z0 = hs.rec[REC_LO + 2];
+        const int L0 = hs.rec[REC_HI] - lo0, L1 = hs.rec[REC_HI + 1] - lo1, z1 = hs.rec[REC_HI + 2];
         for (int c = tid; c < L0 * L1; c += nth) {
             const int q1 = c / L0, q0 = c - q1 * L0;
-            const int px = hs.lo3[0] + q0, py = hs.lo3[1] + q1;
+            const int px = lo0 + q0, py = lo1 + q1;
             const int rx = bs0 + px, ry = bs1 + py;
             const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0), ey = ry < 0 ? -1 : (ry >= n ? 1 : 0);
             const int lx = rx - ex * n, ly = ry - ey * n;
             const int ox = lx >= h, oy = ly >= h;
             const int FX = 2 * lx - ox * n + 1, FY = 2 * ly - oy * n + 1;
             T* pcol = patch + py * PL + px;
-#pragma unroll 4
             for (int pz = z0; pz < z1; ++pz) {
                 const int rz = bs2 + pz;
                 const int ez = rz < 0 ? -1 : (rz >= n ? 1 : 0);
                 const int lz = rz - ez * n;
                 const int d = dir27(ex, ey, ez);
-                const T* src;
-                if (hs.cleaf[d]) {
-                    src = Uc + ((size_t)hs.cnbr[d] * S3 + (size_t)(((lz + 1) * S + ly + 1) * S + lx + 1));
+                const int oz = lz >= h;
+                const int ch = pch[8 * d + ox + 2 * oy + 4 * oz];
+                if (pch[8 * d] < 0) {
+                    // leaf coarse block
+                    cp_async_el(pcol + pz * PL2, Uc + ((size_t)pnbr[d] * S3 + (size_t)(((lz + 1) * S + ly + 1) * S + lx + 1)));
                 } else {
                     // covered coarse node: the coincident fine node of the current level
-                    const int oz = lz >= h;
-                    const int ch = hs.cch[8 * d + ox + 2 * oy + 4 * oz];
                     const int FZ = 2 * lz - oz * n + 1;
-                    src = ch == b ? su + sp.at(FX, FY, FZ) : Uk + ((size_t)ch * S3 + (size_t)((FZ * S + FY) * S + FX));
+                    if (ch == b) pcol[pz * PL2] = su[sp.at(FX, FY, FZ)];
+                    else cp_async_el(pcol + pz * PL2, Uk + ((size_t)ch * S3 + (size_t)((FZ * S + FY) * S + FX)));
                 }
-                pcol[pz * PL2] = *src;
             }
         }
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     T w[I];
 #pragma unroll
     for (int m = 0; m < I; ++m) w[m] = T(midw<I>(m));
     const unsigned mTN = magic_of(TN);
+    const int* __restrict__ rdir = hs.rec + REC_RDIR;
+    const int* __restrict__ roff = hs.rec + REC_ROFF;
+    const int* __restrict__ raoff = hs.rec + REC_RAOFF;
+    const int* __restrict__ coff = hs.rec + REC_COFF;
+    const int* __restrict__ doff = hs.rec + REC_DOFF;
+    // Each pass is one flat loop over the items of all regions; the region of
+    // item f is the last one whose first item is <= f.
+    auto region_at = [&](const int* __restrict__ off, int f) {
+        int lo = 0, hi = nreg;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= f) lo = mid;
+            else hi = mid;
+        }
+        return lo;
+    };
     // 2b. reduction along the normal axes: one value per coarse tangential node
-    for (int r = 0; r < hs.nreg; ++r) {
-        const Region g = region_of(hs.rdir[r], PL, up);
-        const int cnt = g.nt == 2 ? TN2 : (g.nt == 1 ? TN : 1);
-        const int s0 = g.ns0, s1 = g.ns1, s2 = g.ns2, t0 = g.ts0, t1 = g.ts1;
-        T* R = pool + hs.roff[r];
-        for (int e = tid; e < cnt; e += nth) {
-            const int e1 = g.nt == 2 ? fdiv(e, mTN) : 0, e0 = e - e1 * TN;
-            const T* p = patch + g.p0 + e0 * t0 + e1 * t1;
-            T acc = T(0);
-            if (g.nn == 0) {
-                acc = p[0];
-            } else if (g.nn == 1) {
+    const int nB = hs.rec[REC_NTOT], nC = hs.rec[REC_NTOT + 1], nD = hs.rec[REC_NTOT + 2];
+    for (int f = tid; f < nB; f += nth) {
+        const int r = region_at(roff, f);
+        const Region g = region_of(rdir[r], PL, up);
+        const int e = f - roff[r];
+        const int e1 = g.nt == 2 ? fdiv(e, mTN) : 0, e0 = e - e1 * TN;
+        const T* p = patch + g.p0 + e0 * g.ts0 + e1 * g.ts1;
+        const int s0 = g.ns0, s1 = g.ns1, s2 = g.ns2;
+        T acc = T(0);
+        if (g.nn == 0) {
+            acc = p[0];
+        } else if (g.nn == 1) {
 #pragma unroll
-                for (int m = 0; m < I; ++m) acc += w[m] * p[m * s0];
-            } else if (g.nn == 2) {
+            for (int m = 0; m < I; ++m) acc += w[m] * p[m * s0];
+        } else if (g.nn == 2) {
 #pragma unroll
+            for (int m1 = 0; m1 < I; ++m1) {
+                T a = T(0);
+#pragma unroll
+                for (int m = 0; m < I; ++m) a += w[m] * p[m * s0 + m1 * s1];
+                acc += w[m1] * a;
+            }
+        } else {
+#pragma unroll 1
+            for (int m2 = 0; m2 < I; ++m2) {
+                T a2 = T(0);
+#pragma unroll 1
                 for (int m1 = 0; m1 < I; ++m1) {
                     T a = T(0);
 #pragma unroll
-                    for (int m = 0; m < I; ++m) a += w[m] * p[m * s0 + m1 * s1];
-                    acc += w[m1] * a;
+                    for (int m = 0; m < I; ++m) a += w[m] * p[m * s0 + m1 * s1 + m2 * s2];
+                    a2 += T(midw<I>(m1)) * a;
                 }
-            } else {
-#pragma unroll 1
-                for (int m2 = 0; m2 < I; ++m2) {
-                    T a2 = T(0);
-#pragma unroll 1
-                    for (int m1 = 0; m1 < I; ++m1) {
-                        T a = T(0);
-#pragma unroll
-                        for (int m = 0; m < I; ++m) a += w[m] * p[m * s0 + m1 * s1 + m2 * s2];
-                        a2 += T(midw<I>(m1)) * a;
-                    }
-                    acc += T(midw<I>(m2)) * a2;
-                }
+                acc += T(midw<I>(m2)) * a2;
             }
-            R[e] = acc;
         }
+        pool[f] = acc;
     }
     __syncthreads();
     // 2c. faces: along the first tangential axis into A[v'][u] (fine u, coarse
     //     v'); edges and corners: their ghost values.  A reuses the patch.
     //     Reduced-array start of the stencil of fine coordinate q: q/2 + I/2 - 1
-    //     (q even, one point) or (q - 1)/2 (q odd, I points).
+    //     (q even, one point) or (q - 1)/2 (q odd, I points).  A face's items
+    //     run over even u first, then odd u.
     T* A = patch;
     const unsigned mh = magic_of(h), mn = magic_of(n);
-    for (int r = 0; r < hs.nreg; ++r) {
-        const Region g = region_of(hs.rdir[r], PL, up);
-        const T* R = pool + hs.roff[r];
+    for (int f = tid; f < nC; f += nth) {
+        const int r = region_at(coff, f);
+        const Region g = region_of(rdir[r], PL, up);
+        const int e = f - coff[r];
+        const T* R = pool + roff[r];
         if (g.nt == 2) {
-            T* Ar = A + hs.raoff[r];
-            for (int e = tid; e < n * TN; e += nth) {
-                const int par = e >= h * TN;
-                const int e2 = e - par * h * TN;
-                const int v = fdiv(e2, mh), u = 2 * (e2 - v * h) + par;
-                T acc = T(0);
-                if (!par) {
-                    acc = R[v * TN + u / 2 + I / 2 - 1];
-                } else {
-                    const T* q = R + v * TN + (u - 1) / 2;
+            const int par = e >= h * TN;
+            const int e2 = e - par * h * TN;
+            const int v = fdiv(e2, mh), u = 2 * (e2 - v * h) + par;
+            T acc = T(0);
+            if (!par) {
+                acc = R[v * TN + u / 2 + I / 2 - 1];
+            } else {
+                const T* q = R + v * TN + (u - 1) / 2;
 #pragma unroll
-                    for (int m = 0; m < I; ++m) acc += w[m] * q[m];
-                }
-                Ar[v * n + u] = acc;
+                for (int m = 0; m < I; ++m) acc += w[m] * q[m];
             }
+            A[raoff[r] + v * n + u] = acc;
         } else if (g.nt == 1) {
-            for (int u = tid; u < n; u += nth) {
-                T acc = T(0);
-                if (!(u & 1)) {
-                    acc = R[u / 2 + I / 2 - 1];
-                } else {
+            const int u = e;
+            T acc = T(0);
+            if (!(u & 1)) {
+                acc = R[u / 2 + I / 2 - 1];
+            } else {
 #pragma unroll
-                    for (int m = 0; m < I; ++m) acc += w[m] * R[(u - 1) / 2 + m];
-                }
-                su[sp.at(box_coord(g.d0, 0, g, S, u + 1, 0), box_coord(g.d1, 1, g, S, u + 1, 0),
-                         box_coord(g.d2, 2, g, S, u + 1, 0))] = acc;
+                for (int m = 0; m < I; ++m) acc += w[m] * R[(u - 1) / 2 + m];
             }
-        } else if (tid == 0) {
+            su[sp.at(box_coord(g.d0, 0, g, S, u + 1, 0), box_coord(g.d1, 1, g, S, u + 1, 0),
+                     box_coord(g.d2, 2, g, S, u + 1, 0))] = acc;
+        } else {
             su[sp.at(box_coord(g.d0, 0, g, S, 0, 0), box_coord(g.d1, 1, g, S, 0, 0), box_coord(g.d2, 2, g, S, 0, 0))] =
                 R[0];
         }
     }
     __syncthreads();
-    // 2d. faces: along the second tangential axis (fine v), rows of fine u
-    for (int r = 0; r < hs.nreg; ++r) {
-        const Region g = region_of(hs.rdir[r], PL, up);
-        if (g.nt != 2) continue;
-        const T* Ar = A + hs.raoff[r];
-        for (int e = tid; e < n * n; e += nth) {
-            const int row = fdiv(e, mn), u = e - row * n;
-            const int par = row >= h;
-            const int v = 2 * (row - par * h) + par;
-            T acc = T(0);
-            if (!par) {
-                acc = Ar[(v / 2 + I / 2 - 1) * n + u];
-            } else {
-                const T* q = Ar + ((v - 1) / 2) * n + u;
+    // 2d. faces: along the second tangential axis (fine v), rows of fine u,
+    //     even v first
+    for (int f = tid; f < nD; f += nth) {
+        const int r = region_at(doff, f);
+        const Region g = region_of(rdir[r], PL, up);
+        const int e = f - doff[r];
+        const T* Ar = A + raoff[r];
+        const int row = fdiv(e, mn), u = e - row * n;
+        const int par = row >= h;
+        const int v = 2 * (row - par * h) + par;
+        T acc = T(0);
+        if (!par) {
+            acc = Ar[(v / 2 + I / 2 - 1) * n + u];
+        } else {
+            const T* q = Ar + ((v - 1) / 2) * n + u;
 #pragma unroll
-                for (int m = 0; m < I; ++m) acc += w[m] * q[m * n];
-            }
-            su[sp.at(box_coord(g.d0, 0, g, S, u + 1, v + 1), box_coord(g.d1, 1, g, S, u + 1, v + 1),
-                     box_coord(g.d2, 2, g, S, u + 1, v + 1))] = acc;
+            for (int m = 0; m < I; ++m) acc += w[m] * q[m * n];
         }
+        su[sp.at(box_coord(g.d0, 0, g, S, u + 1, v + 1), box_coord(g.d1, 1, g, S, u + 1, v + 1),
+                 box_coord(g.d2, 2, g, S, u + 1, v + 1))] = acc;
     }
     __syncthreads();
 }
@@ -475,9 +481,36 @@ __host__ __device__ inline int patch_size(int n, int I) {
     return PL * PL * PL;
 }
 
+// Dynamic shared memory of the fused kernels: the split box, the reduced
+// array and the patch, then (fstage) the block's right-hand side at a
+// 16-byte boundary.
+__host__ __device__ inline size_t rhs_offset(int n, int I, size_t el) {
+    const size_t b = el * (8 * (size_t)split_h3p(n) + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
+    return (b + 15) / 16 * 16;
+}
 template <typename T>
-__host__ __device__ inline size_t fused_smem(int n, int I) {
-    return sizeof(T) * (8 * (size_t)split_h3p(n) + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
+__host__ __device__ inline size_t fused_smem(int n, int I, bool fstage = false) {
+    return fstage ? rhs_offset(n, I, sizeof(T)) + sizeof(T) * (size_t)n * n * n
+                  : sizeof(T) * (8 * (size_t)split_h3p(n) + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
+}
+
+// Prologue of the fused kernels that stage no right-hand side: the block's
+// record, complete and visible on return.
+__device__ __forceinline__ void record_prologue(HaloSmem& hs, const LevelView& lk, int b) {
+    load_record(hs, lk, b);
+    cp_async_wait<0>();
+    __syncthreads();
+}
+
+// Common prologue of the fused kernels: starts the copies of the block's
+// record and (fstage) right-hand side, waits for the record.
+template <typename T>
+__device__ __forceinline__ void fused_prologue(HaloSmem& hs, T* fs, const T* F, const LevelView& lk, int b, int n,
+                                               bool fstage) {
+    load_record(hs, lk, b);
+    load_rhs(fs, F, b, n, fstage);
+    cp_async_wait<1>();
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- smoother
@@ -486,18 +519,20 @@ __host__ __device__ inline size_t fused_smem(int n, int I) {
 template <int M, typename T, int I>
 __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
                                                       const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
-                                                      LevelView lc, int n, T h2den, const int* __restrict__ order) {
+                                                      int n, T h2den, const int* __restrict__ order, int fstage) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
     const Split sp = split_of(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
-    __shared__ HaloSmem<T> hs;
+    T* fs = reinterpret_cast<T*>(fz_smem + rhs_offset(n, I, sizeof(T)));
+    __shared__ HaloSmem hs;
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, lc, b, n, sp);
-    const T* Fb = F + (size_t)b * n * n * n;
+    fused_prologue(hs, fs, F, lk, b, n, fstage != 0);
+    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, b, n, sp);
+    const T* Fb = fstage ? fs : F + (size_t)b * n * n * n;
     const T inv_c = T(1) / T(LW<M>::c);
     for (int col = 0; col < 8; ++col) {
         const Col c = colour(col, sp, n);
@@ -530,17 +565,18 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
 template <int M, typename T, int I>
 __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const T* __restrict__ U,
                                                         const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
-                                                        LevelView lc, int n, T scale, const int* __restrict__ order) {
+                                                        int n, T scale, const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
     const Split sp = split_of(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
-    __shared__ HaloSmem<T> hs;
+    __shared__ HaloSmem hs;
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
+    record_prologue(hs, lk, b);
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     for (int col = 0; col < 8; ++col) {
         const Col c = colour(col, sp, n);
@@ -560,14 +596,14 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
 // F += L u on covered blocks; H = u on every block.
 template <int M, typename T, int I>
 __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U,
-                                                   const T* __restrict__ Uc, LevelView lk, LevelView lc, int n, T scale,
+                                                   const T* __restrict__ Uc, LevelView lk, int n, T scale,
                                                    const int* __restrict__ order) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
     const Split sp = split_of(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
-    __shared__ HaloSmem<T> hs;
+    __shared__ HaloSmem hs;
     const int S = n + 2, S3 = S * S * S;
     const size_t n3 = (size_t)n * n * n;
     const int b = order ? order[blockIdx.x] : blockIdx.x;
@@ -587,7 +623,8 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
         }
         return;
     }
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
+    record_prologue(hs, lk, b);
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
     for (int col = 0; col < 8; ++col) {
         const Col c = colour(col, sp, n);
 #pragma unroll
@@ -621,18 +658,19 @@ __device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
 template <int M, int I>
 __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
                                                        const double* __restrict__ F, const double* __restrict__ Uc,
-                                                       const int* __restrict__ blocks, LevelView lk, LevelView lc, int n,
+                                                       const int* __restrict__ blocks, LevelView lk, int n,
                                                        double scale, unsigned long long* out) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     double* su = reinterpret_cast<double*>(fz_smem);
     const Split sp = split_of(n);
     double* pool = su + 8 * sp.H3p;
     double* patch = pool + pool_size(n, I);
-    __shared__ HaloSmem<double> hs;
+    __shared__ HaloSmem hs;
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = blocks[blockIdx.x];
-    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
+    record_prologue(hs, lk, b);
+    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     double m = 0.0;
     for (int col = 0; col < 8; ++col) {
@@ -655,17 +693,17 @@ __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, c
 // ---------------------------------------------------------------- halo dump (step API)
 // Writes the ghost layer build_halo() produces into the block's stored ghost layer.
 template <typename T, int I>
-__global__ void __launch_bounds__(512) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, LevelView lc,
-                                                   int n) {
+__global__ void __launch_bounds__(512) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, int n) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
     const Split sp = split_of(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
-    __shared__ HaloSmem<T> hs;
+    __shared__ HaloSmem hs;
     const int S = n + 2, S3 = S * S * S;
     const int b = blockIdx.x;
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, lc, b, n, sp);
+    record_prologue(hs, lk, b);
+    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
     for (int t = threadIdx.x; t < S3 - n * n * n; t += blockDim.x) {
         int x, y, z;
         shell_coords(t, S, x, y, z);
@@ -694,7 +732,7 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(T* __restrict__ A, T* __r
                                                        int n) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* pool = reinterpret_cast<T*>(fz_smem);
-    __shared__ HaloSmem<T> hs;
+    __shared__ HaloSmemT<T> hs;
     const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int b = blockIdx.x;
@@ -900,11 +938,13 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
                          double h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     set_attrs<T>();
-    const size_t sm = fused_smem<T>(n, M + 2);
+    // the block's right-hand side goes to shared memory where it fits
+    const int fst = fused_smem<T>(n, M + 2, true) <= (size_t)MAX_DYN_SMEM && (uintptr_t)F % 16 == 0;
+    const size_t sm = fused_smem<T>(n, M + 2, fst);
     const int ct = cta_size(n, nt);
-    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<2>::den), lk.order);
-    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<4>::den), lk.order);
-    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, lc, n, T(h2 * LW<6>::den), lk.order);
+    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<2>::den), lk.order, fst);
+    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<4>::den), lk.order, fst);
+    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<6>::den), lk.order, fst);
 }
 
 template <typename T>
@@ -914,9 +954,9 @@ void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView 
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
     const int ct = cta_size(n, nt);
-    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, T(inv_h2 / LW<6>::den), lk.order);
 }
 
 template <typename T>
@@ -926,9 +966,9 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
     const int ct = cta_size(n, nt);
-    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, lc, n, T(inv_h2 / LW<6>::den), lk.order);
+    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, T(inv_h2 / LW<2>::den), lk.order);
+    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, T(inv_h2 / LW<4>::den), lk.order);
+    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, T(inv_h2 / LW<6>::den), lk.order);
 }
 
 void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
@@ -937,9 +977,9 @@ void launch_leafres_fused(double* R, const double* U, const double* F, const dou
     if (nblocks == 0) return;
     set_attrs<double>();
     const size_t sm = fused_smem<double>(n, M + 2);
-    if (M == 2) k_leafres_fused<2, 4><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<2>::den, out);
-    if (M == 4) k_leafres_fused<4, 6><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<4>::den, out);
-    if (M == 6) k_leafres_fused<6, 8><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, lc, n, inv_h2 / LW<6>::den, out);
+    if (M == 2) k_leafres_fused<2, 4><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, n, inv_h2 / LW<2>::den, out);
+    if (M == 4) k_leafres_fused<4, 6><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, n, inv_h2 / LW<4>::den, out);
+    if (M == 6) k_leafres_fused<6, 8><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, n, inv_h2 / LW<6>::den, out);
 }
 
 template <typename T>
@@ -947,9 +987,9 @@ void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int 
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    if (M == 2) k_halo_dump<T, 4><<<lk.nb, 256, sm, s>>>(U, Uc, lk, lc, n);
-    if (M == 4) k_halo_dump<T, 6><<<lk.nb, 256, sm, s>>>(U, Uc, lk, lc, n);
-    if (M == 6) k_halo_dump<T, 8><<<lk.nb, 256, sm, s>>>(U, Uc, lk, lc, n);
+    if (M == 2) k_halo_dump<T, 4><<<lk.nb, 256, sm, s>>>(U, Uc, lk, n);
+    if (M == 4) k_halo_dump<T, 6><<<lk.nb, 256, sm, s>>>(U, Uc, lk, n);
+    if (M == 6) k_halo_dump<T, 8><<<lk.nb, 256, sm, s>>>(U, Uc, lk, n);
 }
 
 template void launch_smooth_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView, int,

@@ -30,22 +30,42 @@ struct LevelView {
     const uint8_t* is_leaf;
     const int* order;      // [nb] launch order: blocks with interpolated ghosts first
     const int* prob;       // [nb] problem of each block (per-problem norms of a batched handle)
+    const int* rec;        // [nb][REC_INTS] neighbourhood records (below)
 };
+
+// Per-block neighbourhood record, REC_INTS ints, which the fused stencil
+// kernels copy to shared memory in 16-byte chunks: the same-level
+// neighbours, the ghost regions to interpolate (offsets of their work
+// arrays and the hull of their coarse stencils), the parent's neighbours and
+// the children of each (everything the ghost layer needs besides values).
+constexpr int REC_SNBR = 0;      // [27] same-level neighbour per direction (or NBR_*)
+constexpr int REC_NREG = 27;     // number of interpolated regions (0: none)
+constexpr int REC_PNBR = 28;     // [27] the parent's neighbours at level k-1
+constexpr int REC_RDIR = 56;     // [26] direction of each interpolated region
+constexpr int REC_ROFF = 82;     // [26] its offset in the normal-reduced array
+constexpr int REC_RAOFF = 108;   // [26] its offset in the face array (faces only)
+constexpr int REC_LO = 134;      // [3] coarse patch hull per axis: [lo, hi)
+constexpr int REC_HI = 137;      // [3]
+constexpr int REC_PCH = 140;     // [27][8] children of each parent neighbour (-1: leaf, or no block)
+constexpr int REC_COFF = 356;    // [26] each region's first item in the tangential pass (faces n TN, edges n, corners 1)
+constexpr int REC_DOFF = 382;    // [26] each region's first item in the second face pass (faces n^2, others 0)
+constexpr int REC_NTOT = 408;    // [3] items of the normal reduction, the tangential pass and the second face pass
+constexpr int REC_INTS = 412;    // a multiple of 4
 
 // Host + device tables of one level, plus its FP64 fields.
 struct Level {
     int nb = 0, nleaf = 0, ncov = 0;
     std::vector<int> h_coords, h_nbr, h_parent, h_octant, h_children, h_leaf_blocks, h_cov_blocks, h_order;
     std::vector<uint8_t> h_is_leaf;
-    std::vector<int> h_prob;
+    std::vector<int> h_prob, h_rec;
     int *coords = nullptr, *nbr = nullptr, *parent = nullptr, *octant = nullptr, *children = nullptr;
-    int *leaf_blocks = nullptr, *cov_blocks = nullptr, *order = nullptr, *prob = nullptr;
+    int *leaf_blocks = nullptr, *cov_blocks = nullptr, *order = nullptr, *prob = nullptr, *rec = nullptr;
     uint8_t* is_leaf = nullptr;
     double *U = nullptr, *F = nullptr, *R = nullptr, *H = nullptr, *Fraw = nullptr;
     double* Ualt = nullptr;           // second u buffer: a sweep reads U and writes Ualt, then they swap
     float *U32 = nullptr, *F32 = nullptr, *R32 = nullptr, *H32 = nullptr;   // mixed precision inner cycles
     float* U32alt = nullptr;
-    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order, prob}; }
+    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order, prob, rec}; }
 };
 
 // One padded FFT axis: length, radix sequence, twiddles exp(-2 pi i m / P).
@@ -149,7 +169,7 @@ struct Handle {
 inline double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
 inline int64_t n3(const Handle& h) { return (int64_t)h.n * h.n * h.n; }
 inline LevelView view_or_empty(const Handle& h, int k) {
-    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 }
 
 // Per-level base pointers, passed by value to the leaf scatter / gather kernels.

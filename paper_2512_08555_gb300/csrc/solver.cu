@@ -238,8 +238,66 @@ static int alloc_field(double*& p, size_t count) {
     return MRP_OK;
 }
 
+// Neighbourhood records of every block (layout: REC_* in mrp_internal.h).
+// The interpolated regions are the directions without a same-level
+// neighbour; each takes TN^2 (face), TN (edge) or 1 (corner) entries of the
+// normal-reduced array and, for faces, n TN entries of the face array.  The
+// coarse patch (indices 0..PL-1 per axis, PL = n/2 + I) is needed on
+// [0, I) for a -1 side, at index `up` (the coarse node of fine coordinate n)
+// for a +1 side and on [1, PL) along a tangential axis.
+static void build_records(Handle& h) {
+    const int n = h.n, I = h.M + 2, hh = n / 2;
+    const int TN = hh + I - 1, PL = hh + I, plo = 4 - I / 2, up = 4 + hh - plo;
+    for (size_t k = 0; k < h.lv.size(); ++k) {
+        Level& lv = h.lv[k];
+        lv.h_rec.assign((size_t)lv.nb * REC_INTS, 0);
+        for (int b = 0; b < lv.nb; ++b) {
+            int* r = &lv.h_rec[(size_t)b * REC_INTS];
+            for (int d = 0; d < 27; ++d) r[REC_SNBR + d] = lv.h_nbr[(size_t)27 * b + d];
+            for (int d = 0; d < 27; ++d) {
+                int cb = NBR_OUTSIDE;
+                if (k > 0 && lv.h_parent[b] >= 0) cb = h.lv[k - 1].h_nbr[(size_t)27 * lv.h_parent[b] + d];
+                r[REC_PNBR + d] = cb;
+                const bool inner = cb >= 0 && !h.lv[k - 1].h_is_leaf[cb];
+                for (int o = 0; o < 8; ++o)
+                    r[REC_PCH + 8 * d + o] = inner ? h.lv[k - 1].h_children[(size_t)8 * cb + o] : -1;
+            }
+            int o = 0, oa = 0, oc = 0, od = 0, nr = 0;
+            int lo[3] = {PL, PL, PL}, hi[3] = {0, 0, 0};
+            for (int d = 0; d < 27; ++d) {
+                if (d == 13 || r[REC_SNBR + d] != NBR_MISSING) continue;
+                const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+                int nt = 0;
+                for (int a = 0; a < 3; ++a) {
+                    const int l = dd[a] < 0 ? 0 : (dd[a] > 0 ? up : 1);
+                    const int e = dd[a] < 0 ? I : (dd[a] > 0 ? up + 1 : PL);
+                    nt += dd[a] == 0;
+                    lo[a] = std::min(lo[a], l);
+                    hi[a] = std::max(hi[a], e);
+                }
+                r[REC_RDIR + nr] = d;
+                r[REC_ROFF + nr] = o;
+                r[REC_RAOFF + nr] = oa;
+                r[REC_COFF + nr] = oc;
+                r[REC_DOFF + nr] = od;
+                o += nt == 2 ? TN * TN : (nt == 1 ? TN : 1);
+                oa += nt == 2 ? n * TN : 0;
+                oc += nt == 2 ? n * TN : (nt == 1 ? n : 1);
+                od += nt == 2 ? n * n : 0;
+                ++nr;
+            }
+            r[REC_NREG] = nr;
+            r[REC_NTOT] = o;
+            r[REC_NTOT + 1] = oc;
+            r[REC_NTOT + 2] = od;
+            for (int a = 0; a < 3; ++a) { r[REC_LO + a] = nr ? lo[a] : 0; r[REC_HI + a] = nr ? hi[a] : 0; }
+        }
+    }
+}
+
 int upload_tables(Handle& h) {
     int rc;
+    build_records(h);
     const size_t n = h.n, S = n + 2, S4 = n + 4;
     for (Level& lv : h.lv) {
         if ((rc = up(lv.coords, lv.h_coords))) return rc;
@@ -252,6 +310,7 @@ int upload_tables(Handle& h) {
         if ((rc = up(lv.order, lv.h_order))) return rc;
         if ((rc = up(lv.is_leaf, lv.h_is_leaf))) return rc;
         if ((rc = up(lv.prob, lv.h_prob))) return rc;
+        if ((rc = up(lv.rec, lv.h_rec))) return rc;
         if ((rc = alloc_field(lv.U, lv.nb * S * S * S))) return rc;
         if ((rc = alloc_field(lv.Ualt, lv.nb * S * S * S))) return rc;
         if ((rc = alloc_field(lv.F, lv.nb * n * n * n))) return rc;
@@ -274,6 +333,7 @@ static void release(Handle& h) {
     for (Level& lv : h.lv) {
         cudaFree(lv.coords); cudaFree(lv.nbr); cudaFree(lv.parent); cudaFree(lv.octant); cudaFree(lv.children);
         cudaFree(lv.leaf_blocks); cudaFree(lv.cov_blocks); cudaFree(lv.is_leaf); cudaFree(lv.order); cudaFree(lv.prob);
+        cudaFree(lv.rec);
         cudaFree(lv.U); cudaFree(lv.F); cudaFree(lv.R); cudaFree(lv.H); cudaFree(lv.Fraw);
         cudaFree(lv.U32); cudaFree(lv.F32); cudaFree(lv.R32); cudaFree(lv.H32);
         cudaFree(lv.Ualt); cudaFree(lv.U32alt);
