@@ -29,32 +29,54 @@ template <> struct LW<6> { static constexpr double den = 30, c = -128, f = 14, e
 // ---------------------------------------------------------------- parity-split box
 // The block's (n+2)^3 box (ghost layer included) is kept in shared memory as
 // 8 sub-arrays by the parity of the box coordinates (X, Y, Z):
-//     at(X, Y, Z) = ((Z&1)*4 + (Y&1)*2 + (X&1)) * H3p + ((Z>>1) H + (Y>>1)) H + (X>>1),
-// H = (n+2)/2, sub-array stride H3p >= H^3 with H3p = 16 (mod 32).  In one
-// Gauss-Seidel colour every stencil neighbour of the colour's nodes lies in
-// one sub-array per offset, at unit stride along x across a warp: no bank
-// conflicts; the two x-parities of a row fall 16 banks apart.
+//     at(X, Y, Z) = ((Z&1)*4 + (Y&1)*2 + (X&1)) * H3p + (Z>>1) Hp + (Y>>1) H + (X>>1),
+// H = (n+2)/2, plane stride Hp >= H^2, sub-array stride H3p >= H Hp with
+// H3p = 16 (mod 32).  In one Gauss-Seidel colour every stencil neighbour of
+// the colour's nodes lies in one sub-array per offset.  A warp's lanes take
+// the colour's nodes with x fastest, then z (see cset_init), so a load
+// touches rows (Y) of h consecutive words at plane distance Hp apart; for
+// FP32, Hp is the value in [H^2, H^2 + 32) that minimises the shared-memory
+// wavefronts of such loads over a colour (h = 8: Hp = 88 = 24 mod 32, four
+// disjoint 8-bank windows, no conflicts).  The two x-parities of a row fall 16
+// banks apart.
 struct Split {
-    int H, H2, H3p;
+    int H, H2, H3p;      // H2: plane stride Hp
     __device__ __forceinline__ int at(int X, int Y, int Z) const {
-        return (((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1)) * H3p + ((Z >> 1) * H + (Y >> 1)) * H + (X >> 1);
+        return (((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1)) * H3p + (Z >> 1) * H2 + (Y >> 1) * H + (X >> 1);
     }
 };
-__host__ __device__ inline int split_h3p(int n) {
-    const int H = n / 2 + 1, H3 = H * H * H;
+__host__ __device__ inline int split_hp(int n, int el) {
+    const int H = n / 2 + 1;
+    if (el != 4) return H * H;
+    switch (n) {
+        case 10: return 59;
+        case 12: return 70;
+        case 14: return 71;
+        case 16: return 88;
+        case 18: return 105;
+        case 20: return 138;
+        case 22: return 171;
+        case 24: return 172;
+        default: return H * H;
+    }
+}
+__host__ __device__ inline int split_h3p(int n, int el) {
+    const int H = n / 2 + 1, H3 = H * split_hp(n, el);
     return H3 + ((16 - H3 % 32) % 32 + 32) % 32;
 }
+template <typename T>
 __device__ __forceinline__ Split split_of(int n) {
     Split sp;
     sp.H = n / 2 + 1;
-    sp.H2 = sp.H * sp.H;
-    sp.H3p = split_h3p(n);
+    sp.H2 = split_hp(n, (int)sizeof(T));
+    sp.H3p = split_h3p(n, (int)sizeof(T));
     return sp;
 }
 
 // The thread's nodes of one colour: node q = tid + k * nt (k < KMAX) of the
-// (n/2)^3 nodes (i, j, l) of a colour, packed i | j << 10 | l << 20; a colour
-// c = (cx, cy, cz) places it at interior coordinates (2i+cx, 2j+cy, 2l+cz).
+// (n/2)^3 nodes (i, j, l) of a colour, q = i + h (l + h j), packed
+// i | j << 10 | l << 20; a colour c = (cx, cy, cz) places it at interior
+// coordinates (2i+cx, 2j+cy, 2l+cz).
 constexpr int KMAX = 8;
 struct Cset { int cnt; int q[KMAX]; };
 __device__ __forceinline__ void cset_init(Cset& cs, int h) {
@@ -65,7 +87,7 @@ __device__ __forceinline__ void cset_init(Cset& cs, int h) {
         const int q = threadIdx.x + k * blockDim.x;
         cs.q[k] = 0;
         if (q < h3) {
-            const int i = q % h, j = (q / h) % h, l = q / (h * h);
+            const int i = q % h, l = (q / h) % h, j = q / (h * h);
             cs.q[k] = i | (j << 10) | (l << 20);
             cs.cnt = k + 1;
         }
@@ -74,7 +96,7 @@ __device__ __forceinline__ void cset_init(Cset& cs, int h) {
 
 // Offsets of colour col: cb = sub-array of the (-1,-1,-1) neighbour; dX, dY,
 // dZ = step from a (-1) neighbour to the centre along each axis (the (+1)
-// neighbour is 1, H, H^2 past the (-1) one); fo / go = natural interior /
+// neighbour is 1, H, Hp past the (-1) one); fo / go = natural interior /
 // box offsets of the colour.
 struct Col { int cb, dX, dY, dZ, fo, go; };
 __device__ __forceinline__ Col colour(int col, const Split& sp, int n) {
@@ -97,7 +119,7 @@ __device__ __forceinline__ Node node_of(int packed, const Split& sp, int n) {
     const int i = packed & 1023, j = (packed >> 10) & 1023, l = packed >> 20;
     const int S = n + 2;
     Node d;
-    d.b0 = (l * sp.H + j) * sp.H + i;
+    d.b0 = l * sp.H2 + j * sp.H + i;
     d.f = ((2 * l) * n + 2 * j) * n + 2 * i;
     d.g = ((2 * l + 1) * S + 2 * j + 1) * S + 2 * i + 1;
     return d;
@@ -173,9 +195,6 @@ __host__ __device__ inline int pool_size(int n, int I) {
     return 6 * TN * TN + 12 * TN + 8;
 }
 
-// x / d for 0 <= x < 2^16 and 2 <= d < 2^16, with m = magic_of(d).
-__device__ __forceinline__ unsigned magic_of(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
-__device__ __forceinline__ int fdiv(int x, unsigned m) { return (int)__umulhi((unsigned)x, m); }
 
 // Asynchronous global -> shared copies (cp.async): one element, or 16 bytes.
 template <typename T>
@@ -266,7 +285,7 @@ __device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict
 //     Work items are ordered so that the lanes of a warp share the parity of
 //     the interpolated coordinate (the same stencil length).
 template <typename T, int I>
-__device__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, const HaloSmem& hs,
+__device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, const HaloSmem& hs,
                            const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk, int b, int n,
                            const Split& sp) {
     const int S = n + 2, S2 = S * S, S3 = S2 * S;
@@ -481,17 +500,19 @@ __host__ __device__ inline int patch_size(int n, int I) {
     return PL * PL * PL;
 }
 
-// Dynamic shared memory of the fused kernels: the split box, the reduced
-// array and the patch, then (fstage) the block's right-hand side at a
-// 16-byte boundary.
-__host__ __device__ inline size_t rhs_offset(int n, int I, size_t el) {
-    const size_t b = el * (8 * (size_t)split_h3p(n) + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
-    return (b + 15) / 16 * 16;
-}
+// Dynamic shared memory of the fused kernels: the split box, then the
+// reduced array and the patch of the interpolation; a staged right-hand side
+// (fstage) reuses that second area once the ghost layer is built (it starts
+// at a 16-byte boundary: the split box is a multiple of 32 elements).
+__host__ __device__ inline size_t rhs_offset(int n, size_t el) { return el * 8 * (size_t)split_h3p(n, (int)el); }
 template <typename T>
 __host__ __device__ inline size_t fused_smem(int n, int I, bool fstage = false) {
-    return fstage ? rhs_offset(n, I, sizeof(T)) + sizeof(T) * (size_t)n * n * n
-                  : sizeof(T) * (8 * (size_t)split_h3p(n) + (size_t)pool_size(n, I) + (size_t)patch_size(n, I));
+    const size_t interp = (size_t)pool_size(n, I) + (size_t)patch_size(n, I), f = (size_t)n * n * n;
+    return rhs_offset(n, sizeof(T)) + sizeof(T) * (fstage && f > interp ? f : interp);
+}
+
+size_t fused_smem_bytes(int n, int M, int el) {
+    return el == 8 ? fused_smem<double>(n, M + 2) : fused_smem<float>(n, M + 2);
 }
 
 // Prologue of the fused kernels that stage no right-hand side: the block's
@@ -502,38 +523,39 @@ __device__ __forceinline__ void record_prologue(HaloSmem& hs, const LevelView& l
     __syncthreads();
 }
 
-// Common prologue of the fused kernels: starts the copies of the block's
-// record and (fstage) right-hand side, waits for the record.
-template <typename T>
-__device__ __forceinline__ void fused_prologue(HaloSmem& hs, T* fs, const T* F, const LevelView& lk, int b, int n,
-                                               bool fstage) {
-    load_record(hs, lk, b);
-    load_rhs(fs, F, b, n, fstage);
-    cp_async_wait<1>();
-    __syncthreads();
-}
 
 // ---------------------------------------------------------------- smoother
 // One Gauss-Seidel iteration (Sec. 3.1): 8 colours c = (x&1) + 2(y&1) + 4(z&1),
 // u <- (den h^2 f - offcentre) / c; reads Uin, writes the interior to Uout.
-template <int M, typename T, int I>
+template <int M, typename T, int I, int NC>
 __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
                                                       const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
-                                                      int n, T h2den, const int* __restrict__ order, int fstage) {
+                                                      int n_arg, T h2den, const int* __restrict__ order, int fstage) {
+    const int n = NC ? NC : n_arg;    // NC: block size fixed at compile time (0: runtime)
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const Split sp = split_of(n);
+    const Split sp = split_of<T>(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
-    T* fs = reinterpret_cast<T*>(fz_smem + rhs_offset(n, I, sizeof(T)));
+    T* fs = pool;           // staged right-hand side, after the interpolation is done with this area
     __shared__ HaloSmem hs;
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    fused_prologue(hs, fs, F, lk, b, n, fstage != 0);
+    record_prologue(hs, lk, b);
+    // without interpolated regions the right-hand side copy overlaps the box
+    // copy (build_halo waits for both); otherwise it follows the ghost layer
+    const bool early = fstage && hs.rec[REC_NREG] == 0;
+    if (early) load_rhs(fs, F, b, n, true);
     build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, b, n, sp);
+    if (fstage && !early) {
+        load_rhs(fs, F, b, n, true);
+        cp_async_wait<0>();
+        __syncthreads();
+    }
     const T* Fb = fstage ? fs : F + (size_t)b * n * n * n;
     const T inv_c = T(1) / T(LW<M>::c);
+#pragma unroll
     for (int col = 0; col < 8; ++col) {
         const Col c = colour(col, sp, n);
 #pragma unroll
@@ -562,13 +584,14 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
 }
 
 // ---------------------------------------------------------------- residual r = f - L u (all nodes)
-template <int M, typename T, int I>
+template <int M, typename T, int I, int NC>
 __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const T* __restrict__ U,
                                                         const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
-                                                        int n, T scale, const int* __restrict__ order) {
+                                                        int n_arg, T scale, const int* __restrict__ order) {
+    const int n = NC ? NC : n_arg;    // NC: block size fixed at compile time (0: runtime)
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const Split sp = split_of(n);
+    const Split sp = split_of<T>(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem hs;
@@ -594,13 +617,14 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
 
 // ---------------------------------------------------------------- FAS RHS and u-hat (Alg. 1)
 // F += L u on covered blocks; H = u on every block.
-template <int M, typename T, int I>
+template <int M, typename T, int I, int NC>
 __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restrict__ H, const T* __restrict__ U,
-                                                   const T* __restrict__ Uc, LevelView lk, int n, T scale,
+                                                   const T* __restrict__ Uc, LevelView lk, int n_arg, T scale,
                                                    const int* __restrict__ order) {
+    const int n = NC ? NC : n_arg;    // NC: block size fixed at compile time (0: runtime)
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const Split sp = split_of(n);
+    const Split sp = split_of<T>(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem hs;
@@ -655,14 +679,15 @@ __device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
     }
 }
 
-template <int M, int I>
+template <int M, int I, int NC>
 __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
                                                        const double* __restrict__ F, const double* __restrict__ Uc,
-                                                       const int* __restrict__ blocks, LevelView lk, int n,
+                                                       const int* __restrict__ blocks, LevelView lk, int n_arg,
                                                        double scale, unsigned long long* out) {
+    const int n = NC ? NC : n_arg;
     extern __shared__ __align__(16) unsigned char fz_smem[];
     double* su = reinterpret_cast<double*>(fz_smem);
-    const Split sp = split_of(n);
+    const Split sp = split_of<double>(n);
     double* pool = su + 8 * sp.H3p;
     double* patch = pool + pool_size(n, I);
     __shared__ HaloSmem hs;
@@ -696,7 +721,7 @@ template <typename T, int I>
 __global__ void __launch_bounds__(512) k_halo_dump(T* __restrict__ U, const T* __restrict__ Uc, LevelView lk, int n) {
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
-    const Split sp = split_of(n);
+    const Split sp = split_of<T>(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
     __shared__ HaloSmem hs;
@@ -913,12 +938,17 @@ static int cta_size(int n, int nt) {
     return nt;
 }
 
+// The fused kernels come in two builds: block size 16 fixed at compile time
+// (constant strides and offsets) and any block size at run time.
+constexpr int NC_FIXED = 16;
+
 template <int M, typename T>
 static void set_attrs_m() {
     constexpr int I = M + 2;
-    allow(k_smooth_fused<M, T, I>);
-    allow(k_residual_fused<M, T, I>);
-    allow(k_fas_fused<M, T, I>);
+    allow(k_smooth_fused<M, T, I, NC_FIXED>); allow(k_smooth_fused<M, T, I, 0>);
+    allow(k_residual_fused<M, T, I, NC_FIXED>); allow(k_residual_fused<M, T, I, 0>);
+    allow(k_fas_fused<M, T, I, NC_FIXED>); allow(k_fas_fused<M, T, I, 0>);
+    if constexpr (sizeof(T) == 8) { allow(k_leafres_fused<M, I, NC_FIXED>); allow(k_leafres_fused<M, I, 0>); }
 }
 
 template <typename T>
@@ -927,10 +957,37 @@ static void set_attrs() {
     if (done) return;
     set_attrs_m<2, T>(); set_attrs_m<4, T>(); set_attrs_m<6, T>();
     allow(k_halo_dump<T, 4>); allow(k_halo_dump<T, 6>); allow(k_halo_dump<T, 8>);
-    if constexpr (sizeof(T) == 8) {
-        allow(k_leafres_fused<2, 4>); allow(k_leafres_fused<4, 6>); allow(k_leafres_fused<6, 8>);
-    }
     done = true;
+}
+
+template <int M, typename T>
+static void smooth_m(T* Uout, const T* Uin, const T* F, const T* Uc, const LevelView& lk, int n, T h2den, int fst,
+                     int ct, size_t sm, cudaStream_t s) {
+    constexpr int I = M + 2;
+    if (n == NC_FIXED) k_smooth_fused<M, T, I, NC_FIXED><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
+    else k_smooth_fused<M, T, I, 0><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
+}
+template <int M, typename T>
+static void residual_m(T* R, const T* U, const T* F, const T* Uc, const LevelView& lk, int n, T scale, int ct, size_t sm,
+                       cudaStream_t s) {
+    constexpr int I = M + 2;
+    if (n == NC_FIXED) k_residual_fused<M, T, I, NC_FIXED><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, scale, lk.order);
+    else k_residual_fused<M, T, I, 0><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, scale, lk.order);
+}
+template <int M, typename T>
+static void fas_m(T* F, T* H, const T* U, const T* Uc, const LevelView& lk, int n, T scale, int ct, size_t sm,
+                  cudaStream_t s) {
+    constexpr int I = M + 2;
+    if (n == NC_FIXED) k_fas_fused<M, T, I, NC_FIXED><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, scale, lk.order);
+    else k_fas_fused<M, T, I, 0><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, scale, lk.order);
+}
+template <int M>
+static void leafres_m(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
+                      const LevelView& lk, int n, double scale, unsigned long long* out, int ct, size_t sm,
+                      cudaStream_t s) {
+    constexpr int I = M + 2;
+    if (n == NC_FIXED) k_leafres_fused<M, I, NC_FIXED><<<nblocks, ct, sm, s>>>(R, U, F, Uc, blocks, lk, n, scale, out);
+    else k_leafres_fused<M, I, 0><<<nblocks, ct, sm, s>>>(R, U, F, Uc, blocks, lk, n, scale, out);
 }
 
 template <typename T>
@@ -942,9 +999,9 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
     const int fst = fused_smem<T>(n, M + 2, true) <= (size_t)MAX_DYN_SMEM && (uintptr_t)F % 16 == 0;
     const size_t sm = fused_smem<T>(n, M + 2, fst);
     const int ct = cta_size(n, nt);
-    if (M == 2) k_smooth_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<2>::den), lk.order, fst);
-    if (M == 4) k_smooth_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<4>::den), lk.order, fst);
-    if (M == 6) k_smooth_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<6>::den), lk.order, fst);
+    if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<2>::den), fst, ct, sm, s);
+    if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<4>::den), fst, ct, sm, s);
+    if (M == 6) smooth_m<6, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<6>::den), fst, ct, sm, s);
 }
 
 template <typename T>
@@ -954,9 +1011,9 @@ void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView 
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
     const int ct = cta_size(n, nt);
-    if (M == 2) k_residual_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_residual_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_residual_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, T(inv_h2 / LW<6>::den), lk.order);
+    if (M == 2) residual_m<2, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
+    if (M == 4) residual_m<4, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, s);
+    if (M == 6) residual_m<6, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, s);
 }
 
 template <typename T>
@@ -966,9 +1023,9 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
     const int ct = cta_size(n, nt);
-    if (M == 2) k_fas_fused<2, T, 4><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, T(inv_h2 / LW<2>::den), lk.order);
-    if (M == 4) k_fas_fused<4, T, 6><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, T(inv_h2 / LW<4>::den), lk.order);
-    if (M == 6) k_fas_fused<6, T, 8><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, T(inv_h2 / LW<6>::den), lk.order);
+    if (M == 2) fas_m<2, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
+    if (M == 4) fas_m<4, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, s);
+    if (M == 6) fas_m<6, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, s);
 }
 
 void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
@@ -977,9 +1034,10 @@ void launch_leafres_fused(double* R, const double* U, const double* F, const dou
     if (nblocks == 0) return;
     set_attrs<double>();
     const size_t sm = fused_smem<double>(n, M + 2);
-    if (M == 2) k_leafres_fused<2, 4><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, n, inv_h2 / LW<2>::den, out);
-    if (M == 4) k_leafres_fused<4, 6><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, n, inv_h2 / LW<4>::den, out);
-    if (M == 6) k_leafres_fused<6, 8><<<nblocks, cta_size(n, nt), sm, s>>>(R, U, F, Uc, blocks, lk, n, inv_h2 / LW<6>::den, out);
+    const int ct = cta_size(n, nt);
+    if (M == 2) leafres_m<2>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<2>::den, out, ct, sm, s);
+    if (M == 4) leafres_m<4>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<4>::den, out, ct, sm, s);
+    if (M == 6) leafres_m<6>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<6>::den, out, ct, sm, s);
 }
 
 template <typename T>

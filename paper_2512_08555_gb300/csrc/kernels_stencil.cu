@@ -181,8 +181,164 @@ __global__ void k_ghost_fill(double* __restrict__ A, int g, const double* __rest
     }
 }
 
+// Separable form of the same ghost layer: the interpolant is evaluated over
+// the whole (n+2g)^3 box in three passes from the staged patch, along x
+// (fine x, coarse y, z), along y (fine x, y, coarse z) and along z (fine
+// nodes of the interpolated regions only); the sums nest in the tensor
+// kernel's order (x innermost, then y, then z).  Each pass takes its items
+// with the parity of the interpolated coordinate slowest, so the lanes of a
+// warp share the stencil length (I points at an odd fine coordinate, one
+// coincident node at an even one).  Work arrays: wa (patch, then the y pass)
+// and wb (the x pass).
+__host__ __device__ inline int gsep_wa(int n, int g, int I) {
+    const int S = n + 2 * g, PL = n / 2 + g + I + 1;
+    return PL * PL * PL > S * S * PL ? PL * PL * PL : S * S * PL;
+}
+__host__ __device__ inline int gsep_wb(int n, int g, int I) {
+    const int S = n + 2 * g, PL = n / 2 + g + I + 1;
+    return S * PL * PL;
+}
+
+template <int I>
+__global__ void k_ghost_fill_sep(double* __restrict__ A, int g, const double* __restrict__ Ac, int gc, LevelView lk,
+                                 LevelView lc, int n, InterpW iw, bool zero_outside) {
+    extern __shared__ double gsm[];
+    __shared__ int snbr[27], cnbr[27];
+    __shared__ int interp;
+    const int b = blockIdx.x;
+    const int S = n + 2 * g, S2 = S * S, S3 = S2 * S;
+    const int Sc = n + 2 * gc, Sc2 = Sc * Sc, Sc3 = Sc2 * Sc;
+    const int h = n >> 1, Sh = S >> 1;
+    const int P = lk.parent[b];
+    if (threadIdx.x < 27) {
+        snbr[threadIdx.x] = lk.nbr[27 * b + threadIdx.x];
+        cnbr[threadIdx.x] = P >= 0 ? lc.nbr[27 * P + threadIdx.x] : -1;
+    }
+    if (threadIdx.x == 0) interp = 0;
+    __syncthreads();
+    if (threadIdx.x < 27 && threadIdx.x != 13 && snbr[threadIdx.x] == NBR_MISSING) interp = 1;
+    double w[I];
+#pragma unroll
+    for (int m = 0; m < I; ++m) w[m] = iw.w[m];
+    double* Ab = A + (size_t)b * S3;
+    const unsigned mS = magic_of(S), mSh = magic_of(Sh);
+    // copied and outside regions
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int zy = fdiv(t, mS), x = t - zy * S, z = fdiv(zy, mS), y = zy - z * S;
+        const int dx = x < g ? -1 : (x >= g + n ? 1 : 0);
+        const int dy = y < g ? -1 : (y >= g + n ? 1 : 0);
+        const int dz = z < g ? -1 : (z >= g + n ? 1 : 0);
+        if ((dx | dy | dz) == 0) continue;
+        const int j = snbr[dir27(dx, dy, dz)];
+        if (j >= 0) Ab[t] = A[(size_t)j * S3 + (size_t)((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)];
+        else if (j == NBR_OUTSIDE && zero_outside) Ab[t] = 0.0;
+    }
+    __syncthreads();
+    if (!interp) return;
+    const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
+    const int PL = h + g + I + 1, PL2 = PL * PL;
+    const int pb0 = (bx & 1) * h - (g + 1) / 2 - I / 2, pb1 = (by & 1) * h - (g + 1) / 2 - I / 2,
+              pb2 = (bz & 1) * h - (g + 1) / 2 - I / 2;
+    double* wa = gsm;
+    double* wb = gsm + gsep_wa(n, g, I);
+    const unsigned mPL = magic_of(PL);
+    for (int t = threadIdx.x; t < PL2 * PL; t += blockDim.x) {
+        const int q = fdiv(t, mPL), px = t - q * PL, pz = fdiv(q, mPL), py = q - pz * PL;
+        const int r0 = pb0 + px, r1 = pb1 + py, r2 = pb2 + pz;
+        const int e0 = r0 < 0 ? -1 : (r0 >= n ? 1 : 0), e1 = r1 < 0 ? -1 : (r1 >= n ? 1 : 0),
+                  e2 = r2 < 0 ? -1 : (r2 >= n ? 1 : 0);
+        const int cb = cnbr[dir27(e0, e1, e2)];
+        wa[t] = cb >= 0 ? Ac[(size_t)cb * Sc3 + (size_t)((gc + r2 - e2 * n) * Sc + gc + r1 - e1 * n) * Sc + gc + r0 - e0 * n]
+                        : 0.0;
+    }
+    __syncthreads();
+    // Patch index of the first stencil node of box coordinate X on an axis
+    // whose block origin is bo (fine) and patch base pb: fine coordinate
+    // p = bo + X - g; even p: node p/2, odd p: I nodes from (p-1)/2 - I/2 + 1;
+    // both relative to the parent's origin (bo >> 1 rounded to the parent) and pb.
+    auto start = [&](int bo, int X, int pbase) {
+        const int p = bo + X - g, porig = ((bo / n) >> 1) * n;
+        return ((p & 1) == 0 ? (p >> 1) : ((p - 1) >> 1) - I / 2 + 1) - porig - pbase;
+    };
+    // x pass: wb[(cz PL + cy) S + X]
+    for (int t = threadIdx.x; t < S * PL2; t += blockDim.x) {
+        const int par = t >= Sh * PL2;
+        const int e = t - par * Sh * PL2;
+        const int q = fdiv(e, mSh), Xh = e - q * Sh;          // q = cz PL + cy
+        const int X = 2 * Xh + par;
+        const double* row = wa + q * PL + start(bx * n, X, pb0);
+        double acc;
+        if (!par) acc = row[0];
+        else {
+            acc = 0.0;
+#pragma unroll
+            for (int m = 0; m < I; ++m) acc += w[m] * row[m];
+        }
+        wb[q * S + X] = acc;
+    }
+    __syncthreads();
+    // y pass: wa[(cz S + Y) S + X]
+    for (int t = threadIdx.x; t < S2 * PL; t += blockDim.x) {
+        const int par = t >= Sh * S * PL;
+        const int e = t - par * Sh * S * PL;
+        const int q = fdiv(e, mS), X = e - q * S;               // q = cz Sh + Yh
+        const int cz = fdiv(q, mSh), Yh = q - cz * Sh;
+        const int Y = 2 * Yh + par;
+        const double* col = wb + (cz * PL + start(by * n, Y, pb1)) * S + X;
+        double acc;
+        if (!par) acc = col[0];
+        else {
+            acc = 0.0;
+#pragma unroll
+            for (int m = 0; m < I; ++m) acc += w[m] * col[m * S];
+        }
+        wa[(cz * S + Y) * S + X] = acc;
+    }
+    __syncthreads();
+    // z pass on the interpolated regions
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int par = t >= Sh * S2;
+        const int e = t - par * Sh * S2;
+        const int q = fdiv(e, mS), X = e - q * S;               // q = Zh S + Y
+        const int Zh = fdiv(q, mS), Y = q - Zh * S;
+        const int Z = 2 * Zh + par;
+        const int dx = X < g ? -1 : (X >= g + n ? 1 : 0);
+        const int dy = Y < g ? -1 : (Y >= g + n ? 1 : 0);
+        const int dz = Z < g ? -1 : (Z >= g + n ? 1 : 0);
+        if ((dx | dy | dz) == 0 || snbr[dir27(dx, dy, dz)] != NBR_MISSING) continue;
+        const double* col = wa + start(bz * n, Z, pb2) * S2 + Y * S + X;
+        double acc;
+        if (!par) acc = col[0];
+        else {
+            acc = 0.0;
+#pragma unroll
+            for (int m = 0; m < I; ++m) acc += w[m] * col[m * S2];
+        }
+        Ab[(Z * S + Y) * S + X] = acc;
+    }
+}
+
 void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk, LevelView lkm1, int n, int M,
                        bool zero_outside, cudaStream_t s) {
+    if (lk.nb == 0) return;
+    {
+        const int I = M + 2;
+        const size_t sm = sizeof(double) * ((size_t)gsep_wa(n, g, I) + (size_t)gsep_wb(n, g, I));
+        if (g % 2 == 0 && sm <= (size_t)MAX_DYN_SMEM) {
+            static bool attr_sep = false;
+            if (!attr_sep) {
+                cudaFuncSetAttribute(k_ghost_fill_sep<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+                cudaFuncSetAttribute(k_ghost_fill_sep<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+                cudaFuncSetAttribute(k_ghost_fill_sep<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+                attr_sep = true;
+            }
+            const InterpW iw = interp_weights(M);
+            if (I == 4) k_ghost_fill_sep<4><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
+            if (I == 6) k_ghost_fill_sep<6><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
+            if (I == 8) k_ghost_fill_sep<8><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
+            return;
+        }
+    }
     if (lk.nb == 0) return;
     const InterpW iw = interp_weights(M);
     const int PL = n / 2 + g + iw.I + 1;

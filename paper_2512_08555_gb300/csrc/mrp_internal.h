@@ -15,6 +15,14 @@ namespace mrp {
 // 27 neighbour directions, index = (dz+1)*9 + (dy+1)*3 + (dx+1); 13 is the block itself.
 __host__ __device__ inline int dir27(int dx, int dy, int dz) { return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); }
 
+// x / d for 0 <= x < 2^16 and 2 <= d < 2^16, with m = magic_of(d): the
+// product x m = x (2^32 + e) / d with 0 <= e < d, so its high word is
+// floor(x / d) while x e < 2^32.
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned magic_of(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
+__device__ __forceinline__ int fdiv(int x, unsigned m) { return (int)__umulhi((unsigned)x, m); }
+#endif
+
 // Codes stored in the neighbour table besides block indices.
 constexpr int NBR_MISSING = -1;   // no block of this level there: interpolate from level k-1
 constexpr int NBR_OUTSIDE = -2;   // outside the domain (level 0 only)
@@ -80,7 +88,7 @@ struct FftAxis {
 constexpr int MAX_RADIX_STAGES = 16;
 // Opt-in dynamic shared memory per CTA requested for the large-tile kernels
 // (below the 227 KB limit so that their small static arrays still fit).
-constexpr int MAX_DYN_SMEM = 200 * 1024;
+constexpr int MAX_DYN_SMEM = 225 * 1024;   // dynamic shared memory per CTA (227 KB opt-in less static use)
 
 // One problem of a handle: a forest, or one component of a forest's vector
 // right-hand side.  Its blocks are contiguous in every level's pool; it has
@@ -244,7 +252,10 @@ template <typename T>
 void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc, int n, cudaStream_t s);
 template <typename T>
 void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
-// stencil kernels with the ghost layer built in shared memory (kernels_fused.cu)
+// stencil kernels with the ghost layer built in shared memory (kernels_fused.cu);
+// fused_smem_bytes: their dynamic shared memory for block size n, order M and
+// element size el (bytes), without a staged right-hand side
+size_t fused_smem_bytes(int n, int M, int el);
 template <typename T>
 void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
                          double h2, int nt, cudaStream_t s);

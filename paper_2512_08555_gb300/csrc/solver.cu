@@ -834,6 +834,9 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
         tune_defaults(h);
         std::string why;
         rc = build_forest(h, kv.second, why);
+        if (rc == MRP_OK && (fused_smem_bytes(h.n, h.M, 8) > (size_t)MAX_DYN_SMEM ||
+                             (h.mixed && fused_smem_bytes(h.n, h.M, 4) > (size_t)MAX_DYN_SMEM)))
+            rc = MRP_ERR_UNSUPPORTED;
         if (rc == MRP_OK) rc = upload_tables(h);
         if (rc == MRP_OK) rc = fft_plan(h);
         if (rc == MRP_OK) rc = lgf_build(h, 0);
