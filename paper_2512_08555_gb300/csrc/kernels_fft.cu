@@ -38,6 +38,17 @@ struct FftLine {
     const typename Cx<R>::T* tw;
 };
 
+// The descriptor a CTA works with: twiddles and the stage table in shared
+// memory (st[0..S) radices, st[S..2S) Ns, st[2S..3S) twiddle strides,
+// st[3S..4S) Ns reciprocals, S = MAX_RADIX_STAGES), read there by index.
+template <typename R>
+struct FftDev {
+    int P, nrad;
+    const int* st;
+    const typename Cx<R>::T* tw;
+};
+constexpr int FFT_STAGE_BYTES = 4 * MAX_RADIX_STAGES * 4;
+
 template <typename R>
 static FftLine<R> line_of(const FftAxis& a) {
     FftLine<R> l{};
@@ -122,19 +133,30 @@ template <typename R> struct Dft<5, R> {
 // by w^{(j mod Ns) r P/(Ns RAD)}, applies the RAD-point DFT and writes
 // b[(j / Ns) Ns RAD + (j mod Ns) + r Ns].  Radix 7 uses the direct sum with
 // the line's twiddle table.
-template <int RAD, typename R, typename C>
+// In the first stage (Ns = 1, FIRST) every twiddle is 1; if moreover only
+// a[0 .. nz) can be nonzero and nz <= P / RAD (a zero-padded input), each
+// butterfly sees one nonzero input and all its outputs equal it.
+template <int RAD, bool FIRST, typename R, typename C>
 __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __restrict__ b, int P, int Ns, unsigned nsm,
-                                               int tstep, const C* tw, int sign) {
+                                               int tstep, const C* tw, int sign, int nz) {
     const int PR = P / RAD;
+    if (FIRST && nz <= PR) {
+        for (int j = threadIdx.x; j < PR; j += blockDim.x) {
+            const C x = a[j];
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) b[j * RAD + r] = x;
+        }
+        return;
+    }
     for (int j = threadIdx.x; j < PR; j += blockDim.x) {
-        const int qd = Ns == 1 ? j : (int)__umulhi((unsigned)j, nsm);     // j / Ns
+        const int qd = FIRST ? j : (int)__umulhi((unsigned)j, nsm);       // j / Ns
         const int k = j - qd * Ns;                                         // j % Ns
         const int step = tstep * k;
         C v[RAD];
 #pragma unroll
         for (int r = 0; r < RAD; ++r) {
             const C x = a[j + r * PR];
-            v[r] = r == 0 ? x : cmul(x, twiddle(tw, step * r, sign));
+            v[r] = (r == 0 || FIRST) ? x : cmul(x, twiddle(tw, step * r, sign));
         }
         if constexpr (RAD == 7) {
             C out[7];
@@ -162,23 +184,34 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
 template <typename R> __host__ __device__ constexpr int fft_tx() { return sizeof(R) == 4 ? 32 : 64; }
 template <typename R> __host__ __device__ constexpr int fft_ly() { return sizeof(R) == 4 ? 8 : 4; }
 
-// One line of length P in a[], b[] as scratch; the fft_tx<R>() threads with
-// the same threadIdx.y cooperate.  With one warp per line the stages are
+// One line of length P in a[], b[] as scratch (a[nz ..) known to be zero);
+// the fft_tx<R>() threads with the same threadIdx.y cooperate.  With one warp per line the stages are
 // separated by warp barriers, else by CTA barriers (every thread of the CTA
 // must then call this).  Returns the buffer that holds the result (Stockham
 // autosort, mixed radix).
 template <typename R, typename C>
-__device__ C* fft_line(C* a, C* b, const FftLine<R>& L, int sign) {
+__device__ C* fft_line(C* a, C* b, const FftDev<R>& L, int sign, int nz) {
     const int P = L.P;
+    constexpr int MS = MAX_RADIX_STAGES;
     for (int st = 0; st < L.nrad; ++st) {
-        const int RAD = L.rad[st], Ns = L.ns[st], ts = L.tstep[st];
-        const unsigned nsm = L.nsm[st];
-        switch (RAD) {
-            case 2: stockham_stage<2, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
-            case 3: stockham_stage<3, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
-            case 4: stockham_stage<4, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
-            case 5: stockham_stage<5, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
-            default: stockham_stage<7, R>(a, b, P, Ns, nsm, ts, L.tw, sign); break;
+        const int RAD = L.st[st], Ns = L.st[MS + st], ts = L.st[2 * MS + st];
+        const unsigned nsm = (unsigned)L.st[3 * MS + st];
+        if (st == 0) {
+            switch (RAD) {
+                case 2: stockham_stage<2, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                case 3: stockham_stage<3, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                case 4: stockham_stage<4, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                case 5: stockham_stage<5, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                default: stockham_stage<7, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+            }
+        } else {
+            switch (RAD) {
+                case 2: stockham_stage<2, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 3: stockham_stage<3, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 4: stockham_stage<4, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 5: stockham_stage<5, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                default: stockham_stage<7, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+            }
         }
         if constexpr (fft_tx<R>() == 32) __syncwarp();
         else __syncthreads();
@@ -188,14 +221,26 @@ __device__ C* fft_line(C* a, C* b, const FftLine<R>& L, int sign) {
 }
 
 
-// Copies the line's twiddle table into shared memory (after the CTA's line
-// buffers) and returns the line descriptor that reads it from there; the
-// table is complete when the next __syncthreads() of the caller has passed.
+// Copies the line's twiddle table and stage table into shared memory (after
+// the CTA's line buffers) and returns the descriptor that reads them from
+// there; both are complete when the next __syncthreads() of the caller has
+// passed.
 template <typename R>
-__device__ __forceinline__ FftLine<R> stage_twiddles(const FftLine<R>& Lg, typename Cx<R>::T* stw) {
+__device__ __forceinline__ FftDev<R> stage_twiddles(const FftLine<R>& Lg, typename Cx<R>::T* stw) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     for (int j = tid; j < Lg.P; j += nth) stw[j] = Lg.tw[j];
-    FftLine<R> L = Lg;
+    int* sst = reinterpret_cast<int*>(stw + Lg.P);
+    constexpr int MS = MAX_RADIX_STAGES;
+    if (tid < MS) {
+        sst[tid] = Lg.rad[tid];
+        sst[MS + tid] = Lg.ns[tid];
+        sst[2 * MS + tid] = Lg.tstep[tid];
+        sst[3 * MS + tid] = (int)Lg.nsm[tid];
+    }
+    FftDev<R> L;
+    L.P = Lg.P;
+    L.nrad = Lg.nrad;
+    L.st = sst;
     L.tw = stw;
     return L;
 }
@@ -221,7 +266,7 @@ __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __res
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const FftDev<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
     const int line = blockIdx.x * fft_ly<R>() + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
@@ -244,7 +289,7 @@ __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __res
             a[pidx(x, L.P)] = C{v, R(0)};
         }
     __syncthreads();
-    C* r = fft_line<R>(a, b, L, -1);
+    C* r = fft_line<R>(a, b, L, -1, g.in_lo[0] == 0 ? g.in_n[0] : L.P);
     if (live) {
         const size_t row = ((size_t)pidx(z, g.Pz) * g.Py + pidx(y, g.Py)) * g.Kx;
         for (int k = threadIdx.x; k < g.Kx; k += blockDim.x) spec[row + k] = r[k];
@@ -262,7 +307,7 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const FftDev<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
     const int P = L.P, P2 = 2 * P;
     const int zi = pidx(g.in_lo[2] + (int)blockIdx.y, g.Pz);
     const int kx0 = blockIdx.x * fft_ly<R>();
@@ -278,7 +323,7 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
         sm[ly * P2 + j] = spec[((size_t)zi * g.Py + j) * g.Kx + kx0 + ly];
     }
     __syncthreads();
-    const int roff = (int)(fft_line<R>(a, b, L, -1) - a);
+    const int roff = (int)(fft_line<R>(a, b, L, -1, g.in_lo[1] == 0 ? g.in_n[1] : P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * P; e += nth) {
         const int ly = e % fft_ly<R>(), y = e / fft_ly<R>();
@@ -292,7 +337,7 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const FftDev<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
     const int P = L.P, P2 = 2 * P;
     const int ky = blockIdx.y;
     const int kx0 = blockIdx.x * fft_ly<R>();
@@ -309,17 +354,34 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
         const int j = pidx(g.in_lo[2] + t, g.Pz);
         sm[ly * P2 + j] = spec[((size_t)j * g.Py + ky) * g.Kx + kx0 + ly];
     }
-    __syncthreads();
-    C* r = fft_line<R>(a, b, L, -1);
+    // the line's G-hat values, fetched now so that their latency overlaps the
+    // input's (the first GPRE per thread in registers, the rest later)
+    constexpr int GPRE = sizeof(R) == 4 ? 8 : 4;
     const int fy = ky <= g.Py - ky ? ky : g.Py - ky;
-    for (int kz = threadIdx.x; kz < P; kz += blockDim.x) {
+    auto ghat_at = [&](int kz) {
         const int fz = kz <= g.Pz - kz ? kz : g.Pz - kz;
-        const R gv = live ? ghat[((size_t)fz * g.Ky + fy) * g.Kx + kx] : R(0);
+        return live ? ghat[((size_t)fz * g.Ky + fy) * g.Kx + kx] : R(0);
+    };
+    R gpre[GPRE];
+#pragma unroll
+    for (int m = 0; m < GPRE; ++m) {
+        const int kz = threadIdx.x + m * blockDim.x;
+        gpre[m] = kz < P ? ghat_at(kz) : R(0);
+    }
+    __syncthreads();
+    C* r = fft_line<R>(a, b, L, -1, g.in_lo[2] == 0 ? g.in_n[2] : P);
+#pragma unroll
+    for (int m = 0; m < GPRE; ++m) {
+        const int kz = threadIdx.x + m * blockDim.x;
+        if (kz < P) r[kz] = C{r[kz].x * gpre[m], r[kz].y * gpre[m]};
+    }
+    for (int kz = threadIdx.x + GPRE * blockDim.x; kz < P; kz += blockDim.x) {
+        const R gv = ghat_at(kz);
         r[kz] = C{r[kz].x * gv, r[kz].y * gv};
     }
     __syncthreads();
     C* other = (r == a) ? b : a;
-    const int qoff = (int)(fft_line<R>(r, other, L, +1) - a);
+    const int qoff = (int)(fft_line<R>(r, other, L, +1, P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * g.out_n[2]; e += nth) {
         const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
@@ -335,7 +397,7 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const FftDev<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
     const int P = L.P, P2 = 2 * P;
     const int z = pidx(g.out_lo[2] + (int)blockIdx.y, g.Pz);
     const int kx0 = blockIdx.x * fft_ly<R>();
@@ -347,7 +409,7 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
         sm[ly * P2 + y] = kx0 + ly < g.Kx ? spec[((size_t)z * g.Py + y) * g.Kx + kx0 + ly] : C{R(0), R(0)};
     }
     __syncthreads();
-    const int roff = (int)(fft_line<R>(a, b, L, +1) - a);
+    const int roff = (int)(fft_line<R>(a, b, L, +1, P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * g.out_n[1]; e += nth) {
         const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
@@ -366,7 +428,7 @@ __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __rest
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
-    const FftLine<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
+    const FftDev<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
     const int line = blockIdx.x * fft_ly<R>() + threadIdx.y;
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
@@ -383,7 +445,7 @@ __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __rest
         a[k] = v;
     }
     __syncthreads();
-    C* r = fft_line<R>(a, b, L, +1);
+    C* r = fft_line<R>(a, b, L, +1, L.P);
     if (!live) return;
     if (g.dense_out) {
         for (int ox = threadIdx.x; ox < g.out_n[0]; ox += blockDim.x)
@@ -429,9 +491,9 @@ static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec,
     using C = typename Cx<R>::T;
     const dim3 blk(fft_tx<R>(), fft_ly<R>());
     const FftLine<R> Lx = line_of<R>(p.ax[0]), Ly = line_of<R>(p.ax[1]), Lz = line_of<R>(p.ax[2]);
-    const size_t smx = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Px;
-    const size_t smy = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Py;
-    const size_t smz = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Pz;
+    const size_t smx = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Px + FFT_STAGE_BYTES;
+    const size_t smy = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Py + FFT_STAGE_BYTES;
+    const size_t smz = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Pz + FFT_STAGE_BYTES;
     const int kxb = (g.Kx + fft_ly<R>() - 1) / fft_ly<R>();
     k_fft_x_fwd<R><<<(g.in_n[1] * g.in_n[2] + fft_ly<R>() - 1) / fft_ly<R>(), blk, smx, s>>>(spec, src, g, Lx);
     k_fft_y_fwd<R><<<dim3(kxb, g.in_n[2]), blk, smy, s>>>(spec, g, Ly);
@@ -721,8 +783,12 @@ fail:
 }
 
 // ---------------------------------------------------------------- FFT plan
+// Radices of P: a single 2 first when P is even (the first stage of a
+// zero-padded forward line then only copies, since the padding takes at
+// least half the line), then 4, 2, 3, 5, 7.
 static bool factor(int P, int* rad, int& nrad) {
     nrad = 0;
+    if (P % 2 == 0) { rad[nrad++] = 2; P /= 2; }
     const int order[] = {4, 2, 3, 5, 7};
     for (int r : order)
         while (P % r == 0) {
@@ -750,9 +816,9 @@ int fft_plan(Handle& h) {
             ax.P = smooth_length(2 * p.n0[a] + 1);
             ax.K = ax.P / 2 + 1;
             if (!factor(ax.P, ax.rad, ax.nrad)) return MRP_ERR_UNSUPPORTED;
-            // a CTA holds (2 LY + 1) P complex values of its lines and twiddles
-            if (sizeof(double2) * (2 * fft_ly<double>() + 1) * (size_t)ax.P > (size_t)MAX_DYN_SMEM ||
-                sizeof(float2) * (2 * fft_ly<float>() + 1) * (size_t)ax.P > (size_t)MAX_DYN_SMEM)
+            // a CTA holds (2 LY + 1) P complex values of its lines and twiddles, and the stage table
+            if (sizeof(double2) * (2 * fft_ly<double>() + 1) * (size_t)ax.P + FFT_STAGE_BYTES > (size_t)MAX_DYN_SMEM ||
+                sizeof(float2) * (2 * fft_ly<float>() + 1) * (size_t)ax.P + FFT_STAGE_BYTES > (size_t)MAX_DYN_SMEM)
                 return MRP_ERR_UNSUPPORTED;
             std::vector<double2> tw(ax.P);
             for (int m = 0; m < ax.P; ++m) {
