@@ -276,7 +276,8 @@ __device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict
 //     block's own interior, same-level neighbours' interiors, and the stored
 //     ghost layer where the region lies outside the domain (cp.async).
 //  2. Interpolated regions (no same-level neighbour), separably:
-//     a. stage the coarse patch over the hull of the regions' stencils;
+//     a. stage the coarse patch over the hull of the regions' stencils
+//        (cp.async, issued with the box copies);
 //     b. reduce each region along its normal axes (one value per coarse
 //        tangential node);
 //     c. faces: interpolate along the first tangential axis into fine x
@@ -319,21 +320,19 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
             }
         }
     }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
     const int nreg = hs.rec[REC_NREG];
-    if (nreg == 0) return;
-    // 2. interpolated regions
     constexpr int plo = 4 - I / 2;
     const int TN = tan_n(n, I);
     const int PL = h + I, PL2 = PL * PL;
     const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
     const int* __restrict__ pnbr = hs.rec + REC_PNBR;
     const int* __restrict__ pch = hs.rec + REC_PCH;
-    // 2a. coarse patch over the hull; patch index p on an axis is coarse
-    //     coordinate base + p relative to the parent's origin
-    {
+    // 2a. coarse patch over the hull, copied together with the box; patch
+    //     index p on an axis is coarse coordinate base + p relative to the
+    //     parent's origin.  A covered coarse node takes its coincident fine
+    //     node from the input level (for this block too: the box holds the
+    //     same values until the caller changes it).
+    if (nreg > 0) {
         const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
         const int bs0 = (bx & 1) * h - 4 + plo, bs1 = (by & 1) * h - 4 + plo, bs2 = (bz & 1) * h - 4 + plo;
         const int lo0 = hs.rec[REC_LO], lo1 = hs.rec[REC_LO + 1], z0 = hs.rec[REC_LO + 2];
@@ -360,8 +359,7 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
                 } else {
                     // covered coarse node: the coincident fine node of the current level
                     const int FZ = 2 * lz - oz * n + 1;
-                    if (ch == b) pcol[pz * PL2] = su[sp.at(FX, FY, FZ)];
-                    else cp_async_el(pcol + pz * PL2, Uk + ((size_t)ch * S3 + (size_t)((FZ * S + FY) * S + FX)));
+                    cp_async_el(pcol + pz * PL2, Uk + ((size_t)ch * S3 + (size_t)((FZ * S + FY) * S + FX)));
                 }
             }
         }
@@ -369,6 +367,7 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
+    if (nreg == 0) return;
     T w[I];
 #pragma unroll
     for (int m = 0; m < I; ++m) w[m] = T(midw<I>(m));
@@ -501,14 +500,23 @@ __host__ __device__ inline int patch_size(int n, int I) {
 }
 
 // Dynamic shared memory of the fused kernels: the split box, then the
-// reduced array and the patch of the interpolation; a staged right-hand side
-// (fstage) reuses that second area once the ghost layer is built (it starts
-// at a 16-byte boundary: the split box is a multiple of 32 elements).
+// reduced array and the patch of the interpolation.  The smoother stages the
+// block's right-hand side in one of two ways (fmode):
+//   1: over that second area, once the ghost layer is built;
+//   2: in an area of its own after it, copied together with the box (more
+//      shared memory, one memory round trip less on interface blocks).
+// Both areas start at 16-byte boundaries (the split box is a multiple of 32
+// elements).
 __host__ __device__ inline size_t rhs_offset(int n, size_t el) { return el * 8 * (size_t)split_h3p(n, (int)el); }
+__host__ __device__ inline size_t rhs_offset2(int n, int I, size_t el) {
+    const size_t e = rhs_offset(n, el) + el * ((size_t)pool_size(n, I) + (size_t)patch_size(n, I));
+    return (e + 15) / 16 * 16;
+}
 template <typename T>
-__host__ __device__ inline size_t fused_smem(int n, int I, bool fstage = false) {
+__host__ __device__ inline size_t fused_smem(int n, int I, int fmode = 0) {
     const size_t interp = (size_t)pool_size(n, I) + (size_t)patch_size(n, I), f = (size_t)n * n * n;
-    return rhs_offset(n, sizeof(T)) + sizeof(T) * (fstage && f > interp ? f : interp);
+    if (fmode == 2) return rhs_offset2(n, I, sizeof(T)) + sizeof(T) * f;
+    return rhs_offset(n, sizeof(T)) + sizeof(T) * (fmode == 1 && f > interp ? f : interp);
 }
 
 size_t fused_smem_bytes(int n, int M, int el) {
@@ -530,30 +538,32 @@ __device__ __forceinline__ void record_prologue(HaloSmem& hs, const LevelView& l
 template <int M, typename T, int I, int NC>
 __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, const T* __restrict__ Uin,
                                                       const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
-                                                      int n_arg, T h2den, const int* __restrict__ order, int fstage) {
+                                                      int n_arg, T h2den, const int* __restrict__ order, int fmode) {
     const int n = NC ? NC : n_arg;    // NC: block size fixed at compile time (0: runtime)
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
     const Split sp = split_of<T>(n);
     T* pool = su + 8 * sp.H3p;
     T* patch = pool + pool_size(n, I);
-    T* fs = pool;           // staged right-hand side, after the interpolation is done with this area
+    // staged right-hand side (fmode 1: over the interpolation scratch; 2: its own area)
+    T* fs = fmode == 2 ? reinterpret_cast<T*>(fz_smem + rhs_offset2(n, I, sizeof(T))) : pool;
     __shared__ HaloSmem hs;
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
     record_prologue(hs, lk, b);
-    // without interpolated regions the right-hand side copy overlaps the box
-    // copy (build_halo waits for both); otherwise it follows the ghost layer
-    const bool early = fstage && hs.rec[REC_NREG] == 0;
+    // the right-hand side copy overlaps the box copy (build_halo waits for
+    // both), except on interface blocks in fmode 1, where it follows the
+    // ghost layer
+    const bool early = fmode == 2 || (fmode == 1 && hs.rec[REC_NREG] == 0);
     if (early) load_rhs(fs, F, b, n, true);
     build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, b, n, sp);
-    if (fstage && !early) {
+    if (fmode == 1 && !early) {
         load_rhs(fs, F, b, n, true);
         cp_async_wait<0>();
         __syncthreads();
     }
-    const T* Fb = fstage ? fs : F + (size_t)b * n * n * n;
+    const T* Fb = fmode ? fs : F + (size_t)b * n * n * n;
     const T inv_c = T(1) / T(LW<M>::c);
 #pragma unroll
     for (int col = 0; col < 8; ++col) {
@@ -995,9 +1005,24 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
                          double h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     set_attrs<T>();
-    // the block's right-hand side goes to shared memory where it fits
-    const int fst = fused_smem<T>(n, M + 2, true) <= (size_t)MAX_DYN_SMEM && (uintptr_t)F % 16 == 0;
-    const size_t sm = fused_smem<T>(n, M + 2, fst);
+    // The block's right-hand side goes to shared memory where it fits: in its
+    // own area when the launch fits in one wave at the CTAs per SM that this
+    // leaves, else over the interpolation scratch.
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+    }
+    int fmode = 0;
+    if ((uintptr_t)F % 16 == 0) {
+        if (fused_smem<T>(n, M + 2, 1) <= (size_t)MAX_DYN_SMEM) fmode = 1;
+        const size_t s2 = fused_smem<T>(n, M + 2, 2);
+        const size_t per_sm = 228 * 1024, per_cta = s2 + sizeof(HaloSmem) + 1024;
+        if (s2 <= (size_t)MAX_DYN_SMEM && (size_t)lk.nb <= (size_t)nsm * (per_sm / per_cta)) fmode = 2;
+    }
+    const int fst = fmode;
+    const size_t sm = fused_smem<T>(n, M + 2, fmode);
     const int ct = cta_size(n, nt);
     if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<2>::den), fst, ct, sm, s);
     if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<4>::den), fst, ct, sm, s);
