@@ -196,19 +196,6 @@ __host__ __device__ inline int pool_size(int n, int I) {
 }
 
 
-// Asynchronous global -> shared copies (cp.async): one element, or 16 bytes.
-template <typename T>
-__device__ __forceinline__ void cp_async_el(T* sdst, const T* gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-    if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Per-axis description of one interpolated ghost region d: its tangential
 // axes ta0 < ta1 (x, y, z order) with their patch strides, the patch strides

@@ -477,18 +477,31 @@ __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __re
         ins[m] = ok;
     }
     const int N1 = n + 1, N12 = N1 * N1, n3 = n * n * n, h = n >> 1;
-    for (int t = threadIdx.x; t < N12 * N1; t += blockDim.x) {
-        const int x = t % N1 - 1, y = (t / N1) % N1 - 1, z = t / N12 - 1;
-        const int ex = x < 0 ? -1 : 0, ey = y < 0 ? -1 : 0, ez = z < 0 ? -1 : 0;
-        const int blk = nb27[dir27(ex, ey, ez)];
-        sr[t] = blk >= 0 ? Rf[(size_t)blk * n3 + ((z - ez * n) * n + (y - ey * n)) * n + (x - ex * n)] : T(0);
+    // the residual window, fine nodes [-1, n)^3, one thread per (x, y) column
+    // walking z (cp.async); nodes of missing neighbours read as 0
+    for (int c = threadIdx.x; c < N12; c += blockDim.x) {
+        const int Y = c / N1, X = c - Y * N1, x = X - 1, y = Y - 1;
+        const int ex = x < 0 ? -1 : 0, ey = y < 0 ? -1 : 0;
+        T* dcol = sr + Y * N1 + X;
+        for (int ez = -1; ez <= 0; ++ez) {
+            const int blk = nb27[dir27(ex, ey, ez)];
+            const int z0 = ez < 0 ? -1 : 0, z1 = ez < 0 ? 0 : n;
+            const T* scol = Rf + (blk >= 0 ? (size_t)blk * n3 + (size_t)((y - ey * n) * n + (x - ex * n)) : 0);
+            for (int z = z0; z < z1; ++z) {
+                if (blk >= 0) cp_async_el(dcol + (z + 1) * N12, scol + (size_t)(z - ez * n) * n * n);
+                else dcol[(z + 1) * N12] = T(0);
+            }
+        }
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int P = lf.parent[B], o = lf.octant[B];
     const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
     const int S = n + 2, S3 = S * S * S;
+    const unsigned mh = magic_of(h);
     for (int q = threadIdx.x; q < h * h * h; q += blockDim.x) {
-        const int i = q % h, j = (q / h) % h, l = q / (h * h);
+        const int q1 = fdiv(q, mh), i = q - q1 * h, l = fdiv(q1, mh), j = q1 - l * h;
         const int fx = 2 * i, fy = 2 * j, fz = 2 * l;
         const int cidx = ((oz + l) * n + oy + j) * n + ox + i;
         Uc[(size_t)P * S3 + ((oz + l + 1) * S + oy + j + 1) * S + ox + i + 1] =
@@ -543,8 +556,9 @@ __global__ void k_prolong(T* __restrict__ Uf, const T* __restrict__ Uc, const T*
     const int S = n + 2, S3 = S * S * S, n3 = n * n * n;
     const int ox = (o & 1) * h, oy = ((o >> 1) & 1) * h, oz = ((o >> 2) & 1) * h;
     const int* cn = lc.nbr + 27 * P;
+    const unsigned mE = magic_of(E);
     for (int t = threadIdx.x; t < E * E * E; t += blockDim.x) {
-        const int i = t % E, j = (t / E) % E, l = t / (E * E);
+        const int t1 = fdiv(t, mE), i = t - t1 * E, l = fdiv(t1, mE), j = t1 - l * E;
         const int cx = ox + i, cy = oy + j, cz = oz + l;
         const int ex = cx >= n, ey = cy >= n, ez = cz >= n;
         const int blk = cn[dir27(ex, ey, ez)];
@@ -552,22 +566,30 @@ __global__ void k_prolong(T* __restrict__ Uf, const T* __restrict__ Uc, const T*
         e[t] = Uc[(size_t)blk * S3 + ((lz + 1) * S + ly + 1) * S + lx + 1] - Hc[(size_t)blk * n3 + (lz * n + ly) * n + lx];
     }
     __syncthreads();
+    // one thread per fine (x, y) column: the x-then-y interpolant of each
+    // coarse plane, then z (coincident plane, or the midpoint of two)
     T* Ub = Uf + (size_t)B * S3;
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int ax = x >> 1, ay = y >> 1, az = z >> 1;
-        const int bx = x & 1, by = y & 1, bz = z & 1;
-        T acc = T(0);
-        for (int mz = 0; mz <= bz; ++mz) {
+    const int S2 = S * S;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int y = c / n, x = c - y * n;
+        const int ax = x >> 1, ay = y >> 1, bx = x & 1, by = y & 1;
+        auto plane = [&](int az) {
             T accy = T(0);
             for (int my = 0; my <= by; ++my) {
                 T accx = T(0);
-                for (int mx = 0; mx <= bx; ++mx) accx += e[((az + mz) * E + ay + my) * E + ax + mx];
+                for (int mx = 0; mx <= bx; ++mx) accx += e[(az * E + ay + my) * E + ax + mx];
                 accy += (bx ? T(0.5) : T(1)) * accx;
             }
-            acc += (by ? T(0.5) : T(1)) * accy;
+            return (by ? T(0.5) : T(1)) * accy;
+        };
+        T* col = Ub + (y + 1) * S + x + 1;
+        T cur = plane(0);
+        for (int az = 0; az < h; ++az) {
+            const T nxt = plane(az + 1);
+            col[(2 * az + 1) * S2] += cur;
+            col[(2 * az + 2) * S2] += T(0.5) * (cur + nxt);
+            cur = nxt;
         }
-        Ub[((z + 1) * S + y + 1) * S + x + 1] += (bz ? T(0.5) : T(1)) * acc;
     }
 }
 

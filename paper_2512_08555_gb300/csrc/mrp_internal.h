@@ -21,6 +21,22 @@ __host__ __device__ inline int dir27(int dx, int dy, int dz) { return (dz + 1) *
 #ifdef __CUDACC__
 __device__ __forceinline__ unsigned magic_of(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
 __device__ __forceinline__ int fdiv(int x, unsigned m) { return (int)__umulhi((unsigned)x, m); }
+
+// Asynchronous global -> shared copies (cp.async): one element, or 16 bytes;
+// a thread's copies complete at cp_async_wait<N>() (all but its N most recent
+// committed groups), and are visible to the CTA after the next barrier.
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* sdst, const T* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 #endif
 
 // Codes stored in the neighbour table besides block indices.
