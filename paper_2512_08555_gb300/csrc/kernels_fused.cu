@@ -73,6 +73,28 @@ __device__ __forceinline__ Split split_of(int n) {
     return sp;
 }
 
+// A staged right-hand side uses the same colour split without a ghost layer:
+//     fat(x, y, z) = ((z&1)*4 + (y&1)*2 + (x&1)) * F3 + (z>>1) Fp + (y>>1) h + (x>>1),
+// h = n/2, F3 = h Fp, with the FP32 plane stride Fp in [h^2, h^2 + 32) chosen,
+// like Hp, to minimise the wavefronts of a colour's loads (h = 8: Fp = 72).
+__host__ __device__ inline int split_fp(int n, int el) {
+    const int h = n / 2;
+    if (el != 4) return h * h;
+    switch (n) {
+        case 8: return 24;
+        case 10: return 27;
+        case 12: return 38;
+        case 14: return 71;
+        case 16: return 72;
+        case 18: return 105;
+        case 20: return 106;
+        case 22: return 139;
+        case 24: return 172;
+        default: return h * h;
+    }
+}
+__host__ __device__ inline int split_f3(int n, int el) { return (n / 2) * split_fp(n, el); }
+
 // The thread's nodes of one colour: node q = tid + k * nt (k < KMAX) of the
 // (n/2)^3 nodes (i, j, l) of a colour, q = i + h (l + h j), packed
 // i | j << 10 | l << 20; a colour c = (cx, cy, cz) places it at interior
@@ -114,12 +136,13 @@ __device__ __forceinline__ Col colour(int col, const Split& sp, int n) {
 
 // Per node of a colour: split index of its (-1,-1,-1) neighbour, natural
 // interior index and natural box index (each before the colour's offsets).
-struct Node { int b0, f, g; };
-__device__ __forceinline__ Node node_of(int packed, const Split& sp, int n) {
+struct Node { int b0, f, g, fs; };
+__device__ __forceinline__ Node node_of(int packed, const Split& sp, int n, int fp = 0) {
     const int i = packed & 1023, j = (packed >> 10) & 1023, l = packed >> 20;
     const int S = n + 2;
     Node d;
     d.b0 = l * sp.H2 + j * sp.H + i;
+    d.fs = l * fp + j * (n >> 1) + i;
     d.f = ((2 * l) * n + 2 * j) * n + 2 * i;
     d.g = ((2 * l + 1) * S + 2 * j + 1) * S + 2 * i + 1;
     return d;
@@ -245,13 +268,22 @@ __device__ __forceinline__ void load_record(HaloSmem& hs, const LevelView& lk, i
     cp_async_commit();
 }
 
-// Starts the copy of block b's n^3 right-hand side into shared memory if
-// `on` (F and fs 16-byte aligned), and commits a cp.async group either way.
+// Starts the copy of block b's n^3 right-hand side into shared memory in the
+// split layout (one thread per (x, y) column walking z, cp.async), and
+// commits a cp.async group.
 template <typename T>
-__device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict__ F, int b, int n, bool on) {
-    const int chunks = on ? n * n * n * (int)sizeof(T) / 16 : 0;
-    const char* src = reinterpret_cast<const char*>(F + (size_t)b * n * n * n);
-    for (int c = threadIdx.x; c < chunks; c += blockDim.x) cp_async16(reinterpret_cast<char*>(fs) + 16 * c, src + 16 * c);
+__device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict__ F, int b, int n) {
+    const int h = n >> 1, Fp = split_fp(n, (int)sizeof(T)), F3 = split_f3(n, (int)sizeof(T));
+    const T* Fb = F + (size_t)b * n * n * n;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int y = c / n, x = c - y * n;
+        T* dcol = fs + (((y & 1) << 1) | (x & 1)) * F3 + (y >> 1) * h + (x >> 1);
+        const T* scol = Fb + c;
+        for (int m = 0; m < h; ++m) {
+            cp_async_el(dcol + m * Fp, scol + (size_t)(2 * m) * n * n);
+            cp_async_el(dcol + 4 * F3 + m * Fp, scol + (size_t)(2 * m + 1) * n * n);
+        }
+    }
     cp_async_commit();
 }
 
@@ -501,7 +533,7 @@ __host__ __device__ inline size_t rhs_offset2(int n, int I, size_t el) {
 }
 template <typename T>
 __host__ __device__ inline size_t fused_smem(int n, int I, int fmode = 0) {
-    const size_t interp = (size_t)pool_size(n, I) + (size_t)patch_size(n, I), f = (size_t)n * n * n;
+    const size_t interp = (size_t)pool_size(n, I) + (size_t)patch_size(n, I), f = 8 * (size_t)split_f3(n, sizeof(T));
     if (fmode == 2) return rhs_offset2(n, I, sizeof(T)) + sizeof(T) * f;
     return rhs_offset(n, sizeof(T)) + sizeof(T) * (fmode == 1 && f > interp ? f : interp);
 }
@@ -543,14 +575,15 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
     // both), except on interface blocks in fmode 1, where it follows the
     // ghost layer
     const bool early = fmode == 2 || (fmode == 1 && hs.rec[REC_NREG] == 0);
-    if (early) load_rhs(fs, F, b, n, true);
+    if (early) load_rhs(fs, F, b, n);
     build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, b, n, sp);
     if (fmode == 1 && !early) {
-        load_rhs(fs, F, b, n, true);
+        load_rhs(fs, F, b, n);
         cp_async_wait<0>();
         __syncthreads();
     }
-    const T* Fb = fmode ? fs : F + (size_t)b * n * n * n;
+    const T* Fb = F + (size_t)b * n * n * n;
+    const int Fp = split_fp(n, (int)sizeof(T)), F3 = split_f3(n, (int)sizeof(T));
     const T inv_c = T(1) / T(LW<M>::c);
 #pragma unroll
     for (int col = 0; col < 8; ++col) {
@@ -558,10 +591,10 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
             if (k < cs.cnt) {
-                const Node d = node_of(cs.q[k], sp, n);
+                const Node d = node_of(cs.q[k], sp, n, Fp);
                 const int b0 = c.cb + d.b0;
-                su[b0 + c.dX + c.dY + c.dZ] =
-                    (h2den * Fb[d.f + c.fo] - offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2)) * inv_c;
+                const T fv = fmode ? fs[col * F3 + d.fs] : Fb[d.f + c.fo];
+                su[b0 + c.dX + c.dY + c.dZ] = (h2den * fv - offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2)) * inv_c;
             }
         __syncthreads();
     }
@@ -1002,7 +1035,7 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
     }
     int fmode = 0;
-    if ((uintptr_t)F % 16 == 0) {
+    {
         if (fused_smem<T>(n, M + 2, 1) <= (size_t)MAX_DYN_SMEM) fmode = 1;
         const size_t s2 = fused_smem<T>(n, M + 2, 2);
         const size_t per_sm = 228 * 1024, per_cta = s2 + sizeof(HaloSmem) + 1024;
