@@ -74,9 +74,11 @@ __device__ __forceinline__ Split split_of(int n) {
 }
 
 // A staged right-hand side uses the same colour split without a ghost layer:
-//     fat(x, y, z) = ((z&1)*4 + (y&1)*2 + (x&1)) * F3 + (z>>1) Fp + (y>>1) h + (x>>1),
-// h = n/2, F3 = h Fp, with the FP32 plane stride Fp in [h^2, h^2 + 32) chosen,
-// like Hp, to minimise the wavefronts of a colour's loads (h = 8: Fp = 72).
+//     fat(x, y, z) = ((z&1)*4 + (y&1)*2 + (x&1)) * F3 + (z>>1) Fp + (y>>1) Fr + (x>>1),
+// h = n/2, F3 = h Fp.  FP32 strides minimise the wavefronts of a colour's
+// loads: for n = 16 (node pairs along x, see the smoother) Fr = 9, Fp = 72;
+// otherwise Fr = h and Fp is the best value in [h^2, h^2 + 32); FP64 keeps
+// Fr = h, Fp = h^2.
 __host__ __device__ inline int split_fp(int n, int el) {
     const int h = n / 2;
     if (el != 4) return h * h;
@@ -93,6 +95,7 @@ __host__ __device__ inline int split_fp(int n, int el) {
         default: return h * h;
     }
 }
+__host__ __device__ inline int split_fr(int n, int el) { return (el == 4 && n == 16) ? 9 : n / 2; }
 __host__ __device__ inline int split_f3(int n, int el) { return (n / 2) * split_fp(n, el); }
 
 // The thread's nodes of one colour: node q = tid + k * nt (k < KMAX) of the
@@ -137,12 +140,12 @@ __device__ __forceinline__ Col colour(int col, const Split& sp, int n) {
 // Per node of a colour: split index of its (-1,-1,-1) neighbour, natural
 // interior index and natural box index (each before the colour's offsets).
 struct Node { int b0, f, g, fs; };
-__device__ __forceinline__ Node node_of(int packed, const Split& sp, int n, int fp = 0) {
+__device__ __forceinline__ Node node_of(int packed, const Split& sp, int n, int fp = 0, int fr = 0) {
     const int i = packed & 1023, j = (packed >> 10) & 1023, l = packed >> 20;
     const int S = n + 2;
     Node d;
     d.b0 = l * sp.H2 + j * sp.H + i;
-    d.fs = l * fp + j * (n >> 1) + i;
+    d.fs = l * fp + j * fr + i;
     d.f = ((2 * l) * n + 2 * j) * n + 2 * i;
     d.g = ((2 * l + 1) * S + 2 * j + 1) * S + 2 * i + 1;
     return d;
@@ -273,11 +276,12 @@ __device__ __forceinline__ void load_record(HaloSmem& hs, const LevelView& lk, i
 // commits a cp.async group.
 template <typename T>
 __device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict__ F, int b, int n) {
-    const int h = n >> 1, Fp = split_fp(n, (int)sizeof(T)), F3 = split_f3(n, (int)sizeof(T));
+    const int h = n >> 1, Fp = split_fp(n, (int)sizeof(T)), Fr = split_fr(n, (int)sizeof(T));
+    const int F3 = split_f3(n, (int)sizeof(T));
     const T* Fb = F + (size_t)b * n * n * n;
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
         const int y = c / n, x = c - y * n;
-        T* dcol = fs + (((y & 1) << 1) | (x & 1)) * F3 + (y >> 1) * h + (x >> 1);
+        T* dcol = fs + (((y & 1) << 1) | (x & 1)) * F3 + (y >> 1) * Fr + (x >> 1);
         const T* scol = Fb + c;
         for (int m = 0; m < h; ++m) {
             cp_async_el(dcol + m * Fp, scol + (size_t)(2 * m) * n * n);
@@ -583,20 +587,56 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
         __syncthreads();
     }
     const T* Fb = F + (size_t)b * n * n * n;
-    const int Fp = split_fp(n, (int)sizeof(T)), F3 = split_f3(n, (int)sizeof(T));
+    const int Fp = split_fp(n, (int)sizeof(T)), Fr = split_fr(n, (int)sizeof(T)), F3 = split_f3(n, (int)sizeof(T));
     const T inv_c = T(1) / T(LW<M>::c);
+    if constexpr (NC != 0 && sizeof(T) == 4) {
+        // Fixed block size, FP32: each work item is a pair of a colour's nodes
+        // adjacent along x (split indices i, i + 1), whose stencils share the
+        // values of the fine plane between them (the +x neighbours of the
+        // first are the -x neighbours of the second).  Lanes take i-pairs
+        // fastest (4), then 4 z rows, then 2 y rows: with Hp = 88 (FP32) the
+        // loads of a warp fall in 32 distinct banks.
+        constexpr int hh = NC / 2, NP = hh * hh * hh / 2;
+        static_assert(hh == 8, "the pair lane order assumes h = 8");
 #pragma unroll
-    for (int col = 0; col < 8; ++col) {
-        const Col c = colour(col, sp, n);
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < cs.cnt) {
-                const Node d = node_of(cs.q[k], sp, n, Fp);
-                const int b0 = c.cb + d.b0;
-                const T fv = fmode ? fs[col * F3 + d.fs] : Fb[d.f + c.fo];
-                su[b0 + c.dX + c.dY + c.dZ] = (h2den * fv - offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2)) * inv_c;
+        for (int col = 0; col < 8; ++col) {
+            const Col c = colour(col, sp, n);
+            for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+                const int ip = p & 3, lq = (p >> 2) & 3, jq = (p >> 4) & 1, r3 = p >> 5;
+                const int l = lq + 4 * (r3 & 1), j = jq + 2 * (r3 >> 1), i = 2 * ip;
+                const int b0 = c.cb + l * sp.H2 + j * sp.H + i;
+                T fa, fb;
+                if (fmode) {
+                    const int fi = col * F3 + l * Fp + j * Fr + i;
+                    fa = fs[fi];
+                    fb = fs[fi + 1];
+                } else {
+                    const int fi = ((2 * l) * n + 2 * j) * n + 2 * i + c.fo;
+                    fa = Fb[fi];
+                    fb = Fb[fi + 2];
+                }
+                const T sa = offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const T sb = offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                su[b0 + c.dX + c.dY + c.dZ] = (h2den * fa - sa) * inv_c;
+                su[b0 + 1 + c.dX + c.dY + c.dZ] = (h2den * fb - sb) * inv_c;
             }
-        __syncthreads();
+            __syncthreads();
+        }
+    } else {
+#pragma unroll
+        for (int col = 0; col < 8; ++col) {
+            const Col c = colour(col, sp, n);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < cs.cnt) {
+                    const Node d = node_of(cs.q[k], sp, n, Fp, Fr);
+                    const int b0 = c.cb + d.b0;
+                    const T fv = fmode ? fs[col * F3 + d.fs] : Fb[d.f + c.fo];
+                    su[b0 + c.dX + c.dY + c.dZ] =
+                        (h2den * fv - offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2)) * inv_c;
+                }
+            __syncthreads();
+        }
     }
     // interior back to global, one thread per (x, y) column
     const int S = n + 2, S2 = S * S;

@@ -262,3 +262,23 @@ def test_config2_full_size(M):
     parts.append(s2.field_get("F", 0).cpu().numpy()[cs.cov0].reshape(-1))
     r = cs.residual(np.concatenate(parts))
     assert np.abs(r).max() < 1e-9 * st.fstar_max
+
+
+@pytest.mark.parametrize("n, M", [(24, 6), (22, 4)])
+def test_largest_block_sizes(n, M):
+    """Block sizes 22 and 24: the FP64 kernels' largest shared-memory footprint
+    (n = 24, M = 6 also takes the tensor form of the raw-f ghost fill), two
+    cycles against the oracle; the mixed-precision solve against FP64."""
+    from paper_2512_08555_gb300.mrp import Solver
+    desc = synth.adaptive_forest((3, 3, 3), n, (-1.0, -1.0, -1.0), 2.0 / (3 * n), 1,
+                                 lambda k, c: (c == 1).all(axis=1))
+    f = synth.sample_leaves(desc, synth.c4_bumps(2, k=2, r_lo=0.15, r_hi=0.25, box=0.2))
+    s = Solver(desc, order=M, tol=0.0, max_cycles=2)
+    u, st = s.solve(torch.from_numpy(f).cuda(), allow_not_converged=True)
+    o = OracleSolver(OracleForest.from_desc(desc), M)
+    uo, _ = o.solve(f, tol=0.0, max_cycles=2)
+    assert _rel(u.cpu().numpy(), uo) < 1e-12
+    u64, _ = Solver(desc, order=M, tol=1e-11, max_cycles=60).solve(torch.from_numpy(f).cuda(), allow_not_converged=True)
+    um, stm = Solver(desc, order=M, tol=1e-10, max_cycles=80, precision="mixed").solve(torch.from_numpy(f).cuda())
+    assert stm.residual < 1e-10
+    assert _rel(um.cpu().numpy(), u64.cpu().numpy()) < 1e-8
