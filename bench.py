@@ -248,7 +248,7 @@ def bench_adjoint(desc, f, u_plain, ms_plain, order, flush, stream, steps):
     return out
 
 
-def bench_five_level(order, flush, stream, steps):
+def bench_five_level(order, flush, stream, steps, inner_cycles=4):
     import torch
     from paper_2512_08555_gb300 import synth
     from paper_2512_08555_gb300.mrp import Solver
@@ -258,7 +258,7 @@ def bench_five_level(order, flush, stream, steps):
            "leaf_nodes": int(desc.leaf_nodes)}
     res = {}
     for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
-        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec)
+        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec, inner_cycles=inner_cycles)
         for _ in range(3):
             s.solve(f)
         s.profile(True)
@@ -519,7 +519,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         xs = max(2, min(args.steps, 3))
         line["adjoint"] = bench_adjoint(desc, f, u_p, ms_p, args.order, flush, stream, xs)
-        line["five_level"] = bench_five_level(args.order, flush, stream, xs)
+        line["five_level"] = bench_five_level(args.order, flush, stream, xs, args.inner_cycles)
         line["batched"] = bench_batched(args.order, flush, stream, xs)
         line["fft_large"] = bench_fft_large(args.order, flush, stream, xs)
     if rank == 0:

@@ -555,6 +555,20 @@ __device__ __forceinline__ void record_prologue(HaloSmem& hs, const LevelView& l
 }
 
 
+// Pair p of a colour's nodes for the fixed block size 16 (h = 8): split
+// indices (i, j, l) and (i + 1, j, l), lanes taking i-pairs fastest (4), then
+// 4 z rows, then 2 y rows (with the FP32 plane stride 88 a warp's loads fall
+// in 32 distinct banks).  256 pairs per colour.
+struct Pair { int i, j, l; };
+__device__ __forceinline__ Pair pair_of(int p) {
+    const int ip = p & 3, lq = (p >> 2) & 3, jq = (p >> 4) & 1, r3 = p >> 5;
+    Pair q;
+    q.i = 2 * ip;
+    q.l = lq + 4 * (r3 & 1);
+    q.j = jq + 2 * (r3 >> 1);
+    return q;
+}
+
 // ---------------------------------------------------------------- smoother
 // One Gauss-Seidel iteration (Sec. 3.1): 8 colours c = (x&1) + 2(y&1) + 4(z&1),
 // u <- (den h^2 f - offcentre) / c; reads Uin, writes the interior to Uout.
@@ -602,8 +616,8 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
             for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-                const int ip = p & 3, lq = (p >> 2) & 3, jq = (p >> 4) & 1, r3 = p >> 5;
-                const int l = lq + 4 * (r3 & 1), j = jq + 2 * (r3 >> 1), i = 2 * ip;
+                const Pair q = pair_of(p);
+                const int i = q.i, j = q.j, l = q.l;
                 const int b0 = c.cb + l * sp.H2 + j * sp.H + i;
                 T fa, fb;
                 if (fmode) {
@@ -671,17 +685,36 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
     record_prologue(hs, lk, b);
     build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
-    for (int col = 0; col < 8; ++col) {
-        const Col c = colour(col, sp, n);
+    if constexpr (NC != 0 && sizeof(T) == 4) {
+        // pairs of nodes adjacent along x, as in the smoother
+        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < cs.cnt) {
-                const Node d = node_of(cs.q[k], sp, n);
-                const int b0 = c.cb + d.b0;
-                const T l = T(LW<M>::c) * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const size_t fi = b * n3 + d.f + c.fo;
-                R[fi] = F[fi] - scale * l;
+        for (int col = 0; col < 8; ++col) {
+            const Col c = colour(col, sp, n);
+            for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+                const Pair q = pair_of(p);
+                const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
+                const T la = T(LW<M>::c) * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const T lb = T(LW<M>::c) * su[b0 + 1 + c.dX + c.dY + c.dZ] +
+                             offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const size_t fi = b * n3 + ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo;
+                R[fi] = F[fi] - scale * la;
+                R[fi + 2] = F[fi + 2] - scale * lb;
             }
+        }
+    } else {
+        for (int col = 0; col < 8; ++col) {
+            const Col c = colour(col, sp, n);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < cs.cnt) {
+                    const Node d = node_of(cs.q[k], sp, n);
+                    const int b0 = c.cb + d.b0;
+                    const T l = T(LW<M>::c) * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                    const size_t fi = b * n3 + d.f + c.fo;
+                    R[fi] = F[fi] - scale * l;
+                }
+        }
     }
 }
 
@@ -719,18 +752,39 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
     }
     record_prologue(hs, lk, b);
     build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
-    for (int col = 0; col < 8; ++col) {
-        const Col c = colour(col, sp, n);
+    if constexpr (NC != 0 && sizeof(T) == 4) {
+        // pairs of nodes adjacent along x, as in the smoother
+        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < cs.cnt) {
-                const Node d = node_of(cs.q[k], sp, n);
-                const int b0 = c.cb + d.b0;
-                const T u = su[b0 + c.dX + c.dY + c.dZ];
-                const size_t fi = b * n3 + d.f + c.fo;
-                F[fi] += scale * (T(LW<M>::c) * u + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2));
-                H[fi] = u;
+        for (int col = 0; col < 8; ++col) {
+            const Col c = colour(col, sp, n);
+            for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+                const Pair q = pair_of(p);
+                const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
+                const T ua = su[b0 + c.dX + c.dY + c.dZ], ub = su[b0 + 1 + c.dX + c.dY + c.dZ];
+                const T la = T(LW<M>::c) * ua + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const T lb = T(LW<M>::c) * ub + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const size_t fi = b * n3 + ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo;
+                F[fi] += scale * la;
+                F[fi + 2] += scale * lb;
+                H[fi] = ua;
+                H[fi + 2] = ub;
             }
+        }
+    } else {
+        for (int col = 0; col < 8; ++col) {
+            const Col c = colour(col, sp, n);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < cs.cnt) {
+                    const Node d = node_of(cs.q[k], sp, n);
+                    const int b0 = c.cb + d.b0;
+                    const T u = su[b0 + c.dX + c.dY + c.dZ];
+                    const size_t fi = b * n3 + d.f + c.fo;
+                    F[fi] += scale * (T(LW<M>::c) * u + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2));
+                    H[fi] = u;
+                }
+        }
     }
 }
 
