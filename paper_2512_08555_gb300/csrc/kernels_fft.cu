@@ -260,39 +260,61 @@ struct Geo {
 __device__ __forceinline__ int pidx(int i, int P) { return i < 0 ? i + P : (i >= P ? i - P : i); }
 
 // ---------------------------------------------------------------- pass A (x, real -> half spectrum)
-// lines: input (y, z) range; x input range.
+// lines: input (y, z) range; x input range.  Each warp transforms two real
+// lines at once as one complex line z = a + i b; with Z = FFT(z) and
+// Z' = conj(Z[(P - k) mod P]), the halves are A = (Z + Z') / 2 and
+// B = (Z - Z') / (2 i).
 template <typename R>
 __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ src, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
     const FftDev<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
-    const int line = blockIdx.x * fft_ly<R>() + threadIdx.y;
+    const int nlines = g.in_n[1] * g.in_n[2];
+    const int line0 = 2 * (blockIdx.x * fft_ly<R>() + threadIdx.y);
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
-    const bool live = line < g.in_n[1] * g.in_n[2];
-    const int ty = live ? line % g.in_n[1] : 0, tz = live ? line / g.in_n[1] : 0;
-    const int y = g.in_lo[1] + ty, z = g.in_lo[2] + tz;
     for (int j = threadIdx.x; j < L.P; j += blockDim.x) a[j] = C{R(0), R(0)};
     __syncthreads();
-    if (live)
+    int ty[2], tz[2];
+    bool live[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int line = line0 + h;
+        live[h] = line < nlines;
+        ty[h] = live[h] ? line % g.in_n[1] : 0;
+        tz[h] = live[h] ? line / g.in_n[1] : 0;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!live[h]) continue;
+        const int y = g.in_lo[1] + ty[h], z = g.in_lo[2] + tz[h];
         for (int tx = threadIdx.x; tx < g.in_n[0]; tx += blockDim.x) {
             const int x = g.in_lo[0] + tx;
             R v;
             if (g.dense_in) {
-                v = src[((size_t)tz * g.in_n[1] + ty) * g.in_n[0] + tx];
+                v = src[((size_t)tz[h] * g.in_n[1] + ty[h]) * g.in_n[0] + tx];
             } else {
                 const int bx = x / g.n, lx = x % g.n, by = y / g.n, ly = y % g.n, bz = z / g.n, lz = z % g.n;
                 const int blk = (bz * g.nby + by) * g.nbx + bx;
                 v = src[(size_t)blk * g.n * g.n * g.n + (lz * g.n + ly) * g.n + lx];
             }
-            a[pidx(x, L.P)] = C{v, R(0)};
+            if (h == 0) a[pidx(x, L.P)].x = v;
+            else a[pidx(x, L.P)].y = v;
         }
+    }
     __syncthreads();
     C* r = fft_line<R>(a, b, L, -1, g.in_lo[0] == 0 ? g.in_n[0] : L.P);
-    if (live) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!live[h]) continue;
+        const int y = g.in_lo[1] + ty[h], z = g.in_lo[2] + tz[h];
         const size_t row = ((size_t)pidx(z, g.Pz) * g.Py + pidx(y, g.Py)) * g.Kx;
-        for (int k = threadIdx.x; k < g.Kx; k += blockDim.x) spec[row + k] = r[k];
+        for (int k = threadIdx.x; k < g.Kx; k += blockDim.x) {
+            const C zk = r[k], zm = r[k == 0 ? 0 : L.P - k];
+            spec[row + k] = h == 0 ? C{R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y)}
+                                   : C{R(0.5) * (zk.y + zm.y), R(0.5) * (zm.x - zk.x)};
+        }
     }
 }
 
@@ -420,51 +442,72 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
 }
 
 // ---------------------------------------------------------------- pass A' (x inverse, half spectrum -> real)
-// lines: output (y, z) range.  Block mode writes node (x, y, z) into every
-// level-0 block whose (n+2)^3 box holds it (interior or ghost layer); dense
-// mode writes the dense output range.
+// lines: output (y, z) range.  Each warp inverts two Hermitian lines at once
+// as one complex line A + i B, whose real and imaginary parts are the two
+// real outputs.  Block mode writes node (x, y, z) into every level-0 block
+// whose (n+2)^3 box holds it (interior or ghost layer); dense mode writes the
+// dense output range.
 template <typename R>
 __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
     const FftDev<R> L = stage_twiddles<R>(Lg, sm + fft_ly<R>() * 2 * Lg.P);
-    const int line = blockIdx.x * fft_ly<R>() + threadIdx.y;
+    const int nlines = g.out_n[1] * g.out_n[2];
+    const int line0 = 2 * (blockIdx.x * fft_ly<R>() + threadIdx.y);
     C* a = sm + threadIdx.y * 2 * L.P;
     C* b = a + L.P;
-    const bool live = line < g.out_n[1] * g.out_n[2];
-    const int oy = live ? line % g.out_n[1] : 0, oz = live ? line / g.out_n[1] : 0;
-    const int ty = g.out_lo[1] + oy, tz = g.out_lo[2] + oz;
-    const C* src = spec + ((size_t)pidx(tz, g.Pz) * g.Py + pidx(ty, g.Py)) * g.Kx;
+    int oy[2], oz[2];
+    bool live[2];
+    const C* src[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int line = line0 + h;
+        live[h] = line < nlines;
+        oy[h] = live[h] ? line % g.out_n[1] : 0;
+        oz[h] = live[h] ? line / g.out_n[1] : 0;
+        src[h] = spec + ((size_t)pidx(g.out_lo[2] + oz[h], g.Pz) * g.Py + pidx(g.out_lo[1] + oy[h], g.Py)) * g.Kx;
+    }
     for (int k = threadIdx.x; k < L.P; k += blockDim.x) {
-        C v = C{R(0), R(0)};
-        if (live) {
-            if (k < g.Kx) v = src[k];
-            else { v = src[L.P - k]; v.y = -v.y; }
+        C v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            v[h] = C{R(0), R(0)};
+            if (live[h]) {
+                if (k < g.Kx) v[h] = src[h][k];
+                else { v[h] = src[h][L.P - k]; v[h].y = -v[h].y; }
+            }
         }
-        a[k] = v;
+        a[k] = C{v[0].x - v[1].y, v[0].y + v[1].x};
     }
     __syncthreads();
     C* r = fft_line<R>(a, b, L, +1, L.P);
-    if (!live) return;
-    if (g.dense_out) {
-        for (int ox = threadIdx.x; ox < g.out_n[0]; ox += blockDim.x)
-            dst[((size_t)oz * g.out_n[1] + oy) * g.out_n[0] + ox] = r[pidx(g.out_lo[0] + ox, g.Px)].x;
-        return;
-    }
     const int S = g.n + 2;
-    for (int ox = threadIdx.x; ox < g.out_n[0]; ox += blockDim.x) {
-        const int tx = g.out_lo[0] + ox;
-        const R val = r[pidx(tx, g.Px)].x;
-        for (int bz = (tz - 1 < 0 ? -1 : (tz - 1) / g.n); bz <= (tz + 1) / g.n; ++bz) {
-            if (bz < 0 || bz >= g.nbz || tz < bz * g.n - 1 || tz > bz * g.n + g.n) continue;
-            for (int by = (ty - 1 < 0 ? -1 : (ty - 1) / g.n); by <= (ty + 1) / g.n; ++by) {
-                if (by < 0 || by >= g.nby || ty < by * g.n - 1 || ty > by * g.n + g.n) continue;
-                for (int bx = (tx - 1 < 0 ? -1 : (tx - 1) / g.n); bx <= (tx + 1) / g.n; ++bx) {
-                    if (bx < 0 || bx >= g.nbx || tx < bx * g.n - 1 || tx > bx * g.n + g.n) continue;
-                    const int blk = (bz * g.nby + by) * g.nbx + bx;
-                    const int lx = tx - bx * g.n + 1, ly = ty - by * g.n + 1, lz = tz - bz * g.n + 1;
-                    dst[(size_t)blk * S * S * S + (lz * S + ly) * S + lx] = val;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!live[h]) continue;
+        const int ty = g.out_lo[1] + oy[h], tz = g.out_lo[2] + oz[h];
+        if (g.dense_out) {
+            for (int ox = threadIdx.x; ox < g.out_n[0]; ox += blockDim.x) {
+                const C w = r[pidx(g.out_lo[0] + ox, g.Px)];
+                dst[((size_t)oz[h] * g.out_n[1] + oy[h]) * g.out_n[0] + ox] = h == 0 ? w.x : w.y;
+            }
+            continue;
+        }
+        for (int ox = threadIdx.x; ox < g.out_n[0]; ox += blockDim.x) {
+            const int tx = g.out_lo[0] + ox;
+            const C w = r[pidx(tx, g.Px)];
+            const R val = h == 0 ? w.x : w.y;
+            for (int bz = (tz - 1 < 0 ? -1 : (tz - 1) / g.n); bz <= (tz + 1) / g.n; ++bz) {
+                if (bz < 0 || bz >= g.nbz || tz < bz * g.n - 1 || tz > bz * g.n + g.n) continue;
+                for (int by = (ty - 1 < 0 ? -1 : (ty - 1) / g.n); by <= (ty + 1) / g.n; ++by) {
+                    if (by < 0 || by >= g.nby || ty < by * g.n - 1 || ty > by * g.n + g.n) continue;
+                    for (int bx = (tx - 1 < 0 ? -1 : (tx - 1) / g.n); bx <= (tx + 1) / g.n; ++bx) {
+                        if (bx < 0 || bx >= g.nbx || tx < bx * g.n - 1 || tx > bx * g.n + g.n) continue;
+                        const int blk = (bz * g.nby + by) * g.nbx + bx;
+                        const int lx = tx - bx * g.n + 1, ly = ty - by * g.n + 1, lz = tz - bz * g.n + 1;
+                        dst[(size_t)blk * S * S * S + (lz * S + ly) * S + lx] = val;
+                    }
                 }
             }
         }
@@ -495,11 +538,12 @@ static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec,
     const size_t smy = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Py + FFT_STAGE_BYTES;
     const size_t smz = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Pz + FFT_STAGE_BYTES;
     const int kxb = (g.Kx + fft_ly<R>() - 1) / fft_ly<R>();
-    k_fft_x_fwd<R><<<(g.in_n[1] * g.in_n[2] + fft_ly<R>() - 1) / fft_ly<R>(), blk, smx, s>>>(spec, src, g, Lx);
+    const int lx2 = 2 * fft_ly<R>();   // lines per CTA in the x passes (two per warp)
+    k_fft_x_fwd<R><<<(g.in_n[1] * g.in_n[2] + lx2 - 1) / lx2, blk, smx, s>>>(spec, src, g, Lx);
     k_fft_y_fwd<R><<<dim3(kxb, g.in_n[2]), blk, smy, s>>>(spec, g, Ly);
     k_fft_z_conv<R><<<dim3(kxb, g.Py), blk, smz, s>>>(spec, ghat, g, Lz);
     k_fft_y_inv<R><<<dim3(kxb, g.out_n[2]), blk, smy, s>>>(spec, g, Ly);
-    k_fft_x_inv<R><<<(g.out_n[1] * g.out_n[2] + fft_ly<R>() - 1) / fft_ly<R>(), blk, smx, s>>>(dst, spec, g, Lx);
+    k_fft_x_inv<R><<<(g.out_n[1] * g.out_n[2] + lx2 - 1) / lx2, blk, smx, s>>>(dst, spec, g, Lx);
 }
 
 // Level-0 solve of every problem of the handle, one after another on s (they

@@ -90,11 +90,11 @@ void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int 
 // U64 += U32 on the interior of every block of a level.
 __global__ void k_accumulate_u(double* __restrict__ U64, const float* __restrict__ U32, int n) {
     const int b = blockIdx.x;
-    const int S = n + 2, S3 = S * S * S;
-    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const size_t o = (size_t)b * S3 + ((z + 1) * S + y + 1) * S + x + 1;
-        U64[o] += (double)U32[o];
+    const int S = n + 2, S2 = S * S, S3 = S2 * S;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {       // one thread per (x, y) column
+        const int y = c / n, x = c - y * n;
+        const size_t o = (size_t)b * S3 + (size_t)((y + 1) * S + x + 1);
+        for (int z = 1; z <= n; ++z) U64[o + (size_t)z * S2] += (double)U32[o + (size_t)z * S2];
     }
 }
 

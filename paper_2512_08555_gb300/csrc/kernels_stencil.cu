@@ -418,25 +418,30 @@ __global__ void k_rhs_star(double* __restrict__ F, const double* __restrict__ Fr
     const int S = n + 4, S2 = S * S;
     const double* a = Fraw + (size_t)b * S2 * S;
     double* out = F + (size_t)b * n * n * n;
-    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
-        const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        const int o = ((z + 2) * S + y + 2) * S + x + 2;
-        double v;
-        if (M == 2) {
-            v = a[o];
-        } else {
-            const double sf = (a[o - 1] + a[o + 1]) + (a[o - S] + a[o + S]) + (a[o - S2] + a[o + S2]);
-            if (M == 4) {
-                v = 0.5 * a[o] + sf / 12.0;
+    // one thread per (x, y) column walking z; the weights are multiplied
+    // (reciprocals of 12, 18, 90, 240 rounded once), not divided
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int y = c / n, x = c - y * n;
+        for (int z = 0; z < n; ++z) {
+            const int o = ((z + 2) * S + y + 2) * S + x + 2;
+            double v;
+            if (M == 2) {
+                v = a[o];
             } else {
-                const double se = (a[o - 1 - S] + a[o + 1 - S]) + (a[o - 1 + S] + a[o + 1 + S])
-                                + (a[o - 1 - S2] + a[o + 1 - S2]) + (a[o - 1 + S2] + a[o + 1 + S2])
-                                + (a[o - S - S2] + a[o + S - S2]) + (a[o - S + S2] + a[o + S + S2]);
-                const double s2 = (a[o - 2] + a[o + 2]) + (a[o - 2 * S] + a[o + 2 * S]) + (a[o - 2 * S2] + a[o + 2 * S2]);
-                v = (67.0 / 120.0) * a[o] + sf / 18.0 + se / 90.0 - s2 / 240.0;
+                const double sf = (a[o - 1] + a[o + 1]) + (a[o - S] + a[o + S]) + (a[o - S2] + a[o + S2]);
+                if (M == 4) {
+                    v = 0.5 * a[o] + sf * (1.0 / 12.0);
+                } else {
+                    const double se = (a[o - 1 - S] + a[o + 1 - S]) + (a[o - 1 + S] + a[o + 1 + S])
+                                    + (a[o - 1 - S2] + a[o + 1 - S2]) + (a[o - 1 + S2] + a[o + 1 + S2])
+                                    + (a[o - S - S2] + a[o + S - S2]) + (a[o - S + S2] + a[o + S + S2]);
+                    const double s2 =
+                        (a[o - 2] + a[o + 2]) + (a[o - 2 * S] + a[o + 2 * S]) + (a[o - 2 * S2] + a[o + 2 * S2]);
+                    v = (67.0 / 120.0) * a[o] + sf * (1.0 / 18.0) + se * (1.0 / 90.0) - s2 * (1.0 / 240.0);
+                }
             }
+            out[(z * n + y) * n + x] = v;
         }
-        out[t] = v;
     }
 }
 
