@@ -25,7 +25,8 @@ namespace mrp {
 // max-norm bit patterns (slots 1 and 0); ctr: cycles, refinement steps, status.
 __global__ void k_loop_check(const unsigned long long* __restrict__ res, const unsigned long long* __restrict__ fstar,
                              int np, double tol, int* __restrict__ ctr, double* __restrict__ rel_out, int mixed, int inner,
-                             int max_cycles, int max_ir, int count_step, cudaGraphConditionalHandle hc) {
+                             int max_cycles, int max_ir, int count_step, int need_step,
+                             cudaGraphConditionalHandle hc) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     bool all = true, bad = false;
     for (int p = 0; p < np; ++p) {
@@ -34,6 +35,7 @@ __global__ void k_loop_check(const unsigned long long* __restrict__ res, const u
         const double rel = r / (f > 0.0 ? f : 1.0);
         rel_out[p] = rel;
         if (!(rel < tol)) all = false;
+        if (need_step && rel > 0.0) all = false;       // a nonzero first residual takes a refinement step
         if (!isfinite(rel)) bad = true;
     }
     if (count_step) {
@@ -101,9 +103,9 @@ static int build_group(Handle& h, cudaGraph_t G, cudaStream_t cs, const double* 
     cudaMemsetAsync(h.loop_ctr, 0, sizeof(int) * 4, cs);
     solve_begin(h, f, cs);
     if (h.mixed) {
-        outer_residual_launch(h, cs);
+        outer_residual_launch(h, cs, true);
         k_loop_check<<<1, 32, 0, cs>>>(h.slot(1), h.slot(0), np, h.tol, h.loop_ctr, h.loop_rel, 1, h.inner_cycles,
-                                       h.max_cycles, h.max_ir, 0, hc);
+                                       h.max_cycles, h.max_ir, 0, h.L >= 1 ? 1 : 0, hc);
     }
     std::vector<cudaGraphNode_t> deps;
     int rc = tail_of(cs, deps);
@@ -130,7 +132,7 @@ static int build_group(Handle& h, cudaGraph_t G, cudaStream_t cs, const double* 
         leaf_residual_launch(h, cs);
     }
     k_loop_check<<<1, 32, 0, cs>>>(h.slot(1), h.slot(0), np, h.tol, h.loop_ctr, h.loop_rel, h.mixed ? 1 : 0,
-                                   h.inner_cycles, h.max_cycles, h.max_ir, 1, hc);
+                                   h.inner_cycles, h.max_cycles, h.max_ir, 1, 0, hc);
     restore_buffers(h, p0, cs);
     if (cudaStreamEndCapture(cs, &dummy) != cudaSuccess) return MRP_ERR_CUDA;
     h.gl_body = h.launches - l0 + 1;

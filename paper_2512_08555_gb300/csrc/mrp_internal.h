@@ -242,7 +242,8 @@ int fft_plan(Handle& h);
 template <typename T> void vcycle(Handle& h, cudaStream_t s);
 void solve_begin(Handle& h, const double* f, cudaStream_t s);
 void leaf_residual_launch(Handle& h, cudaStream_t s);
-void outer_residual_launch(Handle& h, cudaStream_t s);
+// first: the residual at u = 0 (its level-0 solution convolved in FP32)
+void outer_residual_launch(Handle& h, cudaStream_t s, bool first = false);
 void correction_launch(Handle& h, cudaStream_t s);
 void solve_end(Handle& h, double* u, cudaStream_t s);
 int autotune(Handle& h, cudaStream_t s);

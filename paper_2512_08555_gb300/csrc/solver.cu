@@ -692,10 +692,30 @@ void leaf_residual_launch(Handle& h, cudaStream_t s) {
 // system (leaf rows, and on covered level-0 nodes the mismatch c0 between the
 // convolution of the accumulated FP64 source and the injection of level 1),
 // FP32 correction cycles from zero, FP64 accumulation.
-void outer_residual_launch(Handle& h, cudaStream_t s) {
+void outer_residual_launch(Handle& h, cudaStream_t s, bool first) {
     Level& l0 = h.lv[0];
     const double inv_h02 = 1.0 / (h.h0 * h.h0);
-    coarse_solve<double>(h, s);
+    if (first && h.L >= 1) {
+        // At u = 0 the level-0 solution only feeds the first correction,
+        // which the FP32 cycles compute to FP32 accuracy anyway: convolve
+        // in FP32.  Every later outer residual convolves in FP64 from the
+        // accumulated source, so the refinement still converges in FP64;
+        // the stop rule takes at least one refinement step after this
+        // residual unless it is exactly zero.  (With one level the level-0
+        // solve is the whole answer and stays FP64.)
+        {
+            PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 2);
+            launch_cast_rhs(l0.F32, l0.F, l0.leaf_blocks, l0.nleaf, h.n, false, s);
+            launch_cast_rhs(l0.F32, l0.F, l0.cov_blocks, l0.ncov, h.n, false, s);
+        }
+        coarse_solve<float>(h, s);
+        const size_t S = h.n + 2;
+        PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 1);
+        cudaMemsetAsync(l0.U, 0, sizeof(double) * l0.nb * S * S * S, s);
+        launch_accumulate_u(l0.U, ucur<float>(h, 0), l0.nb, h.n, s);
+    } else {
+        coarse_solve<double>(h, s);
+    }
     cudaMemsetAsync(h.slot(1), 0, sizeof(unsigned long long) * h.nprob(), s);
     for (int k = h.L; k >= 2; --k) inject_level<double>(h, k, s);
     if (h.L >= 1) {
@@ -739,8 +759,8 @@ static void solve_step(Handle& h, cudaStream_t s, SolveState& st) {
         st.cycles += h.inner_cycles;
         ++st.ir;
     }
+    outer_residual_launch(h, s, !st.started);
     st.started = true;
-    outer_residual_launch(h, s);
 }
 
 static int solve_check(Handle& h, cudaStream_t s, SolveState& st) {
@@ -752,6 +772,7 @@ static int solve_check(Handle& h, cudaStream_t s, SolveState& st) {
         st.rel[p] = r[p] / st.scale[p];
         if (!std::isfinite(st.rel[p])) { st.rc = MRP_ERR_NUMERICAL; st.done = true; return MRP_OK; }
         if (!(st.rel[p] < h.tol)) all = false;
+        if (h.mixed && h.L >= 1 && st.ir == 0 && st.rel[p] > 0.0) all = false;   // first residual: FP32 level 0
     }
     if (all) st.done = true;
     else if (!h.mixed && st.cycles >= h.max_cycles) st.done = true;
