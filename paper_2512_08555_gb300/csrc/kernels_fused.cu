@@ -75,7 +75,7 @@ __device__ __forceinline__ Split split_of(int n) {
 
 // A staged right-hand side uses the same colour split without a ghost layer:
 //     fat(x, y, z) = ((z&1)*4 + (y&1)*2 + (x&1)) * F3 + (z>>1) Fp + (y>>1) Fr + (x>>1),
-// h = n/2, F3 = h Fp.  FP32 strides minimise the wavefronts of a colour's
+// h = n/2, F3 >= h Fp.  FP32 strides minimise the wavefronts of a colour's
 // loads: for n = 16 (node pairs along x, see the smoother) Fr = 9, Fp = 72;
 // otherwise Fr = h and Fp is the best value in [h^2, h^2 + 32); FP64 keeps
 // Fr = h, Fp = h^2.
@@ -96,7 +96,12 @@ __host__ __device__ inline int split_fp(int n, int el) {
     }
 }
 __host__ __device__ inline int split_fr(int n, int el) { return (el == 4 && n == 16) ? 9 : n / 2; }
-__host__ __device__ inline int split_f3(int n, int el) { return (n / 2) * split_fp(n, el); }
+// Colour sub-array stride: FP32 pads h Fp to 16 (mod 32) words, so that the
+// two x-parities of a column copy fall 16 banks apart.
+__host__ __device__ inline int split_f3(int n, int el) {
+    const int f = (n / 2) * split_fp(n, el);
+    return el == 4 ? f + ((16 - f % 32) % 32 + 32) % 32 : f;
+}
 
 // The thread's nodes of one colour: node q = tid + k * nt (k < KMAX) of the
 // (n/2)^3 nodes (i, j, l) of a colour, q = i + h (l + h j), packed
@@ -1107,6 +1112,12 @@ static int cta_size(int n, int nt) {
     while (nt < 512 && nt * KMAX < h3) nt += 32;
     return nt;
 }
+// Kernels whose fixed-size build has 256 work items per phase (FP32 node
+// pairs, FP64 leaf-residual rows) take at most 256 threads: more would idle.
+static int cta_size_fixed(int n, int nt, bool fixed_items) {
+    const int c = cta_size(n, nt);
+    return (fixed_items && n == 16 && c > 256) ? 256 : c;
+}
 
 // The fused kernels come in two builds: block size 16 fixed at compile time
 // (constant strides and offsets) and any block size at run time.
@@ -1183,7 +1194,7 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
     }
     const int fst = fmode;
     const size_t sm = fused_smem<T>(n, M + 2, fmode);
-    const int ct = cta_size(n, nt);
+    const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
     if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<2>::den), fst, ct, sm, s);
     if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<4>::den), fst, ct, sm, s);
     if (M == 6) smooth_m<6, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<6>::den), fst, ct, sm, s);
@@ -1195,7 +1206,7 @@ void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView 
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    const int ct = cta_size(n, nt);
+    const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
     if (M == 2) residual_m<2, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
     if (M == 4) residual_m<4, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, s);
     if (M == 6) residual_m<6, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, s);
@@ -1207,7 +1218,7 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
     if (lk.nb == 0) return;
     set_attrs<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
-    const int ct = cta_size(n, nt);
+    const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
     if (M == 2) fas_m<2, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
     if (M == 4) fas_m<4, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, s);
     if (M == 6) fas_m<6, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, s);
@@ -1219,7 +1230,7 @@ void launch_leafres_fused(double* R, const double* U, const double* F, const dou
     if (nblocks == 0) return;
     set_attrs<double>();
     const size_t sm = fused_smem<double>(n, M + 2);
-    const int ct = cta_size(n, nt);
+    const int ct = cta_size_fixed(n, nt, true);
     if (M == 2) leafres_m<2>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<2>::den, out, ct, sm, s);
     if (M == 4) leafres_m<4>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<4>::den, out, ct, sm, s);
     if (M == 6) leafres_m<6>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<6>::den, out, ct, sm, s);
