@@ -46,10 +46,10 @@ ORACLE_CYCLES = {4: 11, 6: 12, 2: 17}
 STENCIL_POINTS = {2: 7, 4: 19, 6: 27}
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch of the FP32 smoother from one ncu capture
-# (profiles/k_smooth_fused_f32_adaptive_2p8M_o4.md: average over the 24 launches
-# of two V-cycles of the headline forest; profiles/k_smooth_fused_f32_level4_29p5M_o4.md:
-# the level-4 launches of the five-level forest).  Valid while the kernel is unchanged.
+# DRAM bytes (read + write) per launch of the FP32 smoother from one ncu capture:
+# the average over the 24 launches of the first two V-cycles on the headline
+# forest, and the first level-4 launch of the five-level forest (the ncu
+# summaries under profiles/ give the commands).  Valid while the kernel is unchanged.
 SMOOTH32_TRAFFIC = {"headline": 13277994, "five_level_level4": 396550656}
 
 

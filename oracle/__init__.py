@@ -7,9 +7,8 @@ generator with the CUDA library; both sides receive the same seeded inputs
 from the synthetic generator module.
 
 Each function follows the paper (arXiv 2512.08555) step by step and cites the
-passage it implements.  Every numeric choice the paper leaves open is taken
-from the readings listed in the design doc and restated in the docstring where it
-is used.
+passage it implements.  Every numeric choice the paper leaves open is stated
+in the docstring of the function that makes it.
 
 Modules
 -------
