@@ -1,0 +1,9 @@
+// FP64 Gauss-Seidel sweep with the fused ghost layer (instantiations).
+#include "kernels_fused.cuh"
+
+namespace mrp {
+
+template void launch_smooth_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView, int,
+                                          int, double, int, cudaStream_t);
+
+}  // namespace mrp

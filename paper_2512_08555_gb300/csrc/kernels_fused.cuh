@@ -17,6 +17,12 @@
 // All values are read from the input buffers, which no CTA of the launch
 // writes: ghost layers are frozen for the duration of a sweep, which writes
 // its result to a second buffer.
+//
+// This header holds the device code and the launcher templates; the
+// fused_*.cu translation units instantiate them by family and precision, so
+// that they compile in parallel.
+#pragma once
+
 #include "mrp_internal.h"
 
 namespace mrp {
@@ -547,9 +553,6 @@ __host__ __device__ inline size_t fused_smem(int n, int I, int fmode = 0) {
     return rhs_offset(n, sizeof(T)) + sizeof(T) * (fmode == 1 && f > interp ? f : interp);
 }
 
-size_t fused_smem_bytes(int n, int M, int el) {
-    return el == 8 ? fused_smem<double>(n, M + 2) : fused_smem<float>(n, M + 2);
-}
 
 // Prologue of the fused kernels that stage no right-hand side: the block's
 // record, complete and visible on return.
@@ -642,7 +645,9 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
             __syncthreads();
         }
     } else {
-#pragma unroll
+        // (colour loop not unrolled: the FP64 sweep is bound by its arithmetic, and
+        // the runtime-size build has no constant offsets to gain)
+#pragma unroll 1
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
 #pragma unroll
@@ -1102,19 +1107,17 @@ void launch_ghost_T_fused(T* A, T* Ac, LevelView lk, LevelView lc, int n, int M,
     if (M == 4) k_ghost_T_fused<T, 6><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
     if (M == 6) k_ghost_T_fused<T, 8><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
 }
-template void launch_ghost_T_fused<double>(double*, double*, LevelView, LevelView, int, int, cudaStream_t);
-template void launch_ghost_T_fused<float>(float*, float*, LevelView, LevelView, int, int, cudaStream_t);
 
 // CTA size actually launched: the requested one, raised (in warps) until each
 // thread holds at most KMAX nodes of a colour.
-static int cta_size(int n, int nt) {
+inline int cta_size(int n, int nt) {
     const int h3 = (n / 2) * (n / 2) * (n / 2);
     while (nt < 512 && nt * KMAX < h3) nt += 32;
     return nt;
 }
 // Kernels whose fixed-size build has 256 work items per phase (FP32 node
 // pairs, FP64 leaf-residual rows) take at most 256 threads: more would idle.
-static int cta_size_fixed(int n, int nt, bool fixed_items) {
+inline int cta_size_fixed(int n, int nt, bool fixed_items) {
     const int c = cta_size(n, nt);
     return (fixed_items && n == 16 && c > 256) ? 256 : c;
 }
@@ -1123,20 +1126,47 @@ static int cta_size_fixed(int n, int nt, bool fixed_items) {
 // (constant strides and offsets) and any block size at run time.
 constexpr int NC_FIXED = 16;
 
-template <int M, typename T>
-static void set_attrs_m() {
-    constexpr int I = M + 2;
-    allow(k_smooth_fused<M, T, I, NC_FIXED>); allow(k_smooth_fused<M, T, I, 0>);
-    allow(k_residual_fused<M, T, I, NC_FIXED>); allow(k_residual_fused<M, T, I, 0>);
-    allow(k_fas_fused<M, T, I, NC_FIXED>); allow(k_fas_fused<M, T, I, 0>);
-    if constexpr (sizeof(T) == 8) { allow(k_leafres_fused<M, I, NC_FIXED>); allow(k_leafres_fused<M, I, 0>); }
-}
-
+// Per-family shared-memory attributes, set once per process (each family's
+// instantiations live in one translation unit).
 template <typename T>
-static void set_attrs() {
+static void attrs_smooth() {
     static bool done = false;
     if (done) return;
-    set_attrs_m<2, T>(); set_attrs_m<4, T>(); set_attrs_m<6, T>();
+    allow(k_smooth_fused<2, T, 4, NC_FIXED>); allow(k_smooth_fused<2, T, 4, 0>);
+    allow(k_smooth_fused<4, T, 6, NC_FIXED>); allow(k_smooth_fused<4, T, 6, 0>);
+    allow(k_smooth_fused<6, T, 8, NC_FIXED>); allow(k_smooth_fused<6, T, 8, 0>);
+    done = true;
+}
+template <typename T>
+static void attrs_residual() {
+    static bool done = false;
+    if (done) return;
+    allow(k_residual_fused<2, T, 4, NC_FIXED>); allow(k_residual_fused<2, T, 4, 0>);
+    allow(k_residual_fused<4, T, 6, NC_FIXED>); allow(k_residual_fused<4, T, 6, 0>);
+    allow(k_residual_fused<6, T, 8, NC_FIXED>); allow(k_residual_fused<6, T, 8, 0>);
+    done = true;
+}
+template <typename T>
+static void attrs_fas() {
+    static bool done = false;
+    if (done) return;
+    allow(k_fas_fused<2, T, 4, NC_FIXED>); allow(k_fas_fused<2, T, 4, 0>);
+    allow(k_fas_fused<4, T, 6, NC_FIXED>); allow(k_fas_fused<4, T, 6, 0>);
+    allow(k_fas_fused<6, T, 8, NC_FIXED>); allow(k_fas_fused<6, T, 8, 0>);
+    done = true;
+}
+inline void attrs_leafres() {
+    static bool done = false;
+    if (done) return;
+    allow(k_leafres_fused<2, 4, NC_FIXED>); allow(k_leafres_fused<2, 4, 0>);
+    allow(k_leafres_fused<4, 6, NC_FIXED>); allow(k_leafres_fused<4, 6, 0>);
+    allow(k_leafres_fused<6, 8, NC_FIXED>); allow(k_leafres_fused<6, 8, 0>);
+    done = true;
+}
+template <typename T>
+static void attrs_halo_dump() {
+    static bool done = false;
+    if (done) return;
     allow(k_halo_dump<T, 4>); allow(k_halo_dump<T, 6>); allow(k_halo_dump<T, 8>);
     done = true;
 }
@@ -1175,7 +1205,7 @@ template <typename T>
 void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
                          double h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
-    set_attrs<T>();
+    attrs_smooth<T>();
     // The block's right-hand side goes to shared memory where it fits: in its
     // own area when the launch fits in one wave at the CTAs per SM that this
     // leaves, else over the interpolation scratch.
@@ -1204,7 +1234,7 @@ template <typename T>
 void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView lk, LevelView lc, int n, int M,
                            double inv_h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
-    set_attrs<T>();
+    attrs_residual<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
     const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
     if (M == 2) residual_m<2, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
@@ -1216,7 +1246,7 @@ template <typename T>
 void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, double inv_h2,
                       int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
-    set_attrs<T>();
+    attrs_fas<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
     const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
     if (M == 2) fas_m<2, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
@@ -1224,41 +1254,15 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
     if (M == 6) fas_m<6, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, s);
 }
 
-void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
-                          LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, int nt,
-                          cudaStream_t s) {
-    if (nblocks == 0) return;
-    set_attrs<double>();
-    const size_t sm = fused_smem<double>(n, M + 2);
-    const int ct = cta_size_fixed(n, nt, true);
-    if (M == 2) leafres_m<2>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<2>::den, out, ct, sm, s);
-    if (M == 4) leafres_m<4>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<4>::den, out, ct, sm, s);
-    if (M == 6) leafres_m<6>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<6>::den, out, ct, sm, s);
-}
 
 template <typename T>
 void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s) {
     if (lk.nb == 0) return;
-    set_attrs<T>();
+    attrs_halo_dump<T>();
     const size_t sm = fused_smem<T>(n, M + 2);
     if (M == 2) k_halo_dump<T, 4><<<lk.nb, 256, sm, s>>>(U, Uc, lk, n);
     if (M == 4) k_halo_dump<T, 6><<<lk.nb, 256, sm, s>>>(U, Uc, lk, n);
     if (M == 6) k_halo_dump<T, 8><<<lk.nb, 256, sm, s>>>(U, Uc, lk, n);
 }
-
-template void launch_smooth_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView, int,
-                                          int, double, int, cudaStream_t);
-template void launch_smooth_fused<float>(float*, const float*, const float*, const float*, LevelView, LevelView, int, int,
-                                         double, int, cudaStream_t);
-template void launch_residual_fused<double>(double*, const double*, const double*, const double*, LevelView, LevelView,
-                                            int, int, double, int, cudaStream_t);
-template void launch_residual_fused<float>(float*, const float*, const float*, const float*, LevelView, LevelView, int,
-                                           int, double, int, cudaStream_t);
-template void launch_fas_fused<double>(double*, double*, const double*, const double*, LevelView, LevelView, int, int,
-                                       double, int, cudaStream_t);
-template void launch_fas_fused<float>(float*, float*, const float*, const float*, LevelView, LevelView, int, int, double,
-                                      int, cudaStream_t);
-template void launch_halo_dump<double>(double*, const double*, LevelView, LevelView, int, int, cudaStream_t);
-template void launch_halo_dump<float>(float*, const float*, LevelView, LevelView, int, int, cudaStream_t);
 
 }  // namespace mrp

@@ -269,7 +269,7 @@ template <typename T>
 void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc, int n, cudaStream_t s);
 template <typename T>
 void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
-// stencil kernels with the ghost layer built in shared memory (kernels_fused.cu);
+// stencil kernels with the ghost layer built in shared memory (kernels_fused.cuh, fused_*.cu);
 // fused_smem_bytes: their dynamic shared memory for block size n, order M and
 // element size el (bytes), without a staged right-hand side
 size_t fused_smem_bytes(int n, int M, int el);

@@ -21,7 +21,7 @@ import pytest
 pytestmark = pytest.mark.filterwarnings("ignore")
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2512_08555_gb300", "csrc",
-                   "kernels_fused.cu")
+                   "kernels_fused.cuh")
 
 
 def _table(name):
