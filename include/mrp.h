@@ -82,7 +82,10 @@ typedef struct {
                                     MRP_MIXED: FP64 outer refinement (Green's function, outer
                                     residual, level-0 convolution of the accumulated source,
                                     correction accumulation) around FP32 V-cycles; tol then
-                                    bounds the relative residual of the composite system */
+                                    bounds the relative residual of the composite system.
+                                    The first outer residual (u = 0, which only feeds the
+                                    first FP32 correction) convolves level 0 in FP32; a
+                                    nonzero one is always followed by a refinement step */
     double mixed_target;         /* reserved */
     int64_t spin_budget;         /* reserved */
     int32_t inner_cycles;        /* MRP_MIXED: FP32 V-cycles per refinement step (0 = 4) */
