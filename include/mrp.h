@@ -50,9 +50,10 @@ enum {
     MRP_ERR_CUDA = 3,            /* a CUDA runtime call failed */
     MRP_ERR_OOM = 4,             /* device allocation failed */
     MRP_ERR_NOT_CONVERGED = 5,   /* max_cycles reached before the tolerance */
-    MRP_ERR_TIMEOUT = 6,         /* a bounded device wait ran out */
-    MRP_ERR_NUMERICAL = 7,       /* NaN or Inf in the residual norm */
-    MRP_ERR_NO_FORWARD = 8,      /* adjoint requested before a forward solve */
+    MRP_ERR_TIMEOUT = 6,         /* a bounded device wait ran out (reserved: no kernel of this
+                                    library waits on a device flag; waits are stream order only) */
+    MRP_ERR_NUMERICAL = 7,       /* NaN or Inf in the stop-rule norm */
+    /* 8 is not used */
     MRP_ERR_UNSUPPORTED = 9,     /* option combination not built */
     MRP_ERR_TOO_LARGE = 10       /* problem exceeds a fixed-size scratch array */
 };
@@ -75,7 +76,13 @@ typedef struct {
     int32_t order;               /* M = 2, 4 or 6 */
     double tol;                  /* stop when the rule below falls under tol */
     int32_t stop_rule;           /* MRP_STOP_RESIDUAL: max|f* - L u| / max|f*| over leaf nodes
-                                    MRP_STOP_CAUCHY:   max|u_n - u_{n+1}| / max|u_{n+1}| (Sec. 3.4) */
+                                    (Sec. 3.1).
+                                    MRP_STOP_CAUCHY: max|u^n - u^{n+1}| / max|u^{n+1}| over leaf
+                                    nodes between successive iterates (Sec. 3, the criterion for
+                                    problems whose residual stalls): u^0 = 0; an iterate is the
+                                    state after a V-cycle (MRP_FP64) or after a refinement step
+                                    (MRP_MIXED); a zero iterate divides by 1.  Keeps one more FP64
+                                    copy of the leaf values (8 bytes per leaf node). */
     int32_t max_cycles;          /* >= 1 */
     int32_t nu1, nu2;            /* pre- and post-smoothing sweeps, >= 0 */
     int32_t precision;           /* MRP_FP64: every stage in FP64.
@@ -85,9 +92,8 @@ typedef struct {
                                     bounds the relative residual of the composite system.
                                     The first outer residual (u = 0, which only feeds the
                                     first FP32 correction) convolves level 0 in FP32; a
-                                    nonzero one is always followed by a refinement step */
-    double mixed_target;         /* reserved */
-    int64_t spin_budget;         /* reserved */
+                                    nonzero one is always followed by a refinement step
+                                    (stop rule RESIDUAL) */
     int32_t inner_cycles;        /* MRP_MIXED: FP32 V-cycles per refinement step (0 = 4) */
     int32_t max_outer;           /* MRP_MIXED: refinement steps at most (0 = 12) */
 } mrp_options;
@@ -95,8 +101,10 @@ typedef struct {
 typedef struct {
     int32_t cycles;              /* V-cycles run */
     int32_t ir_steps;            /* outer refinement steps (0 for MRP_FP64) */
-    double residual;             /* final relative residual (stop rule RESIDUAL) */
-    double cauchy;               /* final relative increment (stop rule CAUCHY) */
+    double residual;             /* final relative residual (stop rule RESIDUAL; MRP_MIXED also
+                                    under CAUCHY, where the outer residual is computed anyway;
+                                    0 when not computed) */
+    double cauchy;               /* final relative increment (stop rule CAUCHY, else 0) */
     double fstar_max;            /* max |f*| over leaf nodes */
     int64_t leaf_nodes;          /* unknowns of the composite grid */
     int64_t total_nodes;         /* nodes over all levels */
@@ -105,12 +113,17 @@ typedef struct {
 
 typedef struct mrp_handle mrp_handle;
 
-/* Build a solver for n_forests forests (only n_forests == 1 is built).
- * Validates the forest, builds per-level block tables and the ghost plan,
- * allocates every device workspace, tabulates the lattice Green's function
- * of the order-M operator in FP64 on the device (Sec. 2.2, 3.3) and its
- * spectrum on the padded level-0 lattice.  Uses the current CUDA device.
- * On failure *out is NULL and nothing is leaked. */
+/* Build a solver for n_forests independent forests, each with ncomp
+ * right-hand sides (a batch: every (forest, component) pair is one problem,
+ * and one call solves them all; the caller layout of f and u is then
+ * [forest][component][leaf][z][y][x]).  Forests may differ in every field;
+ * those that share a block size n share pooled per-level block arrays, one
+ * group per block size.  Validates each forest, builds per-level block
+ * tables and the ghost plan, allocates every device workspace, tabulates the
+ * lattice Green's function of the order-M operator in FP64 on the device
+ * (Sec. 2.2, 3.3) and each problem's spectrum on its padded level-0 lattice.
+ * Uses the current CUDA device.  On failure *out is NULL and nothing is
+ * leaked. */
 int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, const mrp_options* opt);
 
 /* Solve nabla^2 u = f from u = 0.  f, u: device pointers, layout above.
@@ -134,6 +147,18 @@ int mrp_solve(mrp_handle* h, const double* f, double* u, void* stream, mrp_stats
  * graph ran). */
 int mrp_solve_graph(mrp_handle* h, const double* f, double* u, void* stream, mrp_stats* st);
 
+/* The mrp_solve_graph solve end to end from host memory: copies f_host to a
+ * device buffer the handle owns, launches the solve graph, copies the result
+ * into u_host, all ordered on stream, and returns once u_host is written.
+ * f_host, u_host: host pointers in the layout above (pinned memory, from
+ * cudaHostAlloc or cudaHostRegister, lets the copies run asynchronously at
+ * full bandwidth; pageable memory also works).  The caller keeps ownership.
+ * The first call allocates the two device buffers (8 bytes per element of f
+ * each) and builds the graph; later calls allocate nothing.  Same status and
+ * statistics as mrp_solve_graph; u_host is written also under
+ * MRP_ERR_NOT_CONVERGED and MRP_ERR_NUMERICAL. */
+int mrp_solve_host(mrp_handle* h, const double* f_host, double* u_host, void* stream, mrp_stats* st);
+
 /* Gradient of the converged solve: fbar = S^T w, where u = S f is the
  * composite solution mrp_solve converges to (the map is linear).  S
  * factors as f* = B f (Sec. 3.2 with f ghosts), 0 = c(f*) - K x (the
@@ -148,11 +173,15 @@ int mrp_solve_graph(mrp_handle* h, const double* f, double* u, void* stream, mrp
  * scatters); it stops when max|E_x^T w - K^T lambda| / max|E_x^T w| < tol or
  * after max_cycles transposed cycles (MRP_ERR_NOT_CONVERGED, fbar still
  * written).  w, fbar: device pointers in the leaf layout of f and u.  Needs
- * no earlier mrp_solve (no forward state enters).  The first call allocates
- * the adjoint workspace (about 5 fields per level plus 6 vectors of
- * total_nodes doubles); later calls allocate nothing.  Both precision
- * options run this in FP64.  st->cycles = st->ir_steps = transposed cycles,
- * st->residual = the final relative residual above. */
+ * no earlier mrp_solve (no forward state enters: every factor is linear and
+ * independent of the forward iterates).  The first call allocates the
+ * adjoint workspace (about 5 fields per level plus 6 vectors of total_nodes
+ * doubles); later calls allocate nothing.  The refinement residual
+ * E_x^T w - K^T lambda and the accumulation of lambda are FP64 on both
+ * precision options; the transposed cycles M^T run in FP64 on an MRP_FP64
+ * handle and in FP32 on an MRP_MIXED one.  The stop rule is always the
+ * residual above (stop_rule is ignored).  st->cycles = st->ir_steps =
+ * transposed cycles, st->residual = the final relative residual above. */
 int mrp_solve_adjoint(mrp_handle* h, const double* w, double* fbar, void* stream, mrp_stats* st);
 
 /* Release every resource of h (NULL is allowed). */

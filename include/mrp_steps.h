@@ -90,7 +90,10 @@ int mrp_fft_shape(mrp_handle* h, int32_t* P);
  * capture.  All calls share the array and it keeps the last call's
  * contents; every entry a call reads was written earlier in the same call,
  * so nothing needs clearing.  Calls whose GPU work overlaps (other streams,
- * other threads, other handles) race on the array: serialise them. */
+ * other threads, other handles) race on the array: serialise them.
+ * Returns MRP_ERR_CUDA if a launch error is pending after the launches; the
+ * error is left pending (not cleared), so the caller still sees an error
+ * its own earlier work may have left. */
 int mrp_coarse_solve_noalloc(mrp_handle* h, const double* f0, double* u0, void* stream);
 
 /* The factors of mrp_solve_adjoint one at a time (for parity checks).

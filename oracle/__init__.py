@@ -22,5 +22,20 @@ composite     Independent route to the converged composite solution (GMRES).
 closed_forms  Analytic free-space potentials used as pins.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_*.py``; none is "parity unpinned".
+``tests/test_oracle_*.py``; none is "parity unpinned".  The pins per module:
+
+stencils      polynomial exactness, h^M truncation order, transfer weights;
+lgf           Watson's constant (M = 2), L G = delta, symmetries, far field,
+              direct summation, the Gaussian erf potential at order M;
+forest        rejection of each violated constraint;
+multigrid     single-level solve = brute-force direct sum; V-cycle limit =
+              GMRES composite solution; O(h^M) E_inf order against the
+              manufactured u_unb product (M = 2, 4, 6) and against the C4 bump's
+              closed-form potential (M = 4, 6); stall with a non-LGF kernel;
+              the Cauchy stop rule's limit = the GMRES composite solution;
+composite     zero residual at the V-cycle fixed point;
+closed_forms  Gaussian: order-M convergence of the discrete solution; bump:
+              Gauss's-law quadrature and order-M convergence; u_unb: its
+              Laplacian by finite differences;
+adjoint       dot-product identity, finite differences, GMRES on the transpose.
 """

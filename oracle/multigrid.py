@@ -369,17 +369,31 @@ class OracleSolver:
         n = self.n
         return np.stack([self.U[l][b, 1:1 + n, 1:1 + n, 1:1 + n] for l, b in self.fo.leaf_slot])
 
-    def solve(self, f_leaf, tol=1e-10, max_cycles=30, history=None):
-        """Cycles from u = 0 until max|f* - L u| / max|f*| < tol (Sec. 3.1, stopping on the residual)."""
+    def solve(self, f_leaf, tol=1e-10, max_cycles=30, history=None, stop="residual"):
+        """Cycles from u = 0 until the stop rule falls under tol.
+
+        stop="residual": max|f* - L u| / max|f*| over leaf nodes (Sec. 3.1).
+        stop="cauchy": the increment of the iterates, max|u^n - u^{n+1}| /
+        max|u^{n+1}| over leaf nodes (Sec. 3, the criterion the paper uses
+        for problems whose residual does not reach zero); u^0 = 0, and a
+        zero iterate divides by 1.
+        """
         for A in self.U:
             A[...] = 0.0
         self.cycles_done = 0
         self.prepare_rhs(f_leaf)
         scale = self.fstar_max if self.fstar_max > 0 else 1.0
         rel = np.inf
+        prev = self.leaf_u()
         for _ in range(max_cycles):
             self.vcycle()
-            rel = self.leaf_residual_max() / scale
+            if stop == "cauchy":
+                cur = self.leaf_u()
+                top = float(np.abs(cur).max())
+                rel = float(np.abs(prev - cur).max()) / (top if top > 0 else 1.0)
+                prev = cur
+            else:
+                rel = self.leaf_residual_max() / scale
             if history is not None:
                 history.append(rel)
             if rel < tol:

@@ -22,7 +22,9 @@
 namespace mrp {
 
 // Loop control of one group (single thread).  res / fstar: per-problem
-// max-norm bit patterns (slots 1 and 0); ctr: cycles, refinement steps, status.
+// max-norm bit patterns of the stop rule's numerator and denominator (slots
+// 1 and 0 for the residual rule, 2 and 3 for the Cauchy rule); ctr: cycles,
+// refinement steps, status.
 __global__ void k_loop_check(const unsigned long long* __restrict__ res, const unsigned long long* __restrict__ fstar,
                              int np, double tol, int* __restrict__ ctr, double* __restrict__ rel_out, int mixed, int inner,
                              int max_cycles, int max_ir, int count_step, int need_step,
@@ -102,10 +104,14 @@ static int build_group(Handle& h, cudaGraph_t G, cudaStream_t cs, const double* 
     GK(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     cudaMemsetAsync(h.loop_ctr, 0, sizeof(int) * 4, cs);
     solve_begin(h, f, cs);
+    const bool cauchy = h.stop_rule == MRP_STOP_CAUCHY;
+    const unsigned long long* num = h.slot(cauchy ? 2 : 1);
+    const unsigned long long* den = h.slot(cauchy ? 3 : 0);
     if (h.mixed) {
         outer_residual_launch(h, cs, true);
-        k_loop_check<<<1, 32, 0, cs>>>(h.slot(1), h.slot(0), np, h.tol, h.loop_ctr, h.loop_rel, 1, h.inner_cycles,
-                                       h.max_cycles, h.max_ir, 0, h.L >= 1 ? 1 : 0, hc);
+        if (cauchy) cauchy_launch(h, cs);
+        k_loop_check<<<1, 32, 0, cs>>>(num, den, np, h.tol, h.loop_ctr, h.loop_rel, 1, h.inner_cycles,
+                                       h.max_cycles, h.max_ir, 0, (h.L >= 1 && !cauchy) ? 1 : 0, hc);
     }
     std::vector<cudaGraphNode_t> deps;
     int rc = tail_of(cs, deps);
@@ -127,11 +133,13 @@ static int build_group(Handle& h, cudaGraph_t G, cudaStream_t cs, const double* 
     if (h.mixed) {
         correction_launch(h, cs);
         outer_residual_launch(h, cs);
+        if (cauchy) cauchy_launch(h, cs);
     } else {
         vcycle<double>(h, cs);
-        leaf_residual_launch(h, cs);
+        if (cauchy) cauchy_launch(h, cs);
+        else leaf_residual_launch(h, cs);
     }
-    k_loop_check<<<1, 32, 0, cs>>>(h.slot(1), h.slot(0), np, h.tol, h.loop_ctr, h.loop_rel, h.mixed ? 1 : 0,
+    k_loop_check<<<1, 32, 0, cs>>>(num, den, np, h.tol, h.loop_ctr, h.loop_rel, h.mixed ? 1 : 0,
                                    h.inner_cycles, h.max_cycles, h.max_ir, 1, 0, hc);
     restore_buffers(h, p0, cs);
     if (cudaStreamEndCapture(cs, &dummy) != cudaSuccess) return MRP_ERR_CUDA;
@@ -175,6 +183,10 @@ void graph_release(mrp_handle* H) {
     H->gexec = nullptr;
     H->graph = nullptr;
     H->cap = nullptr;
+    cudaFree(H->host_f);
+    cudaFree(H->host_u);
+    H->host_f = nullptr;
+    H->host_u = nullptr;
     for (auto& g : H->g) {
         cudaFree(g->loop_ctr);
         cudaFree(g->loop_rel);
@@ -219,7 +231,17 @@ extern "C" int mrp_solve_graph(mrp_handle* H, const double* f, double* u, void* 
         if (st) {
             st->cycles = std::max(st->cycles, ctr[0]);
             st->ir_steps = std::max(st->ir_steps, ctr[1]);
-            st->residual = std::max(st->residual, worst);
+            if (h.stop_rule == MRP_STOP_CAUCHY) {
+                st->cauchy = std::max(st->cauchy, worst);
+                if (h.mixed) {       // the last outer residual, relative to max |f*|
+                    std::vector<double> r(np);
+                    if (read_max(h, s, r.data(), 1)) return MRP_ERR_CUDA;
+                    for (int p = 0; p < np; ++p)
+                        st->residual = std::max(st->residual, r[p] / (h.fstar[p] > 0.0 ? h.fstar[p] : 1.0));
+                }
+            } else {
+                st->residual = std::max(st->residual, worst);
+            }
             st->fstar_max = std::max(st->fstar_max, h.fstar_max);
             st->leaf_nodes += h.leaf_nodes;
             st->total_nodes += h.total_nodes;
@@ -228,4 +250,25 @@ extern "C" int mrp_solve_graph(mrp_handle* H, const double* f, double* u, void* 
     }
     if (status) return status;
     return converged ? MRP_OK : MRP_ERR_NOT_CONVERGED;
+}
+
+extern "C" int mrp_solve_host(mrp_handle* H, const double* f_host, double* u_host, void* stream, mrp_stats* st) {
+    if (!H || !f_host || !u_host) return MRP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * (size_t)H->elems;
+    if (!H->host_f) {
+        if (cudaMalloc(&H->host_f, bytes) != cudaSuccess) { cudaGetLastError(); return MRP_ERR_OOM; }
+        if (cudaMalloc(&H->host_u, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(H->host_f);
+            H->host_f = nullptr;
+            return MRP_ERR_OOM;
+        }
+    }
+    if (cudaMemcpyAsync(H->host_f, f_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return MRP_ERR_CUDA;
+    const int rc = mrp_solve_graph(H, H->host_f, H->host_u, stream, st);
+    if (rc != MRP_OK && rc != MRP_ERR_NOT_CONVERGED && rc != MRP_ERR_NUMERICAL) return rc;
+    if (cudaMemcpyAsync(u_host, H->host_u, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MRP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MRP_ERR_CUDA;
+    return rc;
 }

@@ -182,13 +182,12 @@ __global__ void k_smooth_T(T* __restrict__ U, T* __restrict__ F, int n, T h2den)
 template <typename T>
 void launch_smooth_T(T* U, T* F, int nb, int n, int M, double h2, cudaStream_t s) {
     if (nb == 0) return;
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr[MAX_DEVICES];
+    once_per_device(attr, [] {
         cudaFuncSetAttribute(k_smooth_T<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
         cudaFuncSetAttribute(k_smooth_T<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
         cudaFuncSetAttribute(k_smooth_T<6, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        attr = true;
-    }
+    });
     const size_t sm = sizeof(T) * (n + 2) * (n + 2) * (n + 2);
     if (M == 2) k_smooth_T<2, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<2>::den));
     if (M == 4) k_smooth_T<4, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<4>::den));

@@ -1098,11 +1098,10 @@ void launch_ghost_T_fused(T* A, T* Ac, LevelView lk, LevelView lc, int n, int M,
     if (lk.nb == 0) return;
     const int I = M + 2, PL = n / 2 + I;
     const size_t sm = sizeof(T) * ((size_t)pool_size(n, I) + (size_t)PL * PL * PL);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr[MAX_DEVICES];
+    once_per_device(attr, [] {
         allow(k_ghost_T_fused<T, 4>); allow(k_ghost_T_fused<T, 6>); allow(k_ghost_T_fused<T, 8>);
-        attr = true;
-    }
+    });
     if (M == 2) k_ghost_T_fused<T, 4><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
     if (M == 4) k_ghost_T_fused<T, 6><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
     if (M == 6) k_ghost_T_fused<T, 8><<<lk.nb, 256, sm, s>>>(A, Ac, lk, lc, n);
@@ -1126,49 +1125,49 @@ inline int cta_size_fixed(int n, int nt, bool fixed_items) {
 // (constant strides and offsets) and any block size at run time.
 constexpr int NC_FIXED = 16;
 
-// Per-family shared-memory attributes, set once per process (each family's
+// Per-family shared-memory attributes, set once per device (each family's
 // instantiations live in one translation unit).
 template <typename T>
 static void attrs_smooth() {
-    static bool done = false;
-    if (done) return;
-    allow(k_smooth_fused<2, T, 4, NC_FIXED>); allow(k_smooth_fused<2, T, 4, 0>);
-    allow(k_smooth_fused<4, T, 6, NC_FIXED>); allow(k_smooth_fused<4, T, 6, 0>);
-    allow(k_smooth_fused<6, T, 8, NC_FIXED>); allow(k_smooth_fused<6, T, 8, 0>);
-    done = true;
+    static std::once_flag done[MAX_DEVICES];
+    once_per_device(done, [] {
+        allow(k_smooth_fused<2, T, 4, NC_FIXED>); allow(k_smooth_fused<2, T, 4, 0>);
+        allow(k_smooth_fused<4, T, 6, NC_FIXED>); allow(k_smooth_fused<4, T, 6, 0>);
+        allow(k_smooth_fused<6, T, 8, NC_FIXED>); allow(k_smooth_fused<6, T, 8, 0>);
+    });
 }
 template <typename T>
 static void attrs_residual() {
-    static bool done = false;
-    if (done) return;
-    allow(k_residual_fused<2, T, 4, NC_FIXED>); allow(k_residual_fused<2, T, 4, 0>);
-    allow(k_residual_fused<4, T, 6, NC_FIXED>); allow(k_residual_fused<4, T, 6, 0>);
-    allow(k_residual_fused<6, T, 8, NC_FIXED>); allow(k_residual_fused<6, T, 8, 0>);
-    done = true;
+    static std::once_flag done[MAX_DEVICES];
+    once_per_device(done, [] {
+        allow(k_residual_fused<2, T, 4, NC_FIXED>); allow(k_residual_fused<2, T, 4, 0>);
+        allow(k_residual_fused<4, T, 6, NC_FIXED>); allow(k_residual_fused<4, T, 6, 0>);
+        allow(k_residual_fused<6, T, 8, NC_FIXED>); allow(k_residual_fused<6, T, 8, 0>);
+    });
 }
 template <typename T>
 static void attrs_fas() {
-    static bool done = false;
-    if (done) return;
-    allow(k_fas_fused<2, T, 4, NC_FIXED>); allow(k_fas_fused<2, T, 4, 0>);
-    allow(k_fas_fused<4, T, 6, NC_FIXED>); allow(k_fas_fused<4, T, 6, 0>);
-    allow(k_fas_fused<6, T, 8, NC_FIXED>); allow(k_fas_fused<6, T, 8, 0>);
-    done = true;
+    static std::once_flag done[MAX_DEVICES];
+    once_per_device(done, [] {
+        allow(k_fas_fused<2, T, 4, NC_FIXED>); allow(k_fas_fused<2, T, 4, 0>);
+        allow(k_fas_fused<4, T, 6, NC_FIXED>); allow(k_fas_fused<4, T, 6, 0>);
+        allow(k_fas_fused<6, T, 8, NC_FIXED>); allow(k_fas_fused<6, T, 8, 0>);
+    });
 }
 inline void attrs_leafres() {
-    static bool done = false;
-    if (done) return;
-    allow(k_leafres_fused<2, 4, NC_FIXED>); allow(k_leafres_fused<2, 4, 0>);
-    allow(k_leafres_fused<4, 6, NC_FIXED>); allow(k_leafres_fused<4, 6, 0>);
-    allow(k_leafres_fused<6, 8, NC_FIXED>); allow(k_leafres_fused<6, 8, 0>);
-    done = true;
+    static std::once_flag done[MAX_DEVICES];
+    once_per_device(done, [] {
+        allow(k_leafres_fused<2, 4, NC_FIXED>); allow(k_leafres_fused<2, 4, 0>);
+        allow(k_leafres_fused<4, 6, NC_FIXED>); allow(k_leafres_fused<4, 6, 0>);
+        allow(k_leafres_fused<6, 8, NC_FIXED>); allow(k_leafres_fused<6, 8, 0>);
+    });
 }
 template <typename T>
 static void attrs_halo_dump() {
-    static bool done = false;
-    if (done) return;
-    allow(k_halo_dump<T, 4>); allow(k_halo_dump<T, 6>); allow(k_halo_dump<T, 8>);
-    done = true;
+    static std::once_flag done[MAX_DEVICES];
+    once_per_device(done, [] {
+        allow(k_halo_dump<T, 4>); allow(k_halo_dump<T, 6>); allow(k_halo_dump<T, 8>);
+    });
 }
 
 template <int M, typename T>
@@ -1209,12 +1208,10 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
     // The block's right-hand side goes to shared memory where it fits: in its
     // own area when the launch fits in one wave at the CTAs per SM that this
     // leaves, else over the interpolation scratch.
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
-    }
+    int nsm = 1, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        nsm < 1)
+        nsm = 1;
     int fmode = 0;
     {
         if (fused_smem<T>(n, M + 2, 1) <= (size_t)MAX_DYN_SMEM) fmode = 1;

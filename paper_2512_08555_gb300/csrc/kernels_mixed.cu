@@ -1,4 +1,5 @@
-// Kernels of the FP64 iterative-refinement loop around FP32 V-cycles.
+// Kernels of the FP64 iterative-refinement loop around FP32 V-cycles, and of
+// the Cauchy stop rule.
 //
 // The FP64 state is u at every node of levels >= 1 and the level-0 source f0
 // (f* on level-0 leaves, the unknown source s on level-0 nodes covered by
@@ -7,6 +8,8 @@
 // equations f* - L_k u of levels >= 1, and c0 = u0(X) - u1(2X) on covered
 // level-0 nodes (the injection the converged multigrid state satisfies).
 #include "mrp_internal.h"
+
+#include <algorithm>
 
 namespace mrp {
 
@@ -113,6 +116,51 @@ __global__ void k_accumulate_f(double* __restrict__ F64, const float* __restrict
 void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int nblocks, int n, cudaStream_t s) {
     if (nblocks == 0) return;
     k_accumulate_f<<<nblocks, 256, 0, s>>>(F64, F32, blocks, n);
+}
+
+// U64 = U32 on every node of every block's (n+2)^3 box, ghost layer and (on
+// level 0) the exterior ring included.
+__global__ void k_cast_box(double* __restrict__ U64, const float* __restrict__ U32, size_t count) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        U64[i] = (double)U32[i];
+}
+
+void launch_cast_box(double* U64, const float* U32, int nb, int n, cudaStream_t s) {
+    const size_t S = n + 2, count = (size_t)nb * S * S * S;
+    if (count == 0) return;
+    const int grid = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
+    k_cast_box<<<grid, 256, 0, s>>>(U64, U32, count);
+}
+
+// Cauchy stop rule (Sec. 3): over the interiors of the given leaf blocks,
+// max |u - u_prev| into num[prob] and max |u| into den[prob]; then u_prev = u.
+__global__ void k_cauchy(double* __restrict__ Uprev, const double* __restrict__ U, const int* __restrict__ blocks, int n,
+                         unsigned long long* num, unsigned long long* den, const int* __restrict__ prob) {
+    const int b = blocks[blockIdx.x];
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
+    double md = 0.0, mu = 0.0;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {       // one thread per (x, y) column
+        const int y = c / n, x = c - y * n;
+        const size_t o = (size_t)b * S3 + (size_t)((y + 1) * S + x + 1);
+        for (int z = 0; z < n; ++z) {
+            const double u = U[o + (size_t)(z + 1) * S2];
+            const size_t q = (size_t)b * n3 + (size_t)z * n * n + c;
+            const double d = fabs(u - Uprev[q]);
+            Uprev[q] = u;
+            md = (d != d) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(md, d);
+            mu = (u != u) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(mu, fabs(u));
+        }
+    }
+    const int p = prob ? prob[b] : 0;
+    block_max_atomic64(md, num + p);
+    __syncthreads();                 // the reduction's shared scratch is reused
+    block_max_atomic64(mu, den + p);
+}
+
+void launch_cauchy(double* Uprev, const double* U, const int* leaf_blocks, int nleaf, int n, unsigned long long* num,
+                   unsigned long long* den, const int* prob, cudaStream_t s) {
+    if (nleaf == 0) return;
+    k_cauchy<<<nleaf, 256, 0, s>>>(Uprev, U, leaf_blocks, n, num, den, prob);
 }
 
 }  // namespace mrp

@@ -325,13 +325,12 @@ void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk,
         const int I = M + 2;
         const size_t sm = sizeof(double) * ((size_t)gsep_wa(n, g, I) + (size_t)gsep_wb(n, g, I));
         if (g % 2 == 0 && sm <= (size_t)MAX_DYN_SMEM) {
-            static bool attr_sep = false;
-            if (!attr_sep) {
+            static std::once_flag attr_sep[MAX_DEVICES];
+            once_per_device(attr_sep, [] {
                 cudaFuncSetAttribute(k_ghost_fill_sep<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
                 cudaFuncSetAttribute(k_ghost_fill_sep<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
                 cudaFuncSetAttribute(k_ghost_fill_sep<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-                attr_sep = true;
-            }
+            });
             const InterpW iw = interp_weights(M);
             if (I == 4) k_ghost_fill_sep<4><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
             if (I == 6) k_ghost_fill_sep<6><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
@@ -343,13 +342,12 @@ void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk,
     const InterpW iw = interp_weights(M);
     const int PL = n / 2 + g + iw.I + 1;
     const size_t sm = sizeof(double) * PL * PL * PL;
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr[MAX_DEVICES];
+    once_per_device(attr, [] {
         cudaFuncSetAttribute(k_ghost_fill<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
         cudaFuncSetAttribute(k_ghost_fill<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
         cudaFuncSetAttribute(k_ghost_fill<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        attr = true;
-    }
+    });
     if (iw.I == 4) k_ghost_fill<4><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
     if (iw.I == 6) k_ghost_fill<6><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
     if (iw.I == 8) k_ghost_fill<8><<<lk.nb, 256, sm, s>>>(A, g, Ac, gc, lk, lkm1, n, iw, zero_outside);
@@ -534,11 +532,10 @@ __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __re
 template <typename T>
 void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, LevelView lf, int n, const T* off, cudaStream_t s) {
     if (lf.nb == 0) return;
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr[MAX_DEVICES];
+    once_per_device(attr, [] {
         cudaFuncSetAttribute(k_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
-        attr = true;
-    }
+    });
     const size_t sm = sizeof(T) * (n + 1) * (n + 1) * (n + 1);
     k_restrict<T><<<lf.nb, 256, sm, s>>>(Uc, Fc, Uf, Rf, lf, n, off);
 }

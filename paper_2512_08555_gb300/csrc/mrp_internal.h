@@ -6,6 +6,7 @@
 #include <vector>
 #include <string>
 #include <memory>
+#include <mutex>
 
 #include "mrp.h"
 #include "mrp_steps.h"
@@ -38,6 +39,17 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 #endif
+
+// Runs fn once per device (the current one) for each distinct flags array,
+// thread-safe: kernel attributes such as the opt-in shared-memory size are
+// per device, and several host threads may create handles at once.
+constexpr int MAX_DEVICES = 64;
+template <typename Fn>
+inline void once_per_device(std::once_flag (&flags)[MAX_DEVICES], Fn&& fn) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) { fn(); return; }
+    std::call_once(flags[dev], fn);
+}
 
 // Codes stored in the neighbour table besides block indices.
 constexpr int NBR_MISSING = -1;   // no block of this level there: interpolate from level k-1
@@ -87,6 +99,7 @@ struct Level {
     uint8_t* is_leaf = nullptr;
     double *U = nullptr, *F = nullptr, *R = nullptr, *H = nullptr, *Fraw = nullptr;
     double* Ualt = nullptr;           // second u buffer: a sweep reads U and writes Ualt, then they swap
+    double* Uprev = nullptr;          // [nb][n^3] leaf values of the previous iterate (Cauchy stop rule only)
     float *U32 = nullptr, *F32 = nullptr, *R32 = nullptr, *H32 = nullptr;   // mixed precision inner cycles
     float* U32alt = nullptr;
     LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order, prob, rec}; }
@@ -242,6 +255,7 @@ int fft_plan(Handle& h);
 template <typename T> void vcycle(Handle& h, cudaStream_t s);
 void solve_begin(Handle& h, const double* f, cudaStream_t s);
 void leaf_residual_launch(Handle& h, cudaStream_t s);
+void cauchy_launch(Handle& h, cudaStream_t s);   // Cauchy stop rule into slots 2 (num) and 3 (den)
 // first: the residual at u = 0 (its level-0 solution convolved in FP32)
 void outer_residual_launch(Handle& h, cudaStream_t s, bool first = false);
 void correction_launch(Handle& h, cudaStream_t s);
@@ -337,6 +351,10 @@ void launch_c0(double* c0, float* off32, const double* U0, const double* U1, con
 void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int nleaf, int n, bool zero, cudaStream_t s);
 void launch_accumulate_u(double* U64, const float* U32, int nb, int n, cudaStream_t s);
 void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int nblocks, int n, cudaStream_t s);
+void launch_cast_box(double* U64, const float* U32, int nb, int n, cudaStream_t s);
+// Cauchy stop rule: max |u - u_prev| and max |u| over leaf interiors per problem; u_prev = u
+void launch_cauchy(double* Uprev, const double* U, const int* leaf_blocks, int nleaf, int n, unsigned long long* num,
+                   unsigned long long* den, const int* prob, cudaStream_t s);
 }  // namespace mrp
 
 // Opaque handle of the C ABI: one internal handle per block size; the
@@ -352,4 +370,7 @@ struct mrp_handle {
     cudaStream_t cap = nullptr;       // capture stream
     const double* gf = nullptr;
     double* gu = nullptr;
+    // device copies of f and u for mrp_solve_host, allocated at its first call
+    double* host_f = nullptr;
+    double* host_u = nullptr;
 };

@@ -50,5 +50,7 @@ extern "C" int mrp_coarse_solve_noalloc(mrp_handle* H, const double* f0, double*
     const int rc = noalloc_scratch(&spec);
     if (rc != MRP_OK) return rc;
     launch_coarse_solve_ext(h, spec, f0, u0, (cudaStream_t)stream);
-    return cudaGetLastError() == cudaSuccess ? MRP_OK : MRP_ERR_CUDA;
+    // peek, not get: an error left by the caller's own earlier work stays
+    // pending for the caller to see
+    return cudaPeekAtLastError() == cudaSuccess ? MRP_OK : MRP_ERR_CUDA;
 }

@@ -317,6 +317,7 @@ int upload_tables(Handle& h) {
         if ((rc = alloc_field(lv.R, lv.nb * n * n * n))) return rc;
         if ((rc = alloc_field(lv.H, lv.nb * n * n * n))) return rc;
         if ((rc = alloc_field(lv.Fraw, lv.nb * S4 * S4 * S4))) return rc;
+        if (h.stop_rule == MRP_STOP_CAUCHY && (rc = alloc_field(lv.Uprev, lv.nb * n * n * n))) return rc;
     }
     if ((rc = up(h.leaf_level, h.h_leaf_level))) return rc;
     if ((rc = up(h.leaf_block, h.h_leaf_block))) return rc;
@@ -336,7 +337,7 @@ static void release(Handle& h) {
         cudaFree(lv.rec);
         cudaFree(lv.U); cudaFree(lv.F); cudaFree(lv.R); cudaFree(lv.H); cudaFree(lv.Fraw);
         cudaFree(lv.U32); cudaFree(lv.F32); cudaFree(lv.R32); cudaFree(lv.H32);
-        cudaFree(lv.Ualt); cudaFree(lv.U32alt);
+        cudaFree(lv.Ualt); cudaFree(lv.U32alt); cudaFree(lv.Uprev);
     }
     h.lv.clear();
     for (Problem& p : h.pr) {
@@ -563,13 +564,20 @@ int read_max(Handle& h, cudaStream_t s, double* out, int slot) {
 // handle with several block sizes runs one such sequence per block size, in
 // lockstep, each on its own stream.
 struct SolveState {
-    std::vector<double> scale, rel;   // per problem: max |f*| (or 1) and the last relative residual
+    // per problem: max |f*| (or 1), the last value of the stop rule and the
+    // last relative residual (equal to rel under the residual rule)
+    std::vector<double> scale, rel, res;
     int cycles = 0, ir = 0;
     bool started = false, done = false;
     int rc = MRP_OK;
     double worst() const {
         double w = 0.0;
         for (double r : rel) w = std::max(w, r);
+        return w;
+    }
+    double worst_res() const {
+        double w = 0.0;
+        for (double r : res) w = std::max(w, r);
         return w;
     }
 };
@@ -660,6 +668,8 @@ void solve_begin(Handle& h, const double* f, cudaStream_t s) {
             launch_absmax(h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.slot(0), h.lv[k].prob, s);
     }
     for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U, 0, sizeof(double) * h.lv[k].nb * S * S * S, s);
+    if (h.stop_rule == MRP_STOP_CAUCHY)          // the iterate before the first cycle: u = 0
+        for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].Uprev, 0, sizeof(double) * h.lv[k].nb * n3(h), s);
 }
 
 static int solve_begin_read(Handle& h, cudaStream_t s, SolveState& st) {
@@ -668,6 +678,7 @@ static int solve_begin_read(Handle& h, cudaStream_t s, SolveState& st) {
     st = SolveState();
     st.scale.resize(h.nprob());
     st.rel.assign(h.nprob(), INFINITY);
+    st.res.assign(h.nprob(), 0.0);
     h.fstar_max = 0.0;
     for (int p = 0; p < h.nprob(); ++p) {
         st.scale[p] = h.fstar[p] > 0.0 ? h.fstar[p] : 1.0;
@@ -711,10 +722,10 @@ void outer_residual_launch(Handle& h, cudaStream_t s, bool first) {
             launch_cast_rhs(l0.F32, l0.F, l0.cov_blocks, l0.ncov, h.n, false, s);
         }
         coarse_solve<float>(h, s);
-        const size_t S = h.n + 2;
+        // the whole box, exterior ring included: later steps read the ring
+        // as the last level-0 solve's values
         PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 1);
-        cudaMemsetAsync(l0.U, 0, sizeof(double) * l0.nb * S * S * S, s);
-        launch_accumulate_u(l0.U, ucur<float>(h, 0), l0.nb, h.n, s);
+        launch_cast_box(l0.U, ucur<float>(h, 0), l0.nb, h.n, s);
     } else {
         coarse_solve<double>(h, s);
     }
@@ -749,11 +760,24 @@ void correction_launch(Handle& h, cudaStream_t s) {
     launch_accumulate_f(l0.F, l0.F32, l0.cov_blocks, l0.ncov, h.n, s);
 }
 
+// Cauchy stop rule (Sec. 3): per problem, max |u - u_prev| over the leaf
+// nodes of every level into slot 2 and max |u| into slot 3; u_prev = u.
+void cauchy_launch(Handle& h, cudaStream_t s) {
+    cudaMemsetAsync(h.slot(2), 0, sizeof(unsigned long long) * 2 * h.nprob(), s);
+    for (int k = 0; k <= h.L; ++k) {
+        PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
+        launch_cauchy(h.lv[k].Uprev, h.lv[k].U, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.slot(2), h.slot(3),
+                      h.lv[k].prob, s);
+    }
+}
+
 static void solve_step(Handle& h, cudaStream_t s, SolveState& st) {
+    const bool cauchy = h.stop_rule == MRP_STOP_CAUCHY;
     if (!h.mixed) {
         vcycle<double>(h, s);
         ++st.cycles;
-        leaf_residual_launch(h, s);
+        if (cauchy) cauchy_launch(h, s);
+        else leaf_residual_launch(h, s);
         return;
     }
     if (st.started) {
@@ -762,19 +786,31 @@ static void solve_step(Handle& h, cudaStream_t s, SolveState& st) {
         ++st.ir;
     }
     outer_residual_launch(h, s, !st.started);
+    if (cauchy) cauchy_launch(h, s);
     st.started = true;
 }
 
 static int solve_check(Handle& h, cudaStream_t s, SolveState& st) {
-    std::vector<double> r(h.nprob());
-    const int rc = read_max(h, s, r.data(), 1);
+    const int np = h.nprob();
+    const bool cauchy = h.stop_rule == MRP_STOP_CAUCHY;
+    std::vector<double> r(np), d(np), u(np);
+    int rc = MRP_OK;
+    if (!cauchy || h.mixed) rc = read_max(h, s, r.data(), 1);
+    if (!rc && cauchy) rc = read_max(h, s, d.data(), 2);
+    if (!rc && cauchy) rc = read_max(h, s, u.data(), 3);
     if (rc) { st.rc = rc; st.done = true; return rc; }
     bool all = true;
-    for (int p = 0; p < h.nprob(); ++p) {
-        st.rel[p] = r[p] / st.scale[p];
-        if (!std::isfinite(st.rel[p])) { st.rc = MRP_ERR_NUMERICAL; st.done = true; return MRP_OK; }
+    for (int p = 0; p < np; ++p) {
+        st.res[p] = (!cauchy || h.mixed) ? r[p] / st.scale[p] : 0.0;
+        st.rel[p] = cauchy ? d[p] / (u[p] > 0.0 ? u[p] : 1.0) : st.res[p];
+        if (!std::isfinite(st.rel[p]) || !std::isfinite(st.res[p])) {
+            st.rc = MRP_ERR_NUMERICAL;
+            st.done = true;
+            return MRP_OK;
+        }
         if (!(st.rel[p] < h.tol)) all = false;
-        if (h.mixed && h.L >= 1 && st.ir == 0 && st.rel[p] > 0.0) all = false;   // first residual: FP32 level 0
+        // first residual: FP32 level 0
+        if (!cauchy && h.mixed && h.L >= 1 && st.ir == 0 && st.rel[p] > 0.0) all = false;
     }
     if (all) st.done = true;
     else if (!h.mixed && st.cycles >= h.max_cycles) st.done = true;
@@ -804,7 +840,6 @@ const char* mrp_error_string(int status) {
         case MRP_ERR_NOT_CONVERGED: return "not converged within max_cycles";
         case MRP_ERR_TIMEOUT: return "device wait budget exhausted";
         case MRP_ERR_NUMERICAL: return "NaN or Inf in the residual";
-        case MRP_ERR_NO_FORWARD: return "adjoint needs a forward solve on this handle";
         case MRP_ERR_UNSUPPORTED: return "unsupported option";
         case MRP_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the no-allocation entry point";
         default: return "unknown status";
@@ -828,7 +863,6 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
     if (opt->stop_rule != MRP_STOP_RESIDUAL && opt->stop_rule != MRP_STOP_CAUCHY) return MRP_ERR_INVALID_ARG;
     if (opt->precision != MRP_FP64 && opt->precision != MRP_MIXED) return MRP_ERR_INVALID_ARG;
     if (opt->inner_cycles < 0 || opt->max_outer < 0) return MRP_ERR_INVALID_ARG;
-    if (opt->stop_rule == MRP_STOP_CAUCHY) return MRP_ERR_UNSUPPORTED;
     // problems (forest, component) in the caller's layout order, grouped by block size
     std::map<int, std::vector<ProblemDesc>> by_n;
     int64_t off = 0;
@@ -949,7 +983,8 @@ int mrp_solve(mrp_handle* H, const double* f, double* u, void* stream, mrp_stats
             const Handle& h = *H->g[i];
             st->cycles = std::max(st->cycles, ss[i].cycles);
             st->ir_steps = std::max(st->ir_steps, ss[i].ir);
-            st->residual = std::max(st->residual, ss[i].worst());
+            st->residual = std::max(st->residual, ss[i].worst_res());
+            if (h.stop_rule == MRP_STOP_CAUCHY) st->cauchy = std::max(st->cauchy, ss[i].worst());
             st->fstar_max = std::max(st->fstar_max, h.fstar_max);
             st->leaf_nodes += h.leaf_nodes;
             st->total_nodes += h.total_nodes;

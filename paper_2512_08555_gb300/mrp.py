@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmrp.so")
 MRP_OK = 0
 MRP_ERR_NOT_CONVERGED = 5
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid forest", 3: "CUDA error", 4: "out of memory",
-          5: "not converged", 6: "timeout", 7: "numerical", 8: "no forward", 9: "unsupported",
+          5: "not converged", 6: "timeout", 7: "numerical", 9: "unsupported",
           10: "too large for the fixed scratch"}
 FIELDS = {"U": 0, "F": 1, "R": 2, "UHAT": 3, "FRAW": 4}
 STEPS = {"prepare_rhs": 0, "ghost_u": 1, "smooth": 2, "residual": 3, "restrict": 4,
@@ -25,7 +25,8 @@ STEPS = {"prepare_rhs": 0, "ghost_u": 1, "smooth": 2, "residual": 3, "restrict":
 EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_error_string",
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
-            "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph"]
+            "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph",
+            "mrp_solve_host"]
 ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
@@ -45,8 +46,8 @@ class _Forest(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("order", C.c_int32), ("tol", C.c_double), ("stop_rule", C.c_int32), ("max_cycles", C.c_int32),
-                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("mixed_target", C.c_double),
-                ("spin_budget", C.c_int64), ("inner_cycles", C.c_int32), ("max_outer", C.c_int32)]
+                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("inner_cycles", C.c_int32),
+                ("max_outer", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -89,6 +90,7 @@ def load_library(path=LIB_PATH):
     lib.mrp_adjoint_len.argtypes = [P, C.POINTER(I64)]
     lib.mrp_adjoint_op.argtypes = [P, I32, P, P, P]
     lib.mrp_solve_graph.argtypes = [P, P, P, P, C.POINTER(Stats)]
+    lib.mrp_solve_host.argtypes = [P, P, P, P, C.POINTER(Stats)]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
     lib.mrp_error_string.restype = C.c_char_p
@@ -117,7 +119,7 @@ class Solver:
     """
 
     def __init__(self, forest, order=4, tol=1e-10, max_cycles=50, nu1=3, nu2=3, precision="fp64",
-                 inner_cycles=0, max_outer=0, ncomp=1):
+                 inner_cycles=0, max_outer=0, ncomp=1, stop="residual"):
         import torch  # noqa: F401  (CUDA context and memory come from torch)
         self.lib = load_library()
         forests = list(forest) if isinstance(forest, (list, tuple)) else [forest]
@@ -146,7 +148,8 @@ class Solver:
             fd.leaf_ijk = ijk.ctypes.data_as(C.POINTER(C.c_int32))
             fd.ncomp = int(c)
         op = _Options()
-        op.order, op.tol, op.stop_rule, op.max_cycles = int(order), float(tol), 0, int(max_cycles)
+        op.order, op.tol, op.max_cycles = int(order), float(tol), int(max_cycles)
+        op.stop_rule = {"residual": 0, "cauchy": 1}[stop]
         op.nu1, op.nu2 = int(nu1), int(nu2)
         op.precision = {"fp64": 0, "mixed": 1}[precision]
         op.inner_cycles, op.max_outer = int(inner_cycles), int(max_outer)
@@ -300,23 +303,22 @@ class Solver:
         return {p: {"ms": float(ms[i]), "launches": int(cnt[i]), "nodes": int(nodes[i])}
                 for i, p in enumerate(PHASES16) if cnt[i] > 0}
 
-    def solve_host(self, f_host, u_host=None, stream=None):
-        """End-to-end call from host memory: copy f in, solve, copy u out (all on ``stream``).
+    def solve_host(self, f_host, u_host=None, stream=None, allow_not_converged=False):
+        """End to end from host memory through ``mrp_solve_host``: f in, solve graph, u out.
 
-        ``f_host``/``u_host``: CPU float64 tensors (pinned for asynchronous copies).
+        ``f_host``/``u_host``: contiguous CPU float64 tensors in the caller
+        layout (pinned for asynchronous copies at full bandwidth).
         """
         import torch
-        s = stream if stream is not None else torch.cuda.current_stream()
-        if not hasattr(self, "_dev_f") or self._dev_f.numel() != f_host.numel():
-            self._dev_f = torch.empty(f_host.shape, dtype=torch.float64, device="cuda")
-            self._dev_u = torch.empty_like(self._dev_f)
+        if f_host.dtype != torch.float64 or f_host.is_cuda or not f_host.is_contiguous() or f_host.numel() != self.elems:
+            raise ValueError("f_host must be a contiguous CPU float64 tensor in the caller layout")
         if u_host is None:
             u_host = torch.empty(f_host.shape, dtype=torch.float64, pin_memory=True)
-        with torch.cuda.stream(s):
-            self._dev_f.copy_(f_host, non_blocking=True)
-            _, st = self.solve(self._dev_f, self._dev_u, stream=s)
-            u_host.copy_(self._dev_u, non_blocking=True)
-        s.synchronize()
+        st = Stats()
+        allow = (MRP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        rc = self.lib.mrp_solve_host(self.h, C.c_void_p(f_host.data_ptr()), C.c_void_p(u_host.data_ptr()),
+                                     _stream_ptr(stream), C.byref(st))
+        _check(rc, "mrp_solve_host", allow)
         return u_host, st
 
     def fft_shape(self):

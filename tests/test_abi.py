@@ -55,6 +55,27 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.mrp_destroy(None) == 0
     st = mrp.Stats()
     assert lib.mrp_solve(None, None, None, None, ctypes.byref(st)) == 1
+    assert lib.mrp_solve_graph(None, None, None, None, ctypes.byref(st)) == 1
+    assert lib.mrp_solve_host(None, None, None, None, ctypes.byref(st)) == 1
+    assert lib.mrp_solve_adjoint(None, None, None, None, ctypes.byref(st)) == 1
+
+
+def test_option_and_stats_structs_match_the_header():
+    """The binding's ctypes structs have the header's field order (parsed from include/mrp.h)."""
+    from paper_2512_08555_gb300 import mrp
+    txt = open(os.path.join(ROOT, "include", "mrp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    for name, cls in (("mrp_options", mrp._Options), ("mrp_stats", mrp.Stats), ("mrp_forest", mrp._Forest)):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", txt).group(1)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            names = decl.split(None, 1)[1] if not decl.startswith("const") else decl.split("*", 1)[1]
+            for nm in names.split(","):
+                fields.append(re.sub(r"[\s*]|\[.*\]", "", nm))
+        assert fields == [f for f, _ in cls._fields_], (name, fields)
 
 
 def _forest_struct(nb0, n, lev, ijk):

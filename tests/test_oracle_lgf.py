@@ -126,3 +126,13 @@ def test_manufactured_unbounded_solution(lgf_cache):
         return manufactured_unb(x, y, z)[1]
     e = [_uniform_error(6, n0, lgf_cache(6, n0 + 1), fu, ff) for n0 in (32, 64)]
     assert e[1] < 2e-4 and e[1] < e[0] / 20, e
+
+
+def test_manufactured_second_derivative_by_finite_differences():
+    """u_unb'' of the closed form equals a fourth-order central difference of u_unb (step 1e-3)."""
+    from oracle.closed_forms import u_unb, u_unb_dd
+    x = np.linspace(0.05, 0.95, 37)
+    d = 1e-3
+    fd = (-u_unb(x + 2 * d) + 16 * u_unb(x + d) - 30 * u_unb(x) + 16 * u_unb(x - d) - u_unb(x - 2 * d)) / (12 * d * d)
+    assert np.abs(fd - u_unb_dd(x)).max() < 1e-5 * np.abs(u_unb_dd(x)).max()
+    assert np.all(u_unb(np.array([-0.1, 0.0, 1.0, 1.3])) == 0.0)

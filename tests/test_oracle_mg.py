@@ -8,7 +8,7 @@ from oracle.multigrid import OracleSolver
 from oracle.composite import CompositeSystem
 from oracle.lgf import free_space_solve, direct_sum
 from oracle.stencils import rhs_stencil
-from oracle.closed_forms import manufactured_unb
+from oracle.closed_forms import manufactured_unb, bump_potential
 
 
 def _all(level, coords):
@@ -136,9 +136,12 @@ def test_incompatible_kernel_does_not_converge(lgf_cache):
     assert min(h2) < 1e-7
 
 
-@pytest.mark.parametrize("M,min_order", [(2, 1.8), (4, 3.3)])
+@pytest.mark.parametrize("M,min_order", [(2, 1.8), (4, 3.3), (6, 4.6)])
 def test_adaptive_convergence_order(lgf_cache, M, min_order):
-    """E_inf against the manufactured u_unb product decays like h^M under uniform refinement of a 2-level forest."""
+    """E_inf against the manufactured u_unb product decays like h^M under uniform refinement of a 2-level forest.
+
+    (M = 6 observes 4.9 at these sizes: u_unb's steep flanks keep n = 8 -> 16
+    short of the asymptotic range; the bump test below shows 6.)"""
     errs = []
     for n in (8, 16):
         desc, fo = _forest(4, n, 1, lo=0.0, L=1.0)
@@ -170,3 +173,70 @@ def test_uniform_solve_operator_is_symmetric(lgf_cache):
     w[2:-2, 2:-2, 2:-2] = rng.normal(size=(N - 4,) * 3)
     a, b = np.vdot(v, S(w)), np.vdot(S(v), w)
     assert abs(a - b) < 1e-13 * max(abs(a), 1.0)
+
+
+def test_bump_potential_matches_gauss_law_quadrature():
+    """The closed-form bump potential equals u(r) = -int_r^inf m(s)/s^2 ds, m(s) = int_0^s t^2 f(t) dt,
+    both integrals by adaptive quadrature (Gauss's law for nabla^2 u = f, u -> 0 at infinity)."""
+    from scipy.integrate import quad
+    R, A = 0.37, -1.7
+
+    def f(t):
+        return A * (1 - t * t / (R * R)) ** 5 if t < R else 0.0
+
+    def m(s):
+        return quad(lambda t: t * t * f(t), 0.0, min(s, R), epsabs=1e-15, epsrel=1e-13)[0]
+
+    def u(r):
+        inner = quad(lambda s: m(s) / (s * s), r, R, epsabs=1e-15, epsrel=1e-13)[0] if r < R else 0.0
+        return -(inner + m(R) / max(r, R))
+    c = (0.1, -0.2, 0.05)
+    for r in (0.0, 0.05, 0.2, R * 0.999, R, 0.6, 2.5):
+        got = float(bump_potential(np.array(c[0] + r), np.array(c[1]), np.array(c[2]), c, R, A))
+        ref = u(max(r, 1e-12))
+        assert abs(got - ref) < 1e-12 * abs(ref), (r, got, ref)
+
+
+@pytest.mark.parametrize("M,min_order", [(4, 3.8), (6, 5.7)])
+def test_bump_forest_converges_to_closed_form(lgf_cache, M, min_order):
+    """Sec. 4 error norm E_inf of the converged adaptive solve against the exact free-space potential of a
+    C4 bump (Gauss's law), on a two-level forest with resolution jumps at h0 = 1/16 and 1/32: the error
+    decays like h^M (observed 4.04 and 6.07), which pins the closed form, the stencils, the I = M + 2 ghost
+    interpolation and the LGF together (a dropped term or a wrong weight anywhere breaks the order)."""
+    c, R, A = (0.0, 0.0, 0.0), 0.3, 1.0
+
+    def src(x, y, z):
+        r2 = ((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / R ** 2
+        return A * np.where(r2 < 1, np.clip(1 - r2, 0, None) ** 5, 0.0)
+    errs = []
+    for n in (8, 16):
+        desc, fo = _forest(4, n, 1)
+        f = synth.sample_leaves(desc, src)
+        uref = synth.sample_leaves(desc, lambda x, y, z: bump_potential(x, y, z, c, R, A))
+        s = OracleSolver(fo, M, G=lgf_cache(M, 4 * n + 1))
+        u, rel = s.solve(f, tol=1e-12, max_cycles=40)
+        assert rel < 1e-12
+        errs.append(np.abs(u - uref).max() / np.abs(uref).max())
+    assert errs[1] < (3e-6 if M == 4 else 1e-7), errs
+    assert np.log2(errs[0] / errs[1]) > min_order, errs
+
+
+def test_cauchy_stop_reaches_composite_solution(lgf_cache):
+    """Sec. 3 Cauchy rule: stopping when max|u^n - u^(n+1)| / max|u^(n+1)| < 1e-14 leaves the iterate at the
+    composite solution that GMRES finds without multigrid (to 1e-12), and the rule's history is the increment
+    of the iterates: it falls with the residual's contraction and is 1 after the first cycle from u = 0."""
+    desc, fo = _forest(3, 8, 1)
+    f = synth.sample_leaves(desc, synth.c4_bumps(1, k=2, r_lo=0.1, r_hi=0.15, box=0.3))
+    G = lgf_cache(4, 25)
+    s = OracleSolver(fo, 4, G=G)
+    hist = []
+    u, rel = s.solve(f, tol=1e-14, max_cycles=40, history=hist, stop="cauchy")
+    assert rel < 1e-14 and hist[0] == 1.0
+    assert np.all(np.diff(np.log10(np.array(hist[:8]))) < -0.5), hist
+    cs = CompositeSystem(OracleSolver(fo, 4, G=G), f)
+    ug = cs.leaf_values(cs.solve(rtol=1e-14))
+    assert np.abs(u - ug).max() < 1e-12 * np.abs(ug).max()
+    # a zero source gives a zero iterate, whose increment is 0 after one cycle
+    z = OracleSolver(fo, 4, G=G)
+    uz, rz = z.solve(np.zeros_like(f), tol=1e-14, max_cycles=5, stop="cauchy")
+    assert z.cycles_done == 1 and rz == 0.0 and not np.any(uz)
