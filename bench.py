@@ -1,29 +1,37 @@
-"""Benchmark: free-space multigrid-FFT Poisson solve on the adaptive bump forest.
+"""Benchmark: free-space multigrid-FFT Poisson solve on the five-level adaptive bump forest.
 
-One step = one full solve (mrp_solve: RHS preparation, cycles to a relative
-residual of 1e-10, gather) of the three-level forest (Omega = [-1,1)^3,
-5^3 level-0 blocks of 16^3 nodes, 8 C4 bumps, 2.8M leaf nodes), order-4
-Mehrstellen.  value = leaf nodes / solve time of the chosen form (FP32
-V(3,3) cycles inside FP64 iterative refinement), inputs resident in HBM; the
-plain FP64 path is timed beside it and the chosen result's max error against
-it is reported.  e2e = the chosen form through the host-memory call (pinned
-H2D of f, solve, D2H of u inside the timed region).
+One step = one full solve, launched as one CUDA graph (mrp_solve_graph: RHS
+preparation, refinement steps until the relative residual of the composite
+system is below 1e-10, gather), of the five-level forest: Omega = [-1,1)^3,
+6^3 level-0 blocks of 16^3 nodes, levels 0..4, 8 C4 bumps (seed = rank),
+97.9M leaf nodes, order-4 Mehrstellen, V(3,3) cycles.  value = leaf nodes /
+solve time of the chosen form (FP32 V(3,3) cycles inside FP64 iterative
+refinement), inputs resident in HBM; the plain FP64 path is timed beside it
+and the chosen result's max error against it is reported.  e2e = the same
+solve through mrp_solve_host: f from pinned host memory, u back to it, both
+copies inside the timed region.
 
 Besides the headline, rank 0 reports (unless --no-extras):
-  adjoint     the gradient of the converged solve (mrp_solve_adjoint, FP64) on
-              the same forest, with the dot-product identity <w, S f> = <S^T w, f>;
-  five_level  the same generator at five levels (29.5M leaf nodes), chosen vs
-              plain FP64, with the smoother's roofline at sizes beyond L2;
-  batched     the vortex ring (3 components, 4 levels) plus 16 uneven scalar
-              problems (2..5 levels, blocks of 12^3..20^3): 195M leaf nodes
-              solved as one CUDA graph launch, chosen vs plain FP64.
+  three_level  the same generator at three levels on 5^3 level-0 blocks
+               (2.8M leaf nodes), chosen vs plain FP64;
+  adjoint      the gradient of the converged solve (mrp_solve_adjoint) on the
+               headline forest, FP32 and FP64 transposed cycles, with the
+               dot-product identity <w, S f> = <S^T w, f>;
+  batched      the vortex ring (3 components, 4 levels) plus 16 uneven scalar
+               problems (2..5 levels, blocks of 12^3..20^3): 195M leaf nodes
+               solved as one CUDA graph launch, chosen vs plain FP64;
+  fft_large    one level-0 convolution on a lattice far beyond L2;
+  peaks        the measured FP64 and FP32 FMA throughput of the device.
 
---impl reference times the CPU oracle (plain numpy FP64) on the same
-workload: preparation plus one V-cycle, extrapolated to the cycle count of
-the solve.  N > 1 ranks run independent replicas (seed = rank).
+The CPU baseline is the oracle (plain numpy FP64) as it stands: full solves
+to the same stop rule of small forests from the same generator, one
+independent solve per host core at once, plus one core alone.
+--impl reference times exactly that, each step one such round.  N > 1 ranks
+run independent replicas (seed = rank).
 """
 import argparse
 import json
+import multiprocessing as mp
 import os
 import subprocess
 import sys
@@ -39,30 +47,23 @@ METRIC = "cells/s per solve at stated max error vs FP64 oracle (chosen vs plain)
 ORDER = 4
 TOL = 1e-10
 MAX_CYCLES = 60
-# V(3,3) cycles the oracle needs on this workload to reach TOL (order 4, seed 0);
-# measured once with oracle.multigrid on the CPU, used to extrapolate the
-# reference arm's one-cycle sample to a full solve.
-ORACLE_CYCLES = {4: 11, 6: 12, 2: 17}
 STENCIL_POINTS = {2: 7, 4: 19, 6: 27}
-# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch of the FP32 smoother from one ncu capture:
-# the average over the 24 launches of the first two V-cycles on the headline
-# forest, and the first level-4 launch of the five-level forest (the ncu
-# summaries under profiles/ give the commands).  Valid while the kernel is unchanged.
-SMOOTH32_TRAFFIC = {"headline": 13277994, "five_level_level4": 396550656}
+# DRAM bytes (read + write) of one launch of the FP32 smoother, per node it
+# updates, from one ncu capture of the current kernel (the summary under
+# profiles/ gives the command); None until such a capture exists.
+SMOOTH32_DRAM_BYTES_PER_NODE = None
 
 
 def _hbm_peak():
     """Measured copy bandwidth of the GB300s (GB/s), else the recipe's fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["hbm_gbs"])
+            return float(json.load(fh)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
     except (OSError, KeyError, ValueError):
-        return 6800.0
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
-HBM_PEAK_GBS = _hbm_peak()
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
 
 
 def _dist():
@@ -72,6 +73,13 @@ def _dist():
     return ws, rank, local
 
 
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def max_over_ranks(vals, device):
     """Element-wise max of per-rank values over the process group (the timing rule: slowest rank)."""
     import torch
@@ -79,13 +87,6 @@ def max_over_ranks(vals, device):
     t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return [float(v) for v in t.cpu()]
-
-
-def workload(seed):
-    from paper_2512_08555_gb300 import synth
-    desc, src = synth.config2(seed)
-    f = synth.sample_leaves(desc, src)
-    return desc, f
 
 
 def start_clock_sampler(index):
@@ -126,84 +127,6 @@ def stop_clock_sampler(p, path):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(desc, f, order):
-    """Time the CPU oracle as it stands: RHS preparation + one V-cycle + residual."""
-    from oracle.forest import OracleForest
-    from oracle.multigrid import OracleSolver
-    fo = OracleForest.from_desc(desc)
-    o = OracleSolver(fo, order)              # LGF tabulation: create-time, not timed
-    for A in o.U:
-        A[...] = 0.0
-    t0 = time.perf_counter()
-    o.prepare_rhs(f)
-    t1 = time.perf_counter()
-    o.vcycle()
-    o.leaf_residual_max()
-    t2 = time.perf_counter()
-    return o, t1 - t0, t2 - t1
-
-
-def run_reference(args):
-    ws, rank, local = _dist()
-    if rank != 0:
-        return 0
-    desc, f = workload(0)
-    cyc = ORACLE_CYCLES[args.order]
-    times = []
-    for i in range(args.warmup + args.steps):
-        _, tp, tc = oracle_sample(desc, f, args.order)
-        if i >= args.warmup:
-            times.append(tp + cyc * tc)
-    t = float(np.mean(times))
-    value = desc.leaf_nodes / t
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(desc, args.order),
-        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": f"RHS preparation + 1 V(3,3) cycle of the full workload per step, "
-                                   f"solve time extrapolated to {cyc} cycles"},
-        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line))
-    return 0
-
-
-def _config(desc, order):
-    return {"workload": f"adaptive free-space Poisson, [-1,1)^3, levels 0..{desc.max_level}, "
-                        f"{desc.nb0[0]}^3 level-0 blocks of {desc.n}^3, 8 C4 bumps (seed 0)",
-            "leaf_nodes": int(desc.leaf_nodes), "n_leaves": int(desc.n_leaves), "order": order,
-            "cycle": "V(3,3)", "tol": TOL, "l2": "flushed (256 MB write) before every timed solve"}
-
-
-def _time_solves(solver, f, steps, warmup, flush, stream):
-    """Warm up, then time `steps` solves (L2 flushed before each) with CUDA events."""
-    import torch
-    for _ in range(warmup):
-        u, st = solver.solve(f)
-    torch.cuda.synchronize()
-    solver.profile(True)
-    solver.profile_read(reset=True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    launches, sts = 0, []
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        u, st = solver.solve(f)
-        ev[i][1].record(stream)
-        launches += int(st.launches)
-        sts.append(st)
-    torch.cuda.synchronize()
-    host = (time.perf_counter() - t0) / steps
-    prof = solver.profile_read(reset=True)
-    solver.profile(False)
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    return ms, u, sts[-1], launches, prof, host
-
-
 def _time_calls(fn, steps, warmup, flush, stream):
     """Warm up, then time `steps` calls of fn() (L2 flushed before each) with CUDA events; returns (ms, last result)."""
     import torch
@@ -221,77 +144,6 @@ def _time_calls(fn, steps, warmup, flush, stream):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     return float(np.mean(times)), out
-
-
-def bench_adjoint(desc, f, u_plain, ms_plain, order, flush, stream, steps):
-    """Gradient of <w, u> for a seeded Gaussian weight w on the headline forest, chosen and plain FP64."""
-    import torch
-    from paper_2512_08555_gb300 import synth
-    from paper_2512_08555_gb300.mrp import Solver
-    w = torch.from_numpy(synth.sample_leaves(desc, synth.gaussian_weight(0))).cuda()
-    out = {"what": "f-bar = S^T w: FP64 refinement lambda += M^T (E^T w - K^T lambda) with transposed V-cycles M^T"}
-    grads = {}
-    for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
-        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec)
-        ms, (g, st) = _time_calls(lambda: s.solve_adjoint(w), steps, 3, flush, stream)
-        grads[name] = g.clone()
-        a = float((w * u_plain).sum())
-        b = float((g * f).sum())
-        out[name] = {"ms_per_gradient": ms, "transposed_cycles": int(st.cycles), "final_rel_residual": float(st.residual),
-                     "ratio_to_plain_fp64_forward": ms / ms_plain, "dot_identity_rel": abs(a - b) / abs(a),
-                     "launches_per_gradient": int(st.launches)}
-        s.close()
-    out["chosen"]["cycles_precision"] = "FP32 transposed cycles"
-    out["plain_fp64"]["cycles_precision"] = "FP64 transposed cycles"
-    out["max_rel_diff_chosen_vs_fp64"] = float((grads["chosen"] - grads["plain_fp64"]).abs().max()
-                                               / grads["plain_fp64"].abs().max())
-    return out
-
-
-def bench_five_level(order, flush, stream, steps, inner_cycles=4):
-    import torch
-    from paper_2512_08555_gb300 import synth
-    from paper_2512_08555_gb300.mrp import Solver
-    desc, src = synth.config3(0)
-    f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
-    out = {"workload": f"adaptive [-1,1)^3, levels 0..{desc.max_level}, 5^3 level-0 blocks of 16^3, 8 C4 bumps",
-           "leaf_nodes": int(desc.leaf_nodes)}
-    res = {}
-    for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
-        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec, inner_cycles=inner_cycles)
-        for _ in range(3):
-            s.solve(f)
-        s.profile(True)
-        s.profile_read(reset=True)
-        ms_h, (u, st) = _time_calls(lambda: s.solve(f), steps, 0, flush, stream)
-        prof = s.profile_read(reset=True)
-        s.profile(False)
-        # the same solve as one CUDA graph launch
-        ug = torch.empty_like(f)
-        ms_g, (u_g, st_g) = _time_calls(lambda: s.solve_graph(f, ug), steps, 3, flush, stream)
-        ms = min(ms_h, ms_g)
-        if ms_g < ms_h:
-            u, st = u_g, st_g
-        res[name] = (ms, u, st, prof)
-        out[name] = {"value": desc.leaf_nodes / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms,
-                     "launch": "graph" if ms_g < ms_h else "host-driven",
-                     "launch_modes_ms": {"graph": ms_g, "host_driven": ms_h},
-                     "cycles": int(st.cycles), "ir_steps": int(st.ir_steps), "final_rel_residual": float(st.residual),
-                     "phases_ms_per_step": {k: v["ms"] / steps for k, v in prof.items()}}
-        if name == "chosen":
-            out["roofline_smoother"] = _roofline(prof, order, steps)
-            out["roofline_smoother"]["traffic_level4_launch"] = SMOOTH32_TRAFFIC["five_level_level4"]
-            w = torch.from_numpy(synth.sample_leaves(desc, synth.gaussian_weight(0))).cuda()
-            msg, (g, stg) = _time_calls(lambda: s.solve_adjoint(w), steps, 1, flush, stream)
-            out["gradient_chosen"] = {"ms_per_gradient": msg, "transposed_cycles": int(stg.cycles),
-                                      "final_rel_residual": float(stg.residual),
-                                      "dot_identity_rel": abs(float((w * u).sum()) - float((g * f).sum()))
-                                      / abs(float((w * u).sum()))}
-        s.close()
-    out["max_rel_err_vs_fp64"] = float((res["chosen"][1] - res["plain_fp64"][1]).abs().max()
-                                       / res["plain_fp64"][1].abs().max())
-    out["speedup_vs_plain_fp64"] = res["plain_fp64"][0] / res["chosen"][0]
-    return out
 
 
 def fft_bytes_flops(N0, P, elem):
@@ -317,7 +169,7 @@ def fft_bytes_flops(N0, P, elem):
     return byt, lines * fft
 
 
-def bench_fft_large(order, flush, stream, steps):
+def bench_fft_large(order, flush, stream, steps, fp64_peak):
     """Level-0 convolution on a lattice far larger than L2: 15^3 blocks of 16^3 (N0 = 240, P = 486), one central
     block refined once; each FP32 cycle is then essentially one FP32 convolution."""
     import torch
@@ -353,7 +205,8 @@ def bench_fft_large(order, flush, stream, steps):
              "achieved_GBs": byt / t / 1e9, "hbm_frac": byt / t / 1e9 / HBM_PEAK_GBS,
              "achieved_TFLOPs": fl / t / 1e12}
         if name == "fp64":
-            r["fp64_alu_frac"] = fl / t / 1e12 / FP64_PEAK_TFLOPS
+            r["fp64_alu_frac"] = fl / t / 1e12 / fp64_peak
+            r["fp64_peak_source"] = "measured FP64 FMA throughput (mrp_fma_peak, this run)"
             r["bound"] = "alu (FP64)"
         else:
             r["bound"] = "hbm"
@@ -361,7 +214,240 @@ def bench_fft_large(order, flush, stream, steps):
     return out
 
 
-def bench_batched(order, flush, stream, steps):
+
+# ---------------------------------------------------------------- CPU baseline: the oracle on every host core
+def _oracle_worker(conn, seed, order, tol):
+    """One host core: builds the oracle for the sample forest (create-time, untimed), then on each "go"
+    runs one full solve (RHS preparation + V(3,3) cycles to tol) and sends back its time."""
+    from paper_2512_08555_gb300 import synth
+    from oracle.forest import OracleForest
+    from oracle.multigrid import OracleSolver
+    desc, src = synth.oracle_sample_forest(seed)
+    f = synth.sample_leaves(desc, src)
+    o = OracleSolver(OracleForest.from_desc(desc), order)
+    conn.send(int(desc.leaf_nodes))
+    while True:
+        msg = conn.recv()
+        if msg != "go":
+            break
+        t0 = time.perf_counter()
+        u, rel = o.solve(f, tol=tol, max_cycles=MAX_CYCLES)
+        conn.send((time.perf_counter() - t0, int(o.cycles_done), float(rel)))
+
+
+class OraclePool:
+    """One spawned process per host core, each holding an oracle for the sample forest."""
+
+    def __init__(self, cores, order, seed=0):
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"            # one thread per worker (inherited by the spawned processes)
+        ctx = mp.get_context("spawn")
+        self.procs, self.conns = [], []
+        for _ in range(cores):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, seed, order, TOL), daemon=True)
+            p.start()
+            self.procs.append(p)
+            self.conns.append(a)
+        self.nodes = [c.recv() for c in self.conns]
+
+    def round(self, k=None):
+        """k workers (all by default) each run one full solve at once; returns (wall s, leaf nodes, results)."""
+        sel = self.conns[:k] if k else self.conns
+        t0 = time.perf_counter()
+        for c in sel:
+            c.send("go")
+        res = [c.recv() for c in sel]
+        return time.perf_counter() - t0, int(sum(self.nodes[:len(sel)])), res
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def _sample_text(cores, nodes1, cycles):
+    return (f"full oracle solves (RHS preparation + V(3,3) cycles to a relative residual of {TOL:g}, order 4; "
+            f"{cycles} cycles) of the same generator's smallest forest: 4^3 level-0 blocks of 8^3, levels 0..2, "
+            f"8 C4 bumps, {nodes1} leaf nodes; one independent solve per host core at once ({cores} cores); "
+            f"create-time work (LGF tabulation, tables) untimed")
+
+
+def cpu_baseline(order, warm_rounds=1, rounds=1):
+    """The oracle as it stands on every host core, and on one core alone (a bounded sample, about 10-30 s)."""
+    cores = _host_cores()
+    pool = OraclePool(cores, order)
+    try:
+        for _ in range(warm_rounds):
+            pool.round()
+        one_wall, one_nodes, r1 = pool.round(1)
+        walls = []
+        for _ in range(rounds):
+            wall, nodes, res = pool.round()
+            walls.append(wall)
+    finally:
+        pool.close()
+    t = float(np.mean(walls))
+    return {"value": nodes / t, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": _sample_text(cores, pool.nodes[0], res[0][1]),
+            "ms_per_round": t * 1e3, "rounds": rounds,
+            "one_thread": {"value": one_nodes / one_wall, "unit": "cells/s", "cores": 1,
+                           "ms_per_solve": one_wall * 1e3}}
+
+
+def run_reference(args):
+    """Reference arm: the oracle, each step one round of full solves on every host core."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    cores = _host_cores()
+    pool = OraclePool(cores, args.order)
+    try:
+        for _ in range(args.warmup):
+            pool.round()
+        one_wall, one_nodes, _ = pool.round(1)
+        walls, res = [], None
+        for _ in range(args.steps):
+            wall, nodes, res = pool.round()
+            walls.append(wall)
+    finally:
+        pool.close()
+    t = float(np.mean(walls))
+    value = nodes / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(None, args.order, args.inner_cycles),
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                         "sample": _sample_text(cores, pool.nodes[0], res[0][1]),
+                         "one_thread": {"value": one_nodes / one_wall, "unit": "cells/s", "cores": 1,
+                                        "ms_per_solve": one_wall * 1e3}},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+HEADLINE_LEAF_NODES = 97853440
+
+
+def _config(desc, order, inner):
+    nodes = int(desc.leaf_nodes) if desc is not None else HEADLINE_LEAF_NODES
+    return {"workload": "adaptive free-space Poisson, [-1,1)^3, 6^3 level-0 blocks of 16^3 nodes, levels 0..4, "
+                        "8 C4 bumps (seed = rank), refined where max|f| > 1e-3 max|A|",
+            "leaf_nodes": nodes, "order": order, "cycle": "V(3,3)", "tol": TOL,
+            "chosen": f"FP32 V(3,3) cycles ({inner} per step) inside FP64 iterative refinement",
+            "l2": "inputs (783 MB of f) larger than L2, and a 256 MB buffer written before every timed solve"}
+
+
+def _profiled(solver, f, n):
+    """n host-driven solves with per-phase CUDA events (on the launching stream): phase totals."""
+    s = solver
+    s.solve(f)
+    s.profile(True)
+    s.profile_read(reset=True)
+    for _ in range(n):
+        u, st = s.solve(f)
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    return prof, st
+
+
+def _roofline(prof32, prof64, order, nsolves, fp64_peak):
+    """Dominant kernel (the FP32 smoother) against measured HBM bandwidth; the FP64 smoother against the
+    measured FP64 FMA peak."""
+    out = {}
+    sm32 = prof32.get("smooth_f32")
+    if sm32 and sm32["ms"] > 0:
+        byt = sm32["nodes"] * 3 * 4                   # read u, read f, write u (FP32 words)
+        ach = byt / (sm32["ms"] / 1e3) / 1e9
+        nl = max(sm32["launches"], 1)
+        traffic = (SMOOTH32_DRAM_BYTES_PER_NODE * sm32["nodes"] / nl) if SMOOTH32_DRAM_BYTES_PER_NODE else None
+        out = {"bound": "hbm", "kernel": "k_smooth_fused<4,float,6,16> (Gauss-Seidel sweep, ghost layer built "
+                                         "in shared memory, FP32)",
+               "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
+               "traffic": traffic, "algorithmic_bytes_per_launch": byt / nl, "bytes_per_node": 12,
+               "peak_source": HBM_PEAK_SOURCE + ", burst figure (kernel timed alone per launch)",
+               "avg_launch_us": sm32["ms"] * 1e3 / nl, "launches_per_solve": nl / nsolves,
+               "timed_by": "CUDA events around every smoother launch of host-driven solves, on the launching stream"}
+    sm64 = prof64.get("smooth_f64")
+    if sm64 and sm64["ms"] > 0 and fp64_peak:
+        fl = sm64["nodes"] * 2 * STENCIL_POINTS[order]
+        ach = fl / (sm64["ms"] / 1e3) / 1e12
+        r64 = {"bound": "alu", "kernel": "k_smooth_fused<4,double,6,16> (Gauss-Seidel sweep, FP64)", "achieved": ach,
+               "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+               "peak_source": "measured FP64 FMA throughput of this device (mrp_fma_peak, this run)",
+               "flops_per_node": 2 * STENCIL_POINTS[order],
+               "avg_launch_us": sm64["ms"] * 1e3 / max(sm64["launches"], 1)}
+        if not out:
+            out = r64
+        else:
+            out["fp64_smoother"] = r64
+    return out
+
+
+def bench_pair(desc, f, order, flush, stream, steps, warmup, inner, plain_steps=None):
+    """Chosen (mixed) and plain FP64 graph solves of one workload: ms, results, statistics."""
+    import torch
+    from paper_2512_08555_gb300.mrp import Solver
+    out, res = {}, {}
+    for name, prec, k in (("chosen", "mixed", steps), ("plain_fp64", "fp64", plain_steps or steps)):
+        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec, inner_cycles=inner)
+        u = torch.empty_like(f)
+        ms, (u, st) = _time_calls(lambda: s.solve_graph(f, u), k, warmup, flush, stream)
+        res[name] = (ms, u.clone(), st, s)
+        out[name] = {"value": desc.leaf_nodes / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms, "steps": k,
+                     "cycles": int(st.cycles), "ir_steps": int(st.ir_steps), "final_rel_residual": float(st.residual),
+                     "kernels_per_solve": int(st.launches)}
+    out["max_rel_err_vs_fp64"] = float((res["chosen"][1] - res["plain_fp64"][1]).abs().max()
+                                       / res["plain_fp64"][1].abs().max())
+    out["speedup_vs_plain_fp64"] = res["plain_fp64"][0] / res["chosen"][0]
+    return out, res
+
+
+def bench_three_level(order, flush, stream, steps, inner):
+    import torch
+    from paper_2512_08555_gb300 import synth
+    desc, src = synth.config2(0)
+    f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
+    out, res = bench_pair(desc, f, order, flush, stream, steps, 3, inner)
+    for _, _, _, s in res.values():
+        s.close()
+    out["workload"] = "adaptive [-1,1)^3, 5^3 level-0 blocks of 16^3, levels 0..2, 8 C4 bumps (seed 0)"
+    out["leaf_nodes"] = int(desc.leaf_nodes)
+    return out
+
+
+def bench_adjoint(desc, f, u_plain, order, flush, stream, steps, inner):
+    """Gradient of <w, u> for a seeded Gaussian weight w on the headline forest, chosen and plain FP64."""
+    import torch
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver
+    w = torch.from_numpy(synth.sample_leaves(desc, synth.gaussian_weight(0))).cuda()
+    out = {"what": "f-bar = S^T w: FP64 refinement lambda += M^T (E^T w - K^T lambda) with transposed V-cycles M^T",
+           "workload": "the headline forest"}
+    grads = {}
+    for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
+        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec, inner_cycles=inner)
+        ms, (g, st) = _time_calls(lambda: s.solve_adjoint(w), steps, 1, flush, stream)
+        grads[name] = g.clone()
+        a = float((w * u_plain).sum())
+        b = float((g * f).sum())
+        out[name] = {"ms_per_gradient": ms, "steps": steps, "transposed_cycles": int(st.cycles),
+                     "final_rel_residual": float(st.residual), "dot_identity_rel": abs(a - b) / abs(a),
+                     "launches_per_gradient": int(st.launches)}
+        s.close()
+        del g
+    out["chosen"]["cycles_precision"] = "FP32 transposed cycles"
+    out["plain_fp64"]["cycles_precision"] = "FP64 transposed cycles"
+    out["max_rel_diff_chosen_vs_fp64"] = float((grads["chosen"] - grads["plain_fp64"]).abs().max()
+                                               / grads["plain_fp64"].abs().max())
+    return out
+
+
+def bench_batched(order, flush, stream, steps, inner):
     import torch
     from paper_2512_08555_gb300 import synth
     from paper_2512_08555_gb300.mrp import Solver
@@ -375,13 +461,14 @@ def bench_batched(order, flush, stream, steps):
            "problems": int(sum(comps)), "forests": len(forests), "leaf_nodes": nodes,
            "launch": "one CUDA graph launch per solve (mrp_solve_graph): device-controlled loops per block size"}
     res = {}
-    for name, prec in (("chosen", "mixed"), ("plain_fp64", "fp64")):
-        s = Solver(forests, order=order, tol=TOL, max_cycles=MAX_CYCLES, ncomp=comps, precision=prec)
+    for name, prec, k in (("chosen", "mixed", steps), ("plain_fp64", "fp64", min(steps, 5))):
+        s = Solver(forests, order=order, tol=TOL, max_cycles=MAX_CYCLES, ncomp=comps, precision=prec,
+                   inner_cycles=inner)
         u = torch.empty_like(f)
-        ms, (u, st) = _time_calls(lambda: s.solve_graph(f, u), steps, 3, flush, stream)
+        ms, (u, st) = _time_calls(lambda: s.solve_graph(f, u), k, 3, flush, stream)
         res[name] = (ms, u.clone(), st)
-        out[name] = {"value": nodes / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms, "cycles": int(st.cycles),
-                     "ir_steps": int(st.ir_steps), "final_rel_residual": float(st.residual),
+        out[name] = {"value": nodes / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms, "steps": k,
+                     "cycles": int(st.cycles), "ir_steps": int(st.ir_steps), "final_rel_residual": float(st.residual),
                      "kernels_per_solve": int(st.launches)}
         s.close()
     out["max_rel_err_vs_fp64"] = float((res["chosen"][1] - res["plain_fp64"][1]).abs().max()
@@ -390,32 +477,24 @@ def bench_batched(order, flush, stream, steps):
     return out
 
 
-def _roofline(prof, order, steps, traffic=None):
-    """Dominant-kernel roofline: the smoother of the chosen path (FP32, bytes) and of the FP64 path (flops)."""
-    out = {}
-    sm32 = prof.get("smooth_f32")
-    if sm32 and sm32["ms"] > 0:
-        byt = sm32["nodes"] * 3 * 4                   # read u, read f, write u (FP32 words)
-        ach = byt / (sm32["ms"] / 1e3) / 1e9
-        nl = max(sm32["launches"], 1)
-        out = {"bound": "hbm", "kernel": "k_smooth_fused<M,float,I> (Gauss-Seidel sweep with fused ghost layer, FP32)",
-               "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
-               "traffic": traffic, "algorithmic_bytes_per_launch": byt / nl,
-               "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-               "bytes_per_node": 12, "avg_launch_us": sm32["ms"] * 1e3 / nl}
-    sm64 = prof.get("smooth_f64")
-    if sm64 and sm64["ms"] > 0:
-        fl = sm64["nodes"] * 2 * STENCIL_POINTS[order]
-        ach = fl / (sm64["ms"] / 1e3) / 1e12
-        r64 = {"bound": "alu", "kernel": "k_smooth_fused<M,double,I> (Gauss-Seidel sweep, FP64)", "achieved": ach,
-               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-               "peak_source": "FP64 units x clock (152 SMs x 2 FMA/clk x 2.07 GHz), nominal",
-               "flops_per_node": 2 * STENCIL_POINTS[order],
-               "avg_launch_us": sm64["ms"] * 1e3 / max(sm64["launches"], 1)}
-        if not out:
-            out = r64
-        else:
-            out["fp64_smoother"] = r64
+def parity_sample(order):
+    """The oracle sample forest solved by the oracle and by the CUDA path (FP64 and mixed): max rel diffs."""
+    import torch
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver
+    from oracle.forest import OracleForest
+    from oracle.multigrid import OracleSolver
+    desc, src = synth.oracle_sample_forest(0)
+    f = synth.sample_leaves(desc, src)
+    o = OracleSolver(OracleForest.from_desc(desc), order)
+    uo, _ = o.solve(f, tol=TOL, max_cycles=MAX_CYCLES)
+    out = {"forest": "the CPU baseline's sample forest (90,112 leaf nodes)", "oracle_cycles": int(o.cycles_done)}
+    for name, prec in (("fp64", "fp64"), ("mixed", "mixed")):
+        s = Solver(desc, order=order, tol=TOL, max_cycles=MAX_CYCLES, precision=prec)
+        u, st = s.solve(torch.from_numpy(f).cuda())
+        out[name] = {"max_rel_diff_vs_oracle": float(np.abs(u.cpu().numpy() - uo).max() / np.abs(uo).max()),
+                     "cycles": int(st.cycles)}
+        s.close()
     return out
 
 
@@ -430,98 +509,79 @@ def run_ours(args):
         torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2512_08555_gb300.mrp import Solver
-    desc, f_np = workload(rank)
+    from paper_2512_08555_gb300 import synth
+    from paper_2512_08555_gb300.mrp import Solver, fma_peak_tflops
+    desc, src = synth.config3(rank)
+    f_np = synth.sample_leaves(desc, src)
     f = torch.from_numpy(f_np).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    plain = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES)
+    fp64_peak = fma_peak_tflops("fp64")
+    fp32_peak = fma_peak_tflops("fp32")
     chosen = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed",
                     inner_cycles=args.inner_cycles)
+    plain = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES)
+    uc, up = torch.empty_like(f), torch.empty_like(f)
+    chosen.solve_graph(f, uc)               # graph build, autotune
+    plain.solve_graph(f, up)
     if ws > 1:
         dist.barrier()
     p, path = start_clock_sampler(local)
-    # host-driven solves (per-phase events on: the phase breakdown)
-    ms_ch, u_c, st_c, launches, prof_c, host_c = _time_solves(chosen, f, args.steps, args.warmup, flush, stream)
-    ms_ph, u_p, st_p, _, prof_p, host_p = _time_solves(plain, f, args.steps, args.warmup, flush, stream)
-    # the same solves as one CUDA graph launch each (loop control on the device, no host round trips)
-    ug, upg = torch.empty_like(f), torch.empty_like(f)
-    ms_cg, (u_cg, st_cg) = _time_calls(lambda: chosen.solve_graph(f, ug), args.steps, args.warmup, flush, stream)
-    ms_pg, (u_pg, st_pg) = _time_calls(lambda: plain.solve_graph(f, upg), args.steps, args.warmup, flush, stream)
-    clocks = stop_clock_sampler(p, path)
-    use_graph = ms_cg < ms_ch
-    if use_graph:
-        ms_c, ms_p, u_c, u_p, st_c, st_p = ms_cg, ms_pg, u_cg, u_pg, st_cg, st_pg
-        launches = args.steps * int(st_cg.launches)
-    else:
-        ms_c, ms_p = ms_ch, ms_ph
-    err = float((u_c - u_p).abs().max() / u_p.abs().max())
-    t_step, t_plain = ms_c / 1e3, ms_p / 1e3
-    if ws > 1:
-        t_step, t_plain = max_over_ranks([t_step, t_plain], "cuda")
-    value = ws * desc.leaf_nodes / t_step
-    # end to end through host memory (chosen path)
+    ms_c, (uc, st_c) = _time_calls(lambda: chosen.solve_graph(f, uc), args.steps, args.warmup, flush, stream)
+    plain_steps = max(3, min(args.steps, 5))
+    ms_p, (up, st_p) = _time_calls(lambda: plain.solve_graph(f, up), plain_steps, 1, flush, stream)
+    # end to end through host memory: pinned f in, u out, inside the timed region
     f_host = torch.from_numpy(f_np).pin_memory()
     u_host = torch.empty_like(f_host).pin_memory()
-    chosen.solve_host(f_host, u_host)
-    e2e_t = []
-    for i in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        chosen.solve_host(f_host, u_host)
-        b.record(stream)
-        torch.cuda.synchronize()
-        e2e_t.append(a.elapsed_time(b) / 1e3)
-    e2e_step = float(np.mean(e2e_t))
+    ms_e, (u_host, st_e) = _time_calls(lambda: chosen.solve_host(f_host, u_host), args.steps, 1, flush, stream)
+    clocks = stop_clock_sampler(p, path)
+    err = float((uc - up).abs().max() / up.abs().max())
+    e2e_err = float(np.abs(u_host.numpy() - uc.cpu().numpy()).max())
+    t_step, t_plain, t_e2e = ms_c / 1e3, ms_p / 1e3, ms_e / 1e3
     if ws > 1:
-        e2e_step = max_over_ranks([e2e_step], "cuda")[0]
+        t_step, t_plain, t_e2e = max_over_ranks([t_step, t_plain, t_e2e], "cuda")
+    value = ws * desc.leaf_nodes / t_step
+    # per-phase breakdown and the smoother's launches: host-driven solves with CUDA events per phase
+    prof_c, _ = _profiled(chosen, f, min(args.steps, 3))
+    prof_p, _ = _profiled(plain, f, 1)
+    nprof = min(args.steps, 3)
     tot_c = sum(v["ms"] for v in prof_c.values())
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": _config(desc, args.order),
-        "chosen": "mixed precision: FP32 V(3,3) cycles inside FP64 iterative refinement",
-        "launch": ("one CUDA graph launch per solve (mrp_solve_graph)" if use_graph
-                   else "host-driven solve (mrp_solve)"),
-        "launch_modes_ms": {"graph": {"chosen": ms_cg, "plain_fp64": ms_pg},
-                            "host_driven": {"chosen": ms_ch, "plain_fp64": ms_ph}},
-        "phases_from": "host-driven solves with per-phase CUDA events",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": _config(desc, args.order, args.inner_cycles),
+        "launch": "one CUDA graph launch per solve (mrp_solve_graph)",
         "max_rel_err_vs_fp64": err,
         "cycles": int(st_c.cycles), "ir_steps": int(st_c.ir_steps), "final_rel_residual": float(st_c.residual),
         "plain_fp64": {"value": ws * desc.leaf_nodes / t_plain, "unit": "cells/s", "ms_per_step": t_plain * 1e3,
-                       "cycles": int(st_p.cycles), "final_rel_residual": float(st_p.residual),
-                       "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof_p.items()}},
+                       "steps": plain_steps, "cycles": int(st_p.cycles), "final_rel_residual": float(st_p.residual),
+                       "phases_ms_per_step": {k: v["ms"] for k, v in prof_p.items()}},
         "speedup_vs_plain_fp64": t_plain / t_step,
-        "e2e": {"value": ws * desc.leaf_nodes / e2e_step, "unit": "cells/s",
-                "h2d_bytes_per_step": int(f_host.numel() * 8), "d2h_bytes_per_step": int(u_host.numel() * 8)},
-        "roofline": _roofline({**prof_c, **{k: v for k, v in prof_p.items() if k == "smooth_f64"}}, args.order,
-                              args.steps, SMOOTH32_TRAFFIC["headline"] if args.order == ORDER else None),
-        "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof_c.items()},
+        "e2e": {"value": ws * desc.leaf_nodes / t_e2e, "unit": "cells/s", "ms_per_step": t_e2e * 1e3,
+                "h2d_bytes_per_step": int(f_host.numel() * 8), "d2h_bytes_per_step": int(u_host.numel() * 8),
+                "call": "mrp_solve_host (C ABI, host buffers; H2D, graph solve, D2H on the stream)",
+                "max_abs_diff_vs_device_call": e2e_err},
+        "roofline": _roofline(prof_c, prof_p, args.order, nprof, fp64_peak),
+        "phases_ms_per_step": {k: v["ms"] / nprof for k, v in prof_c.items()},
         "phase_share": {k: (v["ms"] / tot_c if tot_c else None) for k, v in prof_c.items()},
-        "gpu_launches": launches,
+        "kernels_per_solve": int(st_c.launches),
+        "gpu_launches": args.steps * int(st_c.launches),
         "clocks": clocks,
-        "host_wall_s_per_step": host_c,
+        "peaks": {"fp64_fma_tflops": fp64_peak, "fp32_fma_tflops": fp32_peak, "hbm_gbs": HBM_PEAK_GBS,
+                  "how": "mrp_fma_peak: 8 independent FMA chains per thread, 8 CTAs of 256 per SM, best of 3"},
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        o, tp, tc = oracle_sample(desc, f_np, args.order)
-        cyc = ORACLE_CYCLES[args.order]
-        cpu_value = desc.leaf_nodes / (tp + cyc * tc)
-        line["cpu_baseline"] = {"value": cpu_value, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                                "sample": f"RHS preparation ({tp:.1f} s) + 1 V(3,3) cycle ({tc:.1f} s) of the full "
-                                          f"workload, extrapolated to {cyc} cycles (the oracle's count to 1e-10)"}
-        # live parity of that first cycle against the FP64 CUDA path
-        s1 = Solver(desc, order=args.order, tol=0.0, max_cycles=1)
-        u1, _ = s1.solve(f, allow_not_converged=True)
-        uo = o.leaf_u()
-        line["parity_1cycle_max_rel"] = float(np.abs(u1.cpu().numpy() - uo).max() / np.abs(uo).max())
-        s1.close()
+    plain.close()
     if rank == 0 and not args.no_extras:
         xs = max(2, min(args.steps, 3))
-        line["adjoint"] = bench_adjoint(desc, f, u_p, ms_p, args.order, flush, stream, xs)
-        line["five_level"] = bench_five_level(args.order, flush, stream, xs, args.inner_cycles)
-        line["batched"] = bench_batched(args.order, flush, stream, xs)
-        line["fft_large"] = bench_fft_large(args.order, flush, stream, xs)
+        line["adjoint"] = bench_adjoint(desc, f, up, args.order, flush, stream, xs, args.inner_cycles)
+        chosen.close()
+        del uc
+        line["three_level"] = bench_three_level(args.order, flush, stream, args.steps, args.inner_cycles)
+        line["batched"] = bench_batched(args.order, flush, stream, args.steps, args.inner_cycles)
+        line["fft_large"] = bench_fft_large(args.order, flush, stream, xs, fp64_peak)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["parity_sample"] = parity_sample(args.order)
+        line["cpu_baseline"] = cpu_baseline(args.order)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -537,8 +597,10 @@ def run_profile_case(args):
     __graft_entry__.build()
     from paper_2512_08555_gb300 import synth
     from paper_2512_08555_gb300.mrp import Solver
-    if args.profile_case == "five_level":
+    if args.profile_case == "headline":
         desc, src = synth.config3(0)
+    elif args.profile_case == "five_level_5cube":
+        desc, src = synth.config3(0, nb=5)
     elif args.profile_case == "fft_large":
         desc = synth.adaptive_forest((15, 15, 15), 16, (-1.0, -1.0, -1.0), 2.0 / 240, 1,
                                      lambda level, coords: (coords == 7).all(axis=1))
@@ -546,7 +608,8 @@ def run_profile_case(args):
     else:
         desc, src = synth.config2(0)
     f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
-    s = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed")
+    s = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed",
+               inner_cycles=args.inner_cycles)
     for _ in range(args.warmup + args.steps):
         s.solve(f)
     torch.cuda.synchronize()
@@ -557,15 +620,15 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--order", type=int, default=ORDER, choices=[2, 4, 6])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline line only")
     ap.add_argument("--inner-cycles", type=int, default=4, help="FP32 cycles per refinement step of the chosen form")
-    ap.add_argument("--profile-case", choices=["headline", "five_level", "fft_large"], default=None,
-                    help="run the chosen solver on one workload without timing (for ncu)")
+    ap.add_argument("--profile-case", choices=["headline", "three_level", "five_level_5cube", "fft_large"],
+                    default=None, help="run the chosen solver on one workload without timing (for ncu)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

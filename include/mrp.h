@@ -79,10 +79,12 @@ typedef struct {
                                     (Sec. 3.1).
                                     MRP_STOP_CAUCHY: max|u^n - u^{n+1}| / max|u^{n+1}| over leaf
                                     nodes between successive iterates (Sec. 3, the criterion for
-                                    problems whose residual stalls): u^0 = 0; an iterate is the
-                                    state after a V-cycle (MRP_FP64) or after a refinement step
-                                    (MRP_MIXED); a zero iterate divides by 1.  Keeps one more FP64
-                                    copy of the leaf values (8 bytes per leaf node). */
+                                    problems whose residual stalls).  MRP_FP64: an iterate is the
+                                    state after a V-cycle, u^0 = 0.  MRP_MIXED: an iterate is the
+                                    state after a refinement step, u^0 the state after the first
+                                    outer residual, so at least one step runs.  A zero iterate
+                                    divides by 1.  Keeps one more FP64 copy of the leaf values
+                                    (8 bytes per leaf node). */
     int32_t max_cycles;          /* >= 1 */
     int32_t nu1, nu2;            /* pre- and post-smoothing sweeps, >= 0 */
     int32_t precision;           /* MRP_FP64: every stage in FP64.

@@ -112,6 +112,16 @@ int mrp_coarse_solve_noalloc(mrp_handle* h, const double* f0, double* u0, void* 
  *   MRP_ADJ_OUT_T    in: w (leaf layout) -> out[0, len): E_x^T w,
  *                    out[len, 2 len): E_f^T w
  *   MRP_ADJ_RHS_T    in: f*-bar (len, leaf blocks) -> out: B^T f*-bar (leaf layout) */
+/* Measured FMA throughput of the current device in TFLOP/s (2 flops per
+ * FMA): precision MRP_FP64 times FP64 FMAs, MRP_MIXED FP32 FMAs.  Every
+ * thread of a grid of 8 CTAs per SM runs 8 independent FMA chains; the best
+ * of 3 launches timed with CUDA events on stream counts.  It is the
+ * measured denominator of the FP64 stencil kernels' roofline (their flops
+ * per byte lie far above this GPU's FP64 ridge).  Allocates and frees a few
+ * bytes; synchronises the stream.  The paper has no counterpart (a
+ * measurement aid). */
+int mrp_fma_peak(int32_t precision, double* tflops, void* stream);
+
 enum { MRP_ADJ_CYCLE_T = 0, MRP_ADJ_RES_T = 1, MRP_ADJ_OUT_T = 2, MRP_ADJ_RHS_T = 3 };
 int mrp_adjoint_len(mrp_handle* h, int64_t* len);
 int mrp_adjoint_op(mrp_handle* h, int32_t op, const double* in, double* out, void* stream);

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libmrp.so")
 SOURCES = ["fused_smooth_f32.cu", "fused_smooth_f64.cu", "fused_other_f32.cu", "fused_other_f64.cu", "fused_leafres.cu",
            "solver.cu", "kernels_stencil.cu", "kernels_fft.cu", "kernels_mixed.cu", "noalloc.cu", "adjoint.cu",
-           "kernels_adjoint.cu", "graph.cu"]
+           "kernels_adjoint.cu", "graph.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -37,7 +37,10 @@ __global__ void k_loop_check(const unsigned long long* __restrict__ res, const u
         const double rel = r / (f > 0.0 ? f : 1.0);
         rel_out[p] = rel;
         if (!(rel < tol)) all = false;
-        if (need_step && rel > 0.0) all = false;       // a nonzero first residual takes a refinement step
+        // need_step 1: a nonzero first residual takes a refinement step; 2: the
+        // first check never stops (Cauchy rule with refinement: the first
+        // increment is the first step's)
+        if (need_step == 2 || (need_step == 1 && rel > 0.0)) all = false;
         if (!isfinite(rel)) bad = true;
     }
     if (count_step) {
@@ -111,7 +114,7 @@ static int build_group(Handle& h, cudaGraph_t G, cudaStream_t cs, const double* 
         outer_residual_launch(h, cs, true);
         if (cauchy) cauchy_launch(h, cs);
         k_loop_check<<<1, 32, 0, cs>>>(num, den, np, h.tol, h.loop_ctr, h.loop_rel, 1, h.inner_cycles,
-                                       h.max_cycles, h.max_ir, 0, (h.L >= 1 && !cauchy) ? 1 : 0, hc);
+                                       h.max_cycles, h.max_ir, 0, cauchy ? 2 : (h.L >= 1 ? 1 : 0), hc);
     }
     std::vector<cudaGraphNode_t> deps;
     int rc = tail_of(cs, deps);

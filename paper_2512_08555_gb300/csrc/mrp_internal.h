@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <vector>
 #include <string>
@@ -217,7 +218,17 @@ enum Phase { PH_GHOST = 0, PH_SMOOTH = 1, PH_RESIDUAL = 2, PH_RESTRICT = 3, PH_C
 // Phases of FP32 work are counted separately, at index + 8.
 template <typename T> constexpr int ph(int p) { return p + (sizeof(T) == 4 ? 8 : 0); }
 
-// Per-phase accounting: counts launches; with profiling on, records a CUDA
+// Phase names (NVTX ranges), index as in Phase, FP32 work at index + 8.
+inline const char* phase_name(int p) {
+    static const char* names[16] = {"ghost_f64", "smooth_f64", "residual_f64", "restrict_f64", "coarse_fft_f64",
+                                    "prolong_f64", "norm_f64", "other_f64", "ghost_f32", "smooth_f32", "residual_f32",
+                                    "restrict_f32", "coarse_fft_f32", "prolong_f32", "norm_f32", "other_f32"};
+    return (p >= 0 && p < 16) ? names[p] : "phase";
+}
+
+// Per-phase accounting: counts launches; opens an NVTX range named for the
+// phase around its launches (host side; a profiler attached to the process
+// shows each phase's launches under it); with profiling on, records a CUDA
 // event pair around the phase (harvested at the next host synchronisation).
 struct PhaseScope {
     Handle& h;
@@ -225,6 +236,7 @@ struct PhaseScope {
     int phase, e0 = -1, launches;
     int64_t nodes;
     PhaseScope(Handle& hh, cudaStream_t ss, int ph, int64_t nd, int nl) : h(hh), s(ss), phase(ph), launches(nl), nodes(nd) {
+        nvtxRangePushA(phase_name(phase));
         if (h.prof && h.ev_used + 2 <= (int)h.ev.size()) {
             e0 = h.ev_used;
             h.ev_used += 2;
@@ -232,6 +244,7 @@ struct PhaseScope {
         }
     }
     ~PhaseScope() {
+        nvtxRangePop();
         h.launches += launches;
         if (e0 >= 0) {
             cudaEventRecord(h.ev[e0 + 1], s);

@@ -811,6 +811,8 @@ static int solve_check(Handle& h, cudaStream_t s, SolveState& st) {
         if (!(st.rel[p] < h.tol)) all = false;
         // first residual: FP32 level 0
         if (!cauchy && h.mixed && h.L >= 1 && st.ir == 0 && st.rel[p] > 0.0) all = false;
+        // Cauchy rule with refinement: the first increment is the first step's
+        if (cauchy && h.mixed && st.ir == 0) all = false;
     }
     if (all) st.done = true;
     else if (!h.mixed && st.cycles >= h.max_cycles) st.done = true;

@@ -26,7 +26,7 @@ EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
             "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph",
-            "mrp_solve_host"]
+            "mrp_solve_host", "mrp_fma_peak"]
 ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
@@ -91,6 +91,7 @@ def load_library(path=LIB_PATH):
     lib.mrp_adjoint_op.argtypes = [P, I32, P, P, P]
     lib.mrp_solve_graph.argtypes = [P, P, P, P, C.POINTER(Stats)]
     lib.mrp_solve_host.argtypes = [P, P, P, P, C.POINTER(Stats)]
+    lib.mrp_fma_peak.argtypes = [I32, C.POINTER(D), P]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
     lib.mrp_error_string.restype = C.c_char_p
@@ -325,6 +326,14 @@ class Solver:
         P = np.zeros(3, np.int32)
         _check(self.lib.mrp_fft_shape(self.h, P.ctypes.data_as(C.c_void_p)), "mrp_fft_shape")
         return tuple(int(v) for v in P)
+
+
+def fma_peak_tflops(precision="fp64", stream=None):
+    """Measured FMA throughput of the current device (``mrp_fma_peak``), TFLOP/s."""
+    lib = load_library()
+    v = C.c_double()
+    _check(lib.mrp_fma_peak({"fp64": 0, "fp32": 1}[precision], C.byref(v), _stream_ptr(stream)), "mrp_fma_peak")
+    return v.value
 
 
 def poisson_solve(solver, f):

@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "Forest", "uniform_forest", "adaptive_forest", "sample_leaves",
     "gaussian_blobs", "c4_bumps", "vortex_ring", "gaussian_weight",
-    "config1", "config2", "config3", "batched_scalar_problem",
+    "config1", "config2", "config3", "oracle_sample_forest", "batched_scalar_problem",
 ]
 
 
@@ -356,22 +356,36 @@ def _bump_forest(seed, max_level, n=16, nb=5, half=1.0, thresh=1e-3, k=8):
     return forest, src
 
 
-def config2(seed=0, max_level=2, n=16):
-    """Adaptive forest on [-1,1)^3, 5^3 level-0 blocks of 16^3 (h0 = 1/40), levels 0..2; 8 C4 bumps.
+def config2(seed=0, max_level=2, n=16, nb=5):
+    """Adaptive forest on [-1,1)^3, nb^3 level-0 blocks of n^3 (5^3 of 16^3: h0 = 1/40), levels 0..max_level;
+    8 C4 bumps.
 
     A block is refined where max |f| over its nodes exceeds 1e-3 times the
     largest bump amplitude, subject to the boundary and 2:1 rules of
-    :func:`adaptive_forest`.
+    :func:`adaptive_forest`.  Seed 0 at levels 0..2: 2,805,760 leaf nodes.
     """
-    forest, src = _bump_forest(seed, max_level, n=n)
-    forest.meta.update(workload=f"adaptive [-1,1)^3 levels 0..{max_level}, {n}^3 blocks, 8 C4 bumps",
-                       seed=seed)
+    forest, src = _bump_forest(seed, max_level, n=n, nb=nb)
+    forest.meta.update(workload=f"adaptive [-1,1)^3, {nb}^3 level-0 blocks of {n}^3, levels 0..{max_level}, "
+                                f"8 C4 bumps", seed=seed)
     return forest, src
 
 
-def config3(seed=0, max_level=4, n=16):
-    """The config-2 generator at 5 levels (0..4)."""
-    return config2(seed, max_level=max_level, n=n)
+def config3(seed=0, max_level=4, n=16, nb=6):
+    """The config-2 generator at 5 levels (0..4) on 6^3 level-0 blocks (h0 = 1/48).
+
+    Seed 0 gives 97,853,440 leaf nodes (23,890 leaves); 5^3 level-0 blocks
+    would give 29,528,064 and 7^3 174,325,760.
+    """
+    return config2(seed, max_level=max_level, n=n, nb=nb)
+
+
+def oracle_sample_forest(seed=0):
+    """The config-2 generator at its smallest block size: 4^3 level-0 blocks of 8^3 (h0 = 1/16), levels 0..2.
+
+    Seed 0 gives 90,112 leaf nodes (176 leaves: 56 per level at 0 and 1, 64 at 2),
+    small enough for a full oracle solve in seconds.
+    """
+    return config2(seed, max_level=2, n=8, nb=4)
 
 
 def vortex_forest(seed=0, max_level=3, n=16, nb=6, half=1.5, thresh=1e-3):
