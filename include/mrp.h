@@ -81,8 +81,7 @@ typedef struct {
                                     nodes between successive iterates (Sec. 3, the criterion for
                                     problems whose residual stalls).  MRP_FP64: an iterate is the
                                     state after a V-cycle, u^0 = 0.  MRP_MIXED: an iterate is the
-                                    state after a refinement step, u^0 the state after the first
-                                    outer residual, so at least one step runs.  A zero iterate
+                                    state after a refinement step, u^0 = 0.  A zero iterate
                                     divides by 1.  Keeps one more FP64 copy of the leaf values
                                     (8 bytes per leaf node). */
     int32_t max_cycles;          /* >= 1 */
@@ -92,13 +91,23 @@ typedef struct {
                                     residual, level-0 convolution of the accumulated source,
                                     correction accumulation) around FP32 V-cycles; tol then
                                     bounds the relative residual of the composite system.
-                                    The first outer residual (u = 0, which only feeds the
-                                    first FP32 correction) convolves level 0 in FP32; a
-                                    nonzero one is always followed by a refinement step
-                                    (stop rule RESIDUAL) */
+                                    The first refinement step starts from u = 0, so its FP32
+                                    cycles solve the problem itself (f* on every level's
+                                    leaves); each step ends with an FP64 outer residual and
+                                    the stop check, so at least one step runs */
     int32_t inner_cycles;        /* MRP_MIXED: FP32 V-cycles per refinement step (0 = 4) */
     int32_t max_outer;           /* MRP_MIXED: refinement steps at most (0 = 12) */
+    int32_t launch;              /* 0: the CTA size of each stencil kernel and level, and for block
+                                    size 16 in FP32 whether a smoothing sweep runs the blocks
+                                    without interpolated ghosts in a separate leaner launch, are
+                                    chosen by timing at the first solve.  Otherwise a fixed choice
+                                    for every kernel and level: a CTA size (128, 256 or 512) plus
+                                    MRP_LAUNCH_SPLIT (the sweep split), plus MRP_LAUNCH_PLAIN256
+                                    (the lean launch with 256 threads instead of 128).  Results do
+                                    not depend on this choice. */
 } mrp_options;
+
+enum { MRP_LAUNCH_SPLIT = 1 << 12, MRP_LAUNCH_PLAIN256 = 1 << 13 };
 
 typedef struct {
     int32_t cycles;              /* V-cycles run */

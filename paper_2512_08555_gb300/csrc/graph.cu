@@ -3,7 +3,9 @@
 //
 // Per block-size group the graph holds a chain
 //     prologue:  right-hand side f*, its per-problem norms, u = 0
-//                (mixed precision: also the first FP64 outer residual and a check)
+//                (mixed precision: also the first refinement step, FP32
+//                cycles on the problem itself, its FP64 outer residual and a
+//                check, which may skip the loop)
 //     WHILE loop (conditional node): one V-cycle (FP64), or one refinement
 //                step (FP32 correction cycles + FP64 accumulation + FP64 outer
 //                residual), then a check kernel that compares every
@@ -27,8 +29,7 @@ namespace mrp {
 // refinement steps, status.
 __global__ void k_loop_check(const unsigned long long* __restrict__ res, const unsigned long long* __restrict__ fstar,
                              int np, double tol, int* __restrict__ ctr, double* __restrict__ rel_out, int mixed, int inner,
-                             int max_cycles, int max_ir, int count_step, int need_step,
-                             cudaGraphConditionalHandle hc) {
+                             int max_cycles, int max_ir, int count_step, cudaGraphConditionalHandle hc) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     bool all = true, bad = false;
     for (int p = 0; p < np; ++p) {
@@ -37,10 +38,6 @@ __global__ void k_loop_check(const unsigned long long* __restrict__ res, const u
         const double rel = r / (f > 0.0 ? f : 1.0);
         rel_out[p] = rel;
         if (!(rel < tol)) all = false;
-        // need_step 1: a nonzero first residual takes a refinement step; 2: the
-        // first check never stops (Cauchy rule with refinement: the first
-        // increment is the first step's)
-        if (need_step == 2 || (need_step == 1 && rel > 0.0)) all = false;
         if (!isfinite(rel)) bad = true;
     }
     if (count_step) {
@@ -111,10 +108,12 @@ static int build_group(Handle& h, cudaGraph_t G, cudaStream_t cs, const double* 
     const unsigned long long* num = h.slot(cauchy ? 2 : 1);
     const unsigned long long* den = h.slot(cauchy ? 3 : 0);
     if (h.mixed) {
-        outer_residual_launch(h, cs, true);
+        // (one level: no FP32 cycles; the FP64 level-0 convolution is the answer)
+        if (h.L >= 1) first_step_launch(h, cs);
+        outer_residual_launch(h, cs);
         if (cauchy) cauchy_launch(h, cs);
         k_loop_check<<<1, 32, 0, cs>>>(num, den, np, h.tol, h.loop_ctr, h.loop_rel, 1, h.inner_cycles,
-                                       h.max_cycles, h.max_ir, 0, cauchy ? 2 : (h.L >= 1 ? 1 : 0), hc);
+                                       h.max_cycles, h.max_ir, h.L >= 1 ? 1 : 0, hc);
     }
     std::vector<cudaGraphNode_t> deps;
     int rc = tail_of(cs, deps);
@@ -143,7 +142,7 @@ static int build_group(Handle& h, cudaGraph_t G, cudaStream_t cs, const double* 
         else leaf_residual_launch(h, cs);
     }
     k_loop_check<<<1, 32, 0, cs>>>(num, den, np, h.tol, h.loop_ctr, h.loop_rel, h.mixed ? 1 : 0,
-                                   h.inner_cycles, h.max_cycles, h.max_ir, 1, 0, hc);
+                                   h.inner_cycles, h.max_cycles, h.max_ir, 1, hc);
     restore_buffers(h, p0, cs);
     if (cudaStreamEndCapture(cs, &dummy) != cudaSuccess) return MRP_ERR_CUDA;
     h.gl_body = h.launches - l0 + 1;

@@ -319,15 +319,15 @@ __device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict
 //     d. faces: interpolate along the second tangential axis.
 //     Work items are ordered so that the lanes of a warp share the parity of
 //     the interpolated coordinate (the same stencil length).
-template <typename T, int I>
-__device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch, const HaloSmem& hs,
-                           const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk, int b, int n,
-                           const Split& sp) {
+template <typename T, int I, bool INTERP = true>
+__device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch,
+                                           const int* __restrict__ rec, const T* __restrict__ Uk, const T* __restrict__ Uc,
+                                           const LevelView& lk, int b, int n, const Split& sp) {
     const int S = n + 2, S2 = S * S, S3 = S2 * S;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int H = sp.H, H2 = sp.H2, H3p = sp.H3p;
     const int h = n >> 1;
-    const int* __restrict__ snbr = hs.rec + REC_SNBR;
+    const int* __restrict__ snbr = rec + REC_SNBR;
     // 1. copied values
     for (int c = tid; c < S2; c += nth) {
         const int Y = c / S, X = c - Y * S;
@@ -354,13 +354,20 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
             }
         }
     }
-    const int nreg = hs.rec[REC_NREG];
+    if constexpr (!INTERP) {
+        // a block without interpolated regions (the caller guarantees it)
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        return;
+    }
+    const int nreg = rec[REC_NREG];
     constexpr int plo = 4 - I / 2;
     const int TN = tan_n(n, I);
     const int PL = h + I, PL2 = PL * PL;
     const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
-    const int* __restrict__ pnbr = hs.rec + REC_PNBR;
-    const int* __restrict__ pch = hs.rec + REC_PCH;
+    const int* __restrict__ pnbr = rec + REC_PNBR;
+    const int* __restrict__ pch = rec + REC_PCH;
     // 2a. coarse patch over the hull, copied together with the box; patch
     //     index p on an axis is coarse coordinate base + p relative to the
     //     parent's origin.  A covered coarse node takes its coincident fine
@@ -369,8 +376,8 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
     if (nreg > 0) {
         const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
         const int bs0 = (bx & 1) * h - 4 + plo, bs1 = (by & 1) * h - 4 + plo, bs2 = (bz & 1) * h - 4 + plo;
-        const int lo0 = hs.rec[REC_LO], lo1 = hs.rec[REC_LO + 1], z0 = hs.rec[REC_LO + 2];
-        const int L0 = hs.rec[REC_HI] - lo0, L1 = hs.rec[REC_HI + 1] - lo1, z1 = hs.rec[REC_HI + 2];
+        const int lo0 = rec[REC_LO], lo1 = rec[REC_LO + 1], z0 = rec[REC_LO + 2];
+        const int L0 = rec[REC_HI] - lo0, L1 = rec[REC_HI + 1] - lo1, z1 = rec[REC_HI + 2];
         for (int c = tid; c < L0 * L1; c += nth) {
             const int q1 = c / L0, q0 = c - q1 * L0;
             const int px = lo0 + q0, py = lo1 + q1;
@@ -406,11 +413,11 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
 #pragma unroll
     for (int m = 0; m < I; ++m) w[m] = T(midw<I>(m));
     const unsigned mTN = magic_of(TN);
-    const int* __restrict__ rdir = hs.rec + REC_RDIR;
-    const int* __restrict__ roff = hs.rec + REC_ROFF;
-    const int* __restrict__ raoff = hs.rec + REC_RAOFF;
-    const int* __restrict__ coff = hs.rec + REC_COFF;
-    const int* __restrict__ doff = hs.rec + REC_DOFF;
+    const int* __restrict__ rdir = rec + REC_RDIR;
+    const int* __restrict__ roff = rec + REC_ROFF;
+    const int* __restrict__ raoff = rec + REC_RAOFF;
+    const int* __restrict__ coff = rec + REC_COFF;
+    const int* __restrict__ doff = rec + REC_DOFF;
     // Each pass is one flat loop over the items of all regions; the region of
     // item f is the last one whose first item is <= f.
     auto region_at = [&](const int* __restrict__ off, int f) {
@@ -423,7 +430,7 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
         return lo;
     };
     // 2b. reduction along the normal axes: one value per coarse tangential node
-    const int nB = hs.rec[REC_NTOT], nC = hs.rec[REC_NTOT + 1], nD = hs.rec[REC_NTOT + 2];
+    const int nB = rec[REC_NTOT], nC = rec[REC_NTOT + 1], nD = rec[REC_NTOT + 2];
     for (int f = tid; f < nB; f += nth) {
         const int r = region_at(roff, f);
         const Region g = region_of(rdir[r], PL, up);
@@ -577,6 +584,31 @@ __device__ __forceinline__ Pair pair_of(int p) {
     return q;
 }
 
+// Writes planes Z = 1..16 of a block-size-16 FP32 box, ghost rows and
+// columns included, from the split box in shared memory to the block's 18^3
+// array: one contiguous run of 16 x 18^2 floats that starts on a 16-byte
+// boundary (18^3 and 18^2 are multiples of 4), written with 16-byte stores,
+// so that every 32-byte sector is written whole (no read-modify-write of
+// partly written sectors in DRAM).  On levels >= 1 nothing reads the stored
+// ghost layer of a field (the stencil kernels rebuild it from the
+// neighbours' interiors and the coarse level, the prolongation reads the
+// neighbours' interiors), so the halo values stored there are harmless.
+__device__ __forceinline__ void store_planes16(float* __restrict__ Ub, const float* __restrict__ su, const Split& sp,
+                                               int nthreads) {
+    constexpr int S = 18, S2 = S * S, NV = 16 * S2 / 4;
+    float4* __restrict__ dst = reinterpret_cast<float4*>(Ub + S2);
+    for (int t = threadIdx.x; t < NV; t += nthreads) {
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = 4 * t + e;
+            const int Z = 1 + q / S2, r = q - (Z - 1) * S2, Y = r / S, X = r - Y * S;
+            v[e] = su[sp.at(X, Y, Z)];
+        }
+        dst[t] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 // ---------------------------------------------------------------- smoother
 // One Gauss-Seidel iteration (Sec. 3.1): 8 colours c = (x&1) + 2(y&1) + 4(z&1),
 // u <- (den h^2 f - offcentre) / c; reads Uin, writes the interior to Uout.
@@ -602,7 +634,7 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
     // ghost layer
     const bool early = fmode == 2 || (fmode == 1 && hs.rec[REC_NREG] == 0);
     if (early) load_rhs(fs, F, b, n);
-    build_halo<T, I>(su, pool, patch, hs, Uin, Uc, lk, b, n, sp);
+    build_halo<T, I>(su, pool, patch, hs.rec, Uin, Uc, lk, b, n, sp);
     if (fmode == 1 && !early) {
         load_rhs(fs, F, b, n);
         cp_async_wait<0>();
@@ -662,9 +694,13 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
             __syncthreads();
         }
     }
-    // interior back to global, one thread per (x, y) column
     const int S = n + 2, S2 = S * S;
     T* Ob = Uout + (size_t)b * S2 * S;
+    if constexpr (NC == 16 && sizeof(T) == 4) {
+        store_planes16(reinterpret_cast<float*>(Ob), reinterpret_cast<const float*>(su), sp, blockDim.x);
+        return;
+    }
+    // interior back to global, one thread per (x, y) column
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
         const int y = c / n, x = c - y * n;
         const int X = x + 1, Y = y + 1;
@@ -675,6 +711,59 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
             gcol[(2 * m + 2) * S2] = scol[(m + 1) * sp.H2];
         }
     }
+}
+
+// Gauss-Seidel sweep of a block without interpolated ghost regions (block
+// size 16, FP32): the same arithmetic, node pairs and lane order as
+// k_smooth_fused<M, float, I, 16>, with less shared memory per CTA (the split
+// box and the 28-int head of the record; no interpolation scratch, no staged
+// right-hand side) so that more CTAs fit on an SM.  Each thread's 2 x 8 x KP
+// right-hand-side values are loaded into registers before the box copy and
+// consumed by the colour sweeps.  Blocks order[first + blockIdx.x].
+template <int M, int NT>
+__global__ void __launch_bounds__(NT) k_smooth_plain16(float* __restrict__ Uout, const float* __restrict__ Uin,
+                                                       const float* __restrict__ F, LevelView lk, float h2den, int first) {
+    constexpr int n = 16, NP = 256, KP = NP / NT;
+    static_assert(NP % NT == 0, "CTA size divides the 256 pairs of a colour");
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    float* su = reinterpret_cast<float*>(fz_smem);
+    __shared__ __align__(16) int rec[28];
+    const Split sp = split_of<float>(n);
+    const int b = lk.order[first + blockIdx.x];
+    if (threadIdx.x < 7) cp_async16(&rec[4 * threadIdx.x], lk.rec + (size_t)b * REC_INTS + 4 * threadIdx.x);
+    cp_async_commit();
+    float fa[8][KP], fb[8][KP];
+    const float* __restrict__ Fb = F + (size_t)b * (n * n * n);
+#pragma unroll
+    for (int col = 0; col < 8; ++col) {
+        const int fo = (((col >> 2) & 1) * n + ((col >> 1) & 1)) * n + (col & 1);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const Pair q = pair_of(threadIdx.x + k * NT);
+            const int fi = ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + fo;
+            fa[col][k] = ldg_now(Fb + fi);
+            fb[col][k] = ldg_now(Fb + fi + 2);
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    build_halo<float, M + 2, false>(su, nullptr, nullptr, rec, Uin, nullptr, lk, b, n, sp);
+    const float inv_c = 1.0f / float(LW<M>::c);
+#pragma unroll
+    for (int col = 0; col < 8; ++col) {
+        const Col c = colour(col, sp, n);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const Pair q = pair_of(threadIdx.x + k * NT);
+            const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
+            const float sa = offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+            const float sb = offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+            su[b0 + c.dX + c.dY + c.dZ] = (h2den * fa[col][k] - sa) * inv_c;
+            su[b0 + 1 + c.dX + c.dY + c.dZ] = (h2den * fb[col][k] - sb) * inv_c;
+        }
+        __syncthreads();
+    }
+    store_planes16(Uout + (size_t)b * 5832, su, sp, NT);
 }
 
 // ---------------------------------------------------------------- residual r = f - L u (all nodes)
@@ -693,7 +782,7 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
     record_prologue(hs, lk, b);
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
+    build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     if constexpr (NC != 0 && sizeof(T) == 4) {
         // pairs of nodes adjacent along x, as in the smoother
@@ -761,7 +850,7 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
         return;
     }
     record_prologue(hs, lk, b);
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
+    build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     if constexpr (NC != 0 && sizeof(T) == 4) {
         // pairs of nodes adjacent along x, as in the smoother
         constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2;
@@ -829,7 +918,7 @@ __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, c
     cset_init(cs, n >> 1);
     const int b = blocks[blockIdx.x];
     record_prologue(hs, lk, b);
-    build_halo<double, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
+    build_halo<double, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     double m = 0.0;
     if constexpr (NC != 0) {
@@ -908,7 +997,7 @@ __global__ void __launch_bounds__(512) k_halo_dump(T* __restrict__ U, const T* _
     const int S = n + 2, S3 = S * S * S;
     const int b = blockIdx.x;
     record_prologue(hs, lk, b);
-    build_halo<T, I>(su, pool, patch, hs, U, Uc, lk, b, n, sp);
+    build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     for (int t = threadIdx.x; t < S3 - n * n * n; t += blockDim.x) {
         int x, y, z;
         shell_coords(t, S, x, y, z);
@@ -1171,11 +1260,21 @@ static void attrs_halo_dump() {
 }
 
 template <int M, typename T>
-static void smooth_m(T* Uout, const T* Uin, const T* F, const T* Uc, const LevelView& lk, int n, T h2den, int fst,
-                     int ct, size_t sm, cudaStream_t s) {
+static void smooth_m(T* Uout, const T* Uin, const T* F, const T* Uc, const LevelView& lk, int nblocks, int n, T h2den,
+                     int fst, int ct, size_t sm, cudaStream_t s) {
     constexpr int I = M + 2;
-    if (n == NC_FIXED) k_smooth_fused<M, T, I, NC_FIXED><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
-    else k_smooth_fused<M, T, I, 0><<<lk.nb, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
+    if (nblocks == 0) return;
+    if (n == NC_FIXED) k_smooth_fused<M, T, I, NC_FIXED><<<nblocks, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
+    else k_smooth_fused<M, T, I, 0><<<nblocks, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
+}
+template <int M>
+static void smooth_plain_m(float* Uout, const float* Uin, const float* F, const LevelView& lk, float h2den, bool nt256,
+                           cudaStream_t s) {
+    const int cnt = lk.nb - lk.nint;
+    if (cnt == 0) return;
+    const size_t sm = sizeof(float) * 8 * (size_t)split_h3p(16, 4);
+    if (nt256) k_smooth_plain16<M, 256><<<cnt, 256, sm, s>>>(Uout, Uin, F, lk, h2den, lk.nint);
+    else k_smooth_plain16<M, 128><<<cnt, 128, sm, s>>>(Uout, Uin, F, lk, h2den, lk.nint);
 }
 template <int M, typename T>
 static void residual_m(T* R, const T* U, const T* F, const T* Uc, const LevelView& lk, int n, T scale, int ct, size_t sm,
@@ -1217,14 +1316,29 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
         if (fused_smem<T>(n, M + 2, 1) <= (size_t)MAX_DYN_SMEM) fmode = 1;
         const size_t s2 = fused_smem<T>(n, M + 2, 2);
         const size_t per_sm = 228 * 1024, per_cta = s2 + sizeof(HaloSmem) + 1024;
-        if (s2 <= (size_t)MAX_DYN_SMEM && (size_t)lk.nb <= (size_t)nsm * (per_sm / per_cta)) fmode = 2;
+        const size_t nlaunch = (sizeof(T) == 4 && n == NC_FIXED && (nt & SMOOTH_SPLIT)) ? (size_t)lk.nint : (size_t)lk.nb;
+        if (s2 <= (size_t)MAX_DYN_SMEM && nlaunch <= (size_t)nsm * (per_sm / per_cta)) fmode = 2;
     }
     const int fst = fmode;
     const size_t sm = fused_smem<T>(n, M + 2, fmode);
-    const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
-    if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<2>::den), fst, ct, sm, s);
-    if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<4>::den), fst, ct, sm, s);
-    if (M == 6) smooth_m<6, T>(Uout, Uin, F, Uc, lk, n, T(h2 * LW<6>::den), fst, ct, sm, s);
+    const int ct = cta_size_fixed(n, nt & SMOOTH_NT_MASK, sizeof(T) == 4);
+    // split: interface blocks (first in lk.order) here, the others in the lean kernel
+    const bool split = sizeof(T) == 4 && n == NC_FIXED && (nt & SMOOTH_SPLIT);
+    const int ngen = split ? lk.nint : lk.nb;
+    if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, ngen, n, T(h2 * LW<2>::den), fst, ct, sm, s);
+    if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, ngen, n, T(h2 * LW<4>::den), fst, ct, sm, s);
+    if (M == 6) smooth_m<6, T>(Uout, Uin, F, Uc, lk, ngen, n, T(h2 * LW<6>::den), fst, ct, sm, s);
+    if constexpr (sizeof(T) == 4) {
+        if (split) {
+            const bool nt256 = (nt & SMOOTH_PLAIN256) != 0;
+            float* uo = reinterpret_cast<float*>(Uout);
+            const float* ui = reinterpret_cast<const float*>(Uin);
+            const float* ff = reinterpret_cast<const float*>(F);
+            if (M == 2) smooth_plain_m<2>(uo, ui, ff, lk, float(h2 * LW<2>::den), nt256, s);
+            if (M == 4) smooth_plain_m<4>(uo, ui, ff, lk, float(h2 * LW<4>::den), nt256, s);
+            if (M == 6) smooth_plain_m<6>(uo, ui, ff, lk, float(h2 * LW<6>::den), nt256, s);
+        }
+    }
 }
 
 template <typename T>

@@ -118,20 +118,6 @@ void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int n
     k_accumulate_f<<<nblocks, 256, 0, s>>>(F64, F32, blocks, n);
 }
 
-// U64 = U32 on every node of every block's (n+2)^3 box, ghost layer and (on
-// level 0) the exterior ring included.
-__global__ void k_cast_box(double* __restrict__ U64, const float* __restrict__ U32, size_t count) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        U64[i] = (double)U32[i];
-}
-
-void launch_cast_box(double* U64, const float* U32, int nb, int n, cudaStream_t s) {
-    const size_t S = n + 2, count = (size_t)nb * S * S * S;
-    if (count == 0) return;
-    const int grid = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
-    k_cast_box<<<grid, 256, 0, s>>>(U64, U32, count);
-}
-
 // Cauchy stop rule (Sec. 3): over the interiors of the given leaf blocks,
 // max |u - u_prev| into num[prob] and max |u| into den[prob]; then u_prev = u.
 __global__ void k_cauchy(double* __restrict__ Uprev, const double* __restrict__ U, const int* __restrict__ blocks, int n,

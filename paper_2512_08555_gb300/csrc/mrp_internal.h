@@ -37,6 +37,13 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+// Read-only global load issued where it stands (volatile: not moved past the
+// copies and barriers that follow), for values prefetched into registers.
+__device__ __forceinline__ float ldg_now(const float* p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];\n" : "=f"(v) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 #endif
@@ -68,6 +75,7 @@ struct LevelView {
     const int* order;      // [nb] launch order: blocks with interpolated ghosts first
     const int* prob;       // [nb] problem of each block (per-problem norms of a batched handle)
     const int* rec;        // [nb][REC_INTS] neighbourhood records (below)
+    int nint;              // blocks with interpolated ghost regions; they come first in `order`
 };
 
 // Per-block neighbourhood record, REC_INTS ints, which the fused stencil
@@ -92,6 +100,7 @@ constexpr int REC_INTS = 412;    // a multiple of 4
 // Host + device tables of one level, plus its FP64 fields.
 struct Level {
     int nb = 0, nleaf = 0, ncov = 0;
+    int nint = 0;                     // blocks with interpolated ghost regions (first in h_order)
     std::vector<int> h_coords, h_nbr, h_parent, h_octant, h_children, h_leaf_blocks, h_cov_blocks, h_order;
     std::vector<uint8_t> h_is_leaf;
     std::vector<int> h_prob, h_rec;
@@ -103,7 +112,7 @@ struct Level {
     double* Uprev = nullptr;          // [nb][n^3] leaf values of the previous iterate (Cauchy stop rule only)
     float *U32 = nullptr, *F32 = nullptr, *R32 = nullptr, *H32 = nullptr;   // mixed precision inner cycles
     float* U32alt = nullptr;
-    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order, prob, rec}; }
+    LevelView view() const { return LevelView{nb, coords, nbr, parent, octant, children, is_leaf, order, prob, rec, nint}; }
 };
 
 // One padded FFT axis: length, radix sequence, twiddles exp(-2 pi i m / P).
@@ -189,6 +198,7 @@ struct Handle {
     static constexpr int MAXL = 32;
     int nt_smooth[2][MAXL], nt_res[2][MAXL], nt_fas[2][MAXL], nt_leafres[MAXL];
     bool tuned = false;
+    int launch_override = 0;          // mrp_options.launch (0: autotune)
     // device-side loop control of the graph-captured solve (graph.cu)
     int* loop_ctr = nullptr;          // [4]: cycles, refinement steps, status, unused
     double* loop_rel = nullptr;       // [nprob] relative residuals
@@ -207,7 +217,8 @@ struct Handle {
 inline double level_h(const Handle& h, int k) { return h.h0 / (double)(1 << k); }
 inline int64_t n3(const Handle& h) { return (int64_t)h.n * h.n * h.n; }
 inline LevelView view_or_empty(const Handle& h, int k) {
-    return k >= 0 ? h.lv[k].view() : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return k >= 0 ? h.lv[k].view()
+                  : LevelView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
 }
 
 // Per-level base pointers, passed by value to the leaf scatter / gather kernels.
@@ -269,8 +280,8 @@ template <typename T> void vcycle(Handle& h, cudaStream_t s);
 void solve_begin(Handle& h, const double* f, cudaStream_t s);
 void leaf_residual_launch(Handle& h, cudaStream_t s);
 void cauchy_launch(Handle& h, cudaStream_t s);   // Cauchy stop rule into slots 2 (num) and 3 (den)
-// first: the residual at u = 0 (its level-0 solution convolved in FP32)
-void outer_residual_launch(Handle& h, cudaStream_t s, bool first = false);
+void outer_residual_launch(Handle& h, cudaStream_t s);
+void first_step_launch(Handle& h, cudaStream_t s);   // mixed precision: FP32 cycles on the problem itself, from u = 0
 void correction_launch(Handle& h, cudaStream_t s);
 void solve_end(Handle& h, double* u, cudaStream_t s);
 int autotune(Handle& h, cudaStream_t s);
@@ -297,6 +308,11 @@ void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc,
 template <typename T>
 void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
 // stencil kernels with the ghost layer built in shared memory (kernels_fused.cuh, fused_*.cu);
+// Smoother launch choices (the `nt` argument of launch_smooth_fused): the CTA
+// size of the generic kernel in the low bits; SMOOTH_SPLIT (block size 16,
+// FP32) runs the blocks without interpolated ghost regions in a separate
+// launch of the lean kernel, whose CTA size is 256 with SMOOTH_PLAIN256, else 128.
+constexpr int SMOOTH_NT_MASK = 0xFFF, SMOOTH_SPLIT = MRP_LAUNCH_SPLIT, SMOOTH_PLAIN256 = MRP_LAUNCH_PLAIN256;
 // fused_smem_bytes: their dynamic shared memory for block size n, order M and
 // element size el (bytes), without a staged right-hand side
 size_t fused_smem_bytes(int n, int M, int el);
@@ -364,7 +380,6 @@ void launch_c0(double* c0, float* off32, const double* U0, const double* U1, con
 void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int nleaf, int n, bool zero, cudaStream_t s);
 void launch_accumulate_u(double* U64, const float* U32, int nb, int n, cudaStream_t s);
 void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int nblocks, int n, cudaStream_t s);
-void launch_cast_box(double* U64, const float* U32, int nb, int n, cudaStream_t s);
 // Cauchy stop rule: max |u - u_prev| and max |u| over leaf interiors per problem; u_prev = u
 void launch_cauchy(double* Uprev, const double* U, const int* leaf_blocks, int nleaf, int n, unsigned long long* num,
                    unsigned long long* den, const int* prob, cudaStream_t s);

@@ -187,6 +187,8 @@ int build_forest(Handle& h, const std::vector<ProblemDesc>& list, std::string& w
         };
         for (int pass = 0; pass < 2; ++pass)
             for (int b = 0; b < lv.nb; ++b) if (interp(b) == (pass == 0)) lv.h_order.push_back(b);
+        lv.nint = 0;
+        for (int b = 0; b < lv.nb; ++b) lv.nint += interp(b) ? 1 : 0;
         std::stable_partition(lv.h_leaf_blocks.begin(), lv.h_leaf_blocks.end(), interp);
     }
     // level-0 list ranges per problem (level 0 never interpolates, so its lists stay in block order)
@@ -465,11 +467,20 @@ template <typename T> static constexpr int pidx() { return sizeof(T) == 4 ? 1 : 
 // Launches of a fused stencil kernel on a level.
 static int fused_launches(const Level& lv) { return lv.nb > 0 ? 1 : 0; }
 
+// Kernels one smoother launch runs: two when the level's sweep is split into
+// interface blocks and the others (SMOOTH_SPLIT), else one.
+static int smooth_launches(const Handle& h, const Level& lv, int nt, bool fp32) {
+    if (lv.nb == 0) return 0;
+    const bool split = fp32 && h.n == 16 && (nt & SMOOTH_SPLIT);
+    return split ? (lv.nint > 0 ? 1 : 0) + (lv.nb > lv.nint ? 1 : 0) : 1;
+}
+
 // One Gauss-Seidel sweep with its ghost layer built in the kernel; reads the
 // current buffer, writes the other, then the two swap.
 template <typename T>
 static void smooth(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h), fused_launches(h.lv[k]));
+    PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h),
+                  smooth_launches(h, h.lv[k], h.nt_smooth[pidx<T>()][k], sizeof(T) == 4));
     const double hk = level_h(h, k);
     launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
                            view_or_empty(h, k - 1), h.n, h.M, hk * hk, h.nt_smooth[pidx<T>()][k], s);
@@ -590,9 +601,14 @@ struct SolveState {
 // and F, H of covered blocks).
 template <typename T>
 static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
-    const int cand[3] = {128, 256, 512};
+    const std::vector<int> cta = {128, 256, 512};
+    // the smoother of FP32 block-size-16 levels may also split its sweep
+    std::vector<int> smooth_cand = cta;
+    if (sizeof(T) == 4 && h.n == 16)
+        for (int c : {128, 256})
+            for (int x : {SMOOTH_SPLIT, SMOOTH_SPLIT | SMOOTH_PLAIN256}) smooth_cand.push_back(c | x);
     constexpr int pi = pidx<T>();
-    auto pick = [&](auto&& launch) {
+    auto pick_from = [&](const std::vector<int>& cand, auto&& launch) {
         float best = 1e30f;
         int arg = 256;
         for (int c : cand) {
@@ -608,11 +624,12 @@ static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_
         }
         return arg;
     };
+    auto pick = [&](auto&& launch) { return pick_from(cta, launch); };
     for (int k = 0; k <= h.L; ++k) {
         const double hk = level_h(h, k);
         Level& lv = h.lv[k];
         if (k >= 1) {
-            h.nt_smooth[pi][k] = pick([&](int nt) {
+            h.nt_smooth[pi][k] = pick_from(smooth_cand, [&](int nt) {
                 launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), lv.view(),
                                        view_or_empty(h, k - 1), h.n, h.M, hk * hk, nt, s);
             });
@@ -645,6 +662,17 @@ static void tune_defaults(Handle& h) {
 int autotune(Handle& h, cudaStream_t s) {
     if (h.tuned) return MRP_OK;
     tune_defaults(h);
+    if (h.launch_override) {
+        const int ct = h.launch_override & SMOOTH_NT_MASK;
+        for (int p = 0; p < 2; ++p)
+            for (int k = 0; k < Handle::MAXL; ++k) {
+                h.nt_smooth[p][k] = h.launch_override;
+                h.nt_res[p][k] = h.nt_fas[p][k] = ct;
+                h.nt_leafres[k] = ct;
+            }
+        h.tuned = true;
+        return MRP_OK;
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return MRP_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MRP_ERR_CUDA; }
@@ -705,30 +733,10 @@ void leaf_residual_launch(Handle& h, cudaStream_t s) {
 // system (leaf rows, and on covered level-0 nodes the mismatch c0 between the
 // convolution of the accumulated FP64 source and the injection of level 1),
 // FP32 correction cycles from zero, FP64 accumulation.
-void outer_residual_launch(Handle& h, cudaStream_t s, bool first) {
+void outer_residual_launch(Handle& h, cudaStream_t s) {
     Level& l0 = h.lv[0];
     const double inv_h02 = 1.0 / (h.h0 * h.h0);
-    if (first && h.L >= 1) {
-        // At u = 0 the level-0 solution only feeds the first correction,
-        // which the FP32 cycles compute to FP32 accuracy anyway: convolve
-        // in FP32.  Every later outer residual convolves in FP64 from the
-        // accumulated source, so the refinement still converges in FP64;
-        // the stop rule takes at least one refinement step after this
-        // residual unless it is exactly zero.  (With one level the level-0
-        // solve is the whole answer and stays FP64.)
-        {
-            PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 2);
-            launch_cast_rhs(l0.F32, l0.F, l0.leaf_blocks, l0.nleaf, h.n, false, s);
-            launch_cast_rhs(l0.F32, l0.F, l0.cov_blocks, l0.ncov, h.n, false, s);
-        }
-        coarse_solve<float>(h, s);
-        // the whole box, exterior ring included: later steps read the ring
-        // as the last level-0 solve's values
-        PhaseScope ps(h, s, PH_OTHER, l0.nb * n3(h), 1);
-        launch_cast_box(l0.U, ucur<float>(h, 0), l0.nb, h.n, s);
-    } else {
-        coarse_solve<double>(h, s);
-    }
+    coarse_solve<double>(h, s);
     cudaMemsetAsync(h.slot(1), 0, sizeof(unsigned long long) * h.nprob(), s);
     for (int k = h.L; k >= 2; --k) inject_level<double>(h, k, s);
     if (h.L >= 1) {
@@ -742,6 +750,27 @@ void outer_residual_launch(Handle& h, cudaStream_t s, bool first) {
                              h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1),
                              h.nt_leafres[k], s);
     }
+}
+
+// First refinement step, from u = 0: the FP32 cycles solve the problem itself
+// (f* on the leaves of every level, level 0 included; no offset on the
+// level-1 -> 0 injection), and the FP64 state takes their result (u on levels
+// >= 1, the level-0 source on covered nodes).  The correction from u = 0
+// solves the problem itself, so no FP64 residual precedes this step.
+void first_step_launch(Handle& h, cudaStream_t s) {
+    const size_t S = h.n + 2;
+    Level& l0 = h.lv[0];
+    {
+        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, h.L + 1);
+        for (int k = 0; k <= h.L; ++k)
+            launch_cast_rhs(h.lv[k].F32, h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, false, s);
+    }
+    cudaMemsetAsync(h.off32, 0, sizeof(float) * l0.nb * n3(h), s);
+    for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U32, 0, sizeof(float) * h.lv[k].nb * S * S * S, s);
+    for (int c = 0; c < h.inner_cycles; ++c) vcycle<float>(h, s);
+    PhaseScope ps(h, s, PH_OTHER, h.total_nodes, h.L + 1);
+    for (int k = 1; k <= h.L; ++k) launch_accumulate_u(h.lv[k].U, h.lv[k].U32, h.lv[k].nb, h.n, s);
+    launch_accumulate_f(l0.F, l0.F32, l0.cov_blocks, l0.ncov, h.n, s);
 }
 
 void correction_launch(Handle& h, cudaStream_t s) {
@@ -780,12 +809,15 @@ static void solve_step(Handle& h, cudaStream_t s, SolveState& st) {
         else leaf_residual_launch(h, s);
         return;
     }
-    if (st.started) {
-        correction_launch(h, s);
+    // (one level: the FP64 level-0 convolution of the outer residual is the
+    // whole answer, so the first pass runs no FP32 cycles and counts no step)
+    if (st.started || h.L >= 1) {
+        if (st.started) correction_launch(h, s);
+        else first_step_launch(h, s);
         st.cycles += h.inner_cycles;
         ++st.ir;
     }
-    outer_residual_launch(h, s, !st.started);
+    outer_residual_launch(h, s);
     if (cauchy) cauchy_launch(h, s);
     st.started = true;
 }
@@ -809,10 +841,6 @@ static int solve_check(Handle& h, cudaStream_t s, SolveState& st) {
             return MRP_OK;
         }
         if (!(st.rel[p] < h.tol)) all = false;
-        // first residual: FP32 level 0
-        if (!cauchy && h.mixed && h.L >= 1 && st.ir == 0 && st.rel[p] > 0.0) all = false;
-        // Cauchy rule with refinement: the first increment is the first step's
-        if (cauchy && h.mixed && st.ir == 0) all = false;
     }
     if (all) st.done = true;
     else if (!h.mixed && st.cycles >= h.max_cycles) st.done = true;
@@ -865,6 +893,11 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
     if (opt->stop_rule != MRP_STOP_RESIDUAL && opt->stop_rule != MRP_STOP_CAUCHY) return MRP_ERR_INVALID_ARG;
     if (opt->precision != MRP_FP64 && opt->precision != MRP_MIXED) return MRP_ERR_INVALID_ARG;
     if (opt->inner_cycles < 0 || opt->max_outer < 0) return MRP_ERR_INVALID_ARG;
+    if (opt->launch != 0) {
+        const int ct = opt->launch & SMOOTH_NT_MASK;
+        if ((ct != 128 && ct != 256 && ct != 512) || (opt->launch & ~(SMOOTH_NT_MASK | SMOOTH_SPLIT | SMOOTH_PLAIN256)))
+            return MRP_ERR_INVALID_ARG;
+    }
     // problems (forest, component) in the caller's layout order, grouped by block size
     std::map<int, std::vector<ProblemDesc>> by_n;
     int64_t off = 0;
@@ -890,6 +923,7 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
         h.mixed = opt->precision == MRP_MIXED;
         h.inner_cycles = opt->inner_cycles > 0 ? opt->inner_cycles : 4;
         h.max_ir = opt->max_outer > 0 ? opt->max_outer : 12;
+        h.launch_override = opt->launch;
         tune_defaults(h);
         std::string why;
         rc = build_forest(h, kv.second, why);

@@ -28,6 +28,7 @@ EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_
             "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph",
             "mrp_solve_host", "mrp_fma_peak"]
 ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
+LAUNCH_SPLIT, LAUNCH_PLAIN256 = 1 << 12, 1 << 13
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
 
@@ -47,7 +48,7 @@ class _Forest(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("order", C.c_int32), ("tol", C.c_double), ("stop_rule", C.c_int32), ("max_cycles", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("inner_cycles", C.c_int32),
-                ("max_outer", C.c_int32)]
+                ("max_outer", C.c_int32), ("launch", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -120,7 +121,7 @@ class Solver:
     """
 
     def __init__(self, forest, order=4, tol=1e-10, max_cycles=50, nu1=3, nu2=3, precision="fp64",
-                 inner_cycles=0, max_outer=0, ncomp=1, stop="residual"):
+                 inner_cycles=0, max_outer=0, ncomp=1, stop="residual", launch=0):
         import torch  # noqa: F401  (CUDA context and memory come from torch)
         self.lib = load_library()
         forests = list(forest) if isinstance(forest, (list, tuple)) else [forest]
@@ -154,6 +155,7 @@ class Solver:
         op.nu1, op.nu2 = int(nu1), int(nu2)
         op.precision = {"fp64": 0, "mixed": 1}[precision]
         op.inner_cycles, op.max_outer = int(inner_cycles), int(max_outer)
+        op.launch = int(launch)
         self.h = C.c_void_p()
         _check(self.lib.mrp_create(C.byref(self.h), arr, len(forests), C.byref(op)), "mrp_create")
 

@@ -111,20 +111,20 @@ def test_mixed_five_levels():
 
 
 def test_mixed_zero_source_and_first_step():
-    """A zero source returns exactly zero; a nonzero one takes at least one
-    refinement step after the first (FP32-convolved) outer residual and ends
-    at FP64 accuracy."""
+    """A zero source returns exactly zero after the one refinement step that
+    always runs; a loose tolerance stops after that first step (FP32 cycles on
+    the problem itself); a tight one ends at FP64 accuracy."""
     from paper_2512_08555_gb300.mrp import Solver
     desc = synth.adaptive_forest((4, 4, 4), 8, (-1, -1, -1), 2 / 32, 1, _all)
     s = Solver(desc, order=4, tol=1e-10, max_cycles=60, precision="mixed")
     z = torch.zeros((desc.n_leaves, 8, 8, 8), dtype=torch.float64, device="cuda")
     u0, st0 = s.solve(z)
-    assert st0.ir_steps == 0 and float(u0.abs().max()) == 0.0
+    assert st0.ir_steps == 1 and float(u0.abs().max()) == 0.0
     ug0, _ = s.solve_graph(z)
     assert float(ug0.abs().max()) == 0.0
     f = torch.from_numpy(synth.sample_leaves(desc, synth.c4_bumps(4, k=3, r_lo=0.2, r_hi=0.3))).cuda()
     u, st = Solver(desc, order=4, tol=0.5, max_cycles=60, precision="mixed").solve(f)
-    assert st.ir_steps >= 1
+    assert st.ir_steps == 1 and st.residual < 0.5
     up, _ = Solver(desc, order=4, tol=1e-12, max_cycles=60).solve(f)
     um, stm = s.solve(f)
     assert stm.residual < 1e-10
