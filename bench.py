@@ -609,11 +609,12 @@ def run_profile_case(args):
         desc, src = synth.config2(0)
     f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
     s = Solver(desc, order=args.order, tol=TOL, max_cycles=MAX_CYCLES, precision="mixed",
-               inner_cycles=args.inner_cycles)
+               inner_cycles=args.inner_cycles, launch=args.launch)
     for _ in range(args.warmup + args.steps):
         s.solve(f)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": args.profile_case, "leaf_nodes": int(desc.leaf_nodes)}))
+    print(json.dumps({"profile_case": args.profile_case, "leaf_nodes": int(desc.leaf_nodes), "launch": args.launch,
+                      "levels": [int((desc.leaf_level == k).sum()) for k in range(desc.max_level + 1)]}))
     return 0
 
 
@@ -629,6 +630,8 @@ def main():
     ap.add_argument("--inner-cycles", type=int, default=4, help="FP32 cycles per refinement step of the chosen form")
     ap.add_argument("--profile-case", choices=["headline", "three_level", "five_level_5cube", "fft_large"],
                     default=None, help="run the chosen solver on one workload without timing (for ncu)")
+    ap.add_argument("--launch", type=int, default=0,
+                    help="--profile-case only: fixed launch choice (mrp_options.launch; 0 = autotuned)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

@@ -97,17 +97,12 @@ typedef struct {
                                     the stop check, so at least one step runs */
     int32_t inner_cycles;        /* MRP_MIXED: FP32 V-cycles per refinement step (0 = 4) */
     int32_t max_outer;           /* MRP_MIXED: refinement steps at most (0 = 12) */
-    int32_t launch;              /* 0: the CTA size of each stencil kernel and level, and for block
-                                    size 16 in FP32 whether a smoothing sweep runs the blocks
-                                    without interpolated ghosts in a separate leaner launch, are
-                                    chosen by timing at the first solve.  Otherwise a fixed choice
-                                    for every kernel and level: a CTA size (128, 256 or 512) plus
-                                    MRP_LAUNCH_SPLIT (the sweep split), plus MRP_LAUNCH_PLAIN256
-                                    (the lean launch with 256 threads instead of 128).  Results do
-                                    not depend on this choice. */
+    int32_t launch;              /* 0: the CTA size of each stencil kernel and level is chosen by
+                                    timing at the first solve.  Otherwise that size (128, 256 or
+                                    512) for every kernel and level.  Results do not depend on
+                                    this choice. */
 } mrp_options;
 
-enum { MRP_LAUNCH_SPLIT = 1 << 12, MRP_LAUNCH_PLAIN256 = 1 << 13 };
 
 typedef struct {
     int32_t cycles;              /* V-cycles run */

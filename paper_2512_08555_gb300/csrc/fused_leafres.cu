@@ -3,7 +3,7 @@
 
 namespace mrp {
 
-void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
+void launch_leafres_fused(float* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
                           LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, int nt,
                           cudaStream_t s) {
     if (nblocks == 0) return;

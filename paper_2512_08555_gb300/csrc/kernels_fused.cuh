@@ -42,9 +42,10 @@ template <> struct LW<6> { static constexpr double den = 30, c = -128, f = 14, e
 // the colour's nodes with x fastest, then z (see cset_init), so a load
 // touches rows (Y) of h consecutive words at plane distance Hp apart; for
 // FP32, Hp is the value in [H^2, H^2 + 32) that minimises the shared-memory
-// wavefronts of such loads over a colour (h = 8: Hp = 88 = 24 mod 32, four
-// disjoint 8-bank windows, no conflicts).  The two x-parities of a row fall 16
-// banks apart.
+// wavefronts of such loads over a colour; block size 16 uses node pairs with
+// their own lane order (pair_of) and Hp = 84, whose four rows of one z parity
+// fall in disjoint 8-bank windows (no conflicts).  The two x-parities of a row
+// fall 16 banks apart.
 struct Split {
     int H, H2, H3p;      // H2: plane stride Hp
     __device__ __forceinline__ int at(int X, int Y, int Z) const {
@@ -58,7 +59,7 @@ __host__ __device__ inline int split_hp(int n, int el) {
         case 10: return 59;
         case 12: return 70;
         case 14: return 71;
-        case 16: return 88;
+        case 16: return 84;
         case 18: return 105;
         case 20: return 138;
         case 22: return 171;
@@ -82,7 +83,7 @@ __device__ __forceinline__ Split split_of(int n) {
 // A staged right-hand side uses the same colour split without a ghost layer:
 //     fat(x, y, z) = ((z&1)*4 + (y&1)*2 + (x&1)) * F3 + (z>>1) Fp + (y>>1) Fr + (x>>1),
 // h = n/2, F3 >= h Fp.  FP32 strides minimise the wavefronts of a colour's
-// loads: for n = 16 (node pairs along x, see the smoother) Fr = 9, Fp = 72;
+// loads: for n = 16 (node pairs along x, see pair_of) Fr = 9, Fp = 76;
 // otherwise Fr = h and Fp is the best value in [h^2, h^2 + 32); FP64 keeps
 // Fr = h, Fp = h^2.
 __host__ __device__ inline int split_fp(int n, int el) {
@@ -93,7 +94,7 @@ __host__ __device__ inline int split_fp(int n, int el) {
         case 10: return 27;
         case 12: return 38;
         case 14: return 71;
-        case 16: return 72;
+        case 16: return 76;
         case 18: return 105;
         case 20: return 106;
         case 22: return 139;
@@ -103,9 +104,13 @@ __host__ __device__ inline int split_fp(int n, int el) {
 }
 __host__ __device__ inline int split_fr(int n, int el) { return (el == 4 && n == 16) ? 9 : n / 2; }
 // Colour sub-array stride: FP32 pads h Fp to 16 (mod 32) words, so that the
-// two x-parities of a column copy fall 16 banks apart.
+// two x-parities of a column copy fall 16 banks apart; block size 16 pads to
+// 8 (mod 32), which puts the x-parities 8 banks and the y-parities 16 banks
+// apart (a warp's column copy of two rows is then conflict-free) with less
+// shared memory.
 __host__ __device__ inline int split_f3(int n, int el) {
     const int f = (n / 2) * split_fp(n, el);
+    if (el == 4 && n == 16) return f + ((8 - f % 32) % 32 + 32) % 32;
     return el == 4 ? f + ((16 - f % 32) % 32 + 32) % 32 : f;
 }
 
@@ -319,10 +324,13 @@ __device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict
 //     d. faces: interpolate along the second tangential axis.
 //     Work items are ordered so that the lanes of a warp share the parity of
 //     the interpolated coordinate (the same stencil length).
+// Issues the cp.async copies of block b's box (step 1 below) and, for a block
+// with interpolated regions, of its coarse patch (step 2a) without committing
+// them; the caller commits, waits and synchronises before halo_interpolate.
 template <typename T, int I, bool INTERP = true>
-__device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch,
-                                           const int* __restrict__ rec, const T* __restrict__ Uk, const T* __restrict__ Uc,
-                                           const LevelView& lk, int b, int n, const Split& sp) {
+__device__ __forceinline__ void halo_issue(T* __restrict__ su, T* __restrict__ patch, const int* __restrict__ rec,
+                                           const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk,
+                                           int b, int n, const Split& sp) {
     const int S = n + 2, S2 = S * S, S3 = S2 * S;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int H = sp.H, H2 = sp.H2, H3p = sp.H3p;
@@ -354,13 +362,64 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
             }
         }
     }
-    if constexpr (!INTERP) {
-        // a block without interpolated regions (the caller guarantees it)
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
-        return;
+    if constexpr (INTERP) {
+        const int nreg = rec[REC_NREG];
+        constexpr int plo = 4 - I / 2;
+        const int TN = tan_n(n, I);
+        const int PL = h + I, PL2 = PL * PL;
+        const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
+        const int* __restrict__ pnbr = rec + REC_PNBR;
+        const int* __restrict__ pch = rec + REC_PCH;
+        // 2a. coarse patch over the hull, copied together with the box; patch
+        //     index p on an axis is coarse coordinate base + p relative to the
+        //     parent's origin.  A covered coarse node takes its coincident fine
+        //     node from the input level (for this block too: the box holds the
+        //     same values until the caller changes it).
+        if (nreg > 0) {
+            const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
+            const int bs0 = (bx & 1) * h - 4 + plo, bs1 = (by & 1) * h - 4 + plo, bs2 = (bz & 1) * h - 4 + plo;
+            const int lo0 = rec[REC_LO], lo1 = rec[REC_LO + 1], z0 = rec[REC_LO + 2];
+            const int L0 = rec[REC_HI] - lo0, L1 = rec[REC_HI + 1] - lo1, z1 = rec[REC_HI + 2];
+            for (int c = tid; c < L0 * L1; c += nth) {
+                const int q1 = c / L0, q0 = c - q1 * L0;
+                const int px = lo0 + q0, py = lo1 + q1;
+                const int rx = bs0 + px, ry = bs1 + py;
+                const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0), ey = ry < 0 ? -1 : (ry >= n ? 1 : 0);
+                const int lx = rx - ex * n, ly = ry - ey * n;
+                const int ox = lx >= h, oy = ly >= h;
+                const int FX = 2 * lx - ox * n + 1, FY = 2 * ly - oy * n + 1;
+                T* pcol = patch + py * PL + px;
+                for (int pz = z0; pz < z1; ++pz) {
+                    const int rz = bs2 + pz;
+                    const int ez = rz < 0 ? -1 : (rz >= n ? 1 : 0);
+                    const int lz = rz - ez * n;
+                    const int d = dir27(ex, ey, ez);
+                    const int oz = lz >= h;
+                    const int ch = pch[8 * d + ox + 2 * oy + 4 * oz];
+                    if (pch[8 * d] < 0) {
+                        // leaf coarse block
+                        cp_async_el(pcol + pz * PL2, Uc + ((size_t)pnbr[d] * S3 + (size_t)(((lz + 1) * S + ly + 1) * S + lx + 1)));
+                    } else {
+                        // covered coarse node: the coincident fine node of the current level
+                        const int FZ = 2 * lz - oz * n + 1;
+                        cp_async_el(pcol + pz * PL2, Uk + ((size_t)ch * S3 + (size_t)((FZ * S + FY) * S + FX)));
+                    }
+                }
+            }
+        }
     }
+}
+
+// Steps 2b-2d below for block b, whose box and coarse patch copies are
+// complete and visible; returns after a barrier (at once without
+// interpolated regions).
+template <typename T, int I>
+__device__ __forceinline__ void halo_interpolate(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch,
+                                                 const int* __restrict__ rec, const LevelView& lk, int b, int n,
+                                                 const Split& sp) {
+    const int S = n + 2;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int h = n >> 1;
     const int nreg = rec[REC_NREG];
     constexpr int plo = 4 - I / 2;
     const int TN = tan_n(n, I);
@@ -368,46 +427,6 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
     const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
     const int* __restrict__ pnbr = rec + REC_PNBR;
     const int* __restrict__ pch = rec + REC_PCH;
-    // 2a. coarse patch over the hull, copied together with the box; patch
-    //     index p on an axis is coarse coordinate base + p relative to the
-    //     parent's origin.  A covered coarse node takes its coincident fine
-    //     node from the input level (for this block too: the box holds the
-    //     same values until the caller changes it).
-    if (nreg > 0) {
-        const int bx = lk.coords[3 * b], by = lk.coords[3 * b + 1], bz = lk.coords[3 * b + 2];
-        const int bs0 = (bx & 1) * h - 4 + plo, bs1 = (by & 1) * h - 4 + plo, bs2 = (bz & 1) * h - 4 + plo;
-        const int lo0 = rec[REC_LO], lo1 = rec[REC_LO + 1], z0 = rec[REC_LO + 2];
-        const int L0 = rec[REC_HI] - lo0, L1 = rec[REC_HI + 1] - lo1, z1 = rec[REC_HI + 2];
-        for (int c = tid; c < L0 * L1; c += nth) {
-            const int q1 = c / L0, q0 = c - q1 * L0;
-            const int px = lo0 + q0, py = lo1 + q1;
-            const int rx = bs0 + px, ry = bs1 + py;
-            const int ex = rx < 0 ? -1 : (rx >= n ? 1 : 0), ey = ry < 0 ? -1 : (ry >= n ? 1 : 0);
-            const int lx = rx - ex * n, ly = ry - ey * n;
-            const int ox = lx >= h, oy = ly >= h;
-            const int FX = 2 * lx - ox * n + 1, FY = 2 * ly - oy * n + 1;
-            T* pcol = patch + py * PL + px;
-            for (int pz = z0; pz < z1; ++pz) {
-                const int rz = bs2 + pz;
-                const int ez = rz < 0 ? -1 : (rz >= n ? 1 : 0);
-                const int lz = rz - ez * n;
-                const int d = dir27(ex, ey, ez);
-                const int oz = lz >= h;
-                const int ch = pch[8 * d + ox + 2 * oy + 4 * oz];
-                if (pch[8 * d] < 0) {
-                    // leaf coarse block
-                    cp_async_el(pcol + pz * PL2, Uc + ((size_t)pnbr[d] * S3 + (size_t)(((lz + 1) * S + ly + 1) * S + lx + 1)));
-                } else {
-                    // covered coarse node: the coincident fine node of the current level
-                    const int FZ = 2 * lz - oz * n + 1;
-                    cp_async_el(pcol + pz * PL2, Uk + ((size_t)ch * S3 + (size_t)((FZ * S + FY) * S + FX)));
-                }
-            }
-        }
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
     if (nreg == 0) return;
     T w[I];
 #pragma unroll
@@ -535,6 +554,17 @@ __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ p
     __syncthreads();
 }
 
+template <typename T, int I, bool INTERP = true>
+__device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch,
+                                           const int* __restrict__ rec, const T* __restrict__ Uk, const T* __restrict__ Uc,
+                                           const LevelView& lk, int b, int n, const Split& sp) {
+    halo_issue<T, I, INTERP>(su, patch, rec, Uk, Uc, lk, b, n, sp);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    if constexpr (INTERP) halo_interpolate<T, I>(su, pool, patch, rec, lk, b, n, sp);
+}
+
 __host__ __device__ inline int patch_size(int n, int I) {
     const int PL = n / 2 + I;
     return PL * PL * PL;
@@ -570,17 +600,21 @@ __device__ __forceinline__ void record_prologue(HaloSmem& hs, const LevelView& l
 }
 
 
-// Pair p of a colour's nodes for the fixed block size 16 (h = 8): split
-// indices (i, j, l) and (i + 1, j, l), lanes taking i-pairs fastest (4), then
-// 4 z rows, then 2 y rows (with the FP32 plane stride 88 a warp's loads fall
-// in 32 distinct banks).  256 pairs per colour.
+// Pair p (0 <= p < 256) of a colour's nodes for the fixed block size 16
+// (h = 8): split indices (i, j, l) and (i + 1, j, l) with i = 2 (p & 3),
+// l = 2 ((p >> 2) & 3) + (p >> 7), j = ((p >> 4) & 1) + 2 ((p >> 5) & 3).  A
+// warp's lanes take i-pairs fastest (4), then 4 z rows of one parity
+// (l = 0, 2, 4, 6 or 1, 3, 5, 7), then 2 y rows; with the FP32 plane strides
+// Hp = 84 (box) and Fp = 76 (staged right-hand side) and row strides 9, its
+// loads fall in 32 distinct banks.  Pairs p and p + 128 are z-adjacent (l and
+// l + 1): a thread that takes both shares between their stencils the plane
+// that lies between them.
 struct Pair { int i, j, l; };
 __device__ __forceinline__ Pair pair_of(int p) {
-    const int ip = p & 3, lq = (p >> 2) & 3, jq = (p >> 4) & 1, r3 = p >> 5;
     Pair q;
-    q.i = 2 * ip;
-    q.l = lq + 4 * (r3 & 1);
-    q.j = jq + 2 * (r3 >> 1);
+    q.i = 2 * (p & 3);
+    q.l = 2 * ((p >> 2) & 3) + (p >> 7);
+    q.j = ((p >> 4) & 1) + 2 * ((p >> 5) & 3);
     return q;
 }
 
@@ -595,17 +629,24 @@ __device__ __forceinline__ Pair pair_of(int p) {
 // neighbours' interiors), so the halo values stored there are harmless.
 __device__ __forceinline__ void store_planes16(float* __restrict__ Ub, const float* __restrict__ su, const Split& sp,
                                                int nthreads) {
+    // A float4 starts at an even x (S is even): its elements x, x+1, x+2, x+3
+    // sit at a, a + H3p, a + 1, a + H3p + 1 of the split box (a = at(x, y, z)),
+    // except at x = 16, where the last two start the next row.
     constexpr int S = 18, S2 = S * S, NV = 16 * S2 / 4;
     float4* __restrict__ dst = reinterpret_cast<float4*>(Ub + S2);
     for (int t = threadIdx.x; t < NV; t += nthreads) {
-        float v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int q = 4 * t + e;
-            const int Z = 1 + q / S2, r = q - (Z - 1) * S2, Y = r / S, X = r - Y * S;
-            v[e] = su[sp.at(X, Y, Z)];
-        }
-        dst[t] = make_float4(v[0], v[1], v[2], v[3]);
+        const int q = 4 * t;
+        const int Zr = q / S2, r = q - Zr * S2, Y = r / S, X = r - Y * S;
+        const int a = sp.at(X, Y, Zr + 1);
+        // x + 2 at a + 1, or (x = 16) column 0 of the next row, never in the
+        // next plane (x = 16 in a plane's last row has 4 t = 2 (mod 4))
+        const int a2 = X < S - 2 ? a + 1 : sp.at(0, Y + 1, Zr + 1);
+        float4 v;
+        v.x = su[a];
+        v.y = su[a + sp.H3p];
+        v.z = su[a2];
+        v.w = su[a2 + sp.H3p];
+        dst[t] = v;
     }
 }
 
@@ -647,14 +688,40 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
         // Fixed block size, FP32: each work item is a pair of a colour's nodes
         // adjacent along x (split indices i, i + 1), whose stencils share the
         // values of the fine plane between them (the +x neighbours of the
-        // first are the -x neighbours of the second).  Lanes take i-pairs
-        // fastest (4), then 4 z rows, then 2 y rows: with Hp = 88 (FP32) the
-        // loads of a warp fall in 32 distinct banks.
-        constexpr int hh = NC / 2, NP = hh * hh * hh / 2;
+        // first are the -x neighbours of the second); lane order: pair_of.
+        // A 128-thread CTA gives each thread the z-adjacent pairs p and
+        // p + 128 and loads all four stencils before it stores, so that the
+        // plane between the pairs is loaded once.
+        constexpr int hh = NC / 2, NP = hh * hh * hh / 2, NU = NP / 2;
         static_assert(hh == 8, "the pair lane order assumes h = 8");
 #pragma unroll
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
+            if (blockDim.x == NU) {
+                const Pair q = pair_of(threadIdx.x);
+                const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i, b1 = b0 + sp.H2;
+                T fa0, fb0, fa1, fb1;
+                if (fmode) {
+                    const int fi = col * F3 + q.l * Fp + q.j * Fr + q.i;
+                    fa0 = fs[fi]; fb0 = fs[fi + 1];
+                    fa1 = fs[fi + Fp]; fb1 = fs[fi + Fp + 1];
+                } else {
+                    const int fi = ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo;
+                    fa0 = Fb[fi]; fb0 = Fb[fi + 2];
+                    fa1 = Fb[fi + 2 * n * n]; fb1 = Fb[fi + 2 * n * n + 2];
+                }
+                const T sa0 = offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const T sb0 = offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const T sa1 = offc_s<M>(su, b1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const T sb1 = offc_s<M>(su, b1 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const int d = c.dX + c.dY + c.dZ;
+                su[b0 + d] = (h2den * fa0 - sa0) * inv_c;
+                su[b0 + 1 + d] = (h2den * fb0 - sb0) * inv_c;
+                su[b1 + d] = (h2den * fa1 - sa1) * inv_c;
+                su[b1 + 1 + d] = (h2den * fb1 - sb1) * inv_c;
+                __syncthreads();
+                continue;
+            }
             for (int p = threadIdx.x; p < NP; p += blockDim.x) {
                 const Pair q = pair_of(p);
                 const int i = q.i, j = q.j, l = q.l;
@@ -713,59 +780,6 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
     }
 }
 
-// Gauss-Seidel sweep of a block without interpolated ghost regions (block
-// size 16, FP32): the same arithmetic, node pairs and lane order as
-// k_smooth_fused<M, float, I, 16>, with less shared memory per CTA (the split
-// box and the 28-int head of the record; no interpolation scratch, no staged
-// right-hand side) so that more CTAs fit on an SM.  Each thread's 2 x 8 x KP
-// right-hand-side values are loaded into registers before the box copy and
-// consumed by the colour sweeps.  Blocks order[first + blockIdx.x].
-template <int M, int NT>
-__global__ void __launch_bounds__(NT) k_smooth_plain16(float* __restrict__ Uout, const float* __restrict__ Uin,
-                                                       const float* __restrict__ F, LevelView lk, float h2den, int first) {
-    constexpr int n = 16, NP = 256, KP = NP / NT;
-    static_assert(NP % NT == 0, "CTA size divides the 256 pairs of a colour");
-    extern __shared__ __align__(16) unsigned char fz_smem[];
-    float* su = reinterpret_cast<float*>(fz_smem);
-    __shared__ __align__(16) int rec[28];
-    const Split sp = split_of<float>(n);
-    const int b = lk.order[first + blockIdx.x];
-    if (threadIdx.x < 7) cp_async16(&rec[4 * threadIdx.x], lk.rec + (size_t)b * REC_INTS + 4 * threadIdx.x);
-    cp_async_commit();
-    float fa[8][KP], fb[8][KP];
-    const float* __restrict__ Fb = F + (size_t)b * (n * n * n);
-#pragma unroll
-    for (int col = 0; col < 8; ++col) {
-        const int fo = (((col >> 2) & 1) * n + ((col >> 1) & 1)) * n + (col & 1);
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            const Pair q = pair_of(threadIdx.x + k * NT);
-            const int fi = ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + fo;
-            fa[col][k] = ldg_now(Fb + fi);
-            fb[col][k] = ldg_now(Fb + fi + 2);
-        }
-    }
-    cp_async_wait<0>();
-    __syncthreads();
-    build_halo<float, M + 2, false>(su, nullptr, nullptr, rec, Uin, nullptr, lk, b, n, sp);
-    const float inv_c = 1.0f / float(LW<M>::c);
-#pragma unroll
-    for (int col = 0; col < 8; ++col) {
-        const Col c = colour(col, sp, n);
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            const Pair q = pair_of(threadIdx.x + k * NT);
-            const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
-            const float sa = offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-            const float sb = offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-            su[b0 + c.dX + c.dY + c.dZ] = (h2den * fa[col][k] - sa) * inv_c;
-            su[b0 + 1 + c.dX + c.dY + c.dZ] = (h2den * fb[col][k] - sb) * inv_c;
-        }
-        __syncthreads();
-    }
-    store_planes16(Uout + (size_t)b * 5832, su, sp, NT);
-}
-
 // ---------------------------------------------------------------- residual r = f - L u (all nodes)
 template <int M, typename T, int I, int NC>
 __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const T* __restrict__ U,
@@ -782,26 +796,70 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
     record_prologue(hs, lk, b);
-    build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     if constexpr (NC != 0 && sizeof(T) == 4) {
-        // pairs of nodes adjacent along x, as in the smoother
-        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2;
+        // F staged in shared memory in the colour split (as the smoother's),
+        // over the interpolation scratch: copied with the box where the block
+        // has no interpolated regions, after the ghost layer otherwise.  Each
+        // pair's residual replaces its F there; the block's R then goes out by
+        // columns (whole 64-byte rows).  Pairs of nodes adjacent along x as in
+        // the smoother (two z-adjacent pairs per thread in a 128-thread CTA).
+        T* fs = pool;
+        const bool early = hs.rec[REC_NREG] == 0;
+        if (early) load_rhs(fs, F, b, n);
+        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+        if (!early) {
+            load_rhs(fs, F, b, n);
+            cp_async_wait<0>();
+            __syncthreads();
+        }
+        const int Fp = split_fp(n, 4), Fr = split_fr(n, 4), F3 = split_f3(n, 4);
+        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2, NU = NP / 2;
+        auto lpair = [&](const Col& c, int b0, T& la, T& lb) {
+            la = T(LW<M>::c) * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+            lb = T(LW<M>::c) * su[b0 + 1 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+        };
 #pragma unroll
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
+            if (blockDim.x == NU) {
+                const Pair q = pair_of(threadIdx.x);
+                const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
+                T la0, lb0, la1, lb1;
+                lpair(c, b0, la0, lb0);
+                lpair(c, b0 + sp.H2, la1, lb1);
+                const int fi = col * F3 + q.l * Fp + q.j * Fr + q.i, fj = fi + Fp;
+                fs[fi] = fs[fi] - scale * la0;
+                fs[fi + 1] = fs[fi + 1] - scale * lb0;
+                fs[fj] = fs[fj] - scale * la1;
+                fs[fj + 1] = fs[fj + 1] - scale * lb1;
+                continue;
+            }
             for (int p = threadIdx.x; p < NP; p += blockDim.x) {
                 const Pair q = pair_of(p);
                 const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
-                const T la = T(LW<M>::c) * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const T lb = T(LW<M>::c) * su[b0 + 1 + c.dX + c.dY + c.dZ] +
-                             offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const size_t fi = b * n3 + ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo;
-                R[fi] = F[fi] - scale * la;
-                R[fi + 2] = F[fi + 2] - scale * lb;
+                T la, lb;
+                lpair(c, b0, la, lb);
+                const int fi = col * F3 + q.l * Fp + q.j * Fr + q.i;
+                fs[fi] = fs[fi] - scale * la;
+                fs[fi + 1] = fs[fi + 1] - scale * lb;
+            }
+        }
+        __syncthreads();
+        // R by (x, y) columns walking z, the inverse of load_rhs's copy
+        T* Rb = R + b * n3;
+        for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+            const int y = c / n, x = c - y * n;
+            const T* scol = fs + (((y & 1) << 1) | (x & 1)) * F3 + (y >> 1) * Fr + (x >> 1);
+            T* gcol = Rb + c;
+#pragma unroll
+            for (int m = 0; m < NC / 2; ++m) {
+                gcol[(size_t)(2 * m) * n * n] = scol[m * Fp];
+                gcol[(size_t)(2 * m + 1) * n * n] = scol[4 * F3 + m * Fp];
             }
         }
     } else {
+        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
 #pragma unroll
@@ -852,22 +910,25 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
     record_prologue(hs, lk, b);
     build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     if constexpr (NC != 0 && sizeof(T) == 4) {
-        // pairs of nodes adjacent along x, as in the smoother
-        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2;
+        // pairs of nodes adjacent along x, as in the smoother (two z-adjacent
+        // pairs per thread in a 128-thread CTA)
+        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2, NU = NP / 2;
+        auto fpair = [&](const Col& c, int b0, size_t fi) {
+            const T ua = su[b0 + c.dX + c.dY + c.dZ], ub = su[b0 + 1 + c.dX + c.dY + c.dZ];
+            const T la = T(LW<M>::c) * ua + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+            const T lb = T(LW<M>::c) * ub + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+            F[fi] += scale * la;
+            F[fi + 2] += scale * lb;
+            H[fi] = ua;
+            H[fi + 2] = ub;
+        };
 #pragma unroll
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
             for (int p = threadIdx.x; p < NP; p += blockDim.x) {
                 const Pair q = pair_of(p);
                 const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
-                const T ua = su[b0 + c.dX + c.dY + c.dZ], ub = su[b0 + 1 + c.dX + c.dY + c.dZ];
-                const T la = T(LW<M>::c) * ua + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const T lb = T(LW<M>::c) * ub + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const size_t fi = b * n3 + ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo;
-                F[fi] += scale * la;
-                F[fi + 2] += scale * lb;
-                H[fi] = ua;
-                H[fi + 2] = ub;
+                fpair(c, b0, b * n3 + ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo);
             }
         }
     } else {
@@ -888,6 +949,7 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
 }
 
 // ---------------------------------------------------------------- leaf residual (FP64 stop rule / outer residual)
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 __device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
     __shared__ double red[32];
     if (v != v) v = __longlong_as_double(0x7ff0000000000000ULL);
@@ -903,7 +965,7 @@ __device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
 }
 
 template <int M, int I, int NC>
-__global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, const double* __restrict__ U,
+__global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, const double* __restrict__ U,
                                                        const double* __restrict__ F, const double* __restrict__ Uc,
                                                        const int* __restrict__ blocks, LevelView lk, int n_arg,
                                                        double scale, unsigned long long* out) {
@@ -920,14 +982,18 @@ __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, c
     record_prologue(hs, lk, b);
     build_halo<double, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
-    double m = 0.0;
+    unsigned long long mb = 0;        // max |r| as a bit pattern
     if constexpr (NC != 0) {
         // Fixed block size: one thread per interior (y, z) row walking x.
-        // Per box plane X it forms the centre value, the sum c of the 4
+        // Per box plane X it forms the centre value u, the sum c of the 4
         // face-adjacent (y, z) neighbours and the sum d of the 4 diagonal
-        // ones; then faces = u(X-1) + u(X+1) + c(X), edges = c(X-1) + c(X+1)
-        // + d(X), corners = d(X-1) + d(X+1), each plane's sums computed once
-        // for three nodes (fewer FP64 additions than the 26-neighbour sum).
+        // ones; a node's faces are u(X-1) + u(X+1) + c(X), its edges c(X-1) +
+        // c(X+1) + d(X), its corners d(X-1) + d(X+1).  So with the plane's
+        // weighted sums P = w_f u + w_e c + w_k d (what a neighbouring plane
+        // contributes) and Q = w_c u + w_f c + w_e d (what the node's own plane
+        // contributes), L u(X) = P(X-1) + P(X+1) + Q(X): each plane's sums are
+        // formed once for three nodes (fewer FP64 operations, GB300's scarce
+        // resource, than the 26-neighbour sum).
         constexpr int nn = NC;
         const int H = sp.H, Hp = sp.H2, H3p = sp.H3p;
         for (int r = threadIdx.x; r < nn * nn; r += blockDim.x) {
@@ -939,29 +1005,34 @@ __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, c
             };
             const int r00 = rowb(0, 0), rm0 = rowb(-1, 0), rp0 = rowb(1, 0), r0m = rowb(0, -1), r0p = rowb(0, 1);
             const int rmm = rowb(-1, -1), rpm = rowb(1, -1), rmp = rowb(-1, 1), rpp = rowb(1, 1);
-            auto plane = [&](int X, double& uc, double& c, double& d) {
+            auto plane = [&](int X, double& P, double& Q) {
                 const int o = (X & 1) * H3p + (X >> 1);
-                uc = su[r00 + o];
-                c = (su[rm0 + o] + su[rp0 + o]) + (su[r0m + o] + su[r0p + o]);
-                d = (su[rmm + o] + su[rpm + o]) + (su[rmp + o] + su[rpp + o]);
+                const double u = su[r00 + o];
+                const double c = (su[rm0 + o] + su[rp0 + o]) + (su[r0m + o] + su[r0p + o]);
+                const double d = (su[rmm + o] + su[rpm + o]) + (su[rmp + o] + su[rpp + o]);
+                double p = LW<M>::f * u, q = LW<M>::c * u + LW<M>::f * c;
+                if (LW<M>::e != 0) { p += LW<M>::e * c; q += LW<M>::e * d; }
+                if (LW<M>::k != 0) p += LW<M>::k * d;
+                P = p;
+                Q = q;
             };
-            double u0, c0, d0, u1, c1, d1;
-            plane(0, u0, c0, d0);
-            plane(1, u1, c1, d1);
+            double P0, P1, Q1, Qg;
+            plane(0, P0, Qg);             // (the ghost plane's own-plane sum is not needed)
+            plane(1, P1, Q1);
             const size_t rowf = b * n3 + (size_t)r * nn;
 #pragma unroll
             for (int X = 1; X <= nn; ++X) {
-                double u2, c2, d2;
-                plane(X + 1, u2, c2, d2);
-                double l = LW<M>::c * u1 + LW<M>::f * ((u0 + u2) + c1);
-                if (LW<M>::e != 0) l += LW<M>::e * ((c0 + c2) + d1);
-                if (LW<M>::k != 0) l += LW<M>::k * (d0 + d2);
+                double P2, Q2;
+                plane(X + 1, P2, Q2);
+                const double l = (P0 + P2) + Q1;
                 const size_t fi = rowf + (X - 1);
                 const double res = F[fi] - scale * l;
-                if (R) R[fi] = res;
-                m = (res != res) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(res));
-                u0 = u1; c0 = c1; d0 = d1;
-                u1 = u2; c1 = c2; d1 = d2;
+                if (R) R[fi] = (float)res;
+                // |res| as its bit pattern (sign cleared): ordered like the
+                // value for non-negative doubles, NaN above +Inf
+                mb = umax64(mb, (unsigned long long)__double_as_longlong(res) & 0x7fffffffffffffffULL);
+                P0 = P1;
+                P1 = P2; Q1 = Q2;
             }
         }
     } else {
@@ -976,12 +1047,12 @@ __global__ void __launch_bounds__(512) k_leafres_fused(double* __restrict__ R, c
                         LW<M>::c * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
                     const size_t fi = b * n3 + d.f + c.fo;
                     const double r = F[fi] - scale * l;
-                    if (R) R[fi] = r;
-                    m = (r != r) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(r));
+                    if (R) R[fi] = (float)r;
+                    mb = umax64(mb, (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffULL);
                 }
         }
     }
-    bmax_atomic(m, out + (lk.prob ? lk.prob[b] : 0));
+    bmax_atomic(__longlong_as_double((long long)mb), out + (lk.prob ? lk.prob[b] : 0));
 }
 
 // ---------------------------------------------------------------- halo dump (step API)
@@ -1267,15 +1338,6 @@ static void smooth_m(T* Uout, const T* Uin, const T* F, const T* Uc, const Level
     if (n == NC_FIXED) k_smooth_fused<M, T, I, NC_FIXED><<<nblocks, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
     else k_smooth_fused<M, T, I, 0><<<nblocks, ct, sm, s>>>(Uout, Uin, F, Uc, lk, n, h2den, lk.order, fst);
 }
-template <int M>
-static void smooth_plain_m(float* Uout, const float* Uin, const float* F, const LevelView& lk, float h2den, bool nt256,
-                           cudaStream_t s) {
-    const int cnt = lk.nb - lk.nint;
-    if (cnt == 0) return;
-    const size_t sm = sizeof(float) * 8 * (size_t)split_h3p(16, 4);
-    if (nt256) k_smooth_plain16<M, 256><<<cnt, 256, sm, s>>>(Uout, Uin, F, lk, h2den, lk.nint);
-    else k_smooth_plain16<M, 128><<<cnt, 128, sm, s>>>(Uout, Uin, F, lk, h2den, lk.nint);
-}
 template <int M, typename T>
 static void residual_m(T* R, const T* U, const T* F, const T* Uc, const LevelView& lk, int n, T scale, int ct, size_t sm,
                        cudaStream_t s) {
@@ -1291,7 +1353,7 @@ static void fas_m(T* F, T* H, const T* U, const T* Uc, const LevelView& lk, int 
     else k_fas_fused<M, T, I, 0><<<lk.nb, ct, sm, s>>>(F, H, U, Uc, lk, n, scale, lk.order);
 }
 template <int M>
-static void leafres_m(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
+static void leafres_m(float* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
                       const LevelView& lk, int n, double scale, unsigned long long* out, int ct, size_t sm,
                       cudaStream_t s) {
     constexpr int I = M + 2;
@@ -1316,29 +1378,14 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
         if (fused_smem<T>(n, M + 2, 1) <= (size_t)MAX_DYN_SMEM) fmode = 1;
         const size_t s2 = fused_smem<T>(n, M + 2, 2);
         const size_t per_sm = 228 * 1024, per_cta = s2 + sizeof(HaloSmem) + 1024;
-        const size_t nlaunch = (sizeof(T) == 4 && n == NC_FIXED && (nt & SMOOTH_SPLIT)) ? (size_t)lk.nint : (size_t)lk.nb;
-        if (s2 <= (size_t)MAX_DYN_SMEM && nlaunch <= (size_t)nsm * (per_sm / per_cta)) fmode = 2;
+        if (s2 <= (size_t)MAX_DYN_SMEM && (size_t)lk.nb <= (size_t)nsm * (per_sm / per_cta)) fmode = 2;
     }
     const int fst = fmode;
     const size_t sm = fused_smem<T>(n, M + 2, fmode);
-    const int ct = cta_size_fixed(n, nt & SMOOTH_NT_MASK, sizeof(T) == 4);
-    // split: interface blocks (first in lk.order) here, the others in the lean kernel
-    const bool split = sizeof(T) == 4 && n == NC_FIXED && (nt & SMOOTH_SPLIT);
-    const int ngen = split ? lk.nint : lk.nb;
-    if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, ngen, n, T(h2 * LW<2>::den), fst, ct, sm, s);
-    if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, ngen, n, T(h2 * LW<4>::den), fst, ct, sm, s);
-    if (M == 6) smooth_m<6, T>(Uout, Uin, F, Uc, lk, ngen, n, T(h2 * LW<6>::den), fst, ct, sm, s);
-    if constexpr (sizeof(T) == 4) {
-        if (split) {
-            const bool nt256 = (nt & SMOOTH_PLAIN256) != 0;
-            float* uo = reinterpret_cast<float*>(Uout);
-            const float* ui = reinterpret_cast<const float*>(Uin);
-            const float* ff = reinterpret_cast<const float*>(F);
-            if (M == 2) smooth_plain_m<2>(uo, ui, ff, lk, float(h2 * LW<2>::den), nt256, s);
-            if (M == 4) smooth_plain_m<4>(uo, ui, ff, lk, float(h2 * LW<4>::den), nt256, s);
-            if (M == 6) smooth_plain_m<6>(uo, ui, ff, lk, float(h2 * LW<6>::den), nt256, s);
-        }
-    }
+    const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
+    if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, lk.nb, n, T(h2 * LW<2>::den), fst, ct, sm, s);
+    if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, lk.nb, n, T(h2 * LW<4>::den), fst, ct, sm, s);
+    if (M == 6) smooth_m<6, T>(Uout, Uin, F, Uc, lk, lk.nb, n, T(h2 * LW<6>::den), fst, ct, sm, s);
 }
 
 template <typename T>
@@ -1346,7 +1393,8 @@ void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView 
                            double inv_h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     attrs_residual<T>();
-    const size_t sm = fused_smem<T>(n, M + 2);
+    // FP32 block size 16 stages F over the interpolation scratch (fmode-1 sizing)
+    const size_t sm = fused_smem<T>(n, M + 2, (sizeof(T) == 4 && n == NC_FIXED) ? 1 : 0);
     const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
     if (M == 2) residual_m<2, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
     if (M == 4) residual_m<4, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, s);

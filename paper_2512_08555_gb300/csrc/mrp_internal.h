@@ -308,11 +308,6 @@ void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc,
 template <typename T>
 void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
 // stencil kernels with the ghost layer built in shared memory (kernels_fused.cuh, fused_*.cu);
-// Smoother launch choices (the `nt` argument of launch_smooth_fused): the CTA
-// size of the generic kernel in the low bits; SMOOTH_SPLIT (block size 16,
-// FP32) runs the blocks without interpolated ghost regions in a separate
-// launch of the lean kernel, whose CTA size is 256 with SMOOTH_PLAIN256, else 128.
-constexpr int SMOOTH_NT_MASK = 0xFFF, SMOOTH_SPLIT = MRP_LAUNCH_SPLIT, SMOOTH_PLAIN256 = MRP_LAUNCH_PLAIN256;
 // fused_smem_bytes: their dynamic shared memory for block size n, order M and
 // element size el (bytes), without a staged right-hand side
 size_t fused_smem_bytes(int n, int M, int el);
@@ -327,7 +322,7 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
                       int nt, cudaStream_t s);
 template <typename T>
 void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s);
-void launch_leafres_fused(double* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
+void launch_leafres_fused(float* R, const double* U, const double* F, const double* Uc, const int* blocks, int nblocks,
                           LevelView lk, LevelView lc, int n, int M, double inv_h2, unsigned long long* out, int nt,
                           cudaStream_t s);
 

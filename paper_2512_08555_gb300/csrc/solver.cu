@@ -467,20 +467,11 @@ template <typename T> static constexpr int pidx() { return sizeof(T) == 4 ? 1 : 
 // Launches of a fused stencil kernel on a level.
 static int fused_launches(const Level& lv) { return lv.nb > 0 ? 1 : 0; }
 
-// Kernels one smoother launch runs: two when the level's sweep is split into
-// interface blocks and the others (SMOOTH_SPLIT), else one.
-static int smooth_launches(const Handle& h, const Level& lv, int nt, bool fp32) {
-    if (lv.nb == 0) return 0;
-    const bool split = fp32 && h.n == 16 && (nt & SMOOTH_SPLIT);
-    return split ? (lv.nint > 0 ? 1 : 0) + (lv.nb > lv.nint ? 1 : 0) : 1;
-}
-
 // One Gauss-Seidel sweep with its ghost layer built in the kernel; reads the
 // current buffer, writes the other, then the two swap.
 template <typename T>
 static void smooth(Handle& h, int k, cudaStream_t s) {
-    PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h),
-                  smooth_launches(h, h.lv[k], h.nt_smooth[pidx<T>()][k], sizeof(T) == 4));
+    PhaseScope ps(h, s, ph<T>(PH_SMOOTH), h.lv[k].nb * n3(h), fused_launches(h.lv[k]));
     const double hk = level_h(h, k);
     launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), h.lv[k].view(),
                            view_or_empty(h, k - 1), h.n, h.M, hk * hk, h.nt_smooth[pidx<T>()][k], s);
@@ -602,11 +593,6 @@ struct SolveState {
 template <typename T>
 static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     const std::vector<int> cta = {128, 256, 512};
-    // the smoother of FP32 block-size-16 levels may also split its sweep
-    std::vector<int> smooth_cand = cta;
-    if (sizeof(T) == 4 && h.n == 16)
-        for (int c : {128, 256})
-            for (int x : {SMOOTH_SPLIT, SMOOTH_SPLIT | SMOOTH_PLAIN256}) smooth_cand.push_back(c | x);
     constexpr int pi = pidx<T>();
     auto pick_from = [&](const std::vector<int>& cand, auto&& launch) {
         float best = 1e30f;
@@ -629,7 +615,7 @@ static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_
         const double hk = level_h(h, k);
         Level& lv = h.lv[k];
         if (k >= 1) {
-            h.nt_smooth[pi][k] = pick_from(smooth_cand, [&](int nt) {
+            h.nt_smooth[pi][k] = pick([&](int nt) {
                 launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), lv.view(),
                                        view_or_empty(h, k - 1), h.n, h.M, hk * hk, nt, s);
             });
@@ -663,11 +649,10 @@ int autotune(Handle& h, cudaStream_t s) {
     if (h.tuned) return MRP_OK;
     tune_defaults(h);
     if (h.launch_override) {
-        const int ct = h.launch_override & SMOOTH_NT_MASK;
+        const int ct = h.launch_override;
         for (int p = 0; p < 2; ++p)
             for (int k = 0; k < Handle::MAXL; ++k) {
-                h.nt_smooth[p][k] = h.launch_override;
-                h.nt_res[p][k] = h.nt_fas[p][k] = ct;
+                h.nt_smooth[p][k] = h.nt_res[p][k] = h.nt_fas[p][k] = ct;
                 h.nt_leafres[k] = ct;
             }
         h.tuned = true;
@@ -746,7 +731,8 @@ void outer_residual_launch(Handle& h, cudaStream_t s) {
     for (int k = 1; k <= h.L; ++k) {
         PhaseScope ps(h, s, PH_NORM, h.lv[k].nleaf * n3(h), h.lv[k].nleaf > 0 ? 1 : 0);
         const double hk = level_h(h, k);
-        launch_leafres_fused(h.lv[k].R, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
+        // the residual rows go straight into the FP32 right-hand side of the next correction
+        launch_leafres_fused(h.lv[k].F32, h.lv[k].U, h.lv[k].F, ucoarse<double>(h, k), h.lv[k].leaf_blocks, h.lv[k].nleaf,
                              h.lv[k].view(), view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), h.slot(1),
                              h.nt_leafres[k], s);
     }
@@ -777,9 +763,8 @@ void correction_launch(Handle& h, cudaStream_t s) {
     const size_t S = h.n + 2;
     Level& l0 = h.lv[0];
     {
-        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, h.L + 1);
-        for (int k = 1; k <= h.L; ++k)
-            launch_cast_rhs(h.lv[k].F32, h.lv[k].R, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, false, s);
+        // leaf rows of levels >= 1: written by the outer residual; level-0 leaves are exact
+        PhaseScope ps(h, s, PH_OTHER, l0.nleaf * n3(h), 1);
         launch_cast_rhs(l0.F32, nullptr, l0.leaf_blocks, l0.nleaf, h.n, true, s);
     }
     for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].U32, 0, sizeof(float) * h.lv[k].nb * S * S * S, s);
@@ -893,11 +878,7 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
     if (opt->stop_rule != MRP_STOP_RESIDUAL && opt->stop_rule != MRP_STOP_CAUCHY) return MRP_ERR_INVALID_ARG;
     if (opt->precision != MRP_FP64 && opt->precision != MRP_MIXED) return MRP_ERR_INVALID_ARG;
     if (opt->inner_cycles < 0 || opt->max_outer < 0) return MRP_ERR_INVALID_ARG;
-    if (opt->launch != 0) {
-        const int ct = opt->launch & SMOOTH_NT_MASK;
-        if ((ct != 128 && ct != 256 && ct != 512) || (opt->launch & ~(SMOOTH_NT_MASK | SMOOTH_SPLIT | SMOOTH_PLAIN256)))
-            return MRP_ERR_INVALID_ARG;
-    }
+    if (opt->launch != 0 && opt->launch != 128 && opt->launch != 256 && opt->launch != 512) return MRP_ERR_INVALID_ARG;
     // problems (forest, component) in the caller's layout order, grouped by block size
     std::map<int, std::vector<ProblemDesc>> by_n;
     int64_t off = 0;

@@ -28,7 +28,6 @@ EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_
             "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph",
             "mrp_solve_host", "mrp_fma_peak"]
 ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
-LAUNCH_SPLIT, LAUNCH_PLAIN256 = 1 << 12, 1 << 13
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
 

@@ -129,3 +129,76 @@ def test_mixed_zero_source_and_first_step():
     um, stm = s.solve(f)
     assert stm.residual < 1e-10
     assert _rel(um.cpu().numpy(), up.cpu().numpy()) < MIXED_TOL
+
+
+def _dense_window(desc, u_leaf, leaf_index, k, c, w):
+    """Leaf values on the (n + 2w)^3 window around level-k block c, from the leaves of level k (None if a node
+    of the window lies in no level-k leaf)."""
+    n = desc.n
+    out = np.empty((n + 2 * w,) * 3)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                q = (c[0] + dx, c[1] + dy, c[2] + dz)
+                i = leaf_index.get((k,) + q)
+                if i is None:
+                    return None
+                zs = slice(n - w, n) if dz < 0 else (slice(0, n) if dz == 0 else slice(0, w))
+                ys = slice(n - w, n) if dy < 0 else (slice(0, n) if dy == 0 else slice(0, w))
+                xs = slice(n - w, n) if dx < 0 else (slice(0, n) if dx == 0 else slice(0, w))
+                zo = 0 if dz < 0 else (w if dz == 0 else w + n)
+                yo = 0 if dy < 0 else (w if dy == 0 else w + n)
+                xo = 0 if dx < 0 else (w if dx == 0 else w + n)
+                blk = u_leaf[i][zs, ys, xs]
+                out[zo:zo + blk.shape[0], yo:yo + blk.shape[1], xo:xo + blk.shape[2]] = blk
+    return out
+
+
+def test_mixed_config3_full_size():
+    """The five-level forest on 6^3 level-0 blocks (97.9M leaf nodes), mixed precision: within the mixed
+    bound of the FP64 GPU solve, and -- checked by the oracle's own stencils, node by node -- the leaf
+    equations R^M f = L u (Sec. 3.2) hold on sampled finest-level blocks whose whole neighbourhood is
+    finest-level leaves (ghosts are then plain copies): the GPU answer, the analytic source and the
+    oracle's LHS/RHS weights, nothing else."""
+    from paper_2512_08555_gb300.mrp import Solver
+    from oracle.stencils import lhs_stencil, rhs_stencil
+    desc, src = synth.config3(0)
+    assert desc.leaf_nodes == 97853440
+    fd = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
+    m = Solver(desc, order=4, tol=1e-10, max_cycles=80, precision="mixed")
+    um, st = m.solve(fd)
+    m.close()
+    p = Solver(desc, order=4, tol=1e-11, max_cycles=60)
+    up, sp = p.solve(fd, allow_not_converged=True)
+    p.close()
+    assert st.residual < 1e-10 and sp.residual < 1e-10
+    u = um.cpu().numpy()
+    assert _rel(u, up.cpu().numpy()) < MIXED_TOL
+    del fd, up
+    # sampled leaf equations at the finest level
+    L = desc.max_level
+    n = desc.n
+    h = desc.h0 / (1 << L)
+    leaf_index = {(int(l), *map(int, c)): i for i, (l, c) in enumerate(zip(desc.leaf_level, desc.leaf_ijk))}
+    rng = np.random.default_rng(5)
+    cand = np.nonzero(desc.leaf_level == L)[0]
+    wL, wR = lhs_stencil(4), rhs_stencil(4)
+    checked, worst = 0, 0.0
+    for i in rng.permutation(cand):
+        c = desc.leaf_ijk[i]
+        U = _dense_window(desc, u, leaf_index, L, c, 1)
+        if U is None:
+            continue
+        g = np.arange(-2, n + 2)
+        X = desc.origin[0] + (c[0] * n + g) * h
+        Y = desc.origin[1] + (c[1] * n + g) * h
+        Z = desc.origin[2] + (c[2] * n + g) * h
+        fwin = src(X[None, None, :], Y[None, :, None], Z[:, None, None])
+        lu = sum(wv * U[a:a + n, b:b + n, cc:cc + n] for (a, b, cc), wv in np.ndenumerate(wL) if wv != 0.0) / h ** 2
+        fs = sum(wv * fwin[a:a + n, b:b + n, cc:cc + n] for (a, b, cc), wv in np.ndenumerate(wR) if wv != 0.0)
+        worst = max(worst, float(np.abs(fs - lu).max()) / st.fstar_max)
+        checked += 1
+        if checked == 24:
+            break
+    assert checked == 24
+    assert worst < 2e-10, worst

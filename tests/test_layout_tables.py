@@ -9,9 +9,10 @@ test reads them from there and recomputes the rule they claim:
 * box, FP32, one node per lane (lanes take x fastest, then z, then y): the
   plane stride Hp in [H^2, H^2 + 32) minimises the wavefronts over a colour;
 * staged right-hand side, same lane order, row stride h: Fp likewise;
-* block size 16 with node pairs (lanes take i-pairs fastest, then 4 z rows,
-  then 2 y rows): Hp = 88 with row stride 9, and Fp = 72 with row stride 9,
-  put a warp's 32 loads in 32 distinct banks.
+* block size 16 with node pairs (lanes take i-pairs fastest, then 4 z rows
+  of one parity, l = 0, 2, 4, 6 or 1, 3, 5, 7, then 2 y rows): Hp = 84 with
+  row stride 9, and Fp = 76 with row stride 9, put a warp's 32 loads in 32
+  distinct banks, for either node of a pair and either z parity.
 """
 import os
 import re
@@ -49,7 +50,7 @@ def _best(h, row, lo):
     return min(range(lo, lo + 32), key=lambda p: (_wavefronts(h, row, p), p))
 
 
-@pytest.mark.parametrize("n", [10, 12, 14, 16, 18, 20, 22, 24])
+@pytest.mark.parametrize("n", [10, 12, 14, 18, 20, 22, 24])
 def test_box_plane_stride(n):
     h, H = n // 2, n // 2 + 1
     hp = _table("split_hp")[n]
@@ -66,14 +67,37 @@ def test_rhs_plane_stride(n):
     assert _wavefronts(h, h, fp) == _wavefronts(h, h, _best(h, h, h * h))
 
 
+def _pair(p):
+    """The pair lane order of the CUDA source (pair_of): split indices (i, j, l) of pair p."""
+    return 2 * (p & 3), ((p >> 4) & 1) + 2 * ((p >> 5) & 3), 2 * ((p >> 2) & 3) + (p >> 7)
+
+
 def test_pair_lane_order_is_conflict_free():
     hp, fp = _table("split_hp")[16], _table("split_fp")[16]
-    assert (hp, fp) == (88, 72)
-    lanes = [(ip, lq, jq) for jq in range(2) for lq in range(4) for ip in range(4)]
-    for row, plane in ((9, hp), (9, fp)):            # box row stride H = 9; staged f row stride 9
-        for second in (0, 1):                        # both nodes of a pair
-            banks = {(2 * ip + second + lq * plane + jq * row) % 32 for ip, lq, jq in lanes}
-            assert len(banks) == 32
-    # the 8 colour sub-arrays of the staged f hold h Fp words each, padded to 16 (mod 32)
-    f3 = 8 * fp
-    assert (f3 + ((16 - f3 % 32) % 32 + 32) % 32) % 32 == 16
+    assert (hp, fp) == (84, 76)
+    src = open(SRC).read()
+    assert "q.l = 2 * ((p >> 2) & 3) + (p >> 7);" in src and "q.j = ((p >> 4) & 1) + 2 * ((p >> 5) & 3);" in src
+    assert sorted(_pair(p) for p in range(256)) == sorted((i, j, l) for i in range(0, 8, 2) for j in range(8)
+                                                          for l in range(8))
+    for w0 in range(0, 256, 32):                     # every warp of a 256-pair colour
+        for row, plane in ((9, hp), (9, fp)):        # box row stride H = 9; staged f row stride 9
+            for second in (0, 1):                    # both nodes of a pair
+                banks = set()
+                for p in range(w0, w0 + 32):
+                    i, j, l = _pair(p)
+                    banks.add((i + second + l * plane + j * row) % 32)
+                assert len(banks) == 32, (w0, plane, second)
+    # pairs p and p + 128 are z-adjacent
+    for p in range(128):
+        i, j, l = _pair(p)
+        assert _pair(p + 128) == (i, j, l + 1)
+    # the 8 colour sub-arrays of the staged f hold h Fp words each, padded to 8 (mod 32): a warp's column copy
+    # (lanes x = 0..15 of rows y and y + 1, y even) then writes 32 distinct banks
+    src = open(SRC).read()
+    assert "if (el == 4 && n == 16) return f + ((8 - f % 32) % 32 + 32) % 32;" in src
+    f3 = 8 * fp + ((8 - 8 * fp % 32) % 32 + 32) % 32
+    for y in (0, 2, 14):
+        banks = {((((yy & 1) << 1) | (x & 1)) * f3 + (yy >> 1) * 9 + (x >> 1)) % 32 for yy in (y, y + 1)
+                 for x in range(16)}
+        assert len(banks) == 32
+
