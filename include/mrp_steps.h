@@ -12,7 +12,9 @@
  *   MRP_FIELD_F     n^3       right-hand side (f* on leaves, FAS RHS on covered blocks)
  *   MRP_FIELD_R     n^3       residual f - L u
  *   MRP_FIELD_UHAT  n^3       stored approximation u-hat (Alg. 1)
- *   MRP_FIELD_FRAW  (n+4)^3   raw source f with two ghost layers
+ *   MRP_FIELD_FRAW  (n+4)^3   raw source f with two ghost layers (order 6 only; other
+ *                             orders keep raw f in the U arrays during
+ *                             MRP_STEP_PREPARE_RHS and return MRP_ERR_UNSUPPORTED)
  * All arrays are [block][z][y][x], x fastest.
  */
 #ifndef MRP_STEPS_H
@@ -30,7 +32,9 @@ enum {
 };
 
 enum {
-    MRP_STEP_PREPARE_RHS = 0,  /* f (leaf layout, arg) -> FRAW all levels -> F = R^M f on leaves (Sec. 3.2) */
+    MRP_STEP_PREPARE_RHS = 0,  /* f (leaf layout, arg) -> raw f on every level (FRAW with two ghost layers for
+                                  M = 6; for M = 2, 4 the interiors of U, which it overwrites, with zero ghost
+                                  layers) -> F = R^M f on leaves (Sec. 3.2) */
     MRP_STEP_GHOST_U = 1,      /* level k: inject U_k into covered U_{k-1}, then write into U_k's stored
                                   ghost layer the ghosts the stencil kernels build (Sec. 2.1) */
     MRP_STEP_SMOOTH = 2,       /* level k: one 8-colour Gauss-Seidel sweep with the ghost layer built from

@@ -1,4 +1,4 @@
-// FP64 leaf residual of the refinement and the stop rule.
+// FP64 leaf residual of the refinement and the stop rule; f* = R^M f with its ghost layer (M = 2, 4).
 #include "kernels_fused.cuh"
 
 namespace mrp {
@@ -13,6 +13,19 @@ void launch_leafres_fused(float* R, const double* U, const double* F, const doub
     if (M == 2) leafres_m<2>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<2>::den, out, ct, sm, s);
     if (M == 4) leafres_m<4>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<4>::den, out, ct, sm, s);
     if (M == 6) leafres_m<6>(R, U, F, Uc, blocks, nblocks, lk, n, inv_h2 / LW<6>::den, out, ct, sm, s);
+}
+
+void launch_rhs_fused(double* F, const double* Af, const double* Ac, const int* blocks, int nblocks, LevelView lk,
+                             int n, int M, cudaStream_t s) {
+    if (nblocks == 0) return;
+    static std::once_flag done[MAX_DEVICES];
+    once_per_device(done, [] {
+        allow(k_rhs_fused<2, 4, NC_FIXED>); allow(k_rhs_fused<2, 4, 0>);
+        allow(k_rhs_fused<4, 6, NC_FIXED>); allow(k_rhs_fused<4, 6, 0>);
+    });
+    const size_t sm = fused_smem<double>(n, M + 2);
+    if (M == 2) rhs_fused_m<2>(F, Af, Ac, blocks, nblocks, lk, n, sm, s);
+    if (M == 4) rhs_fused_m<4>(F, Af, Ac, blocks, nblocks, lk, n, sm, s);
 }
 
 }  // namespace mrp

@@ -129,10 +129,34 @@ template <typename R> struct Dft<5, R> {
     }
 };
 
+template <typename R> struct Dft<7, R> {
+    // symmetric pairs (j, 7 - j): a_j = v_j + v_{7-j}, b_j = v_j - v_{7-j};
+    // X_k = v_0 + sum_j a_j cos(2 pi j k / 7) + i sign sum_j b_j sin(2 pi j k / 7)
+    template <typename C> static __device__ __forceinline__ void run(C* v, int sign) {
+        const R c1 = R(0.62348980185873353053), c2 = R(-0.22252093395631440429), c3 = R(-0.90096886790241912624);
+        const R s1 = R(0.78183148246802980871), s2 = R(0.97492791218182360702), s3 = R(0.43388373911755812048);
+        const C a1 = cadd(v[1], v[6]), b1 = csub(v[1], v[6]);
+        const C a2 = cadd(v[2], v[5]), b2 = csub(v[2], v[5]);
+        const C a3 = cadd(v[3], v[4]), b3 = csub(v[3], v[4]);
+        const C m1 = cadd(v[0], cadd(cadd(cscale(a1, c1), cscale(a2, c2)), cscale(a3, c3)));
+        const C m2 = cadd(v[0], cadd(cadd(cscale(a1, c2), cscale(a2, c3)), cscale(a3, c1)));
+        const C m3 = cadd(v[0], cadd(cadd(cscale(a1, c3), cscale(a2, c1)), cscale(a3, c2)));
+        const C t1 = cmuli(cadd(cadd(cscale(b1, s1), cscale(b2, s2)), cscale(b3, s3)), R(sign));
+        const C t2 = cmuli(csub(csub(cscale(b1, s2), cscale(b2, s3)), cscale(b3, s1)), R(sign));
+        const C t3 = cmuli(cadd(csub(cscale(b1, s3), cscale(b2, s1)), cscale(b3, s2)), R(sign));
+        v[0] = cadd(v[0], cadd(cadd(a1, a2), a3));
+        v[1] = cadd(m1, t1);
+        v[6] = csub(m1, t1);
+        v[2] = cadd(m2, t2);
+        v[5] = csub(m2, t2);
+        v[3] = cadd(m3, t3);
+        v[4] = csub(m3, t3);
+    }
+};
+
 // One Stockham stage of radix RAD: butterfly j reads a[j + r P/RAD], twiddles
 // by w^{(j mod Ns) r P/(Ns RAD)}, applies the RAD-point DFT and writes
-// b[(j / Ns) Ns RAD + (j mod Ns) + r Ns].  Radix 7 uses the direct sum with
-// the line's twiddle table.
+// b[(j / Ns) Ns RAD + (j mod Ns) + r Ns].
 // In the first stage (Ns = 1, FIRST) every twiddle is 1; if moreover only
 // a[0 .. nz) can be nonzero and nz <= P / RAD (a zero-padded input), each
 // butterfly sees one nonzero input and all its outputs equal it.
@@ -158,20 +182,7 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
             const C x = a[j + r * PR];
             v[r] = (r == 0 || FIRST) ? x : cmul(x, twiddle(tw, step * r, sign));
         }
-        if constexpr (RAD == 7) {
-            C out[7];
-#pragma unroll
-            for (int r = 0; r < 7; ++r) {
-                C acc = v[0];
-#pragma unroll
-                for (int q = 1; q < 7; ++q) acc = cadd(acc, cmul(v[q], twiddle(tw, ((r * q) % 7) * PR, sign)));
-                out[r] = acc;
-            }
-#pragma unroll
-            for (int r = 0; r < 7; ++r) v[r] = out[r];
-        } else {
-            Dft<RAD, R>::run(v, sign);
-        }
+        Dft<RAD, R>::run(v, sign);
         const int base = qd * Ns * RAD + k;
 #pragma unroll
         for (int r = 0; r < RAD; ++r) b[base + r * Ns] = v[r];

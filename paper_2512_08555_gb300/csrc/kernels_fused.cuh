@@ -908,30 +908,52 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
         return;
     }
     record_prologue(hs, lk, b);
-    build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     if constexpr (NC != 0 && sizeof(T) == 4) {
-        // pairs of nodes adjacent along x, as in the smoother (two z-adjacent
-        // pairs per thread in a 128-thread CTA)
-        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2, NU = NP / 2;
-        auto fpair = [&](const Col& c, int b0, size_t fi) {
-            const T ua = su[b0 + c.dX + c.dY + c.dZ], ub = su[b0 + 1 + c.dX + c.dY + c.dZ];
-            const T la = T(LW<M>::c) * ua + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-            const T lb = T(LW<M>::c) * ub + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-            F[fi] += scale * la;
-            F[fi + 2] += scale * lb;
-            H[fi] = ua;
-            H[fi + 2] = ub;
-        };
+        // F staged in shared memory over the interpolation scratch as in the
+        // residual kernel, updated in place and written back by columns;
+        // node pairs adjacent along x as in the smoother
+        T* fs = pool;
+        const bool early = hs.rec[REC_NREG] == 0;
+        if (early) load_rhs(fs, F, b, n);
+        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+        if (!early) {
+            load_rhs(fs, F, b, n);
+            cp_async_wait<0>();
+            __syncthreads();
+        }
+        const int Fp = split_fp(n, 4), Fr = split_fr(n, 4), F3 = split_f3(n, 4);
+        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2;
 #pragma unroll
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
             for (int p = threadIdx.x; p < NP; p += blockDim.x) {
                 const Pair q = pair_of(p);
                 const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
-                fpair(c, b0, b * n3 + ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo);
+                const T ua = su[b0 + c.dX + c.dY + c.dZ], ub = su[b0 + 1 + c.dX + c.dY + c.dZ];
+                const T la = T(LW<M>::c) * ua + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const T lb = T(LW<M>::c) * ub + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const int si = col * F3 + q.l * Fp + q.j * Fr + q.i;
+                fs[si] += scale * la;
+                fs[si + 1] += scale * lb;
+                const size_t fi = b * n3 + ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo;
+                H[fi] = ua;
+                H[fi + 2] = ub;
+            }
+        }
+        __syncthreads();
+        T* Fb = F + b * n3;
+        for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+            const int y = c / n, x = c - y * n;
+            const T* scol = fs + (((y & 1) << 1) | (x & 1)) * F3 + (y >> 1) * Fr + (x >> 1);
+            T* gcol = Fb + c;
+#pragma unroll
+            for (int m = 0; m < NC / 2; ++m) {
+                gcol[(size_t)(2 * m) * n * n] = scol[m * Fp];
+                gcol[(size_t)(2 * m + 1) * n * n] = scol[4 * F3 + m * Fp];
             }
         }
     } else {
+        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
 #pragma unroll
@@ -1053,6 +1075,43 @@ __global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, co
         }
     }
     bmax_atomic(__longlong_as_double((long long)mb), out + (lk.prob ? lk.prob[b] : 0));
+}
+
+// ---------------------------------------------------------------- f* = R^M f (M = 2, 4), fused with its ghost layer
+// Raw f of level k in the (n+2)^3 box layout (Af; the level-(k-1) array Ac
+// holds f on covered nodes by injection): build_halo() builds the one ghost
+// layer R^2 and R^4 read (same-level copies, I-point interpolation at
+// resolution jumps, zero outside the domain from the stored ghost layer,
+// which nothing writes), then f* = R^M f on the listed leaf blocks (Sec. 3.2;
+// the arithmetic of k_rhs_star).
+template <int M, int I, int NC>
+__global__ void __launch_bounds__(512) k_rhs_fused(double* __restrict__ F, const double* __restrict__ Af,
+                                                   const double* __restrict__ Ac, const int* __restrict__ blocks,
+                                                   LevelView lk, int n_arg) {
+    static_assert(M == 2 || M == 4, "R^6 reads two ghost layers");
+    const int n = NC ? NC : n_arg;
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    double* su = reinterpret_cast<double*>(fz_smem);
+    const Split sp = split_of<double>(n);
+    double* pool = su + 8 * sp.H3p;
+    double* patch = pool + pool_size(n, I);
+    __shared__ HaloSmem hs;
+    const int b = blocks[blockIdx.x];
+    record_prologue(hs, lk, b);
+    build_halo<double, I>(su, pool, patch, hs.rec, Af, Ac, lk, b, n, sp);
+    double* out = F + (size_t)b * n * n * n;
+    for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
+        const int x = t % n, y = (t / n) % n, z = t / (n * n);
+        const int X = x + 1, Y = y + 1, Z = z + 1;
+        double v = su[sp.at(X, Y, Z)];
+        if (M == 4) {
+            const double sf = (su[sp.at(X - 1, Y, Z)] + su[sp.at(X + 1, Y, Z)]) +
+                              (su[sp.at(X, Y - 1, Z)] + su[sp.at(X, Y + 1, Z)]) +
+                              (su[sp.at(X, Y, Z - 1)] + su[sp.at(X, Y, Z + 1)]);
+            v = 0.5 * v + sf * (1.0 / 12.0);
+        }
+        out[t] = v;
+    }
 }
 
 // ---------------------------------------------------------------- halo dump (step API)
@@ -1374,7 +1433,7 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
         nsm < 1)
         nsm = 1;
     int fmode = 0;
-    {
+    if (!(nt & SMOOTH_NOSTAGE)) {
         if (fused_smem<T>(n, M + 2, 1) <= (size_t)MAX_DYN_SMEM) fmode = 1;
         const size_t s2 = fused_smem<T>(n, M + 2, 2);
         const size_t per_sm = 228 * 1024, per_cta = s2 + sizeof(HaloSmem) + 1024;
@@ -1382,7 +1441,7 @@ void launch_smooth_fused(T* Uout, const T* Uin, const T* F, const T* Uc, LevelVi
     }
     const int fst = fmode;
     const size_t sm = fused_smem<T>(n, M + 2, fmode);
-    const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
+    const int ct = cta_size_fixed(n, nt & SMOOTH_NT_MASK, sizeof(T) == 4);
     if (M == 2) smooth_m<2, T>(Uout, Uin, F, Uc, lk, lk.nb, n, T(h2 * LW<2>::den), fst, ct, sm, s);
     if (M == 4) smooth_m<4, T>(Uout, Uin, F, Uc, lk, lk.nb, n, T(h2 * LW<4>::den), fst, ct, sm, s);
     if (M == 6) smooth_m<6, T>(Uout, Uin, F, Uc, lk, lk.nb, n, T(h2 * LW<6>::den), fst, ct, sm, s);
@@ -1406,13 +1465,22 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
                       int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     attrs_fas<T>();
-    const size_t sm = fused_smem<T>(n, M + 2);
+    // FP32 block size 16 stages F over the interpolation scratch (fmode-1 sizing)
+    const size_t sm = fused_smem<T>(n, M + 2, (sizeof(T) == 4 && n == NC_FIXED) ? 1 : 0);
     const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
     if (M == 2) fas_m<2, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
     if (M == 4) fas_m<4, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, s);
     if (M == 6) fas_m<6, T>(F, H, U, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, s);
 }
 
+
+template <int M>
+static void rhs_fused_m(double* F, const double* Af, const double* Ac, const int* blocks, int nblocks, const LevelView& lk,
+                        int n, size_t sm, cudaStream_t s) {
+    constexpr int I = M + 2;
+    if (n == NC_FIXED) k_rhs_fused<M, I, NC_FIXED><<<nblocks, 256, sm, s>>>(F, Af, Ac, blocks, lk, n);
+    else k_rhs_fused<M, I, 0><<<nblocks, 256, sm, s>>>(F, Af, Ac, blocks, lk, n);
+}
 
 template <typename T>
 void launch_halo_dump(T* U, const T* Uc, LevelView lk, LevelView lc, int n, int M, cudaStream_t s) {

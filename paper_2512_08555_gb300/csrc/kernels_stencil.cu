@@ -460,6 +460,15 @@ void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int 
 // them (local coordinates -1 .. n-1, from the lower neighbours); the window
 // of X is complete when those neighbours exist along the axes where 2X sits
 // on B's lower face (the upper side always lies in B).
+// Row stride of the restriction's residual window: at least n + 1 (the
+// n/2 + 1 even and n/2 odd columns of a row), and 4 (mod 16), so that a warp
+// of 8 consecutive coarse i by 4 consecutive j reads 32 distinct banks.
+__host__ __device__ inline int restrict_row(int n) {
+    int r = n + 1;
+    while (r % 16 != 4) ++r;
+    return r;
+}
+
 template <typename T>
 __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __restrict__ Uf, const T* __restrict__ Rf,
                            LevelView lf, int n, const T* __restrict__ off) {
@@ -479,20 +488,25 @@ __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __re
                     if (nb27[dir27(-sx, -sy, -sz)] < 0) ok = 0;
         ins[m] = ok;
     }
-    const int N1 = n + 1, N12 = N1 * N1, n3 = n * n * n, h = n >> 1;
-    // the residual window, fine nodes [-1, n)^3, one thread per (x, y) column
-    // walking z (cp.async); nodes of missing neighbours read as 0
-    for (int c = threadIdx.x; c < N12; c += blockDim.x) {
+    const int N1 = n + 1, n3 = n * n * n, h = n >> 1;
+    // the residual window, fine nodes [-1, n)^3 (window coordinates X = x + 1
+    // etc.), split by the parity of X within each row (see restrict_rows), so
+    // that the full weighting's reads at X = 2i, 2i + 1, 2i + 2 of a warp's
+    // consecutive i are consecutive words; one thread per (X, Y) column walking
+    // Z (cp.async); nodes of missing neighbours read as 0
+    const int RR = restrict_row(n), OE = h + 1, PR = RR * N1;
+    auto wi = [&](int X, int Y, int Z) { return Z * PR + Y * RR + (X & 1) * OE + (X >> 1); };
+    for (int c = threadIdx.x; c < N1 * N1; c += blockDim.x) {
         const int Y = c / N1, X = c - Y * N1, x = X - 1, y = Y - 1;
         const int ex = x < 0 ? -1 : 0, ey = y < 0 ? -1 : 0;
-        T* dcol = sr + Y * N1 + X;
+        T* dcol = sr + wi(X, Y, 0);
         for (int ez = -1; ez <= 0; ++ez) {
             const int blk = nb27[dir27(ex, ey, ez)];
             const int z0 = ez < 0 ? -1 : 0, z1 = ez < 0 ? 0 : n;
             const T* scol = Rf + (blk >= 0 ? (size_t)blk * n3 + (size_t)((y - ey * n) * n + (x - ex * n)) : 0);
             for (int z = z0; z < z1; ++z) {
-                if (blk >= 0) cp_async_el(dcol + (z + 1) * N12, scol + (size_t)(z - ez * n) * n * n);
-                else dcol[(z + 1) * N12] = T(0);
+                if (blk >= 0) cp_async_el(dcol + (z + 1) * PR, scol + (size_t)(z - ez * n) * n * n);
+                else dcol[(z + 1) * PR] = T(0);
             }
         }
     }
@@ -509,15 +523,18 @@ __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __re
         const int cidx = ((oz + l) * n + oy + j) * n + ox + i;
         Uc[(size_t)P * S3 + ((oz + l + 1) * S + oy + j + 1) * S + ox + i + 1] =
             Uf[(size_t)B * S3 + ((fz + 1) * S + fy + 1) * S + fx + 1] + (off ? off[(size_t)P * n3 + cidx] : T(0));
-        const T* c = sr + ((fz + 1) * N1 + fy + 1) * N1 + fx + 1;
+        // window X = fx + 1 = 2i + 1 (odd half, index i); its x neighbours are
+        // X = 2i, 2i + 2 (even half, indices i, i + 1)
+        const T* c = sr + wi(fx + 1, fy + 1, fz + 1);
+        const T* ce = sr + wi(fx, fy + 1, fz + 1);
         T v;
         if (ins[(fx == 0) | ((fy == 0) << 1) | ((fz == 0) << 2)]) {
             T acc = T(0);
             for (int dz = -1; dz <= 1; ++dz) {
                 T accy = T(0);
                 for (int dy = -1; dy <= 1; ++dy) {
-                    const T* r = c + dz * N12 + dy * N1;
-                    accy += T(2 - (dy < 0 ? -dy : dy)) * (r[-1] + T(2) * r[0] + r[1]);
+                    const int d = dz * PR + dy * RR;
+                    accy += T(2 - (dy < 0 ? -dy : dy)) * (ce[d] + T(2) * c[d] + ce[d + 1]);
                 }
                 acc += T(2 - (dz < 0 ? -dz : dz)) * accy;
             }
@@ -536,7 +553,7 @@ void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, LevelView lf, int n
     once_per_device(attr, [] {
         cudaFuncSetAttribute(k_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     });
-    const size_t sm = sizeof(T) * (n + 1) * (n + 1) * (n + 1);
+    const size_t sm = sizeof(T) * (size_t)restrict_row(n) * (n + 1) * (n + 1);
     k_restrict<T><<<lf.nb, 256, sm, s>>>(Uc, Fc, Uf, Rf, lf, n, off);
 }
 template void launch_restrict<double>(double*, double*, const double*, const double*, LevelView, int, const double*,
@@ -584,13 +601,50 @@ __global__ void k_prolong(T* __restrict__ Uf, const T* __restrict__ Uc, const T*
             }
             return (by ? T(0.5) : T(1)) * accy;
         };
-        T* col = Ub + (y + 1) * S + x + 1;
         T cur = plane(0);
-        for (int az = 0; az < h; ++az) {
-            const T nxt = plane(az + 1);
-            col[(2 * az + 1) * S2] += cur;
-            col[(2 * az + 2) * S2] += T(0.5) * (cur + nxt);
-            cur = nxt;
+        if constexpr (sizeof(T) == 4) {
+            // FP32: the corrections go to shared memory first (below)
+            T* cc = e + E * E * E + c;
+            for (int az = 0; az < h; ++az) {
+                const T nxt = plane(az + 1);
+                cc[(2 * az) * n * n] = cur;
+                cc[(2 * az + 1) * n * n] = T(0.5) * (cur + nxt);
+                cur = nxt;
+            }
+        } else {
+            T* col = Ub + (y + 1) * S + x + 1;
+            for (int az = 0; az < h; ++az) {
+                const T nxt = plane(az + 1);
+                col[(2 * az + 1) * S2] += cur;
+                col[(2 * az + 2) * S2] += T(0.5) * (cur + nxt);
+                cur = nxt;
+            }
+        }
+    }
+    if constexpr (sizeof(T) == 4) {
+        // FP32: u += correction over the whole planes z = 1..n of the block's
+        // box with 16-byte accesses (S^2 is a multiple of 4 for even n), whole
+        // 32-byte sectors and independent loads; ghost entries add nothing
+        __syncthreads();
+        const T* corr = e + E * E * E;
+        float4* p = reinterpret_cast<float4*>(Ub + S2);
+        auto add = [&](float& v, int X, int Y, int Zr) {
+            if (X >= 1 && X <= n && Y >= 1 && Y <= n) v += corr[(Zr * n + Y - 1) * n + X - 1];
+        };
+        const int NV = n * S2 / 4;
+        for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+            const int q = 4 * t, Zr = q / S2, r = q - Zr * S2, Y = r / S, X = r - Y * S;
+            float4 v = p[t];
+            add(v.x, X, Y, Zr);
+            add(v.y, X + 1, Y, Zr);
+            if (X + 2 < S) {
+                add(v.z, X + 2, Y, Zr);
+                add(v.w, X + 3, Y, Zr);
+            } else {             // the row ends: columns 0 and 1 of the next row (never the next plane)
+                add(v.z, 0, Y + 1, Zr);
+                add(v.w, 1, Y + 1, Zr);
+            }
+            p[t] = v;
         }
     }
 }
@@ -599,7 +653,13 @@ template <typename T>
 void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc, int n, cudaStream_t s) {
     if (lf.nb == 0) return;
     const int E = n / 2 + 1;
-    k_prolong<T><<<lf.nb, 256, sizeof(T) * E * E * E, s>>>(Uf, Uc, Hc, lf, lc, n);
+    // FP32 adds an n^3 buffer of corrections (64 KB at n = 24: opt-in size)
+    const size_t sm = sizeof(T) * ((size_t)E * E * E + (sizeof(T) == 4 ? (size_t)n * n * n : 0));
+    static std::once_flag attr[MAX_DEVICES];
+    once_per_device(attr, [] {
+        cudaFuncSetAttribute(k_prolong<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    });
+    k_prolong<T><<<lf.nb, 256, sm, s>>>(Uf, Uc, Hc, lf, lc, n);
 }
 template void launch_prolong<double>(double*, const double*, const double*, LevelView, LevelView, int, cudaStream_t);
 template void launch_prolong<float>(float*, const float*, const float*, LevelView, LevelView, int, cudaStream_t);

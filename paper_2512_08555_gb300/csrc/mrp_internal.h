@@ -308,6 +308,11 @@ void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc,
 template <typename T>
 void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
 // stencil kernels with the ghost layer built in shared memory (kernels_fused.cuh, fused_*.cu);
+// Smoother launch choice (the `nt` argument of launch_smooth_fused): the CTA
+// size in the low bits; SMOOTH_NOSTAGE reads the right-hand side from global
+// memory where it is used instead of staging it in shared memory (less shared
+// memory per CTA, so more CTAs per SM).
+constexpr int SMOOTH_NT_MASK = 0xFFF, SMOOTH_NOSTAGE = 1 << 12;
 // fused_smem_bytes: their dynamic shared memory for block size n, order M and
 // element size el (bytes), without a staged right-hand side
 size_t fused_smem_bytes(int n, int M, int el);
@@ -331,6 +336,10 @@ void launch_ghost_fill(double* A, int g, const double* Ac, int gc, LevelView lk,
 void launch_scatter_leaves(Handle& h, const double* f, cudaStream_t s);
 void launch_gather_leaves(Handle& h, double* u, cudaStream_t s);
 void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int nleaf, int n, int M, cudaStream_t s);
+// f* = R^M f (M = 2, 4) on the listed leaf blocks of level k, the one ghost layer built in the kernel from raw f
+// in the (n+2)^3 box layout (Af: level k; Ac: level k-1, covered nodes injected)
+void launch_rhs_fused(double* F, const double* Af, const double* Ac, const int* blocks, int nblocks, LevelView lk, int n,
+                      int M, cudaStream_t s);
 void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, const int* prob,
                    cudaStream_t s);
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s);

@@ -318,7 +318,7 @@ int upload_tables(Handle& h) {
         if ((rc = alloc_field(lv.F, lv.nb * n * n * n))) return rc;
         if ((rc = alloc_field(lv.R, lv.nb * n * n * n))) return rc;
         if ((rc = alloc_field(lv.H, lv.nb * n * n * n))) return rc;
-        if ((rc = alloc_field(lv.Fraw, lv.nb * S4 * S4 * S4))) return rc;
+        if (h.M == 6 && (rc = alloc_field(lv.Fraw, lv.nb * S4 * S4 * S4))) return rc;   // R^6: two ghost layers
         if (h.stop_rule == MRP_STOP_CAUCHY && (rc = alloc_field(lv.Uprev, lv.nb * n * n * n))) return rc;
     }
     if ((rc = up(h.leaf_level, h.h_leaf_level))) return rc;
@@ -516,6 +516,26 @@ static void prolong(Handle& h, int k, cudaStream_t s) {
 }
 
 static void prepare_rhs(Handle& h, const double* f, cudaStream_t s) {
+    if (h.M <= 4) {
+        // R^2, R^4 read one ghost layer: raw f goes into the FP64 u arrays
+        // (zero ghost layers; u is cleared again before the cycles), covered
+        // nodes take its injection, and each level's f* is formed with its
+        // ghost layer built in the kernel
+        PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1 + h.L + (h.L + 1));
+        const size_t S = h.n + 2;
+        LevelPtrs lp{};
+        for (int k = 0; k <= h.L; ++k) {
+            cudaMemsetAsync(h.lv[k].U, 0, sizeof(double) * h.lv[k].nb * S * S * S, s);
+            lp.p[k] = h.lv[k].U;
+        }
+        launch_scatter_leaves_to(h, f, lp, 1, true, s);
+        for (int k = h.L - 1; k >= 0; --k)
+            launch_inject_to_parent<double>(h.lv[k].U, 1, h.lv[k + 1].U, 1, h.lv[k + 1].view(), h.n, nullptr, s);
+        for (int k = 0; k <= h.L; ++k)
+            launch_rhs_fused(h.lv[k].F, h.lv[k].U, k >= 1 ? h.lv[k - 1].U : nullptr, h.lv[k].leaf_blocks, h.lv[k].nleaf,
+                             h.lv[k].view(), h.n, h.M, s);
+        return;
+    }
     PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1 + h.L + 2 * (h.L + 1));
     const size_t S4 = h.n + 4;
     for (int k = 0; k <= h.L; ++k) cudaMemsetAsync(h.lv[k].Fraw, 0, sizeof(double) * h.lv[k].nb * S4 * S4 * S4, s);
@@ -593,6 +613,9 @@ struct SolveState {
 template <typename T>
 static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     const std::vector<int> cta = {128, 256, 512};
+    // the smoother may also read its right-hand side from global memory
+    std::vector<int> smooth_cand = cta;
+    for (int c : {128, 256}) smooth_cand.push_back(c | SMOOTH_NOSTAGE);
     constexpr int pi = pidx<T>();
     auto pick_from = [&](const std::vector<int>& cand, auto&& launch) {
         float best = 1e30f;
@@ -615,7 +638,7 @@ static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_
         const double hk = level_h(h, k);
         Level& lv = h.lv[k];
         if (k >= 1) {
-            h.nt_smooth[pi][k] = pick([&](int nt) {
+            h.nt_smooth[pi][k] = pick_from(smooth_cand, [&](int nt) {
                 launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), lv.view(),
                                        view_or_empty(h, k - 1), h.n, h.M, hk * hk, nt, s);
             });
@@ -1076,7 +1099,9 @@ int mrp_field_copy(mrp_handle* H, int32_t field, int32_t level, double* buf, int
         case MRP_FIELD_F: p = lv.F; cnt = lv.nb * n * n * n; break;
         case MRP_FIELD_R: p = lv.R; cnt = lv.nb * n * n * n; break;
         case MRP_FIELD_UHAT: p = lv.H; cnt = lv.nb * n * n * n; break;
-        case MRP_FIELD_FRAW: p = lv.Fraw; cnt = lv.nb * (n + 4) * (n + 4) * (n + 4); break;
+        case MRP_FIELD_FRAW:
+            if (!lv.Fraw) return MRP_ERR_UNSUPPORTED;        // kept for order 6 only
+            p = lv.Fraw; cnt = lv.nb * (n + 4) * (n + 4) * (n + 4); break;
         default: return MRP_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
