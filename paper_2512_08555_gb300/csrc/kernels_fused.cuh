@@ -184,6 +184,65 @@ __device__ __forceinline__ T offc_s(const T* __restrict__ a, int b0, int dX, int
     return acc;
 }
 
+// Packed FP32 pairs (Blackwell's f32x2 arithmetic: one instruction applies
+// the same IEEE operation, round to nearest, to both halves).  A node pair of
+// the fixed block size 16 runs the same operations on neighbour values one
+// word apart, so its two stencils are evaluated as one packed stencil.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2pk(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2up(f2_t v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2_t f2add(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2sub(f2_t a, f2_t b) {
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2mul(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t f2splat(float a) { return f2pk(a, a); }
+
+// offc_s for the nodes with (-1,-1,-1) neighbours at b0 and b0 + 1 at once
+// (packed: low half the first node, high half the second), same sums in the
+// same order.
+template <int M>
+__device__ __forceinline__ f2_t offc2(const float* __restrict__ a, int b0, int dX, int dY, int dZ, int H, int H2) {
+    using W = LW<M>;
+    auto L = [&](int o) { return f2pk(a[b0 + o], a[b0 + 1 + o]); };
+    f2_t acc = f2mul(f2splat(float(W::f)),
+                     f2add(f2add(f2add(L(dY + dZ), L(1 + dY + dZ)), f2add(L(dX + dZ), L(dX + H + dZ))),
+                           f2add(L(dX + dY), L(dX + dY + H2))));
+    if (W::e != 0) {
+        const f2_t e = f2add(f2add(f2add(f2add(f2add(f2add(L(dZ), L(1 + dZ)), f2add(L(H + dZ), L(1 + H + dZ))),
+                                                   f2add(L(dY), L(1 + dY))),
+                                             f2add(L(dY + H2), L(1 + dY + H2))),
+                                       f2add(L(dX), L(dX + H))),
+                                 f2add(L(dX + H2), L(dX + H + H2)));
+        acc = W::e == 1 ? f2add(acc, e) : f2fma(f2splat(float(W::e)), e, acc);
+    }
+    if (W::k != 0) {
+        const f2_t k = f2add(f2add(f2add(L(0), L(1)), f2add(L(H), L(1 + H))),
+                             f2add(f2add(L(H2), L(1 + H2)), f2add(L(H + H2), L(1 + H + H2))));
+        acc = W::k == 1 ? f2add(acc, k) : f2fma(f2splat(float(W::k)), k, acc);
+    }
+    return acc;
+}
+
 template <int I> __device__ __forceinline__ double midw(int m);
 template <> __device__ __forceinline__ double midw<4>(int m) { return (m == 0 || m == 3 ? -1.0 : 9.0) / 16.0; }
 template <> __device__ __forceinline__ double midw<6>(int m) {
@@ -710,15 +769,14 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
                     fa0 = Fb[fi]; fb0 = Fb[fi + 2];
                     fa1 = Fb[fi + 2 * n * n]; fb1 = Fb[fi + 2 * n * n + 2];
                 }
-                const T sa0 = offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const T sb0 = offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const T sa1 = offc_s<M>(su, b1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const T sb1 = offc_s<M>(su, b1 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const f2_t s0 = offc2<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const f2_t s1 = offc2<M>(su, b1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const f2_t hd = f2splat(h2den), ic = f2splat(inv_c);
+                const f2_t v0 = f2mul(f2sub(f2mul(hd, f2pk(fa0, fb0)), s0), ic);
+                const f2_t v1 = f2mul(f2sub(f2mul(hd, f2pk(fa1, fb1)), s1), ic);
                 const int d = c.dX + c.dY + c.dZ;
-                su[b0 + d] = (h2den * fa0 - sa0) * inv_c;
-                su[b0 + 1 + d] = (h2den * fb0 - sb0) * inv_c;
-                su[b1 + d] = (h2den * fa1 - sa1) * inv_c;
-                su[b1 + 1 + d] = (h2den * fb1 - sb1) * inv_c;
+                f2up(v0, su[b0 + d], su[b0 + 1 + d]);
+                f2up(v1, su[b1 + d], su[b1 + 1 + d]);
                 __syncthreads();
                 continue;
             }
@@ -736,10 +794,9 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
                     fa = Fb[fi];
                     fb = Fb[fi + 2];
                 }
-                const T sa = offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const T sb = offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                su[b0 + c.dX + c.dY + c.dZ] = (h2den * fa - sa) * inv_c;
-                su[b0 + 1 + c.dX + c.dY + c.dZ] = (h2den * fb - sb) * inv_c;
+                const f2_t sab = offc2<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                const f2_t v = f2mul(f2sub(f2mul(f2splat(h2den), f2pk(fa, fb)), sab), f2splat(inv_c));
+                f2up(v, su[b0 + c.dX + c.dY + c.dZ], su[b0 + 1 + c.dX + c.dY + c.dZ]);
             }
             __syncthreads();
         }
@@ -816,8 +873,10 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
         const int Fp = split_fp(n, 4), Fr = split_fr(n, 4), F3 = split_f3(n, 4);
         constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2, NU = NP / 2;
         auto lpair = [&](const Col& c, int b0, T& la, T& lb) {
-            la = T(LW<M>::c) * su[b0 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-            lb = T(LW<M>::c) * su[b0 + 1 + c.dX + c.dY + c.dZ] + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+            const int d = c.dX + c.dY + c.dZ;
+            const f2_t l = f2fma(f2splat(float(LW<M>::c)), f2pk(su[b0 + d], su[b0 + 1 + d]),
+                                 offc2<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2));
+            f2up(l, la, lb);
         };
 #pragma unroll
         for (int col = 0; col < 8; ++col) {
@@ -930,8 +989,9 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
                 const Pair q = pair_of(p);
                 const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i;
                 const T ua = su[b0 + c.dX + c.dY + c.dZ], ub = su[b0 + 1 + c.dX + c.dY + c.dZ];
-                const T la = T(LW<M>::c) * ua + offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2);
-                const T lb = T(LW<M>::c) * ub + offc_s<M>(su, b0 + 1, c.dX, c.dY, c.dZ, sp.H, sp.H2);
+                T la, lb;
+                f2up(f2fma(f2splat(float(LW<M>::c)), f2pk(ua, ub), offc2<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2)),
+                     la, lb);
                 const int si = col * F3 + q.l * Fp + q.j * Fr + q.i;
                 fs[si] += scale * la;
                 fs[si + 1] += scale * lb;
