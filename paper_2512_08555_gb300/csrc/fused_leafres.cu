@@ -16,7 +16,7 @@ void launch_leafres_fused(float* R, const double* U, const double* F, const doub
 }
 
 void launch_rhs_fused(double* F, const double* Af, const double* Ac, const int* blocks, int nblocks, LevelView lk,
-                             int n, int M, cudaStream_t s) {
+                             int n, int M, unsigned long long* fmax_out, cudaStream_t s) {
     if (nblocks == 0) return;
     static std::once_flag done[MAX_DEVICES];
     once_per_device(done, [] {
@@ -24,8 +24,8 @@ void launch_rhs_fused(double* F, const double* Af, const double* Ac, const int* 
         allow(k_rhs_fused<4, 6, NC_FIXED>); allow(k_rhs_fused<4, 6, 0>);
     });
     const size_t sm = fused_smem<double>(n, M + 2);
-    if (M == 2) rhs_fused_m<2>(F, Af, Ac, blocks, nblocks, lk, n, sm, s);
-    if (M == 4) rhs_fused_m<4>(F, Af, Ac, blocks, nblocks, lk, n, sm, s);
+    if (M == 2) rhs_fused_m<2>(F, Af, Ac, blocks, nblocks, lk, n, fmax_out, sm, s);
+    if (M == 4) rhs_fused_m<4>(F, Af, Ac, blocks, nblocks, lk, n, fmax_out, sm, s);
 }
 
 }  // namespace mrp

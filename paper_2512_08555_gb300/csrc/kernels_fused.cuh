@@ -424,9 +424,7 @@ __device__ __forceinline__ void halo_issue(T* __restrict__ su, T* __restrict__ p
     if constexpr (INTERP) {
         const int nreg = rec[REC_NREG];
         constexpr int plo = 4 - I / 2;
-        const int TN = tan_n(n, I);
         const int PL = h + I, PL2 = PL * PL;
-        const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
         const int* __restrict__ pnbr = rec + REC_PNBR;
         const int* __restrict__ pch = rec + REC_PCH;
         // 2a. coarse patch over the hull, copied together with the box; patch
@@ -482,10 +480,8 @@ __device__ __forceinline__ void halo_interpolate(T* __restrict__ su, T* __restri
     const int nreg = rec[REC_NREG];
     constexpr int plo = 4 - I / 2;
     const int TN = tan_n(n, I);
-    const int PL = h + I, PL2 = PL * PL;
+    const int PL = h + I;
     const int up = 4 + h - plo;          // patch index coincident with fine coordinate n
-    const int* __restrict__ pnbr = rec + REC_PNBR;
-    const int* __restrict__ pch = rec + REC_PCH;
     if (nreg == 0) return;
     T w[I];
 #pragma unroll
@@ -1147,7 +1143,7 @@ __global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, co
 template <int M, int I, int NC>
 __global__ void __launch_bounds__(512) k_rhs_fused(double* __restrict__ F, const double* __restrict__ Af,
                                                    const double* __restrict__ Ac, const int* __restrict__ blocks,
-                                                   LevelView lk, int n_arg) {
+                                                   LevelView lk, int n_arg, unsigned long long* fmax_out) {
     static_assert(M == 2 || M == 4, "R^6 reads two ghost layers");
     const int n = NC ? NC : n_arg;
     extern __shared__ __align__(16) unsigned char fz_smem[];
@@ -1160,6 +1156,7 @@ __global__ void __launch_bounds__(512) k_rhs_fused(double* __restrict__ F, const
     record_prologue(hs, lk, b);
     build_halo<double, I>(su, pool, patch, hs.rec, Af, Ac, lk, b, n, sp);
     double* out = F + (size_t)b * n * n * n;
+    unsigned long long mb = 0;        // max |f*| as a bit pattern
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
         const int X = x + 1, Y = y + 1, Z = z + 1;
@@ -1171,7 +1168,10 @@ __global__ void __launch_bounds__(512) k_rhs_fused(double* __restrict__ F, const
             v = 0.5 * v + sf * (1.0 / 12.0);
         }
         out[t] = v;
+        mb = umax64(mb, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL);
     }
+    // max |f*| over the leaves (the stop rule's scale), per problem
+    bmax_atomic(__longlong_as_double((long long)mb), fmax_out + (lk.prob ? lk.prob[b] : 0));
 }
 
 // ---------------------------------------------------------------- halo dump (step API)
@@ -1400,10 +1400,6 @@ inline int cta_size_fixed(int n, int nt, bool fixed_items) {
     return (fixed_items && n == 16 && c > 256) ? 256 : c;
 }
 
-// The fused kernels come in two builds: block size 16 fixed at compile time
-// (constant strides and offsets) and any block size at run time.
-constexpr int NC_FIXED = 16;
-
 // Per-family shared-memory attributes, set once per device (each family's
 // instantiations live in one translation unit).
 template <typename T>
@@ -1536,10 +1532,10 @@ void launch_fas_fused(T* F, T* H, const T* U, const T* Uc, LevelView lk, LevelVi
 
 template <int M>
 static void rhs_fused_m(double* F, const double* Af, const double* Ac, const int* blocks, int nblocks, const LevelView& lk,
-                        int n, size_t sm, cudaStream_t s) {
+                        int n, unsigned long long* fmax_out, size_t sm, cudaStream_t s) {
     constexpr int I = M + 2;
-    if (n == NC_FIXED) k_rhs_fused<M, I, NC_FIXED><<<nblocks, 256, sm, s>>>(F, Af, Ac, blocks, lk, n);
-    else k_rhs_fused<M, I, 0><<<nblocks, 256, sm, s>>>(F, Af, Ac, blocks, lk, n);
+    if (n == NC_FIXED) k_rhs_fused<M, I, NC_FIXED><<<nblocks, 256, sm, s>>>(F, Af, Ac, blocks, lk, n, fmax_out);
+    else k_rhs_fused<M, I, 0><<<nblocks, 256, sm, s>>>(F, Af, Ac, blocks, lk, n, fmax_out);
 }
 
 template <typename T>

@@ -93,11 +93,29 @@ void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int 
 // U64 += U32 on the interior of every block of a level.
 __global__ void k_accumulate_u(double* __restrict__ U64, const float* __restrict__ U32, int n) {
     const int b = blockIdx.x;
-    const int S = n + 2, S2 = S * S, S3 = S2 * S;
-    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {       // one thread per (x, y) column
-        const int y = c / n, x = c - y * n;
-        const size_t o = (size_t)b * S3 + (size_t)((y + 1) * S + x + 1);
-        for (int z = 1; z <= n; ++z) U64[o + (size_t)z * S2] += (double)U32[o + (size_t)z * S2];
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, nn = n * n, n3 = nn * n;
+    const unsigned mnn = magic_of(nn), mn = magic_of(n);
+    const size_t base = (size_t)b * S3 + S2 + S + 1;     // interior node (0, 0, 0)
+    // K nodes per thread and round, all loads issued before the stores (the
+    // stores could alias later loads as far as the compiler knows)
+    constexpr int K = 4;
+    for (int t0 = threadIdx.x; t0 < n3; t0 += K * blockDim.x) {
+        double u[K];
+        float v[K];
+        size_t o[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int t = t0 + k * blockDim.x;
+            const int z = fdiv(t, mnn), r = t - z * nn, y = fdiv(r, mn), x = r - y * n;
+            o[k] = base + (size_t)z * S2 + y * S + x;
+            if (t < n3) {
+                u[k] = U64[o[k]];
+                v[k] = U32[o[k]];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (t0 + k * blockDim.x < n3) U64[o[k]] = u[k] + (double)v[k];
     }
 }
 

@@ -469,9 +469,10 @@ __host__ __device__ inline int restrict_row(int n) {
     return r;
 }
 
-template <typename T>
+template <typename T, int NC>
 __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __restrict__ Uf, const T* __restrict__ Rf,
-                           LevelView lf, int n, const T* __restrict__ off) {
+                           LevelView lf, int n_arg, const T* __restrict__ off) {
+    const int n = NC ? NC : n_arg;    // NC: block size fixed at compile time (0: runtime)
     extern __shared__ __align__(16) unsigned char rs_raw[];
     T* sr = reinterpret_cast<T*>(rs_raw);
     __shared__ int nb27[27];
@@ -518,7 +519,7 @@ __global__ void k_restrict(T* __restrict__ Uc, T* __restrict__ Fc, const T* __re
     const int S = n + 2, S3 = S * S * S;
     const unsigned mh = magic_of(h);
     for (int q = threadIdx.x; q < h * h * h; q += blockDim.x) {
-        const int q1 = fdiv(q, mh), i = q - q1 * h, l = fdiv(q1, mh), j = q1 - l * h;
+        const int q1 = NC ? q / h : fdiv(q, mh), i = q - q1 * h, l = NC ? q1 / h : fdiv(q1, mh), j = q1 - l * h;
         const int fx = 2 * i, fy = 2 * j, fz = 2 * l;
         const int cidx = ((oz + l) * n + oy + j) * n + ox + i;
         Uc[(size_t)P * S3 + ((oz + l + 1) * S + oy + j + 1) * S + ox + i + 1] =
@@ -551,10 +552,12 @@ void launch_restrict(T* Uc, T* Fc, const T* Uf, const T* Rf, LevelView lf, int n
     if (lf.nb == 0) return;
     static std::once_flag attr[MAX_DEVICES];
     once_per_device(attr, [] {
-        cudaFuncSetAttribute(k_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_restrict<T, NC_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_restrict<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     });
     const size_t sm = sizeof(T) * (size_t)restrict_row(n) * (n + 1) * (n + 1);
-    k_restrict<T><<<lf.nb, 256, sm, s>>>(Uc, Fc, Uf, Rf, lf, n, off);
+    if (n == NC_FIXED) k_restrict<T, NC_FIXED><<<lf.nb, 256, sm, s>>>(Uc, Fc, Uf, Rf, lf, n, off);
+    else k_restrict<T, 0><<<lf.nb, 256, sm, s>>>(Uc, Fc, Uf, Rf, lf, n, off);
 }
 template void launch_restrict<double>(double*, double*, const double*, const double*, LevelView, int, const double*,
                                       cudaStream_t);
@@ -564,9 +567,10 @@ template void launch_restrict<float>(float*, float*, const float*, const float*,
 // Coarse-grid correction (Alg. 1): eps = u_{k-1} - uhat_{k-1} on the coarse
 // nodes of the fine block's extent plus the next coarse node on each upper
 // side, then u_k += trilinear(eps).
-template <typename T>
+template <typename T, int NC>
 __global__ void k_prolong(T* __restrict__ Uf, const T* __restrict__ Uc, const T* __restrict__ Hc, LevelView lf,
-                          LevelView lc, int n) {
+                          LevelView lc, int n_arg) {
+    const int n = NC ? NC : n_arg;    // NC: block size fixed at compile time (0: runtime)
     extern __shared__ unsigned char smem_raw[];
     T* e = reinterpret_cast<T*>(smem_raw);
     const int B = blockIdx.x;
@@ -577,7 +581,7 @@ __global__ void k_prolong(T* __restrict__ Uf, const T* __restrict__ Uc, const T*
     const int* cn = lc.nbr + 27 * P;
     const unsigned mE = magic_of(E);
     for (int t = threadIdx.x; t < E * E * E; t += blockDim.x) {
-        const int t1 = fdiv(t, mE), i = t - t1 * E, l = fdiv(t1, mE), j = t1 - l * E;
+        const int t1 = NC ? t / E : fdiv(t, mE), i = t - t1 * E, l = NC ? t1 / E : fdiv(t1, mE), j = t1 - l * E;
         const int cx = ox + i, cy = oy + j, cz = oz + l;
         const int ex = cx >= n, ey = cy >= n, ez = cz >= n;
         const int blk = cn[dir27(ex, ey, ez)];
@@ -592,14 +596,13 @@ __global__ void k_prolong(T* __restrict__ Uf, const T* __restrict__ Uc, const T*
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
         const int y = c / n, x = c - y * n;
         const int ax = x >> 1, ay = y >> 1, bx = x & 1, by = y & 1;
+        // bilinear value at (x, y): rows ay and ay + by, columns ax and ax + bx;
+        // on a coincident axis both indices are equal and the halving undoes
+        // the doubling exactly
         auto plane = [&](int az) {
-            T accy = T(0);
-            for (int my = 0; my <= by; ++my) {
-                T accx = T(0);
-                for (int mx = 0; mx <= bx; ++mx) accx += e[(az * E + ay + my) * E + ax + mx];
-                accy += (bx ? T(0.5) : T(1)) * accx;
-            }
-            return (by ? T(0.5) : T(1)) * accy;
+            const T* r0 = e + (az * E + ay) * E + ax;
+            const T* r1 = r0 + by * E;
+            return T(0.25) * ((r0[0] + r0[bx]) + (r1[0] + r1[bx]));
         };
         T cur = plane(0);
         if constexpr (sizeof(T) == 4) {
@@ -657,9 +660,11 @@ void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc,
     const size_t sm = sizeof(T) * ((size_t)E * E * E + (sizeof(T) == 4 ? (size_t)n * n * n : 0));
     static std::once_flag attr[MAX_DEVICES];
     once_per_device(attr, [] {
-        cudaFuncSetAttribute(k_prolong<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_prolong<T, NC_FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_prolong<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     });
-    k_prolong<T><<<lf.nb, 256, sm, s>>>(Uf, Uc, Hc, lf, lc, n);
+    if (n == NC_FIXED) k_prolong<T, NC_FIXED><<<lf.nb, 256, sm, s>>>(Uf, Uc, Hc, lf, lc, n);
+    else k_prolong<T, 0><<<lf.nb, 256, sm, s>>>(Uf, Uc, Hc, lf, lc, n);
 }
 template void launch_prolong<double>(double*, const double*, const double*, LevelView, LevelView, int, cudaStream_t);
 template void launch_prolong<float>(float*, const float*, const float*, LevelView, LevelView, int, cudaStream_t);

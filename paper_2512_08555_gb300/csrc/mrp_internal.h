@@ -128,6 +128,9 @@ constexpr int MAX_RADIX_STAGES = 16;
 // Opt-in dynamic shared memory per CTA requested for the large-tile kernels
 // (below the 227 KB limit so that their small static arrays still fit).
 constexpr int MAX_DYN_SMEM = 225 * 1024;   // dynamic shared memory per CTA (227 KB opt-in less static use)
+// The block kernels come in two builds: block size 16 fixed at compile time
+// (constant strides, offsets and divisions) and any block size at run time.
+constexpr int NC_FIXED = 16;
 
 // One problem of a handle: a forest, or one component of a forest's vector
 // right-hand side.  Its blocks are contiguous in every level's pool; it has
@@ -337,9 +340,10 @@ void launch_scatter_leaves(Handle& h, const double* f, cudaStream_t s);
 void launch_gather_leaves(Handle& h, double* u, cudaStream_t s);
 void launch_rhs_star(double* F, const double* Fraw, const int* leaf_blocks, int nleaf, int n, int M, cudaStream_t s);
 // f* = R^M f (M = 2, 4) on the listed leaf blocks of level k, the one ghost layer built in the kernel from raw f
-// in the (n+2)^3 box layout (Af: level k; Ac: level k-1, covered nodes injected)
+// in the (n+2)^3 box layout (Af: level k; Ac: level k-1, covered nodes injected); max |f*| per problem into
+// fmax_out[prob] (atomic max on the bit pattern, NaN as +Inf)
 void launch_rhs_fused(double* F, const double* Af, const double* Ac, const int* blocks, int nblocks, LevelView lk, int n,
-                      int M, cudaStream_t s);
+                      int M, unsigned long long* fmax_out, cudaStream_t s);
 void launch_absmax(const double* F, const int* blocks, int nblocks, int n, unsigned long long* out, const int* prob,
                    cudaStream_t s);
 void launch_coarse_solve_ext(const Handle& h, double2* spec, const double* F0, double* U0, cudaStream_t s);

@@ -520,7 +520,7 @@ static void prepare_rhs(Handle& h, const double* f, cudaStream_t s) {
         // R^2, R^4 read one ghost layer: raw f goes into the FP64 u arrays
         // (zero ghost layers; u is cleared again before the cycles), covered
         // nodes take its injection, and each level's f* is formed with its
-        // ghost layer built in the kernel
+        // ghost layer built in the kernel, which also takes max |f*| (slot 0)
         PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1 + h.L + (h.L + 1));
         const size_t S = h.n + 2;
         LevelPtrs lp{};
@@ -533,7 +533,7 @@ static void prepare_rhs(Handle& h, const double* f, cudaStream_t s) {
             launch_inject_to_parent<double>(h.lv[k].U, 1, h.lv[k + 1].U, 1, h.lv[k + 1].view(), h.n, nullptr, s);
         for (int k = 0; k <= h.L; ++k)
             launch_rhs_fused(h.lv[k].F, h.lv[k].U, k >= 1 ? h.lv[k - 1].U : nullptr, h.lv[k].leaf_blocks, h.lv[k].nleaf,
-                             h.lv[k].view(), h.n, h.M, s);
+                             h.lv[k].view(), h.n, h.M, h.slot(0), s);
         return;
     }
     PhaseScope ps(h, s, PH_OTHER, h.leaf_nodes, 1 + h.L + 2 * (h.L + 1));
@@ -696,9 +696,10 @@ int autotune(Handle& h, cudaStream_t s) {
 void solve_begin(Handle& h, const double* f, cudaStream_t s) {
     const size_t S = h.n + 2;
     if (h.mixed) cudaMemsetAsync(h.lv[0].F, 0, sizeof(double) * h.lv[0].nb * n3(h), s);
-    prepare_rhs(h, f, s);
+    // max |f*| over the leaves (slot 0): taken while f* is formed for M = 2, 4
     cudaMemsetAsync(h.slot(0), 0, sizeof(unsigned long long) * h.nprob(), s);
-    {
+    prepare_rhs(h, f, s);
+    if (h.M > 4) {
         PhaseScope ps(h, s, PH_NORM, h.leaf_nodes, h.L + 1);
         for (int k = 0; k <= h.L; ++k)
             launch_absmax(h.lv[k].F, h.lv[k].leaf_blocks, h.lv[k].nleaf, h.n, h.slot(0), h.lv[k].prob, s);
