@@ -45,7 +45,11 @@ enum {
                                   blocks (ghosts of U_{k-1} built in the kernel), u-hat (Alg. 1) */
     MRP_STEP_COARSE_SOLVE = 5, /* level 0: U = h0^2 G * F on all nodes and the exterior ring (Sec. 2.2) */
     MRP_STEP_PROLONG = 6,      /* level k: U_k += trilinear(U_{k-1} - UHAT_{k-1}) (Alg. 1) */
-    MRP_STEP_VCYCLE = 7        /* one full V(nu1,nu2) cycle (level argument ignored) */
+    MRP_STEP_VCYCLE = 7,       /* one full V(nu1,nu2) cycle (level argument ignored) */
+    MRP_STEP_COARSE_SOLVE_F32 = 8  /* level 0 of a mixed-precision handle: the FP32 level-0 solve of its
+                                      correction cycles (Sec. 2.2 in FP32): F rounded to FP32, the FP32
+                                      zero-padded convolution, and its result widened into U (interiors
+                                      and exterior ring); MRP_ERR_UNSUPPORTED on an FP64 handle */
 };
 
 /* Number of levels (max leaf level + 1). */

@@ -125,58 +125,86 @@ void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nb
 
 // ---------------------------------------------------------------- Gauss-Seidel sweep
 // Transpose of one 8-colour sweep with frozen halo (forward: nodes p of colour
-// c take (den h^2 f_p - sum_q w_q u_q) / w_c).  Colours run 7..0.  For one
-// colour, a node q whose parity differs from c in m axes has exactly the
-// colour-c neighbours q +- 1 in those axes (2^m of them, all of weight w_m):
-// it gathers -w_m / w_c times their adjoints; then the colour-c nodes pass
-// den h^2 / w_c of their adjoint to f and clear it.  The halo accumulates too
-// (it is scattered afterwards by the ghost transpose).
+// c take (den h^2 f_p - sum_q w_q u_q) / w_c).  Colours run 7..0.  With x the
+// adjoint restricted to the colour-c interior nodes, colour c's transposed
+// update is u-bar -= (1 / w_c) N x on every node of the box (halo included:
+// it is scattered afterwards by the ghost transpose), N the off-centre
+// stencil; then the colour-c nodes pass den h^2 / w_c of their adjoint to f
+// and clear it.  N x vanishes on colour c itself, and a node whose parity
+// differs from c in m axes has exactly the colour-c neighbours q +- 1 in those
+// axes (2^m of them, all of weight w_m).
+//
+// Layout: the (n+2)^3 box in shared memory split by the parity of its box
+// coordinates (8 sub-arrays of H^3, H = n/2 + 1, at X >> 1 etc.), so that a
+// colour is one sub-array; x goes to a copy of that sub-array with a zero
+// border (and zeros where the colour's positions are halo), so the gathers
+// need no bounds tests.  Along an axis where a destination of box parity p
+// differs from the colour, its two sources sit at split offsets p - 1 and p.
 template <int M, typename T>
-__global__ void k_smooth_T(T* __restrict__ U, T* __restrict__ F, int n, T h2den) {
+__global__ void __launch_bounds__(256) k_smooth_T(T* __restrict__ U, T* __restrict__ F, int n, T h2den) {
     extern __shared__ __align__(16) unsigned char st_raw[];
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n;
+    const int H = n / 2 + 1, H2 = H * H, H3 = H2 * H;
+    const int E = H + 2, E2 = E * E;
     T* su = reinterpret_cast<T*>(st_raw);
-    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n, h = n >> 1, h3 = h * h * h;
+    T* xs = su + 8 * H3;                  // E^3, zero border
     const int b = blockIdx.x;
     T* Ub = U + (size_t)b * S3;
     T* Fb = F + (size_t)b * n3;
-    for (int t = threadIdx.x; t < S3; t += blockDim.x) su[t] = Ub[t];
+    const unsigned mS = magic_of(S), mS2 = magic_of(S2), mH = magic_of(H), mH2 = magic_of(H2), mH3 = magic_of(H3);
+    auto split = [&](int X, int Y, int Z) {
+        return (((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1)) * H3 + (Z >> 1) * H2 + (Y >> 1) * H + (X >> 1);
+    };
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int Z = fdiv(t, mS2), r = t - Z * S2, Y = fdiv(r, mS), X = r - Y * S;
+        su[split(X, Y, Z)] = Ub[t];
+    }
+    for (int t = threadIdx.x; t < E2 * E; t += blockDim.x) xs[t] = T(0);
     __syncthreads();
-    const T inv_c = T(1.0 / LWa<M>::c);
+    const T inv_c = T(1.0 / LWa<M>::c), fscale = h2den * inv_c;
     for (int col = 7; col >= 0; --col) {
-        const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
-        for (int t = threadIdx.x; t < S3; t += blockDim.x) {
-            const int qx = t % S - 1, qy = (t / S) % S - 1, qz = t / S2 - 1;
-            const int mx = (qx & 1) != cx, my = (qy & 1) != cy, mz = (qz & 1) != cz;
-            const int m = mx + my + mz;
-            if (m == 0) continue;
-            const T w = T(lhs_w<M>(m));
-            if (w == T(0)) continue;
-            T acc = T(0);
-            for (int sz = -mz; sz <= mz; sz += 2) {
-                const int pz = qz + sz;
-                if (pz < 0 || pz >= n) continue;
-                for (int sy = -my; sy <= my; sy += 2) {
-                    const int py = qy + sy;
-                    if (py < 0 || py >= n) continue;
-                    for (int sx = -mx; sx <= mx; sx += 2) {
-                        const int px = qx + sx;
-                        if (px < 0 || px >= n) continue;
-                        acc += su[((pz + 1) * S + py + 1) * S + px + 1];
-                    }
-                }
+        // colour col in interior coordinates; its box parity is the opposite
+        const int cs = col ^ 7;
+        const int px = cs & 1, py = (cs >> 1) & 1, pz = (cs >> 2) & 1;
+        T* sc = su + cs * H3;
+        for (int t = threadIdx.x; t < H3; t += blockDim.x) {
+            const int l = fdiv(t, mH2), r = t - l * H2, j = fdiv(r, mH), i = r - j * H;
+            const int X = 2 * i + px, Y = 2 * j + py, Z = 2 * l + pz;
+            const bool in = X >= 1 && X <= n && Y >= 1 && Y <= n && Z >= 1 && Z <= n;
+            const T v = in ? sc[t] : T(0);
+            xs[(l + 1) * E2 + (j + 1) * E + i + 1] = v;
+            if (in) {
+                sc[t] = T(0);
+                Fb[((Z - 1) * n + Y - 1) * n + X - 1] += fscale * v;
             }
-            su[t] -= w * inv_c * acc;
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < h3; q += blockDim.x) {
-            const int x = 2 * (q % h) + cx, y = 2 * ((q / h) % h) + cy, z = 2 * (q / (h * h)) + cz;
-            const int o = ((z + 1) * S + y + 1) * S + x + 1;
-            Fb[(z * n + y) * n + x] += h2den * inv_c * su[o];
-            su[o] = T(0);
+        for (int t = threadIdx.x; t < 7 * H3; t += blockDim.x) {
+            const int q = fdiv(t, mH3), pos = t - q * H3;
+            const int d = q < cs ? q : q + 1;           // destination sub-array (box parity)
+            const int D = d ^ cs;                       // axes in which it differs from the colour
+            const int m = (D & 1) + ((D >> 1) & 1) + ((D >> 2) & 1);
+            const T w = T(lhs_w<M>(m));
+            if (w == T(0)) continue;
+            const int l = fdiv(pos, mH2), r = pos - l * H2, j = fdiv(r, mH), i = r - j * H;
+            // per axis: sources at split offsets {p - 1, p} where it differs, {0} where not
+            const int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+            const int x0 = (D & 1) ? dx - 1 : 0, x1 = (D & 1) ? dx : 0;
+            const int y0 = (D & 2) ? dy - 1 : 0, y1 = (D & 2) ? dy : 0;
+            const int z0 = (D & 4) ? dz - 1 : 0, z1 = (D & 4) ? dz : 0;
+            const T* c0 = xs + (l + 1) * E2 + (j + 1) * E + i + 1;
+            T acc = T(0);
+            for (int oz = z0; oz <= z1; ++oz)
+                for (int oy = y0; oy <= y1; ++oy)
+                    for (int ox = x0; ox <= x1; ++ox) acc += c0[oz * E2 + oy * E + ox];
+            su[d * H3 + pos] -= w * inv_c * acc;
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < S3; t += blockDim.x) Ub[t] = su[t];
+    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
+        const int Z = fdiv(t, mS2), r = t - Z * S2, Y = fdiv(r, mS), X = r - Y * S;
+        Ub[t] = su[split(X, Y, Z)];
+    }
 }
 
 template <typename T>
@@ -188,7 +216,8 @@ void launch_smooth_T(T* U, T* F, int nb, int n, int M, double h2, cudaStream_t s
         cudaFuncSetAttribute(k_smooth_T<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
         cudaFuncSetAttribute(k_smooth_T<6, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     });
-    const size_t sm = sizeof(T) * (n + 2) * (n + 2) * (n + 2);
+    const size_t H = n / 2 + 1, E = H + 2;
+    const size_t sm = sizeof(T) * (8 * H * H * H + E * E * E);
     if (M == 2) k_smooth_T<2, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<2>::den));
     if (M == 4) k_smooth_T<4, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<4>::den));
     if (M == 6) k_smooth_T<6, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<6>::den));

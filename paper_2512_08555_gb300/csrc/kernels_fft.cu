@@ -17,6 +17,7 @@
 #include "mrp_internal.h"
 
 #include <cmath>
+#include <vector>
 
 namespace mrp {
 
@@ -52,15 +53,16 @@ constexpr int FFT_STAGE_BYTES = 4 * MAX_RADIX_STAGES * 4;
 template <typename R>
 static FftLine<R> line_of(const FftAxis& a) {
     FftLine<R> l{};
+    const int* rad = sizeof(R) == 8 ? a.rad : a.rad32;
     l.P = a.P;
-    l.nrad = a.nrad;
+    l.nrad = sizeof(R) == 8 ? a.nrad : a.nrad32;
     int ns = 1;
-    for (int i = 0; i < a.nrad; ++i) {
-        l.rad[i] = a.rad[i];
+    for (int i = 0; i < l.nrad; ++i) {
+        l.rad[i] = rad[i];
         l.ns[i] = ns;
         l.nsm[i] = ns > 1 ? (unsigned)((1ULL << 32) / (unsigned long long)ns + 1ULL) : 0u;
-        l.tstep[i] = a.P / (ns * a.rad[i]);
-        ns *= a.rad[i];
+        l.tstep[i] = a.P / (ns * rad[i]);
+        ns *= rad[i];
     }
     if constexpr (sizeof(R) == 8) l.tw = a.tw;
     else l.tw = a.tw32;
@@ -154,6 +156,146 @@ template <typename R> struct Dft<7, R> {
     }
 };
 
+// Composite R = A B points in registers (Cooley-Tukey inside one butterfly):
+// with j = j1 + A j2 and k = k2 + B k1,
+//   X[k2 + B k1] = sum_j1 w_A^(j1 k1) w_R^(j1 k2) sum_j2 w_B^(j2 k2) v[j1 + A j2],
+// w_n = exp(sign 2 pi i / n).  One shared-memory round trip of a Stockham
+// stage then does the work of two.  unit_root<R>(m) = (cos, sin)(2 pi m / R);
+// the loops are unrolled, so every m is a constant.
+template <int RR> __device__ __forceinline__ double2 unit_root(int m);
+template <> __device__ __forceinline__ double2 unit_root<8>(int m) {
+    switch (m) {
+        case 0: return double2{1.0, 0.0};
+        case 1: return double2{0.707106781186547524401, 0.707106781186547524401};
+        case 2: return double2{0.0, 1.0};
+        case 3: return double2{-0.707106781186547524401, 0.707106781186547524401};
+        case 4: return double2{-1.0, 0.0};
+        case 5: return double2{-0.707106781186547524401, -0.707106781186547524401};
+        case 6: return double2{0.0, -1.0};
+        case 7: return double2{0.707106781186547524401, -0.707106781186547524401};
+        default: return double2{1.0, 0.0};
+    }
+}
+template <> __device__ __forceinline__ double2 unit_root<9>(int m) {
+    switch (m) {
+        case 0: return double2{1.0, 0.0};
+        case 1: return double2{0.766044443118978035202, 0.642787609686539326323};
+        case 2: return double2{0.173648177666930348852, 0.984807753012208059367};
+        case 3: return double2{-0.5, 0.866025403784438646764};
+        case 4: return double2{-0.939692620785908384054, 0.342020143325668733044};
+        case 5: return double2{-0.939692620785908384054, -0.342020143325668733044};
+        case 6: return double2{-0.5, -0.866025403784438646764};
+        case 7: return double2{0.173648177666930348852, -0.984807753012208059367};
+        case 8: return double2{0.766044443118978035202, -0.642787609686539326323};
+        default: return double2{1.0, 0.0};
+    }
+}
+template <> __device__ __forceinline__ double2 unit_root<14>(int m) {
+    switch (m) {
+        case 0: return double2{1.0, 0.0};
+        case 1: return double2{0.900968867902419126236, 0.433883739117558120476};
+        case 2: return double2{0.623489801858733530525, 0.781831482468029808708};
+        case 3: return double2{0.222520933956314404289, 0.974927912181823607018};
+        case 4: return double2{-0.222520933956314404289, 0.974927912181823607018};
+        case 5: return double2{-0.623489801858733530525, 0.781831482468029808708};
+        case 6: return double2{-0.900968867902419126236, 0.433883739117558120476};
+        case 7: return double2{-1.0, 0.0};
+        case 8: return double2{-0.900968867902419126236, -0.433883739117558120476};
+        case 9: return double2{-0.623489801858733530525, -0.781831482468029808708};
+        case 10: return double2{-0.222520933956314404289, -0.974927912181823607018};
+        case 11: return double2{0.222520933956314404289, -0.974927912181823607018};
+        case 12: return double2{0.623489801858733530525, -0.781831482468029808708};
+        case 13: return double2{0.900968867902419126236, -0.433883739117558120476};
+        default: return double2{1.0, 0.0};
+    }
+}
+template <> __device__ __forceinline__ double2 unit_root<15>(int m) {
+    switch (m) {
+        case 0: return double2{1.0, 0.0};
+        case 1: return double2{0.913545457642600895502, 0.406736643075800207754};
+        case 2: return double2{0.669130606358858213826, 0.743144825477394235015};
+        case 3: return double2{0.309016994374947424102, 0.951056516295153572116};
+        case 4: return double2{-0.1045284632676534714, 0.994521895368273336923};
+        case 5: return double2{-0.5, 0.866025403784438646764};
+        case 6: return double2{-0.809016994374947424102, 0.587785252292473129169};
+        case 7: return double2{-0.978147600733805637929, 0.207911690817759337102};
+        case 8: return double2{-0.978147600733805637929, -0.207911690817759337102};
+        case 9: return double2{-0.809016994374947424102, -0.587785252292473129169};
+        case 10: return double2{-0.5, -0.866025403784438646764};
+        case 11: return double2{-0.1045284632676534714, -0.994521895368273336923};
+        case 12: return double2{0.309016994374947424102, -0.951056516295153572116};
+        case 13: return double2{0.669130606358858213826, -0.743144825477394235015};
+        case 14: return double2{0.913545457642600895502, -0.406736643075800207754};
+        default: return double2{1.0, 0.0};
+    }
+}
+template <> __device__ __forceinline__ double2 unit_root<16>(int m) {
+    switch (m) {
+        case 0: return double2{1.0, 0.0};
+        case 1: return double2{0.923879532511286756128, 0.382683432365089771728};
+        case 2: return double2{0.707106781186547524401, 0.707106781186547524401};
+        case 3: return double2{0.382683432365089771728, 0.923879532511286756128};
+        case 4: return double2{0.0, 1.0};
+        case 5: return double2{-0.382683432365089771728, 0.923879532511286756128};
+        case 6: return double2{-0.707106781186547524401, 0.707106781186547524401};
+        case 7: return double2{-0.923879532511286756128, 0.382683432365089771728};
+        case 8: return double2{-1.0, 0.0};
+        case 9: return double2{-0.923879532511286756128, -0.382683432365089771728};
+        case 10: return double2{-0.707106781186547524401, -0.707106781186547524401};
+        case 11: return double2{-0.382683432365089771728, -0.923879532511286756128};
+        case 12: return double2{0.0, -1.0};
+        case 13: return double2{0.382683432365089771728, -0.923879532511286756128};
+        case 14: return double2{0.707106781186547524401, -0.707106781186547524401};
+        case 15: return double2{0.923879532511286756128, -0.382683432365089771728};
+        default: return double2{1.0, 0.0};
+    }
+}
+
+template <int A, int B, typename R> struct DftAB {
+    template <typename C> static __device__ __forceinline__ void run(C* v, int sign) {
+        constexpr int RR = A * B;
+#pragma unroll
+        for (int j1 = 0; j1 < A; ++j1) {
+            C t[B];
+#pragma unroll
+            for (int j2 = 0; j2 < B; ++j2) t[j2] = v[j1 + A * j2];
+            Dft<B, R>::run(t, sign);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) {
+                const int m = (j1 * k2) % RR;
+                C x = t[k2];
+                if (m != 0) {
+                    if ((4 * m) % RR == 0) {             // w = i^q: a swap and sign changes
+                        const int q = 4 * m / RR;
+                        x = q == 2 ? C{-x.x, -x.y} : cmuli(x, R(q == 1 ? sign : -sign));
+                    } else {
+                        const double2 w = unit_root<RR>(m);
+                        x = cmul(x, C{R(w.x), R(sign) * R(w.y)});
+                    }
+                }
+                v[j1 + A * k2] = x;
+            }
+        }
+        C out[RR];
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+            C t[A];
+#pragma unroll
+            for (int j1 = 0; j1 < A; ++j1) t[j1] = v[j1 + A * k2];
+            Dft<A, R>::run(t, sign);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) out[k2 + B * k1] = t[k1];
+        }
+#pragma unroll
+        for (int k = 0; k < RR; ++k) v[k] = out[k];
+    }
+};
+template <typename R> struct Dft<8, R> : DftAB<2, 4, R> {};
+template <typename R> struct Dft<9, R> : DftAB<3, 3, R> {};
+template <typename R> struct Dft<14, R> : DftAB<2, 7, R> {};
+template <typename R> struct Dft<15, R> : DftAB<3, 5, R> {};
+template <typename R> struct Dft<16, R> : DftAB<4, 4, R> {};
+
 // One Stockham stage of radix RAD: butterfly j reads a[j + r P/RAD], twiddles
 // by w^{(j mod Ns) r P/(Ns RAD)}, applies the RAD-point DFT and writes
 // b[(j / Ns) Ns RAD + (j mod Ns) + r Ns].
@@ -200,20 +342,43 @@ template <typename R> __host__ __device__ constexpr int fft_ly() { return sizeof
 // separated by warp barriers, else by CTA barriers (every thread of the CTA
 // must then call this).  Returns the buffer that holds the result (Stockham
 // autosort, mixed radix).
-template <typename R, typename C>
+template <typename R, bool CMP, typename C>
 __device__ C* fft_line(C* a, C* b, const FftDev<R>& L, int sign, int nz) {
     const int P = L.P;
     constexpr int MS = MAX_RADIX_STAGES;
     for (int st = 0; st < L.nrad; ++st) {
         const int RAD = L.st[st], Ns = L.st[MS + st], ts = L.st[2 * MS + st];
         const unsigned nsm = (unsigned)L.st[3 * MS + st];
-        if (st == 0) {
+        if constexpr (!CMP) {
+            // plans of prime radices (and 4): 2 first for even P
+            if (st == 0) {
+                switch (RAD) {
+                    case 2: stockham_stage<2, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                    case 3: stockham_stage<3, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                    case 4: stockham_stage<4, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                    case 5: stockham_stage<5, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                    default: stockham_stage<7, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                }
+            } else {
+                switch (RAD) {
+                    case 2: stockham_stage<2, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                    case 3: stockham_stage<3, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                    case 4: stockham_stage<4, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                    case 5: stockham_stage<5, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                    default: stockham_stage<7, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                }
+            }
+        } else if (st == 0) {
+            // plans with composite radices (a separate build, so that the
+            // prime-radix lines keep their smaller code): the first radix is 2
+            // for even P, else an odd one
             switch (RAD) {
                 case 2: stockham_stage<2, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
                 case 3: stockham_stage<3, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
-                case 4: stockham_stage<4, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
                 case 5: stockham_stage<5, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
-                default: stockham_stage<7, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                case 7: stockham_stage<7, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                case 9: stockham_stage<9, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
+                default: stockham_stage<15, true, R>(a, b, P, Ns, nsm, ts, L.tw, sign, nz); break;
             }
         } else {
             switch (RAD) {
@@ -221,7 +386,12 @@ __device__ C* fft_line(C* a, C* b, const FftDev<R>& L, int sign, int nz) {
                 case 3: stockham_stage<3, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
                 case 4: stockham_stage<4, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
                 case 5: stockham_stage<5, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
-                default: stockham_stage<7, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 7: stockham_stage<7, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 8: stockham_stage<8, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 9: stockham_stage<9, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 14: stockham_stage<14, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                case 15: stockham_stage<15, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
+                default: stockham_stage<16, false, R>(a, b, P, Ns, nsm, ts, L.tw, sign, P); break;
             }
         }
         if constexpr (fft_tx<R>() == 32) __syncwarp();
@@ -275,7 +445,7 @@ __device__ __forceinline__ int pidx(int i, int P) { return i < 0 ? i + P : (i >=
 // lines at once as one complex line z = a + i b; with Z = FFT(z) and
 // Z' = conj(Z[(P - k) mod P]), the halves are A = (Z + Z') / 2 and
 // B = (Z - Z') / (2 i).
-template <typename R>
+template <typename R, bool CMP>
 __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ src, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -315,7 +485,7 @@ __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __res
         }
     }
     __syncthreads();
-    C* r = fft_line<R>(a, b, L, -1, g.in_lo[0] == 0 ? g.in_n[0] : L.P);
+    C* r = fft_line<R, CMP>(a, b, L, -1, g.in_lo[0] == 0 ? g.in_n[0] : L.P);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         if (!live[h]) continue;
@@ -335,7 +505,7 @@ __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __res
 // a warp touches whole sectors; the transforms themselves run per line.
 
 // ---------------------------------------------------------------- pass B (y, forward), lines (input z, kx)
-template <typename R>
+template <typename R, bool CMP>
 __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -356,7 +526,7 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
         sm[ly * P2 + j] = spec[((size_t)zi * g.Py + j) * g.Kx + kx0 + ly];
     }
     __syncthreads();
-    const int roff = (int)(fft_line<R>(a, b, L, -1, g.in_lo[1] == 0 ? g.in_n[1] : P) - a);
+    const int roff = (int)(fft_line<R, CMP>(a, b, L, -1, g.in_lo[1] == 0 ? g.in_n[1] : P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * P; e += nth) {
         const int ly = e % fft_ly<R>(), y = e / fft_ly<R>();
@@ -365,7 +535,7 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
 }
 
 // ---------------------------------------------------------------- pass C (z forward, x G-hat, z inverse), lines (ky, kx)
-template <typename R>
+template <typename R, bool CMP>
 __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -402,7 +572,7 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
         gpre[m] = kz < P ? ghat_at(kz) : R(0);
     }
     __syncthreads();
-    C* r = fft_line<R>(a, b, L, -1, g.in_lo[2] == 0 ? g.in_n[2] : P);
+    C* r = fft_line<R, CMP>(a, b, L, -1, g.in_lo[2] == 0 ? g.in_n[2] : P);
 #pragma unroll
     for (int m = 0; m < GPRE; ++m) {
         const int kz = threadIdx.x + m * blockDim.x;
@@ -414,7 +584,7 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
     }
     __syncthreads();
     C* other = (r == a) ? b : a;
-    const int qoff = (int)(fft_line<R>(r, other, L, +1, P) - a);
+    const int qoff = (int)(fft_line<R, CMP>(r, other, L, +1, P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * g.out_n[2]; e += nth) {
         const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
@@ -425,7 +595,7 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
 }
 
 // ---------------------------------------------------------------- pass B' (y inverse), lines (output z, kx)
-template <typename R>
+template <typename R, bool CMP>
 __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -442,7 +612,7 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
         sm[ly * P2 + y] = kx0 + ly < g.Kx ? spec[((size_t)z * g.Py + y) * g.Kx + kx0 + ly] : C{R(0), R(0)};
     }
     __syncthreads();
-    const int roff = (int)(fft_line<R>(a, b, L, +1, P) - a);
+    const int roff = (int)(fft_line<R, CMP>(a, b, L, +1, P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * g.out_n[1]; e += nth) {
         const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
@@ -458,7 +628,7 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
 // real outputs.  Block mode writes node (x, y, z) into every level-0 block
 // whose (n+2)^3 box holds it (interior or ghost layer); dense mode writes the
 // dense output range.
-template <typename R>
+template <typename R, bool CMP>
 __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -492,7 +662,7 @@ __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __rest
         a[k] = C{v[0].x - v[1].y, v[0].y + v[1].x};
     }
     __syncthreads();
-    C* r = fft_line<R>(a, b, L, +1, L.P);
+    C* r = fft_line<R, CMP>(a, b, L, +1, L.P);
     const int S = g.n + 2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -539,6 +709,14 @@ static Geo geo_of(const Handle& h, const Problem& p) {
     return g;
 }
 
+// Whether a line's plan holds a composite radix (8, 9, 14, 15, 16).
+template <typename R>
+static bool has_composite(const FftLine<R>& l) {
+    for (int i = 0; i < l.nrad; ++i)
+        if (l.rad[i] > 7) return true;
+    return false;
+}
+
 template <typename R>
 static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec, const R* ghat, const R* src, R* dst,
                         cudaStream_t s) {
@@ -550,11 +728,17 @@ static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec,
     const size_t smz = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Pz + FFT_STAGE_BYTES;
     const int kxb = (g.Kx + fft_ly<R>() - 1) / fft_ly<R>();
     const int lx2 = 2 * fft_ly<R>();   // lines per CTA in the x passes (two per warp)
-    k_fft_x_fwd<R><<<(g.in_n[1] * g.in_n[2] + lx2 - 1) / lx2, blk, smx, s>>>(spec, src, g, Lx);
-    k_fft_y_fwd<R><<<dim3(kxb, g.in_n[2]), blk, smy, s>>>(spec, g, Ly);
-    k_fft_z_conv<R><<<dim3(kxb, g.Py), blk, smz, s>>>(spec, ghat, g, Lz);
-    k_fft_y_inv<R><<<dim3(kxb, g.out_n[2]), blk, smy, s>>>(spec, g, Ly);
-    k_fft_x_inv<R><<<(g.out_n[1] * g.out_n[2] + lx2 - 1) / lx2, blk, smx, s>>>(dst, spec, g, Lx);
+    // FP32 lines whose plan holds a composite radix take the composite build
+    constexpr bool F32 = sizeof(R) == 4;
+#define MRP_FFT_LAUNCH(KERN, LINE, GRID, SM, ...)                                   \
+    if (F32 && has_composite(LINE)) KERN<R, F32><<<GRID, blk, SM, s>>>(__VA_ARGS__); \
+    else KERN<R, false><<<GRID, blk, SM, s>>>(__VA_ARGS__)
+    MRP_FFT_LAUNCH(k_fft_x_fwd, Lx, (g.in_n[1] * g.in_n[2] + lx2 - 1) / lx2, smx, spec, src, g, Lx);
+    MRP_FFT_LAUNCH(k_fft_y_fwd, Ly, dim3(kxb, g.in_n[2]), smy, spec, g, Ly);
+    MRP_FFT_LAUNCH(k_fft_z_conv, Lz, dim3(kxb, g.Py), smz, spec, ghat, g, Lz);
+    MRP_FFT_LAUNCH(k_fft_y_inv, Ly, dim3(kxb, g.out_n[2]), smy, spec, g, Ly);
+    MRP_FFT_LAUNCH(k_fft_x_inv, Lx, (g.out_n[1] * g.out_n[2] + lx2 - 1) / lx2, smx, dst, spec, g, Lx);
+#undef MRP_FFT_LAUNCH
 }
 
 // Level-0 solve of every problem of the handle, one after another on s (they
@@ -840,18 +1024,35 @@ fail:
 // ---------------------------------------------------------------- FFT plan
 // Radices of P: a single 2 first when P is even (the first stage of a
 // zero-padded forward line then only copies, since the padding takes at
-// least half the line), then 4, 2, 3, 5, 7.
-static bool factor(int P, int* rad, int& nrad) {
+// least half the line); then, where the stage still gives every thread of a
+// line a butterfly (P / R >= minb), two prime factors per stage with a
+// composite butterfly (16, 8, 9, 15, 14: one shared-memory round trip instead
+// of two); then 4, and the primes left.
+static bool factor(int P, int* rad, int& nrad, int minb) {
     nrad = 0;
+    const int P0 = P;
     if (P % 2 == 0) { rad[nrad++] = 2; P /= 2; }
-    const int order[] = {4, 2, 3, 5, 7};
-    for (int r : order)
-        while (P % r == 0) {
-            if (nrad >= MAX_RADIX_STAGES) return false;
-            rad[nrad++] = r;
-            P /= r;
-        }
-    return P == 1;
+    int c2 = 0, c3 = 0, c5 = 0, c7 = 0;
+    while (P % 2 == 0) { ++c2; P /= 2; }
+    while (P % 3 == 0) { ++c3; P /= 3; }
+    while (P % 5 == 0) { ++c5; P /= 5; }
+    while (P % 7 == 0) { ++c7; P /= 7; }
+    if (P != 1) return false;
+    std::vector<int> r;
+    auto ok = [&](int R) { return P0 / R >= minb; };
+    for (; c2 >= 4 && ok(16); c2 -= 4) r.push_back(16);
+    for (; c2 >= 3 && ok(8); c2 -= 3) r.push_back(8);
+    for (; c3 >= 2 && ok(9); c3 -= 2) r.push_back(9);
+    for (; c3 >= 1 && c5 >= 1 && ok(15); --c3, --c5) r.push_back(15);
+    for (; c2 >= 1 && c7 >= 1 && ok(14); --c2, --c7) r.push_back(14);
+    for (; c2 >= 2; c2 -= 2) r.push_back(4);
+    for (; c2 >= 1; --c2) r.push_back(2);
+    for (; c3 >= 1; --c3) r.push_back(3);
+    for (; c5 >= 1; --c5) r.push_back(5);
+    for (; c7 >= 1; --c7) r.push_back(7);
+    if (nrad + (int)r.size() > MAX_RADIX_STAGES) return false;
+    for (int x : r) rad[nrad++] = x;
+    return true;
 }
 
 static int smooth_length(int need) {
@@ -870,7 +1071,10 @@ int fft_plan(Handle& h) {
             FftAxis& ax = p.ax[a];
             ax.P = smooth_length(2 * p.n0[a] + 1);
             ax.K = ax.P / 2 + 1;
-            if (!factor(ax.P, ax.rad, ax.nrad)) return MRP_ERR_UNSUPPORTED;
+            // FP64 lines (bound by their arithmetic) keep one prime per stage; FP32
+            // lines take the composite radices that leave a butterfly per thread
+            if (!factor(ax.P, ax.rad, ax.nrad, ax.P + 1) || !factor(ax.P, ax.rad32, ax.nrad32, fft_tx<float>()))
+                return MRP_ERR_UNSUPPORTED;
             // a CTA holds (2 LY + 1) P complex values of its lines and twiddles, and the stage table
             if (sizeof(double2) * (2 * fft_ly<double>() + 1) * (size_t)ax.P + FFT_STAGE_BYTES > (size_t)MAX_DYN_SMEM ||
                 sizeof(float2) * (2 * fft_ly<float>() + 1) * (size_t)ax.P + FFT_STAGE_BYTES > (size_t)MAX_DYN_SMEM)
@@ -889,16 +1093,13 @@ int fft_plan(Handle& h) {
     }
     if (cudaMalloc(&h.spec, sizeof(double2) * ns) != cudaSuccess) return MRP_ERR_OOM;
     const int mx = MAX_DYN_SMEM;
-    cudaFuncSetAttribute(k_fft_x_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_y_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_z_conv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_y_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_x_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_x_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_y_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_z_conv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_y_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_fft_x_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    const void* kernels[] = {
+        (const void*)k_fft_x_fwd<double, false>, (const void*)k_fft_x_fwd<float, false>, (const void*)k_fft_x_fwd<float, true>,
+        (const void*)k_fft_y_fwd<double, false>, (const void*)k_fft_y_fwd<float, false>, (const void*)k_fft_y_fwd<float, true>,
+        (const void*)k_fft_z_conv<double, false>, (const void*)k_fft_z_conv<float, false>, (const void*)k_fft_z_conv<float, true>,
+        (const void*)k_fft_y_inv<double, false>, (const void*)k_fft_y_inv<float, false>, (const void*)k_fft_y_inv<float, true>,
+        (const void*)k_fft_x_inv<double, false>, (const void*)k_fft_x_inv<float, false>, (const void*)k_fft_x_inv<float, true>};
+    for (const void* k : kernels) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return MRP_OK;
 }
 

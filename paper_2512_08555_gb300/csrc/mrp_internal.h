@@ -118,8 +118,8 @@ struct Level {
 // One padded FFT axis: length, radix sequence, twiddles exp(-2 pi i m / P).
 struct FftAxis {
     int P = 0, K = 0;                 // K = P/2 + 1 (half spectrum along x)
-    int nrad = 0;
-    int rad[16];
+    int nrad = 0, nrad32 = 0;
+    int rad[16], rad32[16];           // radix sequences of the FP64 and FP32 lines
     double2* tw = nullptr;            // device [P]
     float2* tw32 = nullptr;           // device [P], FP32 copy
 };

@@ -1147,6 +1147,15 @@ int mrp_step(mrp_handle* H, int32_t step, int32_t level, const double* f_leaf, v
         case MRP_STEP_VCYCLE:
             vcycle<double>(h, s);
             break;
+        case MRP_STEP_COARSE_SOLVE_F32: {
+            if (!h.mixed) return MRP_ERR_UNSUPPORTED;
+            Level& l0 = h.lv[0];
+            launch_block_copy<float, double>(l0.F32, l0.F, l0.order, l0.nb, h.n, 1.0, s);
+            coarse_solve<float>(h, s);
+            // the (n+2)^3 boxes, widened
+            launch_block_copy<double, float>(l0.U, ucur<float>(h, 0), l0.order, l0.nb, h.n + 2, 1.0, s);
+            break;
+        }
         default:
             return MRP_ERR_INVALID_ARG;
     }

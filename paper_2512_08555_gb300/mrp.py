@@ -21,7 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "invalid forest", 3: "CUDA error", 
           10: "too large for the fixed scratch"}
 FIELDS = {"U": 0, "F": 1, "R": 2, "UHAT": 3, "FRAW": 4}
 STEPS = {"prepare_rhs": 0, "ghost_u": 1, "smooth": 2, "residual": 3, "restrict": 4,
-         "coarse_solve": 5, "prolong": 6, "vcycle": 7}
+         "coarse_solve": 5, "prolong": 6, "vcycle": 7, "coarse_solve_f32": 8}
 EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_error_string",
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",

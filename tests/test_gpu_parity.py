@@ -149,6 +149,62 @@ def test_coarse_solve(M):
     assert _rel(s.field_get("U", 0).cpu().numpy(), o.U[0]) < 1e-12
 
 
+@pytest.mark.parametrize("n, nb, P", [(12, 3, 75), (8, 5, 81), (18, 3, 112), (10, 7, 144), (8, 7, 120),
+                                       (16, 6, 196), (18, 6, 224)])
+def test_coarse_solve_lattices(n, nb, P):
+    """Odd and even padded lengths (radices 2, 3, 4, 5, 7): the FP64 level-0
+    solve against the oracle's convolution at 1e-12, and the FP32 solve of a
+    mixed-precision handle at 1e-5."""
+    from paper_2512_08555_gb300.mrp import Solver
+    desc = small_forest(nb=nb, n=n, max_level=0)
+    s, o = _pair(desc, 4)
+    assert s.fft_shape()[0] == P
+    rng = np.random.default_rng(11)
+    _load(s, o, rng, ("F",))
+    s.step("coarse_solve")
+    o.coarse_solve()
+    assert _rel(s.field_get("U", 0).cpu().numpy(), o.U[0]) < 1e-12
+    m = Solver(desc, order=4, tol=0.0, max_cycles=1, precision="mixed")
+    m.field_set("F", 0, o.F[0])
+    m.step("coarse_solve_f32")
+    assert _rel(m.field_get("U", 0).cpu().numpy(), o.U[0]) < 1e-5
+
+
+@pytest.mark.parametrize("n, nb, P", [(20, 7, 288), (18, 13, 480), (18, 14, 512)])
+def test_coarse_solve_f32_composite_radices(n, nb, P):
+    """Lattices long enough for the FP32 lines' composite butterflies (P = 288:
+    radices 2 8 9 2; 480: 2 8 15 2; 512: 2 16 16): the FP32 level-0 solve at
+    sampled targets (interior nodes and the exterior ring) against the oracle's
+    brute-force sum h0^2 sum_s G(t - s) f(s) over the whole lattice, at 1e-5."""
+    from paper_2512_08555_gb300.mrp import Solver
+    from oracle.lgf import direct_sum
+    desc = small_forest(nb=nb, n=n, max_level=0)
+    m = Solver(desc, order=4, tol=0.0, max_cycles=1, precision="mixed")
+    assert m.fft_shape()[0] == P
+    N0 = nb * n
+    rng = np.random.default_rng(12)
+    F0 = rng.normal(size=(nb ** 3, n, n, n))
+    m.field_set("F", 0, F0)
+    m.step("coarse_solve_f32")
+    U = m.field_get("U", 0).cpu().numpy()
+    coords, _ = m.level_info(0)
+    f0 = np.zeros((N0, N0, N0))
+    where = {}
+    for b, c in enumerate(coords):
+        x, y, z = (int(v) * n for v in c)
+        f0[z:z + n, y:y + n, x:x + n] = F0[b]
+        where[(int(c[2]), int(c[1]), int(c[0]))] = b
+    G = lgf_table(4, N0 + 1)
+    t = rng.integers(0, N0, size=(12, 3))
+    t = np.concatenate([t, [[-1, -1, -1], [N0, N0, N0], [-1, N0 // 2, N0], [N0 // 3, -1, 0]]])
+    ref = direct_sum(f0, G, float(desc.h0), t)
+    got = []
+    for z, y, x in t:
+        bz, by, bx = (min(max(v, 0), N0 - 1) // n for v in (z, y, x))
+        got.append(U[where[(bz, by, bx)], z - bz * n + 1, y - by * n + 1, x - bx * n + 1])
+    assert _rel(got, ref) < 1e-5
+
+
 @pytest.mark.parametrize("M", [2, 4, 6])
 @pytest.mark.parametrize("k", [1, 2])
 def test_prolong(M, k):
