@@ -140,6 +140,21 @@ void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nb
 // border (and zeros where the colour's positions are halo), so the gathers
 // need no bounds tests.  Along an axis where a destination of box parity p
 // differs from the colour, its two sources sit at split offsets p - 1 and p.
+// One destination sub-array's gathers: every position subtracts coef times the
+// sum of the CNT colour-c values at the (uniform) offsets off[] from its own
+// place in the bordered copy xs (offsets in z, y, x order, ascending).
+template <int CNT, typename T>
+__device__ __forceinline__ void gather_T(T* __restrict__ sd, const T* __restrict__ xs, const int* __restrict__ ptab,
+                                         const int (&off)[8], T coef, int H3) {
+    for (int pos = threadIdx.x; pos < H3; pos += blockDim.x) {
+        const T* c0 = xs + (ptab[pos] & 0xFFF);
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) acc += c0[off[k]];
+        sd[pos] -= coef * acc;
+    }
+}
+
 template <int M, typename T>
 __global__ void __launch_bounds__(256) k_smooth_T(T* __restrict__ U, T* __restrict__ F, int n, T h2den) {
     extern __shared__ __align__(16) unsigned char st_raw[];
@@ -148,10 +163,12 @@ __global__ void __launch_bounds__(256) k_smooth_T(T* __restrict__ U, T* __restri
     const int E = H + 2, E2 = E * E;
     T* su = reinterpret_cast<T*>(st_raw);
     T* xs = su + 8 * H3;                  // E^3, zero border
+    // per position of a sub-array: its place in xs (12 bits) and i, j, l (4 bits each)
+    int* ptab = reinterpret_cast<int*>(xs + E2 * E);
     const int b = blockIdx.x;
     T* Ub = U + (size_t)b * S3;
     T* Fb = F + (size_t)b * n3;
-    const unsigned mS = magic_of(S), mS2 = magic_of(S2), mH = magic_of(H), mH2 = magic_of(H2), mH3 = magic_of(H3);
+    const unsigned mS = magic_of(S), mS2 = magic_of(S2), mH = magic_of(H), mH2 = magic_of(H2);
     auto split = [&](int X, int Y, int Z) {
         return (((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1)) * H3 + (Z >> 1) * H2 + (Y >> 1) * H + (X >> 1);
     };
@@ -160,44 +177,60 @@ __global__ void __launch_bounds__(256) k_smooth_T(T* __restrict__ U, T* __restri
         su[split(X, Y, Z)] = Ub[t];
     }
     for (int t = threadIdx.x; t < E2 * E; t += blockDim.x) xs[t] = T(0);
+    for (int t = threadIdx.x; t < H3; t += blockDim.x) {
+        const int l = fdiv(t, mH2), r = t - l * H2, j = fdiv(r, mH), i = r - j * H;
+        ptab[t] = ((l + 1) * E2 + (j + 1) * E + i + 1) | (i << 12) | (j << 16) | (l << 20);
+    }
     __syncthreads();
     const T inv_c = T(1.0 / LWa<M>::c), fscale = h2den * inv_c;
     for (int col = 7; col >= 0; --col) {
         // colour col in interior coordinates; its box parity is the opposite
         const int cs = col ^ 7;
         const int px = cs & 1, py = (cs >> 1) & 1, pz = (cs >> 2) & 1;
+        // split index of the colour's halo positions along each axis
+        const int hx = px ? H - 1 : 0, hy = py ? H - 1 : 0, hz = pz ? H - 1 : 0;
         T* sc = su + cs * H3;
         for (int t = threadIdx.x; t < H3; t += blockDim.x) {
-            const int l = fdiv(t, mH2), r = t - l * H2, j = fdiv(r, mH), i = r - j * H;
-            const int X = 2 * i + px, Y = 2 * j + py, Z = 2 * l + pz;
-            const bool in = X >= 1 && X <= n && Y >= 1 && Y <= n && Z >= 1 && Z <= n;
+            const int pt = ptab[t];
+            const int i = (pt >> 12) & 15, j = (pt >> 16) & 15, l = (pt >> 20) & 15;
+            const bool in = i != hx && j != hy && l != hz;
             const T v = in ? sc[t] : T(0);
-            xs[(l + 1) * E2 + (j + 1) * E + i + 1] = v;
+            xs[pt & 0xFFF] = v;
             if (in) {
                 sc[t] = T(0);
-                Fb[((Z - 1) * n + Y - 1) * n + X - 1] += fscale * v;
+                Fb[((2 * l + pz - 1) * n + 2 * j + py - 1) * n + 2 * i + px - 1] += fscale * v;
             }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < 7 * H3; t += blockDim.x) {
-            const int q = fdiv(t, mH3), pos = t - q * H3;
+        for (int q = 0; q < 7; ++q) {
             const int d = q < cs ? q : q + 1;           // destination sub-array (box parity)
             const int D = d ^ cs;                       // axes in which it differs from the colour
             const int m = (D & 1) + ((D >> 1) & 1) + ((D >> 2) & 1);
             const T w = T(lhs_w<M>(m));
             if (w == T(0)) continue;
-            const int l = fdiv(pos, mH2), r = pos - l * H2, j = fdiv(r, mH), i = r - j * H;
-            // per axis: sources at split offsets {p - 1, p} where it differs, {0} where not
-            const int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
-            const int x0 = (D & 1) ? dx - 1 : 0, x1 = (D & 1) ? dx : 0;
-            const int y0 = (D & 2) ? dy - 1 : 0, y1 = (D & 2) ? dy : 0;
-            const int z0 = (D & 4) ? dz - 1 : 0, z1 = (D & 4) ? dz : 0;
-            const T* c0 = xs + (l + 1) * E2 + (j + 1) * E + i + 1;
-            T acc = T(0);
-            for (int oz = z0; oz <= z1; ++oz)
-                for (int oy = y0; oy <= y1; ++oy)
-                    for (int ox = x0; ox <= x1; ++ox) acc += c0[oz * E2 + oy * E + ox];
-            su[d * H3 + pos] -= w * inv_c * acc;
+            // along an axis where it differs, the sources sit at split offsets p - 1 and p
+            // (p its parity bit); offsets in z, y, x order
+            int ax[3], na = 0;
+            if (D & 4) ax[na++] = 2;
+            if (D & 2) ax[na++] = 1;
+            if (D & 1) ax[na++] = 0;
+            int off[8];
+            int cnt = 1;
+            off[0] = 0;
+            for (int a = 0; a < na; ++a) {
+                const int st = ax[a] == 2 ? E2 : (ax[a] == 1 ? E : 1);
+                const int p = (d >> ax[a]) & 1;
+                for (int k = cnt - 1; k >= 0; --k) {
+                    off[2 * k + 1] = off[k] + p * st;
+                    off[2 * k] = off[k] + (p - 1) * st;
+                }
+                cnt *= 2;
+            }
+            T* sd = su + d * H3;
+            const T coef = w * inv_c;
+            if (m == 1) gather_T<2>(sd, xs, ptab, off, coef, H3);
+            else if (m == 2) gather_T<4>(sd, xs, ptab, off, coef, H3);
+            else gather_T<8>(sd, xs, ptab, off, coef, H3);
         }
         __syncthreads();
     }
@@ -217,7 +250,7 @@ void launch_smooth_T(T* U, T* F, int nb, int n, int M, double h2, cudaStream_t s
         cudaFuncSetAttribute(k_smooth_T<6, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
     });
     const size_t H = n / 2 + 1, E = H + 2;
-    const size_t sm = sizeof(T) * (8 * H * H * H + E * E * E);
+    const size_t sm = sizeof(T) * (8 * H * H * H + E * E * E) + sizeof(int) * H * H * H;
     if (M == 2) k_smooth_T<2, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<2>::den));
     if (M == 4) k_smooth_T<4, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<4>::den));
     if (M == 6) k_smooth_T<6, T><<<nb, 256, sm, s>>>(U, F, n, T(h2 * LWa<6>::den));
