@@ -418,43 +418,54 @@ template void launch_prolong_T<float>(float*, float*, const float*, LevelView, L
 // with |2X - p| <= 1.  The fine image 2X lies in B or in B's upper
 // neighbours; X's window is complete when the level-k blocks below 2X exist
 // along the axes where 2X sits on the block's lower face.  Writes Rf[B].
+// The neighbour tables those tests need are read once per block into shared
+// memory: for each upper neighbour e in {0, 1}^3 (the block holding 2X), its
+// index, parent and octant, and for each pattern m of axes on which 2X lies on
+// its lower face, whether the window is complete.
 template <typename T>
 __global__ void k_fw_T(T* __restrict__ Rf, const T* __restrict__ Fc, LevelView lf, int n) {
-    __shared__ int nb27[27];
+    __shared__ int cblk[8], cpar[8], coct[8];
+    __shared__ unsigned char ins[8][8];
     const int B = blockIdx.x;
-    if (threadIdx.x < 27) nb27[threadIdx.x] = lf.nbr[27 * B + threadIdx.x];
+    if (threadIdx.x < 8) {
+        const int e = threadIdx.x;
+        const int c = lf.nbr[27 * B + dir27(e & 1, (e >> 1) & 1, (e >> 2) & 1)];
+        cblk[e] = c;
+        cpar[e] = c >= 0 ? lf.parent[c] : 0;
+        coct[e] = c >= 0 ? lf.octant[c] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int e = threadIdx.x >> 3, m = threadIdx.x & 7, c = cblk[e];
+        bool inside = c >= 0;
+        for (int sz = 0; sz <= ((m >> 2) & 1) && inside; ++sz)
+            for (int sy = 0; sy <= ((m >> 1) & 1); ++sy)
+                for (int sx = 0; sx <= (m & 1); ++sx)
+                    if (lf.nbr[27 * c + dir27(-sx, -sy, -sz)] < 0) inside = false;
+        ins[e][m] = inside;
+    }
     __syncthreads();
     const int h = n >> 1, n3 = n * n * n;
+    const unsigned mn = magic_of(n), mn2 = magic_of(n * n);
     for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const int p[3] = {t % n, (t / n) % n, t / (n * n)};
-        int lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) {
-            if (p[a] & 1) { lo[a] = -1; hi[a] = 1; }
-            else { lo[a] = 0; hi[a] = 0; }
-        }
+        const int pz = fdiv(t, mn2), r = t - pz * n * n, py = fdiv(r, mn), px = r - py * n;
+        // odd coordinates reach the coarse nodes at p - 1 and p + 1, even ones the node at p
+        const int lx = px & 1 ? -1 : 0, ly = py & 1 ? -1 : 0, lz = pz & 1 ? -1 : 0;
         T acc = T(0);
-        for (int dz = lo[2]; dz <= hi[2]; dz += 2)
-            for (int dy = lo[1]; dy <= hi[1]; dy += 2)
-                for (int dx = lo[0]; dx <= hi[0]; dx += 2) {
-                    const int d[3] = {dx, dy, dz};
-                    int e[3], q[3];
-                    for (int a = 0; a < 3; ++a) {
-                        const int v = p[a] + d[a];          // 0..n, even
-                        e[a] = v >= n ? 1 : 0;
-                        q[a] = v - e[a] * n;
-                    }
-                    const int c = nb27[dir27(e[0], e[1], e[2])];
-                    if (c < 0) continue;                     // 2X not in Omega_k: X is not covered
-                    bool inside = true;
-                    for (int sz = 0; sz <= (q[2] == 0); ++sz)
-                        for (int sy = 0; sy <= (q[1] == 0); ++sy)
-                            for (int sx = 0; sx <= (q[0] == 0); ++sx)
-                                if (lf.nbr[27 * c + dir27(-sx, -sy, -sz)] < 0) inside = false;
-                    const int P = lf.parent[c], o = lf.octant[c];
-                    const int X = (o & 1) * h + (q[0] >> 1), Y = ((o >> 1) & 1) * h + (q[1] >> 1),
-                              Z = ((o >> 2) & 1) * h + (q[2] >> 1);
-                    const T v = Fc[(size_t)P * n3 + (Z * n + Y) * n + X];
-                    if (inside) {
+        for (int dz = lz; dz <= -lz; dz += 2)
+            for (int dy = ly; dy <= -ly; dy += 2)
+                for (int dx = lx; dx <= -lx; dx += 2) {
+                    const int vx = px + dx, vy = py + dy, vz = pz + dz;      // 0..n, even
+                    const int ex = vx >= n, ey = vy >= n, ez = vz >= n;
+                    const int e = ex | (ey << 1) | (ez << 2);
+                    if (cblk[e] < 0) continue;                  // 2X not in Omega_k: X is not covered
+                    const int qx = vx - ex * n, qy = vy - ey * n, qz = vz - ez * n;
+                    const int m = (qx == 0) | ((qy == 0) << 1) | ((qz == 0) << 2);
+                    const int o = coct[e];
+                    const int X = (o & 1) * h + (qx >> 1), Y = ((o >> 1) & 1) * h + (qy >> 1),
+                              Z = ((o >> 2) & 1) * h + (qz >> 1);
+                    const T v = Fc[(size_t)cpar[e] * n3 + (Z * n + Y) * n + X];
+                    if (ins[e][m]) {
                         const T w = T((dx ? 1.0 : 2.0) * (dy ? 1.0 : 2.0) * (dz ? 1.0 : 2.0) / 64.0);
                         acc += w * v;
                     } else if ((dx | dy | dz) == 0) {

@@ -288,7 +288,7 @@ template <typename T>
 struct HaloSmemT {
     int snbr[27], cnbr[27], cleaf[27], cch[27 * 8], off[27], rdir[27], rstart[27];
     T sw[8];
-    int interp, nreg, ntot;
+    int interp, outside, nreg, ntot;
 };
 
 __host__ __device__ inline int pool_size(int n, int I) {
@@ -1224,33 +1224,60 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(T* __restrict__ A, T* __r
     if (tid < I) hs.sw[tid] = T(midw<I>(tid));
     __syncthreads();
     if (tid == 0) {
-        int any = 0;
-        for (int d = 0; d < 27; ++d) any |= (d != 13 && hs.snbr[d] == NBR_MISSING);
+        int any = 0, out = 0;
+        for (int d = 0; d < 27; ++d) {
+            any |= (d != 13 && hs.snbr[d] == NBR_MISSING);
+            out |= (d != 13 && hs.snbr[d] == NBR_OUTSIDE);
+        }
         hs.interp = any;
+        hs.outside = out;
     }
     T* Ab = A + (size_t)b * S3;
     const int shell = S3 - n3;
-    // copied regions
-    for (int t = tid; t < shell; t += nth) {
-        int x, y, z;
-        shell_coords(t, S, x, y, z);
-        const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
-        const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
-        const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
-        const int j = hs.snbr[dir27(dx, dy, dz)];
-        if (j < 0) continue;
-        const int o = (z * S + y) * S + x;
-        const T a = Ab[o];
-        Ab[o] = T(0);
-        if (a != T(0)) atomicAdd(&A[(size_t)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n)], a);
+    // copied regions: K ghost nodes per thread and round, all loads issued
+    // before the stores and atomics (which could alias them as far as the
+    // compiler knows), so that their latencies overlap
+    constexpr int K = 8;
+    for (int t0 = tid; t0 < shell; t0 += K * nth) {
+        T a[K];
+        int o[K];
+        long long to[K];                  // target index in A, or -1
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int t = t0 + k * nth;
+            to[k] = -1;
+            o[k] = 0;
+            a[k] = T(0);
+            if (t < shell) {
+                int x, y, z;
+                shell_coords(t, S, x, y, z);
+                const int dx = x == 0 ? -1 : (x == S - 1 ? 1 : 0);
+                const int dy = y == 0 ? -1 : (y == S - 1 ? 1 : 0);
+                const int dz = z == 0 ? -1 : (z == S - 1 ? 1 : 0);
+                const int j = hs.snbr[dir27(dx, dy, dz)];
+                if (j >= 0) {
+                    o[k] = (z * S + y) * S + x;
+                    to[k] = (long long)j * S3 + ((z - dz * n) * S + (y - dy * n)) * S + (x - dx * n);
+                    a[k] = Ab[o[k]];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (to[k] < 0) continue;
+            Ab[o[k]] = T(0);
+            if (a[k] != T(0)) atomicAdd(&A[to[k]], a[k]);
+        }
     }
     __syncthreads();
     if (!hs.interp) {
-        for (int t = tid; t < shell; t += nth) {      // outside-domain ghosts: dropped
-            int x, y, z;
-            shell_coords(t, S, x, y, z);
-            Ab[(z * S + y) * S + x] = T(0);
-        }
+        // outside-domain ghosts: dropped (the copied ones are clear already)
+        if (hs.outside)
+            for (int t = tid; t < shell; t += nth) {
+                int x, y, z;
+                shell_coords(t, S, x, y, z);
+                Ab[(z * S + y) * S + x] = T(0);
+            }
         return;
     }
     const int P = lk.parent[b];
