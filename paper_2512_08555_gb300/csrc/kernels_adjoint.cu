@@ -49,30 +49,59 @@ __device__ __forceinline__ double rhs_weight(int dx, int dy, int dz) {
 // out[b] (halo layout, g = 1) += scale * L^T lam[b] on the listed blocks: every
 // node q of the (n+2)^3 box gathers the weights of the interior rows p with
 // |p - q| <= 1.  With fadd, also fadd[b] += lam[b] (the f-part of r = f - L u).
+// The weights are symmetric, so this is the stencil applied to lam extended by
+// zeros: lam goes to shared memory with a two-node zero border, and one thread
+// per box column (x, y) walks z with plane sums (for the plane at z,
+// P = f u + e c + k d is what it gives a neighbouring plane and
+// Q = c_w u + f c + e d what it gives its own, c and d the sums of the 4 face
+// and the 4 diagonal neighbours in (x, y)), so L lam(z) = P(z - 1) + P(z + 1)
+// + Q(z); a warp's threads take consecutive x, so its global accesses are
+// contiguous.
 template <int M, typename T>
 __global__ void k_stencil_T(T* __restrict__ out, const T* __restrict__ lam, T* __restrict__ fadd,
                             const int* __restrict__ blocks, int n, T scale) {
+    using W = LWa<M>;
+    extern __shared__ __align__(16) unsigned char sl_raw[];
+    T* lp = reinterpret_cast<T*>(sl_raw);
     const int b = blocks[blockIdx.x];
-    const int S = n + 2, S3 = S * S * S, n3 = n * n * n;
+    const int S = n + 2, S2 = S * S, S3 = S2 * S, n3 = n * n * n, A = n + 4, A2 = A * A, A3 = A2 * A;
     const T* lb = lam + (size_t)b * n3;
-    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
-        const int qx = t % S - 1, qy = (t / S) % S - 1, qz = t / (S * S) - 1;   // interior coordinates of q
-        T acc = T(0);
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int pz = qz + dz;
-            if (pz < 0 || pz >= n) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int py = qy + dy;
-                if (py < 0 || py >= n) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int px = qx + dx;
-                    if (px < 0 || px >= n) continue;
-                    const T w = T(lhs_w<M>((dx != 0) + (dy != 0) + (dz != 0)));
-                    if (w != T(0)) acc += w * lb[(pz * n + py) * n + px];
-                }
-            }
+    for (int t = threadIdx.x; t < A3; t += blockDim.x) lp[t] = T(0);
+    __syncthreads();
+    const unsigned mn = magic_of(n), mn2 = magic_of(n * n), mS = magic_of(S);
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int z = fdiv(t, mn2), r = t - z * n * n, y = fdiv(r, mn), x = r - y * n;
+        lp[(z + 2) * A2 + (y + 2) * A + x + 2] = lb[t];
+    }
+    __syncthreads();
+    T* ob = out + (size_t)b * S3;
+    for (int r = threadIdx.x; r < S2; r += blockDim.x) {
+        const int Y = fdiv(r, mS), X = r - Y * S;
+        // padded coordinates of box node (X, Y, Z): (X + 1, Y + 1, Z + 1)
+        const T* c0 = lp + (Y + 1) * A + X + 1;
+        auto plane = [&](int a, T& P, T& Q) {
+            const T* q0 = c0 + a * A2;
+            const T u = q0[0];
+            const T c = (q0[-1] + q0[1]) + (q0[-A] + q0[A]);
+            const T d = (q0[-1 - A] + q0[1 - A]) + (q0[-1 + A] + q0[1 + A]);
+            T p = T(W::f) * u, q = T(W::c) * u + T(W::f) * c;
+            if (W::e != 0) { p += T(W::e) * c; q += T(W::e) * d; }
+            if (W::k != 0) p += T(W::k) * d;
+            P = p;
+            Q = q;
+        };
+        T P0, P1, Q1, Qg;
+        plane(0, P0, Qg);
+        plane(1, P1, Q1);
+        T* ocol = ob + Y * S + X;
+        for (int Z = 0; Z < S; ++Z) {
+            T P2, Q2;
+            plane(Z + 2, P2, Q2);
+            ocol[(size_t)Z * S2] += scale * ((P0 + P2) + Q1);
+            P0 = P1;
+            P1 = P2;
+            Q1 = Q2;
         }
-        out[(size_t)b * S3 + t] += scale * acc;
     }
     if (fadd)
         for (int t = threadIdx.x; t < n3; t += blockDim.x) fadd[(size_t)b * n3 + t] += lb[t];
@@ -82,9 +111,16 @@ template <typename T>
 void launch_stencil_T(T* out, const T* lam, T* fadd, const int* blocks, int nblocks, int n, int M, double inv_h2,
                       cudaStream_t s) {
     if (nblocks == 0) return;
-    if (M == 2) k_stencil_T<2, T><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<2>::den));
-    if (M == 4) k_stencil_T<4, T><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<4>::den));
-    if (M == 6) k_stencil_T<6, T><<<nblocks, 256, 0, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<6>::den));
+    static std::once_flag attr[MAX_DEVICES];
+    once_per_device(attr, [] {
+        cudaFuncSetAttribute(k_stencil_T<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_stencil_T<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+        cudaFuncSetAttribute(k_stencil_T<6, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    });
+    const size_t sm = sizeof(T) * (size_t)(n + 4) * (n + 4) * (n + 4);
+    if (M == 2) k_stencil_T<2, T><<<nblocks, 256, sm, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<2>::den));
+    if (M == 4) k_stencil_T<4, T><<<nblocks, 256, sm, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<4>::den));
+    if (M == 6) k_stencil_T<6, T><<<nblocks, 256, sm, s>>>(out, lam, fadd, blocks, n, T(inv_h2 / LWa<6>::den));
 }
 template void launch_stencil_T<double>(double*, const double*, double*, const int*, int, int, int, double, cudaStream_t);
 template void launch_stencil_T<float>(float*, const float*, float*, const int*, int, int, int, double, cudaStream_t);
@@ -389,7 +425,8 @@ __global__ void k_prolong_T(T* __restrict__ Uc, T* __restrict__ Hc, const T* __r
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int x = 2 * i + dx;
                     if (x < 0 || x >= n) continue;
-                    const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+                    // 1 or 1/2 per axis: exact, without FP64 arithmetic
+                    const T w = T(1.0 / 8.0) * T(1 << ((dx == 0) + (dy == 0) + (dz == 0)));
                     acc += w * Ub[((z + 1) * S + y + 1) * S + x + 1];
                 }
             }
@@ -466,7 +503,8 @@ __global__ void k_fw_T(T* __restrict__ Rf, const T* __restrict__ Fc, LevelView l
                               Z = ((o >> 2) & 1) * h + (qz >> 1);
                     const T v = Fc[(size_t)cpar[e] * n3 + (Z * n + Y) * n + X];
                     if (ins[e][m]) {
-                        const T w = T((dx ? 1.0 : 2.0) * (dy ? 1.0 : 2.0) * (dz ? 1.0 : 2.0) / 64.0);
+                        // (1 or 2 per axis) / 64: exact, without FP64 arithmetic
+                        const T w = T(((dx == 0) + 1) * ((dy == 0) + 1) * ((dz == 0) + 1)) * T(1.0 / 64.0);
                         acc += w * v;
                     } else if ((dx | dy | dz) == 0) {
                         acc += v;
@@ -543,15 +581,25 @@ template void launch_dense_to_blocks<float>(float*, const float*, const int*, in
                                             cudaStream_t);
 
 // ---------------------------------------------------------------- block and vector helpers
+// scale * v in the output's type: a scale of 1 is a plain conversion, and
+// float to float stays in FP32 (GB300's FP64 pipe is the scarce one).
+template <typename TO, typename TI>
+__device__ __forceinline__ TO scaled(TI v, double scale, bool unit) {
+    if (unit) return TO(v);
+    if constexpr (sizeof(TO) == 4 && sizeof(TI) == 4) return TO(float(scale) * v);
+    else return TO(scale * (double)v);
+}
+
 // out[b] = scale * interior of A[b] (halo g) for the listed blocks.
 template <typename TO, typename TI>
 __global__ void k_interior_get(TO* __restrict__ out, const TI* __restrict__ A, int g, const int* __restrict__ blocks, int n,
                                double scale) {
     const int b = blocks[blockIdx.x];
     const int S = n + 2 * g;
+    const bool unit = scale == 1.0;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        out[(size_t)b * n * n * n + t] = TO(scale * (double)A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g]);
+        out[(size_t)b * n * n * n + t] = scaled<TO>(A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g], scale, unit);
     }
 }
 
@@ -569,9 +617,10 @@ __global__ void k_interior_add(TA* __restrict__ A, int g, const TV* __restrict__
                                double scale) {
     const int b = blocks[blockIdx.x];
     const int S = n + 2 * g;
+    const bool unit = scale == 1.0;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
-        A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g] += TA(scale * (double)v[(size_t)b * n * n * n + t]);
+        A[(size_t)b * S * S * S + ((z + g) * S + y + g) * S + x + g] += scaled<TA>(v[(size_t)b * n * n * n + t], scale, unit);
     }
 }
 
@@ -589,8 +638,9 @@ template <typename TO, typename TI>
 __global__ void k_block_copy(TO* __restrict__ out, const TI* __restrict__ in, const int* __restrict__ blocks, int n,
                              double scale) {
     const int b = blocks[blockIdx.x];
+    const bool unit = scale == 1.0;
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x)
-        out[(size_t)b * n * n * n + t] = in ? TO(scale * (double)in[(size_t)b * n * n * n + t]) : TO(0);
+        out[(size_t)b * n * n * n + t] = in ? scaled<TO>(in[(size_t)b * n * n * n + t], scale, unit) : TO(0);
 }
 
 template <typename TO, typename TI>
@@ -615,13 +665,19 @@ template void launch_block_zero<float>(float*, const int*, int, int, cudaStream_
 __global__ void k_lincomb(double* out, double a, const double* x, double b, const double* y, size_t len,
                           unsigned long long* absmax) {
     __shared__ double red[32];
-    double m = 0.0;
+    // max |v| on bit patterns (integer pipe; NaN patterns sort above +Inf and
+    // are mapped to +Inf below), and a plain add for a = b = 1: the FP64 pipe
+    // would otherwise bound this memory-bound loop
+    unsigned long long mb = 0;
+    const bool add = a == 1.0 && b == 1.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x) {
-        const double v = a * x[i] + b * y[i];
+        const double v = add ? x[i] + y[i] : a * x[i] + b * y[i];
         out[i] = v;
-        m = fmax(m, v != v ? __longlong_as_double(0x7ff0000000000000ULL) : fabs(v));
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+        mb = bits > mb ? bits : mb;
     }
     if (!absmax) return;
+    double m = mb > 0x7ff0000000000000ULL ? __longlong_as_double(0x7ff0000000000000ULL) : __longlong_as_double((long long)mb);
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) red[w] = m;
