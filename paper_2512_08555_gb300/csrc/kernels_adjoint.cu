@@ -177,16 +177,17 @@ void launch_rstencil_T(double* out, const double* fsb, const int* blocks, int nb
 // need no bounds tests.  Along an axis where a destination of box parity p
 // differs from the colour, its two sources sit at split offsets p - 1 and p.
 // One destination sub-array's gathers: every position subtracts coef times the
-// sum of the CNT colour-c values at the (uniform) offsets off[] from its own
-// place in the bordered copy xs (offsets in z, y, x order, ascending).
+// sum of its CNT colour-c values in the bordered copy xs, at uniform offsets
+// from its own place (z, y, x order, ascending).
 template <int CNT, typename T>
 __device__ __forceinline__ void gather_T(T* __restrict__ sd, const T* __restrict__ xs, const int* __restrict__ ptab,
-                                         const int (&off)[8], T coef, int H3) {
+                                         int o0, int hi, int lo, int E, int E2, T coef, int H3) {
     for (int pos = threadIdx.x; pos < H3; pos += blockDim.x) {
-        const T* c0 = xs + (ptab[pos] & 0xFFF);
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < CNT; ++k) acc += c0[off[k]];
+        const T* g = xs + (ptab[pos] & 0xFFF) + o0;
+        T acc;
+        if (CNT == 2) acc = g[0] + g[lo];
+        else if (CNT == 4) acc = ((g[0] + g[lo]) + g[hi]) + g[hi + lo];
+        else acc = ((((((g[0] + g[1]) + g[E]) + g[E + 1]) + g[E2]) + g[E2 + 1]) + g[E2 + E]) + g[E2 + E + 1];
         sd[pos] -= coef * acc;
     }
 }
@@ -245,28 +246,17 @@ __global__ void __launch_bounds__(256) k_smooth_T(T* __restrict__ U, T* __restri
             const T w = T(lhs_w<M>(m));
             if (w == T(0)) continue;
             // along an axis where it differs, the sources sit at split offsets p - 1 and p
-            // (p its parity bit); offsets in z, y, x order
-            int ax[3], na = 0;
-            if (D & 4) ax[na++] = 2;
-            if (D & 2) ax[na++] = 1;
-            if (D & 1) ax[na++] = 0;
-            int off[8];
-            int cnt = 1;
-            off[0] = 0;
-            for (int a = 0; a < na; ++a) {
-                const int st = ax[a] == 2 ? E2 : (ax[a] == 1 ? E : 1);
-                const int p = (d >> ax[a]) & 1;
-                for (int k = cnt - 1; k >= 0; --k) {
-                    off[2 * k + 1] = off[k] + p * st;
-                    off[2 * k] = off[k] + (p - 1) * st;
-                }
-                cnt *= 2;
-            }
+            // (p its parity bit); o0 is the first (all axes at p - 1), hi and lo the
+            // strides of the differing axes (the larger first; one axis: lo only)
+            const int o0 = ((D & 4) ? (((d >> 2) & 1) - 1) * E2 : 0) + ((D & 2) ? (((d >> 1) & 1) - 1) * E : 0) +
+                           ((D & 1) ? (d & 1) - 1 : 0);
+            const int hi = (D & 4) ? E2 : E;
+            const int lo = (D & 1) ? 1 : ((D & 2) ? E : E2);
             T* sd = su + d * H3;
             const T coef = w * inv_c;
-            if (m == 1) gather_T<2>(sd, xs, ptab, off, coef, H3);
-            else if (m == 2) gather_T<4>(sd, xs, ptab, off, coef, H3);
-            else gather_T<8>(sd, xs, ptab, off, coef, H3);
+            if (m == 1) gather_T<2>(sd, xs, ptab, o0, hi, lo, E, E2, coef, H3);
+            else if (m == 2) gather_T<4>(sd, xs, ptab, o0, hi, lo, E, E2, coef, H3);
+            else gather_T<8>(sd, xs, ptab, o0, hi, lo, E, E2, coef, H3);
         }
         __syncthreads();
     }
