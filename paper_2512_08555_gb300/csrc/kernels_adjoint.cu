@@ -205,18 +205,23 @@ __global__ void __launch_bounds__(256) k_smooth_T(T* __restrict__ U, T* __restri
     const int b = blockIdx.x;
     T* Ub = U + (size_t)b * S3;
     T* Fb = F + (size_t)b * n3;
-    const unsigned mS = magic_of(S), mS2 = magic_of(S2), mH = magic_of(H), mH2 = magic_of(H2);
-    auto split = [&](int X, int Y, int Z) {
-        return (((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1)) * H3 + (Z >> 1) * H2 + (Y >> 1) * H + (X >> 1);
-    };
-    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
-        const int Z = fdiv(t, mS2), r = t - Z * S2, Y = fdiv(r, mS), X = r - Y * S;
-        su[split(X, Y, Z)] = Ub[t];
-    }
+    const unsigned mH = magic_of(H), mH2 = magic_of(H2), mH3 = magic_of(H3);
     for (int t = threadIdx.x; t < E2 * E; t += blockDim.x) xs[t] = T(0);
     for (int t = threadIdx.x; t < H3; t += blockDim.x) {
         const int l = fdiv(t, mH2), r = t - l * H2, j = fdiv(r, mH), i = r - j * H;
         ptab[t] = ((l + 1) * E2 + (j + 1) * E + i + 1) | (i << 12) | (j << 16) | (l << 20);
+    }
+    __syncthreads();
+    // global box index of split position pos of sub-array d (box parity d)
+    auto boxidx = [&](int d, int pos) {
+        const int pt = ptab[pos];
+        const int X = 2 * ((pt >> 12) & 15) + (d & 1), Y = 2 * ((pt >> 16) & 15) + ((d >> 1) & 1),
+                  Z = 2 * ((pt >> 20) & 15) + (d >> 2);
+        return (Z * S + Y) * S + X;
+    };
+    for (int t = threadIdx.x; t < 8 * H3; t += blockDim.x) {
+        const int d = fdiv(t, mH3);
+        su[t] = Ub[boxidx(d, t - d * H3)];
     }
     __syncthreads();
     const T inv_c = T(1.0 / LWa<M>::c), fscale = h2den * inv_c;
@@ -260,9 +265,9 @@ __global__ void __launch_bounds__(256) k_smooth_T(T* __restrict__ U, T* __restri
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < S3; t += blockDim.x) {
-        const int Z = fdiv(t, mS2), r = t - Z * S2, Y = fdiv(r, mS), X = r - Y * S;
-        Ub[t] = su[split(X, Y, Z)];
+    for (int t = threadIdx.x; t < 8 * H3; t += blockDim.x) {
+        const int d = fdiv(t, mH3);
+        Ub[boxidx(d, t - d * H3)] = su[t];
     }
 }
 
