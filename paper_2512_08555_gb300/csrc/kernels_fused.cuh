@@ -1237,7 +1237,7 @@ __global__ void __launch_bounds__(256) k_ghost_T_fused(T* __restrict__ A, T* __r
     // copied regions: K ghost nodes per thread and round, all loads issued
     // before the stores and atomics (which could alias them as far as the
     // compiler knows), so that their latencies overlap
-    constexpr int K = 8;
+    constexpr int K = 4;
     for (int t0 = tid; t0 < shell; t0 += K * nth) {
         T a[K];
         int o[K];

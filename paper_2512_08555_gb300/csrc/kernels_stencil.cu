@@ -692,11 +692,14 @@ __global__ void k_absmax(const double* __restrict__ F, const int* __restrict__ b
                          const int* __restrict__ prob) {
     const int b = blocks[blockIdx.x];
     const int n3 = n * n * n;
-    double m = 0.0;
+    // max |v| on bit patterns (integer pipe): ordered like the values for
+    // non-negative doubles; NaN patterns sort above +Inf and become +Inf
+    unsigned long long mb = 0;
     for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-        const double v = F[(size_t)b * n3 + t];
-        m = (v != v) ? __longlong_as_double(0x7ff0000000000000ULL) : fmax(m, fabs(v));
+        const unsigned long long v = (unsigned long long)__double_as_longlong(F[(size_t)b * n3 + t]) & 0x7fffffffffffffffULL;
+        mb = v > mb ? v : mb;
     }
+    const double m = mb > 0x7ff0000000000000ULL ? __longlong_as_double(0x7ff0000000000000ULL) : __longlong_as_double((long long)mb);
     block_max_atomic(m, out + (prob ? prob[b] : 0));
 }
 
