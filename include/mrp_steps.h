@@ -130,6 +130,16 @@ int mrp_coarse_solve_noalloc(mrp_handle* h, const double* f0, double* u0, void* 
  * measurement aid). */
 int mrp_fma_peak(int32_t precision, double* tflops, void* stream);
 
+/* The two float/double conversions of the mixed-precision path, for their
+ * tests: f_out[i] = d_in[i] rounded to float (nearest, ties to even) as the
+ * FP64 leaf residual writes the FP32 right-hand side, and d_out[i] = f_in[i]
+ * widened to double as the FP32 corrections are added to u.  Both are done
+ * with integer operations where the result is a normal number (GB300's FP64
+ * pipe is the scarce unit) and must equal the IEEE conversions bit for bit.
+ * Device buffers of n elements (any may be NULL when n == 0), ordered on
+ * stream.  The paper has no counterpart (an implementation detail). */
+int mrp_convert_check(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n, void* stream);
+
 enum { MRP_ADJ_CYCLE_T = 0, MRP_ADJ_RES_T = 1, MRP_ADJ_OUT_T = 2, MRP_ADJ_RHS_T = 3 };
 int mrp_adjoint_len(mrp_handle* h, int64_t* len);
 int mrp_adjoint_op(mrp_handle* h, int32_t op, const double* in, double* out, void* stream);

@@ -1105,7 +1105,7 @@ __global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, co
                 const double l = (P0 + P2) + Q1;
                 const size_t fi = rowf + (X - 1);
                 const double res = F[fi] - scale * l;
-                if (R) R[fi] = (float)res;
+                if (R) R[fi] = narrow_rn(res);
                 // |res| as its bit pattern (sign cleared): ordered like the
                 // value for non-negative doubles, NaN above +Inf
                 mb = umax64(mb, (unsigned long long)__double_as_longlong(res) & 0x7fffffffffffffffULL);
@@ -1157,6 +1157,38 @@ __global__ void __launch_bounds__(512) k_rhs_fused(double* __restrict__ F, const
     build_halo<double, I>(su, pool, patch, hs.rec, Af, Ac, lk, b, n, sp);
     double* out = F + (size_t)b * n * n * n;
     unsigned long long mb = 0;        // max |f*| as a bit pattern
+    if constexpr (NC != 0) {
+        // Fixed block size: one thread per interior (y, z) row walking x, the
+        // row's x neighbours kept in registers (same sums, same order)
+        const int H = sp.H, Hp = sp.H2, H3p = sp.H3p;
+        for (int r = threadIdx.x; r < NC * NC; r += blockDim.x) {
+            const int z = r / NC, y = r - z * NC;
+            const int Y = y + 1, Z = z + 1;
+            auto rowb = [&](int dy, int dz) {
+                const int YY = Y + dy, ZZ = Z + dz;
+                return (((ZZ & 1) << 2) | ((YY & 1) << 1)) * H3p + (ZZ >> 1) * Hp + (YY >> 1) * H;
+            };
+            const int r00 = rowb(0, 0), rm0 = rowb(-1, 0), rp0 = rowb(1, 0), r0m = rowb(0, -1), r0p = rowb(0, 1);
+            auto at = [&](int rb, int X) { return su[rb + (X & 1) * H3p + (X >> 1)]; };
+            double um = at(r00, 0), uc = at(r00, 1);
+            double* orow = out + (size_t)r * NC;
+#pragma unroll
+            for (int X = 1; X <= NC; ++X) {
+                const double up = at(r00, X + 1);
+                double v = uc;
+                if (M == 4) {
+                    const double sf = (um + up) + (at(rm0, X) + at(rp0, X)) + (at(r0m, X) + at(r0p, X));
+                    v = 0.5 * uc + sf * (1.0 / 12.0);
+                }
+                orow[X - 1] = v;
+                mb = umax64(mb, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL);
+                um = uc;
+                uc = up;
+            }
+        }
+        bmax_atomic(__longlong_as_double((long long)mb), fmax_out + (lk.prob ? lk.prob[b] : 0));
+        return;
+    }
     for (int t = threadIdx.x; t < n * n * n; t += blockDim.x) {
         const int x = t % n, y = (t / n) % n, z = t / (n * n);
         const int X = x + 1, Y = y + 1, Z = z + 1;

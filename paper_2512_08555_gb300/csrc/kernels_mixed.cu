@@ -90,6 +90,7 @@ void launch_cast_rhs(float* F32, const double* R64, const int* leaf_blocks, int 
     k_cast_rhs<<<nleaf, 256, 0, s>>>(F32, R64, leaf_blocks, n, zero);
 }
 
+
 // U64 += U32 on the interior of every block of a level.
 __global__ void k_accumulate_u(double* __restrict__ U64, const float* __restrict__ U32, int n) {
     const int b = blockIdx.x;
@@ -115,7 +116,7 @@ __global__ void k_accumulate_u(double* __restrict__ U64, const float* __restrict
         }
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (t0 + k * blockDim.x < n3) U64[o[k]] = u[k] + (double)v[k];
+            if (t0 + k * blockDim.x < n3) U64[o[k]] = u[k] + widen_exact(v[k]);
     }
 }
 
@@ -128,7 +129,7 @@ void launch_accumulate_u(double* U64, const float* U32, int nb, int n, cudaStrea
 __global__ void k_accumulate_f(double* __restrict__ F64, const float* __restrict__ F32, const int* __restrict__ blocks, int n) {
     const int b = blocks[blockIdx.x];
     const int n3 = n * n * n;
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) F64[(size_t)b * n3 + t] += (double)F32[(size_t)b * n3 + t];
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) F64[(size_t)b * n3 + t] += widen_exact(F32[(size_t)b * n3 + t]);
 }
 
 void launch_accumulate_f(double* F64, const float* F32, const int* blocks, int nblocks, int n, cudaStream_t s) {
@@ -168,3 +169,22 @@ void launch_cauchy(double* Uprev, const double* U, const int* leaf_blocks, int n
 }
 
 }  // namespace mrp
+
+namespace mrp {
+__global__ void k_convert_check(const double* __restrict__ d_in, float* __restrict__ f_out, const float* __restrict__ f_in,
+                                double* __restrict__ d_out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        f_out[i] = narrow_rn(d_in[i]);
+        d_out[i] = widen_exact(f_in[i]);
+    }
+}
+}  // namespace mrp
+
+extern "C" int mrp_convert_check(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n,
+                                 void* stream) {
+    if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out))) return MRP_ERR_INVALID_ARG;
+    if (n == 0) return MRP_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mrp::k_convert_check<<<grid, 256, 0, (cudaStream_t)stream>>>(d_in, f_out, f_in, d_out, (long long)n);
+    return cudaGetLastError() == cudaSuccess ? MRP_OK : MRP_ERR_CUDA;
+}

@@ -24,6 +24,38 @@ __host__ __device__ inline int dir27(int dx, int dy, int dz) { return (dz + 1) *
 __device__ __forceinline__ unsigned magic_of(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
 __device__ __forceinline__ int fdiv(int x, unsigned m) { return (int)__umulhi((unsigned)x, m); }
 
+// (double)v for a float v without the conversion instruction, which runs on
+// GB300's scarce FP64 pipe: a normal float's exponent is rebiased (+896 =
+// 1023 - 127) and its 23-bit fraction moved to the top of the 52-bit one,
+// which is exact; zeros, subnormals, Inf and NaN take the plain conversion.
+__device__ __forceinline__ double widen_exact(float v) {
+    const unsigned long long u = __float_as_uint(v);
+    const unsigned e = (unsigned)(u >> 23) & 0xFFu;
+    if (e - 1u < 254u)
+        return __longlong_as_double((long long)(((u & 0x80000000ull) << 32) | ((unsigned long long)(e + 896u) << 52) |
+                                                ((u & 0x7FFFFFull) << 29)));
+    return (double)v;
+}
+
+// (float)d, rounded to nearest with ties to even, without the conversion
+// instruction (it runs on GB300's scarce FP64 pipe): for results in the
+// normal float range the 52-bit fraction is cut to 23 bits and rounded on the
+// 29 bits dropped; a carry out of the fraction moves into the exponent, which
+// is the correct rounding (up to +-Inf past the largest float).  Zeros,
+// subnormal results, overflow before rounding, Inf and NaN take the plain
+// conversion.
+__device__ __forceinline__ float narrow_rn(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((u >> 52) & 0x7FF) - 896;         // float exponent field (1023 - 127 = 896)
+    if (e >= 1 && e <= 254) {
+        unsigned keep = (unsigned)((u >> 29) & 0x7FFFFFu);
+        const unsigned rem = (unsigned)(u & 0x1FFFFFFFu), half = 0x10000000u;
+        keep += (rem > half || (rem == half && (keep & 1u))) ? 1u : 0u;
+        return __uint_as_float((((unsigned)(u >> 32)) & 0x80000000u) + ((unsigned)e << 23) + keep);
+    }
+    return (float)d;
+}
+
 // Asynchronous global -> shared copies (cp.async): one element, or 16 bytes;
 // a thread's copies complete at cp_async_wait<N>() (all but its N most recent
 // committed groups), and are visible to the CTA after the next barrier.

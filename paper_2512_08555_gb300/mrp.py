@@ -26,7 +26,7 @@ EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
             "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph",
-            "mrp_solve_host", "mrp_fma_peak"]
+            "mrp_solve_host", "mrp_fma_peak", "mrp_convert_check"]
 ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
@@ -92,6 +92,7 @@ def load_library(path=LIB_PATH):
     lib.mrp_solve_graph.argtypes = [P, P, P, P, C.POINTER(Stats)]
     lib.mrp_solve_host.argtypes = [P, P, P, P, C.POINTER(Stats)]
     lib.mrp_fma_peak.argtypes = [I32, C.POINTER(D), P]
+    lib.mrp_convert_check.argtypes = [P, P, P, P, I64, P]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
     lib.mrp_error_string.restype = C.c_char_p
@@ -335,6 +336,18 @@ def fma_peak_tflops(precision="fp64", stream=None):
     v = C.c_double()
     _check(lib.mrp_fma_peak({"fp64": 0, "fp32": 1}[precision], C.byref(v), _stream_ptr(stream)), "mrp_fma_peak")
     return v.value
+
+
+def convert_check(d_in, f_in, stream=None):
+    """The library's float/double conversions (``mrp_convert_check``): (float32 of d_in, float64 of f_in)."""
+    import torch
+    lib = load_library()
+    f_out = torch.empty_like(d_in, dtype=torch.float32)
+    d_out = torch.empty_like(f_in, dtype=torch.float64)
+    _check(lib.mrp_convert_check(C.c_void_p(d_in.data_ptr()), C.c_void_p(f_out.data_ptr()), C.c_void_p(f_in.data_ptr()),
+                                 C.c_void_p(d_out.data_ptr()), d_in.numel(), _stream_ptr(stream)), "mrp_convert_check")
+    torch.cuda.current_stream().synchronize()
+    return f_out, d_out
 
 
 def poisson_solve(solver, f):

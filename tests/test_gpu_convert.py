@@ -1,0 +1,71 @@
+"""The mixed-precision path's own float/double conversions against IEEE.
+
+The FP64 leaf residual rounds its result to FP32 and the accumulation widens
+the FP32 corrections to FP64 with integer operations (GB300's FP64 pipe is
+the scarce unit); ``mrp_convert_check`` runs both on device buffers.  numpy's
+casts are the IEEE conversions (round to nearest, ties to even; exact
+widening), so the results must agree bit for bit, special values included.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _doubles(rng):
+    # random magnitudes over the whole float range and beyond
+    e = rng.integers(-160, 160, size=200000)
+    v = rng.uniform(1.0, 2.0, size=e.size) * np.exp2(e.astype(np.float64)) * rng.choice([-1.0, 1.0], size=e.size)
+    # exact ties and near-ties of the 29 dropped fraction bits, both parities of the kept bit
+    base = rng.integers(0, 1 << 52, size=4000, dtype=np.uint64) & ~np.uint64((1 << 29) - 1)
+    exp = (rng.integers(900, 1140, size=base.size).astype(np.uint64) << np.uint64(52))
+    ties = []
+    for low in (0x10000000, 0x0FFFFFFF, 0x10000001, 0x1FFFFFFF, 0):
+        ties.append((exp | base | np.uint64(low)).view(np.float64))
+    f32 = np.finfo(np.float32)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, float(f32.max), -float(f32.max),
+                        float(f32.max) * (1 + 2.0 ** -25), float(f32.max) * (1 + 2.0 ** -23), 1e39, -1e39,
+                        float(f32.tiny), float(f32.tiny) * (1 - 2.0 ** -30), float(f32.tiny) / 3, 1e-46, 1e-50,
+                        2.0 ** -149, 2.0 ** -150, 1.5 * 2.0 ** -149, 1.0, -1.0, 1.0 + 2.0 ** -24,
+                        1.0 + 3 * 2.0 ** -24, 5e-324, 1.7976931348623157e308])
+    return np.concatenate([v] + ties + [special])
+
+
+def _floats(rng):
+    bits = rng.integers(0, 1 << 32, size=200000, dtype=np.uint64).astype(np.uint32)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-45, -1e-45, 1.17549435e-38, 1.1754942e-38,
+                        3.4028235e38, -3.4028235e38, 1.0, -2.5], dtype=np.float32)
+    return np.concatenate([bits.view(np.float32), special])
+
+
+def _same_bits(a, b):
+    """Equal bit patterns, any NaN matching any NaN."""
+    na, nb = np.isnan(a), np.isnan(b)
+    assert np.array_equal(na, nb)
+    ia = a.view(np.int32 if a.dtype == np.float32 else np.int64)
+    ib = b.view(np.int32 if b.dtype == np.float32 else np.int64)
+    bad = (ia != ib) & ~na
+    assert not bad.any(), (a[bad][:5], b[bad][:5])
+
+
+def test_narrow_and_widen_match_ieee():
+    from paper_2512_08555_gb300.mrp import convert_check
+    rng = np.random.default_rng(7)
+    with np.errstate(over="ignore", invalid="ignore"):
+        d = _doubles(rng)
+        f = _floats(rng)
+        n = max(d.size, f.size)
+        d = np.resize(d, n)
+        f = np.resize(f, n)
+        f_out, d_out = convert_check(torch.from_numpy(d).cuda(), torch.from_numpy(f).cuda())
+        _same_bits(f_out.cpu().numpy(), d.astype(np.float32))
+        _same_bits(d_out.cpu().numpy(), f.astype(np.float64))
