@@ -140,6 +140,18 @@ int mrp_fma_peak(int32_t precision, double* tflops, void* stream);
  * stream.  The paper has no counterpart (an implementation detail). */
 int mrp_convert_check(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n, void* stream);
 
+/* The two conversions of the FP64 leaf residual's fixed-point stencil sum,
+ * for their tests: fx_out[i] = trunc(u_in[i] 2^(shb + 1075)) as a 64-bit
+ * integer (the caller keeps it below 2^62 in magnitude: shb + the exponent
+ * field of every u_in[i] <= 9), and d_out[i] = i_in[i] rounded to double
+ * (nearest, ties to even).  Both use integer operations only; the second
+ * must equal the IEEE conversion bit for bit.  Device buffers of n elements
+ * (any may be NULL when n == 0), ordered on stream.  Returns
+ * MRP_ERR_INVALID_ARG for n < 0, a NULL buffer with n > 0, or shb > 0.  The
+ * paper has no counterpart (an implementation detail). */
+int mrp_fixed_check(const double* u_in, int32_t shb, int64_t* fx_out, const int64_t* i_in, double* d_out, int64_t n,
+                    void* stream);
+
 enum { MRP_ADJ_CYCLE_T = 0, MRP_ADJ_RES_T = 1, MRP_ADJ_OUT_T = 2, MRP_ADJ_RHS_T = 3 };
 int mrp_adjoint_len(mrp_handle* h, int64_t* len);
 int mrp_adjoint_op(mrp_handle* h, int32_t op, const double* in, double* out, void* stream);

@@ -1042,6 +1042,36 @@ __device__ __forceinline__ void bmax_atomic(double v, unsigned long long* out) {
     }
 }
 
+// The FP64 box of a fixed block size NC in 64-bit fixed point, in place: its
+// largest exponent field E (a block-wide max held in *emax, zero on entry)
+// fixes the scale 2^s, s = 1084 - G - E, so that every |u 2^s| < 2^(62 - G);
+// each value becomes trunc(u 2^s) (to_fixed) as the bit pattern of its
+// double slot.  Returns E, or -1 with the box unchanged where the box holds
+// Inf or NaN, only zeros and subnormals, or exponents whose scales 2^-s
+// would leave the normal range (E < 128 or E > 1900).  Ends with a barrier.
+template <int NC, int G>
+__device__ __forceinline__ int box_to_fixed(double* __restrict__ su, const Split& sp, unsigned* emax) {
+    constexpr int H3 = (NC / 2 + 1) * (NC / 2 + 1) * (NC / 2 + 1);
+    unsigned em = 0;
+    for (int t = threadIdx.x; t < 8 * H3; t += blockDim.x) {
+        const int q = t / H3, i = t - q * H3;
+        em = max(em, ((unsigned)__double2hiint(su[q * sp.H3p + i]) >> 20) & 0x7FFu);
+    }
+    em = __reduce_max_sync(0xffffffffu, em);
+    if ((threadIdx.x & 31) == 0) atomicMax(emax, em);
+    __syncthreads();
+    const int E = (int)*emax;
+    if (E < 128 || E > 1900) return -1;
+    const int shb = 9 - G - E;
+    for (int t = threadIdx.x; t < 8 * H3; t += blockDim.x) {
+        const int q = t / H3, i = t - q * H3;
+        double* a = su + q * sp.H3p + i;
+        *a = __longlong_as_double(to_fixed(__double_as_longlong(*a), shb));
+    }
+    __syncthreads();
+    return E;
+}
+
 template <int M, int I, int NC>
 __global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, const double* __restrict__ U,
                                                        const double* __restrict__ F, const double* __restrict__ Uc,
@@ -1054,9 +1084,11 @@ __global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, co
     double* pool = su + 8 * sp.H3p;
     double* patch = pool + pool_size(n, I);
     __shared__ HaloSmem hs;
+    __shared__ unsigned s_emax;       // largest exponent field in the box
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = blocks[blockIdx.x];
+    if (threadIdx.x == 0) s_emax = 0u;
     record_prologue(hs, lk, b);
     build_halo<double, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
@@ -1070,8 +1102,70 @@ __global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, co
         // weighted sums P = w_f u + w_e c + w_k d (what a neighbouring plane
         // contributes) and Q = w_c u + w_f c + w_e d (what the node's own plane
         // contributes), L u(X) = P(X-1) + P(X+1) + Q(X): each plane's sums are
-        // formed once for three nodes (fewer FP64 operations, GB300's scarce
-        // resource, than the 26-neighbour sum).
+        // formed once for three nodes.
+        //
+        // L u in 64-bit fixed point.  Every box value becomes the integer
+        // trunc(u 2^s), with s set by the box's largest exponent field E so
+        // that |u 2^s| < 2^(62 - G) and the stencil's weights (integers whose
+        // absolute values sum to at most 2^G) cannot overflow; the stencil sum
+        // is then exact, rounded once to double and scaled by 2^-s.  A value
+        // loses only bits below 2^(E - 1084 + G) (2^-55 of the box's largest
+        // magnitude for G = 6), less than the rounding of a double stencil
+        // sum, and the integer sums cost a fraction of the FP64 operations
+        // they replace.  Boxes with Inf or NaN, only zeros, or extreme
+        // exponents take the FP64 sums below.
+        constexpr int G = M == 6 ? 8 : 6;
+        const int E = box_to_fixed<NC, G>(su, sp, &s_emax);
+        if (E >= 0) {
+            const double scale2 = scale * __longlong_as_double((long long)(E + G - 1084 + 1023) << 52);
+            constexpr long long wc = (long long)LW<M>::c, wf = (long long)LW<M>::f, we = (long long)LW<M>::e,
+                                wk = (long long)LW<M>::k;
+            constexpr int nn = NC;
+            const int H = sp.H, Hp = sp.H2, H3p = sp.H3p;
+            for (int r = threadIdx.x; r < nn * nn; r += blockDim.x) {
+                const int z = r / nn, y = r - z * nn;
+                const int Y = y + 1, Z = z + 1;
+                auto rowb = [&](int dy, int dz) {
+                    const int YY = Y + dy, ZZ = Z + dz;
+                    return (((ZZ & 1) << 2) | ((YY & 1) << 1)) * H3p + (ZZ >> 1) * Hp + (YY >> 1) * H;
+                };
+                const int r00 = rowb(0, 0), rm0 = rowb(-1, 0), rp0 = rowb(1, 0), r0m = rowb(0, -1), r0p = rowb(0, 1);
+                const int rmm = rowb(-1, -1), rpm = rowb(1, -1), rmp = rowb(-1, 1), rpp = rowb(1, 1);
+                auto ld = [&](int i) { return __double_as_longlong(su[i]); };
+                auto plane = [&](int X, long long& P, long long& Q) {
+                    const int o = (X & 1) * H3p + (X >> 1);
+                    const long long u = ld(r00 + o);
+                    const long long c = (ld(rm0 + o) + ld(rp0 + o)) + (ld(r0m + o) + ld(r0p + o));
+                    long long p = wf * u, q = wc * u + wf * c;
+                    if (we != 0 || wk != 0) {
+                        const long long d = (ld(rmm + o) + ld(rpm + o)) + (ld(rmp + o) + ld(rpp + o));
+                        p += we * c + wk * d;
+                        q += we * d;
+                    }
+                    P = p;
+                    Q = q;
+                };
+                long long P0, P1, Q1, Qg;
+                plane(0, P0, Qg);
+                plane(1, P1, Q1);
+                const size_t rowf = b * n3 + (size_t)r * nn;
+#pragma unroll
+                for (int X = 1; X <= nn; ++X) {
+                    long long P2, Q2;
+                    plane(X + 1, P2, Q2);
+                    const double l = i64_to_double_rn((P0 + P2) + Q1);
+                    const size_t fi = rowf + (X - 1);
+                    const double res = fma(-scale2, l, F[fi]);
+                    if (R) R[fi] = narrow_rn(res);
+                    mb = umax64(mb, (unsigned long long)__double_as_longlong(res) & 0x7fffffffffffffffULL);
+                    P0 = P1;
+                    P1 = P2; Q1 = Q2;
+                }
+            }
+            bmax_atomic(__longlong_as_double((long long)mb), out + (lk.prob ? lk.prob[b] : 0));
+            return;
+        }
+        // The same plane sums in FP64.
         constexpr int nn = NC;
         const int H = sp.H, Hp = sp.H2, H3p = sp.H3p;
         for (int r = threadIdx.x; r < nn * nn; r += blockDim.x) {
@@ -1152,15 +1246,52 @@ __global__ void __launch_bounds__(512) k_rhs_fused(double* __restrict__ F, const
     double* pool = su + 8 * sp.H3p;
     double* patch = pool + pool_size(n, I);
     __shared__ HaloSmem hs;
+    __shared__ unsigned s_emax;       // largest exponent field in the box
     const int b = blocks[blockIdx.x];
+    if (threadIdx.x == 0) s_emax = 0u;
     record_prologue(hs, lk, b);
     build_halo<double, I>(su, pool, patch, hs.rec, Af, Ac, lk, b, n, sp);
     double* out = F + (size_t)b * n * n * n;
     unsigned long long mb = 0;        // max |f*| as a bit pattern
     if constexpr (NC != 0) {
         // Fixed block size: one thread per interior (y, z) row walking x, the
-        // row's x neighbours kept in registers (same sums, same order)
+        // row's x neighbours kept in registers.
         const int H = sp.H, Hp = sp.H2, H3p = sp.H3p;
+        if constexpr (M == 4) {
+            // f* = (6 f + the sum of the 6 face neighbours) / 12 with the sum
+            // exact in 64-bit fixed point (weights 6 and 1: at most 2^4 in
+            // all), rounded once to double and scaled by 2^-s / 12; boxes
+            // box_to_fixed() turns down take the FP64 sums below.
+            constexpr int G = 4;
+            const int E = box_to_fixed<NC, G>(su, sp, &s_emax);
+            if (E >= 0) {
+                const double sc = (1.0 / 12.0) * __longlong_as_double((long long)(E + G - 1084 + 1023) << 52);
+                for (int r = threadIdx.x; r < NC * NC; r += blockDim.x) {
+                    const int z = r / NC, y = r - z * NC;
+                    const int Y = y + 1, Z = z + 1;
+                    auto rowb = [&](int dy, int dz) {
+                        const int YY = Y + dy, ZZ = Z + dz;
+                        return (((ZZ & 1) << 2) | ((YY & 1) << 1)) * H3p + (ZZ >> 1) * Hp + (YY >> 1) * H;
+                    };
+                    const int r00 = rowb(0, 0), rm0 = rowb(-1, 0), rp0 = rowb(1, 0), r0m = rowb(0, -1), r0p = rowb(0, 1);
+                    auto at = [&](int rb, int X) { return __double_as_longlong(su[rb + (X & 1) * H3p + (X >> 1)]); };
+                    long long um = at(r00, 0), uc = at(r00, 1);
+                    double* orow = out + (size_t)r * NC;
+#pragma unroll
+                    for (int X = 1; X <= NC; ++X) {
+                        const long long up = at(r00, X + 1);
+                        const long long S = 6 * uc + (um + up) + (at(rm0, X) + at(rp0, X)) + (at(r0m, X) + at(r0p, X));
+                        const double v = sc * i64_to_double_rn(S);
+                        orow[X - 1] = v;
+                        mb = umax64(mb, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL);
+                        um = uc;
+                        uc = up;
+                    }
+                }
+                bmax_atomic(__longlong_as_double((long long)mb), fmax_out + (lk.prob ? lk.prob[b] : 0));
+                return;
+            }
+        }
         for (int r = threadIdx.x; r < NC * NC; r += blockDim.x) {
             const int z = r / NC, y = r - z * NC;
             const int Y = y + 1, Z = z + 1;

@@ -180,6 +180,27 @@ __global__ void k_convert_check(const double* __restrict__ d_in, float* __restri
 }
 }  // namespace mrp
 
+namespace mrp {
+__global__ void k_fixed_check(const double* __restrict__ u_in, int shb, long long* __restrict__ fx_out,
+                              const long long* __restrict__ i_in, double* __restrict__ d_out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        fx_out[i] = to_fixed(__double_as_longlong(u_in[i]), shb);
+        d_out[i] = i64_to_double_rn(i_in[i]);
+    }
+}
+}  // namespace mrp
+
+extern "C" int mrp_fixed_check(const double* u_in, int32_t shb, int64_t* fx_out, const int64_t* i_in, double* d_out,
+                               int64_t n, void* stream) {
+    if (n < 0 || shb > 0 || (n > 0 && (!u_in || !fx_out || !i_in || !d_out))) return MRP_ERR_INVALID_ARG;
+    if (n == 0) return MRP_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mrp::k_fixed_check<<<grid, 256, 0, (cudaStream_t)stream>>>(u_in, shb, reinterpret_cast<long long*>(fx_out),
+                                                              reinterpret_cast<const long long*>(i_in), d_out,
+                                                              (long long)n);
+    return cudaGetLastError() == cudaSuccess ? MRP_OK : MRP_ERR_CUDA;
+}
+
 extern "C" int mrp_convert_check(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n,
                                  void* stream) {
     if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out))) return MRP_ERR_INVALID_ARG;

@@ -56,6 +56,36 @@ __device__ __forceinline__ float narrow_rn(double d) {
     return (float)d;
 }
 
+// Fixed-point form of a double: trunc(u 2^(shb + 1075)) as a 64-bit integer,
+// the 53-bit significand (hidden bit included; a subnormal's exponent field
+// counts as 1) shifted by (exponent field + shb) and the sign applied.  The
+// caller picks shb so that the left shifts stay small (box_to_fixed: at most
+// 9 - G bits, for every value of the box whose largest exponent field fixed
+// shb).
+__device__ __forceinline__ long long to_fixed(long long bits, int shb) {
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFULL) | (e ? (1ULL << 52) : 0ULL);
+    const int sh = (e ? e : 1) + shb;
+    const unsigned long long a = sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0ULL);
+    return bits < 0 ? -(long long)a : (long long)a;
+}
+
+// (double)v, rounded to nearest with ties to even, with integer operations:
+// |v| is normalised so that its top bit is bit 63, the 53 bits from there are
+// the significand (hidden bit included) and the 11 bits below decide the
+// rounding; a carry out of the significand moves into the exponent.
+__device__ __forceinline__ double i64_to_double_rn(long long v) {
+    const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ULL;
+    unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+    if (a == 0) return 0.0;
+    const int lz = __clzll((long long)a);
+    a <<= lz;
+    unsigned long long keep = a >> 11;
+    const unsigned rem = (unsigned)(a & 0x7FFu);
+    keep += (rem > 0x400u || (rem == 0x400u && (keep & 1ULL))) ? 1ULL : 0ULL;
+    return __longlong_as_double((long long)(sgn | ((((unsigned long long)(1085 - lz)) << 52) + keep)));
+}
+
 // Asynchronous global -> shared copies (cp.async): one element, or 16 bytes;
 // a thread's copies complete at cp_async_wait<N>() (all but its N most recent
 // committed groups), and are visible to the CTA after the next barrier.

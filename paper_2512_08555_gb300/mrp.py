@@ -26,7 +26,7 @@ EXPORTED = ["mrp_create", "mrp_solve", "mrp_solve_adjoint", "mrp_destroy", "mrp_
             "mrp_level_count", "mrp_level_info", "mrp_field_copy", "mrp_step", "mrp_lgf_extent",
             "mrp_lgf_copy", "mrp_fft_shape", "mrp_profile_enable", "mrp_profile_read",
             "mrp_coarse_solve_noalloc", "mrp_adjoint_len", "mrp_adjoint_op", "mrp_solve_graph",
-            "mrp_solve_host", "mrp_fma_peak", "mrp_convert_check"]
+            "mrp_solve_host", "mrp_fma_peak", "mrp_convert_check", "mrp_fixed_check"]
 ADJ_OPS = {"cycle_T": 0, "res_T": 1, "out_T": 2, "rhs_T": 3}
 PHASES = ["ghost", "smooth", "residual", "restrict", "coarse_fft", "prolong", "norm", "other"]
 PHASES16 = [p + "_f64" for p in PHASES] + [p + "_f32" for p in PHASES]
@@ -93,6 +93,7 @@ def load_library(path=LIB_PATH):
     lib.mrp_solve_host.argtypes = [P, P, P, P, C.POINTER(Stats)]
     lib.mrp_fma_peak.argtypes = [I32, C.POINTER(D), P]
     lib.mrp_convert_check.argtypes = [P, P, P, P, I64, P]
+    lib.mrp_fixed_check.argtypes = [P, I32, P, P, P, I64, P]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or C.c_int
     lib.mrp_error_string.restype = C.c_char_p
@@ -348,6 +349,20 @@ def convert_check(d_in, f_in, stream=None):
                                  C.c_void_p(d_out.data_ptr()), d_in.numel(), _stream_ptr(stream)), "mrp_convert_check")
     torch.cuda.current_stream().synchronize()
     return f_out, d_out
+
+
+def fixed_check(u_in, shb, i_in, stream=None):
+    """The leaf residual's fixed-point conversions (``mrp_fixed_check``): (int64 trunc(u_in 2^(shb+1075)),
+    float64 of i_in)."""
+    import torch
+    lib = load_library()
+    fx_out = torch.empty_like(u_in, dtype=torch.int64)
+    d_out = torch.empty_like(i_in, dtype=torch.float64)
+    _check(lib.mrp_fixed_check(C.c_void_p(u_in.data_ptr()), int(shb), C.c_void_p(fx_out.data_ptr()),
+                               C.c_void_p(i_in.data_ptr()), C.c_void_p(d_out.data_ptr()), u_in.numel(),
+                               _stream_ptr(stream)), "mrp_fixed_check")
+    torch.cuda.current_stream().synchronize()
+    return fx_out, d_out
 
 
 def poisson_solve(solver, f):

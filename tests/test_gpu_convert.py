@@ -69,3 +69,40 @@ def test_narrow_and_widen_match_ieee():
         f_out, d_out = convert_check(torch.from_numpy(d).cuda(), torch.from_numpy(f).cuda())
         _same_bits(f_out.cpu().numpy(), d.astype(np.float32))
         _same_bits(d_out.cpu().numpy(), f.astype(np.float64))
+
+
+def test_fixed_point_conversions():
+    """The leaf residual's fixed-point form trunc(u 2^(shb+1075)) and its int64 -> double rounding.
+
+    For a box whose largest exponent field is E the residual kernel takes
+    shb = 9 - G - E (G = 6 for orders 2 and 4, 8 for order 6); numpy's ldexp is
+    exact at these scales (results below one truncate to zero either way) and
+    its int64 -> float64 cast rounds to nearest, ties to even.
+    """
+    from paper_2512_08555_gb300.mrp import fixed_check
+    rng = np.random.default_rng(11)
+    n = 60000
+    for G in (6, 8):
+        for E in (128, 700, 1023, 1030, 1900):
+            shb = 9 - G - E
+            top = 2.0 ** (E - 1022)                  # every |u| of the box lies below it
+            u = rng.uniform(-1.0, 1.0, n) * top * np.exp2(-rng.integers(0, 90, n).astype(np.float64))
+            u = np.concatenate([u, [0.0, -0.0, np.nextafter(top, 0.0), -np.nextafter(top, 0.0), top / 2, -top / 2,
+                                    5e-324, -5e-324, 2.2250738585072014e-308]])
+            i = np.concatenate([rng.integers(-(1 << 62), 1 << 62, n // 2, dtype=np.int64),
+                                rng.integers(-(1 << 40), 1 << 40, n // 4, dtype=np.int64),
+                                rng.integers(-1000, 1000, n // 4, dtype=np.int64)])
+            # exact ties and near-ties of the bits below a 53-bit significand
+            k = rng.integers(1, 9, 64)
+            base = (rng.integers(1 << 52, 1 << 53, 64, dtype=np.int64) << k)
+            ties = np.concatenate([base + (np.int64(1) << (k - 1)), base + (np.int64(1) << (k - 1)) - 1,
+                                   base + (np.int64(1) << (k - 1)) + 1, -(base + (np.int64(1) << (k - 1)))])
+            i = np.concatenate([i, ties, np.array([0, 1, -1, (1 << 53) + 1, -(1 << 63), (1 << 63) - 1],
+                                                  dtype=np.int64)])
+            m = max(u.size, i.size)
+            u = np.resize(u, m)
+            i = np.resize(i, m)
+            fx, d = fixed_check(torch.from_numpy(u).cuda(), shb, torch.from_numpy(i).cuda())
+            want = np.trunc(np.ldexp(u, shb + 1075)).astype(np.int64)
+            assert np.array_equal(fx.cpu().numpy(), want), (G, E)
+            _same_bits(d.cpu().numpy(), i.astype(np.float64))
