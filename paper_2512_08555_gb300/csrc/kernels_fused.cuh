@@ -386,7 +386,7 @@ __device__ __forceinline__ void load_rhs(T* __restrict__ fs, const T* __restrict
 // Issues the cp.async copies of block b's box (step 1 below) and, for a block
 // with interpolated regions, of its coarse patch (step 2a) without committing
 // them; the caller commits, waits and synchronises before halo_interpolate.
-template <typename T, int I, bool INTERP = true>
+template <typename T, int I, bool INTERP = true, bool OWN = false>
 __device__ __forceinline__ void halo_issue(T* __restrict__ su, T* __restrict__ patch, const int* __restrict__ rec,
                                            const T* __restrict__ Uk, const T* __restrict__ Uc, const LevelView& lk,
                                            int b, int n, const Split& sp) {
@@ -403,6 +403,7 @@ __device__ __forceinline__ void halo_issue(T* __restrict__ su, T* __restrict__ p
         T* dcol = su + ((((Y & 1) << 1) | (X & 1)) * H3p + (Y >> 1) * H + (X >> 1));
 #pragma unroll
         for (int rz = -1; rz <= 1; ++rz) {
+            if (OWN && (rx | ry | rz) == 0) continue;     // the block's own interior: issued by own_box_issue()
             const int j = snbr[dir27(rx, ry, rz)];
             if (j == NBR_MISSING) continue;
             // source column: same-level block j (shifted into its own box), or this block's stored ghost layer
@@ -609,11 +610,11 @@ __device__ __forceinline__ void halo_interpolate(T* __restrict__ su, T* __restri
     __syncthreads();
 }
 
-template <typename T, int I, bool INTERP = true>
+template <typename T, int I, bool INTERP = true, bool OWN = false>
 __device__ __forceinline__ void build_halo(T* __restrict__ su, T* __restrict__ pool, T* __restrict__ patch,
                                            const int* __restrict__ rec, const T* __restrict__ Uk, const T* __restrict__ Uc,
                                            const LevelView& lk, int b, int n, const Split& sp) {
-    halo_issue<T, I, INTERP>(su, patch, rec, Uk, Uc, lk, b, n, sp);
+    halo_issue<T, I, INTERP, OWN>(su, patch, rec, Uk, Uc, lk, b, n, sp);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
@@ -646,11 +647,42 @@ __host__ __device__ inline size_t fused_smem(int n, int I, int fmode = 0) {
 }
 
 
-// Prologue of the fused kernels that stage no right-hand side: the block's
-// record, complete and visible on return.
-__device__ __forceinline__ void record_prologue(HaloSmem& hs, const LevelView& lk, int b) {
+// The copies of block b's own interior into its split box (the part of the
+// box that needs no record: z = 1..n of its own columns), one thread per
+// (x, y) column walking z; not committed.
+template <typename T>
+__device__ __forceinline__ void own_box_issue(T* __restrict__ su, const T* __restrict__ Uk, int b, int n, const Split& sp) {
+    const int S = n + 2, S2 = S * S, h = n >> 1;
+    const T* Ub = Uk + (size_t)b * S2 * S;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int y = c / n, x = c - y * n;
+        const int X = x + 1, Y = y + 1;
+        T* dcol = su + ((((Y & 1) << 1) | (X & 1)) * sp.H3p + (Y >> 1) * sp.H + (X >> 1));
+        const T* col = Ub + (Y * S + X);
+        for (int m = 0; m < h; ++m) {
+            cp_async_el(dcol + 4 * sp.H3p + m * sp.H2, col + (size_t)(2 * m + 1) * S2);
+            cp_async_el(dcol + (m + 1) * sp.H2, col + (size_t)(2 * m + 2) * S2);
+        }
+    }
+}
+
+// Prologue of the fused kernels: the block's record, complete and visible on
+// return.  With OWN, the copy of the block's own interior from Uk, which
+// needs no record, is in flight behind it (build_halo<..., OWN = true> copies
+// the rest and waits for both), so that the record's memory round trip
+// overlaps the largest copy.  FP64 boxes take OWN; FP32 boxes measured
+// slightly slower with it and keep the record first.
+template <typename T, bool OWN = (sizeof(T) == 8)>
+__device__ __forceinline__ void record_prologue_own(HaloSmem& hs, const LevelView& lk, int b, T* __restrict__ su,
+                                                    const T* __restrict__ Uk, int n, const Split& sp) {
     load_record(hs, lk, b);
-    cp_async_wait<0>();
+    if constexpr (OWN) {
+        own_box_issue(su, Uk, b, n, sp);
+        cp_async_commit();
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
     __syncthreads();
 }
 
@@ -724,13 +756,13 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    record_prologue(hs, lk, b);
+    record_prologue_own(hs, lk, b, su, Uin, n, sp);
     // the right-hand side copy overlaps the box copy (build_halo waits for
     // both), except on interface blocks in fmode 1, where it follows the
     // ghost layer
     const bool early = fmode == 2 || (fmode == 1 && hs.rec[REC_NREG] == 0);
     if (early) load_rhs(fs, F, b, n);
-    build_halo<T, I>(su, pool, patch, hs.rec, Uin, Uc, lk, b, n, sp);
+    build_halo<T, I, true, sizeof(T) == 8>(su, pool, patch, hs.rec, Uin, Uc, lk, b, n, sp);
     if (fmode == 1 && !early) {
         load_rhs(fs, F, b, n);
         cp_async_wait<0>();
@@ -848,7 +880,7 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
     Cset cs;
     cset_init(cs, n >> 1);
     const int b = order ? order[blockIdx.x] : blockIdx.x;
-    record_prologue(hs, lk, b);
+    record_prologue_own(hs, lk, b, su, U, n, sp);
     const size_t n3 = (size_t)n * n * n;
     if constexpr (NC != 0 && sizeof(T) == 4) {
         // F staged in shared memory in the colour split (as the smoother's),
@@ -860,7 +892,7 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
         T* fs = pool;
         const bool early = hs.rec[REC_NREG] == 0;
         if (early) load_rhs(fs, F, b, n);
-        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+        build_halo<T, I, true, sizeof(T) == 8>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
         if (!early) {
             load_rhs(fs, F, b, n);
             cp_async_wait<0>();
@@ -914,7 +946,7 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
             }
         }
     } else {
-        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+        build_halo<T, I, true, sizeof(T) == 8>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
 #pragma unroll
@@ -962,7 +994,7 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
         }
         return;
     }
-    record_prologue(hs, lk, b);
+    record_prologue_own(hs, lk, b, su, U, n, sp);
     if constexpr (NC != 0 && sizeof(T) == 4) {
         // F staged in shared memory over the interpolation scratch as in the
         // residual kernel, updated in place and written back by columns;
@@ -970,7 +1002,7 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
         T* fs = pool;
         const bool early = hs.rec[REC_NREG] == 0;
         if (early) load_rhs(fs, F, b, n);
-        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+        build_halo<T, I, true, sizeof(T) == 8>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
         if (!early) {
             load_rhs(fs, F, b, n);
             cp_async_wait<0>();
@@ -1009,7 +1041,7 @@ __global__ void __launch_bounds__(512) k_fas_fused(T* __restrict__ F, T* __restr
             }
         }
     } else {
-        build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+        build_halo<T, I, true, sizeof(T) == 8>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
 #pragma unroll
@@ -1089,8 +1121,8 @@ __global__ void __launch_bounds__(512) k_leafres_fused(float* __restrict__ R, co
     cset_init(cs, n >> 1);
     const int b = blocks[blockIdx.x];
     if (threadIdx.x == 0) s_emax = 0u;
-    record_prologue(hs, lk, b);
-    build_halo<double, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+    record_prologue_own(hs, lk, b, su, U, n, sp);
+    build_halo<double, I, true, true>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     const size_t n3 = (size_t)n * n * n;
     unsigned long long mb = 0;        // max |r| as a bit pattern
     if constexpr (NC != 0) {
@@ -1249,8 +1281,8 @@ __global__ void __launch_bounds__(512) k_rhs_fused(double* __restrict__ F, const
     __shared__ unsigned s_emax;       // largest exponent field in the box
     const int b = blocks[blockIdx.x];
     if (threadIdx.x == 0) s_emax = 0u;
-    record_prologue(hs, lk, b);
-    build_halo<double, I>(su, pool, patch, hs.rec, Af, Ac, lk, b, n, sp);
+    record_prologue_own(hs, lk, b, su, Af, n, sp);
+    build_halo<double, I, true, true>(su, pool, patch, hs.rec, Af, Ac, lk, b, n, sp);
     double* out = F + (size_t)b * n * n * n;
     unsigned long long mb = 0;        // max |f*| as a bit pattern
     if constexpr (NC != 0) {
@@ -1349,8 +1381,8 @@ __global__ void __launch_bounds__(512) k_halo_dump(T* __restrict__ U, const T* _
     __shared__ HaloSmem hs;
     const int S = n + 2, S3 = S * S * S;
     const int b = blockIdx.x;
-    record_prologue(hs, lk, b);
-    build_halo<T, I>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+    record_prologue_own(hs, lk, b, su, U, n, sp);
+    build_halo<T, I, true, sizeof(T) == 8>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
     for (int t = threadIdx.x; t < S3 - n * n * n; t += blockDim.x) {
         int x, y, z;
         shell_coords(t, S, x, y, z);
