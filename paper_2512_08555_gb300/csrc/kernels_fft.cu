@@ -251,6 +251,62 @@ template <> __device__ __forceinline__ double2 unit_root<16>(int m) {
     }
 }
 
+template <> __device__ __forceinline__ double2 unit_root<18>(int m) {
+    switch (m) {
+        case 0: return double2{1.0, 0.0};
+        case 1: return double2{0.939692620785908384054, 0.342020143325668733044};
+        case 2: return double2{0.766044443118978035202, 0.642787609686539326323};
+        case 3: return double2{0.5, 0.866025403784438646764};
+        case 4: return double2{0.173648177666930348852, 0.984807753012208059367};
+        case 5: return double2{-0.173648177666930348852, 0.984807753012208059367};
+        case 6: return double2{-0.5, 0.866025403784438646764};
+        case 7: return double2{-0.766044443118978035202, 0.642787609686539326323};
+        case 8: return double2{-0.939692620785908384054, 0.342020143325668733044};
+        case 9: return double2{-1.0, 0.0};
+        case 10: return double2{-0.939692620785908384054, -0.342020143325668733044};
+        case 11: return double2{-0.766044443118978035202, -0.642787609686539326323};
+        case 12: return double2{-0.5, -0.866025403784438646764};
+        case 13: return double2{-0.173648177666930348852, -0.984807753012208059367};
+        case 14: return double2{0.173648177666930348852, -0.984807753012208059367};
+        case 15: return double2{0.5, -0.866025403784438646764};
+        case 16: return double2{0.766044443118978035202, -0.642787609686539326323};
+        case 17: return double2{0.939692620785908384054, -0.342020143325668733044};
+        default: return double2{1.0, 0.0};
+    }
+}
+template <> __device__ __forceinline__ double2 unit_root<27>(int m) {
+    switch (m) {
+        case 0: return double2{1.0, 0.0};
+        case 1: return double2{0.973044870579823838833, 0.23061587074244017845};
+        case 2: return double2{0.893632640323412248193, 0.448799180200462172785};
+        case 3: return double2{0.766044443118978035202, 0.642787609686539326323};
+        case 4: return double2{0.597158591702786164852, 0.802123192755043785083};
+        case 5: return double2{0.396079766039156823696, 0.918216106880274014759};
+        case 6: return double2{0.173648177666930348852, 0.984807753012208059367};
+        case 7: return double2{-0.058144828910475828539, 0.998308158271268208048};
+        case 8: return double2{-0.286803232711090253103, 0.957989512315488874437};
+        case 9: return double2{-0.5, 0.866025403784438646764};
+        case 10: return double2{-0.68624163786873358573, 0.727373641573048695987};
+        case 11: return double2{-0.835487811412936419654, 0.549508978070806035263};
+        case 12: return double2{-0.939692620785908384054, 0.342020143325668733044};
+        case 13: return double2{-0.993238357741942988548, 0.116092914125230229676};
+        case 14: return double2{-0.993238357741942988548, -0.116092914125230229676};
+        case 15: return double2{-0.939692620785908384054, -0.342020143325668733044};
+        case 16: return double2{-0.835487811412936419654, -0.549508978070806035263};
+        case 17: return double2{-0.68624163786873358573, -0.727373641573048695987};
+        case 18: return double2{-0.5, -0.866025403784438646764};
+        case 19: return double2{-0.286803232711090253103, -0.957989512315488874437};
+        case 20: return double2{-0.058144828910475828539, -0.998308158271268208048};
+        case 21: return double2{0.173648177666930348852, -0.984807753012208059367};
+        case 22: return double2{0.396079766039156823696, -0.918216106880274014759};
+        case 23: return double2{0.597158591702786164852, -0.802123192755043785083};
+        case 24: return double2{0.766044443118978035202, -0.642787609686539326323};
+        case 25: return double2{0.893632640323412248193, -0.448799180200462172785};
+        case 26: return double2{0.973044870579823838833, -0.23061587074244017845};
+        default: return double2{1.0, 0.0};
+    }
+}
+
 template <int A, int B, typename R> struct DftAB {
     template <typename C> static __device__ __forceinline__ void run(C* v, int sign) {
         constexpr int RR = A * B;
@@ -295,6 +351,8 @@ template <typename R> struct Dft<9, R> : DftAB<3, 3, R> {};
 template <typename R> struct Dft<14, R> : DftAB<2, 7, R> {};
 template <typename R> struct Dft<15, R> : DftAB<3, 5, R> {};
 template <typename R> struct Dft<16, R> : DftAB<4, 4, R> {};
+template <typename R> struct Dft<18, R> : DftAB<2, 9, R> {};
+template <typename R> struct Dft<27, R> : DftAB<3, 9, R> {};
 
 // One Stockham stage of radix RAD: butterfly j reads a[j + r P/RAD], twiddles
 // by w^{(j mod Ns) r P/(Ns RAD)}, applies the RAD-point DFT and writes
@@ -337,13 +395,108 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ a, C* __res
 template <typename R> __host__ __device__ constexpr int fft_tx() { return sizeof(R) == 4 ? 32 : 64; }
 template <typename R> __host__ __device__ constexpr int fft_ly() { return sizeof(R) == 4 ? 8 : 4; }
 
+// Four-step transform of one line of length P = P1 P2 (P1, P2 <= 32; one
+// warp per line).  With n = P2 n1 + n2 and k = k1 + P1 k2,
+//   X[k1 + P1 k2] = sum_n2 w_P2^(n2 k2) w_P^(n2 k1) sum_n1 w_P1^(n1 k1) x[P2 n1 + n2],
+// w_m = exp(sign 2 pi i / m).  Lane n2 < P2 forms the inner P1-point
+// transform in registers and writes it, twiddled, to b[k1 P2 + n2]; after a
+// warp barrier lane k1 < P1 forms the outer P2-point transform of
+// b[k1 P2 + ...] and writes X in natural order to a.  Two shared-memory
+// round trips in all, where a Stockham plan takes one per radix stage.
+// a[nz ..) is zero and not read.  Returns a.
+template <int P1, int P2, typename R, typename C>
+__device__ C* fft_4step(C* a, C* b, const FftDev<R>& L, int sign, int nz) {
+    const int t = threadIdx.x;
+    if (t < P2) {
+        C v[P1];
+#pragma unroll
+        for (int n1 = 0; n1 < P1; ++n1) {
+            const int i = P2 * n1 + t;
+            v[n1] = i < nz ? a[i] : C{R(0), R(0)};
+        }
+        Dft<P1, R>::run(v, sign);
+        b[t] = v[0];
+#pragma unroll
+        for (int k1 = 1; k1 < P1; ++k1) b[k1 * P2 + t] = cmul(v[k1], twiddle(L.tw, t * k1, sign));
+    }
+    __syncwarp();
+    if (t < P1) {
+        C u[P2];
+#pragma unroll
+        for (int n2 = 0; n2 < P2; ++n2) u[n2] = b[t * P2 + n2];
+        Dft<P2, R>::run(u, sign);
+#pragma unroll
+        for (int k2 = 0; k2 < P2; ++k2) a[t + P1 * k2] = u[k2];
+    }
+    __syncwarp();
+    return a;
+}
+
 // One line of length P in a[], b[] as scratch (a[nz ..) known to be zero);
 // the fft_tx<R>() threads with the same threadIdx.y cooperate.  With one warp per line the stages are
 // separated by warp barriers, else by CTA barriers (every thread of the CTA
 // must then call this).  Returns the buffer that holds the result (Stockham
 // autosort, mixed radix).
-template <typename R, bool CMP, typename C>
+// The z pass of the convolution on a four-step line: forward transform,
+// product with the Green's function spectrum (lane k1 < P1 brings its
+// values gk[k2] = G(k1 + P1 k2) in registers), inverse transform, with
+// the spectrum kept in registers between the two.  The forward transform
+// leaves X[k1 + P1 k2] in lane k1 (k2 = 0 .. P2-1), which is the inner
+// transform's input of the inverse taken as P = P2 P1 (index P1 n1' + n2',
+// lane n2' = k1): that lane multiplies by gk, transforms over n1', twiddles
+// and writes to a[k1' P1 + n2']; after a warp barrier lane k1' < P2 forms
+// the outer P1-point transform and writes the result in natural order to b.
+// Three shared-memory round trips instead of four (and of two per radix
+// stage in a Stockham plan).  Returns b.
+template <int P1, int P2, typename R, typename C>
+__device__ C* fft_conv_4step(C* a, C* b, const FftDev<R>& L, int nz, const R (&gk)[P2]) {
+    const int t = threadIdx.x;
+    if (t < P2) {
+        C v[P1];
+#pragma unroll
+        for (int n1 = 0; n1 < P1; ++n1) {
+            const int i = P2 * n1 + t;
+            v[n1] = i < nz ? a[i] : C{R(0), R(0)};
+        }
+        Dft<P1, R>::run(v, -1);
+        b[t] = v[0];
+#pragma unroll
+        for (int k1 = 1; k1 < P1; ++k1) b[k1 * P2 + t] = cmul(v[k1], twiddle(L.tw, t * k1, -1));
+    }
+    __syncwarp();
+    if (t < P1) {
+        C u[P2];
+#pragma unroll
+        for (int n2 = 0; n2 < P2; ++n2) u[n2] = b[t * P2 + n2];
+        Dft<P2, R>::run(u, -1);
+#pragma unroll
+        for (int k2 = 0; k2 < P2; ++k2) {
+            u[k2] = C{u[k2].x * gk[k2], u[k2].y * gk[k2]};
+        }
+        Dft<P2, R>::run(u, +1);
+        a[t] = u[0];
+#pragma unroll
+        for (int k = 1; k < P2; ++k) a[k * P1 + t] = cmul(u[k], twiddle(L.tw, t * k, +1));
+    }
+    __syncwarp();
+    if (t < P2) {
+        C w[P1];
+#pragma unroll
+        for (int n = 0; n < P1; ++n) w[n] = a[t * P1 + n];
+        Dft<P1, R>::run(w, +1);
+#pragma unroll
+        for (int k = 0; k < P1; ++k) b[t + P2 * k] = w[k];
+    }
+    __syncwarp();
+    return b;
+}
+
+// PLAN: 0 a Stockham plan of prime radices (and 4), 1 one with composite
+// radices, P1 * 100 + P2 the four-step transform of P = P1 P2 (FP32 lines).
+template <typename R, int PLAN, typename C>
 __device__ C* fft_line(C* a, C* b, const FftDev<R>& L, int sign, int nz) {
+    if constexpr (PLAN >= 100) return fft_4step<PLAN / 100, PLAN % 100, R>(a, b, L, sign, nz);
+    constexpr bool CMP = PLAN == 1;
     const int P = L.P;
     constexpr int MS = MAX_RADIX_STAGES;
     for (int st = 0; st < L.nrad; ++st) {
@@ -440,12 +593,37 @@ struct Geo {
 // Padded index of a lattice coordinate i in [-P, 2P) (every range here lies inside).
 __device__ __forceinline__ int pidx(int i, int P) { return i < 0 ? i + P : (i >= P ? i - P : i); }
 
+// Copies elements e = 0 .. n-1 of the CTA's lines from global into shared
+// memory (value src(e), stored by dst(e, v)) with B loads of a thread in
+// flight before their stores: the passes are bound by memory latency, and
+// with a run-time loop bound one load at a time would be in flight.
+// The elements are spread over the whole CTA (WARP = false) or over the
+// threads of one line (WARP = true: threadIdx.x).
+template <int B, typename C, bool WARP = false, typename S, typename D>
+__device__ __forceinline__ void gather_lines(int n, const S& src, const D& dst) {
+    const int tid = WARP ? (int)threadIdx.x : (int)(threadIdx.y * blockDim.x + threadIdx.x);
+    const int nth = WARP ? (int)blockDim.x : (int)(blockDim.x * blockDim.y);
+    for (int e0 = tid; e0 < n; e0 += B * nth) {
+        C v[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int e = e0 + i * nth;
+            v[i] = e < n ? src(e) : C{};
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int e = e0 + i * nth;
+            if (e < n) dst(e, v[i]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- pass A (x, real -> half spectrum)
 // lines: input (y, z) range; x input range.  Each warp transforms two real
 // lines at once as one complex line z = a + i b; with Z = FFT(z) and
 // Z' = conj(Z[(P - k) mod P]), the halves are A = (Z + Z') / 2 and
 // B = (Z - Z') / (2 i).
-template <typename R, bool CMP>
+template <typename R, int PLAN>
 __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ src, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -470,22 +648,23 @@ __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __res
     for (int h = 0; h < 2; ++h) {
         if (!live[h]) continue;
         const int y = g.in_lo[1] + ty[h], z = g.in_lo[2] + tz[h];
-        for (int tx = threadIdx.x; tx < g.in_n[0]; tx += blockDim.x) {
-            const int x = g.in_lo[0] + tx;
-            R v;
-            if (g.dense_in) {
-                v = src[((size_t)tz[h] * g.in_n[1] + ty[h]) * g.in_n[0] + tx];
-            } else {
+        gather_lines<8, R, true>(
+            g.in_n[0],
+            [&](int tx) {
+                if (g.dense_in) return src[((size_t)tz[h] * g.in_n[1] + ty[h]) * g.in_n[0] + tx];
+                const int x = g.in_lo[0] + tx;
                 const int bx = x / g.n, lx = x % g.n, by = y / g.n, ly = y % g.n, bz = z / g.n, lz = z % g.n;
                 const int blk = (bz * g.nby + by) * g.nbx + bx;
-                v = src[(size_t)blk * g.n * g.n * g.n + (lz * g.n + ly) * g.n + lx];
-            }
-            if (h == 0) a[pidx(x, L.P)].x = v;
-            else a[pidx(x, L.P)].y = v;
-        }
+                return src[(size_t)blk * g.n * g.n * g.n + (lz * g.n + ly) * g.n + lx];
+            },
+            [&](int tx, R v) {
+                const int x = g.in_lo[0] + tx;
+                if (h == 0) a[pidx(x, L.P)].x = v;
+                else a[pidx(x, L.P)].y = v;
+            });
     }
     __syncthreads();
-    C* r = fft_line<R, CMP>(a, b, L, -1, g.in_lo[0] == 0 ? g.in_n[0] : L.P);
+    C* r = fft_line<R, PLAN>(a, b, L, -1, g.in_lo[0] == 0 ? g.in_n[0] : L.P);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         if (!live[h]) continue;
@@ -505,7 +684,7 @@ __global__ void k_fft_x_fwd(typename Cx<R>::T* __restrict__ spec, const R* __res
 // a warp touches whole sectors; the transforms themselves run per line.
 
 // ---------------------------------------------------------------- pass B (y, forward), lines (input z, kx)
-template <typename R, bool CMP>
+template <typename R, int PLAN>
 __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -519,14 +698,15 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
     C* b = a + P;
     for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
     __syncthreads();
-    for (int e = tid; e < fft_ly<R>() * g.in_n[1]; e += nth) {
-        const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
-        if (kx0 + ly >= g.Kx) continue;
-        const int j = pidx(g.in_lo[1] + t, g.Py);
-        sm[ly * P2 + j] = spec[((size_t)zi * g.Py + j) * g.Kx + kx0 + ly];
-    }
+    gather_lines<8, C>(
+        fft_ly<R>() * g.in_n[1],
+        [&](int e) {
+            const int ly = e % fft_ly<R>(), j = pidx(g.in_lo[1] + e / fft_ly<R>(), g.Py);
+            return kx0 + ly < g.Kx ? spec[((size_t)zi * g.Py + j) * g.Kx + kx0 + ly] : C{R(0), R(0)};
+        },
+        [&](int e, C v) { sm[(e % fft_ly<R>()) * P2 + pidx(g.in_lo[1] + e / fft_ly<R>(), g.Py)] = v; });
     __syncthreads();
-    const int roff = (int)(fft_line<R, CMP>(a, b, L, -1, g.in_lo[1] == 0 ? g.in_n[1] : P) - a);
+    const int roff = (int)(fft_line<R, PLAN>(a, b, L, -1, g.in_lo[1] == 0 ? g.in_n[1] : P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * P; e += nth) {
         const int ly = e % fft_ly<R>(), y = e / fft_ly<R>();
@@ -535,7 +715,7 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
 }
 
 // ---------------------------------------------------------------- pass C (z forward, x G-hat, z inverse), lines (ky, kx)
-template <typename R, bool CMP>
+template <typename R, int PLAN>
 __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -551,12 +731,13 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
     const bool live = kx < g.Kx;
     for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
     __syncthreads();
-    for (int e = tid; e < fft_ly<R>() * g.in_n[2]; e += nth) {
-        const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
-        if (kx0 + ly >= g.Kx) continue;
-        const int j = pidx(g.in_lo[2] + t, g.Pz);
-        sm[ly * P2 + j] = spec[((size_t)j * g.Py + ky) * g.Kx + kx0 + ly];
-    }
+    gather_lines<8, C>(
+        fft_ly<R>() * g.in_n[2],
+        [&](int e) {
+            const int ly = e % fft_ly<R>(), j = pidx(g.in_lo[2] + e / fft_ly<R>(), g.Pz);
+            return kx0 + ly < g.Kx ? spec[((size_t)j * g.Py + ky) * g.Kx + kx0 + ly] : C{R(0), R(0)};
+        },
+        [&](int e, C v) { sm[(e % fft_ly<R>()) * P2 + pidx(g.in_lo[2] + e / fft_ly<R>(), g.Pz)] = v; });
     // the line's G-hat values, fetched now so that their latency overlaps the
     // input's (the first GPRE per thread in registers, the rest later)
     constexpr int GPRE = sizeof(R) == 4 ? 8 : 4;
@@ -565,6 +746,17 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
         const int fz = kz <= g.Pz - kz ? kz : g.Pz - kz;
         return live ? ghat[((size_t)fz * g.Ky + fy) * g.Kx + kx] : R(0);
     };
+    int qoff;
+    if constexpr (PLAN >= 100) {
+        // the G-hat values of lane k1 (k = k1 + P1 k2), fetched with the input
+        constexpr int P1 = PLAN / 100, P2 = PLAN % 100;
+        R gk[P2];
+#pragma unroll
+        for (int k2 = 0; k2 < P2; ++k2) gk[k2] = threadIdx.x < P1 ? ghat_at(threadIdx.x + P1 * k2) : R(0);
+        __syncthreads();
+        qoff = (int)(fft_conv_4step<P1, P2, R>(a, b, L, g.in_lo[2] == 0 ? g.in_n[2] : P, gk) - a);
+        __syncthreads();
+    } else {
     R gpre[GPRE];
 #pragma unroll
     for (int m = 0; m < GPRE; ++m) {
@@ -572,7 +764,7 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
         gpre[m] = kz < P ? ghat_at(kz) : R(0);
     }
     __syncthreads();
-    C* r = fft_line<R, CMP>(a, b, L, -1, g.in_lo[2] == 0 ? g.in_n[2] : P);
+    C* r = fft_line<R, PLAN>(a, b, L, -1, g.in_lo[2] == 0 ? g.in_n[2] : P);
 #pragma unroll
     for (int m = 0; m < GPRE; ++m) {
         const int kz = threadIdx.x + m * blockDim.x;
@@ -584,8 +776,9 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
     }
     __syncthreads();
     C* other = (r == a) ? b : a;
-    const int qoff = (int)(fft_line<R, CMP>(r, other, L, +1, P) - a);
+    qoff = (int)(fft_line<R, PLAN>(r, other, L, +1, P) - a);
     __syncthreads();
+    }
     for (int e = tid; e < fft_ly<R>() * g.out_n[2]; e += nth) {
         const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
         if (kx0 + ly >= g.Kx) continue;
@@ -595,7 +788,7 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
 }
 
 // ---------------------------------------------------------------- pass B' (y inverse), lines (output z, kx)
-template <typename R, bool CMP>
+template <typename R, int PLAN>
 __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -607,12 +800,15 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     C* a = sm + threadIdx.y * P2;
     C* b = a + P;
-    for (int e = tid; e < fft_ly<R>() * P; e += nth) {
-        const int ly = e % fft_ly<R>(), y = e / fft_ly<R>();
-        sm[ly * P2 + y] = kx0 + ly < g.Kx ? spec[((size_t)z * g.Py + y) * g.Kx + kx0 + ly] : C{R(0), R(0)};
-    }
+    gather_lines<8, C>(
+        fft_ly<R>() * P,
+        [&](int e) {
+            const int ly = e % fft_ly<R>(), y = e / fft_ly<R>();
+            return kx0 + ly < g.Kx ? spec[((size_t)z * g.Py + y) * g.Kx + kx0 + ly] : C{R(0), R(0)};
+        },
+        [&](int e, C v) { sm[(e % fft_ly<R>()) * P2 + e / fft_ly<R>()] = v; });
     __syncthreads();
-    const int roff = (int)(fft_line<R, CMP>(a, b, L, +1, P) - a);
+    const int roff = (int)(fft_line<R, PLAN>(a, b, L, +1, P) - a);
     __syncthreads();
     for (int e = tid; e < fft_ly<R>() * g.out_n[1]; e += nth) {
         const int ly = e % fft_ly<R>(), t = e / fft_ly<R>();
@@ -628,7 +824,7 @@ __global__ void k_fft_y_inv(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
 // real outputs.  Block mode writes node (x, y, z) into every level-0 block
 // whose (n+2)^3 box holds it (interior or ghost layer); dense mode writes the
 // dense output range.
-template <typename R, bool CMP>
+template <typename R, int PLAN>
 __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __restrict__ spec, Geo g, FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
@@ -649,20 +845,23 @@ __global__ void k_fft_x_inv(R* __restrict__ dst, const typename Cx<R>::T* __rest
         oz[h] = live[h] ? line / g.out_n[1] : 0;
         src[h] = spec + ((size_t)pidx(g.out_lo[2] + oz[h], g.Pz) * g.Py + pidx(g.out_lo[1] + oy[h], g.Py)) * g.Kx;
     }
-    for (int k = threadIdx.x; k < L.P; k += blockDim.x) {
-        C v[2];
+    gather_lines<8, C, true>(
+        L.P,
+        [&](int k) {
+            C v[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            v[h] = C{R(0), R(0)};
-            if (live[h]) {
-                if (k < g.Kx) v[h] = src[h][k];
-                else { v[h] = src[h][L.P - k]; v[h].y = -v[h].y; }
+            for (int h = 0; h < 2; ++h) {
+                v[h] = C{R(0), R(0)};
+                if (live[h]) {
+                    if (k < g.Kx) v[h] = src[h][k];
+                    else { v[h] = src[h][L.P - k]; v[h].y = -v[h].y; }
+                }
             }
-        }
-        a[k] = C{v[0].x - v[1].y, v[0].y + v[1].x};
-    }
+            return C{v[0].x - v[1].y, v[0].y + v[1].x};
+        },
+        [&](int k, C v) { a[k] = v; });
     __syncthreads();
-    C* r = fft_line<R, CMP>(a, b, L, +1, L.P);
+    C* r = fft_line<R, PLAN>(a, b, L, +1, L.P);
     const int S = g.n + 2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -717,6 +916,18 @@ static bool has_composite(const FftLine<R>& l) {
     return false;
 }
 
+// FP32 line lengths with a four-step build (P1 * 100 + P2, P = P1 P2), else 0:
+// the solver's own level-0 lattice (N0 = 96, P = 196), the 240^3 lattice
+// (P = 486) and a smaller one (P = 144).
+static int fourstep_plan(int P) {
+    switch (P) {
+        case 144: return 916;
+        case 196: return 1414;
+        case 486: return 1827;
+        default: return 0;
+    }
+}
+
 template <typename R>
 static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec, const R* ghat, const R* src, R* dst,
                         cudaStream_t s) {
@@ -728,11 +939,22 @@ static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec,
     const size_t smz = sizeof(C) * (2 * fft_ly<R>() + 1) * g.Pz + FFT_STAGE_BYTES;
     const int kxb = (g.Kx + fft_ly<R>() - 1) / fft_ly<R>();
     const int lx2 = 2 * fft_ly<R>();   // lines per CTA in the x passes (two per warp)
-    // FP32 lines whose plan holds a composite radix take the composite build
+    // FP32 lines take the four-step build where their length has one, else
+    // the composite-radix build where their plan holds a composite radix
     constexpr bool F32 = sizeof(R) == 4;
-#define MRP_FFT_LAUNCH(KERN, LINE, GRID, SM, ...)                                   \
-    if (F32 && has_composite(LINE)) KERN<R, F32><<<GRID, blk, SM, s>>>(__VA_ARGS__); \
-    else KERN<R, false><<<GRID, blk, SM, s>>>(__VA_ARGS__)
+#define MRP_FFT_LAUNCH(KERN, LINE, GRID, SM, ...)                                      \
+    do {                                                                               \
+        if constexpr (F32) {                                                           \
+            const int fs = fourstep_plan(LINE.P);                                      \
+            if (fs == 916) KERN<R, 916><<<GRID, blk, SM, s>>>(__VA_ARGS__);            \
+            else if (fs == 1414) KERN<R, 1414><<<GRID, blk, SM, s>>>(__VA_ARGS__);     \
+            else if (fs == 1827) KERN<R, 1827><<<GRID, blk, SM, s>>>(__VA_ARGS__);     \
+            else if (has_composite(LINE)) KERN<R, 1><<<GRID, blk, SM, s>>>(__VA_ARGS__); \
+            else KERN<R, 0><<<GRID, blk, SM, s>>>(__VA_ARGS__);                        \
+        } else {                                                                       \
+            KERN<R, 0><<<GRID, blk, SM, s>>>(__VA_ARGS__);                             \
+        }                                                                              \
+    } while (0)
     MRP_FFT_LAUNCH(k_fft_x_fwd, Lx, (g.in_n[1] * g.in_n[2] + lx2 - 1) / lx2, smx, spec, src, g, Lx);
     MRP_FFT_LAUNCH(k_fft_y_fwd, Ly, dim3(kxb, g.in_n[2]), smy, spec, g, Ly);
     MRP_FFT_LAUNCH(k_fft_z_conv, Lz, dim3(kxb, g.Py), smz, spec, ghat, g, Lz);
@@ -1093,12 +1315,12 @@ int fft_plan(Handle& h) {
     }
     if (cudaMalloc(&h.spec, sizeof(double2) * ns) != cudaSuccess) return MRP_ERR_OOM;
     const int mx = MAX_DYN_SMEM;
-    const void* kernels[] = {
-        (const void*)k_fft_x_fwd<double, false>, (const void*)k_fft_x_fwd<float, false>, (const void*)k_fft_x_fwd<float, true>,
-        (const void*)k_fft_y_fwd<double, false>, (const void*)k_fft_y_fwd<float, false>, (const void*)k_fft_y_fwd<float, true>,
-        (const void*)k_fft_z_conv<double, false>, (const void*)k_fft_z_conv<float, false>, (const void*)k_fft_z_conv<float, true>,
-        (const void*)k_fft_y_inv<double, false>, (const void*)k_fft_y_inv<float, false>, (const void*)k_fft_y_inv<float, true>,
-        (const void*)k_fft_x_inv<double, false>, (const void*)k_fft_x_inv<float, false>, (const void*)k_fft_x_inv<float, true>};
+#define MRP_FFT_KERNELS(K)                                                                           \
+    (const void*)K<double, 0>, (const void*)K<float, 0>, (const void*)K<float, 1>, (const void*)K<float, 916>, \
+        (const void*)K<float, 1414>, (const void*)K<float, 1827>
+    const void* kernels[] = {MRP_FFT_KERNELS(k_fft_x_fwd), MRP_FFT_KERNELS(k_fft_y_fwd), MRP_FFT_KERNELS(k_fft_z_conv),
+                             MRP_FFT_KERNELS(k_fft_y_inv), MRP_FFT_KERNELS(k_fft_x_inv)};
+#undef MRP_FFT_KERNELS
     for (const void* k : kernels) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return MRP_OK;
 }

@@ -152,9 +152,10 @@ def test_coarse_solve(M):
 @pytest.mark.parametrize("n, nb, P", [(12, 3, 75), (8, 5, 81), (18, 3, 112), (10, 7, 144), (8, 7, 120),
                                        (16, 6, 196), (18, 6, 224)])
 def test_coarse_solve_lattices(n, nb, P):
-    """Odd and even padded lengths (radices 2, 3, 4, 5, 7): the FP64 level-0
-    solve against the oracle's convolution at 1e-12, and the FP32 solve of a
-    mixed-precision handle at 1e-5."""
+    """Odd and even padded lengths (radices 2, 3, 4, 5, 7; the FP32 lines of
+    P = 144 = 9 x 16 and 196 = 14 x 14 take the four-step build): the FP64
+    level-0 solve against the oracle's convolution at 1e-12, and the FP32
+    solve of a mixed-precision handle at 1e-5."""
     from paper_2512_08555_gb300.mrp import Solver
     desc = small_forest(nb=nb, n=n, max_level=0)
     s, o = _pair(desc, 4)
@@ -170,12 +171,13 @@ def test_coarse_solve_lattices(n, nb, P):
     assert _rel(m.field_get("U", 0).cpu().numpy(), o.U[0]) < 1e-5
 
 
-@pytest.mark.parametrize("n, nb, P", [(20, 7, 288), (18, 13, 480), (18, 14, 512)])
+@pytest.mark.parametrize("n, nb, P", [(20, 7, 288), (18, 13, 480), (18, 14, 512), (16, 15, 486)])
 def test_coarse_solve_f32_composite_radices(n, nb, P):
     """Lattices long enough for the FP32 lines' composite butterflies (P = 288:
-    radices 2 8 9 2; 480: 2 8 15 2; 512: 2 16 16): the FP32 level-0 solve at
-    sampled targets (interior nodes and the exterior ring) against the oracle's
-    brute-force sum h0^2 sum_s G(t - s) f(s) over the whole lattice, at 1e-5."""
+    radices 2 8 9 2; 480: 2 8 15 2; 512: 2 16 16) or with a four-step build
+    (486 = 18 x 27): the FP32 level-0 solve at sampled targets (interior nodes
+    and the exterior ring) against the oracle's brute-force sum
+    h0^2 sum_s G(t - s) f(s) over the whole lattice, at 1e-5."""
     from paper_2512_08555_gb300.mrp import Solver
     from oracle.lgf import direct_sum
     desc = small_forest(nb=nb, n=n, max_level=0)
