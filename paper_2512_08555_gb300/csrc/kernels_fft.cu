@@ -716,7 +716,8 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
 
 // ---------------------------------------------------------------- pass C (z forward, x G-hat, z inverse), lines (ky, kx)
 template <typename R, int PLAN>
-__global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g, FftLine<R> Lg) {
+__device__ __forceinline__ void z_conv_body(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g,
+                                            FftLine<R> Lg) {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char fsm[];
     C* sm = reinterpret_cast<C*>(fsm);
@@ -785,6 +786,14 @@ __global__ void k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __re
         const int z = pidx(g.out_lo[2] + t, g.Pz);
         spec[((size_t)z * g.Py + ky) * g.Kx + kx0 + ly] = sm[ly * P2 + qoff + z];
     }
+}
+
+// Registers capped for 3 CTAs of 256 threads per SM (the FP32 shared-memory
+// limit): the pass is bound by memory latency.
+template <typename R, int PLAN>
+__global__ void __launch_bounds__(256, 3)
+k_fft_z_conv(typename Cx<R>::T* __restrict__ spec, const R* __restrict__ ghat, Geo g, FftLine<R> Lg) {
+    z_conv_body<R, PLAN>(spec, ghat, g, Lg);
 }
 
 // ---------------------------------------------------------------- pass B' (y inverse), lines (output z, kx)
@@ -957,7 +966,19 @@ static void conv_passes(const Problem& p, const Geo& g, typename Cx<R>::T* spec,
     } while (0)
     MRP_FFT_LAUNCH(k_fft_x_fwd, Lx, (g.in_n[1] * g.in_n[2] + lx2 - 1) / lx2, smx, spec, src, g, Lx);
     MRP_FFT_LAUNCH(k_fft_y_fwd, Ly, dim3(kxb, g.in_n[2]), smy, spec, g, Ly);
-    MRP_FFT_LAUNCH(k_fft_z_conv, Lz, dim3(kxb, g.Py), smz, spec, ghat, g, Lz);
+    {
+        const int fz = F32 ? fourstep_plan(Lz.P) : 0;
+        const dim3 gz(kxb, g.Py);
+        if constexpr (F32) {
+            if (fz == 916) k_fft_z_conv<R, 916><<<gz, blk, smz, s>>>(spec, ghat, g, Lz);
+            else if (fz == 1414) k_fft_z_conv<R, 1414><<<gz, blk, smz, s>>>(spec, ghat, g, Lz);
+            else if (fz == 1827) k_fft_z_conv<R, 1827><<<gz, blk, smz, s>>>(spec, ghat, g, Lz);
+            else if (has_composite(Lz)) k_fft_z_conv<R, 1><<<gz, blk, smz, s>>>(spec, ghat, g, Lz);
+            else k_fft_z_conv<R, 0><<<gz, blk, smz, s>>>(spec, ghat, g, Lz);
+        } else {
+            k_fft_z_conv<R, 0><<<gz, blk, smz, s>>>(spec, ghat, g, Lz);
+        }
+    }
     MRP_FFT_LAUNCH(k_fft_y_inv, Ly, dim3(kxb, g.out_n[2]), smy, spec, g, Ly);
     MRP_FFT_LAUNCH(k_fft_x_inv, Lx, (g.out_n[1] * g.out_n[2] + lx2 - 1) / lx2, smx, dst, spec, g, Lx);
 #undef MRP_FFT_LAUNCH
@@ -1318,7 +1339,10 @@ int fft_plan(Handle& h) {
 #define MRP_FFT_KERNELS(K)                                                                           \
     (const void*)K<double, 0>, (const void*)K<float, 0>, (const void*)K<float, 1>, (const void*)K<float, 916>, \
         (const void*)K<float, 1414>, (const void*)K<float, 1827>
-    const void* kernels[] = {MRP_FFT_KERNELS(k_fft_x_fwd), MRP_FFT_KERNELS(k_fft_y_fwd), MRP_FFT_KERNELS(k_fft_z_conv),
+    const void* kernels[] = {MRP_FFT_KERNELS(k_fft_x_fwd), MRP_FFT_KERNELS(k_fft_y_fwd), (const void*)k_fft_z_conv<double, 0>,
+                             (const void*)k_fft_z_conv<float, 0>, (const void*)k_fft_z_conv<float, 1>,
+                             (const void*)k_fft_z_conv<float, 916>, (const void*)k_fft_z_conv<float, 1414>,
+                             (const void*)k_fft_z_conv<float, 1827>,
                              MRP_FFT_KERNELS(k_fft_y_inv), MRP_FFT_KERNELS(k_fft_x_inv)};
 #undef MRP_FFT_KERNELS
     for (const void* k : kernels) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
