@@ -696,8 +696,11 @@ __global__ void k_fft_y_fwd(typename Cx<R>::T* __restrict__ spec, Geo g, FftLine
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     C* a = sm + threadIdx.y * P2;
     C* b = a + P;
-    for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
-    __syncthreads();
+    // (four-step lines read only a[0 .. nz), the input itself where it starts at 0)
+    if (PLAN < 100 || g.in_lo[1] != 0) {
+        for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
+        __syncthreads();
+    }
     gather_lines<8, C>(
         fft_ly<R>() * g.in_n[1],
         [&](int e) {
@@ -730,8 +733,11 @@ __device__ __forceinline__ void z_conv_body(typename Cx<R>::T* __restrict__ spec
     C* a = sm + threadIdx.y * P2;
     C* b = a + P;
     const bool live = kx < g.Kx;
-    for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
-    __syncthreads();
+    // (four-step lines read only a[0 .. nz), the input itself where it starts at 0)
+    if (PLAN < 100 || g.in_lo[2] != 0) {
+        for (int j = threadIdx.x; j < P; j += blockDim.x) a[j] = C{R(0), R(0)};
+        __syncthreads();
+    }
     gather_lines<8, C>(
         fft_ly<R>() * g.in_n[2],
         [&](int e) {
