@@ -60,6 +60,8 @@ enum {
 
 enum { MRP_FP64 = 0, MRP_MIXED = 1 };
 enum { MRP_STOP_RESIDUAL = 0, MRP_STOP_CAUCHY = 1 };
+/* Flag of mrp_options.launch (see there). */
+enum { MRP_LAUNCH_NOSTAGE = 4096 };
 
 typedef struct {
     int32_t nb0[3];              /* level-0 blocks per axis (x, y, z) */
@@ -99,8 +101,11 @@ typedef struct {
     int32_t max_outer;           /* MRP_MIXED: refinement steps at most (0 = 12) */
     int32_t launch;              /* 0: the CTA size of each stencil kernel and level is chosen by
                                     timing at the first solve.  Otherwise that size (128, 256 or
-                                    512) for every kernel and level.  Results do not depend on
-                                    this choice. */
+                                    512) for every kernel and level; 128 or 256 may carry
+                                    MRP_LAUNCH_NOSTAGE, with which the Gauss-Seidel sweep and the
+                                    FP32 residual of block size 16 read the right-hand side from
+                                    global memory instead of staging it in shared memory.
+                                    Results do not depend on this choice. */
 } mrp_options;
 
 

@@ -869,7 +869,7 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
 template <int M, typename T, int I, int NC>
 __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const T* __restrict__ U,
                                                         const T* __restrict__ F, const T* __restrict__ Uc, LevelView lk,
-                                                        int n_arg, T scale, const int* __restrict__ order) {
+                                                        int n_arg, T scale, const int* __restrict__ order, int stage) {
     const int n = NC ? NC : n_arg;    // NC: block size fixed at compile time (0: runtime)
     extern __shared__ __align__(16) unsigned char fz_smem[];
     T* su = reinterpret_cast<T*>(fz_smem);
@@ -883,6 +883,34 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
     record_prologue_own(hs, lk, b, su, U, n, sp);
     const size_t n3 = (size_t)n * n * n;
     if constexpr (NC != 0 && sizeof(T) == 4) {
+        const int Fp = split_fp(n, 4), Fr = split_fr(n, 4), F3 = split_f3(n, 4);
+        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2, NU = NP / 2;
+        auto lpair = [&](const Col& c, int b0, T& la, T& lb) {
+            const int d = c.dX + c.dY + c.dZ;
+            const f2_t l = f2fma(f2splat(float(LW<M>::c)), f2pk(su[b0 + d], su[b0 + 1 + d]),
+                                 offc2<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2));
+            f2up(l, la, lb);
+        };
+        if (!stage) {
+            // F read and R written in global memory by the pairs themselves
+            // (no staging round trip; the same arithmetic as below)
+            build_halo<T, I, true, false>(su, pool, patch, hs.rec, U, Uc, lk, b, n, sp);
+            const T* Fb = F + b * n3;
+            T* Rb = R + b * n3;
+#pragma unroll
+            for (int col = 0; col < 8; ++col) {
+                const Col c = colour(col, sp, n);
+                for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+                    const Pair q = pair_of(p);
+                    T la, lb;
+                    lpair(c, c.cb + q.l * sp.H2 + q.j * sp.H + q.i, la, lb);
+                    const int gi = ((2 * q.l) * n + 2 * q.j) * n + 2 * q.i + c.fo;
+                    Rb[gi] = Fb[gi] - scale * la;
+                    Rb[gi + 2] = Fb[gi + 2] - scale * lb;
+                }
+            }
+            return;
+        }
         // F staged in shared memory in the colour split (as the smoother's),
         // over the interpolation scratch: copied with the box where the block
         // has no interpolated regions, after the ghost layer otherwise.  Each
@@ -898,14 +926,6 @@ __global__ void __launch_bounds__(512) k_residual_fused(T* __restrict__ R, const
             cp_async_wait<0>();
             __syncthreads();
         }
-        const int Fp = split_fp(n, 4), Fr = split_fr(n, 4), F3 = split_f3(n, 4);
-        constexpr int NP = (NC / 2) * (NC / 2) * (NC / 2) / 2, NU = NP / 2;
-        auto lpair = [&](const Col& c, int b0, T& la, T& lb) {
-            const int d = c.dX + c.dY + c.dZ;
-            const f2_t l = f2fma(f2splat(float(LW<M>::c)), f2pk(su[b0 + d], su[b0 + 1 + d]),
-                                 offc2<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2));
-            f2up(l, la, lb);
-        };
 #pragma unroll
         for (int col = 0; col < 8; ++col) {
             const Col c = colour(col, sp, n);
@@ -1677,10 +1697,10 @@ static void smooth_m(T* Uout, const T* Uin, const T* F, const T* Uc, const Level
 }
 template <int M, typename T>
 static void residual_m(T* R, const T* U, const T* F, const T* Uc, const LevelView& lk, int n, T scale, int ct, size_t sm,
-                       cudaStream_t s) {
+                       int stage, cudaStream_t s) {
     constexpr int I = M + 2;
-    if (n == NC_FIXED) k_residual_fused<M, T, I, NC_FIXED><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, scale, lk.order);
-    else k_residual_fused<M, T, I, 0><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, scale, lk.order);
+    if (n == NC_FIXED) k_residual_fused<M, T, I, NC_FIXED><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, scale, lk.order, stage);
+    else k_residual_fused<M, T, I, 0><<<lk.nb, ct, sm, s>>>(R, U, F, Uc, lk, n, scale, lk.order, stage);
 }
 template <int M, typename T>
 static void fas_m(T* F, T* H, const T* U, const T* Uc, const LevelView& lk, int n, T scale, int ct, size_t sm,
@@ -1730,12 +1750,15 @@ void launch_residual_fused(T* R, const T* U, const T* F, const T* Uc, LevelView 
                            double inv_h2, int nt, cudaStream_t s) {
     if (lk.nb == 0) return;
     attrs_residual<T>();
-    // FP32 block size 16 stages F over the interpolation scratch (fmode-1 sizing)
-    const size_t sm = fused_smem<T>(n, M + 2, (sizeof(T) == 4 && n == NC_FIXED) ? 1 : 0);
-    const int ct = cta_size_fixed(n, nt, sizeof(T) == 4);
-    if (M == 2) residual_m<2, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, s);
-    if (M == 4) residual_m<4, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, s);
-    if (M == 6) residual_m<6, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, s);
+    // FP32 block size 16 stages F over the interpolation scratch (fmode-1
+    // sizing), unless the CTA choice carries SMOOTH_NOSTAGE (F read and R
+    // written in global memory by the pairs)
+    const int stage = (sizeof(T) == 4 && n == NC_FIXED && !(nt & SMOOTH_NOSTAGE)) ? 1 : 0;
+    const size_t sm = fused_smem<T>(n, M + 2, stage);
+    const int ct = cta_size_fixed(n, nt & SMOOTH_NT_MASK, sizeof(T) == 4);
+    if (M == 2) residual_m<2, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<2>::den), ct, sm, stage, s);
+    if (M == 4) residual_m<4, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<4>::den), ct, sm, stage, s);
+    if (M == 6) residual_m<6, T>(R, U, F, Uc, lk, n, T(inv_h2 / LW<6>::den), ct, sm, stage, s);
 }
 
 template <typename T>

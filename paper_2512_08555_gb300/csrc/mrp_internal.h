@@ -373,10 +373,11 @@ void launch_prolong(T* Uf, const T* Uc, const T* Hc, LevelView lf, LevelView lc,
 template <typename T>
 void launch_coarse_solve_t(const Handle& h, const T* F0, T* U0, cudaStream_t s);
 // stencil kernels with the ghost layer built in shared memory (kernels_fused.cuh, fused_*.cu);
-// Smoother launch choice (the `nt` argument of launch_smooth_fused): the CTA
-// size in the low bits; SMOOTH_NOSTAGE reads the right-hand side from global
-// memory where it is used instead of staging it in shared memory (less shared
-// memory per CTA, so more CTAs per SM).
+// Smoother and residual launch choice (the `nt` argument of
+// launch_smooth_fused and launch_residual_fused): the CTA size in the low
+// bits; SMOOTH_NOSTAGE reads the right-hand side from global memory where it
+// is used instead of staging it in shared memory (less shared memory per
+// CTA, so more CTAs per SM; the FP32 residual also writes R there).
 constexpr int SMOOTH_NT_MASK = 0xFFF, SMOOTH_NOSTAGE = 1 << 12;
 // fused_smem_bytes: their dynamic shared memory for block size n, order M and
 // element size el (bytes), without a staged right-hand side

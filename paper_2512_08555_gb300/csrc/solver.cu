@@ -613,7 +613,8 @@ struct SolveState {
 template <typename T>
 static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     const std::vector<int> cta = {128, 256, 512};
-    // the smoother may also read its right-hand side from global memory
+    // the smoother (and the FP32 residual) may also read the right-hand side
+    // from global memory
     std::vector<int> smooth_cand = cta;
     for (int c : {128, 256}) smooth_cand.push_back(c | SMOOTH_NOSTAGE);
     constexpr int pi = pidx<T>();
@@ -642,7 +643,7 @@ static void tune_precision(Handle& h, cudaStream_t s, cudaEvent_t e0, cudaEvent_
                 launch_smooth_fused<T>(ualt<T>(h, k), ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), lv.view(),
                                        view_or_empty(h, k - 1), h.n, h.M, hk * hk, nt, s);
             });
-            h.nt_res[pi][k] = pick([&](int nt) {
+            h.nt_res[pi][k] = pick_from(sizeof(T) == 4 ? smooth_cand : cta, [&](int nt) {
                 launch_residual_fused<T>(fld<T>(h, k).R, ucur<T>(h, k), fld<T>(h, k).F, ucoarse<T>(h, k), lv.view(),
                                          view_or_empty(h, k - 1), h.n, h.M, 1.0 / (hk * hk), nt, s);
             });
@@ -672,10 +673,13 @@ int autotune(Handle& h, cudaStream_t s) {
     if (h.tuned) return MRP_OK;
     tune_defaults(h);
     if (h.launch_override) {
-        const int ct = h.launch_override;
+        // the NOSTAGE flag applies to the kernels that stage a right-hand side
+        const int ct = h.launch_override & ~MRP_LAUNCH_NOSTAGE;
+        const int cs = (h.launch_override & MRP_LAUNCH_NOSTAGE) ? (ct | SMOOTH_NOSTAGE) : ct;
         for (int p = 0; p < 2; ++p)
             for (int k = 0; k < Handle::MAXL; ++k) {
-                h.nt_smooth[p][k] = h.nt_res[p][k] = h.nt_fas[p][k] = ct;
+                h.nt_smooth[p][k] = h.nt_res[p][k] = cs;
+                h.nt_fas[p][k] = ct;
                 h.nt_leafres[k] = ct;
             }
         h.tuned = true;
@@ -902,7 +906,11 @@ int mrp_create(mrp_handle** out, const mrp_forest* forests, int32_t n_forests, c
     if (opt->stop_rule != MRP_STOP_RESIDUAL && opt->stop_rule != MRP_STOP_CAUCHY) return MRP_ERR_INVALID_ARG;
     if (opt->precision != MRP_FP64 && opt->precision != MRP_MIXED) return MRP_ERR_INVALID_ARG;
     if (opt->inner_cycles < 0 || opt->max_outer < 0) return MRP_ERR_INVALID_ARG;
-    if (opt->launch != 0 && opt->launch != 128 && opt->launch != 256 && opt->launch != 512) return MRP_ERR_INVALID_ARG;
+    {
+        const int ct = opt->launch & ~MRP_LAUNCH_NOSTAGE;
+        const bool nostage = (opt->launch & MRP_LAUNCH_NOSTAGE) != 0;
+        if (opt->launch != 0 && ct != 128 && ct != 256 && (ct != 512 || nostage)) return MRP_ERR_INVALID_ARG;
+    }
     // problems (forest, component) in the caller's layout order, grouped by block size
     std::map<int, std::vector<ProblemDesc>> by_n;
     int64_t off = 0;

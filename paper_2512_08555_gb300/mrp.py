@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmrp.so")
 
 MRP_OK = 0
 MRP_ERR_NOT_CONVERGED = 5
+MRP_LAUNCH_NOSTAGE = 4096      # flag of the launch option (include/mrp.h)
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid forest", 3: "CUDA error", 4: "out of memory",
           5: "not converged", 6: "timeout", 7: "numerical", 9: "unsupported",
           10: "too large for the fixed scratch"}

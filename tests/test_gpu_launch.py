@@ -2,10 +2,12 @@
 
 The stencil kernels' CTA size only changes which thread computes which node
 (for block size 16 in FP32, a 128-thread CTA gives each thread two
-z-adjacent node pairs of a colour, a 256-thread CTA one): every node's
-arithmetic and operand order stay the same.  So solves under every fixed launch choice and under the autotuned one
-must agree bit for bit; the generic kernels are the ones the parity tests
-compare with the oracle.
+z-adjacent node pairs of a colour, a 256-thread CTA one), and reading the
+right-hand side from global memory instead of a staged copy
+(MRP_LAUNCH_NOSTAGE) only where it comes from: every node's arithmetic and
+operand order stay the same.  So solves under every fixed launch choice and
+under the autotuned one must agree bit for bit; the generic kernels are the
+ones the parity tests compare with the oracle.
 """
 import numpy as np
 import pytest
@@ -27,11 +29,11 @@ def _built():
 
 @pytest.mark.parametrize("M", [4, 6])
 def test_launch_choices_agree_bitwise(M):
-    from paper_2512_08555_gb300.mrp import Solver
+    from paper_2512_08555_gb300.mrp import Solver, MRP_LAUNCH_NOSTAGE
     desc, src = synth.config2(0)                # 16^3 blocks; interface and other blocks on levels 1, 2
     f = torch.from_numpy(synth.sample_leaves(desc, src)).cuda()
     ref = None
-    for launch in (128, 256, 512, 0):
+    for launch in (128, 256, 512, 128 | MRP_LAUNCH_NOSTAGE, 256 | MRP_LAUNCH_NOSTAGE, 0):
         s = Solver(desc, order=M, tol=1e-10, max_cycles=60, precision="mixed", launch=launch)
         u, st = s.solve(f)
         ug, _ = s.solve_graph(f)
@@ -46,7 +48,7 @@ def test_launch_choices_agree_bitwise(M):
 def test_bad_launch_rejected():
     from paper_2512_08555_gb300.mrp import Solver, MrpError
     desc = synth.uniform_forest((2, 2, 2), 16, (0, 0, 0), 0.1)
-    for bad in (100, 128 | (1 << 12)):
+    for bad in (100, 512 | (1 << 12), 1 << 12, 128 | (1 << 13)):
         with pytest.raises(MrpError) as e:
             Solver(desc, order=4, launch=bad)
         assert e.value.status == 1
