@@ -49,10 +49,10 @@ TOL = 1e-10
 MAX_CYCLES = 60
 STENCIL_POINTS = {2: 7, 4: 19, 6: 27}
 # DRAM bytes (read + write) of one launch of the FP32 smoother, per node it
-# updates: 348,188,672 B over the 23,625,728 nodes of the level-4 launch of the
+# updates: 348,225,536 B over the 23,625,728 nodes of the level-4 launch of the
 # 5-level forest on 5^3 level-0 blocks, 128-thread CTAs, from one ncu capture of
 # the current kernel (the smoother's summary under profiles/ gives the command).
-SMOOTH32_DRAM_BYTES_PER_NODE = 348188672 / 23625728
+SMOOTH32_DRAM_BYTES_PER_NODE = 348225536 / 23625728
 
 
 def _hbm_peak():

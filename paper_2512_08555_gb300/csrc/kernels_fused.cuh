@@ -758,16 +758,12 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
     const int b = order ? order[blockIdx.x] : blockIdx.x;
     record_prologue_own(hs, lk, b, su, Uin, n, sp);
     // the right-hand side copy overlaps the box copy (build_halo waits for
-    // both), except on interface blocks in fmode 1, where it follows the
-    // ghost layer
-    const bool early = fmode == 2 || (fmode == 1 && hs.rec[REC_NREG] == 0);
-    if (early) load_rhs(fs, F, b, n);
+    // both); in fmode 1 it goes over the interpolation scratch, so an
+    // interface block, which needs that scratch first, reads its right-hand
+    // side from global memory instead (fm = 0)
+    const int fm = (fmode == 1 && hs.rec[REC_NREG] != 0) ? 0 : fmode;
+    if (fm) load_rhs(fs, F, b, n);
     build_halo<T, I, true, sizeof(T) == 8>(su, pool, patch, hs.rec, Uin, Uc, lk, b, n, sp);
-    if (fmode == 1 && !early) {
-        load_rhs(fs, F, b, n);
-        cp_async_wait<0>();
-        __syncthreads();
-    }
     const T* Fb = F + (size_t)b * n * n * n;
     const int Fp = split_fp(n, (int)sizeof(T)), Fr = split_fr(n, (int)sizeof(T)), F3 = split_f3(n, (int)sizeof(T));
     const T inv_c = T(1) / T(LW<M>::c);
@@ -788,7 +784,7 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
                 const Pair q = pair_of(threadIdx.x);
                 const int b0 = c.cb + q.l * sp.H2 + q.j * sp.H + q.i, b1 = b0 + sp.H2;
                 T fa0, fb0, fa1, fb1;
-                if (fmode) {
+                if (fm) {
                     const int fi = col * F3 + q.l * Fp + q.j * Fr + q.i;
                     fa0 = fs[fi]; fb0 = fs[fi + 1];
                     fa1 = fs[fi + Fp]; fb1 = fs[fi + Fp + 1];
@@ -813,7 +809,7 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
                 const int i = q.i, j = q.j, l = q.l;
                 const int b0 = c.cb + l * sp.H2 + j * sp.H + i;
                 T fa, fb;
-                if (fmode) {
+                if (fm) {
                     const int fi = col * F3 + l * Fp + j * Fr + i;
                     fa = fs[fi];
                     fb = fs[fi + 1];
@@ -839,7 +835,7 @@ __global__ void __launch_bounds__(512) k_smooth_fused(T* __restrict__ Uout, cons
                 if (k < cs.cnt) {
                     const Node d = node_of(cs.q[k], sp, n, Fp, Fr);
                     const int b0 = c.cb + d.b0;
-                    const T fv = fmode ? fs[col * F3 + d.fs] : Fb[d.f + c.fo];
+                    const T fv = fm ? fs[col * F3 + d.fs] : Fb[d.f + c.fo];
                     su[b0 + c.dX + c.dY + c.dZ] =
                         (h2den * fv - offc_s<M>(su, b0, c.dX, c.dY, c.dZ, sp.H, sp.H2)) * inv_c;
                 }
