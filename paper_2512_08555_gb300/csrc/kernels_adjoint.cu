@@ -69,12 +69,76 @@ __global__ void k_stencil_T(T* __restrict__ out, const T* __restrict__ lam, T* _
     for (int t = threadIdx.x; t < A3; t += blockDim.x) lp[t] = T(0);
     __syncthreads();
     const unsigned mn = magic_of(n), mn2 = magic_of(n * n), mS = magic_of(S);
+    __shared__ unsigned s_emax;
+    if (threadIdx.x == 0) s_emax = 0u;
+    unsigned em = 0;                  // largest exponent field of the staged values (FP64)
     for (int t = threadIdx.x; t < n3; t += blockDim.x) {
         const int z = fdiv(t, mn2), r = t - z * n * n, y = fdiv(r, mn), x = r - y * n;
-        lp[(z + 2) * A2 + (y + 2) * A + x + 2] = lb[t];
+        const T v = lb[t];
+        lp[(z + 2) * A2 + (y + 2) * A + x + 2] = v;
+        if constexpr (sizeof(T) == 8) em = max(em, ((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
     }
     __syncthreads();
     T* ob = out + (size_t)b * S3;
+    if constexpr (sizeof(T) == 8) {
+        // The same plane sums in 64-bit fixed point (as the FP64 leaf
+        // residual's): every staged value becomes trunc(lambda 2^s) with s set
+        // by the largest exponent field E, so that the integer weights (their
+        // magnitudes summing to at most 2^G) cannot overflow; the exact sum is
+        // rounded once to double and scaled by 2^-s, one FP64 operation per
+        // node.  Blocks with Inf or NaN, only zeros, or extreme exponents keep
+        // the FP64 sums below.
+        constexpr int G = M == 6 ? 8 : 6;
+        em = __reduce_max_sync(0xffffffffu, em);
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_emax, em);
+        __syncthreads();
+        const int E = (int)s_emax;
+        if (E >= 128 && E <= 1900) {
+            const int shb = 9 - G - E;
+            for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+                const int z = fdiv(t, mn2), r = t - z * n * n, y = fdiv(r, mn), x = r - y * n;
+                T* a = lp + (z + 2) * A2 + (y + 2) * A + x + 2;
+                *a = __longlong_as_double(to_fixed(__double_as_longlong(*a), shb));
+            }
+            __syncthreads();
+            const double scale2 = (double)scale * __longlong_as_double((long long)(E + G - 1084 + 1023) << 52);
+            constexpr long long wc = (long long)W::c, wf = (long long)W::f, we = (long long)W::e, wk = (long long)W::k;
+            for (int r = threadIdx.x; r < S2; r += blockDim.x) {
+                const int Y = fdiv(r, mS), X = r - Y * S;
+                const T* c0 = lp + (Y + 1) * A + X + 1;
+                auto ld = [&](const T* q) { return __double_as_longlong(*q); };
+                auto plane = [&](int a, long long& P, long long& Q) {
+                    const T* q0 = c0 + a * A2;
+                    const long long u = ld(q0);
+                    const long long c = (ld(q0 - 1) + ld(q0 + 1)) + (ld(q0 - A) + ld(q0 + A));
+                    long long p = wf * u, q = wc * u + wf * c;
+                    if (we != 0 || wk != 0) {
+                        const long long d = (ld(q0 - 1 - A) + ld(q0 + 1 - A)) + (ld(q0 - 1 + A) + ld(q0 + 1 + A));
+                        p += we * c + wk * d;
+                        q += we * d;
+                    }
+                    P = p;
+                    Q = q;
+                };
+                long long P0, P1, Q1, Qg;
+                plane(0, P0, Qg);
+                plane(1, P1, Q1);
+                T* ocol = ob + Y * S + X;
+                for (int Z = 0; Z < S; ++Z) {
+                    long long P2, Q2;
+                    plane(Z + 2, P2, Q2);
+                    T* o = ocol + (size_t)Z * S2;
+                    *o = fma(scale2, i64_to_double_rn((P0 + P2) + Q1), *o);
+                    P0 = P1;
+                    P1 = P2;
+                    Q1 = Q2;
+                }
+            }
+            if (fadd)
+                for (int t = threadIdx.x; t < n3; t += blockDim.x) fadd[(size_t)b * n3 + t] += lb[t];
+            return;
+        }
+    }
     for (int r = threadIdx.x; r < S2; r += blockDim.x) {
         const int Y = fdiv(r, mS), X = r - Y * S;
         // padded coordinates of box node (X, Y, Z): (X + 1, Y + 1, Z + 1)
