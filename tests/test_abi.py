@@ -141,3 +141,21 @@ def test_bad_options_rejected(lib):
     op = _opts()
     op.max_cycles = 0
     assert lib.mrp_create(ctypes.byref(h), ctypes.byref(fd), 1, ctypes.byref(op)) == 1
+
+
+@pytest.mark.parametrize("launch", [100, 129, 512 | 4096, 4096, 128 | 8192, 64])
+def test_bad_launch_choices_rejected(lib, launch):
+    """mrp_options.launch takes 0, 128, 256 or 512, and 128 or 256 with MRP_LAUNCH_NOSTAGE (4096) only."""
+    from paper_2512_08555_gb300 import synth
+    desc = synth.uniform_forest((2, 2, 2), 8, (0, 0, 0), 0.1)
+    fd, keep = _forest_struct([2, 2, 2], 8, desc.leaf_level, desc.leaf_ijk)
+    h = ctypes.c_void_p()
+    op = _opts()
+    op.launch = launch
+    assert lib.mrp_create(ctypes.byref(h), ctypes.byref(fd), 1, ctypes.byref(op)) == 1 and not h
+
+
+def test_launch_flag_matches_the_header():
+    from paper_2512_08555_gb300.mrp import MRP_LAUNCH_NOSTAGE
+    hdr = open(os.path.join(ROOT, "include", "mrp.h")).read()
+    assert f"MRP_LAUNCH_NOSTAGE = {MRP_LAUNCH_NOSTAGE}" in hdr
